@@ -1,0 +1,184 @@
+/*
+ * trimwq.h -- C-ABI of the GB300 (sm_103a) library that forms the Galerkin mass
+ * matrix of a trimmed bi-variate B-spline patch by row-wise weighted quadrature
+ * with sum factorisation, after Marussig, "Fast formation and assembly of
+ * isogeometric Galerkin matrices for trimmed patches" (arXiv 2101.08053).
+ *
+ * Conventions
+ *  - Every entry point returns 0 (TW_OK) or a negative TW_E* code; the text of
+ *    the last error of the calling thread is returned by tw_last_error().
+ *  - Descriptors (tw_patch_desc, tw_func) and the arrays they point to are HOST
+ *    memory owned by the caller; they are copied during the call.
+ *  - Output arrays passed to tw_form_mass, tw_rhs, tw_l2_project, tw_states and
+ *    tw_patch_table are DEVICE memory owned by the caller (e.g. torch tensors).
+ *  - A tw_patch owns its device tables (allocated in tw_patch_create, freed in
+ *    tw_patch_destroy).  It is not thread-safe; distinct patches are.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  All work is
+ *    ordered on it; calls that must size outputs synchronise it (documented).
+ *  - There is no CPU fallback: without a usable sm_103a device every call that
+ *    touches the GPU returns TW_ECUDA.
+ */
+#ifndef TRIMWQ_H
+#define TRIMWQ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define TW_OK 0
+#define TW_EINVAL -1        /* malformed descriptor or argument              */
+#define TW_EUNSUPPORTED -2  /* valid input outside what this build handles   */
+#define TW_ENOMEM -3        /* device allocation failed                      */
+#define TW_ECUDA -4         /* CUDA runtime error, or a kernel's error flag   */
+#define TW_ENOCONV -5       /* CG did not reach the tolerance within maxit   */
+
+/* ---- descriptor enums ---- */
+/* trimming curve (Sect. 2.2): a closed curve in the parameter space */
+#define TW_TRIM_NONE 0
+#define TW_TRIM_CIRCLE 1   /* params: cx, cy, r                                  */
+#define TW_TRIM_ELLIPSE 2  /* params: cx, cy, a, b, phi (semi-axes, rotation)    */
+#define TW_TRIM_BSPLINE3 3 /* periodic uniform cubic B-spline, nctrl x 2 points,
+                              C(tau) = sum_m P_m N3((tau - m) mod nctrl)          */
+/* geometry map x(xi) */
+#define TW_GEOM_IDENTITY 0
+#define TW_GEOM_SPLINE 1   /* control net in the patch basis, n2 x n1 x 2, i1 fastest */
+/* the coefficient c(xi) of Eq. 6 */
+#define TW_COEF_ONE 0      /* c = 1                                             */
+#define TW_COEF_DETJ 1     /* c = det J (pull-back of the physical mass matrix)  */
+#define TW_COEF_DENSITY 2  /* c = rho(xi) det J, rho a tensor B-spline           */
+/* treatment of cut basis functions */
+#define TW_METHOD_GAUSS 0  /* element-wise Gauss for every row (the paper's reference, Sect. 4) */
+#define TW_METHOD_HYBRID 1 /* WQ + sum factorisation for interior rows; Gauss on S^r and the
+                              cut-element rule on S^t for cut rows (Sect. 3.2, Eq. 8)           */
+#define TW_METHOD_DWQ 2    /* discontinuous WQ on a regular rectangle of S^r, Gauss on the rest
+                              of S^r, cut rule on S^t (Sect. 3.3)                               */
+#define TW_METHOD_NAIVE 3  /* WQ with c zeroed off S^r plus the cut rule: Table 1's negative control */
+/* precision of the contraction (tw_form_mass) */
+#define TW_PREC_FP64 0     /* val is double*                                     */
+#define TW_PREC_FP32 1     /* val is float*; tables rounded to FP32, FP32 FMA     */
+/* target functions for the L2 projection (Sect. 4.2), evaluated at x(xi) */
+#define TW_FUNC_SPLINE 0   /* sum_k a_k N_k(xi): own tensor spline (knots/p/coef) */
+#define TW_FUNC_SINSIN 1   /* sin(a x) sin(b y), prm = a, b                       */
+#define TW_FUNC_SINCOS 2   /* sin(a x) cos(b y), prm = a, b                       */
+#define TW_FUNC_GAUSS 3    /* exp(-k |x - (x0, y0)|^2), prm = k, x0, y0           */
+
+/* element / function states (Sect. 2.2, Eq. 8) */
+#define TW_ELEM_INVISIBLE 0
+#define TW_ELEM_REGULAR 1
+#define TW_ELEM_CUT 2
+#define TW_FUNC_EXTERIOR 0
+#define TW_FUNC_INTERIOR 1
+#define TW_FUNC_CUT 2
+
+/* Patch descriptor.  Field layout is shared with the CPU oracle's descriptor
+ * so that one seeded generator can fill both; the values are the contract.
+ *  p[d]          degree per direction, 1..6; p[0] must equal p[1]
+ *  knots[d]      open knot vector (p+1 equal end knots, strictly increasing
+ *                simple interior knots), nknots[d] = n_d + p + 1, >= 2 elements
+ *  trim_*        the trimming curve; keep_inside = 0 keeps the outside (a hole)
+ *  geom_ctrl     n2*n1*2 doubles for TW_GEOM_SPLINE, else NULL
+ *  dens_*        density spline for TW_COEF_DENSITY
+ *  cut_order     Gauss order on the pieces of a cut element (0 -> p+1)
+ *  stream        stream for the set-up kernels */
+typedef struct {
+  int p[2];
+  int nknots[2];
+  const double *knots[2];
+  int trim_kind;
+  int trim_keep_inside;
+  double trim_params[6];
+  int trim_nctrl;
+  const double *trim_ctrl;
+  int geom_kind;
+  const double *geom_ctrl;
+  int coef_kind;
+  int dens_p[2];
+  int dens_nknots[2];
+  const double *dens_knots[2];
+  const double *dens_coef;
+  int method;
+  int cut_order;
+  void *stream;
+} tw_patch_desc;
+
+typedef struct {
+  int kind;
+  double prm[4];
+  int p[2];
+  int nknots[2];
+  const double *knots[2];
+  const double *coef;
+} tw_func;
+
+typedef struct tw_patch tw_patch;
+
+/* Build every patch table on the device (Sect. 2.1-3.3):
+ *   WQ points (one rule per test function, Eq. 4) and their weights from the
+ *   exactness system Eq. 5 (min-norm solution), basis tables, c at the WQ grid,
+ *   classification of elements and functions (Sect. 2.2), the cut-element rules
+ *   (Sect. 3.1), the DWQ rules (Sect. 3.3, Eqs. 9-10) and the CSR pattern.
+ * Synchronises desc->stream once at the end (sizes).  Returns TW_EINVAL for a
+ * malformed descriptor, TW_EUNSUPPORTED for p outside 1..6, p[0] != p[1] or a
+ * curve too complex for one element, TW_ENOMEM / TW_ECUDA otherwise. */
+int tw_patch_create(const tw_patch_desc *desc, tw_patch **out);
+int tw_patch_destroy(tw_patch *patch);
+
+/* Host copy of the patch sizes:
+ *  [0] n1 [1] n2 [2] nel1 [3] nel2 [4] nq1 [5] nq2 [6] n_rows [7] nnz
+ *  [8] cut elements [9] cut functions [10] cut-rule points [11] DWQ rows
+ *  [12] disc knots (both directions) [13] interior rows [14] p [15] method */
+int tw_patch_info(const tw_patch *patch, int64_t *info16);
+
+/* Form the mass matrix (Eqs. 6-7) into caller-owned device CSR buffers:
+ *   row_ptr[n_rows+1] (int64), col[nnz] (int32, active index, ascending per row),
+ *   val[nnz] (double for TW_PREC_FP64, float for TW_PREC_FP32).
+ * Rows and columns are the active (non-exterior) functions numbered by
+ * ascending i2*n1 + i1; the pattern holds every active pair with
+ * |i1-j1| <= p and |i2-j2| <= p.  The result is deterministic (each entry is
+ * summed by one thread in a fixed order).  Asynchronous on `stream`. */
+int tw_form_mass(tw_patch *patch, int precision, int64_t *row_ptr, int32_t *col, void *val,
+                 void *stream);
+
+/* Right-hand side b[n_rows] of the L2 projection: each row's own quadrature
+ * rule applied to f * c (Sect. 4.2).  Device output, asynchronous. */
+int tw_rhs(tw_patch *patch, const tw_func *f, double *b, void *stream);
+
+/* L2 projection: Jacobi-preconditioned CG on (M + M^T)/2 with the CSR produced
+ * by tw_form_mass (FP64) and the rhs of f, until ||r||/||b|| <= tol or maxit
+ * iterations.  u[n_rows] device output; *iters, *relres host outputs.
+ * Synchronises `stream` every few iterations.  TW_ENOCONV if not converged. */
+int tw_l2_project(tw_patch *patch, const tw_func *f, const int64_t *row_ptr, const int32_t *col,
+                  const double *val, double *u, double tol, int maxit, int *iters,
+                  double *relres, void *stream);
+
+/* Device copies of the classification: estate[nel1*nel2], fstate[n1*n2]
+ * (uint8, TW_ELEM_* / TW_FUNC_*), act[n1*n2] (int32 active index or -1). */
+int tw_states(const tw_patch *patch, uint8_t *estate, uint8_t *fstate, int32_t *act,
+              void *stream);
+
+/* Device copy of an internal table, for parity tests.  `which`:
+ *  0/1  WQ points of direction 0/1 (double, nq)
+ *  2/3  WQ weights of direction 0/1 (double, n x qmax, local point index)
+ *  4    c at the WQ grid (double, nq2 x nq1, k1 fastest)
+ *  5    cut-rule points (double, npts x 3: xi1, xi2, weight) in cut-element order
+ *  6    cut-rule offsets (int64, ncut+1) and 7 the cut element ids (int32, ncut)
+ *  8    DWQ choice per function (int32, n1*n2 x 4: kind1, s1, kind2, s2; -1 none)
+ *  9/10 Gauss-Legendre nodes / weights of order p+1 (double, p+1)
+ * *count receives the number of elements of the table; nothing is copied if
+ * dst is NULL or cap is too small (then TW_EINVAL). */
+int tw_patch_table(const tw_patch *patch, int which, void *dst, int64_t cap, int64_t *count,
+                   void *stream);
+
+/* Number of kernels this library has launched in this process. */
+int64_t tw_launch_count(void);
+
+const char *tw_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif

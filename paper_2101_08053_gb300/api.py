@@ -1,0 +1,275 @@
+"""Thin Python binding of libtrimwq (include/trimwq.h): argument marshalling
+only.  Every step of the method runs in the library's sm_103a kernels; PyTorch
+provides device memory and streams.  There is no CPU fallback: if the library
+or a CUDA device is missing, every call raises."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import _build
+
+TRIM = {"none": 0, "circle": 1, "ellipse": 2, "bspline3": 3}
+GEOM = {"identity": 0, "spline": 1}
+COEF = {"one": 0, "detj": 1, "density": 2}
+METHOD = {"gauss": 0, "hybrid": 1, "dwq": 2, "naive": 3}
+PREC = {"fp64": 0, "fp32": 1}
+FUNC = {"spline": 0, "sinsin": 1, "sincos": 2, "gauss": 3}
+ERRORS = {-1: "EINVAL", -2: "EUNSUPPORTED", -3: "ENOMEM", -4: "ECUDA", -5: "ENOCONV"}
+
+PD = C.POINTER(C.c_double)
+
+
+class TWError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (ERRORS.get(code, "?"), code, msg))
+        self.code = code
+
+
+class PatchDesc(C.Structure):
+    _fields_ = [
+        ("p", C.c_int * 2),
+        ("nknots", C.c_int * 2),
+        ("knots", PD * 2),
+        ("trim_kind", C.c_int),
+        ("trim_keep_inside", C.c_int),
+        ("trim_params", C.c_double * 6),
+        ("trim_nctrl", C.c_int),
+        ("trim_ctrl", PD),
+        ("geom_kind", C.c_int),
+        ("geom_ctrl", PD),
+        ("coef_kind", C.c_int),
+        ("dens_p", C.c_int * 2),
+        ("dens_nknots", C.c_int * 2),
+        ("dens_knots", PD * 2),
+        ("dens_coef", PD),
+        ("method", C.c_int),
+        ("cut_order", C.c_int),
+        ("stream", C.c_void_p),
+    ]
+
+
+class FuncDesc(C.Structure):
+    _fields_ = [
+        ("kind", C.c_int),
+        ("prm", C.c_double * 4),
+        ("p", C.c_int * 2),
+        ("nknots", C.c_int * 2),
+        ("knots", PD * 2),
+        ("coef", PD),
+    ]
+
+
+_lib = None
+
+
+def load(build: bool = True):
+    """Load libtrimwq.so (building it in-tree first if needed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build else _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError("libtrimwq.so is missing; run __graft_entry__.build()")
+    L = C.CDLL(path)
+    vp, i64p = C.c_void_p, C.POINTER(C.c_int64)
+    L.tw_patch_create.argtypes = [C.POINTER(PatchDesc), C.POINTER(C.c_void_p)]
+    L.tw_patch_destroy.argtypes = [vp]
+    L.tw_patch_info.argtypes = [vp, i64p]
+    L.tw_form_mass.argtypes = [vp, C.c_int, vp, vp, vp, vp]
+    L.tw_rhs.argtypes = [vp, C.POINTER(FuncDesc), vp, vp]
+    L.tw_l2_project.argtypes = [vp, C.POINTER(FuncDesc), vp, vp, vp, vp, C.c_double, C.c_int,
+                                C.POINTER(C.c_int), C.POINTER(C.c_double), vp]
+    L.tw_states.argtypes = [vp, vp, vp, vp, vp]
+    L.tw_patch_table.argtypes = [vp, C.c_int, vp, C.c_int64, i64p, vp]
+    L.tw_launch_count.restype = C.c_int64
+    L.tw_last_error.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def _check(rc):
+    if rc != 0:
+        raise TWError(rc, load().tw_last_error().decode())
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("trimwq needs a CUDA device (sm_103a); none is available")
+    return torch
+
+
+def _stream(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _pd(a):
+    return a.ctypes.data_as(PD)
+
+
+def make_patch_desc(spec, keep):
+    d = PatchDesc()
+    p = spec["p"]
+    for k in range(2):
+        U = _f64(spec["knots"][k])
+        keep.append(U)
+        d.p[k] = p
+        d.nknots[k] = len(U)
+        d.knots[k] = _pd(U)
+    t = spec["trim"]
+    d.trim_kind = TRIM[t["kind"]]
+    d.trim_keep_inside = int(bool(t.get("keep_inside", False)))
+    prm = list(t.get("params", [])) + [0.0] * 6
+    for k in range(6):
+        d.trim_params[k] = prm[k]
+    if t.get("ctrl") is not None:
+        ctrl = _f64(t["ctrl"])
+        keep.append(ctrl)
+        d.trim_nctrl = ctrl.shape[0]
+        d.trim_ctrl = _pd(ctrl)
+    g = spec["geom"]
+    d.geom_kind = GEOM[g["kind"]]
+    if g["kind"] == "spline":
+        net = _f64(g["ctrl"])
+        keep.append(net)
+        d.geom_ctrl = _pd(net)
+    c = spec["coef"]
+    d.coef_kind = COEF[c["kind"]]
+    if c["kind"] == "density":
+        for k in range(2):
+            V = _f64(c["knots"][k])
+            keep.append(V)
+            d.dens_p[k] = c["p"]
+            d.dens_nknots[k] = len(V)
+            d.dens_knots[k] = _pd(V)
+        dc = _f64(c["coef"])
+        keep.append(dc)
+        d.dens_coef = _pd(dc)
+    d.method = METHOD[spec["method"]]
+    d.cut_order = spec.get("cut_order", 0)
+    return d
+
+
+def make_func_desc(f, keep):
+    s = FuncDesc()
+    s.kind = FUNC[f["kind"]]
+    prm = list(f.get("prm", [])) + [0.0] * 4
+    for k in range(4):
+        s.prm[k] = prm[k]
+    if f["kind"] == "spline":
+        for k in range(2):
+            U = _f64(f["knots"][k])
+            keep.append(U)
+            s.p[k] = f["p"]
+            s.nknots[k] = len(U)
+            s.knots[k] = _pd(U)
+        cf = _f64(f["coef"])
+        keep.append(cf)
+        s.coef = _pd(cf)
+    return s
+
+
+class Patch:
+    """A trimmed patch with its device tables (tw_patch_create)."""
+
+    def __init__(self, spec, stream=None):
+        L = load()
+        _torch()
+        keep = []
+        d = make_patch_desc(spec, keep)
+        d.stream = _stream(stream)
+        h = C.c_void_p()
+        _check(L.tw_patch_create(C.byref(d), C.byref(h)))
+        self._h = h
+        info = np.zeros(16, dtype=np.int64)
+        _check(L.tw_patch_info(self._h, info.ctypes.data_as(C.POINTER(C.c_int64))))
+        self.info = info
+        (self.n1, self.n2, self.nel1, self.nel2, self.nq1, self.nq2, self.n_rows, self.nnz,
+         self.n_cut_elems, self.n_cut_fns, self.n_cut_pts, self.n_dwq_rows, self.n_discs,
+         self.n_interior, self.p, self.method) = [int(v) for v in info]
+        self.spec = spec
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().tw_patch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def alloc_csr(self, precision="fp64"):
+        torch = _torch()
+        dt = torch.float64 if precision == "fp64" else torch.float32
+        rp = torch.empty(self.n_rows + 1, dtype=torch.int64, device="cuda")
+        col = torch.empty(max(self.nnz, 1), dtype=torch.int32, device="cuda")
+        val = torch.empty(max(self.nnz, 1), dtype=dt, device="cuda")
+        return rp, col, val
+
+    def form_mass(self, precision="fp64", out=None, stream=None):
+        """tw_form_mass into (row_ptr, col, val) device tensors."""
+        rp, col, val = out if out is not None else self.alloc_csr(precision)
+        _check(load().tw_form_mass(self._h, PREC[precision], C.c_void_p(rp.data_ptr()),
+                                   C.c_void_p(col.data_ptr()), C.c_void_p(val.data_ptr()),
+                                   _stream(stream)))
+        return rp, col[:self.nnz], val[:self.nnz]
+
+    def rhs(self, f, stream=None):
+        torch = _torch()
+        keep = []
+        fd = make_func_desc(f, keep)
+        b = torch.empty(max(self.n_rows, 1), dtype=torch.float64, device="cuda")
+        _check(load().tw_rhs(self._h, C.byref(fd), C.c_void_p(b.data_ptr()), _stream(stream)))
+        return b[:self.n_rows]
+
+    def l2_project(self, f, csr, tol=1e-12, maxit=None, stream=None, check=True):
+        torch = _torch()
+        keep = []
+        fd = make_func_desc(f, keep)
+        rp, col, val = csr
+        u = torch.empty(max(self.n_rows, 1), dtype=torch.float64, device="cuda")
+        it = C.c_int(0)
+        rel = C.c_double(0)
+        rc = load().tw_l2_project(self._h, C.byref(fd), C.c_void_p(rp.data_ptr()),
+                                  C.c_void_p(col.data_ptr()), C.c_void_p(val.data_ptr()),
+                                  C.c_void_p(u.data_ptr()), tol,
+                                  int(maxit if maxit is not None else 10 * self.n_rows),
+                                  C.byref(it), C.byref(rel), _stream(stream))
+        if check:
+            _check(rc)
+        return u[:self.n_rows], it.value, rel.value
+
+    def states(self, stream=None):
+        torch = _torch()
+        es = torch.empty(self.nel1 * self.nel2, dtype=torch.uint8, device="cuda")
+        fs = torch.empty(self.n1 * self.n2, dtype=torch.uint8, device="cuda")
+        act = torch.empty(self.n1 * self.n2, dtype=torch.int32, device="cuda")
+        _check(load().tw_states(self._h, C.c_void_p(es.data_ptr()), C.c_void_p(fs.data_ptr()),
+                                C.c_void_p(act.data_ptr()), _stream(stream)))
+        return es, fs, act
+
+    def table(self, which, stream=None):
+        torch = _torch()
+        L = load()
+        n = C.c_int64(0)
+        _check(L.tw_patch_table(self._h, which, None, 0, C.byref(n), _stream(stream)))
+        dt = {6: torch.int64, 7: torch.int32, 8: torch.int32}.get(which, torch.float64)
+        t = torch.empty(max(n.value, 1), dtype=dt, device="cuda")
+        _check(L.tw_patch_table(self._h, which, C.c_void_p(t.data_ptr()), n.value, C.byref(n),
+                                _stream(stream)))
+        return t[:n.value]
+
+
+def launch_count() -> int:
+    return int(load().tw_launch_count())

@@ -1,0 +1,396 @@
+// tw_api.cu -- the C-ABI entry points of include/trimwq.h: descriptor
+// validation, device allocation of the patch tables and dispatch to the
+// set-up, formation and solver kernels.  Host code only orchestrates: every
+// step of the method runs in a kernel.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+
+#include "tw_internal.cuh"
+
+namespace tw {
+
+int64_t g_launches = 0;
+static thread_local char g_err[1024] = "";
+
+void set_error(const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+int check_cuda(cudaError_t e, const char *what) {
+  if (e == cudaSuccess) return 0;
+  set_error("%s: %s", what, cudaGetErrorString(e));
+  return TW_ECUDA;
+}
+
+void *dalloc(tw_patch *P, size_t bytes) {
+  if (P->nallocs >= (int)(sizeof(P->allocs) / sizeof(P->allocs[0]))) {
+    set_error("internal: too many device allocations for one patch");
+    return nullptr;
+  }
+  void *p = nullptr;
+  cudaError_t e = cudaMallocAsync(&p, bytes ? bytes : 16, P->stream);
+  if (e != cudaSuccess) {
+    set_error("device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+    return nullptr;
+  }
+  P->allocs[P->nallocs++] = p;
+  return p;
+}
+
+void release_to(tw_patch *P, int mark) {
+  while (P->nallocs > mark) cudaFreeAsync(P->allocs[--P->nallocs], P->stream);
+}
+
+static int wq_count(int p, int nel) { return 2 * (p + 1) + 2 * (nel - 2); }
+
+static int valid_open_knots(const double *U, int nk, int p, const char *what) {
+  if (!U) {
+    set_error("%s: knots pointer is NULL", what);
+    return 0;
+  }
+  int nel = nk - 2 * p - 1;
+  if (nel < 2) {
+    set_error("%s: need at least 2 elements (nknots = %d, p = %d)", what, nk, p);
+    return 0;
+  }
+  for (int k = 0; k < nk; k++)
+    if (!std::isfinite(U[k])) {
+      set_error("%s: knot %d is not finite", what, k);
+      return 0;
+    }
+  for (int k = 1; k <= p; k++)
+    if (U[k] != U[0] || U[nk - 1 - k] != U[nk - 1]) {
+      set_error("%s: knot vector is not open (p+1 equal end knots)", what);
+      return 0;
+    }
+  for (int k = p; k < nk - p - 1; k++)
+    if (!(U[k + 1] > U[k])) {
+      set_error("%s: interior knots must be strictly increasing (simple)", what);
+      return 0;
+    }
+  return 1;
+}
+
+}  // namespace tw
+
+using namespace tw;
+
+extern "C" const char *tw_last_error(void) { return g_err; }
+extern "C" int64_t tw_launch_count(void) { return g_launches; }
+
+extern "C" int tw_patch_destroy(tw_patch *P) {
+  if (!P) return TW_OK;
+  for (int k = P->nallocs - 1; k >= 0; k--) cudaFreeAsync(P->allocs[k], P->stream);
+  cudaStreamSynchronize(P->stream);
+  free(P);
+  return TW_OK;
+}
+
+extern "C" int tw_patch_create(const tw_patch_desc *desc, tw_patch **out) {
+  if (!desc || !out) {
+    set_error("tw_patch_create: NULL argument");
+    return TW_EINVAL;
+  }
+  *out = nullptr;
+  int p = desc->p[0];
+  if (p < 1 || p > TW_MAXP || desc->p[1] != p) {
+    set_error("tw_patch_create: degrees (%d, %d) unsupported (need p1 == p2 in 1..%d)",
+              desc->p[0], desc->p[1], TW_MAXP);
+    return TW_EUNSUPPORTED;
+  }
+  for (int d = 0; d < 2; d++)
+    if (!valid_open_knots(desc->knots[d], desc->nknots[d], p, d ? "knots[1]" : "knots[0]"))
+      return TW_EINVAL;
+  if (desc->trim_kind < TW_TRIM_NONE || desc->trim_kind > TW_TRIM_BSPLINE3) {
+    set_error("tw_patch_create: unknown trim_kind %d", desc->trim_kind);
+    return TW_EINVAL;
+  }
+  if (desc->trim_kind == TW_TRIM_CIRCLE && !(desc->trim_params[2] > 0)) {
+    set_error("tw_patch_create: circle radius must be > 0");
+    return TW_EINVAL;
+  }
+  if (desc->trim_kind == TW_TRIM_ELLIPSE && !(desc->trim_params[2] > 0 && desc->trim_params[3] > 0)) {
+    set_error("tw_patch_create: ellipse semi-axes must be > 0");
+    return TW_EINVAL;
+  }
+  if (desc->trim_kind == TW_TRIM_BSPLINE3 &&
+      (!desc->trim_ctrl || desc->trim_nctrl < 4 || desc->trim_nctrl > 4096)) {
+    set_error("tw_patch_create: spline curve needs 4..4096 control points");
+    return TW_EINVAL;
+  }
+  if (desc->geom_kind != TW_GEOM_IDENTITY && desc->geom_kind != TW_GEOM_SPLINE) {
+    set_error("tw_patch_create: unknown geom_kind %d", desc->geom_kind);
+    return TW_EINVAL;
+  }
+  if (desc->geom_kind == TW_GEOM_SPLINE && !desc->geom_ctrl) {
+    set_error("tw_patch_create: spline geometry without control net");
+    return TW_EINVAL;
+  }
+  if (desc->coef_kind < TW_COEF_ONE || desc->coef_kind > TW_COEF_DENSITY) {
+    set_error("tw_patch_create: unknown coef_kind %d", desc->coef_kind);
+    return TW_EINVAL;
+  }
+  if (desc->coef_kind == TW_COEF_DENSITY) {
+    for (int d = 0; d < 2; d++) {
+      int q = desc->dens_p[d];
+      if (q < 0 || q > TW_MAXP || !desc->dens_coef ||
+          !valid_open_knots(desc->dens_knots[d], desc->dens_nknots[d], q, "density knots"))
+        return TW_EINVAL;
+    }
+  }
+  if (desc->method < TW_METHOD_GAUSS || desc->method > TW_METHOD_NAIVE) {
+    set_error("tw_patch_create: unknown method %d", desc->method);
+    return TW_EINVAL;
+  }
+  if (desc->cut_order < 0 || desc->cut_order > 64) {
+    set_error("tw_patch_create: cut_order must be in 0..64");
+    return TW_EINVAL;
+  }
+  int dev_count = 0;
+  if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count == 0) {
+    set_error("tw_patch_create: no CUDA device");
+    return TW_ECUDA;
+  }
+
+  tw_patch *P = (tw_patch *)calloc(1, sizeof(tw_patch));
+  P->p = p;
+  P->method = desc->method;
+  P->qc = desc->cut_order > 0 ? desc->cut_order : p + 1;
+  P->stream = (cudaStream_t)desc->stream;
+  int rc = TW_ENOMEM;
+  cudaStream_t st = P->stream;
+#define ALLOC(ptr, T, n)                                   \
+  do {                                                     \
+    (ptr) = (T *)dalloc(P, sizeof(T) * (size_t)(n));       \
+    if (!(ptr)) goto fail;                                 \
+  } while (0)
+  {
+    double *hbp = nullptr;
+    for (int d = 0; d < 2; d++) {
+      Dir &D = P->d[d];
+      D.p = p;
+      D.nk = desc->nknots[d];
+      D.n = D.nk - p - 1;
+      D.nel = D.n - p;
+      D.nq = wq_count(p, D.nel);
+      D.qmax = 0;
+      for (int i = 0; i < D.n; i++) {
+        int lo = i - p < 0 ? 0 : i - p, hi = i < D.nel - 1 ? i : D.nel - 1;
+        auto off = [&](int e) {
+          return e <= 0 ? 0 : (e >= D.nel ? D.nq : (p + 1) + 2 * (e - 1));
+        };
+        int c = off(hi + 1) - off(lo);
+        if (c > D.qmax) D.qmax = c;
+      }
+      if (D.qmax > TW_QMAX) {
+        set_error("tw_patch_create: %d WQ points in one support exceed %d", D.qmax, TW_QMAX);
+        rc = TW_EUNSUPPORTED;
+        goto fail;
+      }
+      int W = 2 * p + 1;
+      ALLOC(D.U, double, D.nk);
+      ALLOC(D.bp, double, D.nel + 1);
+      ALLOC(D.xq, double, D.nq);
+      ALLOC(D.qel, int, D.nq);
+      ALLOC(D.qbeg, int, D.n);
+      ALLOC(D.qcnt, int, D.n);
+      ALLOC(D.Bq, double, (size_t)D.nq * (p + 1));
+      ALLOC(D.dBq, double, (size_t)D.nq * (p + 1));
+      ALLOC(D.W, double, (size_t)D.n * D.qmax);
+      ALLOC(D.V, double, (size_t)D.n * D.qmax * W);
+      ALLOC(D.crange, int, (size_t)D.n * W);
+      ALLOC(D.gx, double, p + 1);
+      ALLOC(D.gw, double, p + 1);
+      ALLOC(D.GB, double, (size_t)D.nel * (p + 1) * (p + 1));
+      ALLOC(D.dGB, double, (size_t)D.nel * (p + 1) * (p + 1));
+      hbp = (double *)malloc(sizeof(double) * (D.nel + 1));
+      for (int e = 0; e <= D.nel; e++) hbp[e] = desc->knots[d][p + e];
+      cudaMemcpyAsync(D.U, desc->knots[d], sizeof(double) * D.nk, cudaMemcpyHostToDevice, st);
+      cudaMemcpyAsync(D.bp, hbp, sizeof(double) * (D.nel + 1), cudaMemcpyHostToDevice, st);
+      cudaStreamSynchronize(st);
+      free(hbp);
+      hbp = nullptr;
+    }
+    Dir &A = P->d[0];
+    Dir &B = P->d[1];
+    // curve
+    P->curve.kind = desc->trim_kind;
+    P->curve.keep_inside = desc->trim_keep_inside;
+    for (int k = 0; k < 6; k++) P->curve.prm[k] = desc->trim_params[k];
+    P->curve.nc = desc->trim_kind == TW_TRIM_BSPLINE3 ? desc->trim_nctrl : 0;
+    if (P->curve.nc > 0) {
+      double *seg, *box;
+      ALLOC(P->curve_ctrl, double, 2 * P->curve.nc);
+      ALLOC(seg, double, 8 * P->curve.nc);
+      ALLOC(box, double, 4 * P->curve.nc);
+      P->curve.seg = seg;
+      P->curve.box = box;
+      cudaMemcpyAsync(P->curve_ctrl, desc->trim_ctrl, sizeof(double) * 2 * P->curve.nc,
+                      cudaMemcpyHostToDevice, st);
+    }
+    // geometry and coefficient
+    P->geo.geom_kind = desc->geom_kind;
+    P->geo.coef_kind = desc->coef_kind;
+    P->geo.n1 = A.n;
+    if (desc->geom_kind == TW_GEOM_SPLINE) {
+      double *g;
+      ALLOC(g, double, 2 * (size_t)A.n * B.n);
+      cudaMemcpyAsync(g, desc->geom_ctrl, sizeof(double) * 2 * (size_t)A.n * B.n,
+                      cudaMemcpyHostToDevice, st);
+      P->geo.ctrl = g;
+    }
+    if (desc->coef_kind == TW_COEF_DENSITY) {
+      for (int d = 0; d < 2; d++) {
+        double *u;
+        P->geo.dp[d] = desc->dens_p[d];
+        P->geo.dnk[d] = desc->dens_nknots[d];
+        ALLOC(u, double, desc->dens_nknots[d]);
+        cudaMemcpyAsync(u, desc->dens_knots[d], sizeof(double) * desc->dens_nknots[d],
+                        cudaMemcpyHostToDevice, st);
+        P->geo.dU[d] = u;
+      }
+      size_t m = (size_t)(desc->dens_nknots[0] - desc->dens_p[0] - 1) *
+                 (desc->dens_nknots[1] - desc->dens_p[1] - 1);
+      double *c;
+      ALLOC(c, double, m);
+      cudaMemcpyAsync(c, desc->dens_coef, sizeof(double) * m, cudaMemcpyHostToDevice, st);
+      P->geo.dcoef = c;
+    }
+    int64_t ne = (int64_t)A.nel * B.nel, nf = (int64_t)A.n * B.n;
+    ALLOC(P->estate, uint8_t, ne);
+    ALLOC(P->fstate, uint8_t, nf);
+    ALLOC(P->act, int32_t, nf);
+    ALLOC(P->choice, int32_t, 4 * nf);
+    ALLOC(P->cut_slot, int32_t, ne);
+    ALLOC(P->gslot, int32_t, ne);
+    ALLOC(P->disc_slot[0], int32_t, A.nel + 1);
+    ALLOC(P->disc_slot[1], int32_t, B.nel + 1);
+    ALLOC(P->C, double, (size_t)A.nq * B.nq);
+    ALLOC(P->flag, int32_t, 4);
+    cudaMemsetAsync(P->flag, 0, 4 * sizeof(int32_t), st);
+    rc = build_tables(P);
+    if (rc) goto fail;
+  }
+#undef ALLOC
+  *out = P;
+  return TW_OK;
+fail:
+  if (rc == TW_ENOMEM && !g_err[0]) set_error("tw_patch_create: out of device memory");
+  tw_patch_destroy(P);
+  return rc;
+}
+
+extern "C" int tw_patch_info(const tw_patch *P, int64_t *info) {
+  if (!P || !info) {
+    set_error("tw_patch_info: NULL argument");
+    return TW_EINVAL;
+  }
+  info[0] = P->d[0].n;
+  info[1] = P->d[1].n;
+  info[2] = P->d[0].nel;
+  info[3] = P->d[1].nel;
+  info[4] = P->d[0].nq;
+  info[5] = P->d[1].nq;
+  info[6] = P->n_rows;
+  info[7] = P->nnz;
+  info[8] = P->ncut;
+  info[9] = P->ncutfns;
+  info[10] = P->ncutpts;
+  info[11] = P->ndwqrows;
+  info[12] = P->ndisc[0] + P->ndisc[1];
+  info[13] = P->n_interior;
+  info[14] = P->p;
+  info[15] = P->method;
+  return TW_OK;
+}
+
+extern "C" int tw_form_mass(tw_patch *P, int precision, int64_t *row_ptr, int32_t *col, void *val,
+                            void *stream) {
+  if (!P || !row_ptr || (P->nnz > 0 && (!col || !val))) {
+    set_error("tw_form_mass: NULL argument");
+    return TW_EINVAL;
+  }
+  if (precision != TW_PREC_FP64 && precision != TW_PREC_FP32) {
+    set_error("tw_form_mass: unknown precision %d", precision);
+    return TW_EINVAL;
+  }
+  return form_mass_launch(P, precision, row_ptr, col, val, (cudaStream_t)stream);
+}
+
+extern "C" int tw_states(const tw_patch *P, uint8_t *estate, uint8_t *fstate, int32_t *act,
+                         void *stream) {
+  if (!P) {
+    set_error("tw_states: NULL patch");
+    return TW_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  int64_t ne = (int64_t)P->d[0].nel * P->d[1].nel, nf = (int64_t)P->d[0].n * P->d[1].n;
+  if (estate) cudaMemcpyAsync(estate, P->estate, ne, cudaMemcpyDeviceToDevice, s);
+  if (fstate) cudaMemcpyAsync(fstate, P->fstate, nf, cudaMemcpyDeviceToDevice, s);
+  if (act) cudaMemcpyAsync(act, P->act, nf * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+  return check_cuda(cudaGetLastError(), "tw_states");
+}
+
+extern "C" int tw_patch_table(const tw_patch *P, int which, void *dst, int64_t cap, int64_t *count,
+                              void *stream) {
+  if (!P) {
+    set_error("tw_patch_table: NULL patch");
+    return TW_EINVAL;
+  }
+  const void *src = nullptr;
+  int64_t n = 0;
+  size_t es = sizeof(double);
+  int p1 = P->p + 1;
+  switch (which) {
+    case 0: case 1: src = P->d[which].xq; n = P->d[which].nq; break;
+    case 2: case 3: src = P->d[which - 2].W; n = (int64_t)P->d[which - 2].n * P->d[which - 2].qmax; break;
+    case 4: src = P->C; n = (int64_t)P->d[0].nq * P->d[1].nq; break;
+    case 5: src = P->cut_pts; n = 3 * P->ncutpts; break;
+    case 6: src = P->cut_off; n = P->ncut + 1; es = sizeof(int64_t); break;
+    case 7: src = P->cut_list; n = P->ncut; es = sizeof(int32_t); break;
+    case 8: src = P->choice; n = 4 * (int64_t)P->d[0].n * P->d[1].n; es = sizeof(int32_t); break;
+    case 9: src = P->d[0].gx; n = p1; break;
+    case 10: src = P->d[0].gw; n = p1; break;
+    default:
+      set_error("tw_patch_table: unknown table %d", which);
+      return TW_EINVAL;
+  }
+  if (count) *count = n;
+  if (!dst) return TW_OK;
+  if (cap < n) {
+    set_error("tw_patch_table: capacity %lld < %lld", (long long)cap, (long long)n);
+    return TW_EINVAL;
+  }
+  if (n > 0)
+    cudaMemcpyAsync(dst, src, es * n, cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
+  return check_cuda(cudaGetLastError(), "tw_patch_table");
+}
+
+extern "C" int tw_rhs(tw_patch *P, const tw_func *f, double *b, void *stream) {
+  if (!P || !f || !b) {
+    set_error("tw_rhs: NULL argument");
+    return TW_EINVAL;
+  }
+  return rhs_launch(P, f, b, (cudaStream_t)stream);
+}
+
+extern "C" int tw_l2_project(tw_patch *P, const tw_func *f, const int64_t *row_ptr,
+                             const int32_t *col, const double *val, double *u, double tol,
+                             int maxit, int *iters, double *relres, void *stream) {
+  if (!P || !f || !row_ptr || !col || !val || !u) {
+    set_error("tw_l2_project: NULL argument");
+    return TW_EINVAL;
+  }
+  if (!(tol > 0) || maxit < 0) {
+    set_error("tw_l2_project: need tol > 0 and maxit >= 0");
+    return TW_EINVAL;
+  }
+  return l2_project_run(P, f, row_ptr, col, val, u, tol, maxit, iters, relres,
+                        (cudaStream_t)stream);
+}

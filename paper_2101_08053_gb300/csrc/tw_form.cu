@@ -1,0 +1,348 @@
+// tw_form.cu -- formation of the trimmed mass matrix (Sect. 2.1 Eqs. 6-7,
+// Sect. 3 Eq. 8, Sects. 3.1-3.3), written straight into the caller's CSR.
+//
+//  k_interior<P,T>  interior test functions: weighted quadrature with sum
+//                   factorisation, row-based.  One thread block per (i2, tile
+//                   of T consecutive i1): stage 1 contracts direction 2 over
+//                   the block's slab of c,
+//                       Y[r2][k1] = sum_{k2 in Q_{i2}} W2[i2,k2] B_{j2}(x_k2) c[k2][k1],
+//                   stage 2 gives every output of the tile's rows,
+//                       m_{i,j} = sum_{k1 in Q_{i1}} W1[i1,k1] B_{j1}(x_k1) Y[r2][k1].
+//                   Both stages skip the zero part of the band (only points in
+//                   supp B_i cap supp B_j contribute).  Consecutive threads own
+//                   consecutive CSR positions of a row, so writes coalesce.
+//  k_cutrows<P>     one block per cut row (all rows for the Gauss method):
+//                   region part (DWQ rectangle or naive masked WQ) by sum
+//                   factorisation, element Gauss on regular elements (element
+//                   level sum factorisation), cut-element rule on cut elements.
+//                   Every output is owned by one thread and summed in a fixed
+//                   order, so the matrix is bitwise reproducible.
+#include "tw_internal.cuh"
+
+namespace tw {
+
+template <int P, int T>
+__global__ void __launch_bounds__(256) k_interior(Dir A, Dir B, const double *__restrict__ C,
+                                                  const uint8_t *__restrict__ fstate,
+                                                  const int32_t *__restrict__ act,
+                                                  const int64_t *__restrict__ rp,
+                                                  int32_t *__restrict__ col,
+                                                  double *__restrict__ val) {
+  constexpr int W = 2 * P + 1;
+  constexpr int KMAX = 2 * T + 4 * P + 4;
+  __shared__ double Y[W * KMAX];
+  __shared__ double V2s[TW_QMAX * W];
+  __shared__ int cr2[W];
+  __shared__ int anyint;
+  const int i2 = blockIdx.y;
+  const int i1a = blockIdx.x * T;
+  const int i1b = min(A.n, i1a + T);
+  const int n1 = A.n;
+  if (threadIdx.x == 0) anyint = 0;
+  __syncthreads();
+  for (int t = threadIdx.x; t < i1b - i1a; t += blockDim.x)
+    if (fstate[i2 * n1 + i1a + t] == TW_FUNC_INTERIOR) anyint = 1;
+  __syncthreads();
+  if (!anyint) return;
+  const int kA = A.qbeg[i1a];
+  const int kB = A.qbeg[i1b - 1] + A.qcnt[i1b - 1];
+  const int K = kB - kA;
+  const int qb2 = B.qbeg[i2], qc2 = B.qcnt[i2];
+  for (int t = threadIdx.x; t < qc2 * W; t += blockDim.x)
+    V2s[t] = B.V[(size_t)i2 * B.qmax * W + t];
+  for (int t = threadIdx.x; t < W; t += blockDim.x) cr2[t] = B.crange[i2 * W + t];
+  __syncthreads();
+  // stage 1
+  for (int idx = threadIdx.x; idx < W * K; idx += blockDim.x) {
+    int r2 = idx / K, kk = idx - r2 * K;
+    int lo = cr2[r2] & 0xffff, hi = cr2[r2] >> 16;
+    const double *cc = C + (size_t)(qb2 + lo) * A.nq + kA + kk;
+    double s = 0.0;
+    for (int c2 = lo; c2 < hi; c2++, cc += A.nq) s = fma(V2s[c2 * W + r2], *cc, s);
+    Y[r2 * KMAX + kk] = s;
+  }
+  __syncthreads();
+  // stage 2
+  const int lo2 = max(0, i2 - P);
+  const int NO = (i1b - i1a) * W * W;
+  for (int idx = threadIdx.x; idx < NO; idx += blockDim.x) {
+    int t = idx / (W * W), rem = idx - t * (W * W);
+    int r2 = rem / W, r1 = rem - r2 * W;
+    int i1 = i1a + t;
+    int g = i2 * n1 + i1;
+    if (fstate[g] != TW_FUNC_INTERIOR) continue;
+    int j1 = i1 - P + r1, j2 = i2 - P + r2;
+    if (j1 < 0 || j1 >= n1 || j2 < 0 || j2 >= B.n) continue;
+    int cr = A.crange[i1 * W + r1];
+    int lo = cr & 0xffff, hi = cr >> 16;
+    const double *v = A.V + ((size_t)i1 * A.qmax) * W + r1;
+    const double *y = Y + r2 * KMAX + (A.qbeg[i1] - kA);
+    double s = 0.0;
+    for (int c1 = lo; c1 < hi; c1++) s = fma(v[c1 * W], y[c1], s);
+    int lo1 = max(0, i1 - P), w1 = min(n1 - 1, i1 + P) - lo1 + 1;
+    int64_t pos = rp[act[g]] + (int64_t)(j2 - lo2) * w1 + (j1 - lo1);
+    val[pos] = s;
+    col[pos] = act[j2 * n1 + j1];
+  }
+}
+
+#define TW_RC 32
+
+template <int P>
+__global__ void __launch_bounds__(256) k_cutrows(RowArgs a, const int32_t *__restrict__ rows,
+                                                 int32_t *__restrict__ col,
+                                                 double *__restrict__ val) {
+  constexpr int W = 2 * P + 1, P1 = P + 1;
+  __shared__ double acc[W * W];
+  __shared__ double rx[2][TW_RC], rw[2][TW_RC], rb[2][TW_RC][W];
+  __shared__ int rk[2][TW_RC];
+  __shared__ int nr[2];
+  __shared__ double cg[TW_RC * TW_RC];
+  __shared__ double Z[W * TW_RC];
+  __shared__ double Tg[P1 * P1];
+  __shared__ int pos[W * W];
+  const Dir &A = a.A;
+  const Dir &B = a.B;
+  const int g = rows[blockIdx.x];
+  const int n1 = A.n;
+  const int i1 = g % n1, i2 = g / n1;
+  const int tid = threadIdx.x;
+  int kind;  // 0: element Gauss on S^r, 1: naive WQ, 2: DWQ region + Gauss rest
+  if (a.method == TW_METHOD_GAUSS || a.method == TW_METHOD_HYBRID) kind = 0;
+  else if (a.method == TW_METHOD_NAIVE) kind = 1;
+  else kind = a.choice[4 * g] >= 0 ? 2 : 0;
+  int ch[4] = {-1, -1, -1, -1};
+  if (kind == 2)
+    for (int k = 0; k < 4; k++) ch[k] = a.choice[4 * g + k];
+  const int lo1 = max(0, i1 - P), hi1 = min(A.nel - 1, i1);
+  const int lo2 = max(0, i2 - P), hi2 = min(B.nel - 1, i2);
+  int r0[2] = {1, 1}, r1[2] = {0, 0};  // region R in elements (empty unless DWQ)
+  if (kind == 2) {
+    int lo[2] = {lo1, lo2}, hi[2] = {hi1, hi2};
+    for (int d = 0; d < 2; d++) {
+      int k = ch[2 * d], s = ch[2 * d + 1];
+      r0[d] = k == 2 ? s : lo[d];
+      r1[d] = k == 1 ? s - 1 : hi[d];
+    }
+  }
+  for (int t = tid; t < W * W; t += blockDim.x) acc[t] = 0.0;
+
+  // ---- region part: naive WQ (full support, c masked) or DWQ rectangle ----
+  if (kind != 0) {
+    if (tid < 2) {
+      const int d = tid;
+      const Dir &D = d == 0 ? A : B;
+      const int i = d == 0 ? i1 : i2;
+      int n = 0;
+      if (kind == 1 || ch[2 * d] == 0) {
+        for (int c = 0; c < D.qcnt[i]; c++) {
+          int k = D.qbeg[i] + c;
+          rx[d][n] = D.xq[k];
+          rw[d][n] = D.W[(size_t)i * D.qmax + c];
+          rk[d][n] = k;
+          for (int r = 0; r < W; r++) {
+            int j = i - P + r, aa = j - D.qel[k];
+            rb[d][n][r] = (aa >= 0 && aa <= P) ? D.Bq[k * P1 + aa] : 0.0;
+          }
+          n++;
+        }
+      } else {
+        int s = ch[2 * d + 1], side = ch[2 * d] - 1;
+        int sl = a.disc_slot[d][s];
+        double t = D.bp[s];
+        int np_ = a.dwq_np[d][sl];
+        const double *xs = a.dwq_x[d] + (size_t)sl * TW_LQMAX;
+        const double *ws = a.dwq_w[d] + (((size_t)sl * P + (i - s)) * 2 + side) * TW_LQMAX;
+        double ulo = D.U[i], uhi = D.U[i + P + 1];
+        for (int k = 0; k < np_; k++) {
+          double x = xs[k];
+          if (!(x > ulo && x < uhi)) continue;
+          if (side == 0 ? !(x < t) : !(x > t)) continue;
+          if (n >= TW_RC) {
+            atomicOr(a.flag, TWF_RULECAP);
+            break;
+          }
+          rx[d][n] = x;
+          rw[d][n] = ws[k];
+          rk[d][n] = -1;
+          int e = elem_of(D.bp, D.nel, x);
+          double N[TW_MAXP1];
+          basis_vals(D.U, e + P, x, P, N);
+          for (int r = 0; r < W; r++) {
+            int j = i - P + r, aa = j - e;
+            rb[d][n][r] = (aa >= 0 && aa <= P) ? N[aa] : 0.0;
+          }
+          n++;
+        }
+      }
+      nr[d] = n;
+    }
+    __syncthreads();
+    const int m1 = nr[0], m2 = nr[1];
+    for (int t = tid; t < m1 * m2; t += blockDim.x) {
+      int ia = t % m1, ib = t / m1;
+      double c;
+      int k1 = rk[0][ia], k2 = rk[1][ib];
+      if (k1 >= 0 && k2 >= 0) {
+        c = a.C[(size_t)k2 * A.nq + k1];
+        if (kind == 1 && a.estate[B.qel[k2] * A.nel + A.qel[k1]] != TW_ELEM_REGULAR) c = 0.0;
+      } else {
+        c = coef_at(a.G, A, B, rx[0][ia], rx[1][ib]);
+      }
+      cg[ia * TW_RC + ib] = c;
+    }
+    __syncthreads();
+    for (int t = tid; t < W * m1; t += blockDim.x) {
+      int r2 = t / m1, ia = t % m1;
+      double s = 0.0;
+      for (int ib = 0; ib < m2; ib++) s = fma(rw[1][ib] * rb[1][ib][r2], cg[ia * TW_RC + ib], s);
+      Z[r2 * TW_RC + ia] = s;
+    }
+    __syncthreads();
+    for (int t = tid; t < W * W; t += blockDim.x) {
+      int r2 = t / W, q1 = t % W;
+      double s = 0.0;
+      for (int ia = 0; ia < m1; ia++) s = fma(rw[0][ia] * rb[0][ia][q1], Z[r2 * TW_RC + ia], s);
+      acc[t] += s;
+    }
+    __syncthreads();
+  } else {
+    __syncthreads();
+  }
+
+  // ---- elements of the support: Gauss on regular (outside R), cut rule on cut ----
+  const int p1 = P1;
+  for (int e2 = lo2; e2 <= hi2; e2++)
+    for (int e1 = lo1; e1 <= hi1; e1++) {
+      const int e = e2 * A.nel + e1;
+      const uint8_t st = a.estate[e];
+      const bool inR = e1 >= r0[0] && e1 <= r1[0] && e2 >= r0[1] && e2 <= r1[1];
+      if (st == TW_ELEM_REGULAR && kind != 1 && !inR) {
+        const double *cgp = a.gc + (size_t)a.gslot[e] * p1 * p1;
+        const double h1 = 0.5 * (A.bp[e1 + 1] - A.bp[e1]), h2 = 0.5 * (B.bp[e2 + 1] - B.bp[e2]);
+        const double *GB1 = A.GB + (size_t)e1 * p1 * p1;
+        const double *GB2 = B.GB + (size_t)e2 * p1 * p1;
+        if (tid < p1 * p1) {
+          int b1 = tid % p1, g2 = tid / p1;
+          double s = 0.0;
+          for (int g1 = 0; g1 < p1; g1++)
+            s = fma(A.gw[g1] * h1 * GB1[g1 * p1 + (i1 - e1)] * GB1[g1 * p1 + b1], cgp[g2 * p1 + g1], s);
+          Tg[g2 * p1 + b1] = s;
+        }
+        __syncthreads();
+        if (tid < p1 * p1) {
+          int b1 = tid % p1, b2 = tid / p1;
+          double s = 0.0;
+          for (int g2 = 0; g2 < p1; g2++)
+            s = fma(Tg[g2 * p1 + b1], B.gw[g2] * h2 * GB2[g2 * p1 + (i2 - e2)] * GB2[g2 * p1 + b2], s);
+          acc[(e2 + b2 - i2 + P) * W + (e1 + b1 - i1 + P)] += s;
+        }
+        __syncthreads();
+      } else if (st == TW_ELEM_CUT) {
+        const int cs = a.cut_slot[e];
+        const int64_t q0 = a.cut_off[cs], q1 = a.cut_off[cs + 1];
+        if (tid < p1 * p1) {
+          int b1 = tid % p1, b2 = tid / p1;
+          double s = 0.0;
+          for (int64_t q = q0; q < q1; q++) {
+            const double *Bv = a.cut_B + 2 * q * p1;
+            double ti = a.cut_wc[q] * Bv[i1 - e1] * Bv[p1 + (i2 - e2)];
+            s = fma(ti, Bv[b1] * Bv[p1 + b2], s);
+          }
+          acc[(e2 + b2 - i2 + P) * W + (e1 + b1 - i1 + P)] += s;
+        }
+        __syncthreads();
+      }
+    }
+
+  // ---- write the row: active columns in ascending order (R11) ----
+  if (tid == 0) {
+    int c = 0;
+    for (int r2 = 0; r2 < W; r2++)
+      for (int q1 = 0; q1 < W; q1++) {
+        int j1 = i1 - P + q1, j2 = i2 - P + r2;
+        int ok = j1 >= 0 && j1 < n1 && j2 >= 0 && j2 < B.n && a.act[j2 * n1 + j1] >= 0;
+        pos[r2 * W + q1] = ok ? c++ : -1;
+      }
+  }
+  __syncthreads();
+  const int64_t base = a.rp[a.act[g]];
+  for (int t = tid; t < W * W; t += blockDim.x) {
+    int ps = pos[t];
+    if (ps < 0) continue;
+    int r2 = t / W, q1 = t % W;
+    int j1 = i1 - P + q1, j2 = i2 - P + r2;
+    val[base + ps] = acc[t];
+    col[base + ps] = a.act[j2 * n1 + j1];
+  }
+}
+
+__global__ void k_copy_i64(const int64_t *src, int64_t *dst, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = src[i];
+}
+
+template <int P>
+static void launch_form(tw_patch *Pt, int64_t *rp, int32_t *col, double *val, cudaStream_t s) {
+  constexpr int T = 32;
+  Dir &A = Pt->d[0];
+  Dir &B = Pt->d[1];
+  if (Pt->method != TW_METHOD_GAUSS && Pt->n_interior > 0) {
+    dim3 grid((A.n + T - 1) / T, B.n);
+    k_interior<P, T><<<grid, 256, 0, s>>>(A, B, Pt->C, Pt->fstate, Pt->act, Pt->row_ptr, col, val);
+    TW_LAUNCH();
+  }
+  if (Pt->ncutrows > 0) {
+    RowArgs ra;
+    ra.A = A;
+    ra.B = B;
+    ra.G = Pt->geo;
+    ra.estate = Pt->estate;
+    ra.fstate = Pt->fstate;
+    ra.act = Pt->act;
+    ra.rp = Pt->row_ptr;
+    ra.C = Pt->C;
+    ra.gslot = Pt->gslot;
+    ra.gc = Pt->gc;
+    ra.cut_slot = Pt->cut_slot;
+    ra.cut_off = Pt->cut_off;
+    ra.cut_B = Pt->cut_B;
+    ra.cut_wc = Pt->cut_wc;
+    ra.cut_pts = Pt->cut_pts;
+    ra.choice = Pt->choice;
+    for (int d = 0; d < 2; d++) {
+      ra.disc_slot[d] = Pt->disc_slot[d];
+      ra.dwq_x[d] = Pt->dwq_x[d];
+      ra.dwq_np[d] = Pt->dwq_np[d];
+      ra.dwq_w[d] = Pt->dwq_w[d];
+    }
+    ra.method = Pt->method;
+    ra.flag = Pt->flag;
+    k_cutrows<P><<<Pt->ncutrows, 256, 0, s>>>(ra, Pt->cutrows, col, val);
+    TW_LAUNCH();
+  }
+}
+
+int form_mass_launch(tw_patch *P, int precision, int64_t *rp, int32_t *col, void *val,
+                     cudaStream_t s) {
+  if (precision != TW_PREC_FP64) {
+    set_error("tw_form_mass: precision %d not available in this build", precision);
+    return TW_EUNSUPPORTED;
+  }
+  int64_t n = P->n_rows + 1;
+  k_copy_i64<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P->row_ptr, rp, n);
+  TW_LAUNCH();
+  double *v = (double *)val;
+  switch (P->p) {
+    case 1: launch_form<1>(P, rp, col, v, s); break;
+    case 2: launch_form<2>(P, rp, col, v, s); break;
+    case 3: launch_form<3>(P, rp, col, v, s); break;
+    case 4: launch_form<4>(P, rp, col, v, s); break;
+    case 5: launch_form<5>(P, rp, col, v, s); break;
+    case 6: launch_form<6>(P, rp, col, v, s); break;
+    default: return TW_EUNSUPPORTED;
+  }
+  return check_cuda(cudaGetLastError(), "tw_form_mass launch");
+}
+
+}  // namespace tw

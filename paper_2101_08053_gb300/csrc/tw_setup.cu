@@ -1,0 +1,1039 @@
+// tw_setup.cu -- patch set-up kernels (everything that depends on the patch but
+// not on the matrix entries' precision):
+//   WQ point layout and weights            Sect. 2.1, Eqs. 4-5 (readings R1-R3)
+//   trimming classification                Sect. 2.2 (reading R8)
+//   c at the WQ grid (sum-factorised det J) Eqs. 6-7
+//   cut-element rules                      Sect. 3.1 (reading R6)
+//   DWQ region choice and rules            Sect. 3.3, Eqs. 9-10 (readings R4, R5, R7)
+//   CSR pattern                            row-based assembly (reading R11)
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+
+#include "tw_internal.cuh"
+
+namespace tw {
+
+// point offset of element e in the WQ layout (R1): elements 0 and nel-1
+// touch the (p+1)-fold end knots and carry p+1 points, every other element 2
+__host__ __device__ __forceinline__ int wq_off(int e, int p, int nel) {
+  if (e <= 0) return 0;
+  if (e >= nel) return 2 * (p + 1) + 2 * (nel - 2);
+  return (p + 1) + 2 * (e - 1);
+}
+
+// ---------------------------------------------------------------------------
+// scans (three-phase, 1024-element blocks)
+
+template <typename T>
+__global__ void k_scan_block(const T *in, T *out, T *bsum, int64_t n) {
+  __shared__ T sh[1024];
+  int t = threadIdx.x;
+  int64_t i = (int64_t)blockIdx.x * 1024 + t;
+  T v = i < n ? in[i] : (T)0;
+  sh[t] = v;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    T a = t >= off ? sh[t - off] : (T)0;
+    __syncthreads();
+    sh[t] += a;
+    __syncthreads();
+  }
+  if (i < n) out[i] = sh[t] - v;
+  if (t == 1023) bsum[blockIdx.x] = sh[1023];
+}
+
+template <typename T>
+__global__ void k_scan_sums(T *bsum, int64_t nb, T *total) {
+  __shared__ T sh[1024];
+  __shared__ T carry;
+  int t = threadIdx.x;
+  if (t == 0) carry = 0;
+  __syncthreads();
+  for (int64_t base = 0; base < nb; base += 1024) {
+    int64_t i = base + t;
+    T v = i < nb ? bsum[i] : (T)0;
+    sh[t] = v;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+      T a = t >= off ? sh[t - off] : (T)0;
+      __syncthreads();
+      sh[t] += a;
+      __syncthreads();
+    }
+    if (i < nb) bsum[i] = carry + sh[t] - v;
+    __syncthreads();
+    if (t == 0) carry += sh[1023];
+    __syncthreads();
+  }
+  if (t == 0) *total = carry;
+}
+
+template <typename T>
+__global__ void k_scan_add(T *out, const T *bsum, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * 1024 + threadIdx.x;
+  if (i < n) out[i] += bsum[blockIdx.x];
+}
+
+template <typename T>
+static int scan_impl(const T *in, T *out, int64_t n, T *total_dev, cudaStream_t s, tw_patch *P) {
+  if (n <= 0) {
+    cudaMemsetAsync(total_dev, 0, sizeof(T), s);
+    return 0;
+  }
+  int64_t nb = (n + 1023) / 1024;
+  T *bsum = (T *)dalloc(P, sizeof(T) * nb);
+  if (!bsum) return TW_ENOMEM;
+  k_scan_block<T><<<(unsigned)nb, 1024, 0, s>>>(in, out, bsum, n);
+  TW_LAUNCH();
+  k_scan_sums<T><<<1, 1024, 0, s>>>(bsum, nb, total_dev);
+  TW_LAUNCH();
+  k_scan_add<T><<<(unsigned)nb, 1024, 0, s>>>(out, bsum, n);
+  TW_LAUNCH();
+  return check_cuda(cudaGetLastError(), "scan");
+}
+
+int exclusive_scan_i32(const int32_t *in, int32_t *out, int64_t n, int32_t *total, cudaStream_t s,
+                       tw_patch *P) {
+  return scan_impl<int32_t>(in, out, n, total, s, P);
+}
+int exclusive_scan_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *total, cudaStream_t s,
+                       tw_patch *P) {
+  return scan_impl<int64_t>(in, out, n, total, s, P);
+}
+
+// ---------------------------------------------------------------------------
+// univariate tables
+
+// q-point Gauss-Legendre by Newton on the Legendre recurrence (double)
+__global__ void k_gauss_nodes(int q, double *x, double *w) {
+  int k = threadIdx.x;
+  if (k >= q) return;
+  double z = cos(3.141592653589793 * (q - k - 0.25) / (q + 0.5));  // ascending order
+  double dp = 1.0;
+  for (int it = 0; it < 64; it++) {
+    double a = 1.0, b = z;  // P0, P1
+    for (int m = 2; m <= q; m++) {
+      double c = ((2 * m - 1) * z * b - (m - 1) * a) / m;
+      a = b;
+      b = c;
+    }
+    if (q == 1) a = 1.0;
+    dp = q * (z * b - a) / (z * z - 1.0);
+    double dz = b / dp;
+    z -= dz;
+    if (fabs(dz) <= 1e-17) break;
+  }
+  {
+    double a = 1.0, b = z;
+    for (int m = 2; m <= q; m++) {
+      double c = ((2 * m - 1) * z * b - (m - 1) * a) / m;
+      a = b;
+      b = c;
+    }
+    if (q == 1) a = 1.0;
+    dp = q * (z * b - a) / (z * z - 1.0);
+  }
+  x[k] = z;
+  w[k] = 2.0 / ((1.0 - z * z) * dp * dp);
+}
+
+__global__ void k_wq_points(Dir D) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= D.nq) return;
+  int p = D.p, e, j, m;
+  if (k < p + 1) {
+    e = 0; j = k; m = p + 1;
+  } else if (k >= D.nq - (p + 1)) {
+    e = D.nel - 1; j = k - (D.nq - p - 1); m = p + 1;
+  } else {
+    e = 1 + (k - p - 1) / 2; j = (k - p - 1) % 2; m = 2;
+  }
+  double a = D.bp[e], b = D.bp[e + 1];
+  double x = a + (b - a) * (double)(j + 1) / (double)(m + 1);
+  D.xq[k] = x;
+  D.qel[k] = e;
+  double N[TW_MAXP1], dN[TW_MAXP1];
+  basis_ders(D.U, e + p, x, p, N, dN);
+  for (int a2 = 0; a2 <= p; a2++) {
+    D.Bq[k * (p + 1) + a2] = N[a2];
+    D.dBq[k * (p + 1) + a2] = dN[a2];
+  }
+}
+
+__global__ void k_wq_ranges(Dir D) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= D.n) return;
+  int lo = max(0, i - D.p), hi = min(D.nel - 1, i);
+  D.qbeg[i] = wq_off(lo, D.p, D.nel);
+  D.qcnt[i] = wq_off(hi + 1, D.p, D.nel) - D.qbeg[i];
+}
+
+__global__ void k_gauss_tables(Dir D) {
+  int id = blockIdx.x * blockDim.x + threadIdx.x;
+  int p1 = D.p + 1;
+  if (id >= D.nel * p1) return;
+  int e = id / p1, g = id % p1;
+  double a = D.bp[e], b = D.bp[e + 1];
+  double x = a + (b - a) * 0.5 * (D.gx[g] + 1.0);
+  double N[TW_MAXP1], dN[TW_MAXP1];
+  basis_ders(D.U, e + D.p, x, D.p, N, dN);
+  for (int k = 0; k < p1; k++) {
+    D.GB[(e * p1 + g) * p1 + k] = N[k];
+    D.dGB[(e * p1 + g) * p1 + k] = dN[k];
+  }
+}
+
+// B_j(x_k) from the WQ basis table (zero off the span)
+__device__ __forceinline__ double Bjk(const Dir &D, int j, int k) {
+  int a = j - D.qel[k];
+  return (a >= 0 && a <= D.p) ? D.Bq[k * (D.p + 1) + a] : 0.0;
+}
+
+// Eq. 5 for test function i: min-norm weights, then V = W * B_j (R2, R3)
+__global__ void k_wq_weights(Dir D, int *flag) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= D.n) return;
+  int p = D.p, p1 = p + 1, W2 = 2 * p + 1;
+  int jlo = max(0, i - p), jhi = min(D.n - 1, i + p);
+  int m = jhi - jlo + 1;
+  int q0 = D.qbeg[i], N = D.qcnt[i];
+  if (N > TW_QMAX) {
+    atomicOr(flag, TWF_QMAX);
+    return;
+  }
+  double A[TW_WIN * TW_QMAX], b[TW_WIN], w[TW_QMAX], beta[TW_WIN];
+  int elo = max(0, i - p), ehi = min(D.nel - 1, i);
+  for (int r = 0; r < m; r++) {
+    int j = jlo + r;
+    for (int c = 0; c < N; c++) A[r * TW_QMAX + c] = Bjk(D, j, q0 + c);
+    double s = 0.0;
+    int ea = max(elo, max(0, j - p)), eb = min(ehi, min(D.nel - 1, j));
+    for (int e = ea; e <= eb; e++) {
+      double h = 0.5 * (D.bp[e + 1] - D.bp[e]);
+      for (int g = 0; g < p1; g++)
+        s += D.gw[g] * h * D.GB[(e * p1 + g) * p1 + (i - e)] * D.GB[(e * p1 + g) * p1 + (j - e)];
+    }
+    b[r] = s;
+  }
+  if (minnorm_lq(m, N, A, TW_QMAX, b, w, beta)) atomicOr(flag, TWF_SINGULAR);
+  for (int c = 0; c < D.qmax; c++) {
+    double wc = c < N ? w[c] : 0.0;
+    D.W[(size_t)i * D.qmax + c] = wc;
+    for (int r = 0; r < W2; r++) {
+      int j = i - p + r;
+      double v = 0.0;
+      if (c < N && j >= 0 && j < D.n) v = wc * Bjk(D, j, q0 + c);
+      D.V[((size_t)i * D.qmax + c) * W2 + r] = v;
+    }
+  }
+  for (int r = 0; r < W2; r++) {
+    int j = i - p + r;
+    int lo = 0, hi = 0;
+    if (j >= 0 && j < D.n) {
+      int ea = max(elo, max(0, j - p)), eb = min(ehi, min(D.nel - 1, j));
+      lo = wq_off(ea, p, D.nel) - q0;
+      hi = wq_off(eb + 1, p, D.nel) - q0;
+    }
+    D.crange[i * W2 + r] = lo | (hi << 16);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// trimming curve: monomial segments of the periodic uniform cubic B-spline
+
+__global__ void k_curve_segments(const double *ctrl, int nc, double *seg, double *box) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nc) return;
+  for (int o = 0; o < 2; o++) {
+    double Q0 = ctrl[2 * (((s - 3) % nc + nc) % nc) + o];
+    double Q1 = ctrl[2 * (((s - 2) % nc + nc) % nc) + o];
+    double Q2 = ctrl[2 * (((s - 1) % nc + nc) % nc) + o];
+    double Q3 = ctrl[2 * s + o];
+    seg[8 * s + 4 * o + 0] = (Q0 + 4.0 * Q1 + Q2) / 6.0;
+    seg[8 * s + 4 * o + 1] = (Q2 - Q0) / 2.0;
+    seg[8 * s + 4 * o + 2] = (Q0 - 2.0 * Q1 + Q2) / 2.0;
+    seg[8 * s + 4 * o + 3] = (-Q0 + 3.0 * Q1 - 3.0 * Q2 + Q3) / 6.0;
+    box[4 * s + 2 * o] = fmin(fmin(Q0, Q1), fmin(Q2, Q3));
+    box[4 * s + 2 * o + 1] = fmax(fmax(Q0, Q1), fmax(Q2, Q3));
+  }
+}
+
+__device__ void curve_point0(const Curve &C, double *xy) {
+  if (C.kind == TW_TRIM_CIRCLE) {
+    xy[0] = C.prm[0] + C.prm[2];
+    xy[1] = C.prm[1];
+  } else if (C.kind == TW_TRIM_ELLIPSE) {
+    xy[0] = C.prm[0] + C.prm[2] * cos(C.prm[4]);
+    xy[1] = C.prm[1] + C.prm[2] * sin(C.prm[4]);
+  } else if (C.kind == TW_TRIM_BSPLINE3) {
+    xy[0] = C.seg[0];
+    xy[1] = C.seg[4];
+  } else {
+    xy[0] = xy[1] = -1e300;
+  }
+}
+
+// R8: an element is cut iff the curve meets its open box: a crossing inside
+// one of its four open edges, or the whole curve inside it
+__global__ void k_classify_elems(Curve C, Dir A, Dir B, uint8_t *estate, int *flag) {
+  int id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= A.nel * B.nel) return;
+  int e1 = id % A.nel, e2 = id / A.nel;
+  double a1 = A.bp[e1], b1 = A.bp[e1 + 1], a2 = B.bp[e2], b2 = B.bp[e2 + 1];
+  if (C.kind == TW_TRIM_NONE) {
+    estate[id] = TW_ELEM_REGULAR;
+    return;
+  }
+  double h[TW_HITCAP];
+  int cut = 0;
+  int n;
+  n = curve_line_hits(C, 0, a1, a2, b2, h, TW_HITCAP);
+  cut |= n != 0;
+  if (!cut) { n = curve_line_hits(C, 0, b1, a2, b2, h, TW_HITCAP); cut |= n != 0; }
+  if (!cut) { n = curve_line_hits(C, 1, a2, a1, b1, h, TW_HITCAP); cut |= n != 0; }
+  if (!cut) { n = curve_line_hits(C, 1, b2, a1, b1, h, TW_HITCAP); cut |= n != 0; }
+  if (!cut) {
+    double p0[2];
+    curve_point0(C, p0);
+    cut = p0[0] > a1 && p0[0] < b1 && p0[1] > a2 && p0[1] < b2;
+  }
+  uint8_t st;
+  if (cut) st = TW_ELEM_CUT;
+  else st = visible(C, 0.5 * (a1 + b1), 0.5 * (a2 + b2)) ? TW_ELEM_REGULAR : TW_ELEM_INVISIBLE;
+  estate[id] = st;
+}
+
+// function state from its support elements; active flag for the scan
+__global__ void k_classify_funcs(Dir A, Dir B, const uint8_t *estate, uint8_t *fstate,
+                                 int32_t *aflag, int method, int32_t *cflag, int32_t *counters) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= A.n * B.n) return;
+  int i1 = g % A.n, i2 = g / A.n;
+  int tot = 0, nreg = 0, ninv = 0;
+  for (int e2 = max(0, i2 - B.p); e2 <= min(B.nel - 1, i2); e2++)
+    for (int e1 = max(0, i1 - A.p); e1 <= min(A.nel - 1, i1); e1++) {
+      uint8_t s = estate[e2 * A.nel + e1];
+      tot++;
+      nreg += s == TW_ELEM_REGULAR;
+      ninv += s == TW_ELEM_INVISIBLE;
+    }
+  uint8_t st = ninv == tot ? TW_FUNC_EXTERIOR : (nreg == tot ? TW_FUNC_INTERIOR : TW_FUNC_CUT);
+  fstate[g] = st;
+  aflag[g] = st != TW_FUNC_EXTERIOR;
+  int c = st != TW_FUNC_EXTERIOR && (method == TW_METHOD_GAUSS || st == TW_FUNC_CUT);
+  cflag[g] = c;
+  if (st == TW_FUNC_CUT) atomicAdd(&counters[0], 1);
+  if (st == TW_FUNC_INTERIOR) atomicAdd(&counters[1], 1);
+}
+
+__global__ void k_act_finalize(const int32_t *aflag, int32_t *act, int32_t *rowg, int64_t nf) {
+  int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= nf) return;
+  if (aflag[g]) {
+    rowg[act[g]] = (int32_t)g;
+  } else {
+    act[g] = -1;
+  }
+}
+
+// compacted list from flags (exclusive scan already in pos)
+__global__ void k_compact(const int32_t *flag, const int32_t *pos, int32_t *list, int32_t *slot,
+                          int64_t n) {
+  int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n) return;
+  if (flag[g]) {
+    list[pos[g]] = (int32_t)g;
+    if (slot) slot[g] = pos[g];
+  } else if (slot) {
+    slot[g] = -1;
+  }
+}
+
+// R11: active columns in the (2p+1)^2 window
+__global__ void k_row_counts(Dir A, Dir B, const int32_t *act, int64_t *cnt) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= A.n * B.n) return;
+  int32_t r = act[g];
+  if (r < 0) return;
+  int i1 = g % A.n, i2 = g / A.n, p = A.p;
+  int64_t c = 0;
+  for (int j2 = max(0, i2 - p); j2 <= min(B.n - 1, i2 + p); j2++)
+    for (int j1 = max(0, i1 - p); j1 <= min(A.n - 1, i1 + p); j1++) c += act[j2 * A.n + j1] >= 0;
+  cnt[r] = c;
+}
+
+__global__ void k_set_last(int64_t *a, int64_t idx, const int64_t *v) { a[idx] = *v; }
+
+// sum-factorised det J on the WQ grid: stage A contracts direction 2
+__global__ void k_geo_stageA(Geo G, Dir A, Dir B, double *Gt) {
+  int id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= B.nq * A.n) return;
+  int k2 = id / A.n, i1 = id % A.n, p1 = B.p + 1;
+  int e2 = B.qel[k2];
+  double x = 0, y = 0, dx = 0, dy = 0;
+  for (int b = 0; b < p1; b++) {
+    const double *pt = G.ctrl + 2 * ((size_t)(e2 + b) * G.n1 + i1);
+    double v = B.Bq[k2 * p1 + b], d = B.dBq[k2 * p1 + b];
+    x += pt[0] * v;
+    y += pt[1] * v;
+    dx += pt[0] * d;
+    dy += pt[1] * d;
+  }
+  double *o = Gt + 4 * (size_t)id;
+  o[0] = x;
+  o[1] = y;
+  o[2] = dx;
+  o[3] = dy;
+}
+
+__global__ void k_cgrid(Geo G, Dir A, Dir B, const double *Gt, double *Cg) {
+  int id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= A.nq * B.nq) return;
+  int k1 = id % A.nq, k2 = id / A.nq;
+  double c = 1.0;
+  if (G.coef_kind != TW_COEF_ONE) {
+    if (G.geom_kind == TW_GEOM_SPLINE) {
+      int p1 = A.p + 1, e1 = A.qel[k1];
+      double xa = 0, ya = 0, xb = 0, yb = 0;
+      for (int a = 0; a < p1; a++) {
+        const double *g = Gt + 4 * ((size_t)k2 * A.n + e1 + a);
+        double v = A.Bq[k1 * p1 + a], d = A.dBq[k1 * p1 + a];
+        xa += g[0] * d;
+        ya += g[1] * d;
+        xb += g[2] * v;
+        yb += g[3] * v;
+      }
+      c = xa * yb - xb * ya;
+    }
+    if (G.coef_kind == TW_COEF_DENSITY) c *= density_at(G, A.xq[k1], B.xq[k2]);
+  }
+  Cg[id] = c;
+}
+
+// ---------------------------------------------------------------------------
+// cut-element rule (Sect. 3.1, reading R6).  Pass 0 counts, pass 1 writes.
+
+__device__ void sort_small(double *v, int n) {
+  for (int i = 1; i < n; i++) {
+    double x = v[i];
+    int j = i - 1;
+    while (j >= 0 && v[j] > x) {
+      v[j + 1] = v[j];
+      j--;
+    }
+    v[j + 1] = x;
+  }
+}
+
+__global__ void k_cut_rule(Curve C, Dir A, Dir B, const int32_t *cut_list, int ncut,
+                           const double *qgx, const double *qgw, int q, int64_t *cnt,
+                           const int64_t *off, double *pts, int *flag) {
+  int ci = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ci >= ncut) return;
+  int e = cut_list[ci];
+  int e1 = e % A.nel, e2 = e / A.nel;
+  double a[2] = {A.bp[e1], B.bp[e2]}, b[2] = {A.bp[e1 + 1], B.bp[e2 + 1]};
+  double h[TW_HITCAP];
+  double fp[2 * TW_HITCAP];
+  // 1. outer direction from the extent of the curve inside the closed box
+  double lo[2] = {1e300, 1e300}, hi[2] = {-1e300, -1e300};
+  for (int o = 0; o < 2; o++)
+    for (int sd = 0; sd < 2; sd++) {
+      double s = sd ? b[o] : a[o];
+      int n = curve_line_hits(C, o, s, a[1 - o], b[1 - o], h, TW_HITCAP);
+      if (n < 0) { atomicOr(flag, TWF_HITCAP); return; }
+      for (int k = 0; k < n; k++) {
+        double X = o == 0 ? s : h[k], Y = o == 0 ? h[k] : s;
+        lo[0] = fmin(lo[0], X); hi[0] = fmax(hi[0], X);
+        lo[1] = fmin(lo[1], Y); hi[1] = fmax(hi[1], Y);
+      }
+    }
+  for (int o = 0; o < 2; o++) {
+    int n = curve_folds(C, o, fp, TW_HITCAP);
+    if (n < 0) { atomicOr(flag, TWF_HITCAP); return; }
+    for (int k = 0; k < n; k++) {
+      double X = fp[2 * k], Y = fp[2 * k + 1];
+      if (X >= a[0] && X <= b[0] && Y >= a[1] && Y <= b[1]) {
+        lo[0] = fmin(lo[0], X); hi[0] = fmax(hi[0], X);
+        lo[1] = fmin(lo[1], Y); hi[1] = fmax(hi[1], Y);
+      }
+    }
+  }
+  int o = (hi[0] - lo[0] >= hi[1] - lo[1]) ? 0 : 1;
+  int in = 1 - o;
+  // 2. breakpoints along o
+  double br[TW_BRCAP];
+  int nbr = 0;
+  br[nbr++] = a[o];
+  br[nbr++] = b[o];
+  for (int sd = 0; sd < 2; sd++) {
+    double s = sd ? b[in] : a[in];
+    int n = curve_line_hits(C, in, s, a[o], b[o], h, TW_HITCAP);
+    if (n < 0 || nbr + n > TW_BRCAP) { atomicOr(flag, TWF_BRCAP); return; }
+    for (int k = 0; k < n; k++) br[nbr++] = h[k];
+  }
+  {
+    int n = curve_folds(C, o, fp, TW_HITCAP);
+    for (int k = 0; k < n; k++) {
+      double xo = fp[2 * k + o], xi = fp[2 * k + in];
+      if (xo > a[o] && xo < b[o] && xi >= a[in] && xi <= b[in]) {
+        if (nbr >= TW_BRCAP) { atomicOr(flag, TWF_BRCAP); return; }
+        br[nbr++] = xo;
+      }
+    }
+    if (C.kind == TW_TRIM_BSPLINE3) {
+      for (int sg = 0; sg < C.nc; sg++) {
+        double X = C.seg[8 * sg], Y = C.seg[8 * sg + 4];
+        double xo = o == 0 ? X : Y, xi = o == 0 ? Y : X;
+        if (xo > a[o] && xo < b[o] && xi >= a[in] && xi <= b[in]) {
+          if (nbr >= TW_BRCAP) { atomicOr(flag, TWF_BRCAP); return; }
+          br[nbr++] = xo;
+        }
+      }
+    }
+  }
+  sort_small(br, nbr);
+  // 3. Gauss lines, crossings, visible intervals
+  int64_t count = 0;
+  int64_t base = off ? off[ci] : 0;
+  double ends[TW_HITCAP + 2];
+  for (int pc = 0; pc + 1 < nbr; pc++) {
+    double s0 = br[pc], s1 = br[pc + 1];
+    if (!(s1 > s0)) continue;
+    for (int g = 0; g < q; g++) {
+      double s = s0 + (s1 - s0) * 0.5 * (qgx[g] + 1.0);
+      double ws = qgw[g] * 0.5 * (s1 - s0);
+      int n = curve_line_hits(C, o, s, a[in], b[in], h, TW_HITCAP);
+      if (n < 0) { atomicOr(flag, TWF_HITCAP); return; }
+      ends[0] = a[in];
+      for (int k = 0; k < n; k++) ends[k + 1] = h[k];
+      ends[n + 1] = b[in];
+      for (int k = 0; k <= n; k++) {
+        double u0 = ends[k], u1 = ends[k + 1];
+        if (!(u1 > u0)) continue;
+        double mid = 0.5 * (u0 + u1);
+        if (!visible(C, o == 0 ? s : mid, o == 0 ? mid : s)) continue;
+        if (pts) {
+          for (int hh = 0; hh < q; hh++) {
+            double u = u0 + (u1 - u0) * 0.5 * (qgx[hh] + 1.0);
+            double w = ws * qgw[hh] * 0.5 * (u1 - u0);
+            double *o3 = pts + 3 * (base + count + hh);
+            o3[0] = o == 0 ? s : u;
+            o3[1] = o == 0 ? u : s;
+            o3[2] = w;
+          }
+        }
+        count += q;
+      }
+    }
+  }
+  if (cnt) cnt[ci] = count;
+}
+
+// per cut point: basis values in both directions and w * c
+__global__ void k_cut_point_tables(Geo G, Dir A, Dir B, const int32_t *cut_list,
+                                   const int64_t *off, int ncut, const double *pts, double *Bt,
+                                   double *wc) {
+  int ci = blockIdx.x;
+  if (ci >= ncut) return;
+  int e = cut_list[ci];
+  int e1 = e % A.nel, e2 = e / A.nel, p1 = A.p + 1;
+  for (int64_t k = off[ci] + threadIdx.x; k < off[ci + 1]; k += blockDim.x) {
+    double x1 = pts[3 * k], x2 = pts[3 * k + 1];
+    double v1[TW_MAXP1], d1[TW_MAXP1], v2[TW_MAXP1], d2[TW_MAXP1];
+    basis_ders(A.U, e1 + A.p, x1, A.p, v1, d1);
+    basis_ders(B.U, e2 + B.p, x2, B.p, v2, d2);
+    for (int a = 0; a < p1; a++) {
+      Bt[(2 * k) * p1 + a] = v1[a];
+      Bt[(2 * k + 1) * p1 + a] = v2[a];
+    }
+    wc[k] = pts[3 * k + 2] * coef_from(G, A.p, x1, x2, e1, v1, d1, e2, v2, d2);
+  }
+}
+
+// regular elements whose Gauss points some row uses (hybrid Gauss, DWQ rest, Gauss method)
+__global__ void k_gauss_flags(Dir A, Dir B, const uint8_t *estate, const uint8_t *fstate,
+                              int method, int32_t *gflag) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= A.nel * B.nel) return;
+  int f = 0;
+  if (estate[e] == TW_ELEM_REGULAR && method != TW_METHOD_NAIVE) {
+    if (method == TW_METHOD_GAUSS) {
+      f = 1;
+    } else {
+      int e1 = e % A.nel, e2 = e / A.nel;
+      for (int b = 0; b <= B.p && !f; b++)
+        for (int a = 0; a <= A.p && !f; a++) f = fstate[(e2 + b) * A.n + (e1 + a)] == TW_FUNC_CUT;
+    }
+  }
+  gflag[e] = f;
+}
+
+__global__ void k_gauss_c(Geo G, Dir A, Dir B, const int32_t *glist, int ng, double *gc) {
+  int id = blockIdx.x * blockDim.x + threadIdx.x;
+  int p1 = A.p + 1;
+  if (id >= ng * p1 * p1) return;
+  int sl = id / (p1 * p1), g1 = id % p1, g2 = (id / p1) % p1;
+  int e = glist[sl], e1 = e % A.nel, e2 = e / A.nel;
+  double x1 = A.bp[e1] + (A.bp[e1 + 1] - A.bp[e1]) * 0.5 * (A.gx[g1] + 1.0);
+  double x2 = B.bp[e2] + (B.bp[e2 + 1] - B.bp[e2]) * 0.5 * (B.gx[g2] + 1.0);
+  gc[(size_t)sl * p1 * p1 + g2 * p1 + g1] =
+      coef_from(G, A.p, x1, x2, e1, A.GB + (e1 * p1 + g1) * p1, A.dGB + (e1 * p1 + g1) * p1, e2,
+                B.GB + (e2 * p1 + g2) * p1, B.dGB + (e2 * p1 + g2) * p1);
+}
+
+// ---------------------------------------------------------------------------
+// DWQ (Sect. 3.3)
+
+// R7: region R = R1 x R2 of regular elements with the most elements
+__global__ void k_dwq_choice(Dir A, Dir B, const uint8_t *estate, const uint8_t *fstate,
+                             int32_t *choice, int32_t *dflag0, int32_t *dflag1, int32_t *counter) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= A.n * B.n) return;
+  int32_t *out = choice + 4 * g;
+  out[0] = out[1] = out[2] = out[3] = -1;
+  if (fstate[g] != TW_FUNC_CUT) return;
+  int i[2] = {g % A.n, g / A.n};
+  const Dir *D[2] = {&A, &B};
+  int lo[2], hi[2], nopt[2];
+  for (int d = 0; d < 2; d++) {
+    lo[d] = max(0, i[d] - D[d]->p);
+    hi[d] = min(D[d]->nel - 1, i[d]);
+    nopt[d] = 1 + 2 * (hi[d] - lo[d]);
+  }
+  int bestn = 0, bestdisc = 0, bk[2] = {-1, -1}, bs[2] = {-1, -1};
+  for (int oa = 0; oa < nopt[0]; oa++)
+    for (int ob = 0; ob < nopt[1]; ob++) {
+      int kind[2], sv[2], r0[2], r1[2];
+      int oo[2] = {oa, ob};
+      for (int d = 0; d < 2; d++) {
+        int m = hi[d] - lo[d];
+        if (oo[d] == 0) { kind[d] = 0; sv[d] = -1; r0[d] = lo[d]; r1[d] = hi[d]; }
+        else if (oo[d] <= m) { kind[d] = 1; sv[d] = lo[d] + oo[d]; r0[d] = lo[d]; r1[d] = sv[d] - 1; }
+        else { kind[d] = 2; sv[d] = lo[d] + oo[d] - m; r0[d] = sv[d]; r1[d] = hi[d]; }
+      }
+      int nel = (r1[0] - r0[0] + 1) * (r1[1] - r0[1] + 1);
+      int disc = (kind[0] != 0) + (kind[1] != 0);
+      if (nel < bestn || (nel == bestn && disc >= bestdisc && bestn > 0)) continue;
+      int ok = 1;
+      for (int e2 = r0[1]; e2 <= r1[1] && ok; e2++)
+        for (int e1 = r0[0]; e1 <= r1[0] && ok; e1++)
+          ok = estate[e2 * A.nel + e1] == TW_ELEM_REGULAR;
+      if (!ok) continue;
+      bestn = nel;
+      bestdisc = disc;
+      bk[0] = kind[0]; bs[0] = sv[0]; bk[1] = kind[1]; bs[1] = sv[1];
+    }
+  if (bestn == 0) return;
+  out[0] = bk[0]; out[1] = bs[0]; out[2] = bk[1]; out[3] = bs[1];
+  if (bk[0]) dflag0[bs[0]] = 1;
+  if (bk[1]) dflag1[bs[1]] = 1;
+  atomicAdd(counter, 1);
+}
+
+// refined knot vector after inserting t = U[p+s] p more times
+__device__ __forceinline__ double ref_knot(const Dir &D, int s, int k) {
+  int p = D.p;
+  if (k <= p + s) return D.U[k];
+  if (k <= 2 * p + s) return D.U[p + s];
+  return D.U[k - p];
+}
+
+// values of the p+1 refined functions on the element e of x
+__device__ void ref_basis(const Dir &D, int s, int e, double x, double *N) {
+  int p = D.p;
+  int span = e + p + (e >= s ? p : 0);
+  double K[2 * TW_MAXP + 2];
+  for (int k = 0; k < 2 * p; k++) K[k] = ref_knot(D, s, span - p + 1 + k);
+  // triangular scheme with knots K[0..2p-1] = U'[span-p+1 .. span+p]
+  double left[TW_MAXP1], right[TW_MAXP1];
+  N[0] = 1.0;
+  for (int j = 1; j <= p; j++) {
+    left[j] = x - K[p - j];
+    right[j] = K[p - 1 + j] - x;
+    double saved = 0.0;
+    for (int r = 0; r < j; r++) {
+      double t = N[r] / (right[r + 1] + left[j - r]);
+      N[r] = saved + right[r + 1] * t;
+      saved = left[j - r] * t;
+    }
+    N[j] = saved;
+  }
+}
+
+// refined function m at x (0 if off its span)
+__device__ double ref_fn(const Dir &D, int s, int m, double x) {
+  int e = elem_of(D.bp, D.nel, x);
+  int span = e + D.p + (e >= s ? D.p : 0);
+  int a = m - (span - D.p);
+  if (a < 0 || a > D.p) return 0.0;
+  double N[TW_MAXP1];
+  ref_basis(D, s, e, x, N);
+  return N[a];
+}
+
+// One block per disc knot t = bp[s] of one direction: steps 1-4 of Sect. 3.3.
+__global__ void k_dwq_build(Dir D, const int32_t *disc_list, int ndisc, double *out_x,
+                            int32_t *out_np, double *out_w, int *flag) {
+  int slot = blockIdx.x;
+  if (slot >= ndisc) return;
+  int s = disc_list[slot];
+  int p = D.p, p1 = p + 1;
+  double t = D.bp[s];
+  __shared__ double xs[TW_LQMAX];
+  __shared__ int npts;
+  __shared__ double Sc[TW_MAXP][TW_MAXP1];             // S[i + r][i], i = s + col
+  __shared__ double Wt[2 * TW_MAXP][TW_LQMAX];         // refined weights of l = s + row
+  int ewlo = max(0, s - p), ewhi = min(D.nel - 1, s + p - 1);
+  if (threadIdx.x == 0) {
+    // refined points: base points + nested points next to t (R5)
+    int n = 0;
+    for (int e = ewlo; e <= ewhi; e++) {
+      int k0 = wq_off(e, p, D.nel), k1 = wq_off(e + 1, p, D.nel);
+      int m = k1 - k0;
+      int nb0 = n;
+      for (int k = k0; k < k1; k++) {
+        if (n < TW_LQMAX) xs[n] = D.xq[k];
+        n++;
+      }
+      if ((e == s - 1 || e == s) && m < p1) {
+        // gaps (a, x1), (x1, x2), (x2, b); fewest points first, ties: middle,
+        // then the gap next to t, then the other
+        int add = p1 - m;
+        double ed[4] = {D.bp[e], D.xq[k0], D.xq[k0 + 1], D.bp[e + 1]};
+        int cnt[3] = {0, 0, 0};
+        int nearg = (e == s - 1) ? 2 : 0;
+        int pref[3] = {1, nearg, 2 - nearg};
+        for (int r = 0; r < add; r++) {
+          int best = pref[0];
+          for (int k = 1; k < 3; k++)
+            if (cnt[pref[k]] < cnt[best]) best = pref[k];
+          cnt[best]++;
+        }
+        for (int gp = 0; gp < 3; gp++)
+          for (int j = 0; j < cnt[gp]; j++) {
+            if (n < TW_LQMAX)
+              xs[n] = ed[gp] + (ed[gp + 1] - ed[gp]) * (double)(j + 1) / (double)(cnt[gp] + 1);
+            n++;
+          }
+      }
+      if (n <= TW_LQMAX) sort_small(xs + nb0, n - nb0);
+    }
+    if (n > TW_LQMAX) {
+      atomicOr(flag, TWF_LQMAX);
+      n = 0;
+    }
+    npts = n;
+  }
+  // step 1: S columns by p local Boehm insertions (Eq. 10) on B_i's own knots
+  if (threadIdx.x < p) {
+    int i = s + threadIdx.x;
+    double tau[2 * TW_MAXP + 2], c[TW_MAXP1], cn[TW_MAXP1];
+    int L = p + 2;
+    for (int k = 0; k < L; k++) tau[k] = D.U[i + k];
+    c[0] = 1.0;
+    int nc = 1;
+    for (int r = 0; r < p; r++) {
+      int sp = 0;
+      for (int k = 0; k < L - 1; k++)
+        if (tau[k] <= t) sp = k;
+      for (int k = 0; k <= nc; k++) {
+        double al;
+        if (k <= sp - p) al = 1.0;
+        else if (k >= sp + 1) al = 0.0;
+        else al = (t - tau[k]) / (tau[k + p] - tau[k]);
+        double ck = k < nc ? c[k] : 0.0, ckm = k > 0 ? c[k - 1] : 0.0;
+        cn[k] = al * ck + (1.0 - al) * ckm;
+      }
+      nc++;
+      for (int k = 0; k < nc; k++) c[k] = cn[k];
+      for (int k = L; k > sp + 1; k--) tau[k] = tau[k - 1];
+      tau[sp + 1] = t;
+      L++;
+    }
+    for (int r = 0; r <= p; r++) Sc[threadIdx.x][r] = c[r];
+  }
+  __syncthreads();
+  int np_ = npts;
+  // step 3: WQ weights of the refined functions l = s .. s+2p-1 (Eq. 5)
+  if (threadIdx.x < 2 * p && np_ > 0) {
+    int l = s + threadIdx.x;
+    int nref = D.n + p;
+    double ul = ref_knot(D, s, l), uh = ref_knot(D, s, l + p + 1);
+    int rows[TW_WIN], m = 0;
+    for (int mm = max(0, l - p); mm <= min(nref - 1, l + p); mm++) {
+      double lo = fmax(ul, ref_knot(D, s, mm)), hi = fmin(uh, ref_knot(D, s, mm + p + 1));
+      if (hi > lo) rows[m++] = mm;
+    }
+    int cols[TW_QMAX], N = 0;
+    for (int k = 0; k < np_; k++)
+      if (xs[k] > ul && xs[k] < uh) {
+        if (N >= TW_QMAX) { atomicOr(flag, TWF_QMAX); N = 0; break; }
+        cols[N++] = k;
+      }
+    double A[TW_WIN * TW_QMAX], bb[TW_WIN], w[TW_QMAX], beta[TW_WIN];
+    for (int r = 0; r < m; r++) {
+      for (int c = 0; c < N; c++) A[r * TW_QMAX + c] = ref_fn(D, s, rows[r], xs[cols[c]]);
+      double acc = 0.0;
+      for (int e = ewlo; e <= ewhi; e++) {
+        double a = D.bp[e], b = D.bp[e + 1];
+        if (b <= ul || a >= uh) continue;
+        for (int g = 0; g < p1; g++) {
+          double x = a + (b - a) * 0.5 * (D.gx[g] + 1.0);
+          double N1[TW_MAXP1];
+          ref_basis(D, s, e, x, N1);
+          int span = e + p + (e >= s ? p : 0);
+          int al = l - (span - p), am = rows[r] - (span - p);
+          if (al < 0 || al > p || am < 0 || am > p) continue;
+          acc += D.gw[g] * 0.5 * (b - a) * N1[al] * N1[am];
+        }
+      }
+      bb[r] = acc;
+    }
+    for (int k = 0; k < np_; k++) Wt[threadIdx.x][k] = 0.0;
+    if (N > 0) {
+      if (minnorm_lq(m, N, A, TW_QMAX, bb, w, beta)) atomicOr(flag, TWF_SINGULAR);
+      for (int c = 0; c < N; c++) Wt[threadIdx.x][cols[c]] = w[c];
+    }
+  }
+  __syncthreads();
+  // step 4: w_i = sum over refined l on the side of S[l][i] w~_l  (reading R4)
+  for (int id = threadIdx.x; id < p * 2 * TW_LQMAX; id += blockDim.x) {
+    int col = id / (2 * TW_LQMAX), side = (id / TW_LQMAX) % 2, k = id % TW_LQMAX;
+    double acc = 0.0;
+    if (k < np_) {
+      int i = s + col;
+      for (int r = 0; r <= p; r++) {
+        int l = i + r;
+        int lside = (l <= p + s - 1) ? 0 : 1;
+        if (lside != side) continue;
+        acc += Sc[col][r] * Wt[l - s][k];
+      }
+    }
+    out_w[(((size_t)slot * p + col) * 2 + side) * TW_LQMAX + k] = acc;
+  }
+  for (int k = threadIdx.x; k < TW_LQMAX; k += blockDim.x)
+    out_x[(size_t)slot * TW_LQMAX + k] = k < np_ ? xs[k] : 0.0;
+  if (threadIdx.x == 0) out_np[slot] = np_;
+}
+
+__global__ void k_is_cut(const uint8_t *es, int32_t *f, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) f[i] = es[i] == TW_ELEM_CUT;
+}
+
+// ---------------------------------------------------------------------------
+// host orchestration
+
+static int read_flag(tw_patch *P, const char *stage) {
+  int f = 0;
+  if (check_cuda(cudaMemcpyAsync(&f, P->flag, sizeof(int), cudaMemcpyDeviceToHost, P->stream),
+                 stage))
+    return TW_ECUDA;
+  if (check_cuda(cudaStreamSynchronize(P->stream), stage)) return TW_ECUDA;
+  if (f) {
+    set_error("%s: device check failed (flags 0x%x: %s%s%s%s%s%s)", stage, f,
+              (f & TWF_BRCAP) ? "too many breakpoints in a cut element; " : "",
+              (f & TWF_HITCAP) ? "too many curve crossings in a cut element; " : "",
+              (f & TWF_SINGULAR) ? "singular WQ system; " : "",
+              (f & TWF_QMAX) ? "too many points in one support; " : "",
+              (f & TWF_LQMAX) ? "too many refined points around a disc; " : "",
+              (f & TWF_RULECAP) ? "region rule too long; " : "");
+    return (f & TWF_SINGULAR) ? TW_ECUDA : TW_EUNSUPPORTED;
+  }
+  return 0;
+}
+
+#define G1(n) (unsigned)(((n) + 255) / 256), 256, 0, st
+
+int build_tables(tw_patch *P) {
+  cudaStream_t st = P->stream;
+  Dir &A = P->d[0];
+  Dir &B = P->d[1];
+  int p = P->p, p1 = p + 1;
+  int rc;
+  int32_t *counters = (int32_t *)dalloc(P, 16 * sizeof(int32_t));
+  int64_t *tot64 = (int64_t *)dalloc(P, 4 * sizeof(int64_t));
+  int32_t *tot32 = (int32_t *)dalloc(P, 8 * sizeof(int32_t));
+  if (!counters || !tot64 || !tot32) return TW_ENOMEM;
+  cudaMemsetAsync(counters, 0, 16 * sizeof(int32_t), st);
+
+  // Gauss rules (p+1 for elements, qc for cut pieces)
+  double *qgx = (double *)dalloc(P, sizeof(double) * P->qc);
+  double *qgw = (double *)dalloc(P, sizeof(double) * P->qc);
+  for (int d = 0; d < 2; d++) {
+    Dir &D = P->d[d];
+    k_gauss_nodes<<<1, 32, 0, st>>>(p1, D.gx, D.gw);
+    TW_LAUNCH();
+  }
+  k_gauss_nodes<<<1, 64, 0, st>>>(P->qc, qgx, qgw);
+  TW_LAUNCH();
+
+  // WQ layout, basis tables, weights (Eq. 5)
+  for (int d = 0; d < 2; d++) {
+    Dir &D = P->d[d];
+    k_wq_points<<<G1(D.nq)>>>(D);
+    TW_LAUNCH();
+    k_wq_ranges<<<G1(D.n)>>>(D);
+    TW_LAUNCH();
+    k_gauss_tables<<<G1(D.nel * p1)>>>(D);
+    TW_LAUNCH();
+    k_wq_weights<<<G1(D.n)>>>(D, P->flag);
+    TW_LAUNCH();
+  }
+  if (P->curve.kind == TW_TRIM_BSPLINE3) {
+    k_curve_segments<<<G1(P->curve.nc)>>>(P->curve_ctrl, P->curve.nc, (double *)P->curve.seg,
+                                          (double *)P->curve.box);
+    TW_LAUNCH();
+  }
+  if ((rc = check_cuda(cudaGetLastError(), "wq tables"))) return rc;
+
+  // classification (Sect. 2.2)
+  int64_t ne = (int64_t)A.nel * B.nel, nf = (int64_t)A.n * B.n;
+  int32_t *aflag = (int32_t *)dalloc(P, sizeof(int32_t) * nf);
+  int32_t *cflag = (int32_t *)dalloc(P, sizeof(int32_t) * nf);
+  int32_t *cpos = (int32_t *)dalloc(P, sizeof(int32_t) * nf);
+  if (!aflag || !cflag || !cpos) return TW_ENOMEM;
+  k_classify_elems<<<G1(ne)>>>(P->curve, A, B, P->estate, P->flag);
+  TW_LAUNCH();
+  k_classify_funcs<<<G1(nf)>>>(A, B, P->estate, P->fstate, aflag, P->method, cflag, counters);
+  TW_LAUNCH();
+  if ((rc = exclusive_scan_i32(aflag, P->act, nf, tot32 + 0, st, P))) return rc;
+  if ((rc = exclusive_scan_i32(cflag, cpos, nf, tot32 + 1, st, P))) return rc;
+  // cut elements
+  int32_t *eflag = (int32_t *)dalloc(P, sizeof(int32_t) * ne);
+  int32_t *epos = (int32_t *)dalloc(P, sizeof(int32_t) * ne);
+  int32_t *gflag = (int32_t *)dalloc(P, sizeof(int32_t) * ne);
+  int32_t *gpos = (int32_t *)dalloc(P, sizeof(int32_t) * ne);
+  if (!eflag || !epos || !gflag || !gpos) return TW_ENOMEM;
+  k_is_cut<<<G1(ne)>>>(P->estate, eflag, ne);
+  TW_LAUNCH();
+  if ((rc = exclusive_scan_i32(eflag, epos, ne, tot32 + 2, st, P))) return rc;
+  k_gauss_flags<<<G1(ne)>>>(A, B, P->estate, P->fstate, P->method, gflag);
+  TW_LAUNCH();
+  if ((rc = exclusive_scan_i32(gflag, gpos, ne, tot32 + 3, st, P))) return rc;
+  // DWQ choice (R7) and disc flags
+  int32_t *dflag[2], *dpos[2];
+  for (int d = 0; d < 2; d++) {
+    dflag[d] = (int32_t *)dalloc(P, sizeof(int32_t) * (P->d[d].nel + 1));
+    dpos[d] = (int32_t *)dalloc(P, sizeof(int32_t) * (P->d[d].nel + 1));
+    if (!dflag[d] || !dpos[d]) return TW_ENOMEM;
+    cudaMemsetAsync(dflag[d], 0, sizeof(int32_t) * (P->d[d].nel + 1), st);
+  }
+  if (P->method == TW_METHOD_DWQ) {
+    k_dwq_choice<<<G1(nf)>>>(A, B, P->estate, P->fstate, P->choice, dflag[0], dflag[1],
+                             counters + 2);
+  } else {
+    cudaMemsetAsync(P->choice, 0xff, sizeof(int32_t) * 4 * nf, st);
+  }
+  TW_LAUNCH();
+  for (int d = 0; d < 2; d++)
+    if ((rc = exclusive_scan_i32(dflag[d], dpos[d], P->d[d].nel + 1, tot32 + 4 + d, st, P)))
+      return rc;
+  int32_t hc[8];
+  int32_t hcount[4];
+  cudaMemcpyAsync(hc, tot32, sizeof(hc), cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(hcount, counters, sizeof(hcount), cudaMemcpyDeviceToHost, st);
+  if ((rc = read_flag(P, "classification"))) return rc;
+  P->n_rows = hc[0];
+  P->ncutrows = hc[1];
+  P->ncut = hc[2];
+  P->ngslot = hc[3];
+  P->ndisc[0] = hc[4];
+  P->ndisc[1] = hc[5];
+  P->ncutfns = hcount[0];
+  P->n_interior = hcount[1];
+  P->ndwqrows = hcount[2];
+
+  // active numbering and CSR pattern (R11)
+  P->rowg = (int32_t *)dalloc(P, sizeof(int32_t) * (P->n_rows + 1));
+  P->row_ptr = (int64_t *)dalloc(P, sizeof(int64_t) * (P->n_rows + 1));
+  int64_t *cnt = (int64_t *)dalloc(P, sizeof(int64_t) * (P->n_rows + 1));
+  P->cutrows = (int32_t *)dalloc(P, sizeof(int32_t) * (P->ncutrows + 1));
+  P->cut_list = (int32_t *)dalloc(P, sizeof(int32_t) * (P->ncut + 1));
+  P->cut_off = (int64_t *)dalloc(P, sizeof(int64_t) * (P->ncut + 1));
+  int64_t *ccount = (int64_t *)dalloc(P, sizeof(int64_t) * (P->ncut + 1));
+  int32_t *glist = (int32_t *)dalloc(P, sizeof(int32_t) * (P->ngslot + 1));
+  P->gc = (double *)dalloc(P, sizeof(double) * ((size_t)P->ngslot * p1 * p1 + 1));
+  if (!P->rowg || !P->row_ptr || !cnt || !P->cutrows || !P->cut_list || !P->cut_off || !ccount ||
+      !glist || !P->gc)
+    return TW_ENOMEM;
+  k_act_finalize<<<G1(nf)>>>(aflag, P->act, P->rowg, nf);
+  TW_LAUNCH();
+  k_row_counts<<<G1(nf)>>>(A, B, P->act, cnt);
+  TW_LAUNCH();
+  if ((rc = exclusive_scan_i64(cnt, P->row_ptr, P->n_rows, tot64 + 0, st, P))) return rc;
+  k_set_last<<<1, 1, 0, st>>>(P->row_ptr, P->n_rows, tot64 + 0);
+  TW_LAUNCH();
+  k_compact<<<G1(nf)>>>(cflag, cpos, P->cutrows, nullptr, nf);
+  TW_LAUNCH();
+  k_compact<<<G1(ne)>>>(eflag, epos, P->cut_list, P->cut_slot, ne);
+  TW_LAUNCH();
+  k_compact<<<G1(ne)>>>(gflag, gpos, glist, P->gslot, ne);
+  TW_LAUNCH();
+
+  // c at the WQ grid (Eq. 6), sum-factorised for the spline geometry
+  double *Gt = nullptr;
+  if (P->geo.geom_kind == TW_GEOM_SPLINE && P->geo.coef_kind != TW_COEF_ONE) {
+    Gt = (double *)dalloc(P, sizeof(double) * 4 * (size_t)B.nq * A.n);
+    if (!Gt) return TW_ENOMEM;
+    k_geo_stageA<<<G1((int64_t)B.nq * A.n)>>>(P->geo, A, B, Gt);
+    TW_LAUNCH();
+  }
+  k_cgrid<<<G1((int64_t)A.nq * B.nq)>>>(P->geo, A, B, Gt, P->C);
+  TW_LAUNCH();
+  // element Gauss c tables
+  if (P->ngslot > 0) {
+    k_gauss_c<<<G1((int64_t)P->ngslot * p1 * p1)>>>(P->geo, A, B, glist, P->ngslot, P->gc);
+    TW_LAUNCH();
+  }
+  // cut-element rules: count, scan, fill
+  if (P->ncut > 0) {
+    k_cut_rule<<<G1(P->ncut)>>>(P->curve, A, B, P->cut_list, P->ncut, qgx, qgw, P->qc, ccount,
+                                nullptr, nullptr, P->flag);
+    TW_LAUNCH();
+    if ((rc = exclusive_scan_i64(ccount, P->cut_off, P->ncut, tot64 + 1, st, P))) return rc;
+    k_set_last<<<1, 1, 0, st>>>(P->cut_off, P->ncut, tot64 + 1);
+    TW_LAUNCH();
+  }
+  int64_t h64[2] = {0, 0};
+  cudaMemcpyAsync(h64, tot64, sizeof(h64), cudaMemcpyDeviceToHost, st);
+  if ((rc = read_flag(P, "cut rules"))) return rc;
+  P->nnz = h64[0];
+  P->ncutpts = P->ncut > 0 ? h64[1] : 0;
+  P->cut_pts = (double *)dalloc(P, sizeof(double) * (3 * P->ncutpts + 1));
+  P->cut_wc = (double *)dalloc(P, sizeof(double) * (P->ncutpts + 1));
+  P->cut_B = (double *)dalloc(P, sizeof(double) * (2 * P->ncutpts * p1 + 1));
+  if (!P->cut_pts || !P->cut_wc || !P->cut_B) return TW_ENOMEM;
+  if (P->ncut > 0) {
+    k_cut_rule<<<G1(P->ncut)>>>(P->curve, A, B, P->cut_list, P->ncut, qgx, qgw, P->qc, nullptr,
+                                P->cut_off, P->cut_pts, P->flag);
+    TW_LAUNCH();
+    k_cut_point_tables<<<P->ncut, 128, 0, st>>>(P->geo, A, B, P->cut_list, P->cut_off, P->ncut,
+                                                P->cut_pts, P->cut_B, P->cut_wc);
+    TW_LAUNCH();
+  }
+  // DWQ rules per disc knot
+  for (int d = 0; d < 2; d++) {
+    Dir &D = P->d[d];
+    int nd = P->ndisc[d];
+    P->dwq_x[d] = (double *)dalloc(P, sizeof(double) * ((size_t)nd * TW_LQMAX + 1));
+    P->dwq_np[d] = (int32_t *)dalloc(P, sizeof(int32_t) * (nd + 1));
+    P->dwq_w[d] = (double *)dalloc(P, sizeof(double) * ((size_t)nd * p * 2 * TW_LQMAX + 1));
+    int32_t *dlist = (int32_t *)dalloc(P, sizeof(int32_t) * (nd + 1));
+    if (!P->dwq_x[d] || !P->dwq_np[d] || !P->dwq_w[d] || !dlist) return TW_ENOMEM;
+    k_compact<<<G1(D.nel + 1)>>>(dflag[d], dpos[d], dlist, P->disc_slot[d], D.nel + 1);
+    TW_LAUNCH();
+    if (nd > 0) {
+      k_dwq_build<<<nd, 64, 0, st>>>(D, dlist, nd, P->dwq_x[d], P->dwq_np[d], P->dwq_w[d],
+                                     P->flag);
+      TW_LAUNCH();
+    }
+  }
+  if ((rc = check_cuda(cudaGetLastError(), "set-up kernels"))) return rc;
+  return read_flag(P, "patch set-up");
+}
+
+
+}  // namespace tw

@@ -1,0 +1,480 @@
+// tw_solve.cu -- L2 projection with the formed matrix (Sect. 4.2).
+//   rhs   b_i = the row's own quadrature rule applied to f * c (reading R9):
+//         interior rows  sum_{k1,k2} W1[i1,k1] W2[i2,k2] c f  (WQ, test function in W)
+//         cut rows       region rule + element Gauss + cut-element rule, as in formation
+//   CG    Jacobi-preconditioned CG on M_s = (M + M^T)/2 (reading R10); M^T is read
+//         through a permutation of the symmetric pattern, dot products reduce in a
+//         fixed order so the iteration is bitwise reproducible.
+#include <cmath>
+#include <cstring>
+
+#include "tw_internal.cuh"
+
+namespace tw {
+
+struct Func {
+  int kind;
+  double prm[4];
+  int q[2], nk[2], m1;
+  const double *U[2];
+  const double *coef;
+};
+
+__device__ __forceinline__ void phys_at(const Geo &G, const Dir &A, const Dir &B, double x1,
+                                        double x2, double *X) {
+  if (G.geom_kind != TW_GEOM_SPLINE) {
+    X[0] = x1;
+    X[1] = x2;
+    return;
+  }
+  int e1 = elem_of(A.bp, A.nel, x1), e2 = elem_of(B.bp, B.nel, x2);
+  double v1[TW_MAXP1], v2[TW_MAXP1];
+  basis_vals(A.U, e1 + A.p, x1, A.p, v1);
+  basis_vals(B.U, e2 + B.p, x2, B.p, v2);
+  X[0] = X[1] = 0.0;
+  for (int b = 0; b <= B.p; b++)
+    for (int a = 0; a <= A.p; a++) {
+      const double *pt = G.ctrl + 2 * ((size_t)(e2 + b) * G.n1 + (e1 + a));
+      X[0] += pt[0] * v1[a] * v2[b];
+      X[1] += pt[1] * v1[a] * v2[b];
+    }
+}
+
+__device__ double func_at(const Func &f, double x1, double x2, const double *X) {
+  switch (f.kind) {
+    case TW_FUNC_SPLINE: {
+      double N1[TW_MAXP1], N2[TW_MAXP1];
+      int s1 = find_span(f.U[0], f.q[0], f.nk[0] - f.q[0] - 1, x1);
+      int s2 = find_span(f.U[1], f.q[1], f.nk[1] - f.q[1] - 1, x2);
+      basis_vals(f.U[0], s1, x1, f.q[0], N1);
+      basis_vals(f.U[1], s2, x2, f.q[1], N2);
+      double s = 0.0;
+      for (int b = 0; b <= f.q[1]; b++)
+        for (int a = 0; a <= f.q[0]; a++)
+          s += f.coef[(size_t)(s2 - f.q[1] + b) * f.m1 + (s1 - f.q[0] + a)] * N1[a] * N2[b];
+      return s;
+    }
+    case TW_FUNC_SINSIN: return sin(f.prm[0] * X[0]) * sin(f.prm[1] * X[1]);
+    case TW_FUNC_SINCOS: return sin(f.prm[0] * X[0]) * cos(f.prm[1] * X[1]);
+    case TW_FUNC_GAUSS: {
+      double dx = X[0] - f.prm[1], dy = X[1] - f.prm[2];
+      return exp(-f.prm[0] * (dx * dx + dy * dy));
+    }
+  }
+  return 0.0;
+}
+
+__device__ __forceinline__ double fpoint(const Func &f, const Geo &G, const Dir &A, const Dir &B,
+                                         double x1, double x2) {
+  double X[2];
+  phys_at(G, A, B, x1, x2, X);
+  return func_at(f, x1, x2, X);
+}
+
+// f * c on the WQ grid
+__global__ void k_fc_grid(Func f, Geo G, Dir A, Dir B, const double *C, double *FC) {
+  int id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= A.nq * B.nq) return;
+  int k1 = id % A.nq, k2 = id / A.nq;
+  FC[id] = C[id] * fpoint(f, G, A, B, A.xq[k1], B.xq[k2]);
+}
+
+__global__ void k_rhs_interior(Dir A, Dir B, const uint8_t *fstate, const int32_t *act,
+                               const double *FC, double *b) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= A.n * B.n || fstate[g] != TW_FUNC_INTERIOR) return;
+  int i1 = g % A.n, i2 = g / A.n;
+  double s = 0.0;
+  for (int c2 = 0; c2 < B.qcnt[i2]; c2++) {
+    int k2 = B.qbeg[i2] + c2;
+    double t = 0.0;
+    for (int c1 = 0; c1 < A.qcnt[i1]; c1++)
+      t += A.W[(size_t)i1 * A.qmax + c1] * FC[(size_t)k2 * A.nq + A.qbeg[i1] + c1];
+    s += B.W[(size_t)i2 * B.qmax + c2] * t;
+  }
+  b[act[g]] = s;
+}
+
+// one thread per cut row: the same three parts as k_cutrows, applied to f
+__global__ void k_rhs_cut(RowArgs a, Func f, const int32_t *rows, int nrows, const double *FC,
+                          double *b) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrows) return;
+  const Dir &A = a.A;
+  const Dir &B = a.B;
+  const int P = A.p, p1 = P + 1;
+  int g = rows[r];
+  int i1 = g % A.n, i2 = g / A.n;
+  int kind;
+  if (a.method == TW_METHOD_GAUSS || a.method == TW_METHOD_HYBRID) kind = 0;
+  else if (a.method == TW_METHOD_NAIVE) kind = 1;
+  else kind = a.choice[4 * g] >= 0 ? 2 : 0;
+  int lo1 = max(0, i1 - P), hi1 = min(A.nel - 1, i1);
+  int lo2 = max(0, i2 - P), hi2 = min(B.nel - 1, i2);
+  int r0[2] = {1, 1}, r1[2] = {0, 0};
+  double sum = 0.0;
+  if (kind != 0) {
+    double rx[2][32], rw[2][32];
+    int rk[2][32], nr[2];
+    for (int d = 0; d < 2; d++) {
+      const Dir &D = d == 0 ? A : B;
+      int i = d == 0 ? i1 : i2;
+      int n = 0;
+      int ck = kind == 2 ? a.choice[4 * g + 2 * d] : 0;
+      int s = kind == 2 ? a.choice[4 * g + 2 * d + 1] : -1;
+      int lo = d == 0 ? lo1 : lo2, hi = d == 0 ? hi1 : hi2;
+      r0[d] = ck == 2 ? s : lo;
+      r1[d] = ck == 1 ? s - 1 : hi;
+      if (ck == 0) {
+        for (int c = 0; c < D.qcnt[i]; c++) {
+          rx[d][n] = D.xq[D.qbeg[i] + c];
+          rw[d][n] = D.W[(size_t)i * D.qmax + c];
+          rk[d][n] = D.qbeg[i] + c;
+          n++;
+        }
+      } else {
+        int side = ck - 1, sl = a.disc_slot[d][s];
+        double t = D.bp[s];
+        const double *xs = a.dwq_x[d] + (size_t)sl * TW_LQMAX;
+        const double *ws = a.dwq_w[d] + (((size_t)sl * P + (i - s)) * 2 + side) * TW_LQMAX;
+        for (int k = 0; k < a.dwq_np[d][sl] && n < 32; k++) {
+          double x = xs[k];
+          if (!(x > D.U[i] && x < D.U[i + P + 1])) continue;
+          if (side == 0 ? !(x < t) : !(x > t)) continue;
+          rx[d][n] = x;
+          rw[d][n] = ws[k];
+          rk[d][n] = -1;
+          n++;
+        }
+      }
+      nr[d] = n;
+    }
+    if (kind == 1) {  // region unused for element exclusion: naive uses no Gauss
+      r0[0] = r0[1] = 1;
+      r1[0] = r1[1] = 0;
+    }
+    for (int ib = 0; ib < nr[1]; ib++)
+      for (int ia = 0; ia < nr[0]; ia++) {
+        int k1 = rk[0][ia], k2 = rk[1][ib];
+        double v;
+        if (k1 >= 0 && k2 >= 0) {
+          v = FC[(size_t)k2 * A.nq + k1];
+          if (kind == 1 && a.estate[B.qel[k2] * A.nel + A.qel[k1]] != TW_ELEM_REGULAR) v = 0.0;
+        } else {
+          v = coef_at(a.G, A, B, rx[0][ia], rx[1][ib]) * fpoint(f, a.G, A, B, rx[0][ia], rx[1][ib]);
+        }
+        sum += rw[0][ia] * rw[1][ib] * v;
+      }
+  }
+  for (int e2 = lo2; e2 <= hi2; e2++)
+    for (int e1 = lo1; e1 <= hi1; e1++) {
+      int e = e2 * A.nel + e1;
+      uint8_t st = a.estate[e];
+      bool inR = e1 >= r0[0] && e1 <= r1[0] && e2 >= r0[1] && e2 <= r1[1];
+      if (st == TW_ELEM_REGULAR && kind != 1 && !inR) {
+        const double *cgp = a.gc + (size_t)a.gslot[e] * p1 * p1;
+        double h1 = 0.5 * (A.bp[e1 + 1] - A.bp[e1]), h2 = 0.5 * (B.bp[e2 + 1] - B.bp[e2]);
+        for (int g2 = 0; g2 < p1; g2++)
+          for (int g1 = 0; g1 < p1; g1++) {
+            double x1 = A.bp[e1] + h1 * (A.gx[g1] + 1.0), x2 = B.bp[e2] + h2 * (B.gx[g2] + 1.0);
+            double w = A.gw[g1] * h1 * B.gw[g2] * h2 * A.GB[(e1 * p1 + g1) * p1 + (i1 - e1)] *
+                       B.GB[(e2 * p1 + g2) * p1 + (i2 - e2)];
+            sum += w * cgp[g2 * p1 + g1] * fpoint(f, a.G, A, B, x1, x2);
+          }
+      } else if (st == TW_ELEM_CUT) {
+        int cs = a.cut_slot[e];
+        for (int64_t q = a.cut_off[cs]; q < a.cut_off[cs + 1]; q++) {
+          const double *Bv = a.cut_B + 2 * q * p1;
+          const double *xq = a.cut_pts + 3 * q;
+          sum += a.cut_wc[q] * Bv[i1 - e1] * Bv[p1 + (i2 - e2)] * fpoint(f, a.G, A, B, xq[0], xq[1]);
+        }
+      }
+    }
+  b[a.act[g]] = sum;
+}
+
+// ---------------------------------------------------------------------------
+// CG on (M + M^T)/2
+
+__global__ void k_perm(const int64_t *rp, const int32_t *col, int64_t n, int64_t *perm) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  for (int64_t k = rp[r]; k < rp[r + 1]; k++) {
+    int32_t j = col[k];
+    int64_t lo = rp[j], hi = rp[j + 1] - 1, pos = -1;
+    while (lo <= hi) {
+      int64_t m = (lo + hi) >> 1;
+      if (col[m] == r) { pos = m; break; }
+      if (col[m] < r) lo = m + 1;
+      else hi = m - 1;
+    }
+    perm[k] = pos;
+  }
+}
+
+__global__ void k_msym(const int64_t *rp, const int32_t *col, const double *val,
+                       const int64_t *perm, int64_t n, double *ms, double *dinv) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  double dg = 0.0;
+  for (int64_t k = rp[r]; k < rp[r + 1]; k++) {
+    double v = perm[k] >= 0 ? 0.5 * (val[k] + val[perm[k]]) : val[k];
+    ms[k] = v;
+    if (col[k] == r) dg = v;
+  }
+  dinv[r] = dg != 0.0 ? 1.0 / dg : 1.0;
+}
+
+// warp per row, fixed shuffle tree: deterministic
+__global__ void k_spmv(const int64_t *rp, const int32_t *col, const double *ms, const double *x,
+                       double *y, int64_t n) {
+  int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (r >= n) return;
+  double s = 0.0;
+  for (int64_t k = rp[r] + lane; k < rp[r + 1]; k += 32) s += ms[k] * x[col[k]];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) y[r] = s;
+}
+
+#define DOT_BLOCKS 256
+__global__ void k_dot_partial(const double *x, const double *y, int64_t n, double *part) {
+  __shared__ double sh[256];
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)DOT_BLOCKS * 256)
+    s += x[i] * y[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void k_dot_final(const double *part, double *out) {
+  __shared__ double sh[DOT_BLOCKS];
+  sh[threadIdx.x] = part[threadIdx.x];
+  __syncthreads();
+  for (int o = DOT_BLOCKS / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sh[0];
+}
+
+enum { S_RZ = 0, S_PQ, S_RZN, S_RR, S_BB };
+
+__global__ void k_cg_init(const double *b, const double *dinv, double *u, double *r, double *z,
+                          double *p, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  u[i] = 0.0;
+  r[i] = b[i];
+  z[i] = b[i] * dinv[i];
+  p[i] = z[i];
+}
+
+__global__ void k_cg_update1(const double *sc, const double *p, const double *q,
+                             const double *dinv, double *u, double *r, double *z, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double alpha = sc[S_RZ] / sc[S_PQ];
+  u[i] += alpha * p[i];
+  r[i] -= alpha * q[i];
+  z[i] = r[i] * dinv[i];
+}
+
+__global__ void k_cg_update2(const double *sc, const double *z, double *p, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double beta = sc[S_RZN] / sc[S_RZ];
+  p[i] = z[i] + beta * p[i];
+}
+
+__global__ void k_cg_roll(double *sc) { sc[S_RZ] = sc[S_RZN]; }
+
+static void dot(const double *x, const double *y, int64_t n, double *part, double *out,
+                cudaStream_t s) {
+  k_dot_partial<<<DOT_BLOCKS, 256, 0, s>>>(x, y, n, part);
+  TW_LAUNCH();
+  k_dot_final<<<1, DOT_BLOCKS, 0, s>>>(part, out);
+  TW_LAUNCH();
+}
+
+static Func make_func(const tw_func *f, tw_patch *P, int *rc) {
+  Func F;
+  memset(&F, 0, sizeof(F));
+  F.kind = f->kind;
+  for (int k = 0; k < 4; k++) F.prm[k] = f->prm[k];
+  *rc = 0;
+  if (f->kind < TW_FUNC_SPLINE || f->kind > TW_FUNC_GAUSS) {
+    set_error("unknown function kind %d", f->kind);
+    *rc = TW_EINVAL;
+    return F;
+  }
+  if (f->kind == TW_FUNC_SPLINE) {
+    size_t m = 1;
+    for (int d = 0; d < 2; d++) {
+      if (!f->knots[d] || f->p[d] < 0 || f->p[d] > TW_MAXP || f->nknots[d] < 2 * f->p[d] + 2) {
+        set_error("spline function: bad knots or degree");
+        *rc = TW_EINVAL;
+        return F;
+      }
+      F.q[d] = f->p[d];
+      F.nk[d] = f->nknots[d];
+      double *u = (double *)dalloc(P, sizeof(double) * f->nknots[d]);
+      if (!u) { *rc = TW_ENOMEM; return F; }
+      cudaMemcpyAsync(u, f->knots[d], sizeof(double) * f->nknots[d], cudaMemcpyHostToDevice,
+                      P->stream);
+      F.U[d] = u;
+      m *= (size_t)(f->nknots[d] - f->p[d] - 1);
+    }
+    F.m1 = f->nknots[0] - f->p[0] - 1;
+    double *c = (double *)dalloc(P, sizeof(double) * m);
+    if (!c || !f->coef) { *rc = c ? TW_EINVAL : TW_ENOMEM; return F; }
+    cudaMemcpyAsync(c, f->coef, sizeof(double) * m, cudaMemcpyHostToDevice, P->stream);
+    F.coef = c;
+  }
+  return F;
+}
+
+static RowArgs row_args(tw_patch *Pt) {
+  RowArgs ra;
+  ra.A = Pt->d[0];
+  ra.B = Pt->d[1];
+  ra.G = Pt->geo;
+  ra.estate = Pt->estate;
+  ra.fstate = Pt->fstate;
+  ra.act = Pt->act;
+  ra.rp = Pt->row_ptr;
+  ra.C = Pt->C;
+  ra.gslot = Pt->gslot;
+  ra.gc = Pt->gc;
+  ra.cut_slot = Pt->cut_slot;
+  ra.cut_off = Pt->cut_off;
+  ra.cut_B = Pt->cut_B;
+  ra.cut_wc = Pt->cut_wc;
+  ra.cut_pts = Pt->cut_pts;
+  ra.choice = Pt->choice;
+  for (int d = 0; d < 2; d++) {
+    ra.disc_slot[d] = Pt->disc_slot[d];
+    ra.dwq_x[d] = Pt->dwq_x[d];
+    ra.dwq_np[d] = Pt->dwq_np[d];
+    ra.dwq_w[d] = Pt->dwq_w[d];
+  }
+  ra.method = Pt->method;
+  ra.flag = Pt->flag;
+  return ra;
+}
+
+static int rhs_impl(tw_patch *P, const tw_func *f, double *b, cudaStream_t s) {
+  int rc = 0;
+  Func F = make_func(f, P, &rc);
+  if (rc) return rc;
+  Dir &A = P->d[0];
+  Dir &B = P->d[1];
+  int64_t ng = (int64_t)A.nq * B.nq;
+  double *FC = (double *)dalloc(P, sizeof(double) * ng);
+  if (!FC) return TW_ENOMEM;
+  k_fc_grid<<<(unsigned)((ng + 255) / 256), 256, 0, s>>>(F, P->geo, A, B, P->C, FC);
+  TW_LAUNCH();
+  if (P->method != TW_METHOD_GAUSS) {
+    int64_t nf = (int64_t)A.n * B.n;
+    k_rhs_interior<<<(unsigned)((nf + 255) / 256), 256, 0, s>>>(A, B, P->fstate, P->act, FC, b);
+    TW_LAUNCH();
+  }
+  if (P->ncutrows > 0) {
+    k_rhs_cut<<<(P->ncutrows + 63) / 64, 64, 0, s>>>(row_args(P), F, P->cutrows, P->ncutrows, FC, b);
+    TW_LAUNCH();
+  }
+  return check_cuda(cudaGetLastError(), "tw_rhs");
+}
+
+// temporary allocations are made on `s` and released in stream order
+int rhs_launch(tw_patch *P, const tw_func *f, double *b, cudaStream_t s) {
+  cudaStream_t keep = P->stream;
+  P->stream = s;
+  int mark = P->nallocs;
+  int rc = rhs_impl(P, f, b, s);
+  release_to(P, mark);
+  P->stream = keep;
+  return rc;
+}
+
+static int cg_impl(tw_patch *P, const tw_func *f, const int64_t *rp, const int32_t *col,
+                   const double *val, double *u, double tol, int maxit, int *iters,
+                   double *relres, cudaStream_t s) {
+  int64_t n = P->n_rows, nnz = P->nnz;
+  if (n == 0) {
+    if (iters) *iters = 0;
+    if (relres) *relres = 0.0;
+    return TW_OK;
+  }
+  double *buf = (double *)dalloc(P, sizeof(double) * (6 * n + DOT_BLOCKS + 8));
+  int64_t *perm = (int64_t *)dalloc(P, sizeof(int64_t) * (nnz + 1));
+  double *ms = (double *)dalloc(P, sizeof(double) * (nnz + 1));
+  if (!buf || !perm || !ms) return TW_ENOMEM;
+  double *b = buf, *r = b + n, *z = r + n, *p = z + n, *q = p + n, *dinv = q + n;
+  double *part = dinv + n, *sc = part + DOT_BLOCKS;
+  int rc = rhs_impl(P, f, b, s);
+  if (rc) return rc;
+  unsigned gb = (unsigned)((n + 255) / 256);
+  k_perm<<<gb, 256, 0, s>>>(rp, col, n, perm);
+  TW_LAUNCH();
+  k_msym<<<gb, 256, 0, s>>>(rp, col, val, perm, n, ms, dinv);
+  TW_LAUNCH();
+  k_cg_init<<<gb, 256, 0, s>>>(b, dinv, u, r, z, p, n);
+  TW_LAUNCH();
+  dot(r, z, n, part, sc + S_RZ, s);
+  dot(b, b, n, part, sc + S_BB, s);
+  double hb[5];
+  cudaMemcpyAsync(hb, sc, sizeof(hb), cudaMemcpyDeviceToHost, s);
+  if ((rc = check_cuda(cudaStreamSynchronize(s), "tw_l2_project"))) return rc;
+  double bn = sqrt(hb[S_BB]);
+  double rel = bn > 0 ? 1.0 : 0.0;
+  int it = 0;
+  unsigned gs = (unsigned)((n * 32 + 255) / 256);
+  const int CHECK = 8;
+  while (rel > tol && it < maxit) {
+    int nstep = maxit - it < CHECK ? maxit - it : CHECK;
+    for (int k = 0; k < nstep; k++) {
+      k_spmv<<<gs, 256, 0, s>>>(rp, col, ms, p, q, n);
+      TW_LAUNCH();
+      dot(p, q, n, part, sc + S_PQ, s);
+      k_cg_update1<<<gb, 256, 0, s>>>(sc, p, q, dinv, u, r, z, n);
+      TW_LAUNCH();
+      dot(r, z, n, part, sc + S_RZN, s);
+      k_cg_update2<<<gb, 256, 0, s>>>(sc, z, p, n);
+      TW_LAUNCH();
+      k_cg_roll<<<1, 1, 0, s>>>(sc);
+      TW_LAUNCH();
+    }
+    it += nstep;
+    dot(r, r, n, part, sc + S_RR, s);
+    cudaMemcpyAsync(hb, sc, sizeof(hb), cudaMemcpyDeviceToHost, s);
+    if ((rc = check_cuda(cudaStreamSynchronize(s), "tw_l2_project"))) return rc;
+    rel = bn > 0 ? sqrt(hb[S_RR]) / bn : 0.0;
+  }
+  if (iters) *iters = it;
+  if (relres) *relres = rel;
+  if (rel > tol) {
+    set_error("tw_l2_project: CG stopped at relative residual %.3e after %d iterations", rel, it);
+    return TW_ENOCONV;
+  }
+  return TW_OK;
+}
+
+int l2_project_run(tw_patch *P, const tw_func *f, const int64_t *rp, const int32_t *col,
+                   const double *val, double *u, double tol, int maxit, int *iters,
+                   double *relres, cudaStream_t s) {
+  cudaStream_t keep = P->stream;
+  P->stream = s;
+  int mark = P->nallocs;
+  int rc = cg_impl(P, f, rp, col, val, u, tol, maxit, iters, relres, s);
+  release_to(P, mark);
+  P->stream = keep;
+  return rc;
+}
+
+}  // namespace tw

@@ -1,0 +1,209 @@
+"""Parity of the sm_103a path (through the C-ABI) with the FP64 CPU oracle.
+
+Bar (FP64): CSR pattern, classification, active numbering and DWQ region
+choices bit-exact; WQ points/weights, cut-rule points, rhs and matrix values
+within 1e-12 relative Frobenius (the tolerance the method's FP64 form is held
+to); single entries within 1e-12 of the matrix's max entry.  Sizes span several
+tiles and ragged tails (nel1 != nel2, odd sizes); full-size patches compare
+seeded sampled rows against rows the oracle forms one by one.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+def gpu_patch(spec):
+    from paper_2101_08053_gb300 import Patch
+    return Patch(spec)
+
+
+def rel_fro(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def compare_full(spec, tol=TOL):
+    G = gpu_patch(spec)
+    O = oracle.Patch(spec)
+    assert (G.n1, G.n2, G.nq1, G.nq2, G.n_rows, G.nnz) == (O.n1, O.n2, O.nq1, O.nq2, O.n_rows, O.nnz)
+    es, fs, act = G.states()
+    oes, ofs, oact = O.states()
+    assert np.array_equal(es.cpu().numpy(), oes)
+    assert np.array_equal(fs.cpu().numpy(), ofs)
+    assert np.array_equal(act.cpu().numpy(), oact)
+    rp, col, val = G.form_mass("fp64")
+    torch.cuda.synchronize()
+    orp, ocol, oval = O.form()
+    assert np.array_equal(rp.cpu().numpy(), orp)
+    assert np.array_equal(col.cpu().numpy(), ocol)
+    v = val.cpu().numpy()
+    assert np.all(np.isfinite(v))
+    r = rel_fro(v, oval)
+    assert r <= tol, r
+    assert np.max(np.abs(v - oval)) <= tol * np.max(np.abs(oval))
+    return G, O, (rp, col, val), (orp, ocol, oval)
+
+
+@pytest.mark.parametrize("method", ["gauss", "hybrid", "dwq", "naive"])
+def test_config1_all_methods(method):
+    compare_full(synth.config1(method))
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("method", ["hybrid", "dwq"])
+def test_degrees_circle(p, method):
+    compare_full(synth.make_spec(p, (11, 14), synth.circle(0.47, 0.53, 0.3), method=method))
+
+
+@pytest.mark.parametrize("p", [3, 4, 5])
+@pytest.mark.parametrize("method", ["hybrid", "dwq"])
+def test_spline_geometry_spline_hole(p, method):
+    """Config-2 shape at 24 x 24 elements: perturbed bilinear geometry (c = det J)
+    and a seeded 12-point cubic B-spline hole."""
+    compare_full(synth.config2(p=p, nel=24, method=method, seed=1000 + p))
+
+
+@pytest.mark.parametrize("keep_inside", [False, True])
+def test_ellipse(keep_inside):
+    t = synth.ellipse(0.5, 0.5, 0.33, 0.17, 0.7, keep_inside=keep_inside)
+    compare_full(synth.make_spec(4, (19, 13), t, method="dwq"))
+
+
+def test_density_coefficient():
+    compare_full(synth.config5(nel=20))
+
+
+def test_untrimmed_and_high_cut_order():
+    compare_full(synth.make_spec(5, 9, {"kind": "none", "params": [], "ctrl": None}))
+    compare_full(synth.make_spec(3, 13, synth.circle(0.5, 0.5, 0.3), cut_order=9, method="dwq"))
+
+
+def test_config4_shaped_patches():
+    rng = np.random.default_rng(synth.BASE_SEED + 4)
+    for _ in range(3):
+        spec = synth.config4_patch(rng)
+        spec = synth.make_spec(spec["p"], (min(spec["nel"][0], 40), min(spec["nel"][1], 40)),
+                               spec["trim"], method="hybrid")
+        compare_full(spec)
+
+
+def test_tables_against_oracle():
+    spec = synth.config2(p=4, nel=20, method="dwq", seed=7)
+    G = gpu_patch(spec)
+    O = oracle.Patch(spec)
+    for d in (0, 1):
+        x = G.table(d).cpu().numpy()
+        assert np.allclose(x, O.wq_grid(d), rtol=0, atol=1e-15)
+    C = G.table(4).cpu().numpy().reshape(G.nq2, G.nq1)
+    assert rel_fro(C, O.cgrid()) < 1e-14
+    gx, _ = oracle.gauss_legendre(5)
+    assert np.allclose(G.table(9).cpu().numpy(), gx, atol=1e-15)
+    # cut-element rules as point sets
+    off = G.table(6).cpu().numpy()
+    cl = G.table(7).cpu().numpy()
+    pts = G.table(5).cpu().numpy().reshape(-1, 3)
+    assert len(cl) == G.n_cut_elems
+    for ci, e in enumerate(cl):
+        mine = pts[off[ci]:off[ci + 1]]
+        ref = O.cut_rule(int(e % G.nel1), int(e // G.nel1))
+        assert mine.shape == ref.shape
+        a = mine[np.lexsort((mine[:, 1], mine[:, 0]))]
+        b = ref[np.lexsort((ref[:, 1], ref[:, 0]))]
+        assert np.allclose(a, b, rtol=0, atol=1e-14)
+    # DWQ region choices
+    ch = G.table(8).cpu().numpy().reshape(-1, 4)
+    es, fs, act = O.states()
+    for g in np.where(fs == 2)[0]:
+        assert tuple(ch[g]) == O.dwq_choice(int(g % G.n1), int(g // G.n1))
+
+
+def test_determinism_bitwise():
+    spec = synth.config2(p=4, nel=48, method="dwq", seed=3)
+    G = gpu_patch(spec)
+    a = G.form_mass()[2].clone()
+    b = G.form_mass()[2].clone()
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    H = gpu_patch(spec)
+    c = H.form_mass()[2]
+    torch.cuda.synchronize()
+    assert torch.equal(a, c)
+
+
+@pytest.mark.parametrize("p,method", [(3, "hybrid"), (4, "dwq"), (5, "hybrid")])
+def test_full_size_config2_sampled_rows(p, method):
+    """512 x 512 elements (the benchmark's patches): the whole matrix from the
+    GPU, 400 seeded rows (and every cut row among the first 100k) against the
+    oracle's row-by-row formation."""
+    spec = synth.config2(p=p, nel=512, method=method)
+    G = gpu_patch(spec)
+    O = oracle.Patch(spec)
+    assert (G.n_rows, G.nnz) == (O.n_rows, O.nnz)
+    rp, col, val = G.form_mass()
+    torch.cuda.synchronize()
+    rp = rp.cpu().numpy()
+    col = col.cpu().numpy()
+    val = val.cpu().numpy()
+    assert np.all(np.isfinite(val))
+    rng = np.random.default_rng(p)
+    es, fs, act = O.states()
+    cut_rows = act[(fs == 2)]
+    rows = np.unique(np.concatenate([rng.integers(0, G.n_rows, 400), cut_rows[::7]]))
+    num = den = 0.0
+    for r in rows:
+        oc, ov = O.form_row(int(r))
+        assert np.array_equal(col[rp[r]:rp[r + 1]], oc)
+        mv = val[rp[r]:rp[r + 1]]
+        num += np.sum((mv - ov) ** 2)
+        den += np.sum(ov ** 2)
+    assert np.sqrt(num / den) <= TOL
+
+
+@pytest.mark.parametrize("method", ["hybrid", "dwq", "gauss"])
+def test_rhs_and_l2_projection(method):
+    spec = synth.make_spec(3, (17, 15), synth.circle(0.5, 0.5, 0.27), method=method)
+    G = gpu_patch(spec)
+    O = oracle.Patch(spec)
+    rng = np.random.default_rng(9)
+    fspl = synth.func_spline(spec, rng)
+    b = G.rhs(fspl).cpu().numpy()
+    ob = O.rhs(fspl)
+    assert rel_fro(b, ob) <= TOL
+    f = synth.func_sinsin()
+    assert rel_fro(G.rhs(f).cpu().numpy(), O.rhs(f)) <= TOL
+    csr = G.form_mass()
+    u, it, rel = G.l2_project(f, csr, tol=1e-12)
+    orp, ocol, oval = O.form()
+    ou, oit, orel = O.cg(orp, ocol, oval, O.rhs(f), tol=1e-12)
+    assert rel <= 1e-12
+    assert rel_fro(u.cpu().numpy(), ou) <= 1e-9
+    # reproduction of a function of the spline space (reading R9)
+    ua, _, _ = G.l2_project(fspl, csr, tol=1e-13)
+    es, fs, act = O.states()
+    a = fspl["coef"].ravel()[act >= 0]
+    assert np.max(np.abs(ua.cpu().numpy() - a)) < 1e-8
+
+
+def test_geometry_rhs_and_projection_det_j():
+    spec = synth.config2(p=3, nel=20, method="hybrid", seed=5)
+    G = gpu_patch(spec)
+    O = oracle.Patch(spec)
+    f = synth.func_sincos(2.0, 3.0)
+    assert rel_fro(G.rhs(f).cpu().numpy(), O.rhs(f)) <= TOL
+
+
+def test_cg_reports_non_convergence():
+    spec = synth.config1("hybrid")
+    G = gpu_patch(spec)
+    csr = G.form_mass()
+    from paper_2101_08053_gb300.api import TWError
+    with pytest.raises(TWError) as ei:
+        G.l2_project(synth.func_sinsin(), csr, tol=1e-14, maxit=2)
+    assert ei.value.code == -5
