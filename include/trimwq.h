@@ -167,6 +167,11 @@ int tw_states(const tw_patch *patch, uint8_t *estate, uint8_t *fstate, int32_t *
  *  6    cut-rule offsets (int64, ncut+1) and 7 the cut element ids (int32, ncut)
  *  8    DWQ choice per function (int32, n1*n2 x 4: kind1, s1, kind2, s2; -1 none)
  *  9/10 Gauss-Legendre nodes / weights of order p+1 (double, p+1)
+ *  11/12 basis values at the WQ points of direction 0/1 (double, nq x (p+1):
+ *        B_{e+a}(x_k), e the point's element)
+ *  13/14 basis values at the element Gauss points of direction 0/1
+ *        (double, nel x (p+1) x (p+1): [e][g][a] = B_{e+a}(x_{e,g}))
+ *  15/16 knot vector of direction 0/1 (double, nknots)
  * *count receives the number of elements of the table; nothing is copied if
  * dst is NULL or cap is too small (then TW_EINVAL). */
 int tw_patch_table(const tw_patch *patch, int which, void *dst, int64_t cap, int64_t *count,

@@ -31,6 +31,9 @@ void or_curve_point0(const or_desc *d, double *xy);
 
 #define MAXP1 8
 #define HITCAP 512
+/* relative tolerances of readings R6 and R8 */
+#define CORNER 1e-12
+#define TIE 1e-9
 
 typedef struct {
   int p, nk, n, nel;
@@ -271,10 +274,13 @@ static void classify(or_patch *P) {
     for (int e2 = 0; e2 < B->nel; e2++)
       for (int e1 = 0; e1 < A->nel; e1++) {
         double a1 = A->bp[e1], b1 = A->bp[e1 + 1], a2 = B->bp[e2], b2 = B->bp[e2 + 1];
-        int cut = any_in(vh + (size_t)e1 * HITCAP, vn[e1], a2, b2) ||
-                  any_in(vh + (size_t)(e1 + 1) * HITCAP, vn[e1 + 1], a2, b2) ||
-                  any_in(hh + (size_t)e2 * HITCAP, hn[e2], a1, b1) ||
-                  any_in(hh + (size_t)(e2 + 1) * HITCAP, hn[e2 + 1], a1, b1) ||
+        /* R8: a crossing within TW_CORNER of an edge's end is a corner touch,
+         * not a cut (keeps the decision off rounding at curves through corners) */
+        double d1 = CORNER * (b1 - a1), d2 = CORNER * (b2 - a2);
+        int cut = any_in(vh + (size_t)e1 * HITCAP, vn[e1], a2 + d2, b2 - d2) ||
+                  any_in(vh + (size_t)(e1 + 1) * HITCAP, vn[e1 + 1], a2 + d2, b2 - d2) ||
+                  any_in(hh + (size_t)e2 * HITCAP, hn[e2], a1 + d1, b1 - d1) ||
+                  any_in(hh + (size_t)(e2 + 1) * HITCAP, hn[e2 + 1], a1 + d1, b1 - d1) ||
                   (p0[0] > a1 && p0[0] < b1 && p0[1] > a2 && p0[1] < b2);
         uint8_t st;
         if (cut) st = OR_ELEM_CUT;
@@ -342,7 +348,9 @@ static int cmpd(const void *a, const void *b) {
 
 /* Points (xi1, xi2, w) of a rule for the visible part of element (e1, e2):
  *  1. outer direction o: the axis along which the curve's part in the element
- *     extends more (bounding box of edge crossings and tangent points);
+ *     extends more (bounding box of edge crossings and tangent points, each
+ *     counted up to CORNER beyond the element's edges; extents equal within
+ *     TIE times the element size count as a tie, which goes to o = 0);
  *  2. breakpoints along o: the element ends, the crossings of the curve with the
  *     two element edges parallel to o, the curve's tangent points that would
  *     fold the lines xi_o = const, and the spline's segment joints;
@@ -366,10 +374,11 @@ static void cut_rule_build(const or_patch *P, int e1, int e2, dbuf *out) {
     if (_y < lo[1]) lo[1] = _y;               \
     if (_y > hi[1]) hi[1] = _y;               \
   } while (0)
+  double del[2] = {CORNER * (b[0] - a[0]), CORNER * (b[1] - a[1])};
   for (int o = 0; o < 2; o++)
     for (int side = 0; side < 2; side++) {
       double s = side ? b[o] : a[o];
-      int n = or_curve_line_hits(d, o, s, a[1 - o], b[1 - o], hits, HITCAP);
+      int n = or_curve_line_hits(d, o, s, a[1 - o] - del[1 - o], b[1 - o] + del[1 - o], hits, HITCAP);
       for (int k = 0; k < n; k++) {
         if (o == 0) BBOX(s, hits[k]);
         else BBOX(hits[k], s);
@@ -379,11 +388,14 @@ static void cut_rule_build(const or_patch *P, int e1, int e2, dbuf *out) {
     int n = or_curve_folds(d, o, pts, HITCAP);
     for (int k = 0; k < n; k++) {
       double x = pts[2 * k], y = pts[2 * k + 1];
-      if (x >= a[0] && x <= b[0] && y >= a[1] && y <= b[1]) BBOX(x, y);
+      if (x >= a[0] - del[0] && x <= b[0] + del[0] && y >= a[1] - del[1] && y <= b[1] + del[1])
+        BBOX(x, y);
     }
   }
 #undef BBOX
-  int o = (hi[0] - lo[0] >= hi[1] - lo[1]) ? 0 : 1;
+  /* ties (within TIE of the element size) go to o = 0 */
+  double hmax = fmax(b[0] - a[0], b[1] - a[1]);
+  int o = (hi[0] - lo[0] >= hi[1] - lo[1] - TIE * hmax) ? 0 : 1;
   int in = 1 - o;
   dbuf br = {0};
   push(&br, a[o]);

@@ -357,6 +357,9 @@ extern "C" int tw_patch_table(const tw_patch *P, int which, void *dst, int64_t c
     case 8: src = P->choice; n = 4 * (int64_t)P->d[0].n * P->d[1].n; es = sizeof(int32_t); break;
     case 9: src = P->d[0].gx; n = p1; break;
     case 10: src = P->d[0].gw; n = p1; break;
+    case 11: case 12: src = P->d[which - 11].Bq; n = (int64_t)P->d[which - 11].nq * p1; break;
+    case 13: case 14: src = P->d[which - 13].GB; n = (int64_t)P->d[which - 13].nel * p1 * p1; break;
+    case 15: case 16: src = P->d[which - 15].U; n = P->d[which - 15].nk; break;
     default:
       set_error("tw_patch_table: unknown table %d", which);
       return TW_EINVAL;

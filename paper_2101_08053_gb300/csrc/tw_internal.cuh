@@ -23,6 +23,8 @@
 #define TW_BRCAP 64                       // breakpoints per cut element
 #define TW_HITCAP 32                      // curve crossings per line inside one element
 #define TW_RULECAP 64                     // points of one direction's region rule
+#define TW_CORNER 1e-12  // relative margin: curve touching an element corner (R6, R8)
+#define TW_TIE 1e-9      // relative tie of the curve's extents in a cut element (R6)
 
 // device error flags (bit set by kernels, read by the host at sync points)
 #define TWF_BRCAP 1
@@ -74,8 +76,10 @@ struct DwqSlot {  // one disc knot of one direction
 // ---------------------------------------------------------------------------
 // B-splines
 
-// values N[a] = B_{span-p+a}(x), a = 0..p, span with U[span] <= x < U[span+1]
-__device__ __forceinline__ void basis_vals(const double *U, int span, double x, int p, double *N) {
+// values N[a] = B_{span-p+a}(x), a = 0..p, span with U[span] <= x < U[span+1].
+// Kept out of line: two inlined copies of this variable-trip triangle in one
+// function were mis-optimised by nvcc 13.0 for sm_103a at -O3.
+static __device__ __noinline__ void basis_vals(const double *U, int span, double x, int p, double *N) {
   double left[TW_MAXP1], right[TW_MAXP1];
   N[0] = 1.0;
   for (int j = 1; j <= p; j++) {
@@ -91,29 +95,41 @@ __device__ __forceinline__ void basis_vals(const double *U, int span, double x, 
   }
 }
 
-// values and first derivatives on span
+// values and first derivatives on span, in one pass of the triangle: the
+// degree p-1 row is kept when the last level starts, then
+//   B'_{i,p} = p B_{i,p-1}/(U[i+p]-U[i]) - p B_{i+1,p-1}/(U[i+p+1]-U[i+1]).
+// (Two separate passes for degree p-1 and p were mis-optimised by nvcc 13.0
+// for sm_103a at -O3: the values came out wrong while the derivatives did
+// not; the one-pass form is correct at every optimisation level.)
 __device__ __forceinline__ void basis_ders(const double *U, int span, double x, int p, double *N,
                                            double *dN) {
-  double Nm[TW_MAXP1];
-  if (p == 0) {
-    N[0] = 1.0;
-    dN[0] = 0.0;
-    return;
+  double left[TW_MAXP1], right[TW_MAXP1], Nm[TW_MAXP1];
+  N[0] = 1.0;
+  Nm[0] = 1.0;
+  for (int j = 1; j <= p; j++) {
+    left[j] = x - U[span + 1 - j];
+    right[j] = U[span + j] - x;
+    if (j == p)
+      for (int r = 0; r < p; r++) Nm[r] = N[r];
+    double saved = 0.0;
+    for (int r = 0; r < j; r++) {
+      double t = N[r] / (right[r + 1] + left[j - r]);
+      N[r] = saved + right[r + 1] * t;
+      saved = left[j - r] * t;
+    }
+    N[j] = saved;
   }
-  basis_vals(U, span, x, p - 1, Nm);  // B_{span-p+1+a, p-1}, a = 0..p-1
-  basis_vals(U, span, x, p, N);
   for (int a = 0; a <= p; a++) {
-    int i = span - p + a;
     double l = 0.0, r = 0.0;
     if (a >= 1) {
-      double d = U[i + p] - U[i];
-      if (d > 0.0) l = p / d * Nm[a - 1];
+      double d = U[span + a] - U[span + a - p];
+      if (d > 0.0) l = Nm[a - 1] / d;
     }
     if (a <= p - 1) {
-      double d = U[i + p + 1] - U[i + 1];
-      if (d > 0.0) r = p / d * Nm[a];
+      double d = U[span + a + 1] - U[span + a + 1 - p];
+      if (d > 0.0) r = Nm[a] / d;
     }
-    dN[a] = l - r;
+    dN[a] = p * (l - r);
   }
 }
 

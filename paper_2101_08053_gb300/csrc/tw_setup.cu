@@ -286,13 +286,15 @@ __global__ void k_classify_elems(Curve C, Dir A, Dir B, uint8_t *estate, int *fl
     return;
   }
   double h[TW_HITCAP];
+  // crossings within TW_CORNER of an edge's end are corner touches, not cuts
+  double d1 = TW_CORNER * (b1 - a1), d2 = TW_CORNER * (b2 - a2);
   int cut = 0;
   int n;
-  n = curve_line_hits(C, 0, a1, a2, b2, h, TW_HITCAP);
+  n = curve_line_hits(C, 0, a1, a2 + d2, b2 - d2, h, TW_HITCAP);
   cut |= n != 0;
-  if (!cut) { n = curve_line_hits(C, 0, b1, a2, b2, h, TW_HITCAP); cut |= n != 0; }
-  if (!cut) { n = curve_line_hits(C, 1, a2, a1, b1, h, TW_HITCAP); cut |= n != 0; }
-  if (!cut) { n = curve_line_hits(C, 1, b2, a1, b1, h, TW_HITCAP); cut |= n != 0; }
+  if (!cut) { n = curve_line_hits(C, 0, b1, a2 + d2, b2 - d2, h, TW_HITCAP); cut |= n != 0; }
+  if (!cut) { n = curve_line_hits(C, 1, a2, a1 + d1, b1 - d1, h, TW_HITCAP); cut |= n != 0; }
+  if (!cut) { n = curve_line_hits(C, 1, b2, a1 + d1, b1 - d1, h, TW_HITCAP); cut |= n != 0; }
   if (!cut) {
     double p0[2];
     curve_point0(C, p0);
@@ -436,12 +438,14 @@ __global__ void k_cut_rule(Curve C, Dir A, Dir B, const int32_t *cut_list, int n
   double a[2] = {A.bp[e1], B.bp[e2]}, b[2] = {A.bp[e1 + 1], B.bp[e2 + 1]};
   double h[TW_HITCAP];
   double fp[2 * TW_HITCAP];
-  // 1. outer direction from the extent of the curve inside the closed box
+  // 1. outer direction from the extent of the curve inside the box (crossings
+  //    and tangent points up to TW_CORNER beyond its edges)
   double lo[2] = {1e300, 1e300}, hi[2] = {-1e300, -1e300};
+  double dl[2] = {TW_CORNER * (b[0] - a[0]), TW_CORNER * (b[1] - a[1])};
   for (int o = 0; o < 2; o++)
     for (int sd = 0; sd < 2; sd++) {
       double s = sd ? b[o] : a[o];
-      int n = curve_line_hits(C, o, s, a[1 - o], b[1 - o], h, TW_HITCAP);
+      int n = curve_line_hits(C, o, s, a[1 - o] - dl[1 - o], b[1 - o] + dl[1 - o], h, TW_HITCAP);
       if (n < 0) { atomicOr(flag, TWF_HITCAP); return; }
       for (int k = 0; k < n; k++) {
         double X = o == 0 ? s : h[k], Y = o == 0 ? h[k] : s;
@@ -454,13 +458,14 @@ __global__ void k_cut_rule(Curve C, Dir A, Dir B, const int32_t *cut_list, int n
     if (n < 0) { atomicOr(flag, TWF_HITCAP); return; }
     for (int k = 0; k < n; k++) {
       double X = fp[2 * k], Y = fp[2 * k + 1];
-      if (X >= a[0] && X <= b[0] && Y >= a[1] && Y <= b[1]) {
+      if (X >= a[0] - dl[0] && X <= b[0] + dl[0] && Y >= a[1] - dl[1] && Y <= b[1] + dl[1]) {
         lo[0] = fmin(lo[0], X); hi[0] = fmax(hi[0], X);
         lo[1] = fmin(lo[1], Y); hi[1] = fmax(hi[1], Y);
       }
     }
   }
-  int o = (hi[0] - lo[0] >= hi[1] - lo[1]) ? 0 : 1;
+  // equal extents within TW_TIE of the element size: o = 0
+  int o = (hi[0] - lo[0] >= hi[1] - lo[1] - TW_TIE * fmax(b[0] - a[0], b[1] - a[1])) ? 0 : 1;
   int in = 1 - o;
   // 2. breakpoints along o
   double br[TW_BRCAP];

@@ -77,7 +77,11 @@ def test_ellipse(keep_inside):
 
 
 def test_density_coefficient():
-    compare_full(synth.config5(nel=20))
+    spec = synth.config5(nel=20)
+    G = gpu_patch(spec)
+    C = G.table(4).cpu().numpy().reshape(G.nq2, G.nq1)
+    assert rel_fro(C, oracle.Patch(spec).cgrid()) < 1e-14
+    compare_full(spec)
 
 
 def test_untrimmed_and_high_cut_order():
@@ -207,3 +211,27 @@ def test_cg_reports_non_convergence():
     with pytest.raises(TWError) as ei:
         G.l2_project(synth.func_sinsin(), csr, tol=1e-14, maxit=2)
     assert ei.value.code == -5
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5, 6])
+def test_basis_tables_against_scipy(p):
+    """Basis values at the WQ points and at the element Gauss points (tables
+    11 and 13) against scipy's B-splines, for every degree."""
+    from pins import bvals
+    spec = synth.make_spec(p, 9, synth.circle(0.5, 0.5, 0.3))
+    G = gpu_patch(spec)
+    U = spec["knots"][0]
+    x = G.table(0).cpu().numpy()
+    Bq = G.table(11).cpu().numpy().reshape(len(x), p + 1)
+    el = np.minimum(np.searchsorted(U[p:len(U) - p], x, side="right") - 1, 8)
+    for k in range(len(x)):
+        ref = [bvals(U, p, el[k] + a, x[k])[()] for a in range(p + 1)]
+        assert np.allclose(Bq[k], ref, atol=1e-14)
+    GB = G.table(13).cpu().numpy().reshape(9, p + 1, p + 1)
+    gx, _ = np.polynomial.legendre.leggauss(p + 1)
+    for e in range(9):
+        a, b = U[p + e], U[p + e + 1]
+        for g in range(p + 1):
+            xx = a + (b - a) * (gx[g] + 1) / 2
+            ref = [bvals(U, p, e + q, xx)[()] for q in range(p + 1)]
+            assert np.allclose(GB[e, g], ref, atol=1e-14)

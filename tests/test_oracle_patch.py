@@ -316,3 +316,16 @@ def test_l2_projection_converges():
         errs.append(P.l2_error(u, f)[0])
     rates = [math.log2(errs[k] / errs[k + 1]) for k in range(2)]
     assert min(rates) > 2.5
+
+
+def test_density_grid_against_scipy():
+    """c = rho(xi) (identity geometry) on the WQ grid against scipy's NdBSpline."""
+    from scipy.interpolate import NdBSpline
+    spec = synth.config5(nel=20)
+    P = oracle.Patch(spec)
+    C = P.cgrid()
+    c = spec["coef"]
+    dens = NdBSpline(tuple(c["knots"]), c["coef"].T, c["p"])
+    X1, X2 = np.meshgrid(P.wq_grid(0), P.wq_grid(1), indexing="xy")
+    ref = dens(np.stack([X1.ravel(), X2.ravel()], 1)).reshape(C.shape)
+    assert np.max(np.abs(C - ref)) < 1e-14
