@@ -1,0 +1,394 @@
+#!/usr/bin/env python3
+"""Benchmark: trimmed mass-matrix nnz formed per second on GB300.
+
+Workload (the paper's "plain FP64" shape, Sect. 4): twelve trimmed patches --
+degrees p = 3, 4, 5 x 128^2 and 512^2 elements x hybrid Gauss and
+discontinuous weighted quadrature -- each a perturbed bilinear geometry
+(c = det J) with a seeded 12-point cubic B-spline hole of radius 0.3 +- 0.05.
+One step forms all twelve from their host descriptors: every table kernel
+(WQ points and weights, classification, cut-element rules, DWQ rules, CSR
+pattern) and the formation kernels, writing FP64 CSR into resident buffers.
+value = nnz of the twelve matrices / step time.
+
+The --impl reference arm times the CPU oracle (single thread) on a bounded
+sample of the same workload: full set-up of each patch plus a seeded sample
+of rows, extrapolated to the whole matrix.
+
+Multi-GPU: the path has no exchange step; each rank forms its own copy of the
+workload (weak scaling, replicas), timings are max-reduced over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOAD = [(p, nel, m) for nel in (128, 512) for p in (3, 4, 5) for m in ("hybrid", "dwq")]
+METRIC = "trimmed mass-matrix nnz formed/sec"
+UNIT = "nnz/s"
+
+
+def specs():
+    return [synth.config2(p=p, nel=nel, method=m) for (p, nel, m) in WORKLOAD]
+
+
+def workload_name():
+    return ("config-2 sweep: p in {3,4,5} x {128^2, 512^2} elements x {hybrid Gauss, DWQ}; "
+            "perturbed bilinear geometry (c = det J), seeded 12-point cubic B-spline hole "
+            "r = 0.3 +- 0.05; FP64 CSR")
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu), "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work of the interior-row kernel (for the roofline)
+
+
+def _points_per_element(p, nel):
+    npe = np.full(nel, 2, dtype=np.int64)
+    npe[0] = npe[-1] = p + 1
+    return npe
+
+
+def _overlap_points(p, nel):
+    """ov[i, r] = WQ points in supp B_i cap supp B_j, j = i - p + r."""
+    n = nel + p
+    npe = _points_per_element(p, nel)
+    cs = np.concatenate([[0], np.cumsum(npe)])
+    ov = np.zeros((n, 2 * p + 1), dtype=np.int64)
+    for i in range(n):
+        for r in range(2 * p + 1):
+            j = i - p + r
+            if j < 0 or j >= n:
+                continue
+            lo = max(max(0, i - p), max(0, j - p))
+            hi = min(min(nel - 1, i), min(nel - 1, j))
+            if hi >= lo:
+                ov[i, r] = cs[hi + 1] - cs[lo]
+    return ov, cs
+
+
+def interior_flops(p, nel, fstate):
+    """FP64 flops the sum-factorised WQ contraction of the interior rows needs:
+    stage 2, one FMA per point of supp B_i cap supp B_j in direction 1 for
+    every output; stage 1, one FMA per point of the same overlap in direction
+    2 for every (i2, j2, k1) with k1 a point some interior row of i2 uses."""
+    n = nel + p
+    ov, cs = _overlap_points(p, nel)
+    fs = fstate.reshape(n, n)  # [i2, i1]
+    interior = fs == 1
+    valid = np.zeros((n, 2 * p + 1), dtype=bool)
+    for r in range(2 * p + 1):
+        j = np.arange(n) - p + r
+        valid[:, r] = (j >= 0) & (j < n)
+    s1 = (2 * ov * valid).sum(axis=1)         # per i1: sum_r1 2 ov1
+    nr = valid.sum(axis=1)                    # valid r per i
+    stage2 = float(np.sum(interior * (nr[:, None] * s1[None, :])))
+    qlo = np.array([cs[max(0, i - p)] for i in range(n)])
+    qhi = np.array([cs[min(nel - 1, i) + 1] for i in range(n)])
+    stage1 = 0.0
+    s2 = (2 * ov * valid).sum(axis=1)
+    for i2 in range(n):
+        rows = np.where(interior[i2])[0]
+        if len(rows) == 0:
+            continue
+        mask = np.zeros(cs[-1], dtype=bool)
+        for i1 in rows:
+            mask[qlo[i1]:qhi[i1]] = True
+        stage1 += float(s2[i2] * mask.sum())
+    return stage1 + stage2
+
+
+# ---------------------------------------------------------------------------
+
+
+def fp64_peak_gflops():
+    """FP64 (DFMA) rate of a GB300, as the profiling recipe lists it."""
+    return 1250.0
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2101_08053_gb300 import api
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    api.load()
+    stream = torch.cuda.current_stream()
+    sp = specs()
+    # one build per spec to size the resident outputs
+    outs, infos = [], []
+    for s in sp:
+        P = api.Patch(s)
+        outs.append(P.alloc_csr("fp64"))
+        infos.append((P.n_rows, P.nnz, P.n_cut_fns, P.n_cut_elems, P.n_dwq_rows))
+        P.close()
+    nnz_step = sum(i[1] for i in infos)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        for s, out in zip(sp, outs):
+            P = api.Patch(s)
+            P.form_mass("fp64", out=out)
+            P.close()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    api.profile_enable(True)
+    for st in api.STAGES:
+        api.profile_read(st)
+    clk = ClockSampler(local_rank) if rank == 0 else None
+    if clk:
+        clk.start()
+        time.sleep(0.4)
+    launches0 = api.launch_count()
+    times = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)  # L2 flush between timed steps (outside the events)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    launches = api.launch_count() - launches0
+    clocks = clk.stop() if clk else None
+    api.profile_enable(False)
+    stage = {k: api.profile_read(k) for k in api.STAGES}
+    ms_local = float(np.mean(times))
+    if world > 1:
+        t = torch.tensor([ms_local], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    else:
+        ms = ms_local
+    value = world * nnz_step / (ms * 1e-3)
+
+    # end to end through the C-ABI with host buffers: descriptors from host
+    # memory, CSR copied back to pinned host buffers, inside the timed region
+    host = [(torch.empty(o[0].numel(), dtype=torch.int64, pin_memory=True),
+             torch.empty(o[1].numel(), dtype=torch.int32, pin_memory=True),
+             torch.empty(o[2].numel(), dtype=torch.float64, pin_memory=True)) for o in outs]
+    h2d = 0
+    for s in sp:
+        h2d += sum(np.asarray(u).nbytes for u in s["knots"]) + np.asarray(s["trim"]["ctrl"]).nbytes
+        h2d += np.asarray(s["geom"]["ctrl"]).nbytes
+    d2h = sum(o[0].numel() * 8 + o[1].numel() * 4 + o[2].numel() * 8 for o in outs)
+
+    def e2e_step():
+        for s, out, h in zip(sp, outs, host):
+            P = api.Patch(s)
+            P.form_mass("fp64", out=out)
+            for a, b in zip(h, out):
+                a.copy_(b, non_blocking=True)
+            P.close()
+        torch.cuda.synchronize()
+
+    e2e_step()
+    et = []
+    for _ in range(max(1, min(args.steps, 3))):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_step()
+        et.append(time.perf_counter() - t0)
+    e2e_ms = float(np.mean(et)) * 1e3
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    # roofline of the dominant kernel (interior rows, FP64 DFMA-bound)
+    flops = 0.0
+    for s in sp:
+        P = api.Patch(s)
+        _, fs, _ = P.states()
+        flops += interior_flops(s["p"], s["nel"][0], fs.cpu().numpy())
+        P.close()
+    int_ms, int_n = stage["interior"]
+    launches_per_step = int_n / max(1, args.steps)
+    avg_launch_ms = int_ms / max(1, int_n)
+    flops_per_launch = flops / max(1, launches_per_step)
+    achieved = flops_per_launch / (avg_launch_ms * 1e-3) / 1e12
+    peak = fp64_peak_gflops() / 1e3
+    stage_ms = {k: round(v[0] / max(1, args.steps), 3) for k, v in stage.items() if v[1]}
+    return {
+        "value": value, "ms": ms, "nnz_step": nnz_step, "infos": infos, "launches": launches,
+        "clocks": clocks, "e2e_ms": e2e_ms, "h2d": h2d, "d2h": d2h, "stage_ms": stage_ms,
+        "roofline": {"bound": "alu", "kernel": "k_interior (interior rows, WQ + sum factorisation)",
+                     "achieved": round(achieved, 4), "peak": peak, "unit": "TFLOP/s",
+                     "frac": round(achieved / peak, 4), "traffic": None,
+                     "flops_per_launch": flops_per_launch, "avg_launch_ms": avg_launch_ms,
+                     "peak_source": "FP64 rate listed by the profiling recipe (not measured)"},
+    }
+
+
+def oracle_sample(seconds_budget=None, rows_per_patch=300, seed=0):
+    """Oracle time for the whole workload, extrapolated from full set-up plus a
+    seeded sample of rows per patch (single thread)."""
+    import oracle
+
+    rng = np.random.default_rng(seed)
+    t_full = 0.0
+    nnz = 0
+    cpu0 = time.process_time()
+    for s in specs():
+        t0 = time.perf_counter()
+        O = oracle.Patch(s)
+        t_setup = time.perf_counter() - t0
+        rows = rng.integers(0, O.n_rows, rows_per_patch)
+        t0 = time.perf_counter()
+        for r in rows:
+            O.form_row(int(r))
+        t_rows = time.perf_counter() - t0
+        t_full += t_setup + t_rows * O.n_rows / rows_per_patch
+        nnz += O.nnz
+    cpu = time.process_time() - cpu0
+    return nnz / t_full, t_full, cpu
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    config = {"workload": workload_name(), "patches": len(WORKLOAD), "p": [3, 4, 5],
+              "elements": ["128x128", "512x512"], "methods": ["hybrid", "dwq"],
+              "l2": "flushed between timed steps (256 MB write); outputs > L2"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        for _ in range(args.warmup):
+            oracle_sample(rows_per_patch=100)
+        vals, walls, cpus = [], [], []
+        for k in range(args.steps):
+            v, t, c = oracle_sample(rows_per_patch=100, seed=k)
+            vals.append(v)
+            walls.append(t)
+            cpus.append(c)
+        value = float(np.mean(vals))
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": float(np.mean(walls)) * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": config,
+                "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                 "sample": "full set-up of all 12 patches + 100 seeded rows "
+                                           "per patch, extrapolated per row"},
+                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    if world > 1:
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    r = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline:
+            v, t, c = oracle_sample()
+            cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": "full set-up of all 12 patches + 300 seeded rows per patch, "
+                             "time extrapolated per row to the whole matrices "
+                             "(%.1f s of CPU)" % c}
+        line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": dict(config, nnz_per_step=r["nnz_step"],
+                                                    parallelism="replicas" if world > 1 else "single"),
+                "e2e": {"value": world * r["nnz_step"] / (r["e2e_ms"] * 1e-3), "unit": UNIT,
+                        "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]},
+                "gpu_launches": r["launches"], "clocks": r["clocks"], "roofline": r["roofline"],
+                "cpu_baseline": cpu, "stage_ms_per_step": r["stage_ms"]}
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -180,6 +180,21 @@ int tw_patch_table(const tw_patch *patch, int which, void *dst, int64_t cap, int
 /* Number of kernels this library has launched in this process. */
 int64_t tw_launch_count(void);
 
+/* Stage timing with CUDA events recorded on the launching stream around each
+ * stage (off by default; the paper splits its timings the same way, Sect. 4.2:
+ * quadrature set-up, interior rows, regular part and cut elements of cut rows).
+ * tw_profile_read waits for the recorded events, returns the summed device
+ * time in ms and the number of launches of `stage` since the last read, and
+ * resets that stage. */
+#define TW_STAGE_SETUP 0     /* tw_patch_create: all table kernels            */
+#define TW_STAGE_INTERIOR 1  /* interior rows: WQ + sum factorisation kernel   */
+#define TW_STAGE_CUTROWS 2   /* cut rows: region + element Gauss + cut rule   */
+#define TW_STAGE_RHS 3
+#define TW_STAGE_CG 4
+#define TW_NSTAGES 5
+int tw_profile_enable(int on);
+int tw_profile_read(int stage, double *total_ms, int64_t *count);
+
 const char *tw_last_error(void);
 
 #ifdef __cplusplus

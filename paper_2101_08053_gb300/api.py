@@ -85,6 +85,8 @@ def load(build: bool = True):
     L.tw_states.argtypes = [vp, vp, vp, vp, vp]
     L.tw_patch_table.argtypes = [vp, C.c_int, vp, C.c_int64, i64p, vp]
     L.tw_launch_count.restype = C.c_int64
+    L.tw_profile_enable.argtypes = [C.c_int]
+    L.tw_profile_read.argtypes = [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
     L.tw_last_error.restype = C.c_char_p
     _lib = L
     return L
@@ -273,3 +275,18 @@ class Patch:
 
 def launch_count() -> int:
     return int(load().tw_launch_count())
+
+
+STAGES = {"setup": 0, "interior": 1, "cutrows": 2, "rhs": 3, "cg": 4}
+
+
+def profile_enable(on: bool = True):
+    _check(load().tw_profile_enable(int(bool(on))))
+
+
+def profile_read(stage: str):
+    """(total device ms, launches) of a stage since the last read."""
+    ms = C.c_double(0)
+    n = C.c_int64(0)
+    _check(load().tw_profile_read(STAGES[stage], C.byref(ms), C.byref(n)))
+    return ms.value, n.value

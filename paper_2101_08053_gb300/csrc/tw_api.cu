@@ -8,11 +8,38 @@
 #include <cstdlib>
 #include <cstring>
 
+#include <vector>
+
 #include "tw_internal.cuh"
 
 namespace tw {
 
 int64_t g_launches = 0;
+
+// ---- stage profiler: event pairs on the launching stream ----
+struct ProfRec {
+  int stage;
+  cudaEvent_t a, b;
+};
+static bool g_prof_on = false;
+static std::vector<ProfRec> g_prof;
+
+int prof_start(cudaStream_t s) {
+  if (!g_prof_on) return -1;
+  ProfRec r;
+  r.stage = -1;
+  cudaEventCreate(&r.a);
+  cudaEventCreate(&r.b);
+  cudaEventRecord(r.a, s);
+  g_prof.push_back(r);
+  return (int)g_prof.size() - 1;
+}
+
+void prof_stop(int slot, int stage, cudaStream_t s) {
+  if (slot < 0 || slot >= (int)g_prof.size()) return;
+  g_prof[slot].stage = stage;
+  cudaEventRecord(g_prof[slot].b, s);
+}
 static thread_local char g_err[1024] = "";
 
 void set_error(const char *fmt, ...) {
@@ -83,6 +110,37 @@ using namespace tw;
 
 extern "C" const char *tw_last_error(void) { return g_err; }
 extern "C" int64_t tw_launch_count(void) { return g_launches; }
+
+extern "C" int tw_profile_enable(int on) {
+  g_prof_on = on != 0;
+  return TW_OK;
+}
+
+extern "C" int tw_profile_read(int stage, double *total_ms, int64_t *count) {
+  if (stage < 0 || stage >= TW_NSTAGES) {
+    set_error("tw_profile_read: unknown stage %d", stage);
+    return TW_EINVAL;
+  }
+  double ms = 0.0;
+  int64_t n = 0;
+  std::vector<ProfRec> keep;
+  for (auto &r : g_prof) {
+    if (r.stage != stage) {
+      keep.push_back(r);
+      continue;
+    }
+    float t = 0.f;
+    cudaEventSynchronize(r.b);
+    if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) ms += t;
+    n++;
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  g_prof.swap(keep);
+  if (total_ms) *total_ms = ms;
+  if (count) *count = n;
+  return TW_OK;
+}
 
 extern "C" int tw_patch_destroy(tw_patch *P) {
   if (!P) return TW_OK;
@@ -274,7 +332,11 @@ extern "C" int tw_patch_create(const tw_patch_desc *desc, tw_patch **out) {
     ALLOC(P->C, double, (size_t)A.nq * B.nq);
     ALLOC(P->flag, int32_t, 4);
     cudaMemsetAsync(P->flag, 0, 4 * sizeof(int32_t), st);
-    rc = build_tables(P);
+    {
+      int ps = prof_start(st);
+      rc = build_tables(P);
+      prof_stop(ps, TW_STAGE_SETUP, st);
+    }
     if (rc) goto fail;
   }
 #undef ALLOC

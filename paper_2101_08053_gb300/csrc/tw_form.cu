@@ -289,7 +289,9 @@ static void launch_form(tw_patch *Pt, int64_t *rp, int32_t *col, double *val, cu
   Dir &B = Pt->d[1];
   if (Pt->method != TW_METHOD_GAUSS && Pt->n_interior > 0) {
     dim3 grid((A.n + T - 1) / T, B.n);
+    int ps = prof_start(s);
     k_interior<P, T><<<grid, 256, 0, s>>>(A, B, Pt->C, Pt->fstate, Pt->act, Pt->row_ptr, col, val);
+    prof_stop(ps, TW_STAGE_INTERIOR, s);
     TW_LAUNCH();
   }
   if (Pt->ncutrows > 0) {
@@ -318,7 +320,9 @@ static void launch_form(tw_patch *Pt, int64_t *rp, int32_t *col, double *val, cu
     }
     ra.method = Pt->method;
     ra.flag = Pt->flag;
+    int ps = prof_start(s);
     k_cutrows<P><<<Pt->ncutrows, 256, 0, s>>>(ra, Pt->cutrows, col, val);
+    prof_stop(ps, TW_STAGE_CUTROWS, s);
     TW_LAUNCH();
   }
 }

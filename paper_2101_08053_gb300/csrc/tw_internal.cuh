@@ -592,6 +592,8 @@ struct tw_patch {
 // host helpers shared by the translation units
 namespace tw {
 extern int64_t g_launches;
+int prof_start(cudaStream_t s);                  // -1 when profiling is off
+void prof_stop(int slot, int stage, cudaStream_t s);
 void set_error(const char *fmt, ...);
 int check_cuda(cudaError_t e, const char *what);
 void *dalloc(tw_patch *P, size_t bytes);

@@ -122,7 +122,7 @@ __global__ void k_gauss_nodes(int q, double *x, double *w) {
     dp = q * (z * b - a) / (z * z - 1.0);
     double dz = b / dp;
     z -= dz;
-    if (fabs(dz) <= 1e-17) break;
+    if (fabs(dz) <= 1e-15) break;  // quadratic convergence: z is now exact to rounding
   }
   {
     double a = 1.0, b = z;
@@ -274,35 +274,78 @@ __device__ void curve_point0(const Curve &C, double *xy) {
   }
 }
 
+// Crossings of the curve with whole lines, sorted: lines [0, nel1] are the
+// vertical knot lines x = bp1[l], [nel1+1, nel1+nel2+1] the horizontal knot
+// lines, and the last nel2 the horizontal lines through the element centres of
+// each row (visibility by the parity of crossings to the right, reading R8).
+__global__ void k_line_hits(Curve C, Dir A, Dir B, double *hits, int *nh, int *flag) {
+  int l = blockIdx.x * blockDim.x + threadIdx.x;
+  int nl = (A.nel + 1) + (B.nel + 1) + B.nel;
+  if (l >= nl) return;
+  int o;
+  double s;
+  if (l <= A.nel) {
+    o = 0;
+    s = A.bp[l];
+  } else if (l <= A.nel + B.nel + 1) {
+    o = 1;
+    s = B.bp[l - A.nel - 1];
+  } else {
+    int e2 = l - A.nel - B.nel - 2;
+    o = 1;
+    s = 0.5 * (B.bp[e2] + B.bp[e2 + 1]);
+  }
+  int n = curve_line_hits(C, o, s, -1e300, 1e300, hits + (size_t)l * TW_HITCAP, TW_HITCAP);
+  if (n < 0) {
+    atomicOr(flag, TWF_HITCAP);
+    n = 0;
+  }
+  nh[l] = n;
+}
+
+__device__ __forceinline__ int any_hit_in(const double *h, int n, double lo, double hi) {
+  for (int k = 0; k < n; k++)
+    if (h[k] > lo && h[k] < hi) return 1;
+  return 0;
+}
+
 // R8: an element is cut iff the curve meets its open box: a crossing inside
-// one of its four open edges, or the whole curve inside it
-__global__ void k_classify_elems(Curve C, Dir A, Dir B, uint8_t *estate, int *flag) {
+// one of its four open edges (corner touches excluded), or the whole curve
+// inside it; otherwise visible iff its centre is
+__global__ void k_classify_elems(Curve C, Dir A, Dir B, const double *hits, const int *nh,
+                                 uint8_t *estate) {
   int id = blockIdx.x * blockDim.x + threadIdx.x;
   if (id >= A.nel * B.nel) return;
   int e1 = id % A.nel, e2 = id / A.nel;
-  double a1 = A.bp[e1], b1 = A.bp[e1 + 1], a2 = B.bp[e2], b2 = B.bp[e2 + 1];
   if (C.kind == TW_TRIM_NONE) {
     estate[id] = TW_ELEM_REGULAR;
     return;
   }
-  double h[TW_HITCAP];
-  // crossings within TW_CORNER of an edge's end are corner touches, not cuts
+  double a1 = A.bp[e1], b1 = A.bp[e1 + 1], a2 = B.bp[e2], b2 = B.bp[e2 + 1];
   double d1 = TW_CORNER * (b1 - a1), d2 = TW_CORNER * (b2 - a2);
-  int cut = 0;
-  int n;
-  n = curve_line_hits(C, 0, a1, a2 + d2, b2 - d2, h, TW_HITCAP);
-  cut |= n != 0;
-  if (!cut) { n = curve_line_hits(C, 0, b1, a2 + d2, b2 - d2, h, TW_HITCAP); cut |= n != 0; }
-  if (!cut) { n = curve_line_hits(C, 1, a2, a1 + d1, b1 - d1, h, TW_HITCAP); cut |= n != 0; }
-  if (!cut) { n = curve_line_hits(C, 1, b2, a1 + d1, b1 - d1, h, TW_HITCAP); cut |= n != 0; }
+  const int hv = A.nel + 1;  // first horizontal knot line
+  const int hc = A.nel + B.nel + 2;  // first centre line
+  int cut = any_hit_in(hits + (size_t)e1 * TW_HITCAP, nh[e1], a2 + d2, b2 - d2) ||
+            any_hit_in(hits + (size_t)(e1 + 1) * TW_HITCAP, nh[e1 + 1], a2 + d2, b2 - d2) ||
+            any_hit_in(hits + (size_t)(hv + e2) * TW_HITCAP, nh[hv + e2], a1 + d1, b1 - d1) ||
+            any_hit_in(hits + (size_t)(hv + e2 + 1) * TW_HITCAP, nh[hv + e2 + 1], a1 + d1, b1 - d1);
   if (!cut) {
     double p0[2];
     curve_point0(C, p0);
     cut = p0[0] > a1 && p0[0] < b1 && p0[1] > a2 && p0[1] < b2;
   }
   uint8_t st;
-  if (cut) st = TW_ELEM_CUT;
-  else st = visible(C, 0.5 * (a1 + b1), 0.5 * (a2 + b2)) ? TW_ELEM_REGULAR : TW_ELEM_INVISIBLE;
+  if (cut) {
+    st = TW_ELEM_CUT;
+  } else {
+    double xc = 0.5 * (a1 + b1);
+    const double *h = hits + (size_t)(hc + e2) * TW_HITCAP;
+    int right = 0;
+    for (int k = 0; k < nh[hc + e2]; k++) right += h[k] > xc;
+    int inside = right & 1;
+    int vis = C.keep_inside ? inside : !inside;
+    st = vis ? TW_ELEM_REGULAR : TW_ELEM_INVISIBLE;
+  }
   estate[id] = st;
 }
 
@@ -428,112 +471,177 @@ __device__ void sort_small(double *v, int n) {
   }
 }
 
-__global__ void k_cut_rule(Curve C, Dir A, Dir B, const int32_t *cut_list, int ncut,
-                           const double *qgx, const double *qgw, int q, int64_t *cnt,
-                           const int64_t *off, double *pts, int *flag) {
-  int ci = blockIdx.x * blockDim.x + threadIdx.x;
+// One block of 64 threads per cut element.  Pass 0 (pts == NULL) counts the
+// element's points into cnt[ci], pass 1 writes them from off[ci] on, in the
+// order piece, Gauss line, interval, inner Gauss point.
+#define TW_CUT_THREADS 64
+__global__ void __launch_bounds__(TW_CUT_THREADS)
+    k_cut_rule(Curve C, Dir A, Dir B, const int32_t *cut_list, int ncut, const double *qgx,
+               const double *qgw, int q, int64_t *cnt, const int64_t *off, double *pts, int *flag) {
+  const int ci = blockIdx.x;
   if (ci >= ncut) return;
-  int e = cut_list[ci];
-  int e1 = e % A.nel, e2 = e / A.nel;
-  double a[2] = {A.bp[e1], B.bp[e2]}, b[2] = {A.bp[e1 + 1], B.bp[e2 + 1]};
-  double h[TW_HITCAP];
-  double fp[2 * TW_HITCAP];
-  // 1. outer direction from the extent of the curve inside the box (crossings
-  //    and tangent points up to TW_CORNER beyond its edges)
-  double lo[2] = {1e300, 1e300}, hi[2] = {-1e300, -1e300};
-  double dl[2] = {TW_CORNER * (b[0] - a[0]), TW_CORNER * (b[1] - a[1])};
-  for (int o = 0; o < 2; o++)
-    for (int sd = 0; sd < 2; sd++) {
-      double s = sd ? b[o] : a[o];
+  const int tid = threadIdx.x;
+  const int e = cut_list[ci];
+  const int e1 = e % A.nel, e2 = e / A.nel;
+  const double a[2] = {A.bp[e1], B.bp[e2]}, b[2] = {A.bp[e1 + 1], B.bp[e2 + 1]};
+  const double dl[2] = {TW_CORNER * (b[0] - a[0]), TW_CORNER * (b[1] - a[1])};
+  __shared__ double plo[8][2], phi[8][2];
+  __shared__ double part[4][TW_HITCAP];
+  __shared__ int npart[4];
+  __shared__ double br[TW_BRCAP];
+  __shared__ int nbr, s_o, s_bad;
+  __shared__ int64_t scan[TW_CUT_THREADS];
+  if (tid == 0) s_bad = 0;
+  // 1. extent of the curve in the box: four edges and two kinds of tangent points
+  if (tid < 8) {
+    double lo0 = 1e300, lo1 = 1e300, hi0 = -1e300, hi1 = -1e300;
+    double h[2 * TW_HITCAP];
+    if (tid < 4) {
+      int o = tid >> 1;
+      double s = (tid & 1) ? b[o] : a[o];
       int n = curve_line_hits(C, o, s, a[1 - o] - dl[1 - o], b[1 - o] + dl[1 - o], h, TW_HITCAP);
-      if (n < 0) { atomicOr(flag, TWF_HITCAP); return; }
+      if (n < 0) { s_bad = 1; n = 0; }
       for (int k = 0; k < n; k++) {
         double X = o == 0 ? s : h[k], Y = o == 0 ? h[k] : s;
-        lo[0] = fmin(lo[0], X); hi[0] = fmax(hi[0], X);
-        lo[1] = fmin(lo[1], Y); hi[1] = fmax(hi[1], Y);
+        lo0 = fmin(lo0, X); hi0 = fmax(hi0, X); lo1 = fmin(lo1, Y); hi1 = fmax(hi1, Y);
+      }
+    } else if (tid < 6) {
+      int n = curve_folds(C, tid - 4, h, TW_HITCAP);
+      if (n < 0) { s_bad = 1; n = 0; }
+      for (int k = 0; k < n; k++) {
+        double X = h[2 * k], Y = h[2 * k + 1];
+        if (X >= a[0] - dl[0] && X <= b[0] + dl[0] && Y >= a[1] - dl[1] && Y <= b[1] + dl[1]) {
+          lo0 = fmin(lo0, X); hi0 = fmax(hi0, X); lo1 = fmin(lo1, Y); hi1 = fmax(hi1, Y);
+        }
       }
     }
-  for (int o = 0; o < 2; o++) {
-    int n = curve_folds(C, o, fp, TW_HITCAP);
-    if (n < 0) { atomicOr(flag, TWF_HITCAP); return; }
-    for (int k = 0; k < n; k++) {
-      double X = fp[2 * k], Y = fp[2 * k + 1];
-      if (X >= a[0] - dl[0] && X <= b[0] + dl[0] && Y >= a[1] - dl[1] && Y <= b[1] + dl[1]) {
-        lo[0] = fmin(lo[0], X); hi[0] = fmax(hi[0], X);
-        lo[1] = fmin(lo[1], Y); hi[1] = fmax(hi[1], Y);
-      }
-    }
+    plo[tid][0] = lo0; plo[tid][1] = lo1; phi[tid][0] = hi0; phi[tid][1] = hi1;
   }
-  // equal extents within TW_TIE of the element size: o = 0
-  int o = (hi[0] - lo[0] >= hi[1] - lo[1] - TW_TIE * fmax(b[0] - a[0], b[1] - a[1])) ? 0 : 1;
-  int in = 1 - o;
-  // 2. breakpoints along o
-  double br[TW_BRCAP];
-  int nbr = 0;
-  br[nbr++] = a[o];
-  br[nbr++] = b[o];
-  for (int sd = 0; sd < 2; sd++) {
-    double s = sd ? b[in] : a[in];
-    int n = curve_line_hits(C, in, s, a[o], b[o], h, TW_HITCAP);
-    if (n < 0 || nbr + n > TW_BRCAP) { atomicOr(flag, TWF_BRCAP); return; }
-    for (int k = 0; k < n; k++) br[nbr++] = h[k];
-  }
-  {
-    int n = curve_folds(C, o, fp, TW_HITCAP);
-    for (int k = 0; k < n; k++) {
-      double xo = fp[2 * k + o], xi = fp[2 * k + in];
-      if (xo > a[o] && xo < b[o] && xi >= a[in] && xi <= b[in]) {
-        if (nbr >= TW_BRCAP) { atomicOr(flag, TWF_BRCAP); return; }
-        br[nbr++] = xo;
-      }
+  __syncthreads();
+  if (tid == 0) {
+    double lo0 = 1e300, lo1 = 1e300, hi0 = -1e300, hi1 = -1e300;
+    for (int k = 0; k < 8; k++) {
+      lo0 = fmin(lo0, plo[k][0]); lo1 = fmin(lo1, plo[k][1]);
+      hi0 = fmax(hi0, phi[k][0]); hi1 = fmax(hi1, phi[k][1]);
     }
-    if (C.kind == TW_TRIM_BSPLINE3) {
+    // equal extents within TW_TIE of the element size: o = 0
+    s_o = (hi0 - lo0 >= hi1 - lo1 - TW_TIE * fmax(b[0] - a[0], b[1] - a[1])) ? 0 : 1;
+  }
+  __syncthreads();
+  const int o = s_o, in = 1 - o;
+  // 2. breakpoints along o: crossings of the two edges parallel to o, tangent
+  //    points that fold the lines xi_o = const, the spline's segment joints
+  if (tid < 4) {
+    int n = 0;
+    double h[2 * TW_HITCAP];
+    if (tid < 2) {
+      double s = tid ? b[in] : a[in];
+      n = curve_line_hits(C, in, s, a[o], b[o], part[tid], TW_HITCAP);
+      if (n < 0) { s_bad = 1; n = 0; }
+    } else if (tid == 2) {
+      int m = curve_folds(C, o, h, TW_HITCAP);
+      for (int k = 0; k < m; k++) {
+        double xo = h[2 * k + o], xi = h[2 * k + in];
+        if (xo > a[o] && xo < b[o] && xi >= a[in] && xi <= b[in] && n < TW_HITCAP) part[2][n++] = xo;
+      }
+    } else if (C.kind == TW_TRIM_BSPLINE3) {
       for (int sg = 0; sg < C.nc; sg++) {
         double X = C.seg[8 * sg], Y = C.seg[8 * sg + 4];
         double xo = o == 0 ? X : Y, xi = o == 0 ? Y : X;
         if (xo > a[o] && xo < b[o] && xi >= a[in] && xi <= b[in]) {
-          if (nbr >= TW_BRCAP) { atomicOr(flag, TWF_BRCAP); return; }
-          br[nbr++] = xo;
+          if (n >= TW_HITCAP) { s_bad = 1; break; }
+          part[3][n++] = xo;
         }
       }
     }
+    npart[tid] = n;
   }
-  sort_small(br, nbr);
-  // 3. Gauss lines, crossings, visible intervals
-  int64_t count = 0;
-  int64_t base = off ? off[ci] : 0;
-  double ends[TW_HITCAP + 2];
-  for (int pc = 0; pc + 1 < nbr; pc++) {
-    double s0 = br[pc], s1 = br[pc + 1];
-    if (!(s1 > s0)) continue;
-    for (int g = 0; g < q; g++) {
-      double s = s0 + (s1 - s0) * 0.5 * (qgx[g] + 1.0);
-      double ws = qgw[g] * 0.5 * (s1 - s0);
-      int n = curve_line_hits(C, o, s, a[in], b[in], h, TW_HITCAP);
-      if (n < 0) { atomicOr(flag, TWF_HITCAP); return; }
-      ends[0] = a[in];
-      for (int k = 0; k < n; k++) ends[k + 1] = h[k];
-      ends[n + 1] = b[in];
-      for (int k = 0; k <= n; k++) {
-        double u0 = ends[k], u1 = ends[k + 1];
-        if (!(u1 > u0)) continue;
-        double mid = 0.5 * (u0 + u1);
-        if (!visible(C, o == 0 ? s : mid, o == 0 ? mid : s)) continue;
-        if (pts) {
-          for (int hh = 0; hh < q; hh++) {
-            double u = u0 + (u1 - u0) * 0.5 * (qgx[hh] + 1.0);
-            double w = ws * qgw[hh] * 0.5 * (u1 - u0);
-            double *o3 = pts + 3 * (base + count + hh);
-            o3[0] = o == 0 ? s : u;
-            o3[1] = o == 0 ? u : s;
-            o3[2] = w;
+  __syncthreads();
+  if (tid == 0) {
+    int n = 0;
+    br[n++] = a[o];
+    br[n++] = b[o];
+    for (int k = 0; k < 4; k++)
+      for (int j = 0; j < npart[k]; j++) {
+        if (n >= TW_BRCAP) { s_bad = 1; break; }
+        br[n++] = part[k][j];
+      }
+    sort_small(br, n);
+    nbr = n;
+  }
+  __syncthreads();
+  if (s_bad) {
+    if (tid == 0) {
+      atomicOr(flag, TWF_BRCAP);
+      if (cnt) cnt[ci] = 0;
+    }
+    return;
+  }
+  // 3. Gauss lines of every piece; crossings split the inner range and the
+  //    visibility of the pieces alternates at each crossing
+  const int nlines = (nbr - 1) * q;
+  const int64_t base0 = off ? off[ci] : 0;
+  int64_t base = 0;
+  for (int start = 0; start < nlines; start += TW_CUT_THREADS) {
+    int li = start + tid;
+    double h[TW_HITCAP + 2];
+    int n = -1, vis0 = 0;
+    double s = 0.0, ws = 0.0;
+    int64_t count = 0;
+    if (li < nlines) {
+      int pc = li / q, g = li % q;
+      double s0 = br[pc], s1 = br[pc + 1];
+      if (s1 > s0) {
+        s = s0 + (s1 - s0) * 0.5 * (qgx[g] + 1.0);
+        ws = qgw[g] * 0.5 * (s1 - s0);
+        n = curve_line_hits(C, o, s, a[in], b[in], h + 1, TW_HITCAP);
+        if (n < 0) {
+          atomicOr(flag, TWF_HITCAP);
+          n = -1;
+        } else {
+          h[0] = a[in];
+          h[n + 1] = b[in];
+          // visibility of the first interval by the midpoint test
+          int k0 = 0;
+          while (k0 <= n && !(h[k0 + 1] > h[k0])) k0++;
+          if (k0 <= n) {
+            double mid = 0.5 * (h[k0] + h[k0 + 1]);
+            vis0 = visible(C, o == 0 ? s : mid, o == 0 ? mid : s) ^ (k0 & 1);
           }
+          for (int k = 0; k <= n; k++)
+            if (h[k + 1] > h[k] && (vis0 ^ (k & 1))) count += q;
         }
-        count += q;
       }
     }
+    scan[tid] = count;
+    __syncthreads();
+    for (int d = 1; d < TW_CUT_THREADS; d <<= 1) {
+      int64_t v = tid >= d ? scan[tid - d] : 0;
+      __syncthreads();
+      scan[tid] += v;
+      __syncthreads();
+    }
+    int64_t mine = base + scan[tid] - count;
+    if (pts && count > 0) {
+      int64_t w0 = base0 + mine;
+      for (int k = 0; k <= n; k++) {
+        double u0 = h[k], u1 = h[k + 1];
+        if (!(u1 > u0) || !(vis0 ^ (k & 1))) continue;
+        for (int hh = 0; hh < q; hh++) {
+          double u = u0 + (u1 - u0) * 0.5 * (qgx[hh] + 1.0);
+          double w = ws * qgw[hh] * 0.5 * (u1 - u0);
+          double *o3 = pts + 3 * w0;
+          o3[0] = o == 0 ? s : u;
+          o3[1] = o == 0 ? u : s;
+          o3[2] = w;
+          w0++;
+        }
+      }
+    }
+    base += scan[TW_CUT_THREADS - 1];
+    __syncthreads();
   }
-  if (cnt) cnt[ci] = count;
+  if (cnt && tid == 0) cnt[ci] = base;
 }
 
 // per cut point: basis values in both directions and w * c
@@ -679,18 +787,27 @@ __device__ double ref_fn(const Dir &D, int s, int m, double x) {
 }
 
 // One block per disc knot t = bp[s] of one direction: steps 1-4 of Sect. 3.3.
-__global__ void k_dwq_build(Dir D, const int32_t *disc_list, int ndisc, double *out_x,
-                            int32_t *out_np, double *out_w, int *flag) {
+// The refined basis is tabulated once per window point and per window Gauss
+// point (shared memory); each refined system is then assembled by lookup and
+// solved by its own thread.
+#define TW_DWQ_THREADS 128
+__global__ void __launch_bounds__(TW_DWQ_THREADS)
+    k_dwq_build(Dir D, const int32_t *disc_list, int ndisc, double *out_x, int32_t *out_np,
+                double *out_w, int *flag) {
   int slot = blockIdx.x;
   if (slot >= ndisc) return;
   int s = disc_list[slot];
   int p = D.p, p1 = p + 1;
   double t = D.bp[s];
   __shared__ double xs[TW_LQMAX];
+  __shared__ double RB[TW_LQMAX][TW_MAXP1];      // refined functions on each point's span
+  __shared__ int rsp[TW_LQMAX];                  // first refined function of that span
+  __shared__ double RG[2 * TW_MAXP][TW_MAXP1][TW_MAXP1];  // [window element][g][a]
   __shared__ int npts;
   __shared__ double Sc[TW_MAXP][TW_MAXP1];             // S[i + r][i], i = s + col
   __shared__ double Wt[2 * TW_MAXP][TW_LQMAX];         // refined weights of l = s + row
   int ewlo = max(0, s - p), ewhi = min(D.nel - 1, s + p - 1);
+  int nwe = ewhi - ewlo + 1;
   if (threadIdx.x == 0) {
     // refined points: base points + nested points next to t (R5)
     int n = 0;
@@ -760,7 +877,23 @@ __global__ void k_dwq_build(Dir D, const int32_t *disc_list, int ndisc, double *
     for (int r = 0; r <= p; r++) Sc[threadIdx.x][r] = c[r];
   }
   __syncthreads();
-  int np_ = npts;
+  const int np_ = npts;
+  // refined basis at the window points and at the window elements' Gauss points
+  for (int id = threadIdx.x; id < np_ + nwe * p1; id += blockDim.x) {
+    double N[TW_MAXP1];
+    if (id < np_) {
+      int e = elem_of(D.bp, D.nel, xs[id]);
+      ref_basis(D, s, e, xs[id], N);
+      rsp[id] = e + (e >= s ? p : 0);
+      for (int a2 = 0; a2 <= p; a2++) RB[id][a2] = N[a2];
+    } else {
+      int j = id - np_, el = j / p1, g = j % p1, e = ewlo + el;
+      double x = D.bp[e] + (D.bp[e + 1] - D.bp[e]) * 0.5 * (D.gx[g] + 1.0);
+      ref_basis(D, s, e, x, N);
+      for (int a2 = 0; a2 <= p; a2++) RG[el][g][a2] = N[a2];
+    }
+  }
+  __syncthreads();
   // step 3: WQ weights of the refined functions l = s .. s+2p-1 (Eq. 5)
   if (threadIdx.x < 2 * p && np_ > 0) {
     int l = s + threadIdx.x;
@@ -779,20 +912,20 @@ __global__ void k_dwq_build(Dir D, const int32_t *disc_list, int ndisc, double *
       }
     double A[TW_WIN * TW_QMAX], bb[TW_WIN], w[TW_QMAX], beta[TW_WIN];
     for (int r = 0; r < m; r++) {
-      for (int c = 0; c < N; c++) A[r * TW_QMAX + c] = ref_fn(D, s, rows[r], xs[cols[c]]);
+      int mr = rows[r];
+      for (int c = 0; c < N; c++) {
+        int k = cols[c], aa = mr - rsp[k];
+        A[r * TW_QMAX + c] = (aa >= 0 && aa <= p) ? RB[k][aa] : 0.0;
+      }
       double acc = 0.0;
-      for (int e = ewlo; e <= ewhi; e++) {
-        double a = D.bp[e], b = D.bp[e + 1];
-        if (b <= ul || a >= uh) continue;
-        for (int g = 0; g < p1; g++) {
-          double x = a + (b - a) * 0.5 * (D.gx[g] + 1.0);
-          double N1[TW_MAXP1];
-          ref_basis(D, s, e, x, N1);
-          int span = e + p + (e >= s ? p : 0);
-          int al = l - (span - p), am = rows[r] - (span - p);
-          if (al < 0 || al > p || am < 0 || am > p) continue;
-          acc += D.gw[g] * 0.5 * (b - a) * N1[al] * N1[am];
-        }
+      for (int el = 0; el < nwe; el++) {
+        int e = ewlo + el;
+        double ea = D.bp[e], eb = D.bp[e + 1];
+        if (eb <= ul || ea >= uh) continue;
+        int f0 = e + (e >= s ? p : 0);
+        int al = l - f0, am = mr - f0;
+        if (al < 0 || al > p || am < 0 || am > p) continue;
+        for (int g = 0; g < p1; g++) acc += D.gw[g] * 0.5 * (eb - ea) * RG[el][g][al] * RG[el][g][am];
       }
       bb[r] = acc;
     }
@@ -900,8 +1033,18 @@ int build_tables(tw_patch *P) {
   int32_t *cflag = (int32_t *)dalloc(P, sizeof(int32_t) * nf);
   int32_t *cpos = (int32_t *)dalloc(P, sizeof(int32_t) * nf);
   if (!aflag || !cflag || !cpos) return TW_ENOMEM;
-  k_classify_elems<<<G1(ne)>>>(P->curve, A, B, P->estate, P->flag);
-  TW_LAUNCH();
+  {
+    int nl = (A.nel + 1) + (B.nel + 1) + B.nel;
+    double *lh = (double *)dalloc(P, sizeof(double) * (size_t)nl * TW_HITCAP);
+    int *lnh = (int *)dalloc(P, sizeof(int) * nl);
+    if (!lh || !lnh) return TW_ENOMEM;
+    if (P->curve.kind != TW_TRIM_NONE) {
+      k_line_hits<<<G1(nl)>>>(P->curve, A, B, lh, lnh, P->flag);
+      TW_LAUNCH();
+    }
+    k_classify_elems<<<G1(ne)>>>(P->curve, A, B, lh, lnh, P->estate);
+    TW_LAUNCH();
+  }
   k_classify_funcs<<<G1(nf)>>>(A, B, P->estate, P->fstate, aflag, P->method, cflag, counters);
   TW_LAUNCH();
   if ((rc = exclusive_scan_i32(aflag, P->act, nf, tot32 + 0, st, P))) return rc;
@@ -995,8 +1138,8 @@ int build_tables(tw_patch *P) {
   }
   // cut-element rules: count, scan, fill
   if (P->ncut > 0) {
-    k_cut_rule<<<G1(P->ncut)>>>(P->curve, A, B, P->cut_list, P->ncut, qgx, qgw, P->qc, ccount,
-                                nullptr, nullptr, P->flag);
+    k_cut_rule<<<P->ncut, TW_CUT_THREADS, 0, st>>>(P->curve, A, B, P->cut_list, P->ncut, qgx,
+                                                   qgw, P->qc, ccount, nullptr, nullptr, P->flag);
     TW_LAUNCH();
     if ((rc = exclusive_scan_i64(ccount, P->cut_off, P->ncut, tot64 + 1, st, P))) return rc;
     k_set_last<<<1, 1, 0, st>>>(P->cut_off, P->ncut, tot64 + 1);
@@ -1012,8 +1155,9 @@ int build_tables(tw_patch *P) {
   P->cut_B = (double *)dalloc(P, sizeof(double) * (2 * P->ncutpts * p1 + 1));
   if (!P->cut_pts || !P->cut_wc || !P->cut_B) return TW_ENOMEM;
   if (P->ncut > 0) {
-    k_cut_rule<<<G1(P->ncut)>>>(P->curve, A, B, P->cut_list, P->ncut, qgx, qgw, P->qc, nullptr,
-                                P->cut_off, P->cut_pts, P->flag);
+    k_cut_rule<<<P->ncut, TW_CUT_THREADS, 0, st>>>(P->curve, A, B, P->cut_list, P->ncut, qgx,
+                                                   qgw, P->qc, nullptr, P->cut_off, P->cut_pts,
+                                                   P->flag);
     TW_LAUNCH();
     k_cut_point_tables<<<P->ncut, 128, 0, st>>>(P->geo, A, B, P->cut_list, P->cut_off, P->ncut,
                                                 P->cut_pts, P->cut_B, P->cut_wc);
@@ -1031,7 +1175,7 @@ int build_tables(tw_patch *P) {
     k_compact<<<G1(D.nel + 1)>>>(dflag[d], dpos[d], dlist, P->disc_slot[d], D.nel + 1);
     TW_LAUNCH();
     if (nd > 0) {
-      k_dwq_build<<<nd, 64, 0, st>>>(D, dlist, nd, P->dwq_x[d], P->dwq_np[d], P->dwq_w[d],
+      k_dwq_build<<<nd, TW_DWQ_THREADS, 0, st>>>(D, dlist, nd, P->dwq_x[d], P->dwq_np[d], P->dwq_w[d],
                                      P->flag);
       TW_LAUNCH();
     }

@@ -396,7 +396,9 @@ int rhs_launch(tw_patch *P, const tw_func *f, double *b, cudaStream_t s) {
   cudaStream_t keep = P->stream;
   P->stream = s;
   int mark = P->nallocs;
+  int ps = prof_start(s);
   int rc = rhs_impl(P, f, b, s);
+  prof_stop(ps, TW_STAGE_RHS, s);
   release_to(P, mark);
   P->stream = keep;
   return rc;
@@ -471,7 +473,9 @@ int l2_project_run(tw_patch *P, const tw_func *f, const int64_t *rp, const int32
   cudaStream_t keep = P->stream;
   P->stream = s;
   int mark = P->nallocs;
+  int ps = prof_start(s);
   int rc = cg_impl(P, f, rp, col, val, u, tol, maxit, iters, relres, s);
+  prof_stop(ps, TW_STAGE_CG, s);
   release_to(P, mark);
   P->stream = keep;
   return rc;
