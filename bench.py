@@ -45,6 +45,14 @@ def specs():
     return [synth.config2(p=p, nel=nel, method=m) for (p, nel, m) in WORKLOAD]
 
 
+def select_case(case):
+    """--case p,nel,method restricts the workload to one patch of the sweep
+    (used as the profiling driver)."""
+    global WORKLOAD
+    p, nel, m = case.split(",")
+    WORKLOAD = [(int(p), int(nel), m)]
+
+
 def workload_name():
     return ("config-2 sweep: p in {3,4,5} x {128^2, 512^2} elements x {hybrid Gauss, DWQ}; "
             "perturbed bilinear geometry (c = det J), seeded 12-point cubic B-spline hole "
@@ -331,11 +339,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--case", default=None, help="p,nel,method: one patch of the sweep only")
     args = ap.parse_args()
+    if args.case:
+        select_case(args.case)
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
-    config = {"workload": workload_name(), "patches": len(WORKLOAD), "p": [3, 4, 5],
+    config = {"workload": workload_name() if not args.case else "single patch " + args.case,
+              "patches": len(WORKLOAD), "p": [3, 4, 5],
               "elements": ["128x128", "512x512"], "methods": ["hybrid", "dwq"],
               "l2": "flushed between timed steps (256 MB write); outputs > L2"}
 
