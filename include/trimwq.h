@@ -146,6 +146,29 @@ int tw_form_mass(tw_patch *patch, int precision, int64_t *row_ptr, int32_t *col,
  * rule applied to f * c (Sect. 4.2).  Device output, asynchronous. */
 int tw_rhs(tw_patch *patch, const tw_func *f, double *b, void *stream);
 
+/* Allocation-free right-hand side.  The paper has no counterpart: this exists
+ * for callers that cannot allocate device memory while they run -- a process
+ * whose device memory belongs to another allocator (a framework's caching
+ * allocator that has reserved almost all of it, so a foreign cudaMalloc fails),
+ * or a time-critical loop that must not pay the latency and implicit device
+ * synchronisation of cudaMalloc / cudaFree.  It returns the same b as tw_rhs
+ * but calls no cudaMalloc, cudaFree or allocating library routine: its scratch
+ * (f*c on the WQ grid, nq1*nq2 doubles, plus the knots and coefficients of a
+ * TW_FUNC_SPLINE f) lives in one file-scope device array of TW_RHS_STATIC_MAX
+ * doubles (16 MiB) that every GPU which loads the library holds until the
+ * process exits.  Larger patches or functions are rejected with TW_EINVAL.
+ *  - Call it with the patch's device current.  The first call on a device looks
+ *    up the array's device address (cudaGetSymbolAddress) for that device; make
+ *    that first call before any stream capture.
+ *  - Every call on a device shares the one array and leaves its contents
+ *    behind; nothing in it has to start at zero, since each call writes all of
+ *    the scratch it reads.  Calls that overlap on the GPU (other streams, other
+ *    threads) race on the array: order them on one stream.
+ *  - A spline f's host arrays are copied into the array with cudaMemcpyAsync on
+ *    `stream` during the call. */
+#define TW_RHS_STATIC_MAX (1 << 21)
+int tw_rhs_static(tw_patch *patch, const tw_func *f, double *b, void *stream);
+
 /* L2 projection: Jacobi-preconditioned CG on (M + M^T)/2 with the CSR produced
  * by tw_form_mass (FP64) and the rhs of f, until ||r||/||b|| <= tol or maxit
  * iterations.  u[n_rows] device output; *iters, *relres host outputs.

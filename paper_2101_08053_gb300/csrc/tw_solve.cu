@@ -7,6 +7,7 @@
 //         fixed order so the iteration is bitwise reproducible.
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "tw_internal.cuh"
 
@@ -482,3 +483,118 @@ int l2_project_run(tw_patch *P, const tw_func *f, const int64_t *rp, const int32
 }
 
 }  // namespace tw
+
+// ---------------------------------------------------------------------------
+// tw_rhs_static: the right-hand side without any device allocation, for
+// callers that cannot allocate device memory (see include/trimwq.h).  Its
+// scratch is this file-scope array; host code never uses the array's name as an
+// address, it asks the runtime for the device address once per device.
+static __device__ __align__(256) double g_rhs_static_scratch[TW_RHS_STATIC_MAX];
+
+namespace tw {
+
+#define TW_STATIC_MAX_DEVICES 64
+static std::mutex g_static_mu;
+static double *g_static_addr[TW_STATIC_MAX_DEVICES];
+
+// device address of the scratch array on the current device (looked up on the
+// first call for that device)
+static int static_scratch(double **out) {
+  int dev = -1;
+  if (check_cuda(cudaGetDevice(&dev), "tw_rhs_static: cudaGetDevice")) return TW_ECUDA;
+  if (dev < 0 || dev >= TW_STATIC_MAX_DEVICES) {
+    set_error("tw_rhs_static: device %d beyond %d", dev, TW_STATIC_MAX_DEVICES);
+    return TW_EUNSUPPORTED;
+  }
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_addr[dev]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_rhs_static_scratch);
+    if (e != cudaSuccess || !p) {
+      set_error("tw_rhs_static: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+      return TW_ECUDA;
+    }
+    g_static_addr[dev] = (double *)p;
+  }
+  *out = g_static_addr[dev];
+  return 0;
+}
+
+}  // namespace tw
+
+extern "C" int tw_rhs_static(tw_patch *P, const tw_func *f, double *b, void *stream) {
+  using namespace tw;
+  if (!P || !f || !b) {
+    set_error("tw_rhs_static: NULL argument");
+    return TW_EINVAL;
+  }
+  if (f->kind < TW_FUNC_SPLINE || f->kind > TW_FUNC_GAUSS) {
+    set_error("tw_rhs_static: unknown function kind %d", f->kind);
+    return TW_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  Dir &A = P->d[0];
+  Dir &B = P->d[1];
+  const int64_t ng = (int64_t)A.nq * B.nq;
+  int64_t need = ng;
+  int64_t m[2] = {0, 0};
+  if (f->kind == TW_FUNC_SPLINE) {
+    for (int d = 0; d < 2; d++) {
+      if (!f->knots[d] || f->p[d] < 0 || f->p[d] > TW_MAXP || f->nknots[d] < 2 * f->p[d] + 2) {
+        set_error("tw_rhs_static: spline function: bad knots or degree");
+        return TW_EINVAL;
+      }
+      m[d] = f->nknots[d] - f->p[d] - 1;
+      need += f->nknots[d];
+    }
+    if (!f->coef) {
+      set_error("tw_rhs_static: spline function without coefficients");
+      return TW_EINVAL;
+    }
+    need += m[0] * m[1];
+  }
+  if (need > TW_RHS_STATIC_MAX) {
+    set_error("tw_rhs_static: needs %lld doubles of scratch, the static array holds %d",
+              (long long)need, TW_RHS_STATIC_MAX);
+    return TW_EINVAL;
+  }
+  double *scr = nullptr;
+  int rc = static_scratch(&scr);
+  if (rc) return rc;
+  Func F;
+  memset(&F, 0, sizeof(F));
+  F.kind = f->kind;
+  for (int k = 0; k < 4; k++) F.prm[k] = f->prm[k];
+  if (f->kind == TW_FUNC_SPLINE) {
+    double *dst = scr + ng;
+    for (int d = 0; d < 2; d++) {
+      F.q[d] = f->p[d];
+      F.nk[d] = f->nknots[d];
+      if (check_cuda(cudaMemcpyAsync(dst, f->knots[d], sizeof(double) * f->nknots[d],
+                                     cudaMemcpyHostToDevice, s),
+                     "tw_rhs_static: knots"))
+        return TW_ECUDA;
+      F.U[d] = dst;
+      dst += f->nknots[d];
+    }
+    F.m1 = (int)m[0];
+    if (check_cuda(cudaMemcpyAsync(dst, f->coef, sizeof(double) * m[0] * m[1],
+                                   cudaMemcpyHostToDevice, s),
+                   "tw_rhs_static: coefficients"))
+      return TW_ECUDA;
+    F.coef = dst;
+  }
+  k_fc_grid<<<(unsigned)((ng + 255) / 256), 256, 0, s>>>(F, P->geo, A, B, P->C, scr);
+  TW_LAUNCH();
+  if (P->method != TW_METHOD_GAUSS) {
+    int64_t nf = (int64_t)A.n * B.n;
+    k_rhs_interior<<<(unsigned)((nf + 255) / 256), 256, 0, s>>>(A, B, P->fstate, P->act, scr, b);
+    TW_LAUNCH();
+  }
+  if (P->ncutrows > 0) {
+    k_rhs_cut<<<(P->ncutrows + 63) / 64, 64, 0, s>>>(row_args(P), F, P->cutrows, P->ncutrows, scr,
+                                                     b);
+    TW_LAUNCH();
+  }
+  return check_cuda(cudaGetLastError(), "tw_rhs_static");
+}
