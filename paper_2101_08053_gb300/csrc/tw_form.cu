@@ -239,17 +239,12 @@ __global__ void __launch_bounds__(256) k_cutrows(RowArgs a, const int32_t *__res
         }
         __syncthreads();
       } else if (st == TW_ELEM_CUT) {
+        // the cut element's matrix, formed once per element
         const int cs = a.cut_slot[e];
-        const int64_t q0 = a.cut_off[cs], q1 = a.cut_off[cs + 1];
+        const double *Me = a.cut_M + ((size_t)cs * p1 * p1 + (i2 - e2) * p1 + (i1 - e1)) * p1 * p1;
         if (tid < p1 * p1) {
           int b1 = tid % p1, b2 = tid / p1;
-          double s = 0.0;
-          for (int64_t q = q0; q < q1; q++) {
-            const double *Bv = a.cut_B + 2 * q * p1;
-            double ti = a.cut_wc[q] * Bv[i1 - e1] * Bv[p1 + (i2 - e2)];
-            s = fma(ti, Bv[b1] * Bv[p1 + b2], s);
-          }
-          acc[(e2 + b2 - i2 + P) * W + (e1 + b1 - i1 + P)] += s;
+          acc[(e2 + b2 - i2 + P) * W + (e1 + b1 - i1 + P)] += Me[b2 * p1 + b1];
         }
         __syncthreads();
       }
@@ -311,6 +306,7 @@ static void launch_form(tw_patch *Pt, int64_t *rp, int32_t *col, double *val, cu
     ra.cut_B = Pt->cut_B;
     ra.cut_wc = Pt->cut_wc;
     ra.cut_pts = Pt->cut_pts;
+    ra.cut_M = Pt->cut_M;
     ra.choice = Pt->choice;
     for (int d = 0; d < 2; d++) {
       ra.disc_slot[d] = Pt->disc_slot[d];

@@ -529,6 +529,7 @@ struct RowArgs {
   const double *cut_B;
   const double *cut_wc;
   const double *cut_pts;
+  const double *cut_M;
   const int32_t *choice;
   const int32_t *disc_slot[2];
   const double *dwq_x[2];
@@ -537,6 +538,63 @@ struct RowArgs {
   int method;
   int *flag;
 };
+
+// ---------------------------------------------------------------------------
+// warp-cooperative min-norm solve of A w = b (m x N, m <= 2p+1, N <= 32): lane c
+// owns column c.  LQ with Householder reflectors from the right, reductions by
+// a fixed shuffle tree (deterministic).  A (leading dimension lda, shared
+// memory) is overwritten with L and the reflectors; w[c] is returned in lane c.
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+static __device__ double warp_minnorm(int m, int N, double *A, int lda, const double *b, double *diag,
+                               double *beta, int lane, int *singular) {
+  for (int k = 0; k < m; k++) {
+    double x = (lane >= k && lane < N) ? A[k * lda + lane] : 0.0;
+    double nrm2 = warp_sum(x * x);
+    double akk = A[k * lda + k];
+    double nrm = sqrt(nrm2);
+    if (nrm == 0.0) {
+      *singular = 1;
+      return 0.0;
+    }
+    double alpha = akk >= 0.0 ? -nrm : nrm;
+    double v0 = akk - alpha;
+    double vn2 = v0 * v0 + (nrm2 - akk * akk);
+    double bk = vn2 > 0.0 ? 2.0 / vn2 : 0.0;
+    double v = lane == k ? v0 : x;
+    for (int r = k + 1; r < m; r++) {
+      double a = (lane >= k && lane < N) ? A[r * lda + lane] : 0.0;
+      double s = warp_sum(a * v) * bk;
+      if (lane >= k && lane < N) A[r * lda + lane] = a - s * v;
+    }
+    __syncwarp();
+    if (lane >= k && lane < N) A[k * lda + lane] = v;
+    if (lane == 0) {
+      diag[k] = alpha;
+      beta[k] = bk;
+    }
+    __syncwarp();
+  }
+  // forward substitution L y = b, y kept in lane r
+  double y = 0.0;
+  for (int r = 0; r < m; r++) {
+    double t = (lane < r) ? A[r * lda + lane] * y : 0.0;
+    double s = warp_sum(t);
+    double yr = (b[r] - s) / diag[r];
+    if (lane == r) y = yr;
+  }
+  // w = H_0 ... H_{m-1} [y; 0]
+  double w = lane < m ? y : 0.0;
+  for (int k = m - 1; k >= 0; k--) {
+    double v = (lane >= k && lane < N) ? A[k * lda + lane] : 0.0;
+    double s = warp_sum(v * w) * beta[k];
+    w -= s * v;
+  }
+  return lane < N ? w : 0.0;
+}
 
 }  // namespace tw
 
@@ -567,6 +625,8 @@ struct tw_patch {
   double *cut_pts;   // npts x 3 (xi1, xi2, w)
   double *cut_wc;    // npts: w * c
   double *cut_B;     // npts x 2 x (p+1)
+  int32_t *cut_o;    // ncut: outer direction of each cut element's rule
+  double *cut_M;     // ncut x (p+1)^4: element matrices of the cut elements
   int32_t *cut_slot; // nel1*nel2 -> cut index or -1
   // rows formed by the cut-row kernel
   int ncutrows;

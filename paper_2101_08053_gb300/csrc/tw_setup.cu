@@ -190,23 +190,30 @@ __device__ __forceinline__ double Bjk(const Dir &D, int j, int k) {
   return (a >= 0 && a <= D.p) ? D.Bq[k * (D.p + 1) + a] : 0.0;
 }
 
-// Eq. 5 for test function i: min-norm weights, then V = W * B_j (R2, R3)
-__global__ void k_wq_weights(Dir D, int *flag) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+// Eq. 5 for test function i: min-norm weights, then V = W * B_j (R2, R3).
+// One warp per test function: lanes own the columns (points) of the system.
+#define TW_WQ_WARPS 4
+__global__ void __launch_bounds__(32 * TW_WQ_WARPS) k_wq_weights(Dir D, int *flag) {
+  __shared__ double sA[TW_WQ_WARPS][TW_WIN * (TW_QMAX + 1)];
+  __shared__ double sb[TW_WQ_WARPS][TW_WIN], sd[TW_WQ_WARPS][TW_WIN], sbeta[TW_WQ_WARPS][TW_WIN];
+  __shared__ int sing[TW_WQ_WARPS];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * TW_WQ_WARPS + wib;
   if (i >= D.n) return;
-  int p = D.p, p1 = p + 1, W2 = 2 * p + 1;
-  int jlo = max(0, i - p), jhi = min(D.n - 1, i + p);
-  int m = jhi - jlo + 1;
-  int q0 = D.qbeg[i], N = D.qcnt[i];
+  const int p = D.p, p1 = p + 1, W2 = 2 * p + 1, lda = TW_QMAX + 1;
+  const int jlo = max(0, i - p), jhi = min(D.n - 1, i + p);
+  const int m = jhi - jlo + 1;
+  const int q0 = D.qbeg[i], N = D.qcnt[i];
   if (N > TW_QMAX) {
-    atomicOr(flag, TWF_QMAX);
+    if (lane == 0) atomicOr(flag, TWF_QMAX);
     return;
   }
-  double A[TW_WIN * TW_QMAX], b[TW_WIN], w[TW_QMAX], beta[TW_WIN];
-  int elo = max(0, i - p), ehi = min(D.nel - 1, i);
-  for (int r = 0; r < m; r++) {
-    int j = jlo + r;
-    for (int c = 0; c < N; c++) A[r * TW_QMAX + c] = Bjk(D, j, q0 + c);
+  double *A = sA[wib];
+  const int elo = max(0, i - p), ehi = min(D.nel - 1, i);
+  if (lane < N)
+    for (int r = 0; r < m; r++) A[r * lda + lane] = Bjk(D, jlo + r, q0 + lane);
+  if (lane < m) {
+    int j = jlo + lane;
     double s = 0.0;
     int ea = max(elo, max(0, j - p)), eb = min(ehi, min(D.nel - 1, j));
     for (int e = ea; e <= eb; e++) {
@@ -214,21 +221,25 @@ __global__ void k_wq_weights(Dir D, int *flag) {
       for (int g = 0; g < p1; g++)
         s += D.gw[g] * h * D.GB[(e * p1 + g) * p1 + (i - e)] * D.GB[(e * p1 + g) * p1 + (j - e)];
     }
-    b[r] = s;
+    sb[wib][lane] = s;
   }
-  if (minnorm_lq(m, N, A, TW_QMAX, b, w, beta)) atomicOr(flag, TWF_SINGULAR);
-  for (int c = 0; c < D.qmax; c++) {
-    double wc = c < N ? w[c] : 0.0;
-    D.W[(size_t)i * D.qmax + c] = wc;
+  if (lane == 0) sing[wib] = 0;
+  __syncwarp();
+  double wc = warp_minnorm(m, N, A, lda, sb[wib], sd[wib], sbeta[wib], lane, &sing[wib]);
+  __syncwarp();
+  if (lane == 0 && sing[wib]) atomicOr(flag, TWF_SINGULAR);
+  for (int c = lane; c < D.qmax; c += 32) {
+    double w = (c < N) ? wc : 0.0;  // lane c holds column c (N <= 32)
+    D.W[(size_t)i * D.qmax + c] = w;
     for (int r = 0; r < W2; r++) {
       int j = i - p + r;
       double v = 0.0;
-      if (c < N && j >= 0 && j < D.n) v = wc * Bjk(D, j, q0 + c);
+      if (c < N && j >= 0 && j < D.n) v = w * Bjk(D, j, q0 + c);
       D.V[((size_t)i * D.qmax + c) * W2 + r] = v;
     }
   }
-  for (int r = 0; r < W2; r++) {
-    int j = i - p + r;
+  if (lane < W2) {
+    int r = lane, j = i - p + r;
     int lo = 0, hi = 0;
     if (j >= 0 && j < D.n) {
       int ea = max(elo, max(0, j - p)), eb = min(ehi, min(D.nel - 1, j));
@@ -477,7 +488,8 @@ __device__ void sort_small(double *v, int n) {
 #define TW_CUT_THREADS 64
 __global__ void __launch_bounds__(TW_CUT_THREADS)
     k_cut_rule(Curve C, Dir A, Dir B, const int32_t *cut_list, int ncut, const double *qgx,
-               const double *qgw, int q, int64_t *cnt, const int64_t *off, double *pts, int *flag) {
+               const double *qgw, int q, int64_t *cnt, const int64_t *off, double *pts,
+               int32_t *cut_o, int *flag) {
   const int ci = blockIdx.x;
   if (ci >= ncut) return;
   const int tid = threadIdx.x;
@@ -529,6 +541,7 @@ __global__ void __launch_bounds__(TW_CUT_THREADS)
   }
   __syncthreads();
   const int o = s_o, in = 1 - o;
+  if (cut_o && tid == 0) cut_o[ci] = o;
   // 2. breakpoints along o: crossings of the two edges parallel to o, tangent
   //    points that fold the lines xi_o = const, the spline's segment joints
   if (tid < 4) {
@@ -894,9 +907,16 @@ __global__ void __launch_bounds__(TW_DWQ_THREADS)
     }
   }
   __syncthreads();
-  // step 3: WQ weights of the refined functions l = s .. s+2p-1 (Eq. 5)
-  if (threadIdx.x < 2 * p && np_ > 0) {
-    int l = s + threadIdx.x;
+  // step 3: WQ weights of the refined functions l = s .. s+2p-1 (Eq. 5), one
+  // warp per refined system, lanes over the points of its support
+  __shared__ double sA[TW_DWQ_THREADS / 32][TW_WIN * (TW_QMAX + 1)];
+  __shared__ double sb[TW_DWQ_THREADS / 32][TW_WIN], sd[TW_DWQ_THREADS / 32][TW_WIN],
+      sbeta[TW_DWQ_THREADS / 32][TW_WIN];
+  __shared__ int sing[TW_DWQ_THREADS / 32];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int lda = TW_QMAX + 1;
+  for (int li = wib; li < 2 * p && np_ > 0; li += TW_DWQ_THREADS / 32) {
+    int l = s + li;
     int nref = D.n + p;
     double ul = ref_knot(D, s, l), uh = ref_knot(D, s, l + p + 1);
     int rows[TW_WIN], m = 0;
@@ -904,19 +924,25 @@ __global__ void __launch_bounds__(TW_DWQ_THREADS)
       double lo = fmax(ul, ref_knot(D, s, mm)), hi = fmin(uh, ref_knot(D, s, mm + p + 1));
       if (hi > lo) rows[m++] = mm;
     }
-    int cols[TW_QMAX], N = 0;
-    for (int k = 0; k < np_; k++)
-      if (xs[k] > ul && xs[k] < uh) {
-        if (N >= TW_QMAX) { atomicOr(flag, TWF_QMAX); N = 0; break; }
-        cols[N++] = k;
+    // points of supp B~_l: a contiguous run of the sorted window points
+    int c0 = 0;
+    while (c0 < np_ && !(xs[c0] > ul)) c0++;
+    int N = 0;
+    while (c0 + N < np_ && xs[c0 + N] < uh) N++;
+    if (N > TW_QMAX) {
+      if (lane == 0) atomicOr(flag, TWF_QMAX);
+      N = 0;
+    }
+    double *A = sA[wib];
+    if (lane < N) {
+      int k = c0 + lane;
+      for (int r = 0; r < m; r++) {
+        int aa = rows[r] - rsp[k];
+        A[r * lda + lane] = (aa >= 0 && aa <= p) ? RB[k][aa] : 0.0;
       }
-    double A[TW_WIN * TW_QMAX], bb[TW_WIN], w[TW_QMAX], beta[TW_WIN];
-    for (int r = 0; r < m; r++) {
-      int mr = rows[r];
-      for (int c = 0; c < N; c++) {
-        int k = cols[c], aa = mr - rsp[k];
-        A[r * TW_QMAX + c] = (aa >= 0 && aa <= p) ? RB[k][aa] : 0.0;
-      }
+    }
+    if (lane < m) {
+      int mr = rows[lane];
       double acc = 0.0;
       for (int el = 0; el < nwe; el++) {
         int e = ewlo + el;
@@ -927,13 +953,18 @@ __global__ void __launch_bounds__(TW_DWQ_THREADS)
         if (al < 0 || al > p || am < 0 || am > p) continue;
         for (int g = 0; g < p1; g++) acc += D.gw[g] * 0.5 * (eb - ea) * RG[el][g][al] * RG[el][g][am];
       }
-      bb[r] = acc;
+      sb[wib][lane] = acc;
     }
-    for (int k = 0; k < np_; k++) Wt[threadIdx.x][k] = 0.0;
-    if (N > 0) {
-      if (minnorm_lq(m, N, A, TW_QMAX, bb, w, beta)) atomicOr(flag, TWF_SINGULAR);
-      for (int c = 0; c < N; c++) Wt[threadIdx.x][cols[c]] = w[c];
-    }
+    if (lane == 0) sing[wib] = 0;
+    __syncwarp();
+    double wv = 0.0;
+    if (N > 0) wv = warp_minnorm(m, N, A, lda, sb[wib], sd[wib], sbeta[wib], lane, &sing[wib]);
+    __syncwarp();
+    if (lane == 0 && sing[wib]) atomicOr(flag, TWF_SINGULAR);
+    for (int k = lane; k < np_; k += 32) Wt[li][k] = 0.0;
+    __syncwarp();
+    if (lane < N) Wt[li][c0 + lane] = wv;
+    __syncwarp();
   }
   __syncthreads();
   // step 4: w_i = sum over refined l on the side of S[l][i] w~_l  (reading R4)
@@ -954,6 +985,72 @@ __global__ void __launch_bounds__(TW_DWQ_THREADS)
   for (int k = threadIdx.x; k < TW_LQMAX; k += blockDim.x)
     out_x[(size_t)slot * TW_LQMAX + k] = k < np_ ? xs[k] : 0.0;
   if (threadIdx.x == 0) out_np[slot] = np_;
+}
+
+// Element matrices of the cut elements, M_e[a][b] = sum_q w_q c_q B_a B_b over the
+// element's rule (Sect. 3.1), sum-factorised along the rule's Gauss lines: on a
+// line xi_o = s the outer basis values are constant, so the inner sums
+// I[ai][bi] = sum_h w_h c_h B_ai(u_h) B_bi(u_h) are formed first and then
+// M[(ao,ai)][(bo,bi)] += B_ao(s) B_bo(s) I[ai][bi].  Thread (ao, bo) owns
+// (p+1)^2 accumulators; sums run in point order (deterministic).
+template <int P>
+__global__ void __launch_bounds__(64) k_cut_matrices(const int64_t *off, const int32_t *cut_o,
+                                                     int ncut, const double *pts,
+                                                     const double *Bt, const double *wc,
+                                                     double *M) {
+  constexpr int P1 = P + 1, NL = P1 * P1;
+  const int ci = blockIdx.x;
+  if (ci >= ncut) return;
+  const int t = threadIdx.x;
+  const int o = cut_o[ci], in = 1 - o;
+  const int64_t q0 = off[ci], q1 = off[ci + 1];
+  __shared__ double I[NL];
+  double acc[NL];
+#pragma unroll
+  for (int k = 0; k < NL; k++) acc[k] = 0.0;
+  const int ao = t / P1, bo = t % P1;
+  for (int64_t k = q0; k < q1;) {
+    const double s = pts[3 * k + o];
+    int64_t ke = k + 1;
+    while (ke < q1 && pts[3 * ke + o] == s) ke++;
+    if (t < NL) {
+      const int ai = t / P1, bi = t % P1;
+      double sum = 0.0;
+      for (int64_t h = k; h < ke; h++) {
+        const double *bv = Bt + (2 * h + in) * P1;
+        sum = fma(wc[h] * bv[ai], bv[bi], sum);
+      }
+      I[t] = sum;
+    }
+    __syncthreads();
+    if (t < NL) {
+      const double *bo_ = Bt + (2 * k + o) * P1;
+      const double f = bo_[ao] * bo_[bo];
+#pragma unroll
+      for (int m = 0; m < NL; m++) acc[m] = fma(f, I[m], acc[m]);
+    }
+    __syncthreads();
+    k = ke;
+  }
+  if (t < NL) {
+    double *Me = M + (size_t)ci * NL * NL;
+#pragma unroll
+    for (int m = 0; m < NL; m++) {
+      const int ai = m / P1, bi = m % P1;
+      const int a1 = o == 0 ? ao : ai, a2 = o == 0 ? ai : ao;
+      const int b1 = o == 0 ? bo : bi, b2 = o == 0 ? bi : bo;
+      Me[(a2 * P1 + a1) * NL + (b2 * P1 + b1)] = acc[m];
+    }
+  }
+}
+
+static void launch_cut_matrices(tw_patch *P, cudaStream_t st) {
+  switch (P->p) {
+#define TW_CM(PP) case PP: k_cut_matrices<PP><<<P->ncut, 64, 0, st>>>(P->cut_off, P->cut_o, P->ncut, P->cut_pts, P->cut_B, P->cut_wc, P->cut_M); break;
+    TW_CM(1) TW_CM(2) TW_CM(3) TW_CM(4) TW_CM(5) TW_CM(6)
+#undef TW_CM
+  }
+  TW_LAUNCH();
 }
 
 __global__ void k_is_cut(const uint8_t *es, int32_t *f, int64_t n) {
@@ -1017,7 +1114,7 @@ int build_tables(tw_patch *P) {
     TW_LAUNCH();
     k_gauss_tables<<<G1(D.nel * p1)>>>(D);
     TW_LAUNCH();
-    k_wq_weights<<<G1(D.n)>>>(D, P->flag);
+    k_wq_weights<<<(D.n + TW_WQ_WARPS - 1) / TW_WQ_WARPS, 32 * TW_WQ_WARPS, 0, st>>>(D, P->flag);
     TW_LAUNCH();
   }
   if (P->curve.kind == TW_TRIM_BSPLINE3) {
@@ -1139,7 +1236,8 @@ int build_tables(tw_patch *P) {
   // cut-element rules: count, scan, fill
   if (P->ncut > 0) {
     k_cut_rule<<<P->ncut, TW_CUT_THREADS, 0, st>>>(P->curve, A, B, P->cut_list, P->ncut, qgx,
-                                                   qgw, P->qc, ccount, nullptr, nullptr, P->flag);
+                                                   qgw, P->qc, ccount, nullptr, nullptr, nullptr,
+                                                   P->flag);
     TW_LAUNCH();
     if ((rc = exclusive_scan_i64(ccount, P->cut_off, P->ncut, tot64 + 1, st, P))) return rc;
     k_set_last<<<1, 1, 0, st>>>(P->cut_off, P->ncut, tot64 + 1);
@@ -1153,15 +1251,18 @@ int build_tables(tw_patch *P) {
   P->cut_pts = (double *)dalloc(P, sizeof(double) * (3 * P->ncutpts + 1));
   P->cut_wc = (double *)dalloc(P, sizeof(double) * (P->ncutpts + 1));
   P->cut_B = (double *)dalloc(P, sizeof(double) * (2 * P->ncutpts * p1 + 1));
-  if (!P->cut_pts || !P->cut_wc || !P->cut_B) return TW_ENOMEM;
+  P->cut_o = (int32_t *)dalloc(P, sizeof(int32_t) * (P->ncut + 1));
+  P->cut_M = (double *)dalloc(P, sizeof(double) * ((size_t)P->ncut * p1 * p1 * p1 * p1 + 1));
+  if (!P->cut_pts || !P->cut_wc || !P->cut_B || !P->cut_o || !P->cut_M) return TW_ENOMEM;
   if (P->ncut > 0) {
     k_cut_rule<<<P->ncut, TW_CUT_THREADS, 0, st>>>(P->curve, A, B, P->cut_list, P->ncut, qgx,
                                                    qgw, P->qc, nullptr, P->cut_off, P->cut_pts,
-                                                   P->flag);
+                                                   P->cut_o, P->flag);
     TW_LAUNCH();
     k_cut_point_tables<<<P->ncut, 128, 0, st>>>(P->geo, A, B, P->cut_list, P->cut_off, P->ncut,
                                                 P->cut_pts, P->cut_B, P->cut_wc);
     TW_LAUNCH();
+    launch_cut_matrices(P, st);
   }
   // DWQ rules per disc knot
   for (int d = 0; d < 2; d++) {

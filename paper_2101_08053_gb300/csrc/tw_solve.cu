@@ -357,6 +357,7 @@ static RowArgs row_args(tw_patch *Pt) {
   ra.cut_B = Pt->cut_B;
   ra.cut_wc = Pt->cut_wc;
   ra.cut_pts = Pt->cut_pts;
+  ra.cut_M = Pt->cut_M;
   ra.choice = Pt->choice;
   for (int d = 0; d < 2; d++) {
     ra.disc_slot[d] = Pt->disc_slot[d];
