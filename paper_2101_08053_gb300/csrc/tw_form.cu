@@ -29,7 +29,7 @@ __global__ void __launch_bounds__(256) k_interior(Dir A, Dir B, const double *__
                                                   int32_t *__restrict__ col,
                                                   double *__restrict__ val) {
   constexpr int W = 2 * P + 1;
-  constexpr int KMAX = 2 * T + 4 * P + 4;
+  constexpr int KMAX = (2 * T + 4 * P + 4) | 1;  // odd row stride: no bank conflicts
   __shared__ double Y[W * KMAX];
   __shared__ double V2s[TW_QMAX * W];
   __shared__ int cr2[W];
@@ -62,27 +62,58 @@ __global__ void __launch_bounds__(256) k_interior(Dir A, Dir B, const double *__
     Y[r2 * KMAX + kk] = s;
   }
   __syncthreads();
-  // stage 2
+  // stage 2.  Rows whose support avoids the two end elements (2 points per
+  // element, full band) take the point-major path: thread (row, r2) walks the
+  // 2(P+1) points of supp B_i1 and adds each point's value into the P+1
+  // outputs whose trial function lives on the point's element, so every lane
+  // issues the same (P+1)*2*(P+1) DFMAs.  Other rows use the per-output loop.
   const int lo2 = max(0, i2 - P);
-  const int NO = (i1b - i1a) * W * W;
-  for (int idx = threadIdx.x; idx < NO; idx += blockDim.x) {
-    int t = idx / (W * W), rem = idx - t * (W * W);
-    int r2 = rem / W, r1 = rem - r2 * W;
-    int i1 = i1a + t;
-    int g = i2 * n1 + i1;
-    if (fstate[g] != TW_FUNC_INTERIOR) continue;
-    int j1 = i1 - P + r1, j2 = i2 - P + r2;
-    if (j1 < 0 || j1 >= n1 || j2 < 0 || j2 >= B.n) continue;
-    int cr = A.crange[i1 * W + r1];
-    int lo = cr & 0xffff, hi = cr >> 16;
-    const double *v = A.V + ((size_t)i1 * A.qmax) * W + r1;
+  const int NR = (i1b - i1a) * W;
+  for (int idx = threadIdx.x; idx < NR; idx += blockDim.x) {
+    const int t = idx / W, r2 = idx - t * W;
+    const int i1 = i1a + t;
+    const int g = i2 * n1 + i1;
+    const int j2 = i2 - P + r2;
+    if (fstate[g] != TW_FUNC_INTERIOR || j2 < 0 || j2 >= B.n) continue;
     const double *y = Y + r2 * KMAX + (A.qbeg[i1] - kA);
-    double s = 0.0;
-    for (int c1 = lo; c1 < hi; c1++) s = fma(v[c1 * W], y[c1], s);
-    int lo1 = max(0, i1 - P), w1 = min(n1 - 1, i1 + P) - lo1 + 1;
-    int64_t pos = rp[act[g]] + (int64_t)(j2 - lo2) * w1 + (j1 - lo1);
-    val[pos] = s;
-    col[pos] = act[j2 * n1 + j1];
+    const double *v = A.V + ((size_t)i1 * A.qmax) * W;
+    const int64_t rowbase = rp[act[g]];
+    if (i1 >= P + 1 && i1 <= A.nel - 2) {
+      double acc[W];
+#pragma unroll
+      for (int r = 0; r < W; r++) acc[r] = 0.0;
+#pragma unroll
+      for (int el = 0; el <= P; el++) {
+#pragma unroll
+        for (int pt = 0; pt < 2; pt++) {
+          const int c1 = 2 * el + pt;
+          const double yv = y[c1];
+#pragma unroll
+          for (int a = 0; a <= P; a++) acc[el + a] = fma(v[c1 * W + el + a], yv, acc[el + a]);
+        }
+      }
+      double *out = val + rowbase + (int64_t)(j2 - lo2) * W;
+      int32_t *oc = col + rowbase + (int64_t)(j2 - lo2) * W;
+      const int32_t *arow = act + j2 * n1 + (i1 - P);
+#pragma unroll
+      for (int r = 0; r < W; r++) {
+        out[r] = acc[r];
+        oc[r] = arow[r];
+      }
+    } else {
+      const int lo1 = max(0, i1 - P), w1 = min(n1 - 1, i1 + P) - lo1 + 1;
+      for (int r1 = 0; r1 < W; r1++) {
+        const int j1 = i1 - P + r1;
+        if (j1 < 0 || j1 >= n1) continue;
+        const int cr = A.crange[i1 * W + r1];
+        const int lo = cr & 0xffff, hi = cr >> 16;
+        double s = 0.0;
+        for (int c1 = lo; c1 < hi; c1++) s = fma(v[c1 * W + r1], y[c1], s);
+        const int64_t pos = rowbase + (int64_t)(j2 - lo2) * w1 + (j1 - lo1);
+        val[pos] = s;
+        col[pos] = act[j2 * n1 + j1];
+      }
+    }
   }
 }
 
@@ -153,6 +184,7 @@ __global__ void __launch_bounds__(256) k_cutrows(RowArgs a, const int32_t *__res
         int np_ = a.dwq_np[d][sl];
         const double *xs = a.dwq_x[d] + (size_t)sl * TW_LQMAX;
         const double *ws = a.dwq_w[d] + (((size_t)sl * P + (i - s)) * 2 + side) * TW_LQMAX;
+        const int32_t *ks = a.dwq_k[d] + (size_t)sl * TW_LQMAX;
         double ulo = D.U[i], uhi = D.U[i + P + 1];
         for (int k = 0; k < np_; k++) {
           double x = xs[k];
@@ -164,7 +196,7 @@ __global__ void __launch_bounds__(256) k_cutrows(RowArgs a, const int32_t *__res
           }
           rx[d][n] = x;
           rw[d][n] = ws[k];
-          rk[d][n] = -1;
+          rk[d][n] = ks[k];  // base points read c from the grid
           int e = elem_of(D.bp, D.nel, x);
           double N[TW_MAXP1];
           basis_vals(D.U, e + P, x, P, N);
@@ -313,6 +345,7 @@ static void launch_form(tw_patch *Pt, int64_t *rp, int32_t *col, double *val, cu
       ra.dwq_x[d] = Pt->dwq_x[d];
       ra.dwq_np[d] = Pt->dwq_np[d];
       ra.dwq_w[d] = Pt->dwq_w[d];
+      ra.dwq_k[d] = Pt->dwq_k[d];
     }
     ra.method = Pt->method;
     ra.flag = Pt->flag;

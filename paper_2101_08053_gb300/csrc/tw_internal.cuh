@@ -535,6 +535,7 @@ struct RowArgs {
   const double *dwq_x[2];
   const int32_t *dwq_np[2];
   const double *dwq_w[2];
+  const int32_t *dwq_k[2];
   int method;
   int *flag;
 };
@@ -643,6 +644,7 @@ struct tw_patch {
   double *dwq_x[2];  // ndisc x TW_LQMAX points
   int32_t *dwq_np[2];
   double *dwq_w[2];  // ndisc x p x 2 x TW_LQMAX
+  int32_t *dwq_k[2]; // ndisc x TW_LQMAX: base WQ point index of each window point, -1 nested
   int ndwqrows;
   // scratch
   int32_t *flag;     // error flags (device)

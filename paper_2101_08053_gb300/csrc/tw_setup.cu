@@ -482,13 +482,42 @@ __device__ void sort_small(double *v, int n) {
   }
 }
 
+// Curve-wide features, once per patch: tangent points of both kinds (the
+// curve's tangent parallel to an axis) and the spline's segment joints.
+// feat[(kind * fcap + k) * 2 + {0,1}], nfeat[kind], kind 2 = joints.
+__global__ void k_curve_features(Curve C, double *feat, int *nfeat, int fcap, int *flag) {
+  int kind = threadIdx.x;
+  if (kind >= 3) return;
+  double *out = feat + (size_t)kind * fcap * 2;
+  int n = 0;
+  if (kind < 2) {
+    n = curve_folds(C, kind, out, fcap);
+    if (n < 0) {
+      atomicOr(flag, TWF_HITCAP);
+      n = 0;
+    }
+  } else if (C.kind == TW_TRIM_BSPLINE3) {
+    for (int sg = 0; sg < C.nc && n < fcap; sg++, n++) {
+      out[2 * n] = C.seg[8 * sg];
+      out[2 * n + 1] = C.seg[8 * sg + 4];
+    }
+  }
+  nfeat[kind] = n;
+}
+
 // One block of 64 threads per cut element.  Pass 0 (pts == NULL) counts the
 // element's points into cnt[ci], pass 1 writes them from off[ci] on, in the
-// order piece, Gauss line, interval, inner Gauss point.
+// order piece, Gauss line, interval, inner Gauss point.  The element's edge
+// crossings come from the knot-line table (hits/nh of k_line_hits), the
+// tangent points and joints from the curve-wide feature list; only the Gauss
+// lines are solved here.  The visibility of a line's first interval is that of
+// its end on the element edge, i.e. the parity of the edge line's crossings
+// beyond it (the same ray test as curve_inside, read from the table).
 #define TW_CUT_THREADS 64
 __global__ void __launch_bounds__(TW_CUT_THREADS)
     k_cut_rule(Curve C, Dir A, Dir B, const int32_t *cut_list, int ncut, const double *qgx,
-               const double *qgw, int q, int64_t *cnt, const int64_t *off, double *pts,
+               const double *qgw, int q, const double *hits, const int *nh, const double *feat,
+               const int *nfeat, int fcap, int64_t *cnt, const int64_t *off, double *pts,
                int32_t *cut_o, int *flag) {
   const int ci = blockIdx.x;
   if (ci >= ncut) return;
@@ -497,90 +526,70 @@ __global__ void __launch_bounds__(TW_CUT_THREADS)
   const int e1 = e % A.nel, e2 = e / A.nel;
   const double a[2] = {A.bp[e1], B.bp[e2]}, b[2] = {A.bp[e1 + 1], B.bp[e2 + 1]};
   const double dl[2] = {TW_CORNER * (b[0] - a[0]), TW_CORNER * (b[1] - a[1])};
-  __shared__ double plo[8][2], phi[8][2];
-  __shared__ double part[4][TW_HITCAP];
-  __shared__ int npart[4];
+  const int hv = A.nel + 1;  // first horizontal knot line in the table
+  // knot lines of the four edges: [o][side] (o = 0: x = const, o = 1: y = const)
+  const int eline[2][2] = {{e1, e1 + 1}, {hv + e2, hv + e2 + 1}};
   __shared__ double br[TW_BRCAP];
   __shared__ int nbr, s_o, s_bad;
   __shared__ int64_t scan[TW_CUT_THREADS];
-  if (tid == 0) s_bad = 0;
-  // 1. extent of the curve in the box: four edges and two kinds of tangent points
-  if (tid < 8) {
+  if (tid == 0) {
+    int bad = 0;
+    // 1. extent of the curve in the box: edge crossings and tangent points,
+    //    each counted up to TW_CORNER beyond the element
     double lo0 = 1e300, lo1 = 1e300, hi0 = -1e300, hi1 = -1e300;
-    double h[2 * TW_HITCAP];
-    if (tid < 4) {
-      int o = tid >> 1;
-      double s = (tid & 1) ? b[o] : a[o];
-      int n = curve_line_hits(C, o, s, a[1 - o] - dl[1 - o], b[1 - o] + dl[1 - o], h, TW_HITCAP);
-      if (n < 0) { s_bad = 1; n = 0; }
-      for (int k = 0; k < n; k++) {
-        double X = o == 0 ? s : h[k], Y = o == 0 ? h[k] : s;
-        lo0 = fmin(lo0, X); hi0 = fmax(hi0, X); lo1 = fmin(lo1, Y); hi1 = fmax(hi1, Y);
+    for (int o = 0; o < 2; o++)
+      for (int sd = 0; sd < 2; sd++) {
+        int l = eline[o][sd];
+        double s = sd ? b[o] : a[o];
+        const double *h = hits + (size_t)l * TW_HITCAP;
+        for (int k = 0; k < nh[l]; k++) {
+          double v = h[k];
+          if (!(v > a[1 - o] - dl[1 - o] && v < b[1 - o] + dl[1 - o])) continue;
+          double X = o == 0 ? s : v, Y = o == 0 ? v : s;
+          lo0 = fmin(lo0, X); hi0 = fmax(hi0, X); lo1 = fmin(lo1, Y); hi1 = fmax(hi1, Y);
+        }
       }
-    } else if (tid < 6) {
-      int n = curve_folds(C, tid - 4, h, TW_HITCAP);
-      if (n < 0) { s_bad = 1; n = 0; }
-      for (int k = 0; k < n; k++) {
-        double X = h[2 * k], Y = h[2 * k + 1];
+    for (int kind = 0; kind < 2; kind++)
+      for (int k = 0; k < nfeat[kind]; k++) {
+        double X = feat[((size_t)kind * fcap + k) * 2], Y = feat[((size_t)kind * fcap + k) * 2 + 1];
         if (X >= a[0] - dl[0] && X <= b[0] + dl[0] && Y >= a[1] - dl[1] && Y <= b[1] + dl[1]) {
           lo0 = fmin(lo0, X); hi0 = fmax(hi0, X); lo1 = fmin(lo1, Y); hi1 = fmax(hi1, Y);
         }
       }
-    }
-    plo[tid][0] = lo0; plo[tid][1] = lo1; phi[tid][0] = hi0; phi[tid][1] = hi1;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    double lo0 = 1e300, lo1 = 1e300, hi0 = -1e300, hi1 = -1e300;
-    for (int k = 0; k < 8; k++) {
-      lo0 = fmin(lo0, plo[k][0]); lo1 = fmin(lo1, plo[k][1]);
-      hi0 = fmax(hi0, phi[k][0]); hi1 = fmax(hi1, phi[k][1]);
-    }
     // equal extents within TW_TIE of the element size: o = 0
-    s_o = (hi0 - lo0 >= hi1 - lo1 - TW_TIE * fmax(b[0] - a[0], b[1] - a[1])) ? 0 : 1;
-  }
-  __syncthreads();
-  const int o = s_o, in = 1 - o;
-  if (cut_o && tid == 0) cut_o[ci] = o;
-  // 2. breakpoints along o: crossings of the two edges parallel to o, tangent
-  //    points that fold the lines xi_o = const, the spline's segment joints
-  if (tid < 4) {
-    int n = 0;
-    double h[2 * TW_HITCAP];
-    if (tid < 2) {
-      double s = tid ? b[in] : a[in];
-      n = curve_line_hits(C, in, s, a[o], b[o], part[tid], TW_HITCAP);
-      if (n < 0) { s_bad = 1; n = 0; }
-    } else if (tid == 2) {
-      int m = curve_folds(C, o, h, TW_HITCAP);
-      for (int k = 0; k < m; k++) {
-        double xo = h[2 * k + o], xi = h[2 * k + in];
-        if (xo > a[o] && xo < b[o] && xi >= a[in] && xi <= b[in] && n < TW_HITCAP) part[2][n++] = xo;
-      }
-    } else if (C.kind == TW_TRIM_BSPLINE3) {
-      for (int sg = 0; sg < C.nc; sg++) {
-        double X = C.seg[8 * sg], Y = C.seg[8 * sg + 4];
-        double xo = o == 0 ? X : Y, xi = o == 0 ? Y : X;
-        if (xo > a[o] && xo < b[o] && xi >= a[in] && xi <= b[in]) {
-          if (n >= TW_HITCAP) { s_bad = 1; break; }
-          part[3][n++] = xo;
-        }
-      }
-    }
-    npart[tid] = n;
-  }
-  __syncthreads();
-  if (tid == 0) {
+    const int o = (hi0 - lo0 >= hi1 - lo1 - TW_TIE * fmax(b[0] - a[0], b[1] - a[1])) ? 0 : 1;
+    const int in = 1 - o;
+    // 2. breakpoints along o: crossings of the two edges parallel to o, tangent
+    //    points that fold the lines xi_o = const, the spline's segment joints
     int n = 0;
     br[n++] = a[o];
     br[n++] = b[o];
-    for (int k = 0; k < 4; k++)
-      for (int j = 0; j < npart[k]; j++) {
-        if (n >= TW_BRCAP) { s_bad = 1; break; }
-        br[n++] = part[k][j];
+    for (int sd = 0; sd < 2; sd++) {
+      int l = eline[in][sd];
+      const double *h = hits + (size_t)l * TW_HITCAP;
+      for (int k = 0; k < nh[l]; k++)
+        if (h[k] > a[o] && h[k] < b[o]) {
+          if (n >= TW_BRCAP) { bad = 1; break; }
+          br[n++] = h[k];
+        }
+    }
+    const int kinds[2] = {o, 2};
+    for (int kk = 0; kk < 2; kk++) {
+      int kind = kinds[kk];
+      for (int k = 0; k < nfeat[kind]; k++) {
+        const double *f = feat + ((size_t)kind * fcap + k) * 2;
+        double xo = f[o], xi = f[in];
+        if (xo > a[o] && xo < b[o] && xi >= a[in] && xi <= b[in]) {
+          if (n >= TW_BRCAP) { bad = 1; break; }
+          br[n++] = xo;
+        }
       }
+    }
     sort_small(br, n);
     nbr = n;
+    s_o = o;
+    s_bad = bad;
+    if (cut_o) cut_o[ci] = o;
   }
   __syncthreads();
   if (s_bad) {
@@ -590,8 +599,13 @@ __global__ void __launch_bounds__(TW_CUT_THREADS)
     }
     return;
   }
+  const int o = s_o, in = 1 - o;
+  // crossings of the edge line through each line's first end (xi_in = a_in)
+  const int lfirst = eline[in][0];
+  const double *eh = hits + (size_t)lfirst * TW_HITCAP;
+  const int neh = nh[lfirst];
   // 3. Gauss lines of every piece; crossings split the inner range and the
-  //    visibility of the pieces alternates at each crossing
+  //    visibility alternates at each crossing
   const int nlines = (nbr - 1) * q;
   const int64_t base0 = off ? off[ci] : 0;
   int64_t base = 0;
@@ -614,13 +628,10 @@ __global__ void __launch_bounds__(TW_CUT_THREADS)
         } else {
           h[0] = a[in];
           h[n + 1] = b[in];
-          // visibility of the first interval by the midpoint test
-          int k0 = 0;
-          while (k0 <= n && !(h[k0 + 1] > h[k0])) k0++;
-          if (k0 <= n) {
-            double mid = 0.5 * (h[k0] + h[k0 + 1]);
-            vis0 = visible(C, o == 0 ? s : mid, o == 0 ? mid : s) ^ (k0 & 1);
-          }
+          int right = 0;
+          for (int k = 0; k < neh; k++) right += eh[k] > s;
+          int inside = right & 1;
+          vis0 = C.kind == TW_TRIM_NONE ? 1 : (C.keep_inside ? inside : !inside);
           for (int k = 0; k <= n; k++)
             if (h[k + 1] > h[k] && (vis0 ^ (k & 1))) count += q;
         }
@@ -806,13 +817,14 @@ __device__ double ref_fn(const Dir &D, int s, int m, double x) {
 #define TW_DWQ_THREADS 128
 __global__ void __launch_bounds__(TW_DWQ_THREADS)
     k_dwq_build(Dir D, const int32_t *disc_list, int ndisc, double *out_x, int32_t *out_np,
-                double *out_w, int *flag) {
+                double *out_w, int32_t *out_k, int *flag) {
   int slot = blockIdx.x;
   if (slot >= ndisc) return;
   int s = disc_list[slot];
   int p = D.p, p1 = p + 1;
   double t = D.bp[s];
   __shared__ double xs[TW_LQMAX];
+  __shared__ int xk[TW_LQMAX];                   // base point index, -1 for a nested point
   __shared__ double RB[TW_LQMAX][TW_MAXP1];      // refined functions on each point's span
   __shared__ int rsp[TW_LQMAX];                  // first refined function of that span
   __shared__ double RG[2 * TW_MAXP][TW_MAXP1][TW_MAXP1];  // [window element][g][a]
@@ -829,7 +841,10 @@ __global__ void __launch_bounds__(TW_DWQ_THREADS)
       int m = k1 - k0;
       int nb0 = n;
       for (int k = k0; k < k1; k++) {
-        if (n < TW_LQMAX) xs[n] = D.xq[k];
+        if (n < TW_LQMAX) {
+          xs[n] = D.xq[k];
+          xk[n] = k;
+        }
         n++;
       }
       if ((e == s - 1 || e == s) && m < p1) {
@@ -848,12 +863,26 @@ __global__ void __launch_bounds__(TW_DWQ_THREADS)
         }
         for (int gp = 0; gp < 3; gp++)
           for (int j = 0; j < cnt[gp]; j++) {
-            if (n < TW_LQMAX)
+            if (n < TW_LQMAX) {
               xs[n] = ed[gp] + (ed[gp + 1] - ed[gp]) * (double)(j + 1) / (double)(cnt[gp] + 1);
+              xk[n] = -1;
+            }
             n++;
           }
       }
-      if (n <= TW_LQMAX) sort_small(xs + nb0, n - nb0);
+      if (n <= TW_LQMAX) {  // insertion sort of (x, k) pairs within the element
+        for (int a2 = nb0 + 1; a2 < n; a2++) {
+          double x = xs[a2];
+          int kk = xk[a2], b2 = a2 - 1;
+          while (b2 >= nb0 && xs[b2] > x) {
+            xs[b2 + 1] = xs[b2];
+            xk[b2 + 1] = xk[b2];
+            b2--;
+          }
+          xs[b2 + 1] = x;
+          xk[b2 + 1] = kk;
+        }
+      }
     }
     if (n > TW_LQMAX) {
       atomicOr(flag, TWF_LQMAX);
@@ -982,8 +1011,10 @@ __global__ void __launch_bounds__(TW_DWQ_THREADS)
     }
     out_w[(((size_t)slot * p + col) * 2 + side) * TW_LQMAX + k] = acc;
   }
-  for (int k = threadIdx.x; k < TW_LQMAX; k += blockDim.x)
+  for (int k = threadIdx.x; k < TW_LQMAX; k += blockDim.x) {
     out_x[(size_t)slot * TW_LQMAX + k] = k < np_ ? xs[k] : 0.0;
+    out_k[(size_t)slot * TW_LQMAX + k] = k < np_ ? xk[k] : -1;
+  }
   if (threadIdx.x == 0) out_np[slot] = np_;
 }
 
@@ -1130,13 +1161,20 @@ int build_tables(tw_patch *P) {
   int32_t *cflag = (int32_t *)dalloc(P, sizeof(int32_t) * nf);
   int32_t *cpos = (int32_t *)dalloc(P, sizeof(int32_t) * nf);
   if (!aflag || !cflag || !cpos) return TW_ENOMEM;
+  int fcap = 2 * P->curve.nc + 4;
+  double *lh, *feat;
+  int *lnh, *nfeat;
   {
     int nl = (A.nel + 1) + (B.nel + 1) + B.nel;
-    double *lh = (double *)dalloc(P, sizeof(double) * (size_t)nl * TW_HITCAP);
-    int *lnh = (int *)dalloc(P, sizeof(int) * nl);
-    if (!lh || !lnh) return TW_ENOMEM;
+    lh = (double *)dalloc(P, sizeof(double) * (size_t)nl * TW_HITCAP);
+    lnh = (int *)dalloc(P, sizeof(int) * nl);
+    feat = (double *)dalloc(P, sizeof(double) * 3 * 2 * (size_t)fcap);
+    nfeat = (int *)dalloc(P, sizeof(int) * 4);
+    if (!lh || !lnh || !feat || !nfeat) return TW_ENOMEM;
     if (P->curve.kind != TW_TRIM_NONE) {
       k_line_hits<<<G1(nl)>>>(P->curve, A, B, lh, lnh, P->flag);
+      TW_LAUNCH();
+      k_curve_features<<<1, 32, 0, st>>>(P->curve, feat, nfeat, fcap, P->flag);
       TW_LAUNCH();
     }
     k_classify_elems<<<G1(ne)>>>(P->curve, A, B, lh, lnh, P->estate);
@@ -1236,8 +1274,8 @@ int build_tables(tw_patch *P) {
   // cut-element rules: count, scan, fill
   if (P->ncut > 0) {
     k_cut_rule<<<P->ncut, TW_CUT_THREADS, 0, st>>>(P->curve, A, B, P->cut_list, P->ncut, qgx,
-                                                   qgw, P->qc, ccount, nullptr, nullptr, nullptr,
-                                                   P->flag);
+                                                   qgw, P->qc, lh, lnh, feat, nfeat, fcap, ccount,
+                                                   nullptr, nullptr, nullptr, P->flag);
     TW_LAUNCH();
     if ((rc = exclusive_scan_i64(ccount, P->cut_off, P->ncut, tot64 + 1, st, P))) return rc;
     k_set_last<<<1, 1, 0, st>>>(P->cut_off, P->ncut, tot64 + 1);
@@ -1256,8 +1294,8 @@ int build_tables(tw_patch *P) {
   if (!P->cut_pts || !P->cut_wc || !P->cut_B || !P->cut_o || !P->cut_M) return TW_ENOMEM;
   if (P->ncut > 0) {
     k_cut_rule<<<P->ncut, TW_CUT_THREADS, 0, st>>>(P->curve, A, B, P->cut_list, P->ncut, qgx,
-                                                   qgw, P->qc, nullptr, P->cut_off, P->cut_pts,
-                                                   P->cut_o, P->flag);
+                                                   qgw, P->qc, lh, lnh, feat, nfeat, fcap, nullptr,
+                                                   P->cut_off, P->cut_pts, P->cut_o, P->flag);
     TW_LAUNCH();
     k_cut_point_tables<<<P->ncut, 128, 0, st>>>(P->geo, A, B, P->cut_list, P->cut_off, P->ncut,
                                                 P->cut_pts, P->cut_B, P->cut_wc);
@@ -1271,13 +1309,15 @@ int build_tables(tw_patch *P) {
     P->dwq_x[d] = (double *)dalloc(P, sizeof(double) * ((size_t)nd * TW_LQMAX + 1));
     P->dwq_np[d] = (int32_t *)dalloc(P, sizeof(int32_t) * (nd + 1));
     P->dwq_w[d] = (double *)dalloc(P, sizeof(double) * ((size_t)nd * p * 2 * TW_LQMAX + 1));
+    P->dwq_k[d] = (int32_t *)dalloc(P, sizeof(int32_t) * ((size_t)nd * TW_LQMAX + 1));
+    if (!P->dwq_k[d]) return TW_ENOMEM;
     int32_t *dlist = (int32_t *)dalloc(P, sizeof(int32_t) * (nd + 1));
     if (!P->dwq_x[d] || !P->dwq_np[d] || !P->dwq_w[d] || !dlist) return TW_ENOMEM;
     k_compact<<<G1(D.nel + 1)>>>(dflag[d], dpos[d], dlist, P->disc_slot[d], D.nel + 1);
     TW_LAUNCH();
     if (nd > 0) {
       k_dwq_build<<<nd, TW_DWQ_THREADS, 0, st>>>(D, dlist, nd, P->dwq_x[d], P->dwq_np[d], P->dwq_w[d],
-                                     P->flag);
+                                                 P->dwq_k[d], P->flag);
       TW_LAUNCH();
     }
   }

@@ -364,6 +364,7 @@ static RowArgs row_args(tw_patch *Pt) {
     ra.dwq_x[d] = Pt->dwq_x[d];
     ra.dwq_np[d] = Pt->dwq_np[d];
     ra.dwq_w[d] = Pt->dwq_w[d];
+    ra.dwq_k[d] = Pt->dwq_k[d];
   }
   ra.method = Pt->method;
   ra.flag = Pt->flag;
