@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(256) k_cutrows(RowArgs a, const int32_t *__res
   __shared__ double acc[W * W];
   __shared__ double rx[2][TW_RC], rw[2][TW_RC], rb[2][TW_RC][W];
   __shared__ int rk[2][TW_RC];
-  __shared__ int nr[2];
+  __shared__ int nr[2], nnest[2], nest[2][TW_RC];
   __shared__ double cg[TW_RC * TW_RC];
   __shared__ double Z[W * TW_RC];
   __shared__ double Tg[P1 * P1];
@@ -159,69 +159,96 @@ __global__ void __launch_bounds__(256) k_cutrows(RowArgs a, const int32_t *__res
   for (int t = tid; t < W * W; t += blockDim.x) acc[t] = 0.0;
 
   // ---- region part: naive WQ (full support, c masked) or DWQ rectangle ----
+  // warp d assembles direction d's rule, one lane per point, from the tables
   if (kind != 0) {
-    if (tid < 2) {
-      const int d = tid;
+    const int wd = tid >> 5, lane = tid & 31;
+    if (wd < 2) {
+      const int d = wd;
       const Dir &D = d == 0 ? A : B;
       const int i = d == 0 ? i1 : i2;
-      int n = 0;
+      int n;
       if (kind == 1 || ch[2 * d] == 0) {
-        for (int c = 0; c < D.qcnt[i]; c++) {
-          int k = D.qbeg[i] + c;
-          rx[d][n] = D.xq[k];
-          rw[d][n] = D.W[(size_t)i * D.qmax + c];
-          rk[d][n] = k;
+        n = D.qcnt[i];
+        if (lane < n) {
+          const int k = D.qbeg[i] + lane;
+          rx[d][lane] = D.xq[k];
+          rw[d][lane] = D.W[(size_t)i * D.qmax + lane];
+          rk[d][lane] = k;
           for (int r = 0; r < W; r++) {
-            int j = i - P + r, aa = j - D.qel[k];
-            rb[d][n][r] = (aa >= 0 && aa <= P) ? D.Bq[k * P1 + aa] : 0.0;
+            int aa = i - P + r - D.qel[k];
+            rb[d][lane][r] = (aa >= 0 && aa <= P) ? D.Bq[k * P1 + aa] : 0.0;
           }
-          n++;
         }
       } else {
-        int s = ch[2 * d + 1], side = ch[2 * d] - 1;
-        int sl = a.disc_slot[d][s];
-        double t = D.bp[s];
-        int np_ = a.dwq_np[d][sl];
-        const double *xs = a.dwq_x[d] + (size_t)sl * TW_LQMAX;
-        const double *ws = a.dwq_w[d] + (((size_t)sl * P + (i - s)) * 2 + side) * TW_LQMAX;
-        const int32_t *ks = a.dwq_k[d] + (size_t)sl * TW_LQMAX;
-        double ulo = D.U[i], uhi = D.U[i + P + 1];
-        for (int k = 0; k < np_; k++) {
-          double x = xs[k];
-          if (!(x > ulo && x < uhi)) continue;
-          if (side == 0 ? !(x < t) : !(x > t)) continue;
-          if (n >= TW_RC) {
-            atomicOr(a.flag, TWF_RULECAP);
-            break;
-          }
-          rx[d][n] = x;
-          rw[d][n] = ws[k];
-          rk[d][n] = ks[k];  // base points read c from the grid
-          int e = elem_of(D.bp, D.nel, x);
-          double N[TW_MAXP1];
-          basis_vals(D.U, e + P, x, P, N);
+        const int s = ch[2 * d + 1], side = ch[2 * d] - 1;
+        const int sl = a.disc_slot[d][s];
+        const int run = a.dwq_r[d][((size_t)sl * P + (i - s)) * 2 + side];
+        const int k0 = run & 0xffff, k1 = run >> 16;
+        n = k1 - k0;
+        if (n > TW_RC) {
+          if (lane == 0) atomicOr(a.flag, TWF_RULECAP);
+          n = 0;
+        }
+        if (lane < n) {
+          const size_t k = (size_t)sl * TW_LQMAX + k0 + lane;
+          rx[d][lane] = a.dwq_x[d][k];
+          rw[d][lane] = a.dwq_w[d][(((size_t)sl * P + (i - s)) * 2 + side) * TW_LQMAX + k0 + lane];
+          rk[d][lane] = a.dwq_k[d][k];  // base points read c from the grid
+          const int e = a.dwq_e[d][k];
+          const double *Bv = a.dwq_B[d] + k * P1;
           for (int r = 0; r < W; r++) {
-            int j = i - P + r, aa = j - e;
-            rb[d][n][r] = (aa >= 0 && aa <= P) ? N[aa] : 0.0;
+            int aa = i - P + r - e;
+            rb[d][lane][r] = (aa >= 0 && aa <= P) ? Bv[aa] : 0.0;
           }
-          n++;
         }
       }
-      nr[d] = n;
+      if (lane == 0) nr[d] = n;
     }
     __syncthreads();
     const int m1 = nr[0], m2 = nr[1];
+    // c at the tensor points: grid pairs first, then the pairs with a nested
+    // point packed densely so only a few warps evaluate c directly
     for (int t = tid; t < m1 * m2; t += blockDim.x) {
       int ia = t % m1, ib = t / m1;
-      double c;
       int k1 = rk[0][ia], k2 = rk[1][ib];
       if (k1 >= 0 && k2 >= 0) {
-        c = a.C[(size_t)k2 * A.nq + k1];
+        double c = a.C[(size_t)k2 * A.nq + k1];
         if (kind == 1 && a.estate[B.qel[k2] * A.nel + A.qel[k1]] != TW_ELEM_REGULAR) c = 0.0;
-      } else {
-        c = coef_at(a.G, A, B, rx[0][ia], rx[1][ib]);
+        cg[ia * TW_RC + ib] = c;
       }
-      cg[ia * TW_RC + ib] = c;
+    }
+    if (tid == 0) {
+      int na = 0, nb = 0;
+      for (int ia = 0; ia < m1; ia++)
+        if (rk[0][ia] < 0) nest[0][na++] = ia;
+      for (int ib = 0; ib < m2; ib++)
+        if (rk[1][ib] < 0) nest[1][nb++] = ib;
+      nnest[0] = na;
+      nnest[1] = nb;
+    }
+    __syncthreads();
+    {
+      const int na = nnest[0], nb = nnest[1];
+      const int tot = na * m2 + (m1 - na) * nb;
+      for (int t = tid; t < tot; t += blockDim.x) {
+        int ia, ib;
+        if (t < na * m2) {
+          ia = nest[0][t / m2];
+          ib = t % m2;
+        } else {
+          int u = t - na * m2;
+          ib = nest[1][u % nb];
+          // the (u / nb)-th base point of direction 0
+          int want = u / nb, cntb = -1;
+          ia = 0;
+          for (int q = 0; q < m1; q++)
+            if (rk[0][q] >= 0 && ++cntb == want) {
+              ia = q;
+              break;
+            }
+        }
+        cg[ia * TW_RC + ib] = coef_at(a.G, A, B, rx[0][ia], rx[1][ib]);
+      }
     }
     __syncthreads();
     for (int t = tid; t < W * m1; t += blockDim.x) {
@@ -249,7 +276,15 @@ __global__ void __launch_bounds__(256) k_cutrows(RowArgs a, const int32_t *__res
       const int e = e2 * A.nel + e1;
       const uint8_t st = a.estate[e];
       const bool inR = e1 >= r0[0] && e1 <= r1[0] && e2 >= r0[1] && e2 <= r1[1];
-      if (st == TW_ELEM_REGULAR && kind != 1 && !inR) {
+      if (st == TW_ELEM_REGULAR && kind != 1 && !inR && a.gmat) {
+        // the regular element's matrix, formed once per element
+        const double *Me = a.gmat + ((size_t)a.gslot[e] * p1 * p1 + (i2 - e2) * p1 + (i1 - e1)) * p1 * p1;
+        if (tid < p1 * p1) {
+          int b1 = tid % p1, b2 = tid / p1;
+          acc[(e2 + b2 - i2 + P) * W + (e1 + b1 - i1 + P)] += Me[b2 * p1 + b1];
+        }
+        __syncthreads();
+      } else if (st == TW_ELEM_REGULAR && kind != 1 && !inR) {
         const double *cgp = a.gc + (size_t)a.gslot[e] * p1 * p1;
         const double h1 = 0.5 * (A.bp[e1 + 1] - A.bp[e1]), h2 = 0.5 * (B.bp[e2 + 1] - B.bp[e2]);
         const double *GB1 = A.GB + (size_t)e1 * p1 * p1;
@@ -346,7 +381,11 @@ static void launch_form(tw_patch *Pt, int64_t *rp, int32_t *col, double *val, cu
       ra.dwq_np[d] = Pt->dwq_np[d];
       ra.dwq_w[d] = Pt->dwq_w[d];
       ra.dwq_k[d] = Pt->dwq_k[d];
+      ra.dwq_e[d] = Pt->dwq_e[d];
+      ra.dwq_B[d] = Pt->dwq_B[d];
+      ra.dwq_r[d] = Pt->dwq_r[d];
     }
+    ra.gmat = Pt->gmat;
     ra.method = Pt->method;
     ra.flag = Pt->flag;
     int ps = prof_start(s);

@@ -25,6 +25,7 @@
 #define TW_RULECAP 64                     // points of one direction's region rule
 #define TW_CORNER 1e-12  // relative margin: curve touching an element corner (R6, R8)
 #define TW_TIE 1e-9      // relative tie of the curve's extents in a cut element (R6)
+#define TW_GMAT_BUDGET ((size_t)4 << 30)  // bytes of regular-element matrices per patch
 
 // device error flags (bit set by kernels, read by the host at sync points)
 #define TWF_BRCAP 1
@@ -536,6 +537,10 @@ struct RowArgs {
   const int32_t *dwq_np[2];
   const double *dwq_w[2];
   const int32_t *dwq_k[2];
+  const int32_t *dwq_e[2];
+  const double *dwq_B[2];
+  const int32_t *dwq_r[2];
+  const double *gmat;
   int method;
   int *flag;
 };
@@ -645,6 +650,10 @@ struct tw_patch {
   int32_t *dwq_np[2];
   double *dwq_w[2];  // ndisc x p x 2 x TW_LQMAX
   int32_t *dwq_k[2]; // ndisc x TW_LQMAX: base WQ point index of each window point, -1 nested
+  int32_t *dwq_e[2]; // ndisc x TW_LQMAX: coarse element of each window point
+  double *dwq_B[2];  // ndisc x TW_LQMAX x (p+1): coarse basis values there
+  int32_t *dwq_r[2]; // ndisc x p x 2: window point run of (function, side)
+  double *gmat;      // ngslot x (p+1)^4 element matrices of the Gauss elements (or NULL)
   int ndwqrows;
   // scratch
   int32_t *flag;     // error flags (device)

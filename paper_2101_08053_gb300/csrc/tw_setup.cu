@@ -817,7 +817,8 @@ __device__ double ref_fn(const Dir &D, int s, int m, double x) {
 #define TW_DWQ_THREADS 128
 __global__ void __launch_bounds__(TW_DWQ_THREADS)
     k_dwq_build(Dir D, const int32_t *disc_list, int ndisc, double *out_x, int32_t *out_np,
-                double *out_w, int32_t *out_k, int *flag) {
+                double *out_w, int32_t *out_k, int32_t *out_e, double *out_B, int32_t *out_r,
+                int *flag) {
   int slot = blockIdx.x;
   if (slot >= ndisc) return;
   int s = disc_list[slot];
@@ -1014,6 +1015,26 @@ __global__ void __launch_bounds__(TW_DWQ_THREADS)
   for (int k = threadIdx.x; k < TW_LQMAX; k += blockDim.x) {
     out_x[(size_t)slot * TW_LQMAX + k] = k < np_ ? xs[k] : 0.0;
     out_k[(size_t)slot * TW_LQMAX + k] = k < np_ ? xk[k] : -1;
+    // coarse element and coarse basis values of each window point
+    int e = 0;
+    double N[TW_MAXP1];
+    if (k < np_) {
+      e = elem_of(D.bp, D.nel, xs[k]);
+      basis_vals(D.U, e + p, xs[k], p, N);
+    }
+    out_e[(size_t)slot * TW_LQMAX + k] = e;
+    for (int a2 = 0; a2 <= p; a2++) out_B[((size_t)slot * TW_LQMAX + k) * p1 + a2] = k < np_ ? N[a2] : 0.0;
+  }
+  // per coarse function i = s + col and side: the contiguous run of window
+  // points inside supp B_i on that side of t
+  for (int id = threadIdx.x; id < 2 * p; id += blockDim.x) {
+    int col = id >> 1, side = id & 1, i = s + col;
+    double lo = side == 0 ? D.U[i] : t, hi = side == 0 ? t : D.U[i + p + 1];
+    int k0 = 0;
+    while (k0 < np_ && !(xs[k0] > lo)) k0++;
+    int k1 = k0;
+    while (k1 < np_ && xs[k1] < hi) k1++;
+    out_r[((size_t)slot * p + col) * 2 + side] = k0 | (k1 << 16);
   }
   if (threadIdx.x == 0) out_np[slot] = np_;
 }
@@ -1080,6 +1101,52 @@ static void launch_cut_matrices(tw_patch *P, cudaStream_t st) {
 #define TW_CM(PP) case PP: k_cut_matrices<PP><<<P->ncut, 64, 0, st>>>(P->cut_off, P->cut_o, P->ncut, P->cut_pts, P->cut_B, P->cut_wc, P->cut_M); break;
     TW_CM(1) TW_CM(2) TW_CM(3) TW_CM(4) TW_CM(5) TW_CM(6)
 #undef TW_CM
+  }
+  TW_LAUNCH();
+}
+
+// Element matrices of the regular elements some row integrates by Gauss
+// (Sect. 3.2), sum-factorised at element level:
+//   T[a1][b1][g2] = sum_g1 w1 B_a1 B_b1 c(g1, g2),
+//   M[(a1,a2)][(b1,b2)] = sum_g2 T[a1][b1][g2] w2 B_a2 B_b2.
+template <int P>
+__global__ void __launch_bounds__(256) k_gauss_matrices(Dir A, Dir B, const int32_t *glist, int ng,
+                                                       const double *gc, double *M) {
+  constexpr int P1 = P + 1, NL = P1 * P1;
+  const int sl = blockIdx.x;
+  if (sl >= ng) return;
+  const int e = glist[sl], e1 = e % A.nel, e2 = e / A.nel;
+  __shared__ double T[P1 * P1 * P1];
+  const double h1 = 0.5 * (A.bp[e1 + 1] - A.bp[e1]), h2 = 0.5 * (B.bp[e2 + 1] - B.bp[e2]);
+  const double *GB1 = A.GB + (size_t)e1 * NL;  // [g][a]
+  const double *GB2 = B.GB + (size_t)e2 * NL;
+  const double *c = gc + (size_t)sl * NL;      // [g2][g1]
+  for (int id = threadIdx.x; id < P1 * P1 * P1; id += blockDim.x) {
+    const int a1 = id / NL, b1 = (id / P1) % P1, g2 = id % P1;
+    double s = 0.0;
+#pragma unroll
+    for (int g1 = 0; g1 < P1; g1++)
+      s = fma(A.gw[g1] * h1 * GB1[g1 * P1 + a1] * GB1[g1 * P1 + b1], c[g2 * P1 + g1], s);
+    T[id] = s;
+  }
+  __syncthreads();
+  double *Me = M + (size_t)sl * NL * NL;
+  for (int id = threadIdx.x; id < NL * NL; id += blockDim.x) {
+    const int a = id / NL, b = id % NL;
+    const int a1 = a % P1, a2 = a / P1, b1 = b % P1, b2 = b / P1;
+    double s = 0.0;
+#pragma unroll
+    for (int g2 = 0; g2 < P1; g2++)
+      s = fma(T[(a1 * P1 + b1) * P1 + g2], B.gw[g2] * h2 * GB2[g2 * P1 + a2] * GB2[g2 * P1 + b2], s);
+    Me[id] = s;
+  }
+}
+
+static void launch_gauss_matrices(tw_patch *P, const int32_t *glist, cudaStream_t st) {
+  switch (P->p) {
+#define TW_GM(PP) case PP: k_gauss_matrices<PP><<<P->ngslot, 256, 0, st>>>(P->d[0], P->d[1], glist, P->ngslot, P->gc, P->gmat); break;
+    TW_GM(1) TW_GM(2) TW_GM(3) TW_GM(4) TW_GM(5) TW_GM(6)
+#undef TW_GM
   }
   TW_LAUNCH();
 }
@@ -1266,10 +1333,19 @@ int build_tables(tw_patch *P) {
   }
   k_cgrid<<<G1((int64_t)A.nq * B.nq)>>>(P->geo, A, B, Gt, P->C);
   TW_LAUNCH();
-  // element Gauss c tables
+  // element Gauss c tables and element matrices (skipped above TW_GMAT_BUDGET
+  // bytes: the cut-row kernel then integrates those elements row by row)
   if (P->ngslot > 0) {
     k_gauss_c<<<G1((int64_t)P->ngslot * p1 * p1)>>>(P->geo, A, B, glist, P->ngslot, P->gc);
     TW_LAUNCH();
+    size_t nl = (size_t)p1 * p1;
+    size_t bytes = (size_t)P->ngslot * nl * nl * sizeof(double);
+    P->gmat = nullptr;
+    if (bytes <= TW_GMAT_BUDGET) {
+      P->gmat = (double *)dalloc(P, bytes);
+      if (!P->gmat) return TW_ENOMEM;
+      launch_gauss_matrices(P, glist, st);
+    }
   }
   // cut-element rules: count, scan, fill
   if (P->ncut > 0) {
@@ -1310,14 +1386,18 @@ int build_tables(tw_patch *P) {
     P->dwq_np[d] = (int32_t *)dalloc(P, sizeof(int32_t) * (nd + 1));
     P->dwq_w[d] = (double *)dalloc(P, sizeof(double) * ((size_t)nd * p * 2 * TW_LQMAX + 1));
     P->dwq_k[d] = (int32_t *)dalloc(P, sizeof(int32_t) * ((size_t)nd * TW_LQMAX + 1));
-    if (!P->dwq_k[d]) return TW_ENOMEM;
+    P->dwq_e[d] = (int32_t *)dalloc(P, sizeof(int32_t) * ((size_t)nd * TW_LQMAX + 1));
+    P->dwq_B[d] = (double *)dalloc(P, sizeof(double) * ((size_t)nd * TW_LQMAX * p1 + 1));
+    P->dwq_r[d] = (int32_t *)dalloc(P, sizeof(int32_t) * ((size_t)nd * p * 2 + 1));
+    if (!P->dwq_k[d] || !P->dwq_e[d] || !P->dwq_B[d] || !P->dwq_r[d]) return TW_ENOMEM;
     int32_t *dlist = (int32_t *)dalloc(P, sizeof(int32_t) * (nd + 1));
     if (!P->dwq_x[d] || !P->dwq_np[d] || !P->dwq_w[d] || !dlist) return TW_ENOMEM;
     k_compact<<<G1(D.nel + 1)>>>(dflag[d], dpos[d], dlist, P->disc_slot[d], D.nel + 1);
     TW_LAUNCH();
     if (nd > 0) {
       k_dwq_build<<<nd, TW_DWQ_THREADS, 0, st>>>(D, dlist, nd, P->dwq_x[d], P->dwq_np[d], P->dwq_w[d],
-                                                 P->dwq_k[d], P->flag);
+                                                 P->dwq_k[d], P->dwq_e[d], P->dwq_B[d],
+                                                 P->dwq_r[d], P->flag);
       TW_LAUNCH();
     }
   }

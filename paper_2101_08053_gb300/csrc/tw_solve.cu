@@ -365,7 +365,11 @@ static RowArgs row_args(tw_patch *Pt) {
     ra.dwq_np[d] = Pt->dwq_np[d];
     ra.dwq_w[d] = Pt->dwq_w[d];
     ra.dwq_k[d] = Pt->dwq_k[d];
+    ra.dwq_e[d] = Pt->dwq_e[d];
+    ra.dwq_B[d] = Pt->dwq_B[d];
+    ra.dwq_r[d] = Pt->dwq_r[d];
   }
+  ra.gmat = Pt->gmat;
   ra.method = Pt->method;
   ra.flag = Pt->flag;
   return ra;
