@@ -8,13 +8,16 @@
 #include <cstdlib>
 #include <cstring>
 
+#include <atomic>
+#include <mutex>
 #include <vector>
 
 #include "tw_internal.cuh"
 
 namespace tw {
 
-int64_t g_launches = 0;
+std::atomic<int64_t> g_launches{0};
+static std::mutex g_prof_mu;
 
 // ---- stage profiler: event pairs on the launching stream ----
 struct ProfRec {
@@ -26,6 +29,7 @@ static std::vector<ProfRec> g_prof;
 
 int prof_start(cudaStream_t s) {
   if (!g_prof_on) return -1;
+  std::lock_guard<std::mutex> lock(g_prof_mu);
   ProfRec r;
   r.stage = -1;
   cudaEventCreate(&r.a);
@@ -36,6 +40,7 @@ int prof_start(cudaStream_t s) {
 }
 
 void prof_stop(int slot, int stage, cudaStream_t s) {
+  std::lock_guard<std::mutex> lock(g_prof_mu);
   if (slot < 0 || slot >= (int)g_prof.size()) return;
   g_prof[slot].stage = stage;
   cudaEventRecord(g_prof[slot].b, s);
@@ -109,7 +114,7 @@ static int valid_open_knots(const double *U, int nk, int p, const char *what) {
 using namespace tw;
 
 extern "C" const char *tw_last_error(void) { return g_err; }
-extern "C" int64_t tw_launch_count(void) { return g_launches; }
+extern "C" int64_t tw_launch_count(void) { return g_launches.load(); }
 
 extern "C" int tw_profile_enable(int on) {
   g_prof_on = on != 0;
@@ -123,6 +128,7 @@ extern "C" int tw_profile_read(int stage, double *total_ms, int64_t *count) {
   }
   double ms = 0.0;
   int64_t n = 0;
+  std::lock_guard<std::mutex> lock(g_prof_mu);
   std::vector<ProfRec> keep;
   for (auto &r : g_prof) {
     if (r.stage != stage) {
@@ -263,8 +269,6 @@ extern "C" int tw_patch_create(const tw_patch_desc *desc, tw_patch **out) {
       ALLOC(D.W, double, (size_t)D.n * D.qmax);
       ALLOC(D.V, double, (size_t)D.n * D.qmax * W);
       ALLOC(D.crange, int, (size_t)D.n * W);
-      ALLOC(D.gx, double, p + 1);
-      ALLOC(D.gw, double, p + 1);
       ALLOC(D.GB, double, (size_t)D.nel * (p + 1) * (p + 1));
       ALLOC(D.dGB, double, (size_t)D.nel * (p + 1) * (p + 1));
       hbp = (double *)malloc(sizeof(double) * (D.nel + 1));

@@ -13,6 +13,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "../../include/trimwq.h"
 
 #define TW_MAXP 6
@@ -56,7 +58,7 @@ struct Dir {
   double *W;    // n x qmax
   double *V;    // n x qmax x (2p+1)   W * B_j(x_k), r = j - i + p
   int *crange;  // n x (2p+1): lo | (hi << 16) local point range where V != 0
-  double *gx, *gw;  // Gauss-Legendre on [-1,1], p+1 points
+  const double *gx, *gw;  // Gauss-Legendre on [-1,1], p+1 points (cached, not owned)
   double *GB, *dGB; // nel x (p+1) x (p+1): B_{e+a}(x_{e,g}) at [e][g][a]
 };
 
@@ -609,6 +611,7 @@ static __device__ double warp_minnorm(int m, int N, double *A, int lda, const do
 struct tw_patch {
   int p, method, qc;
   tw::Dir d[2];
+  const double *qrule;  // cut-piece Gauss rule (cached, not owned)
   tw::Curve curve;
   double *curve_ctrl;  // device copy of the spline curve's control points
   tw::Geo geo;
@@ -662,7 +665,7 @@ struct tw_patch {
 
 // host helpers shared by the translation units
 namespace tw {
-extern int64_t g_launches;
+extern std::atomic<int64_t> g_launches;
 int prof_start(cudaStream_t s);                  // -1 when profiling is off
 void prof_stop(int slot, int stage, cudaStream_t s);
 void set_error(const char *fmt, ...);
@@ -674,6 +677,9 @@ int exclusive_scan_i32(const int32_t *in, int32_t *out, int64_t n, int32_t *tota
 int exclusive_scan_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *total, cudaStream_t s,
                        tw_patch *P);
 int build_tables(tw_patch *P);
+// q-point Gauss-Legendre rule (x then w, 2q doubles) on the current device,
+// computed once per process and device and kept until exit
+int gauss_rule(int q, cudaStream_t s, const double **out);
 int form_mass_launch(tw_patch *P, int precision, int64_t *row_ptr, int32_t *col, void *val,
                      cudaStream_t s);
 int rhs_launch(tw_patch *P, const tw_func *f, double *b, cudaStream_t s);

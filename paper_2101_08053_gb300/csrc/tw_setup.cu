@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 
 #include "tw_internal.cuh"
 
@@ -1159,6 +1160,31 @@ __global__ void k_is_cut(const uint8_t *es, int32_t *f, int64_t n) {
 // ---------------------------------------------------------------------------
 // host orchestration
 
+#define TW_GAUSS_DEVICES 64
+static std::mutex g_gauss_mu;
+static double *g_gauss[TW_GAUSS_DEVICES][65];
+
+int gauss_rule(int q, cudaStream_t s, const double **out) {
+  int dev = 0;
+  if (check_cuda(cudaGetDevice(&dev), "gauss_rule")) return TW_ECUDA;
+  if (q < 1 || q > 64 || dev < 0 || dev >= TW_GAUSS_DEVICES) {
+    set_error("gauss_rule: order %d or device %d out of range", q, dev);
+    return TW_EUNSUPPORTED;
+  }
+  std::lock_guard<std::mutex> lock(g_gauss_mu);
+  if (!g_gauss[dev][q]) {
+    double *d = nullptr;
+    if (check_cuda(cudaMalloc(&d, sizeof(double) * 2 * q), "gauss_rule: cudaMalloc")) return TW_ENOMEM;
+    k_gauss_nodes<<<1, 64, 0, s>>>(q, d, d + q);
+    TW_LAUNCH();
+    // other streams read the rule later: complete it now
+    if (check_cuda(cudaStreamSynchronize(s), "gauss_rule")) return TW_ECUDA;
+    g_gauss[dev][q] = d;
+  }
+  *out = g_gauss[dev][q];
+  return 0;
+}
+
 static int read_flag(tw_patch *P, const char *stage) {
   int f = 0;
   if (check_cuda(cudaMemcpyAsync(&f, P->flag, sizeof(int), cudaMemcpyDeviceToHost, P->stream),
@@ -1192,16 +1218,15 @@ int build_tables(tw_patch *P) {
   if (!counters || !tot64 || !tot32) return TW_ENOMEM;
   cudaMemsetAsync(counters, 0, 16 * sizeof(int32_t), st);
 
-  // Gauss rules (p+1 for elements, qc for cut pieces)
-  double *qgx = (double *)dalloc(P, sizeof(double) * P->qc);
-  double *qgw = (double *)dalloc(P, sizeof(double) * P->qc);
+  // Gauss rules (p+1 for elements, qc for cut pieces), cached per process
+  const double *er = nullptr, *qr = nullptr;
+  if ((rc = gauss_rule(p1, st, &er)) || (rc = gauss_rule(P->qc, st, &qr))) return rc;
   for (int d = 0; d < 2; d++) {
-    Dir &D = P->d[d];
-    k_gauss_nodes<<<1, 32, 0, st>>>(p1, D.gx, D.gw);
-    TW_LAUNCH();
+    P->d[d].gx = er;
+    P->d[d].gw = er + p1;
   }
-  k_gauss_nodes<<<1, 64, 0, st>>>(P->qc, qgx, qgw);
-  TW_LAUNCH();
+  P->qrule = qr;
+  const double *qgx = qr, *qgw = qr + P->qc;
 
   // WQ layout, basis tables, weights (Eq. 5)
   for (int d = 0; d < 2; d++) {
