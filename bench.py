@@ -334,6 +334,41 @@ def run_ours(args, rank, world, local_rank):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         e2e_ms = float(t.item())
 
+    # the reduced-precision forms against the plain FP64 GPU form: formation
+    # only (patch tables resident), serialised, relative Frobenius error
+    modes = {}
+    patches = [api.Patch(s_) for s_ in sp]
+    ref = []
+    for P, o in zip(patches, outs):
+        P.form_mass("fp64", out=o)
+        ref.append(o[2][:P.nnz].clone())
+    for mode in ("fp64", "fp32x2", "fp32"):
+        mo = [P.alloc_csr(mode) for P in patches]
+        for P, o in zip(patches, mo):
+            P.form_mass(mode, out=o)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for P, o in zip(patches, mo):
+                P.form_mass(mode, out=o)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        num = sum(float(torch.linalg.norm(o[2][:P.nnz].double() - r_) ** 2)
+                  for P, o, r_ in zip(patches, mo, ref))
+        den = sum(float(torch.linalg.norm(r_) ** 2) for r_ in ref)
+        ms_ = float(np.mean(ts))
+        modes[mode] = {"form_nnz_per_s": nnz_step / (ms_ * 1e-3), "form_ms": round(ms_, 3),
+                       "rel_frobenius_vs_fp64_gpu": math.sqrt(num / den)}
+        del mo
+    for P in patches:
+        P.close()
+
     # roofline of the dominant kernel (interior rows, FP64 DFMA-bound)
     flops = 0.0
     for s in sp:
@@ -353,7 +388,7 @@ def run_ours(args, rank, world, local_rank):
     return {
         "value": value, "ms": ms, "nnz_step": nnz_step, "infos": infos, "launches": launches,
         "clocks": clocks, "e2e_ms": e2e_ms, "h2d": h2d, "d2h": d2h, "stage_ms": stage_ms,
-        "stage_ms_batched": stage_ms_batched,
+        "stage_ms_batched": stage_ms_batched, "modes": modes,
         "roofline": {"bound": "alu", "kernel": "k_interior (interior rows, WQ + sum factorisation)",
                      "achieved": round(achieved, 4), "peak": peak, "unit": "TFLOP/s",
                      "frac": round(achieved / peak, 4), "traffic": None,
@@ -456,7 +491,8 @@ def main():
                         "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]},
                 "gpu_launches": r["launches"], "clocks": r["clocks"], "roofline": r["roofline"],
                 "cpu_baseline": cpu, "stage_ms_per_step_serial": r["stage_ms"],
-                "stage_ms_per_step_batched": r["stage_ms_batched"]}
+                "stage_ms_per_step_batched": r["stage_ms_batched"],
+                "precision_modes_formation_only": r["modes"]}
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()

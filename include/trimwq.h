@@ -58,7 +58,11 @@ extern "C" {
 #define TW_METHOD_NAIVE 3  /* WQ with c zeroed off S^r plus the cut rule: Table 1's negative control */
 /* precision of the contraction (tw_form_mass) */
 #define TW_PREC_FP64 0     /* val is double*                                     */
-#define TW_PREC_FP32 1     /* val is float*; tables rounded to FP32, FP32 FMA     */
+#define TW_PREC_FP32 1     /* val is float*; interior rows: tables rounded to FP32,
+                              FP32 FMA (cut rows in FP64, rounded on output)      */
+#define TW_PREC_FP32X2 2   /* val is double*; interior rows in split precision: FP64
+                              values as hi+lo FP32 pairs, error-free products and
+                              sums on the FP32 pipes (cut rows in FP64)           */
 /* target functions for the L2 projection (Sect. 4.2), evaluated at x(xi) */
 #define TW_FUNC_SPLINE 0   /* sum_k a_k N_k(xi): own tensor spline (knots/p/coef) */
 #define TW_FUNC_SINSIN 1   /* sin(a x) sin(b y), prm = a, b                       */
@@ -134,7 +138,7 @@ int tw_patch_info(const tw_patch *patch, int64_t *info16);
 
 /* Form the mass matrix (Eqs. 6-7) into caller-owned device CSR buffers:
  *   row_ptr[n_rows+1] (int64), col[nnz] (int32, active index, ascending per row),
- *   val[nnz] (double for TW_PREC_FP64, float for TW_PREC_FP32).
+ *   val[nnz] (double for TW_PREC_FP64 / TW_PREC_FP32X2, float for TW_PREC_FP32).
  * Rows and columns are the active (non-exterior) functions numbered by
  * ascending i2*n1 + i1; the pattern holds every active pair with
  * |i1-j1| <= p and |i2-j2| <= p.  The result is deterministic (each entry is

@@ -15,7 +15,7 @@ TRIM = {"none": 0, "circle": 1, "ellipse": 2, "bspline3": 3}
 GEOM = {"identity": 0, "spline": 1}
 COEF = {"one": 0, "detj": 1, "density": 2}
 METHOD = {"gauss": 0, "hybrid": 1, "dwq": 2, "naive": 3}
-PREC = {"fp64": 0, "fp32": 1}
+PREC = {"fp64": 0, "fp32": 1, "fp32x2": 2}
 FUNC = {"spline": 0, "sinsin": 1, "sincos": 2, "gauss": 3}
 ERRORS = {-1: "EINVAL", -2: "EUNSUPPORTED", -3: "ENOMEM", -4: "ECUDA", -5: "ENOCONV"}
 
@@ -213,7 +213,7 @@ class Patch:
 
     def alloc_csr(self, precision="fp64"):
         torch = _torch()
-        dt = torch.float64 if precision == "fp64" else torch.float32
+        dt = torch.float32 if precision == "fp32" else torch.float64
         rp = torch.empty(self.n_rows + 1, dtype=torch.int64, device="cuda")
         col = torch.empty(max(self.nnz, 1), dtype=torch.int32, device="cuda")
         val = torch.empty(max(self.nnz, 1), dtype=dt, device="cuda")

@@ -382,7 +382,7 @@ extern "C" int tw_form_mass(tw_patch *P, int precision, int64_t *row_ptr, int32_
     set_error("tw_form_mass: NULL argument");
     return TW_EINVAL;
   }
-  if (precision != TW_PREC_FP64 && precision != TW_PREC_FP32) {
+  if (precision != TW_PREC_FP64 && precision != TW_PREC_FP32 && precision != TW_PREC_FP32X2) {
     set_error("tw_form_mass: unknown precision %d", precision);
     return TW_EINVAL;
   }

@@ -119,10 +119,10 @@ __global__ void __launch_bounds__(256) k_interior(Dir A, Dir B, const double *__
 
 #define TW_RC 32
 
-template <int P>
+template <int P, typename OutT>
 __global__ void __launch_bounds__(256) k_cutrows(RowArgs a, const int32_t *__restrict__ rows,
                                                  int32_t *__restrict__ col,
-                                                 double *__restrict__ val) {
+                                                 OutT *__restrict__ val) {
   constexpr int W = 2 * P + 1, P1 = P + 1;
   __shared__ double acc[W * W];
   __shared__ double rx[2][TW_RC], rw[2][TW_RC], rb[2][TW_RC][W];
@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(256) k_cutrows(RowArgs a, const int32_t *__res
     if (ps < 0) continue;
     int r2 = t / W, q1 = t % W;
     int j1 = i1 - P + q1, j2 = i2 - P + r2;
-    val[base + ps] = acc[t];
+    val[base + ps] = (OutT)acc[t];
     col[base + ps] = a.act[j2 * n1 + j1];
   }
 }
@@ -345,11 +345,16 @@ __global__ void k_copy_i64(const int64_t *src, int64_t *dst, int64_t n) {
 }
 
 template <int P>
-static void launch_form(tw_patch *Pt, int64_t *rp, int32_t *col, double *val, cudaStream_t s) {
+static int launch_form(tw_patch *Pt, int precision, int64_t *rp, int32_t *col, void *valv,
+                       cudaStream_t s) {
   constexpr int T = 32;
   Dir &A = Pt->d[0];
   Dir &B = Pt->d[1];
-  if (Pt->method != TW_METHOD_GAUSS && Pt->n_interior > 0) {
+  double *val = (double *)valv;
+  if (Pt->method != TW_METHOD_GAUSS && Pt->n_interior > 0 && precision != TW_PREC_FP64) {
+    int rc = launch_interior32(Pt, precision, col, valv, s);
+    if (rc) return rc;
+  } else if (Pt->method != TW_METHOD_GAUSS && Pt->n_interior > 0) {
     dim3 grid((A.n + T - 1) / T, B.n);
     int ps = prof_start(s);
     k_interior<P, T><<<grid, 256, 0, s>>>(A, B, Pt->C, Pt->fstate, Pt->act, Pt->row_ptr, col, val);
@@ -389,31 +394,32 @@ static void launch_form(tw_patch *Pt, int64_t *rp, int32_t *col, double *val, cu
     ra.method = Pt->method;
     ra.flag = Pt->flag;
     int ps = prof_start(s);
-    k_cutrows<P><<<Pt->ncutrows, 256, 0, s>>>(ra, Pt->cutrows, col, val);
+    if (precision == TW_PREC_FP32)
+      k_cutrows<P, float><<<Pt->ncutrows, 256, 0, s>>>(ra, Pt->cutrows, col, (float *)valv);
+    else
+      k_cutrows<P, double><<<Pt->ncutrows, 256, 0, s>>>(ra, Pt->cutrows, col, val);
     prof_stop(ps, TW_STAGE_CUTROWS, s);
     TW_LAUNCH();
   }
+  return 0;
 }
 
 int form_mass_launch(tw_patch *P, int precision, int64_t *rp, int32_t *col, void *val,
                      cudaStream_t s) {
-  if (precision != TW_PREC_FP64) {
-    set_error("tw_form_mass: precision %d not available in this build", precision);
-    return TW_EUNSUPPORTED;
-  }
   int64_t n = P->n_rows + 1;
   k_copy_i64<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P->row_ptr, rp, n);
   TW_LAUNCH();
-  double *v = (double *)val;
+  int rc;
   switch (P->p) {
-    case 1: launch_form<1>(P, rp, col, v, s); break;
-    case 2: launch_form<2>(P, rp, col, v, s); break;
-    case 3: launch_form<3>(P, rp, col, v, s); break;
-    case 4: launch_form<4>(P, rp, col, v, s); break;
-    case 5: launch_form<5>(P, rp, col, v, s); break;
-    case 6: launch_form<6>(P, rp, col, v, s); break;
+    case 1: rc = launch_form<1>(P, precision, rp, col, val, s); break;
+    case 2: rc = launch_form<2>(P, precision, rp, col, val, s); break;
+    case 3: rc = launch_form<3>(P, precision, rp, col, val, s); break;
+    case 4: rc = launch_form<4>(P, precision, rp, col, val, s); break;
+    case 5: rc = launch_form<5>(P, precision, rp, col, val, s); break;
+    case 6: rc = launch_form<6>(P, precision, rp, col, val, s); break;
     default: return TW_EUNSUPPORTED;
   }
+  if (rc) return rc;
   return check_cuda(cudaGetLastError(), "tw_form_mass launch");
 }
 

@@ -657,6 +657,8 @@ struct tw_patch {
   double *dwq_B[2];  // ndisc x TW_LQMAX x (p+1): coarse basis values there
   int32_t *dwq_r[2]; // ndisc x p x 2: window point run of (function, side)
   double *gmat;      // ngslot x (p+1)^4 element matrices of the Gauss elements (or NULL)
+  float2 *Cf;        // c on the WQ grid as hi/lo FP32 pairs (created on first FP32 form)
+  float2 *Vf[2];     // weighted basis tables as hi/lo FP32 pairs
   int ndwqrows;
   // scratch
   int32_t *flag;     // error flags (device)
@@ -682,6 +684,7 @@ int build_tables(tw_patch *P);
 int gauss_rule(int q, cudaStream_t s, const double **out);
 int form_mass_launch(tw_patch *P, int precision, int64_t *row_ptr, int32_t *col, void *val,
                      cudaStream_t s);
+int launch_interior32(tw_patch *P, int precision, int32_t *col, void *val, cudaStream_t s);
 int rhs_launch(tw_patch *P, const tw_func *f, double *b, cudaStream_t s);
 int l2_project_run(tw_patch *P, const tw_func *f, const int64_t *rp, const int32_t *col,
                    const double *val, double *u, double tol, int maxit, int *iters,
