@@ -369,6 +369,14 @@ def run_ours(args, rank, world, local_rank):
     for P in patches:
         P.close()
 
+    # batched variant (config 4): 512 patches of seeded degree 2..6, 16..256
+    # elements per direction, ellipse or 8-point spline holes; tables built on
+    # the streams, then every matrix formed by one persistent launch replayed
+    # from a CUDA graph (tiles by the autotuner), FP64 and FP32
+    batched = None
+    if not args.no_batched:
+        batched = run_batched(api, torch, args, stream, streams, dev)
+
     # roofline of the dominant kernel (interior rows, FP64 DFMA-bound)
     flops = 0.0
     for s in sp:
@@ -388,7 +396,7 @@ def run_ours(args, rank, world, local_rank):
     return {
         "value": value, "ms": ms, "nnz_step": nnz_step, "infos": infos, "launches": launches,
         "clocks": clocks, "e2e_ms": e2e_ms, "h2d": h2d, "d2h": d2h, "stage_ms": stage_ms,
-        "stage_ms_batched": stage_ms_batched, "modes": modes,
+        "stage_ms_batched": stage_ms_batched, "modes": modes, "batched": batched,
         "roofline": {"bound": "alu", "kernel": "k_interior (interior rows, WQ + sum factorisation)",
                      "achieved": round(achieved, 4), "peak": peak, "unit": "TFLOP/s",
                      "frac": round(achieved / peak, 4), "traffic": None,
@@ -398,6 +406,57 @@ def run_ours(args, rank, world, local_rank):
                                "patches)",
                      "peak_source": "FP64 rate listed by the profiling recipe (not measured)"},
     }
+
+
+def run_batched(api, torch, args, stream, streams, dev):
+    rng = np.random.default_rng(synth.BASE_SEED + 4)
+    specs4 = [synth.config4_patch(rng, method="hybrid") for _ in range(args.batched_patches)]
+    patches = [None] * len(specs4)
+    ns = len(streams)
+
+    def build(k):
+        torch.cuda.set_device(dev)
+        with torch.cuda.stream(streams[k]):
+            for idx in range(k, len(specs4), ns):
+                patches[idx] = api.Patch(specs4[idx])
+
+    t0 = time.perf_counter()
+    th = [threading.Thread(target=build, args=(k,)) for k in range(ns)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    nnz = sum(P.nnz for P in patches)
+    res = {"patches": len(patches), "nnz": nnz, "setup_s_4_streams": round(setup_s, 3),
+           "p_hist": {str(p): sum(1 for P in patches if P.p == p) for p in range(2, 7)}}
+    for mode in ("fp64", "fp32"):
+        outs = [P.alloc_csr(mode) for P in patches]
+        t0 = time.perf_counter()
+        B = api.Batch(patches, outs, mode)
+        create_s = time.perf_counter() - t0
+        B.run()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            B.run()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ms = float(np.mean(ts))
+        res[mode] = {"form_nnz_per_s": nnz / (ms * 1e-3), "form_ms": round(ms, 3),
+                     "batch_create_s": round(create_s, 3), "items": B.items,
+                     "persistent_blocks": B.blocks,
+                     "tiles": {str(p): t for p, t in B.tiles.items() if any(P.p == p for P in patches)}}
+        B.close()
+        del outs
+    for P in patches:
+        P.close()
+    return res
 
 
 def oracle_sample(seconds_budget=None, rows_per_patch=300, seed=0):
@@ -433,6 +492,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--case", default=None, help="p,nel,method: one patch of the sweep only")
     ap.add_argument("--streams", type=int, default=4, help="concurrent streams for the batch")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 512-patch batched variant")
+    ap.add_argument("--batched-patches", type=int, default=512)
     args = ap.parse_args()
     if args.case:
         select_case(args.case)
@@ -492,7 +553,8 @@ def main():
                 "gpu_launches": r["launches"], "clocks": r["clocks"], "roofline": r["roofline"],
                 "cpu_baseline": cpu, "stage_ms_per_step_serial": r["stage_ms"],
                 "stage_ms_per_step_batched": r["stage_ms_batched"],
-                "precision_modes_formation_only": r["modes"]}
+                "precision_modes_formation_only": r["modes"],
+                "batched_config4": r["batched"]}
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -204,6 +204,25 @@ int tw_states(const tw_patch *patch, uint8_t *estate, uint8_t *fstate, int32_t *
 int tw_patch_table(const tw_patch *patch, int which, void *dst, int64_t cap, int64_t *count,
                    void *stream);
 
+/* Batched formation (many patches, one persistent launch, CUDA graph).
+ * tw_batch_create takes n existing patches (which must outlive the batch) and
+ * their caller-owned device CSR buffers (sized as for tw_form_mass), picks the
+ * interior-row tile for each degree present by timing candidate tiles on these
+ * patches (cached per device, precision and degree), builds a work list of
+ * interior tiles, cut rows and row-pointer copies ordered by estimated cost,
+ * and captures one graph: a memset of the work counter and one persistent
+ * kernel whose blocks take items until none are left.  Synchronises `stream`.
+ * tw_batch_run replays the graph on `stream` (asynchronous); the CSRs equal
+ * those of tw_form_mass bit for bit.
+ * tw_batch_info: [0] patches [1] items [2] persistent blocks [3] dynamic
+ * shared memory per block [4..9] interior tile chosen for p = 1..6. */
+typedef struct tw_batch tw_batch;
+int tw_batch_create(tw_patch *const *patches, int n, int precision, int64_t *const *row_ptr,
+                    int32_t *const *col, void *const *val, void *stream, tw_batch **out);
+int tw_batch_run(tw_batch *batch, void *stream);
+int tw_batch_info(const tw_batch *batch, int64_t *info10);
+int tw_batch_destroy(tw_batch *batch);
+
 /* Number of kernels this library has launched in this process. */
 int64_t tw_launch_count(void);
 

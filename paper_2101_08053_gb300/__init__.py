@@ -7,4 +7,4 @@ quadrature for cut basis functions, and the L2 projection built on the matrix.
 The compute path is the C-ABI library libtrimwq.so (include/trimwq.h); this
 package only builds it and marshals arguments to it.
 """
-from .api import Patch, TWError, launch_count, load  # noqa: F401
+from .api import Batch, Patch, TWError, launch_count, load  # noqa: F401

@@ -85,6 +85,12 @@ def load(build: bool = True):
     L.tw_states.argtypes = [vp, vp, vp, vp, vp]
     L.tw_patch_table.argtypes = [vp, C.c_int, vp, C.c_int64, i64p, vp]
     L.tw_launch_count.restype = C.c_int64
+    L.tw_batch_create.argtypes = [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.POINTER(C.c_void_p),
+                                  C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), vp,
+                                  C.POINTER(C.c_void_p)]
+    L.tw_batch_run.argtypes = [vp, vp]
+    L.tw_batch_info.argtypes = [vp, i64p]
+    L.tw_batch_destroy.argtypes = [vp]
     L.tw_profile_enable.argtypes = [C.c_int]
     L.tw_profile_read.argtypes = [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
     L.tw_last_error.restype = C.c_char_p
@@ -271,6 +277,44 @@ class Patch:
         _check(L.tw_patch_table(self._h, which, C.c_void_p(t.data_ptr()), n.value, C.byref(n),
                                 _stream(stream)))
         return t[:n.value]
+
+
+class Batch:
+    """tw_batch_create / tw_batch_run: many patches formed by one persistent
+    launch replayed from a CUDA graph.  `outs` are (row_ptr, col, val) device
+    tensors per patch (Patch.alloc_csr); the patches must outlive the batch."""
+
+    def __init__(self, patches, outs, precision="fp64", stream=None):
+        L = load()
+        n = len(patches)
+        arr = lambda vals: (C.c_void_p * n)(*vals)
+        self._keep = (patches, outs)
+        hp = arr([P._h.value for P in patches])
+        rp = arr([o[0].data_ptr() for o in outs])
+        col = arr([o[1].data_ptr() for o in outs])
+        val = arr([o[2].data_ptr() for o in outs])
+        h = C.c_void_p()
+        _check(L.tw_batch_create(hp, n, PREC[precision], rp, col, val, _stream(stream),
+                                 C.byref(h)))
+        self._h = h
+        info = np.zeros(10, dtype=np.int64)
+        _check(L.tw_batch_info(self._h, info.ctypes.data_as(C.POINTER(C.c_int64))))
+        self.n, self.items, self.blocks, self.smem = [int(v) for v in info[:4]]
+        self.tiles = {p: int(info[3 + p]) for p in range(1, 7)}
+
+    def run(self, stream=None):
+        _check(load().tw_batch_run(self._h, _stream(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().tw_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def launch_count() -> int:

@@ -11,7 +11,7 @@
 //                   as FP64.
 // The tables (V of both directions, c on the WQ grid) are split once per
 // patch, on first use.  Cut rows always run in FP64 (k_cutrows).
-#include "tw_internal.cuh"
+#include "tw_bodies.cuh"
 
 namespace tw {
 
@@ -26,20 +26,6 @@ __global__ void k_split_table(const double *src, float2 *dst, int64_t n) {
   if (i < n) dst[i] = split_f64(src[i]);
 }
 
-// s = (sh, sl) += a * b, a and b pairs; products and sums error-free in the
-// leading parts (__fmul_rn / __fadd_rn are never contracted into FMAs)
-__device__ __forceinline__ void df_fma(float2 a, float2 b, float &sh, float &sl) {
-  float p = __fmul_rn(a.x, b.x);
-  float e = fmaf(a.x, b.x, -p);
-  e = fmaf(a.x, b.y, e);
-  e = fmaf(a.y, b.x, e);
-  float t = __fadd_rn(sh, p);
-  float bp = __fadd_rn(t, -sh);
-  float err = __fadd_rn(__fadd_rn(sh, -__fadd_rn(t, -bp)), __fadd_rn(p, -bp));
-  sh = t;
-  sl = __fadd_rn(sl, __fadd_rn(err, e));
-}
-
 template <int P, int T, bool SPLIT>
 __global__ void __launch_bounds__(256) k_interior32(Dir A, Dir B, const float2 *__restrict__ Cf,
                                                     const float2 *__restrict__ V1f,
@@ -48,104 +34,13 @@ __global__ void __launch_bounds__(256) k_interior32(Dir A, Dir B, const float2 *
                                                     const int32_t *__restrict__ act,
                                                     const int64_t *__restrict__ rp,
                                                     int32_t *__restrict__ col, void *__restrict__ valv) {
-  constexpr int W = 2 * P + 1;
-  constexpr int KMAX = (2 * T + 4 * P + 4) | 1;
-  __shared__ float2 Y[W * KMAX];
-  __shared__ float2 V2s[TW_QMAX * W];
-  __shared__ int cr2[W];
-  __shared__ int anyint;
-  const int i2 = blockIdx.y;
-  const int i1a = blockIdx.x * T;
-  const int i1b = min(A.n, i1a + T);
-  const int n1 = A.n;
-  if (threadIdx.x == 0) anyint = 0;
-  __syncthreads();
-  for (int t = threadIdx.x; t < i1b - i1a; t += blockDim.x)
-    if (fstate[i2 * n1 + i1a + t] == TW_FUNC_INTERIOR) anyint = 1;
-  __syncthreads();
-  if (!anyint) return;
-  const int kA = A.qbeg[i1a];
-  const int kB = A.qbeg[i1b - 1] + A.qcnt[i1b - 1];
-  const int K = kB - kA;
-  const int qb2 = B.qbeg[i2], qc2 = B.qcnt[i2];
-  for (int t = threadIdx.x; t < qc2 * W; t += blockDim.x) V2s[t] = V2f[(size_t)i2 * B.qmax * W + t];
-  for (int t = threadIdx.x; t < W; t += blockDim.x) cr2[t] = B.crange[i2 * W + t];
-  __syncthreads();
-  // stage 1: Y[r2][k1] = sum_{k2} V2[i2][k2][r2] c[k2][k1]
-  for (int idx = threadIdx.x; idx < W * K; idx += blockDim.x) {
-    const int r2 = idx / K, kk = idx - r2 * K;
-    const int lo = cr2[r2] & 0xffff, hi = cr2[r2] >> 16;
-    const float2 *cc = Cf + (size_t)(qb2 + lo) * A.nq + kA + kk;
-    float sh = 0.f, sl = 0.f;
-    for (int c2 = lo; c2 < hi; c2++, cc += A.nq) {
-      if (SPLIT) df_fma(V2s[c2 * W + r2], *cc, sh, sl);
-      else sh = fmaf(V2s[c2 * W + r2].x, cc->x, sh);
-    }
-    Y[r2 * KMAX + kk] = make_float2(sh, sl);
-  }
-  __syncthreads();
-  // stage 2 (point-major for rows away from the end elements)
-  const int lo2 = max(0, i2 - P);
-  const int NR = (i1b - i1a) * W;
-  double *vald = (double *)valv;
-  float *valf = (float *)valv;
-  for (int idx = threadIdx.x; idx < NR; idx += blockDim.x) {
-    const int t = idx / W, r2 = idx - t * W;
-    const int i1 = i1a + t;
-    const int g = i2 * n1 + i1;
-    const int j2 = i2 - P + r2;
-    if (fstate[g] != TW_FUNC_INTERIOR || j2 < 0 || j2 >= B.n) continue;
-    const float2 *y = Y + r2 * KMAX + (A.qbeg[i1] - kA);
-    const float2 *v = V1f + ((size_t)i1 * A.qmax) * W;
-    const int64_t rowbase = rp[act[g]];
-    if (i1 >= P + 1 && i1 <= A.nel - 2) {
-      float ah[W], al[W];
-#pragma unroll
-      for (int r = 0; r < W; r++) ah[r] = al[r] = 0.f;
-#pragma unroll
-      for (int el = 0; el <= P; el++) {
-#pragma unroll
-        for (int pt = 0; pt < 2; pt++) {
-          const int c1 = 2 * el + pt;
-          const float2 yv = y[c1];
-#pragma unroll
-          for (int a = 0; a <= P; a++) {
-            if (SPLIT) df_fma(v[c1 * W + el + a], yv, ah[el + a], al[el + a]);
-            else ah[el + a] = fmaf(v[c1 * W + el + a].x, yv.x, ah[el + a]);
-          }
-        }
-      }
-      const int64_t base = rowbase + (int64_t)(j2 - lo2) * W;
-      const int32_t *arow = act + j2 * n1 + (i1 - P);
-#pragma unroll
-      for (int r = 0; r < W; r++) {
-        if (SPLIT) vald[base + r] = (double)ah[r] + (double)al[r];
-        else valf[base + r] = ah[r];
-        col[base + r] = arow[r];
-      }
-    } else {
-      const int lo1 = max(0, i1 - P), w1 = min(n1 - 1, i1 + P) - lo1 + 1;
-      for (int r1 = 0; r1 < W; r1++) {
-        const int j1 = i1 - P + r1;
-        if (j1 < 0 || j1 >= n1) continue;
-        const int cr = A.crange[i1 * W + r1];
-        const int lo = cr & 0xffff, hi = cr >> 16;
-        float sh = 0.f, sl = 0.f;
-        for (int c1 = lo; c1 < hi; c1++) {
-          if (SPLIT) df_fma(v[c1 * W + r1], y[c1], sh, sl);
-          else sh = fmaf(v[c1 * W + r1].x, y[c1].x, sh);
-        }
-        const int64_t pos = rowbase + (int64_t)(j2 - lo2) * w1 + (j1 - lo1);
-        if (SPLIT) vald[pos] = (double)sh + (double)sl;
-        else valf[pos] = sh;
-        col[pos] = act[j2 * n1 + j1];
-      }
-    }
-  }
+  __shared__ __align__(16) char smem[interior32_smem(P, T)];
+  interior_tile32<P, SPLIT>(A, B, Cf, V1f, V2f, fstate, act, rp, col, valv, blockIdx.y,
+                            blockIdx.x * T, T, smem);
 }
 
 // split the patch's tables on first use (patch-owned)
-static int ensure_split_tables(tw_patch *P, cudaStream_t s) {
+int ensure_split_tables(tw_patch *P, cudaStream_t s) {
   if (P->Cf) return 0;
   Dir &A = P->d[0];
   Dir &B = P->d[1];
