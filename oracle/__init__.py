@@ -114,6 +114,9 @@ def lib():
         L.or_l2_error.argtypes = [C.c_void_p, PD, C.POINTER(Func), PD]
         L.or_visible_area.restype = C.c_double
         L.or_visible_area.argtypes = [C.c_void_p]
+        L.or_loss.restype = C.c_double
+        L.or_loss.argtypes = [C.c_void_p, PD, C.POINTER(Func), PD]
+        L.or_density_grad.argtypes = [C.c_void_p, PD, PD, C.POINTER(Func), PD]
         _lib = L
     return _lib
 
@@ -362,3 +365,22 @@ class Patch:
 
     def visible_area(self):
         return lib().or_visible_area(self._h)
+
+    def loss(self, u, g):
+        """(L, dL/du) of reading R12."""
+        keep = []
+        gs = make_func(g, keep)
+        u = _f64(u)
+        dl = np.zeros(self.n_rows)
+        L = lib().or_loss(self._h, _pd(u), C.byref(gs), _pd(dl))
+        return L, dl
+
+    def density_grad(self, u, lam, g):
+        keep = []
+        gs = make_func(g, keep)
+        c = self.spec["coef"]
+        m1 = len(c["knots"][0]) - c["p"] - 1
+        m2 = len(c["knots"][1]) - c["p"] - 1
+        out = np.zeros(m1 * m2)
+        lib().or_density_grad(self._h, _pd(_f64(u)), _pd(_f64(lam)), C.byref(gs), _pd(out))
+        return out.reshape(m2, m1)

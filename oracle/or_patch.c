@@ -16,6 +16,11 @@
  *   cut row, naive WQ       tensor WQ rule with c = 0 off S^r plus the cut rule
  *                           (the negative control of Table 1)
  *   method GAUSS            element Gauss for every row (the paper's reference)
+ * Differentiation with respect to a density spline rho = sum_k d_k N_k in
+ * c = rho det J (reading R12): or_loss gives L = sum_q omega_q detJ (u_h - g)^2
+ * over Omega^v and dL/du; or_density_grad gives dL/dd_k for u and the adjoint
+ * lambda = M_s^{-1} dL/du by walking every row's rule point by point, with c
+ * replaced by N_k det J (each rule is linear in c).
  * No sum factorisation, blocking or reordering is applied here: the point of
  * the oracle is that each step can be checked by eye against the paper.
  */
@@ -53,6 +58,7 @@ typedef struct {
 typedef struct {
   double x[2];
   double wc; /* weight (with the test function folded in) times c */
+  double w;  /* the same weight without c (0 where c is masked)   */
   int e[2];
   double bv[2][MAXP1];
 } rpoint;
@@ -690,6 +696,7 @@ static void add_gauss_elem(or_patch *P, int i1, int i2, int e1, int e2, rbuf *R)
       for (int b = 0; b < p2; b++) r->bv[1][b] = v2[b];
       double w = A->gw[g1] * 0.5 * h1 * B->gw[g2] * 0.5 * h2;
       r->wc = w * v1[i1 - e1] * v2[i2 - e2] * c[g2 * p1 + g1];
+      r->w = w * v1[i1 - e1] * v2[i2 - e2];
     }
 }
 
@@ -705,6 +712,7 @@ static void add_cut_elem(or_patch *P, int i1, int i2, int e1, int e2, rbuf *R) {
     basis_at(A, e1, r->x[0], r->bv[0], NULL);
     basis_at(B, e2, r->x[1], r->bv[1], NULL);
     r->wc = P->cut_pts[3 * k + 2] * r->bv[0][i1 - e1] * r->bv[1][i2 - e2] * P->cut_c[k];
+    r->w = P->cut_pts[3 * k + 2] * r->bv[0][i1 - e1] * r->bv[1][i2 - e2];
   }
 }
 
@@ -724,9 +732,9 @@ static int row_rule(or_patch *P, int g, rbuf *R) {
       for (int k1 = A->qlo[i1]; k1 <= A->qhi[i1]; k1++) {
         double w1 = A->W[(size_t)i1 * A->nq + k1];
         double c = P->C[(size_t)k2 * A->nq + k1];
-        if (kind == ROW_NAIVE &&
-            P->estate[B->qel[k2] * A->nel + A->qel[k1]] != OR_ELEM_REGULAR)
-          c = 0.0;
+        int masked = kind == ROW_NAIVE &&
+                     P->estate[B->qel[k2] * A->nel + A->qel[k1]] != OR_ELEM_REGULAR;
+        if (masked) c = 0.0;
         rpoint *r = rnew(R);
         r->x[0] = A->xq[k1];
         r->x[1] = B->xq[k2];
@@ -735,6 +743,7 @@ static int row_rule(or_patch *P, int g, rbuf *R) {
         for (int a = 0; a < p1; a++) r->bv[0][a] = A->Bv[(size_t)k1 * p1 + a];
         for (int b = 0; b < p2; b++) r->bv[1][b] = B->Bv[(size_t)k2 * p2 + b];
         r->wc = w1 * w2 * c;
+        r->w = masked ? 0.0 : w1 * w2;
       }
     }
     if (kind == ROW_NAIVE) {
@@ -779,6 +788,7 @@ static int row_rule(or_patch *P, int g, rbuf *R) {
         basis_at(B, r->e[1], r->x[1], r->bv[1], d2);
         double c = coef_from(P, r->x[0], r->x[1], r->e[0], r->bv[0], d1, r->e[1], r->bv[1], d2);
         r->wc = rp[0][2 * a + 1] * rp[1][2 * b + 1] * c;
+        r->w = rp[0][2 * a + 1] * rp[1][2 * b + 1];
       }
     free(rp[0]);
     free(rp[1]);
@@ -1112,4 +1122,122 @@ double or_visible_area(const or_patch *P) {
         for (int64_t k = P->cut_off[e]; k < P->cut_off[e + 1]; k++) s += P->cut_pts[3 * k + 2];
     }
   return s;
+}
+
+/* ------------------------------------------------------------------ */
+/* differentiation of the L2 projection w.r.t. the density (reading R12) */
+
+static double detj_at(const or_patch *P, int e1, const double *v1, const double *d1, int e2,
+                      const double *v2, const double *d2) {
+  if (P->d.geom_kind != OR_GEOM_SPLINE) return 1.0;
+  int n1 = P->D[0].n;
+  double xa = 0, xb = 0, ya = 0, yb = 0;
+  for (int b = 0; b <= P->D[1].p; b++)
+    for (int a = 0; a <= P->D[0].p; a++) {
+      const double *pt = P->d.geom_ctrl + 2 * ((size_t)(e2 + b) * n1 + (e1 + a));
+      xa += pt[0] * d1[a] * v2[b];
+      ya += pt[1] * d1[a] * v2[b];
+      xb += pt[0] * v1[a] * d2[b];
+      yb += pt[1] * v1[a] * d2[b];
+    }
+  return xa * yb - xb * ya;
+}
+
+/* spline value sum_j a_j B_j(x) over the active functions j */
+static double active_spline(const or_patch *P, const double *a, int e1, const double *v1, int e2,
+                            const double *v2) {
+  const dirdata *A = &P->D[0];
+  double s = 0.0;
+  for (int b = 0; b <= P->D[1].p; b++)
+    for (int c = 0; c <= A->p; c++) {
+      int32_t r = P->act[(e2 + b) * A->n + (e1 + c)];
+      if (r >= 0) s += a[r] * v1[c] * v2[b];
+    }
+  return s;
+}
+
+/* L = sum_q omega_q detJ (u_h - g)^2 over Omega^v: element Gauss (p+1 per
+ * direction) on regular elements, the cut rule on cut elements; and
+ * dL/du_j = 2 sum_q omega_q detJ (u_h - g) B_j. */
+double or_loss(const or_patch *Pc, const double *u, const or_func *g, double *dLdu) {
+  or_patch *P = (or_patch *)Pc;
+  const dirdata *A = &P->D[0], *B = &P->D[1];
+  int p1 = A->p + 1, p2 = B->p + 1;
+  double L = 0.0;
+  for (int64_t r = 0; r < P->nrows; r++) dLdu[r] = 0.0;
+  for (int e2 = 0; e2 < B->nel; e2++)
+    for (int e1 = 0; e1 < A->nel; e1++) {
+      int e = e2 * A->nel + e1;
+      uint8_t st = P->estate[e];
+      if (st == OR_ELEM_INVISIBLE) continue;
+      int np = st == OR_ELEM_REGULAR ? p1 * p2 : (int)(P->cut_off[e + 1] - P->cut_off[e]);
+      for (int q = 0; q < np; q++) {
+        double x[2], om;
+        if (st == OR_ELEM_REGULAR) {
+          int g1 = q % p1, g2 = q / p1;
+          double h1 = A->bp[e1 + 1] - A->bp[e1], h2 = B->bp[e2 + 1] - B->bp[e2];
+          x[0] = A->bp[e1] + h1 * 0.5 * (A->gx[g1] + 1.0);
+          x[1] = B->bp[e2] + h2 * 0.5 * (B->gx[g2] + 1.0);
+          om = A->gw[g1] * 0.5 * h1 * B->gw[g2] * 0.5 * h2;
+        } else {
+          int64_t k = P->cut_off[e] + q;
+          x[0] = P->cut_pts[3 * k];
+          x[1] = P->cut_pts[3 * k + 1];
+          om = P->cut_pts[3 * k + 2];
+        }
+        double v1[MAXP1], d1[MAXP1], v2[MAXP1], d2[MAXP1], X[2];
+        basis_at(A, e1, x[0], v1, d1);
+        basis_at(B, e2, x[1], v2, d2);
+        double dj = detj_at(P, e1, v1, d1, e2, v2, d2);
+        phys_from(P, x[0], x[1], e1, v1, e2, v2, X);
+        double res = active_spline(P, u, e1, v1, e2, v2) - func_eval(g, x, X);
+        L += om * dj * res * res;
+        for (int b = 0; b < p2; b++)
+          for (int a = 0; a < p1; a++) {
+            int32_t r = P->act[(e2 + b) * A->n + (e1 + a)];
+            if (r >= 0) dLdu[r] += 2.0 * om * dj * res * v1[a] * v2[b];
+          }
+      }
+    }
+  return L;
+}
+
+/* dL/dd_k = lambda^T (db/dd_k - dM_s/dd_k u) with M_s lambda = dL/du:
+ * sum over rows i and their rule points q of w_q detJ N_k(x_q)
+ * [lambda_i g - lambda_i U / 2 - u_i Lambda / 2](x_q), U = sum u_j B_j and
+ * Lambda = sum lambda_j B_j over the active j, w_q the row's weight without c. */
+void or_density_grad(const or_patch *Pc, const double *u, const double *lam, const or_func *g,
+                     double *grad) {
+  or_patch *P = (or_patch *)Pc;
+  const dirdata *A = &P->D[0], *B = &P->D[1];
+  const or_desc *d = &P->d;
+  int m1 = d->dens_nknots[0] - d->dens_p[0] - 1, m2 = d->dens_nknots[1] - d->dens_p[1] - 1;
+  for (int k = 0; k < m1 * m2; k++) grad[k] = 0.0;
+  rbuf R = {0};
+  for (int64_t row = 0; row < P->nrows; row++) {
+    int gi = (int)P->rowg[row];
+    row_rule(P, gi, &R);
+    for (int q = 0; q < R.n; q++) {
+      rpoint *r = &R.v[q];
+      if (r->w == 0.0) continue;
+      double v1[MAXP1], d1[MAXP1], v2[MAXP1], d2[MAXP1], X[2];
+      basis_at(A, r->e[0], r->x[0], v1, d1);
+      basis_at(B, r->e[1], r->x[1], v2, d2);
+      double dj = detj_at(P, r->e[0], v1, d1, r->e[1], v2, d2);
+      phys_from(P, r->x[0], r->x[1], r->e[0], v1, r->e[1], v2, X);
+      double U = active_spline(P, u, r->e[0], v1, r->e[1], v2);
+      double Lm = active_spline(P, lam, r->e[0], v1, r->e[1], v2);
+      double h = lam[row] * func_eval(g, r->x, X) - 0.5 * lam[row] * U - 0.5 * u[row] * Lm;
+      double wh = r->w * dj * h;
+      for (int k2 = 0; k2 < m2; k2++) {
+        double b2 = or_bspline(d->dens_knots[1], d->dens_nknots[1], d->dens_p[1], k2, r->x[1]);
+        if (b2 == 0.0) continue;
+        for (int k1 = 0; k1 < m1; k1++) {
+          double b1 = or_bspline(d->dens_knots[0], d->dens_nknots[0], d->dens_p[0], k1, r->x[0]);
+          if (b1 != 0.0) grad[k2 * m1 + k1] += wh * b1 * b2;
+        }
+      }
+    }
+  }
+  free(R.v);
 }

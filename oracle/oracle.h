@@ -140,5 +140,11 @@ int or_cg(const or_patch *P, const int64_t *row_ptr, const int32_t *col,
 double or_l2_error(const or_patch *P, const double *u, const or_func *f,
                    double *fnorm);
 double or_visible_area(const or_patch *P);
+/* reading R12: loss sum_q omega_q detJ (u_h - g)^2 and its gradient in u */
+double or_loss(const or_patch *P, const double *u, const or_func *g, double *dLdu);
+/* gradient of the loss w.r.t. the density coefficients, given u and the
+ * adjoint lambda = M_s^{-1} dL/du */
+void or_density_grad(const or_patch *P, const double *u, const double *lam, const or_func *g,
+                     double *grad);
 
 #endif
