@@ -376,6 +376,9 @@ def run_ours(args, rank, world, local_rank):
     batched = None
     if not args.no_batched:
         batched = run_batched(api, torch, args, stream, streams, dev)
+    adjoint = None
+    if not args.no_adjoint:
+        adjoint = run_adjoint(api, torch, args, stream)
 
     # roofline of the dominant kernel (interior rows, FP64 DFMA-bound)
     flops = 0.0
@@ -397,6 +400,7 @@ def run_ours(args, rank, world, local_rank):
         "value": value, "ms": ms, "nnz_step": nnz_step, "infos": infos, "launches": launches,
         "clocks": clocks, "e2e_ms": e2e_ms, "h2d": h2d, "d2h": d2h, "stage_ms": stage_ms,
         "stage_ms_batched": stage_ms_batched, "modes": modes, "batched": batched,
+        "adjoint": adjoint,
         "roofline": {"bound": "alu", "kernel": "k_interior (interior rows, WQ + sum factorisation)",
                      "achieved": round(achieved, 4), "peak": peak, "unit": "TFLOP/s",
                      "frac": round(achieved / peak, 4), "traffic": None,
@@ -459,6 +463,66 @@ def run_batched(api, torch, args, stream, streams, dev):
     return res
 
 
+def run_adjoint(api, torch, args, stream):
+    """Differentiation workload: 256^2 elements, p = 3, circular hole, density
+    spline of degree 2 with 32 x 32 coefficients (c = rho); loss of projecting
+    a Gaussian bump g onto the trimmed space, gradient w.r.t. the 1024 density
+    coefficients.  Forward = patch set-up + formation + CG + loss; backward =
+    adjoint CG + gradient kernels."""
+    spec = synth.config5()
+    g = synth.func_gauss(8.0, 0.3, 0.7)
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1)
+
+    api.profile_enable(True)
+    for _ in range(max(1, args.warmup)):
+        P = api.Patch(spec)
+        csr = P.form_mass("fp64")
+        u, _, _ = P.l2_project(g, csr, tol=1e-12)
+        L, dl = P.loss(u, g)
+        P.l2_project_adjoint(g, csr, dl, u, tol=1e-12)
+        P.close()
+    torch.cuda.synchronize()
+    for st in ("loss", "adjoint", "cg"):
+        api.profile_read(st)
+    acc = {"setup_form": [], "project": [], "loss": [], "adjoint": []}
+    its = []
+    for _ in range(args.steps):
+        def mk():
+            Q = api.Patch(spec)
+            return Q, Q.form_mass("fp64")
+        (P, csr), t_sf = timed(mk)
+        (u, it, _), t_pr = timed(lambda: P.l2_project(g, csr, tol=1e-12))
+        (L, dl), t_lo = timed(lambda: P.loss(u, g))
+        (gr, lam, it2, _), t_ad = timed(lambda: P.l2_project_adjoint(g, csr, dl, u, tol=1e-12))
+        its.append((it, it2))
+        for k, t in zip(acc, (t_sf, t_pr, t_lo, t_ad)):
+            acc[k].append(t)
+        P.close()
+    cg_ms, cg_n = api.profile_read("cg")
+    gr_ms, gr_n = api.profile_read("adjoint")
+    lo_ms, lo_n = api.profile_read("loss")
+    api.profile_enable(False)
+    n = max(1, args.steps)
+    res = {k: round(float(np.mean(v)), 3) for k, v in acc.items()}
+    return {"workload": "256x256 elements, p = 3, circle r = 0.25, density q = 2, 32 x 32 "
+                        "coefficients; g = Gaussian bump",
+            "ms": res, "forward_ms": round(res["setup_form"] + res["project"] + res["loss"], 3),
+            "backward_ms": res["adjoint"],
+            "gradient_kernels_ms": round(gr_ms / n, 3), "loss_kernels_ms": round(lo_ms / n, 3),
+            "cg_ms_forward_plus_adjoint": round(cg_ms / n, 3),
+            "cg_iterations_forward_adjoint": list(its[-1]), "n_coefficients": 1024}
+
+
 def oracle_sample(seconds_budget=None, rows_per_patch=300, seed=0):
     """Oracle time for the whole workload, extrapolated from full set-up plus a
     seeded sample of rows per patch (single thread)."""
@@ -494,6 +558,8 @@ def main():
     ap.add_argument("--streams", type=int, default=4, help="concurrent streams for the batch")
     ap.add_argument("--no-batched", action="store_true", help="skip the 512-patch batched variant")
     ap.add_argument("--batched-patches", type=int, default=512)
+    ap.add_argument("--no-adjoint", action="store_true",
+                    help="skip the density-gradient (adjoint) section")
     args = ap.parse_args()
     if args.case:
         select_case(args.case)
@@ -554,7 +620,7 @@ def main():
                 "cpu_baseline": cpu, "stage_ms_per_step_serial": r["stage_ms"],
                 "stage_ms_per_step_batched": r["stage_ms_batched"],
                 "precision_modes_formation_only": r["modes"],
-                "batched_config4": r["batched"]}
+                "batched_config4": r["batched"], "adjoint_config5": r["adjoint"]}
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()

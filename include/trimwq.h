@@ -181,6 +181,33 @@ int tw_l2_project(tw_patch *patch, const tw_func *f, const int64_t *row_ptr, con
                   const double *val, double *u, double tol, int maxit, int *iters,
                   double *relres, void *stream);
 
+/* Differentiation of the L2 projection with respect to the density (Sect. 4.2's
+ * projection with c = rho det J, rho = sum_k d_k N_k the patch's density
+ * spline, TW_COEF_DENSITY).  The loss compares the projection u_h of f with a
+ * target g on the visible part of the patch:
+ *   L = sum_q omega_q detJ(x_q) (u_h(x_q) - g(x_q))^2
+ * over element Gauss (p+1 points per direction) on regular elements and the
+ * cut rule (Sect. 3.1) on cut elements.
+ *
+ * tw_loss: *loss (device, one double) and dLdu[n_rows] (device) for the
+ * coefficients u[n_rows] (device).  Asynchronous; deterministic. */
+int tw_loss(tw_patch *patch, const tw_func *g, const double *u, double *loss, double *dLdu,
+            void *stream);
+
+/* tw_l2_project_adjoint: given u = M_s^{-1} b(f) from tw_l2_project (same CSR,
+ * FP64) and dL/du, solves M_s lambda = dL/du by the projection's CG (same tol,
+ * maxit semantics; *iters, *relres host outputs) and returns
+ *   grad[k2 * m1 + k1] = dL/dd_k = lambda^T db/dd_k
+ *                        - (lambda^T dM/dd_k u + u^T dM/dd_k lambda) / 2
+ * (m1 x m2 density coefficients, k1 fastest), computed from every row's own
+ * quadrature rule.  lam[n_rows] and grad are device outputs.  The patch must
+ * have been created with TW_COEF_DENSITY (else TW_EINVAL).  Synchronises
+ * `stream`; TW_ENOCONV if the adjoint CG does not converge.  Deterministic. */
+int tw_l2_project_adjoint(tw_patch *patch, const tw_func *f, const int64_t *row_ptr,
+                          const int32_t *col, const double *val, const double *dLdu,
+                          const double *u, double *lam, double *grad, double tol, int maxit,
+                          int *iters, double *relres, void *stream);
+
 /* Device copies of the classification: estate[nel1*nel2], fstate[n1*n2]
  * (uint8, TW_ELEM_* / TW_FUNC_*), act[n1*n2] (int32 active index or -1). */
 int tw_states(const tw_patch *patch, uint8_t *estate, uint8_t *fstate, int32_t *act,
@@ -237,7 +264,10 @@ int64_t tw_launch_count(void);
 #define TW_STAGE_CUTROWS 2   /* cut rows: region + element Gauss + cut rule   */
 #define TW_STAGE_RHS 3
 #define TW_STAGE_CG 4
-#define TW_NSTAGES 5
+#define TW_STAGE_LOSS 5      /* tw_loss                                       */
+#define TW_STAGE_ADJOINT 6   /* tw_l2_project_adjoint's gradient kernels (its  
+                                CG counts as TW_STAGE_CG)                     */
+#define TW_NSTAGES 7
 int tw_profile_enable(int on);
 int tw_profile_read(int stage, double *total_ms, int64_t *count);
 

@@ -8,6 +8,7 @@ import ctypes as C
 import os
 
 import numpy as np
+import torch
 
 from . import _build
 
@@ -82,6 +83,10 @@ def load(build: bool = True):
     L.tw_rhs.argtypes = [vp, C.POINTER(FuncDesc), vp, vp]
     L.tw_l2_project.argtypes = [vp, C.POINTER(FuncDesc), vp, vp, vp, vp, C.c_double, C.c_int,
                                 C.POINTER(C.c_int), C.POINTER(C.c_double), vp]
+    L.tw_loss.argtypes = [vp, C.POINTER(FuncDesc), vp, vp, vp, vp]
+    L.tw_l2_project_adjoint.argtypes = [vp, C.POINTER(FuncDesc), vp, vp, vp, vp, vp, vp, vp,
+                                        C.c_double, C.c_int, C.POINTER(C.c_int),
+                                        C.POINTER(C.c_double), vp]
     L.tw_states.argtypes = [vp, vp, vp, vp, vp]
     L.tw_patch_table.argtypes = [vp, C.c_int, vp, C.c_int64, i64p, vp]
     L.tw_launch_count.restype = C.c_int64
@@ -258,6 +263,49 @@ class Patch:
             _check(rc)
         return u[:self.n_rows], it.value, rel.value
 
+    def loss(self, u, g, stream=None):
+        """tw_loss: (L as a 0-d device tensor, dL/du)."""
+        torch = _torch()
+        keep = []
+        gd = make_func_desc(g, keep)
+        u = u.contiguous()
+        out = torch.empty(max(self.n_rows, 1) + 1, dtype=torch.float64, device="cuda")
+        _check(load().tw_loss(self._h, C.byref(gd), C.c_void_p(u.data_ptr()),
+                              C.c_void_p(out.data_ptr()), C.c_void_p(out[1:].data_ptr()),
+                              _stream(stream)))
+        return out[0], out[1:1 + self.n_rows]
+
+    def density_shape(self):
+        """(m2, m1) of the density spline; (0, 0) without one."""
+        c = self.spec["coef"]
+        if c["kind"] != "density":
+            return (0, 0)
+        return (len(c["knots"][1]) - c["p"] - 1, len(c["knots"][0]) - c["p"] - 1)
+
+    def l2_project_adjoint(self, f, csr, dLdu, u, tol=1e-12, maxit=None, stream=None,
+                           check=True):
+        """tw_l2_project_adjoint: (dL/dd as (m2, m1), lambda, iterations, residual)."""
+        torch = _torch()
+        keep = []
+        fd = make_func_desc(f, keep)
+        rp, col, val = csr
+        dLdu = dLdu.contiguous()
+        u = u.contiguous()
+        lam = torch.empty(max(self.n_rows, 1), dtype=torch.float64, device="cuda")
+        m2, m1 = self.density_shape()
+        grad = torch.empty(max(m2 * m1, 1), dtype=torch.float64, device="cuda")
+        it = C.c_int(0)
+        rel = C.c_double(0)
+        rc = load().tw_l2_project_adjoint(
+            self._h, C.byref(fd), C.c_void_p(rp.data_ptr()), C.c_void_p(col.data_ptr()),
+            C.c_void_p(val.data_ptr()), C.c_void_p(dLdu.data_ptr()), C.c_void_p(u.data_ptr()),
+            C.c_void_p(lam.data_ptr()), C.c_void_p(grad.data_ptr()), tol,
+            int(maxit if maxit is not None else 10 * self.n_rows), C.byref(it), C.byref(rel),
+            _stream(stream))
+        if check:
+            _check(rc)
+        return grad[:m2 * m1].view(m2, m1), lam[:self.n_rows], it.value, rel.value
+
     def states(self, stream=None):
         torch = _torch()
         es = torch.empty(self.nel1 * self.nel2, dtype=torch.uint8, device="cuda")
@@ -321,7 +369,7 @@ def launch_count() -> int:
     return int(load().tw_launch_count())
 
 
-STAGES = {"setup": 0, "interior": 1, "cutrows": 2, "rhs": 3, "cg": 4}
+STAGES = {"setup": 0, "interior": 1, "cutrows": 2, "rhs": 3, "cg": 4, "loss": 5, "adjoint": 6}
 
 
 def profile_enable(on: bool = True):
@@ -334,3 +382,41 @@ def profile_read(stage: str):
     n = C.c_int64(0)
     _check(load().tw_profile_read(STAGES[stage], C.byref(ms), C.byref(n)))
     return ms.value, n.value
+
+
+def _density_spec(spec, coef):
+    s = dict(spec)
+    c = dict(spec["coef"])
+    c["coef"] = coef
+    s["coef"] = c
+    return s
+
+
+class ProjectionLoss(torch.autograd.Function):
+    """L(d) = sum_q omega_q detJ (u_h - g)^2, u_h the L2 projection of f onto
+    the trimmed patch's spline space under c = rho(d) det J, as a function of
+    the density coefficients d (m2 x m1).  forward: patch setup, formation,
+    CG and tw_loss; backward: tw_l2_project_adjoint."""
+
+    @staticmethod
+    def forward(ctx, dcoef, spec, f, g, tol):
+        d = dcoef.detach().to("cpu", torch.float64).numpy()
+        P = Patch(_density_spec(spec, d))
+        csr = P.form_mass("fp64")
+        u, _, _ = P.l2_project(f, csr, tol=tol)
+        L, dLdu = P.loss(u, g)
+        ctx.state = (P, csr, u, dLdu, f, tol)
+        return L.to(dcoef.device, dcoef.dtype)
+
+    @staticmethod
+    def backward(ctx, gout):
+        P, csr, u, dLdu, f, tol = ctx.state
+        grad, _, _, _ = P.l2_project_adjoint(f, csr, dLdu, u, tol=tol)
+        ctx.state = None
+        return gout * grad.to(gout.device, gout.dtype), None, None, None, None
+
+
+def projection_loss(dcoef, spec, f, g, tol=1e-13):
+    """Differentiable projection loss (see ProjectionLoss)."""
+    _torch()
+    return ProjectionLoss.apply(dcoef, spec, f, g, tol)

@@ -463,3 +463,32 @@ extern "C" int tw_l2_project(tw_patch *P, const tw_func *f, const int64_t *row_p
   return l2_project_run(P, f, row_ptr, col, val, u, tol, maxit, iters, relres,
                         (cudaStream_t)stream);
 }
+
+extern "C" int tw_loss(tw_patch *P, const tw_func *g, const double *u, double *loss,
+                       double *dLdu, void *stream) {
+  if (!P || !g || !u || !loss || (!dLdu && P->n_rows > 0)) {
+    set_error("tw_loss: NULL argument");
+    return TW_EINVAL;
+  }
+  return loss_run(P, g, u, loss, dLdu, (cudaStream_t)stream);
+}
+
+extern "C" int tw_l2_project_adjoint(tw_patch *P, const tw_func *f, const int64_t *row_ptr,
+                                     const int32_t *col, const double *val, const double *dLdu,
+                                     const double *u, double *lam, double *grad, double tol,
+                                     int maxit, int *iters, double *relres, void *stream) {
+  if (!P || !f || !row_ptr || !col || !val || !dLdu || !u || !lam || !grad) {
+    set_error("tw_l2_project_adjoint: NULL argument");
+    return TW_EINVAL;
+  }
+  if (P->geo.coef_kind != TW_COEF_DENSITY) {
+    set_error("tw_l2_project_adjoint: the patch has no density spline (TW_COEF_DENSITY)");
+    return TW_EINVAL;
+  }
+  if (!(tol > 0) || maxit < 0) {
+    set_error("tw_l2_project_adjoint: need tol > 0 and maxit >= 0");
+    return TW_EINVAL;
+  }
+  return adjoint_run(P, f, row_ptr, col, val, dLdu, u, lam, grad, tol, maxit, iters, relres,
+                     (cudaStream_t)stream);
+}

@@ -689,6 +689,16 @@ int rhs_launch(tw_patch *P, const tw_func *f, double *b, cudaStream_t s);
 int l2_project_run(tw_patch *P, const tw_func *f, const int64_t *rp, const int32_t *col,
                    const double *val, double *u, double tol, int maxit, int *iters,
                    double *relres, cudaStream_t s);
+RowArgs row_args(tw_patch *P);
+// CG on M_s x = b for a device b; temporary allocations released before return
+int cg_solve(tw_patch *P, const int64_t *rp, const int32_t *col, const double *val,
+             const double *b, double *x, double tol, int maxit, int *iters, double *relres,
+             cudaStream_t s);
+int loss_run(tw_patch *P, const tw_func *g, const double *u, double *loss, double *dLdu,
+             cudaStream_t s);
+int adjoint_run(tw_patch *P, const tw_func *f, const int64_t *rp, const int32_t *col,
+                const double *val, const double *dLdu, const double *u, double *lam,
+                double *grad, double tol, int maxit, int *iters, double *relres, cudaStream_t s);
 }  // namespace tw
 
 #define TW_LAUNCH() (tw::g_launches++)

@@ -9,68 +9,9 @@
 #include <cstring>
 #include <mutex>
 
-#include "tw_internal.cuh"
+#include "tw_func.cuh"
 
 namespace tw {
-
-struct Func {
-  int kind;
-  double prm[4];
-  int q[2], nk[2], m1;
-  const double *U[2];
-  const double *coef;
-};
-
-__device__ __forceinline__ void phys_at(const Geo &G, const Dir &A, const Dir &B, double x1,
-                                        double x2, double *X) {
-  if (G.geom_kind != TW_GEOM_SPLINE) {
-    X[0] = x1;
-    X[1] = x2;
-    return;
-  }
-  int e1 = elem_of(A.bp, A.nel, x1), e2 = elem_of(B.bp, B.nel, x2);
-  double v1[TW_MAXP1], v2[TW_MAXP1];
-  basis_vals(A.U, e1 + A.p, x1, A.p, v1);
-  basis_vals(B.U, e2 + B.p, x2, B.p, v2);
-  X[0] = X[1] = 0.0;
-  for (int b = 0; b <= B.p; b++)
-    for (int a = 0; a <= A.p; a++) {
-      const double *pt = G.ctrl + 2 * ((size_t)(e2 + b) * G.n1 + (e1 + a));
-      X[0] += pt[0] * v1[a] * v2[b];
-      X[1] += pt[1] * v1[a] * v2[b];
-    }
-}
-
-__device__ double func_at(const Func &f, double x1, double x2, const double *X) {
-  switch (f.kind) {
-    case TW_FUNC_SPLINE: {
-      double N1[TW_MAXP1], N2[TW_MAXP1];
-      int s1 = find_span(f.U[0], f.q[0], f.nk[0] - f.q[0] - 1, x1);
-      int s2 = find_span(f.U[1], f.q[1], f.nk[1] - f.q[1] - 1, x2);
-      basis_vals(f.U[0], s1, x1, f.q[0], N1);
-      basis_vals(f.U[1], s2, x2, f.q[1], N2);
-      double s = 0.0;
-      for (int b = 0; b <= f.q[1]; b++)
-        for (int a = 0; a <= f.q[0]; a++)
-          s += f.coef[(size_t)(s2 - f.q[1] + b) * f.m1 + (s1 - f.q[0] + a)] * N1[a] * N2[b];
-      return s;
-    }
-    case TW_FUNC_SINSIN: return sin(f.prm[0] * X[0]) * sin(f.prm[1] * X[1]);
-    case TW_FUNC_SINCOS: return sin(f.prm[0] * X[0]) * cos(f.prm[1] * X[1]);
-    case TW_FUNC_GAUSS: {
-      double dx = X[0] - f.prm[1], dy = X[1] - f.prm[2];
-      return exp(-f.prm[0] * (dx * dx + dy * dy));
-    }
-  }
-  return 0.0;
-}
-
-__device__ __forceinline__ double fpoint(const Func &f, const Geo &G, const Dir &A, const Dir &B,
-                                         double x1, double x2) {
-  double X[2];
-  phys_at(G, A, B, x1, x2, X);
-  return func_at(f, x1, x2, X);
-}
 
 // f * c on the WQ grid
 __global__ void k_fc_grid(Func f, Geo G, Dir A, Dir B, const double *C, double *FC) {
@@ -303,44 +244,7 @@ static void dot(const double *x, const double *y, int64_t n, double *part, doubl
   TW_LAUNCH();
 }
 
-static Func make_func(const tw_func *f, tw_patch *P, int *rc) {
-  Func F;
-  memset(&F, 0, sizeof(F));
-  F.kind = f->kind;
-  for (int k = 0; k < 4; k++) F.prm[k] = f->prm[k];
-  *rc = 0;
-  if (f->kind < TW_FUNC_SPLINE || f->kind > TW_FUNC_GAUSS) {
-    set_error("unknown function kind %d", f->kind);
-    *rc = TW_EINVAL;
-    return F;
-  }
-  if (f->kind == TW_FUNC_SPLINE) {
-    size_t m = 1;
-    for (int d = 0; d < 2; d++) {
-      if (!f->knots[d] || f->p[d] < 0 || f->p[d] > TW_MAXP || f->nknots[d] < 2 * f->p[d] + 2) {
-        set_error("spline function: bad knots or degree");
-        *rc = TW_EINVAL;
-        return F;
-      }
-      F.q[d] = f->p[d];
-      F.nk[d] = f->nknots[d];
-      double *u = (double *)dalloc(P, sizeof(double) * f->nknots[d]);
-      if (!u) { *rc = TW_ENOMEM; return F; }
-      cudaMemcpyAsync(u, f->knots[d], sizeof(double) * f->nknots[d], cudaMemcpyHostToDevice,
-                      P->stream);
-      F.U[d] = u;
-      m *= (size_t)(f->nknots[d] - f->p[d] - 1);
-    }
-    F.m1 = f->nknots[0] - f->p[0] - 1;
-    double *c = (double *)dalloc(P, sizeof(double) * m);
-    if (!c || !f->coef) { *rc = c ? TW_EINVAL : TW_ENOMEM; return F; }
-    cudaMemcpyAsync(c, f->coef, sizeof(double) * m, cudaMemcpyHostToDevice, P->stream);
-    F.coef = c;
-  }
-  return F;
-}
-
-static RowArgs row_args(tw_patch *Pt) {
+RowArgs row_args(tw_patch *Pt) {
   RowArgs ra;
   ra.A = Pt->d[0];
   ra.B = Pt->d[1];
@@ -411,23 +315,23 @@ int rhs_launch(tw_patch *P, const tw_func *f, double *b, cudaStream_t s) {
   return rc;
 }
 
-static int cg_impl(tw_patch *P, const tw_func *f, const int64_t *rp, const int32_t *col,
-                   const double *val, double *u, double tol, int maxit, int *iters,
-                   double *relres, cudaStream_t s) {
+// CG on M_s x = b for a device b (n_rows); x is overwritten
+static int cg_core(tw_patch *P, const int64_t *rp, const int32_t *col, const double *val,
+                   const double *b, double *u, double tol, int maxit, int *iters, double *relres,
+                   cudaStream_t s) {
   int64_t n = P->n_rows, nnz = P->nnz;
   if (n == 0) {
     if (iters) *iters = 0;
     if (relres) *relres = 0.0;
     return TW_OK;
   }
-  double *buf = (double *)dalloc(P, sizeof(double) * (6 * n + DOT_BLOCKS + 8));
+  double *buf = (double *)dalloc(P, sizeof(double) * (5 * n + DOT_BLOCKS + 8));
   int64_t *perm = (int64_t *)dalloc(P, sizeof(int64_t) * (nnz + 1));
   double *ms = (double *)dalloc(P, sizeof(double) * (nnz + 1));
   if (!buf || !perm || !ms) return TW_ENOMEM;
-  double *b = buf, *r = b + n, *z = r + n, *p = z + n, *q = p + n, *dinv = q + n;
+  double *r = buf, *z = r + n, *p = z + n, *q = p + n, *dinv = q + n;
   double *part = dinv + n, *sc = part + DOT_BLOCKS;
-  int rc = rhs_impl(P, f, b, s);
-  if (rc) return rc;
+  int rc = 0;
   unsigned gb = (unsigned)((n + 255) / 256);
   k_perm<<<gb, 256, 0, s>>>(rp, col, n, perm);
   TW_LAUNCH();
@@ -472,6 +376,25 @@ static int cg_impl(tw_patch *P, const tw_func *f, const int64_t *rp, const int32
     return TW_ENOCONV;
   }
   return TW_OK;
+}
+
+static int cg_impl(tw_patch *P, const tw_func *f, const int64_t *rp, const int32_t *col,
+                   const double *val, double *u, double tol, int maxit, int *iters,
+                   double *relres, cudaStream_t s) {
+  double *b = (double *)dalloc(P, sizeof(double) * (P->n_rows + 1));
+  if (!b) return TW_ENOMEM;
+  int rc = rhs_impl(P, f, b, s);
+  if (rc) return rc;
+  return cg_core(P, rp, col, val, b, u, tol, maxit, iters, relres, s);
+}
+
+int cg_solve(tw_patch *P, const int64_t *rp, const int32_t *col, const double *val,
+             const double *b, double *x, double tol, int maxit, int *iters, double *relres,
+             cudaStream_t s) {
+  int mark = P->nallocs;
+  int rc = cg_core(P, rp, col, val, b, x, tol, maxit, iters, relres, s);
+  release_to(P, mark);
+  return rc;
 }
 
 int l2_project_run(tw_patch *P, const tw_func *f, const int64_t *rp, const int32_t *col,
