@@ -214,7 +214,7 @@ def run_ours(args, rank, world, local_rank):
         assign[k].append(idx)
         load[k] += infos[idx][1]
 
-    def run_batch(body):
+    def run_batch(body, tag=None):
         start = torch.cuda.Event()
         start.record(stream)
         errors = []
@@ -222,10 +222,14 @@ def run_ours(args, rank, world, local_rank):
         def worker(k):
             try:
                 torch.cuda.set_device(local_rank)
+                if tag:  # NVTX range per launching thread (ncu --nvtx-include)
+                    torch.cuda.nvtx.range_push(tag)
                 with torch.cuda.stream(streams[k]):
                     streams[k].wait_event(start)
                     for idx in assign[k]:
                         body(idx)
+                if tag:
+                    torch.cuda.nvtx.range_pop()
             except Exception as exc:  # surfaced after the join
                 errors.append(exc)
 
@@ -244,8 +248,8 @@ def run_ours(args, rank, world, local_rank):
         P.form_mass("fp64", out=outs[idx])
         P.close()
 
-    def step():
-        run_batch(form_one)
+    def step(tag=None):
+        run_batch(form_one, tag)
 
     for _ in range(args.warmup):
         step()
@@ -269,7 +273,7 @@ def run_ours(args, rank, world, local_rank):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        step()
+        step("timed_step")
         e1.record(stream)
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))

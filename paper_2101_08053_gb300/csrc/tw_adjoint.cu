@@ -492,6 +492,137 @@ __global__ void k_adj_cut(RowArgs a, Func f, const int32_t *rows, int nrows, con
     }
 }
 
+// one warp per cut row, for windows of at most ADJ_WIN coefficients: the
+// lanes share the row's points, each lane sums into its own window, and the
+// warp adds the lanes' windows entry by entry in a fixed order
+#define ADJ_WIN 64
+__global__ void __launch_bounds__(128) k_adj_cut_warp(RowArgs a, Func f, const int32_t *rows,
+                                                      int nrows, const double *u,
+                                                      const double *lam, const int2 *org, int w1,
+                                                      int w2, double *part, int *flag) {
+  const int lane = threadIdx.x & 31;
+  const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (r >= nrows) return;  // the whole warp
+  double win[ADJ_WIN];
+  const Dir &A = a.A;
+  const Dir &B = a.B;
+  const int P = A.p, p1 = P + 1;
+  int g = rows[r];
+  int i1 = g % A.n, i2 = g / A.n;
+  AdjRow R;
+  R.u = u;
+  R.lam = lam;
+  R.ui = u[a.act[g]];
+  R.li = lam[a.act[g]];
+  R.win = win;
+  R.o1 = org[r].x;
+  R.o2 = org[r].y;
+  R.w1 = w1;
+  R.w2 = w2;
+  R.flag = flag;
+  for (int k = 0; k < w1 * w2; k++) R.win[k] = 0.0;
+  int kind;
+  if (a.method == TW_METHOD_GAUSS || a.method == TW_METHOD_HYBRID) kind = 0;
+  else if (a.method == TW_METHOD_NAIVE) kind = 1;
+  else kind = a.choice[4 * g] >= 0 ? 2 : 0;
+  int lo1 = max(0, i1 - P), hi1 = min(A.nel - 1, i1);
+  int lo2 = max(0, i2 - P), hi2 = min(B.nel - 1, i2);
+  int r0[2] = {1, 1}, r1[2] = {0, 0};
+  if (kind != 0) {
+    double rx[2][32], rw[2][32];
+    int rk[2][32], nr[2];
+    for (int d = 0; d < 2; d++) {
+      const Dir &D = d == 0 ? A : B;
+      int i = d == 0 ? i1 : i2;
+      int n = 0;
+      int ck = kind == 2 ? a.choice[4 * g + 2 * d] : 0;
+      int s = kind == 2 ? a.choice[4 * g + 2 * d + 1] : -1;
+      int lo = d == 0 ? lo1 : lo2, hi = d == 0 ? hi1 : hi2;
+      r0[d] = ck == 2 ? s : lo;
+      r1[d] = ck == 1 ? s - 1 : hi;
+      if (ck == 0) {
+        for (int c = 0; c < D.qcnt[i] && n < 32; c++) {
+          rx[d][n] = D.xq[D.qbeg[i] + c];
+          rw[d][n] = D.W[(size_t)i * D.qmax + c];
+          rk[d][n] = D.qbeg[i] + c;
+          n++;
+        }
+      } else {
+        int side = ck - 1, sl = a.disc_slot[d][s];
+        double t = D.bp[s];
+        const double *xs = a.dwq_x[d] + (size_t)sl * TW_LQMAX;
+        const double *ws = a.dwq_w[d] + (((size_t)sl * P + (i - s)) * 2 + side) * TW_LQMAX;
+        for (int k = 0; k < a.dwq_np[d][sl] && n < 32; k++) {
+          double x = xs[k];
+          if (!(x > D.U[i] && x < D.U[i + P + 1])) continue;
+          if (side == 0 ? !(x < t) : !(x > t)) continue;
+          rx[d][n] = x;
+          rw[d][n] = ws[k];
+          rk[d][n] = -1;
+          n++;
+        }
+      }
+      nr[d] = n;
+    }
+    if (kind == 1) {
+      r0[0] = r0[1] = 1;
+      r1[0] = r1[1] = 0;
+    }
+    for (int t = lane; t < nr[0] * nr[1]; t += 32) {
+        const int ia = t % nr[0], ib = t / nr[0];
+        int k1 = rk[0][ia], k2 = rk[1][ib];
+        double x1 = rx[0][ia], x2 = rx[1][ib];
+        int e1, e2;
+        if (k1 >= 0) e1 = A.qel[k1];
+        else e1 = elem_of(A.bp, A.nel, x1);
+        if (k2 >= 0) e2 = B.qel[k2];
+        else e2 = elem_of(B.bp, B.nel, x2);
+        if (kind == 1 && a.estate[e2 * A.nel + e1] != TW_ELEM_REGULAR) continue;
+        double v1[TW_MAXP1], d1[TW_MAXP1], v2[TW_MAXP1], d2[TW_MAXP1];
+        basis_ders(A.U, e1 + P, x1, P, v1, d1);
+        basis_ders(B.U, e2 + P, x2, P, v2, d2);
+        adj_point(a, f, R, x1, x2, rw[0][ia] * rw[1][ib], e1, v1, d1, e2, v2, d2);
+      }
+  }
+  for (int e2 = lo2; e2 <= hi2; e2++)
+    for (int e1 = lo1; e1 <= hi1; e1++) {
+      int e = e2 * A.nel + e1;
+      uint8_t st = a.estate[e];
+      bool inR = e1 >= r0[0] && e1 <= r1[0] && e2 >= r0[1] && e2 <= r1[1];
+      if (st == TW_ELEM_REGULAR && kind != 1 && !inR) {
+        double h1 = 0.5 * (A.bp[e1 + 1] - A.bp[e1]), h2 = 0.5 * (B.bp[e2 + 1] - B.bp[e2]);
+        for (int t = lane; t < p1 * p1; t += 32) {
+            const int g1 = t % p1, g2 = t / p1;
+            double v1[TW_MAXP1], d1[TW_MAXP1], v2[TW_MAXP1], d2[TW_MAXP1];
+            for (int k = 0; k < p1; k++) {
+              v1[k] = A.GB[((size_t)e1 * p1 + g1) * p1 + k];
+              d1[k] = A.dGB[((size_t)e1 * p1 + g1) * p1 + k];
+              v2[k] = B.GB[((size_t)e2 * p1 + g2) * p1 + k];
+              d2[k] = B.dGB[((size_t)e2 * p1 + g2) * p1 + k];
+            }
+            double x1 = A.bp[e1] + h1 * (A.gx[g1] + 1.0), x2 = B.bp[e2] + h2 * (B.gx[g2] + 1.0);
+            double w = A.gw[g1] * h1 * B.gw[g2] * h2 * v1[i1 - e1] * v2[i2 - e2];
+            adj_point(a, f, R, x1, x2, w, e1, v1, d1, e2, v2, d2);
+          }
+      } else if (st == TW_ELEM_CUT) {
+        int cs = a.cut_slot[e];
+        for (int64_t q = a.cut_off[cs] + lane; q < a.cut_off[cs + 1]; q += 32) {
+          const double *xq = a.cut_pts + 3 * q;
+          double v1[TW_MAXP1], d1[TW_MAXP1], v2[TW_MAXP1], d2[TW_MAXP1];
+          basis_ders(A.U, e1 + P, xq[0], P, v1, d1);
+          basis_ders(B.U, e2 + P, xq[1], P, v2, d2);
+          double w = xq[2] * v1[i1 - e1] * v2[i2 - e2];
+          adj_point(a, f, R, xq[0], xq[1], w, e1, v1, d1, e2, v2, d2);
+        }
+      }
+    }
+  double *out = part + (size_t)r * w1 * w2;
+  for (int k = 0; k < w1 * w2; k++) {
+    double v = warp_sum(win[k]);
+    if (lane == 0) out[k] = v;
+  }
+}
+
 // grad(m1, m2) = WQ part + the cut rows' windows that hold (m1, m2), row order
 __global__ void k_adj_final(int m1n, int m2n, const double *Gw, int nrows, const int2 *org, int w1,
                             int w2, const double *part, double *grad) {
@@ -610,8 +741,12 @@ static int grad_impl(tw_patch *P, const tw_func *f, const double *u, const doubl
     }
     part = (double *)dalloc(P, sizeof(double) * (size_t)nc * w[0] * w[1]);
     if (!part) return TW_ENOMEM;
-    k_adj_cut<<<(nc + 63) / 64, 64, 0, s>>>(ra, F, P->cutrows, nc, u, lam, org, w[0], w[1], part,
-                                            dflag);
+    if (w[0] * w[1] <= ADJ_WIN)
+      k_adj_cut_warp<<<(nc + 3) / 4, 128, 0, s>>>(ra, F, P->cutrows, nc, u, lam, org, w[0], w[1],
+                                                 part, dflag);
+    else
+      k_adj_cut<<<(nc + 63) / 64, 64, 0, s>>>(ra, F, P->cutrows, nc, u, lam, org, w[0], w[1],
+                                              part, dflag);
     TW_LAUNCH();
   }
   k_adj_final<<<(nm + 255) / 256, 256, 0, s>>>(m1n, m2n, Gw, nc, org, w[0], w[1], part, grad);

@@ -121,7 +121,7 @@ struct CutSmem {
   double Tg[P1 * P1];
   int rk[2][TW_RC];
   int nr[2], nnest[2], nest[2][TW_RC];
-  int pos[W * W];
+  int wcnt[8];
 };
 
 template <int P, typename OutT>
@@ -268,6 +268,28 @@ __device__ void cutrow_item(const RowArgs &a, int g, int32_t *__restrict__ col,
 
   // ---- elements of the support: Gauss on regular (outside R), cut rule on cut ----
   const int p1 = P1;
+  if (a.gmat || kind == 1) {
+    // every element matrix is precomputed: one owner thread per row entry adds
+    // its elements' terms in (e2, e1) order, with no barrier per element
+    constexpr int P4 = P1 * P1 * P1 * P1;
+    for (int t = tid; t < W * W; t += blockDim.x) {
+      const int q2 = t / W, q1 = t % W;
+      const int j1 = i1 - P + q1, j2 = i2 - P + q2;
+      double s = S.acc[t];
+      for (int e2 = max(lo2, j2 - P); e2 <= min(hi2, j2); e2++)
+        for (int e1 = max(lo1, j1 - P); e1 <= min(hi1, j1); e1++) {
+          const int e = e2 * A.nel + e1;
+          const uint8_t st = a.estate[e];
+          const bool inR = e1 >= r0[0] && e1 <= r1[0] && e2 >= r0[1] && e2 <= r1[1];
+          const double *Me = nullptr;
+          if (st == TW_ELEM_REGULAR && kind != 1 && !inR) Me = a.gmat + (size_t)a.gslot[e] * P4;
+          else if (st == TW_ELEM_CUT) Me = a.cut_M + (size_t)a.cut_slot[e] * P4;
+          if (Me) s += Me[((i2 - e2) * p1 + (i1 - e1)) * p1 * p1 + (j2 - e2) * p1 + (j1 - e1)];
+        }
+      S.acc[t] = s;
+    }
+    __syncthreads();
+  } else
   for (int e2 = lo2; e2 <= hi2; e2++)
     for (int e1 = lo1; e1 <= hi1; e1++) {
       const int e = e2 * A.nel + e1;
@@ -315,24 +337,30 @@ __device__ void cutrow_item(const RowArgs &a, int g, int32_t *__restrict__ col,
     }
 
   // ---- write the row: active columns in ascending order (R11) ----
-  if (tid == 0) {
-    int c = 0;
-    for (int r2 = 0; r2 < W; r2++)
-      for (int q1 = 0; q1 < W; q1++) {
-        int j1 = i1 - P + q1, j2 = i2 - P + r2;
-        int ok = j1 >= 0 && j1 < n1 && j2 >= 0 && j2 < B.n && a.act[j2 * n1 + j1] >= 0;
-        S.pos[r2 * W + q1] = ok ? c++ : -1;
-      }
+  // an entry's position = active entries before it: warp ballots + the
+  // counts of the warps before (the block has at least NW warps)
+  constexpr int NW = (W * W + 31) / 32;
+  static_assert(NW <= 8, "row entries exceed eight warps");
+  const int lane = tid & 31, wid = tid >> 5;
+  int ok = 0, jact = -1;
+  unsigned msk = 0u;
+  if (wid < NW) {
+    if (tid < W * W) {
+      const int r2 = tid / W, q1 = tid % W;
+      const int j1 = i1 - P + q1, j2 = i2 - P + r2;
+      if (j1 >= 0 && j1 < n1 && j2 >= 0 && j2 < B.n) jact = a.act[j2 * n1 + j1];
+      ok = jact >= 0;
+    }
+    msk = __ballot_sync(0xffffffffu, ok);
+    if (lane == 0) S.wcnt[wid] = __popc(msk);
   }
   __syncthreads();
-  const int64_t base = a.rp[a.act[g]];
-  for (int t = tid; t < W * W; t += blockDim.x) {
-    int ps = S.pos[t];
-    if (ps < 0) continue;
-    int r2 = t / W, q1 = t % W;
-    int j1 = i1 - P + q1, j2 = i2 - P + r2;
-    val[base + ps] = (OutT)S.acc[t];
-    col[base + ps] = a.act[j2 * n1 + j1];
+  if (ok) {
+    int ps = __popc(msk & ((1u << lane) - 1u));
+    for (int w = 0; w < wid; w++) ps += S.wcnt[w];
+    const int64_t base = a.rp[a.act[g]];
+    val[base + ps] = (OutT)S.acc[tid];
+    col[base + ps] = jact;
   }
   __syncthreads();  // smem reused by the next item
 }

@@ -37,11 +37,13 @@ __global__ void k_rhs_interior(Dir A, Dir B, const uint8_t *fstate, const int32_
   b[act[g]] = s;
 }
 
-// one thread per cut row: the same three parts as k_cutrows, applied to f
-__global__ void k_rhs_cut(RowArgs a, Func f, const int32_t *rows, int nrows, const double *FC,
-                          double *b) {
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= nrows) return;
+// one warp per cut row: the same three parts as k_cutrows, applied to f; the
+// lanes share the row's points and the warp adds their sums in a fixed order
+__global__ void __launch_bounds__(128) k_rhs_cut(RowArgs a, Func f, const int32_t *rows,
+                                                 int nrows, const double *FC, double *b) {
+  const int lane = threadIdx.x & 31;
+  const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (r >= nrows) return;  // the whole warp
   const Dir &A = a.A;
   const Dir &B = a.B;
   const int P = A.p, p1 = P + 1;
@@ -68,7 +70,7 @@ __global__ void k_rhs_cut(RowArgs a, Func f, const int32_t *rows, int nrows, con
       r0[d] = ck == 2 ? s : lo;
       r1[d] = ck == 1 ? s - 1 : hi;
       if (ck == 0) {
-        for (int c = 0; c < D.qcnt[i]; c++) {
+        for (int c = 0; c < D.qcnt[i] && n < 32; c++) {
           rx[d][n] = D.xq[D.qbeg[i] + c];
           rw[d][n] = D.W[(size_t)i * D.qmax + c];
           rk[d][n] = D.qbeg[i] + c;
@@ -95,18 +97,18 @@ __global__ void k_rhs_cut(RowArgs a, Func f, const int32_t *rows, int nrows, con
       r0[0] = r0[1] = 1;
       r1[0] = r1[1] = 0;
     }
-    for (int ib = 0; ib < nr[1]; ib++)
-      for (int ia = 0; ia < nr[0]; ia++) {
-        int k1 = rk[0][ia], k2 = rk[1][ib];
-        double v;
-        if (k1 >= 0 && k2 >= 0) {
-          v = FC[(size_t)k2 * A.nq + k1];
-          if (kind == 1 && a.estate[B.qel[k2] * A.nel + A.qel[k1]] != TW_ELEM_REGULAR) v = 0.0;
-        } else {
-          v = coef_at(a.G, A, B, rx[0][ia], rx[1][ib]) * fpoint(f, a.G, A, B, rx[0][ia], rx[1][ib]);
-        }
-        sum += rw[0][ia] * rw[1][ib] * v;
+    for (int t = lane; t < nr[0] * nr[1]; t += 32) {
+      const int ia = t % nr[0], ib = t / nr[0];
+      int k1 = rk[0][ia], k2 = rk[1][ib];
+      double v;
+      if (k1 >= 0 && k2 >= 0) {
+        v = FC[(size_t)k2 * A.nq + k1];
+        if (kind == 1 && a.estate[B.qel[k2] * A.nel + A.qel[k1]] != TW_ELEM_REGULAR) v = 0.0;
+      } else {
+        v = coef_at(a.G, A, B, rx[0][ia], rx[1][ib]) * fpoint(f, a.G, A, B, rx[0][ia], rx[1][ib]);
       }
+      sum += rw[0][ia] * rw[1][ib] * v;
+    }
   }
   for (int e2 = lo2; e2 <= hi2; e2++)
     for (int e1 = lo1; e1 <= hi1; e1++) {
@@ -116,23 +118,24 @@ __global__ void k_rhs_cut(RowArgs a, Func f, const int32_t *rows, int nrows, con
       if (st == TW_ELEM_REGULAR && kind != 1 && !inR) {
         const double *cgp = a.gc + (size_t)a.gslot[e] * p1 * p1;
         double h1 = 0.5 * (A.bp[e1 + 1] - A.bp[e1]), h2 = 0.5 * (B.bp[e2 + 1] - B.bp[e2]);
-        for (int g2 = 0; g2 < p1; g2++)
-          for (int g1 = 0; g1 < p1; g1++) {
-            double x1 = A.bp[e1] + h1 * (A.gx[g1] + 1.0), x2 = B.bp[e2] + h2 * (B.gx[g2] + 1.0);
-            double w = A.gw[g1] * h1 * B.gw[g2] * h2 * A.GB[(e1 * p1 + g1) * p1 + (i1 - e1)] *
-                       B.GB[(e2 * p1 + g2) * p1 + (i2 - e2)];
-            sum += w * cgp[g2 * p1 + g1] * fpoint(f, a.G, A, B, x1, x2);
-          }
+        for (int t = lane; t < p1 * p1; t += 32) {
+          const int g1 = t % p1, g2 = t / p1;
+          double x1 = A.bp[e1] + h1 * (A.gx[g1] + 1.0), x2 = B.bp[e2] + h2 * (B.gx[g2] + 1.0);
+          double w = A.gw[g1] * h1 * B.gw[g2] * h2 * A.GB[(e1 * p1 + g1) * p1 + (i1 - e1)] *
+                     B.GB[(e2 * p1 + g2) * p1 + (i2 - e2)];
+          sum += w * cgp[g2 * p1 + g1] * fpoint(f, a.G, A, B, x1, x2);
+        }
       } else if (st == TW_ELEM_CUT) {
         int cs = a.cut_slot[e];
-        for (int64_t q = a.cut_off[cs]; q < a.cut_off[cs + 1]; q++) {
+        for (int64_t q = a.cut_off[cs] + lane; q < a.cut_off[cs + 1]; q += 32) {
           const double *Bv = a.cut_B + 2 * q * p1;
           const double *xq = a.cut_pts + 3 * q;
           sum += a.cut_wc[q] * Bv[i1 - e1] * Bv[p1 + (i2 - e2)] * fpoint(f, a.G, A, B, xq[0], xq[1]);
         }
       }
     }
-  b[a.act[g]] = sum;
+  sum = warp_sum(sum);
+  if (lane == 0) b[a.act[g]] = sum;
 }
 
 // ---------------------------------------------------------------------------
@@ -167,81 +170,138 @@ __global__ void k_msym(const int64_t *rp, const int32_t *col, const double *val,
   dinv[r] = dg != 0.0 ? 1.0 / dg : 1.0;
 }
 
-// warp per row, fixed shuffle tree: deterministic
-__global__ void k_spmv(const int64_t *rp, const int32_t *col, const double *ms, const double *x,
-                       double *y, int64_t n) {
-  int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
-  if (r >= n) return;
-  double s = 0.0;
-  for (int64_t k = rp[r] + lane; k < rp[r + 1]; k += 32) s += ms[k] * x[col[k]];
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) y[r] = s;
-}
+// One CG iteration = 3 launches, each with a full grid (a warp per row for
+// the product, a thread per entry for the updates):
+//   k_cg_spmv     q = M_s p, p.q
+//   k_cg_update1  alpha = rz / pq; u += alpha p; r -= alpha q; z = D^-1 r; r.z, r.r
+//   k_cg_update2  beta = rz_new / rz; p = z + beta p
+// Each block writes one partial sum; the block that takes the last ticket of
+// a counter sums all partials in index order (a fixed tree inside the block)
+// and writes the scalar, so every scalar is bitwise reproducible.  The r.z
+// scalar is double-buffered by iteration parity.
+#define CG_THREADS 256
 
-#define DOT_BLOCKS 256
-__global__ void k_dot_partial(const double *x, const double *y, int64_t n, double *part) {
-  __shared__ double sh[256];
-  double s = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)DOT_BLOCKS * 256)
-    s += x[i] * y[i];
-  sh[threadIdx.x] = s;
+enum { SC_PQ = 0, SC_RZ0 = 1, SC_RR0 = 3, SC_BB = 5, SC_N = 6 };
+
+// block sum, fixed order (xor tree in the warp, then warp order); all threads
+// get the result; sh has 9 doubles
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();  // sh may still be read from a previous call
+  if (lane == 0) sh[w] = v;
   __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
-    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-    __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < CG_THREADS / 32; k++) t += sh[k];
+    sh[8] = t;
   }
-  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
-}
-
-__global__ void k_dot_final(const double *part, double *out) {
-  __shared__ double sh[DOT_BLOCKS];
-  sh[threadIdx.x] = part[threadIdx.x];
   __syncthreads();
-  for (int o = DOT_BLOCKS / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-    __syncthreads();
+  return sh[8];
+}
+
+// publish this block's partial v of scalar `slot`; the last block to arrive
+// reduces all partials in order into sc[slot] and rearms the ticket
+__device__ __forceinline__ void reduce_scalar(double v, double *part, unsigned *ticket,
+                                              double *sc, int slot, double *sh) {
+  __shared__ int last;
+  __syncthreads();  // every thread has read `last` of a previous call
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = v;
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
   }
-  if (threadIdx.x == 0) *out = sh[0];
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double t = 0.0;
+#pragma unroll 4
+  for (unsigned k = threadIdx.x; k < gridDim.x; k += CG_THREADS) t += __ldcg(part + k);
+  t = block_sum(t, sh);
+  if (threadIdx.x == 0) {
+    sc[slot] = t;
+    *ticket = 0u;
+  }
 }
 
-enum { S_RZ = 0, S_PQ, S_RZN, S_RR, S_BB };
-
-__global__ void k_cg_init(const double *b, const double *dinv, double *u, double *r, double *z,
-                          double *p, int64_t n) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  u[i] = 0.0;
-  r[i] = b[i];
-  z[i] = b[i] * dinv[i];
-  p[i] = z[i];
+__global__ void __launch_bounds__(CG_THREADS) k_cg_init(const double *b, const double *dinv,
+                                                        double *u, double *r, double *z,
+                                                        double *p, int64_t n, double *part,
+                                                        unsigned *ticket, double *sc) {
+  __shared__ double sh[9];
+  int64_t i = (int64_t)blockIdx.x * CG_THREADS + threadIdx.x;
+  double rz = 0.0, bb = 0.0;
+  if (i < n) {
+    double bi = b[i], zi = bi * dinv[i];
+    u[i] = 0.0;
+    r[i] = bi;
+    z[i] = zi;
+    p[i] = zi;
+    rz = bi * zi;
+    bb = bi * bi;
+  }
+  rz = block_sum(rz, sh);
+  bb = block_sum(bb, sh);
+  // r.z of "iteration -1" goes to the odd slot
+  reduce_scalar(rz, part, ticket, sc, SC_RZ0 + 1, sh);
+  reduce_scalar(bb, part + gridDim.x, ticket + 1, sc, SC_BB, sh);
 }
 
-__global__ void k_cg_update1(const double *sc, const double *p, const double *q,
-                             const double *dinv, double *u, double *r, double *z, int64_t n) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  double alpha = sc[S_RZ] / sc[S_PQ];
-  u[i] += alpha * p[i];
-  r[i] -= alpha * q[i];
-  z[i] = r[i] * dinv[i];
+// CG_LPR lanes per row (fixed shuffle tree); measured on GB300 for the banded
+// (2p+1)^2 rows of these matrices, 4 lanes per row keep ~3x more loads in
+// flight than a warp per row
+#define CG_LPR 4
+__global__ void __launch_bounds__(CG_THREADS) k_cg_spmv(const int64_t *rp, const int32_t *col,
+                                                        const double *ms, const double *p,
+                                                        double *q, int64_t n, double *part,
+                                                        unsigned *ticket, double *sc) {
+  __shared__ double sh[9];
+  const int sub = threadIdx.x & (CG_LPR - 1);
+  const int64_t r = ((int64_t)blockIdx.x * CG_THREADS + threadIdx.x) / CG_LPR;
+  double s = 0.0, pq = 0.0;
+  if (r < n) {
+    const int64_t k0 = rp[r], k1 = rp[r + 1];
+#pragma unroll 4
+    for (int64_t k = k0 + sub; k < k1; k += CG_LPR) s += ms[k] * __ldg(p + col[k]);
+  }
+  for (int o = CG_LPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (r < n && sub == 0) {
+    q[r] = s;
+    pq = p[r] * s;
+  }
+  pq = block_sum(pq, sh);
+  reduce_scalar(pq, part, ticket, sc, SC_PQ, sh);
 }
 
-__global__ void k_cg_update2(const double *sc, const double *z, double *p, int64_t n) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  double beta = sc[S_RZN] / sc[S_RZ];
-  p[i] = z[i] + beta * p[i];
+__global__ void __launch_bounds__(CG_THREADS) k_cg_update1(const double *p, const double *q,
+                                                           const double *dinv, double *u,
+                                                           double *r, double *z, int64_t n,
+                                                           int cur, double *part,
+                                                           unsigned *ticket, double *sc) {
+  __shared__ double sh[9];
+  const double alpha = sc[SC_RZ0 + (cur ^ 1)] / sc[SC_PQ];
+  int64_t i = (int64_t)blockIdx.x * CG_THREADS + threadIdx.x;
+  double rz = 0.0, rr = 0.0;
+  if (i < n) {
+    u[i] += alpha * p[i];
+    double ri = r[i] - alpha * q[i];
+    double zi = ri * dinv[i];
+    r[i] = ri;
+    z[i] = zi;
+    rz = ri * zi;
+    rr = ri * ri;
+  }
+  rz = block_sum(rz, sh);
+  rr = block_sum(rr, sh);
+  reduce_scalar(rz, part, ticket, sc, SC_RZ0 + cur, sh);
+  reduce_scalar(rr, part + gridDim.x, ticket + 1, sc, SC_RR0 + cur, sh);
 }
 
-__global__ void k_cg_roll(double *sc) { sc[S_RZ] = sc[S_RZN]; }
-
-static void dot(const double *x, const double *y, int64_t n, double *part, double *out,
-                cudaStream_t s) {
-  k_dot_partial<<<DOT_BLOCKS, 256, 0, s>>>(x, y, n, part);
-  TW_LAUNCH();
-  k_dot_final<<<1, DOT_BLOCKS, 0, s>>>(part, out);
-  TW_LAUNCH();
+__global__ void __launch_bounds__(CG_THREADS) k_cg_update2(const double *z, double *p, int64_t n,
+                                                           int cur, const double *sc) {
+  const double beta = sc[SC_RZ0 + cur] / sc[SC_RZ0 + (cur ^ 1)];
+  int64_t i = (int64_t)blockIdx.x * CG_THREADS + threadIdx.x;
+  if (i < n) p[i] = z[i] + beta * p[i];
 }
 
 RowArgs row_args(tw_patch *Pt) {
@@ -296,7 +356,7 @@ static int rhs_impl(tw_patch *P, const tw_func *f, double *b, cudaStream_t s) {
     TW_LAUNCH();
   }
   if (P->ncutrows > 0) {
-    k_rhs_cut<<<(P->ncutrows + 63) / 64, 64, 0, s>>>(row_args(P), F, P->cutrows, P->ncutrows, FC, b);
+    k_rhs_cut<<<(P->ncutrows + 3) / 4, 128, 0, s>>>(row_args(P), F, P->cutrows, P->ncutrows, FC, b);
     TW_LAUNCH();
   }
   return check_cuda(cudaGetLastError(), "tw_rhs");
@@ -315,7 +375,31 @@ int rhs_launch(tw_patch *P, const tw_func *f, double *b, cudaStream_t s) {
   return rc;
 }
 
-// CG on M_s x = b for a device b (n_rows); x is overwritten
+struct CgBufs {
+  const int64_t *rp;
+  const int32_t *col;
+  const double *ms, *dinv;
+  double *u, *r, *z, *p, *q;
+  double *part, *sc;
+  unsigned *ticket;
+  int64_t n;
+};
+
+// iteration `it` of the three-launch CG step
+static void cg_iteration(const CgBufs &B, int it, cudaStream_t s) {
+  const int cur = it & 1;
+  const unsigned gw = (unsigned)((B.n * CG_LPR + CG_THREADS - 1) / CG_THREADS);
+  const unsigned ge = (unsigned)((B.n + CG_THREADS - 1) / CG_THREADS);
+  k_cg_spmv<<<gw, CG_THREADS, 0, s>>>(B.rp, B.col, B.ms, B.p, B.q, B.n, B.part, B.ticket, B.sc);
+  k_cg_update1<<<ge, CG_THREADS, 0, s>>>(B.p, B.q, B.dinv, B.u, B.r, B.z, B.n, cur, B.part,
+                                         B.ticket, B.sc);
+  k_cg_update2<<<ge, CG_THREADS, 0, s>>>(B.z, B.p, B.n, cur, B.sc);
+}
+
+// CG on M_s x = b for a device b (n_rows); x is overwritten.  Iterations run in
+// chunks of CG_CHUNK replayed from a CUDA graph (captured once per call on a
+// private stream, launched on s); the residual is read back after each chunk.
+#define CG_CHUNK 8
 static int cg_core(tw_patch *P, const int64_t *rp, const int32_t *col, const double *val,
                    const double *b, double *u, double tol, int maxit, int *iters, double *relres,
                    cudaStream_t s) {
@@ -325,50 +409,81 @@ static int cg_core(tw_patch *P, const int64_t *rp, const int32_t *col, const dou
     if (relres) *relres = 0.0;
     return TW_OK;
   }
-  double *buf = (double *)dalloc(P, sizeof(double) * (5 * n + DOT_BLOCKS + 8));
+  const int64_t gw = (n * CG_LPR + CG_THREADS - 1) / CG_THREADS;  // the largest grid
+  double *buf = (double *)dalloc(P, sizeof(double) * (5 * n + 2 * gw + SC_N));
   int64_t *perm = (int64_t *)dalloc(P, sizeof(int64_t) * (nnz + 1));
   double *ms = (double *)dalloc(P, sizeof(double) * (nnz + 1));
-  if (!buf || !perm || !ms) return TW_ENOMEM;
-  double *r = buf, *z = r + n, *p = z + n, *q = p + n, *dinv = q + n;
-  double *part = dinv + n, *sc = part + DOT_BLOCKS;
+  unsigned *ticket = (unsigned *)dalloc(P, sizeof(unsigned) * 2);
+  if (!buf || !perm || !ms || !ticket) return TW_ENOMEM;
+  CgBufs B;
+  B.rp = rp;
+  B.col = col;
+  B.ms = ms;
+  B.n = n;
+  B.u = u;
+  B.r = buf;
+  B.z = B.r + n;
+  B.p = B.z + n;
+  B.q = B.p + n;
+  double *dinv = B.q + n;
+  B.dinv = dinv;
+  B.part = dinv + n;
+  B.sc = B.part + 2 * gw;
+  B.ticket = ticket;
   int rc = 0;
+  cudaMemsetAsync(ticket, 0, sizeof(unsigned) * 2, s);
   unsigned gb = (unsigned)((n + 255) / 256);
   k_perm<<<gb, 256, 0, s>>>(rp, col, n, perm);
   TW_LAUNCH();
   k_msym<<<gb, 256, 0, s>>>(rp, col, val, perm, n, ms, dinv);
   TW_LAUNCH();
-  k_cg_init<<<gb, 256, 0, s>>>(b, dinv, u, r, z, p, n);
+  k_cg_init<<<(unsigned)((n + CG_THREADS - 1) / CG_THREADS), CG_THREADS, 0, s>>>(
+      b, dinv, u, B.r, B.z, B.p, n, B.part, ticket, B.sc);
   TW_LAUNCH();
-  dot(r, z, n, part, sc + S_RZ, s);
-  dot(b, b, n, part, sc + S_BB, s);
-  double hb[5];
-  cudaMemcpyAsync(hb, sc, sizeof(hb), cudaMemcpyDeviceToHost, s);
+  double hs[SC_N];
+  cudaMemcpyAsync(hs, B.sc, sizeof(hs), cudaMemcpyDeviceToHost, s);
   if ((rc = check_cuda(cudaStreamSynchronize(s), "tw_l2_project"))) return rc;
-  double bn = sqrt(hb[S_BB]);
+  double bn = sqrt(hs[SC_BB]);
   double rel = bn > 0 ? 1.0 : 0.0;
   int it = 0;
-  unsigned gs = (unsigned)((n * 32 + 255) / 256);
-  const int CHECK = 8;
-  while (rel > tol && it < maxit) {
-    int nstep = maxit - it < CHECK ? maxit - it : CHECK;
-    for (int k = 0; k < nstep; k++) {
-      k_spmv<<<gs, 256, 0, s>>>(rp, col, ms, p, q, n);
-      TW_LAUNCH();
-      dot(p, q, n, part, sc + S_PQ, s);
-      k_cg_update1<<<gb, 256, 0, s>>>(sc, p, q, dinv, u, r, z, n);
-      TW_LAUNCH();
-      dot(r, z, n, part, sc + S_RZN, s);
-      k_cg_update2<<<gb, 256, 0, s>>>(sc, z, p, n);
-      TW_LAUNCH();
-      k_cg_roll<<<1, 1, 0, s>>>(sc);
-      TW_LAUNCH();
+  cudaGraphExec_t exec = nullptr;
+  if (rel > tol && maxit >= CG_CHUNK) {
+    // capture CG_CHUNK iterations starting at an even index (the parity
+    // pattern of the scalars repeats every two iterations)
+    cudaStream_t cap;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) {
+      e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        for (int k = 0; k < CG_CHUNK; k++) cg_iteration(B, k, cap);
+        e = cudaStreamEndCapture(cap, &graph);
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+      cudaStreamDestroy(cap);
     }
-    it += nstep;
-    dot(r, r, n, part, sc + S_RR, s);
-    cudaMemcpyAsync(hb, sc, sizeof(hb), cudaMemcpyDeviceToHost, s);
-    if ((rc = check_cuda(cudaStreamSynchronize(s), "tw_l2_project"))) return rc;
-    rel = bn > 0 ? sqrt(hb[S_RR]) / bn : 0.0;
+    if ((rc = check_cuda(e, "tw_l2_project: CG graph"))) return rc;
   }
+  while (rel > tol && it < maxit) {
+    int nstep = maxit - it < CG_CHUNK ? maxit - it : CG_CHUNK;
+    if (nstep == CG_CHUNK && exec && (it & 1) == 0) {
+      rc = check_cuda(cudaGraphLaunch(exec, s), "tw_l2_project: CG chunk");
+      g_launches += 3 * CG_CHUNK;
+    } else {
+      for (int k = 0; k < nstep; k++) {
+        cg_iteration(B, it + k, s);
+        g_launches += 3;
+      }
+    }
+    if (rc) break;
+    it += nstep;
+    cudaMemcpyAsync(hs, B.sc, sizeof(hs), cudaMemcpyDeviceToHost, s);
+    if ((rc = check_cuda(cudaStreamSynchronize(s), "tw_l2_project"))) break;
+    rel = bn > 0 ? sqrt(hs[SC_RR0 + ((it - 1) & 1)]) / bn : 0.0;
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (rc) return rc;
   if (iters) *iters = it;
   if (relres) *relres = rel;
   if (rel > tol) {
@@ -521,7 +636,7 @@ extern "C" int tw_rhs_static(tw_patch *P, const tw_func *f, double *b, void *str
     TW_LAUNCH();
   }
   if (P->ncutrows > 0) {
-    k_rhs_cut<<<(P->ncutrows + 63) / 64, 64, 0, s>>>(row_args(P), F, P->cutrows, P->ncutrows, scr,
+    k_rhs_cut<<<(P->ncutrows + 3) / 4, 128, 0, s>>>(row_args(P), F, P->cutrows, P->ncutrows, scr,
                                                      b);
     TW_LAUNCH();
   }
