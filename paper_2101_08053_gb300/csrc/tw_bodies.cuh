@@ -121,7 +121,9 @@ struct CutSmem {
   double Tg[P1 * P1];
   int rk[2][TW_RC];
   int nr[2], nnest[2], nest[2][TW_RC];
-  int wcnt[8];
+  const double *eM[P1 * P1];  // per support element: its matrix row of this test function
+  int jact[W * W];            // active index of each row entry (-1: none)
+  unsigned msk[8];            // ballots of the active entries, one per 32 entries
 };
 
 template <int P, typename OutT>
@@ -269,23 +271,41 @@ __device__ void cutrow_item(const RowArgs &a, int g, int32_t *__restrict__ col,
   // ---- elements of the support: Gauss on regular (outside R), cut rule on cut ----
   const int p1 = P1;
   if (a.gmat || kind == 1) {
-    // every element matrix is precomputed: one owner thread per row entry adds
-    // its elements' terms in (e2, e1) order, with no barrier per element
-    constexpr int P4 = P1 * P1 * P1 * P1;
+    // every element matrix is precomputed.  First the support elements' rows
+    // of this test function (one thread per element), then one owner thread
+    // per row entry adds its elements' terms in (e2, e1) order: independent
+    // loads, no barrier per element
+    constexpr int P2 = P1 * P1;
+    for (int t = tid; t < P2; t += blockDim.x) {
+      const int e1 = i1 - P + t % P1, e2 = i2 - P + t / P1;
+      const double *Me = nullptr;
+      if (e1 >= lo1 && e1 <= hi1 && e2 >= lo2 && e2 <= hi2) {
+        const int e = e2 * A.nel + e1;
+        const uint8_t st = a.estate[e];
+        const bool inR = e1 >= r0[0] && e1 <= r1[0] && e2 >= r0[1] && e2 <= r1[1];
+        const size_t rowoff = (size_t)((i2 - e2) * P1 + (i1 - e1)) * P2;
+        if (st == TW_ELEM_REGULAR && kind != 1 && !inR)
+          Me = a.gmat + (size_t)a.gslot[e] * P2 * P2 + rowoff;
+        else if (st == TW_ELEM_CUT)
+          Me = a.cut_M + (size_t)a.cut_slot[e] * P2 * P2 + rowoff;
+      }
+      S.eM[t] = Me;
+    }
+    __syncthreads();
     for (int t = tid; t < W * W; t += blockDim.x) {
       const int q2 = t / W, q1 = t % W;
-      const int j1 = i1 - P + q1, j2 = i2 - P + q2;
       double s = S.acc[t];
-      for (int e2 = max(lo2, j2 - P); e2 <= min(hi2, j2); e2++)
-        for (int e1 = max(lo1, j1 - P); e1 <= min(hi1, j1); e1++) {
-          const int e = e2 * A.nel + e1;
-          const uint8_t st = a.estate[e];
-          const bool inR = e1 >= r0[0] && e1 <= r1[0] && e2 >= r0[1] && e2 <= r1[1];
-          const double *Me = nullptr;
-          if (st == TW_ELEM_REGULAR && kind != 1 && !inR) Me = a.gmat + (size_t)a.gslot[e] * P4;
-          else if (st == TW_ELEM_CUT) Me = a.cut_M + (size_t)a.cut_slot[e] * P4;
-          if (Me) s += Me[((i2 - e2) * p1 + (i1 - e1)) * p1 * p1 + (j2 - e2) * p1 + (j1 - e1)];
+      // support element u (offset from i - P) covers entry q iff u <= q <= u + P
+#pragma unroll
+      for (int u2 = 0; u2 <= P; u2++) {
+        if (u2 < q2 - P || u2 > q2) continue;
+#pragma unroll
+        for (int u1 = 0; u1 <= P; u1++) {
+          if (u1 < q1 - P || u1 > q1) continue;
+          const double *Me = S.eM[u2 * P1 + u1];
+          if (Me) s += Me[(q2 - u2) * P1 + (q1 - u1)];
         }
+      }
       S.acc[t] = s;
     }
     __syncthreads();
@@ -337,29 +357,31 @@ __device__ void cutrow_item(const RowArgs &a, int g, int32_t *__restrict__ col,
     }
 
   // ---- write the row: active columns in ascending order (R11) ----
-  // an entry's position = active entries before it: warp ballots + the
-  // counts of the warps before (the block has at least NW warps)
+  // an entry's position = active entries before it, from one ballot per 32
+  // entries (blockDim is a multiple of 32, so a warp's lanes share a ballot)
   constexpr int NW = (W * W + 31) / 32;
-  static_assert(NW <= 8, "row entries exceed eight warps");
-  const int lane = tid & 31, wid = tid >> 5;
-  int ok = 0, jact = -1;
-  unsigned msk = 0u;
-  if (wid < NW) {
-    if (tid < W * W) {
-      const int r2 = tid / W, q1 = tid % W;
+  static_assert(NW <= 8, "row entries exceed eight ballots");
+  const int lane = tid & 31;
+  for (int t = tid; t < NW * 32; t += blockDim.x) {
+    int jact = -1;
+    if (t < W * W) {
+      const int r2 = t / W, q1 = t % W;
       const int j1 = i1 - P + q1, j2 = i2 - P + r2;
       if (j1 >= 0 && j1 < n1 && j2 >= 0 && j2 < B.n) jact = a.act[j2 * n1 + j1];
-      ok = jact >= 0;
+      S.jact[t] = jact;
     }
-    msk = __ballot_sync(0xffffffffu, ok);
-    if (lane == 0) S.wcnt[wid] = __popc(msk);
+    const unsigned m = __ballot_sync(0xffffffffu, jact >= 0);
+    if (lane == 0) S.msk[t >> 5] = m;
   }
   __syncthreads();
-  if (ok) {
-    int ps = __popc(msk & ((1u << lane) - 1u));
-    for (int w = 0; w < wid; w++) ps += S.wcnt[w];
-    const int64_t base = a.rp[a.act[g]];
-    val[base + ps] = (OutT)S.acc[tid];
+  const int64_t base = a.rp[a.act[g]];
+  for (int t = tid; t < W * W; t += blockDim.x) {
+    const int jact = S.jact[t];
+    if (jact < 0) continue;
+    const int w = t >> 5;
+    int ps = __popc(S.msk[w] & ((1u << (t & 31)) - 1u));
+    for (int k = 0; k < w; k++) ps += __popc(S.msk[k]);
+    val[base + ps] = (OutT)S.acc[t];
     col[base + ps] = jact;
   }
   __syncthreads();  // smem reused by the next item

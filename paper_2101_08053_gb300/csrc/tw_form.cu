@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(256) k_interior(Dir A, Dir B, const double *__
 }
 
 template <int P, typename OutT>
-__global__ void __launch_bounds__(256) k_cutrows(RowArgs a, const int32_t *__restrict__ rows,
+__global__ void __launch_bounds__(128) k_cutrows(RowArgs a, const int32_t *__restrict__ rows,
                                                  int32_t *__restrict__ col,
                                                  OutT *__restrict__ val) {
   __shared__ __align__(16) char smem[sizeof(CutSmem<P>)];
@@ -96,9 +96,9 @@ static int launch_form(tw_patch *Pt, int precision, int64_t *rp, int32_t *col, v
     ra.flag = Pt->flag;
     int ps = prof_start(s);
     if (precision == TW_PREC_FP32)
-      k_cutrows<P, float><<<Pt->ncutrows, 256, 0, s>>>(ra, Pt->cutrows, col, (float *)valv);
+      k_cutrows<P, float><<<Pt->ncutrows, 128, 0, s>>>(ra, Pt->cutrows, col, (float *)valv);
     else
-      k_cutrows<P, double><<<Pt->ncutrows, 256, 0, s>>>(ra, Pt->cutrows, col, val);
+      k_cutrows<P, double><<<Pt->ncutrows, 128, 0, s>>>(ra, Pt->cutrows, col, val);
     prof_stop(ps, TW_STAGE_CUTROWS, s);
     TW_LAUNCH();
   }

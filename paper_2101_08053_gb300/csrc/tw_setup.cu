@@ -507,8 +507,10 @@ __global__ void k_curve_features(Curve C, double *feat, int *nfeat, int fcap, in
 }
 
 // One block of 64 threads per cut element.  Pass 0 (pts == NULL) counts the
-// element's points into cnt[ci], pass 1 writes them from off[ci] on, in the
-// order piece, Gauss line, interval, inner Gauss point.  The element's edge
+// element's points into cnt[ci] and, given scr, also writes them to the
+// element's slot of cap points there (elements with more points leave cnt >
+// cap and are counted in *ovf); pass 1 writes them from off[ci] on.  Order:
+// piece, Gauss line, interval, inner Gauss point.  The element's edge
 // crossings come from the knot-line table (hits/nh of k_line_hits), the
 // tangent points and joints from the curve-wide feature list; only the Gauss
 // lines are solved here.  The visibility of a line's first interval is that of
@@ -519,7 +521,8 @@ __global__ void __launch_bounds__(TW_CUT_THREADS)
     k_cut_rule(Curve C, Dir A, Dir B, const int32_t *cut_list, int ncut, const double *qgx,
                const double *qgw, int q, const double *hits, const int *nh, const double *feat,
                const int *nfeat, int fcap, int64_t *cnt, const int64_t *off, double *pts,
-               int32_t *cut_o, int *flag) {
+               int32_t *cut_o, int *flag, double *scr, int cap,
+               unsigned long long *ovf) {
   const int ci = blockIdx.x;
   if (ci >= ncut) return;
   const int tid = threadIdx.x;
@@ -647,15 +650,18 @@ __global__ void __launch_bounds__(TW_CUT_THREADS)
       __syncthreads();
     }
     int64_t mine = base + scan[tid] - count;
-    if (pts && count > 0) {
-      int64_t w0 = base0 + mine;
+    double *dst = nullptr;
+    if (pts) dst = pts + 3 * (base0 + mine);
+    else if (scr && mine + count <= cap) dst = scr + 3 * ((int64_t)ci * cap + mine);
+    if (dst && count > 0) {
+      int64_t w0 = 0;
       for (int k = 0; k <= n; k++) {
         double u0 = h[k], u1 = h[k + 1];
         if (!(u1 > u0) || !(vis0 ^ (k & 1))) continue;
         for (int hh = 0; hh < q; hh++) {
           double u = u0 + (u1 - u0) * 0.5 * (qgx[hh] + 1.0);
           double w = ws * qgw[hh] * 0.5 * (u1 - u0);
-          double *o3 = pts + 3 * w0;
+          double *o3 = dst + 3 * w0;
           o3[0] = o == 0 ? s : u;
           o3[1] = o == 0 ? u : s;
           o3[2] = w;
@@ -666,7 +672,21 @@ __global__ void __launch_bounds__(TW_CUT_THREADS)
     base += scan[TW_CUT_THREADS - 1];
     __syncthreads();
   }
-  if (cnt && tid == 0) cnt[ci] = base;
+  if (cnt && tid == 0) {
+    cnt[ci] = base;
+    if (scr && base > cap) atomicAdd(ovf, 1ull);
+  }
+}
+
+// copy each element's points from its scratch slot to the packed array
+__global__ void k_cut_gather(const int64_t *off, int ncut, int cap, const double *scr,
+                             double *pts) {
+  const int ci = blockIdx.x;
+  if (ci >= ncut) return;
+  const int64_t n3 = 3 * (off[ci + 1] - off[ci]);
+  const double *src = scr + 3 * (int64_t)ci * cap;
+  double *dst = pts + 3 * off[ci];
+  for (int64_t k = threadIdx.x; k < n3; k += blockDim.x) dst[k] = src[k];
 }
 
 // per cut point: basis values in both directions and w * c
@@ -1112,12 +1132,25 @@ static void launch_cut_matrices(tw_patch *P, cudaStream_t st) {
 //   M[(a1,a2)][(b1,b2)] = sum_g2 T[a1][b1][g2] w2 B_a2 B_b2.
 template <int P>
 __global__ void __launch_bounds__(256) k_gauss_matrices(Dir A, Dir B, const int32_t *glist, int ng,
-                                                       const double *gc, double *M) {
+                                                       const double *gc, const uint8_t *fstate,
+                                                       int method, double *M) {
   constexpr int P1 = P + 1, NL = P1 * P1;
   const int sl = blockIdx.x;
   if (sl >= ng) return;
   const int e = glist[sl], e1 = e % A.nel, e2 = e / A.nel;
   __shared__ double T[P1 * P1 * P1];
+  // only the rows of test functions formed by the cut-row kernel are ever
+  // read (cut functions; every active function for the Gauss method)
+  __shared__ int need[NL];
+  __shared__ int nneed;
+  if (threadIdx.x == 0) {
+    int n = 0;
+    for (int a = 0; a < NL; a++) {
+      const uint8_t st = fstate[(size_t)(e2 + a / P1) * A.n + (e1 + a % P1)];
+      if (st != TW_FUNC_EXTERIOR && (method == TW_METHOD_GAUSS || st == TW_FUNC_CUT)) need[n++] = a;
+    }
+    nneed = n;
+  }
   const double h1 = 0.5 * (A.bp[e1 + 1] - A.bp[e1]), h2 = 0.5 * (B.bp[e2 + 1] - B.bp[e2]);
   const double *GB1 = A.GB + (size_t)e1 * NL;  // [g][a]
   const double *GB2 = B.GB + (size_t)e2 * NL;
@@ -1132,20 +1165,20 @@ __global__ void __launch_bounds__(256) k_gauss_matrices(Dir A, Dir B, const int3
   }
   __syncthreads();
   double *Me = M + (size_t)sl * NL * NL;
-  for (int id = threadIdx.x; id < NL * NL; id += blockDim.x) {
-    const int a = id / NL, b = id % NL;
+  for (int id = threadIdx.x; id < nneed * NL; id += blockDim.x) {
+    const int a = need[id / NL], b = id % NL;
     const int a1 = a % P1, a2 = a / P1, b1 = b % P1, b2 = b / P1;
     double s = 0.0;
 #pragma unroll
     for (int g2 = 0; g2 < P1; g2++)
       s = fma(T[(a1 * P1 + b1) * P1 + g2], B.gw[g2] * h2 * GB2[g2 * P1 + a2] * GB2[g2 * P1 + b2], s);
-    Me[id] = s;
+    Me[a * NL + b] = s;
   }
 }
 
 static void launch_gauss_matrices(tw_patch *P, const int32_t *glist, cudaStream_t st) {
   switch (P->p) {
-#define TW_GM(PP) case PP: k_gauss_matrices<PP><<<P->ngslot, 256, 0, st>>>(P->d[0], P->d[1], glist, P->ngslot, P->gc, P->gmat); break;
+#define TW_GM(PP) case PP: k_gauss_matrices<PP><<<P->ngslot, 256, 0, st>>>(P->d[0], P->d[1], glist, P->ngslot, P->gc, P->fstate, P->method, P->gmat); break;
     TW_GM(1) TW_GM(2) TW_GM(3) TW_GM(4) TW_GM(5) TW_GM(6)
 #undef TW_GM
   }
@@ -1372,17 +1405,26 @@ int build_tables(tw_patch *P) {
       launch_gauss_matrices(P, glist, st);
     }
   }
-  // cut-element rules: count, scan, fill
+  // cut-element rules: one pass counts the points and writes them to a slot
+  // of `cap` points per element; after the scan they are packed.  Only if an
+  // element overflows its slot is the rule evaluated a second time in place.
+  const int cap = 16 * P->qc * P->qc;
+  double *cscr = nullptr;
+  P->cut_o = (int32_t *)dalloc(P, sizeof(int32_t) * (P->ncut + 1));
+  if (!P->cut_o) return TW_ENOMEM;
+  cudaMemsetAsync(tot64 + 2, 0, sizeof(int64_t), st);
   if (P->ncut > 0) {
-    k_cut_rule<<<P->ncut, TW_CUT_THREADS, 0, st>>>(P->curve, A, B, P->cut_list, P->ncut, qgx,
-                                                   qgw, P->qc, lh, lnh, feat, nfeat, fcap, ccount,
-                                                   nullptr, nullptr, nullptr, P->flag);
+    cscr = (double *)dalloc(P, sizeof(double) * 3 * (size_t)P->ncut * cap);
+    if (!cscr) return TW_ENOMEM;
+    k_cut_rule<<<P->ncut, TW_CUT_THREADS, 0, st>>>(
+        P->curve, A, B, P->cut_list, P->ncut, qgx, qgw, P->qc, lh, lnh, feat, nfeat, fcap, ccount,
+        nullptr, nullptr, P->cut_o, P->flag, cscr, cap, (unsigned long long *)(tot64 + 2));
     TW_LAUNCH();
     if ((rc = exclusive_scan_i64(ccount, P->cut_off, P->ncut, tot64 + 1, st, P))) return rc;
     k_set_last<<<1, 1, 0, st>>>(P->cut_off, P->ncut, tot64 + 1);
     TW_LAUNCH();
   }
-  int64_t h64[2] = {0, 0};
+  int64_t h64[3] = {0, 0, 0};
   cudaMemcpyAsync(h64, tot64, sizeof(h64), cudaMemcpyDeviceToHost, st);
   if ((rc = read_flag(P, "cut rules"))) return rc;
   P->nnz = h64[0];
@@ -1390,13 +1432,16 @@ int build_tables(tw_patch *P) {
   P->cut_pts = (double *)dalloc(P, sizeof(double) * (3 * P->ncutpts + 1));
   P->cut_wc = (double *)dalloc(P, sizeof(double) * (P->ncutpts + 1));
   P->cut_B = (double *)dalloc(P, sizeof(double) * (2 * P->ncutpts * p1 + 1));
-  P->cut_o = (int32_t *)dalloc(P, sizeof(int32_t) * (P->ncut + 1));
   P->cut_M = (double *)dalloc(P, sizeof(double) * ((size_t)P->ncut * p1 * p1 * p1 * p1 + 1));
-  if (!P->cut_pts || !P->cut_wc || !P->cut_B || !P->cut_o || !P->cut_M) return TW_ENOMEM;
+  if (!P->cut_pts || !P->cut_wc || !P->cut_B || !P->cut_M) return TW_ENOMEM;
   if (P->ncut > 0) {
-    k_cut_rule<<<P->ncut, TW_CUT_THREADS, 0, st>>>(P->curve, A, B, P->cut_list, P->ncut, qgx,
-                                                   qgw, P->qc, lh, lnh, feat, nfeat, fcap, nullptr,
-                                                   P->cut_off, P->cut_pts, P->cut_o, P->flag);
+    if (h64[2] == 0) {
+      k_cut_gather<<<P->ncut, 128, 0, st>>>(P->cut_off, P->ncut, cap, cscr, P->cut_pts);
+    } else {
+      k_cut_rule<<<P->ncut, TW_CUT_THREADS, 0, st>>>(
+          P->curve, A, B, P->cut_list, P->ncut, qgx, qgw, P->qc, lh, lnh, feat, nfeat, fcap,
+          nullptr, P->cut_off, P->cut_pts, P->cut_o, P->flag, nullptr, 0, nullptr);
+    }
     TW_LAUNCH();
     k_cut_point_tables<<<P->ncut, 128, 0, st>>>(P->geo, A, B, P->cut_list, P->cut_off, P->ncut,
                                                 P->cut_pts, P->cut_B, P->cut_wc);
