@@ -383,6 +383,9 @@ def run_ours(args, rank, world, local_rank):
     adjoint = None
     if not args.no_adjoint:
         adjoint = run_adjoint(api, torch, args, stream)
+    precision = None
+    if not args.no_precision:
+        precision = run_precision(api, torch, args, stream, flush)
 
     # roofline of the dominant kernel (interior rows, FP64 DFMA-bound)
     flops = 0.0
@@ -404,7 +407,7 @@ def run_ours(args, rank, world, local_rank):
         "value": value, "ms": ms, "nnz_step": nnz_step, "infos": infos, "launches": launches,
         "clocks": clocks, "e2e_ms": e2e_ms, "h2d": h2d, "d2h": d2h, "stage_ms": stage_ms,
         "stage_ms_batched": stage_ms_batched, "modes": modes, "batched": batched,
-        "adjoint": adjoint,
+        "adjoint": adjoint, "precision": precision,
         "roofline": {"bound": "alu", "kernel": "k_interior (interior rows, WQ + sum factorisation)",
                      "achieved": round(achieved, 4), "peak": peak, "unit": "TFLOP/s",
                      "frac": round(achieved / peak, 4), "traffic": None,
@@ -465,6 +468,80 @@ def run_batched(api, torch, args, stream, streams, dev):
     for P in patches:
         P.close()
     return res
+
+
+def run_precision(api, torch, args, stream, flush):
+    """Precision variant: p = 4 and p = 6, 1024^2 elements, perturbed geometry
+    (c = det J), circular hole r = 0.3, hybrid Gauss.  Per mode: formation time
+    (patch tables resident), the interior-row kernel's share and its CSR write
+    rate, the relative Frobenius error of M against the FP64 GPU form, and the
+    L2 projection of f = sin(pi x) sin(pi y) with that matrix (CG in FP64 on the
+    matrix widened to FP64): its L2 error and its L2 distance from the FP64
+    projection (coefficient vectors are not compared: the cut functions with
+    tiny visible support make them ill-determined)."""
+    f = synth.func_sinsin()
+    out = {}
+    for p in (4, 6):
+        spec = synth.config3(p=p)
+        P = api.Patch(spec)
+        res = {"n_rows": P.n_rows, "nnz": P.nnz, "interior_rows": P.n_interior}
+        _, _, act = P.states()
+        act = act.long()
+        ref = None
+        g64 = None
+        n64 = None
+        for mode in ("fp64", "fp32x2", "fp32"):
+            csr = P.form_mass(mode)
+            torch.cuda.synchronize()
+            api.profile_enable(True)
+            for st in ("interior", "cutrows"):
+                api.profile_read(st)
+            ts = []
+            for _ in range(max(1, args.steps)):
+                flush.fill_(1.0)
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                P.form_mass(mode, out=(csr[0], csr[1], csr[2]))
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            im, ic = api.profile_read("interior")
+            cm, cc = api.profile_read("cutrows")
+            api.profile_enable(False)
+            ms = float(np.mean(ts))
+            vb = 4 if mode == "fp32" else 8
+            r = {"form_ms": round(ms, 3), "form_nnz_per_s": P.nnz / (ms * 1e-3),
+                 "interior_kernel_ms": round(im / max(1, ic), 4),
+                 "cutrows_ms": round(cm / max(1, cc), 4)}
+            val = csr[2][:P.nnz].double()
+            if ref is None:
+                ref = val.clone()
+            r["rel_frobenius_vs_fp64_gpu"] = float(torch.linalg.norm(val - ref) /
+                                                   torch.linalg.norm(ref))
+            u, it, rel = P.l2_project(f, (csr[0], csr[1], val), tol=1e-10, maxit=4000,
+                                      check=False)
+            L, _ = P.loss(u, f)
+            r["l2_error"] = math.sqrt(max(float(L.item()), 0.0))
+            r["cg_iterations"] = it
+            r["cg_relres"] = rel
+            if g64 is None:
+                # the FP64 projection as a spline of the patch's own space
+                coef = torch.zeros(P.n1 * P.n2, dtype=torch.float64, device=u.device)
+                on = act >= 0
+                coef[on] = u[act[on]]
+                g64 = {"kind": "spline", "p": spec["p"], "knots": spec["knots"],
+                       "coef": coef.view(P.n2, P.n1).cpu().numpy()}
+                n64 = math.sqrt(float(P.loss(torch.zeros_like(u), g64)[0].item()))
+            r["l2_rel_diff_vs_fp64_projection"] = math.sqrt(
+                max(float(P.loss(u, g64)[0].item()), 0.0)) / n64
+            r["csr_write_bytes_per_nnz"] = vb + 4
+            res[mode] = r
+            del csr, val
+        out["p%d" % p] = res
+        P.close()
+    return out
 
 
 def run_adjoint(api, torch, args, stream):
@@ -564,6 +641,8 @@ def main():
     ap.add_argument("--batched-patches", type=int, default=512)
     ap.add_argument("--no-adjoint", action="store_true",
                     help="skip the density-gradient (adjoint) section")
+    ap.add_argument("--no-precision", action="store_true",
+                    help="skip the 1024^2 precision-variant section")
     args = ap.parse_args()
     if args.case:
         select_case(args.case)
@@ -624,7 +703,8 @@ def main():
                 "cpu_baseline": cpu, "stage_ms_per_step_serial": r["stage_ms"],
                 "stage_ms_per_step_batched": r["stage_ms_batched"],
                 "precision_modes_formation_only": r["modes"],
-                "batched_config4": r["batched"], "adjoint_config5": r["adjoint"]}
+                "batched_config4": r["batched"], "adjoint_config5": r["adjoint"],
+                "precision_config3": r["precision"]}
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(256) k_batch(const BatchPatch *__restrict__ bp
 static size_t batch_smem(int prec, int tmax) {
   size_t s = sizeof(CutSmem<TW_MAXP>);
   size_t i64 = interior_smem(TW_MAXP, tmax);
-  size_t i32 = interior32_smem(TW_MAXP, tmax);
+  size_t i32 = interior32_smem(TW_MAXP, tmax, prec == TW_PREC_FP32X2);
   s = std::max(s, prec == TW_PREC_FP64 ? i64 : i32);
   return (s + 15) / 16 * 16;
 }

@@ -5,14 +5,20 @@
 // any degree and kind one after the other.
 #pragma once
 
+#include <type_traits>
+
 #include "tw_internal.cuh"
 
 namespace tw {
 
-// smem of one interior tile: Y[W * kmax] | V2s[TW_QMAX * W] | cr2[W] | flag
+// smem of one interior tile: Y[W * kmax] | V2s[TW_QMAX * W] | the tile's
+// outputs [T][W][W] (written out row by row with coalesced stores) | cr2[W] | flag
 __host__ __device__ constexpr int interior_kmax(int P, int T) { return (2 * T + 4 * P + 4) | 1; }
+__host__ __device__ constexpr size_t interior_out_off(int P, int T) {
+  return sizeof(double) * ((size_t)(2 * P + 1) * interior_kmax(P, T) + TW_QMAX * (2 * P + 1));
+}
 __host__ __device__ constexpr size_t interior_smem(int P, int T) {
-  return sizeof(double) * ((size_t)(2 * P + 1) * interior_kmax(P, T) + TW_QMAX * (2 * P + 1)) +
+  return interior_out_off(P, T) + sizeof(double) * (size_t)T * (2 * P + 1) * (2 * P + 1) +
          sizeof(int) * (2 * P + 2);
 }
 
@@ -25,7 +31,8 @@ __device__ void interior_tile(const Dir &A, const Dir &B, const double *__restri
   const int KMAX = interior_kmax(P, T);
   double *Y = (double *)smem;
   double *V2s = Y + W * KMAX;
-  int *cr2 = (int *)(V2s + TW_QMAX * W);
+  double *os = (double *)(smem + interior_out_off(P, T));  // [t][r2][r1]
+  int *cr2 = (int *)(os + (size_t)T * W * W);
   int *anyintp = cr2 + W;
   const int i1b = min(A.n, i1a + T);
   const int n1 = A.n;
@@ -58,7 +65,6 @@ __device__ void interior_tile(const Dir &A, const Dir &B, const double *__restri
   // 2(P+1) points of supp B_i1 and adds each point's value into the P+1
   // outputs whose trial function lives on the point's element, so every lane
   // issues the same (P+1)*2*(P+1) DFMAs.  Other rows use the per-output loop.
-  const int lo2 = max(0, i2 - P);
   const int NR = (i1b - i1a) * W;
   for (int idx = threadIdx.x; idx < NR; idx += blockDim.x) {
     const int t = idx / W, r2 = idx - t * W;
@@ -68,7 +74,7 @@ __device__ void interior_tile(const Dir &A, const Dir &B, const double *__restri
     if (fstate[g] != TW_FUNC_INTERIOR || j2 < 0 || j2 >= B.n) continue;
     const double *y = Y + r2 * KMAX + (A.qbeg[i1] - kA);
     const double *v = A.V + ((size_t)i1 * A.qmax) * W;
-    const int64_t rowbase = rp[act[g]];
+    double *o = os + ((size_t)t * W + r2) * W;
     if (i1 >= P + 1 && i1 <= A.nel - 2) {
       double acc[W];
 #pragma unroll
@@ -83,16 +89,9 @@ __device__ void interior_tile(const Dir &A, const Dir &B, const double *__restri
           for (int a = 0; a <= P; a++) acc[el + a] = fma(v[c1 * W + el + a], yv, acc[el + a]);
         }
       }
-      double *out = val + rowbase + (int64_t)(j2 - lo2) * W;
-      int32_t *oc = col + rowbase + (int64_t)(j2 - lo2) * W;
-      const int32_t *arow = act + j2 * n1 + (i1 - P);
 #pragma unroll
-      for (int r = 0; r < W; r++) {
-        out[r] = acc[r];
-        oc[r] = arow[r];
-      }
+      for (int r = 0; r < W; r++) o[r] = acc[r];
     } else {
-      const int lo1 = max(0, i1 - P), w1 = min(n1 - 1, i1 + P) - lo1 + 1;
       for (int r1 = 0; r1 < W; r1++) {
         const int j1 = i1 - P + r1;
         if (j1 < 0 || j1 >= n1) continue;
@@ -100,10 +99,25 @@ __device__ void interior_tile(const Dir &A, const Dir &B, const double *__restri
         const int lo = cr & 0xffff, hi = cr >> 16;
         double s = 0.0;
         for (int c1 = lo; c1 < hi; c1++) s = fma(v[c1 * W + r1], y[c1], s);
-        const int64_t pos = rowbase + (int64_t)(j2 - lo2) * w1 + (j1 - lo1);
-        val[pos] = s;
-        col[pos] = act[j2 * n1 + j1];
+        o[r1] = s;
       }
+    }
+  }
+  __syncthreads();
+  // write out: one warp per row of the tile, consecutive lanes on consecutive
+  // CSR positions (j2 major, j1 minor over the valid part of the band)
+  const int nw = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int lo2 = max(0, i2 - P), w2 = min(B.n - 1, i2 + P) - lo2 + 1, d2 = lo2 - (i2 - P);
+  for (int t = wid; t < i1b - i1a; t += nw) {
+    const int i1 = i1a + t, g = i2 * n1 + i1;
+    if (fstate[g] != TW_FUNC_INTERIOR) continue;  // the whole warp
+    const int lo1 = max(0, i1 - P), w1 = min(n1 - 1, i1 + P) - lo1 + 1, d1 = lo1 - (i1 - P);
+    const int64_t rowbase = rp[act[g]];
+    const double *src = os + (size_t)t * W * W;
+    for (int k = lane; k < w1 * w2; k += 32) {
+      const int q2 = k / w1, q1 = k - q2 * w1;
+      val[rowbase + k] = src[(q2 + d2) * W + q1 + d1];
+      col[rowbase + k] = act[(lo2 + q2) * n1 + lo1 + q1];
     }
   }
   __syncthreads();  // the tile's smem is reused by the next item
@@ -125,6 +139,75 @@ struct CutSmem {
   int jact[W * W];            // active index of each row entry (-1: none)
   unsigned msk[8];            // ballots of the active entries, one per 32 entries
 };
+
+// a cut row with no region part (hybrid Gauss, or DWQ without a region) whose
+// element matrices are all precomputed: a plain gather of element rows
+__device__ __forceinline__ bool cutrow_is_gather(const RowArgs &a, int g) {
+  if (!a.gmat || a.method == TW_METHOD_NAIVE) return false;
+  return a.method != TW_METHOD_DWQ || a.choice[4 * g] < 0;
+}
+
+// One warp per such row, no block barrier: lanes hold the support elements'
+// matrix rows of this test function in the warp's table `tab`, then own the
+// row entries (lane, lane + 32, ...) and add their elements' terms in (e2, e1)
+// order -- the same sums, in the same order, as cutrow_item.
+template <int P, typename OutT>
+__device__ __forceinline__ void cutrow_gather_warp(const RowArgs &a, int g, int lane,
+                                                   const double **tab,
+                                                   int32_t *__restrict__ col,
+                                                   OutT *__restrict__ val) {
+  constexpr int W = 2 * P + 1, P1 = P + 1, P2 = P1 * P1, NE = (W * W + 31) / 32;
+  const Dir &A = a.A;
+  const Dir &B = a.B;
+  const int n1 = A.n;
+  const int i1 = g % n1, i2 = g / n1;
+  const int lo1 = max(0, i1 - P), hi1 = min(A.nel - 1, i1);
+  const int lo2 = max(0, i2 - P), hi2 = min(B.nel - 1, i2);
+  for (int t = lane; t < P2; t += 32) {
+    const int e1 = i1 - P + t % P1, e2 = i2 - P + t / P1;
+    const double *Me = nullptr;
+    if (e1 >= lo1 && e1 <= hi1 && e2 >= lo2 && e2 <= hi2) {
+      const int e = e2 * A.nel + e1;
+      const uint8_t st = a.estate[e];
+      const size_t rowoff = (size_t)((i2 - e2) * P1 + (i1 - e1)) * P2;
+      if (st == TW_ELEM_REGULAR) Me = a.gmat + (size_t)a.gslot[e] * P2 * P2 + rowoff;
+      else if (st == TW_ELEM_CUT) Me = a.cut_M + (size_t)a.cut_slot[e] * P2 * P2 + rowoff;
+    }
+    tab[t] = Me;
+  }
+  __syncwarp();
+  const int64_t base = a.rp[a.act[g]];
+  int before = 0;  // active entries in the previous chunks of 32
+#pragma unroll
+  for (int k = 0; k < NE; k++) {
+    const int t = k * 32 + lane;
+    int jact = -1;
+    double s = 0.0;
+    if (t < W * W) {
+      const int q2 = t / W, q1 = t % W;
+      const int j1 = i1 - P + q1, j2 = i2 - P + q2;
+      if (j1 >= 0 && j1 < n1 && j2 >= 0 && j2 < B.n) jact = a.act[j2 * n1 + j1];
+#pragma unroll
+      for (int u2 = 0; u2 <= P; u2++) {
+        if (u2 < q2 - P || u2 > q2) continue;
+#pragma unroll
+        for (int u1 = 0; u1 <= P; u1++) {
+          if (u1 < q1 - P || u1 > q1) continue;
+          const double *Me = tab[u2 * P1 + u1];
+          if (Me) s += Me[(q2 - u2) * P1 + (q1 - u1)];
+        }
+      }
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, jact >= 0);
+    if (jact >= 0) {
+      const int ps = before + __popc(m & ((1u << lane) - 1u));
+      val[base + ps] = (OutT)s;
+      col[base + ps] = jact;
+    }
+    before += __popc(m);
+  }
+  __syncwarp();  // tab reused by the warp's next row
+}
 
 template <int P, typename OutT>
 __device__ void cutrow_item(const RowArgs &a, int g, int32_t *__restrict__ col,
@@ -401,9 +484,16 @@ __device__ __forceinline__ void df_fma(float2 a, float2 b, float &sh, float &sl)
   sl = __fadd_rn(sl, __fadd_rn(err, e));
 }
 
+// smem of one FP32-pipe tile: Y | V2s | the tile's outputs (T rows x W^2,
+// written out row by row with coalesced stores; double for the split mode) |
+// cr2 | flag
 __host__ __device__ constexpr int interior32_kmax(int P, int T) { return (2 * T + 4 * P + 4) | 1; }
-__host__ __device__ constexpr size_t interior32_smem(int P, int T) {
-  return sizeof(float2) * ((size_t)(2 * P + 1) * interior32_kmax(P, T) + TW_QMAX * (2 * P + 1)) +
+__host__ __device__ constexpr size_t interior32_out_off(int P, int T) {
+  return sizeof(float2) * ((size_t)(2 * P + 1) * interior32_kmax(P, T) + TW_QMAX * (2 * P + 1));
+}
+__host__ __device__ constexpr size_t interior32_smem(int P, int T, bool split = true) {
+  return interior32_out_off(P, T) +
+         (split ? sizeof(double) : sizeof(float)) * (size_t)T * (2 * P + 1) * (2 * P + 1) +
          sizeof(int) * (2 * P + 2);
 }
 
@@ -415,10 +505,12 @@ __device__ void interior_tile32(const Dir &A, const Dir &B, const float2 *__rest
                                 int32_t *__restrict__ col, void *__restrict__ valv, int i2,
                                 int i1a, int T, char *smem) {
   constexpr int W = 2 * P + 1;
+  using OutT = typename std::conditional<SPLIT, double, float>::type;
   const int KMAX = interior32_kmax(P, T);
   float2 *Y = (float2 *)smem;
   float2 *V2s = Y + W * KMAX;
-  int *cr2 = (int *)(V2s + TW_QMAX * W);
+  OutT *os = (OutT *)(smem + interior32_out_off(P, T));  // [t][r2][r1]
+  int *cr2 = (int *)(os + (size_t)T * W * W);
   int *anyintp = cr2 + W;
   const int i1b = min(A.n, i1a + T);
   const int n1 = A.n;
@@ -448,11 +540,9 @@ __device__ void interior_tile32(const Dir &A, const Dir &B, const float2 *__rest
     Y[r2 * KMAX + kk] = make_float2(sh, sl);
   }
   __syncthreads();
-  // stage 2 (point-major for rows away from the end elements)
-  const int lo2 = max(0, i2 - P);
+  // stage 2 (point-major for rows away from the end elements) into the
+  // tile's output buffer os[t][r2][r1]
   const int NR = (i1b - i1a) * W;
-  double *vald = (double *)valv;
-  float *valf = (float *)valv;
   for (int idx = threadIdx.x; idx < NR; idx += blockDim.x) {
     const int t = idx / W, r2 = idx - t * W;
     const int i1 = i1a + t;
@@ -461,7 +551,7 @@ __device__ void interior_tile32(const Dir &A, const Dir &B, const float2 *__rest
     if (fstate[g] != TW_FUNC_INTERIOR || j2 < 0 || j2 >= B.n) continue;
     const float2 *y = Y + r2 * KMAX + (A.qbeg[i1] - kA);
     const float2 *v = V1f + ((size_t)i1 * A.qmax) * W;
-    const int64_t rowbase = rp[act[g]];
+    OutT *o = os + ((size_t)t * W + r2) * W;
     if (i1 >= P + 1 && i1 <= A.nel - 2) {
       float ah[W], al[W];
 #pragma unroll
@@ -479,16 +569,12 @@ __device__ void interior_tile32(const Dir &A, const Dir &B, const float2 *__rest
           }
         }
       }
-      const int64_t base = rowbase + (int64_t)(j2 - lo2) * W;
-      const int32_t *arow = act + j2 * n1 + (i1 - P);
 #pragma unroll
       for (int r = 0; r < W; r++) {
-        if (SPLIT) vald[base + r] = (double)ah[r] + (double)al[r];
-        else valf[base + r] = ah[r];
-        col[base + r] = arow[r];
+        if (SPLIT) o[r] = (double)ah[r] + (double)al[r];
+        else o[r] = ah[r];
       }
     } else {
-      const int lo1 = max(0, i1 - P), w1 = min(n1 - 1, i1 + P) - lo1 + 1;
       for (int r1 = 0; r1 < W; r1++) {
         const int j1 = i1 - P + r1;
         if (j1 < 0 || j1 >= n1) continue;
@@ -499,11 +585,27 @@ __device__ void interior_tile32(const Dir &A, const Dir &B, const float2 *__rest
           if (SPLIT) df_fma(v[c1 * W + r1], y[c1], sh, sl);
           else sh = fmaf(v[c1 * W + r1].x, y[c1].x, sh);
         }
-        const int64_t pos = rowbase + (int64_t)(j2 - lo2) * w1 + (j1 - lo1);
-        if (SPLIT) vald[pos] = (double)sh + (double)sl;
-        else valf[pos] = sh;
-        col[pos] = act[j2 * n1 + j1];
+        if (SPLIT) o[r1] = (double)sh + (double)sl;
+        else o[r1] = sh;
       }
+    }
+  }
+  __syncthreads();
+  // write out: one warp per row of the tile, consecutive lanes on consecutive
+  // CSR positions (j2 major, j1 minor over the valid part of the band)
+  OutT *val = (OutT *)valv;
+  const int nw = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int lo2 = max(0, i2 - P), w2 = min(B.n - 1, i2 + P) - lo2 + 1, d2 = lo2 - (i2 - P);
+  for (int t = wid; t < i1b - i1a; t += nw) {
+    const int i1 = i1a + t, g = i2 * n1 + i1;
+    if (fstate[g] != TW_FUNC_INTERIOR) continue;  // the whole warp
+    const int lo1 = max(0, i1 - P), w1 = min(n1 - 1, i1 + P) - lo1 + 1, d1 = lo1 - (i1 - P);
+    const int64_t rowbase = rp[act[g]];
+    const OutT *src = os + (size_t)t * W * W;
+    for (int k = lane; k < w1 * w2; k += 32) {
+      const int q2 = k / w1, q1 = k - q2 * w1;
+      val[rowbase + k] = src[(q2 + d2) * W + q1 + d1];
+      col[rowbase + k] = act[(lo2 + q2) * n1 + lo1 + q1];
     }
   }
   __syncthreads();  // the tile's smem is reused by the next item

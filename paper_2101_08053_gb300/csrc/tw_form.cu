@@ -15,6 +15,9 @@
 //                   region part (DWQ rectangle or naive masked WQ) by sum
 //                   factorisation, element Gauss on regular elements (element
 //                   level sum factorisation), cut-element rule on cut elements.
+//  k_cutrows_gather rows without a region part whose element matrices are all
+//                   precomputed (hybrid Gauss, Gauss method, DWQ rows without
+//                   a region): one warp per row gathers the element rows.
 //                   Every output is owned by one thread and summed in a fixed
 //                   order, so the matrix is bitwise reproducible.
 #include "tw_bodies.cuh"
@@ -32,12 +35,31 @@ __global__ void __launch_bounds__(256) k_interior(Dir A, Dir B, const double *__
   interior_tile<P>(A, B, C, fstate, act, rp, col, val, blockIdx.y, blockIdx.x * T, T, smem);
 }
 
+// rows that need the region part or element integration (the rest go to
+// k_cutrows_gather)
 template <int P, typename OutT>
 __global__ void __launch_bounds__(128) k_cutrows(RowArgs a, const int32_t *__restrict__ rows,
                                                  int32_t *__restrict__ col,
                                                  OutT *__restrict__ val) {
   __shared__ __align__(16) char smem[sizeof(CutSmem<P>)];
-  cutrow_item<P, OutT>(a, rows[blockIdx.x], col, val, smem);
+  const int g = rows[blockIdx.x];
+  if (cutrow_is_gather(a, g)) return;
+  cutrow_item<P, OutT>(a, g, col, val, smem);
+}
+
+// one warp per gather row
+template <int P, typename OutT>
+__global__ void __launch_bounds__(128) k_cutrows_gather(RowArgs a,
+                                                        const int32_t *__restrict__ rows,
+                                                        int nrows, int32_t *__restrict__ col,
+                                                        OutT *__restrict__ val) {
+  __shared__ const double *tab[4][(P + 1) * (P + 1)];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r = blockIdx.x * 4 + wib;
+  if (r >= nrows) return;  // the whole warp
+  const int g = rows[r];
+  if (!cutrow_is_gather(a, g)) return;
+  cutrow_gather_warp<P, OutT>(a, g, lane, tab[wib], col, val);
 }
 
 __global__ void k_copy_i64(const int64_t *src, int64_t *dst, int64_t n) {
@@ -48,7 +70,7 @@ __global__ void k_copy_i64(const int64_t *src, int64_t *dst, int64_t n) {
 template <int P>
 static int launch_form(tw_patch *Pt, int precision, int64_t *rp, int32_t *col, void *valv,
                        cudaStream_t s) {
-  constexpr int T = 32;
+  constexpr int T = P <= 5 ? 32 : 16;  // the tile's output buffer stays within static smem
   Dir &A = Pt->d[0];
   Dir &B = Pt->d[1];
   double *val = (double *)valv;
@@ -95,12 +117,26 @@ static int launch_form(tw_patch *Pt, int precision, int64_t *rp, int32_t *col, v
     ra.method = Pt->method;
     ra.flag = Pt->flag;
     int ps = prof_start(s);
-    if (precision == TW_PREC_FP32)
-      k_cutrows<P, float><<<Pt->ncutrows, 128, 0, s>>>(ra, Pt->cutrows, col, (float *)valv);
-    else
-      k_cutrows<P, double><<<Pt->ncutrows, 128, 0, s>>>(ra, Pt->cutrows, col, val);
+    const unsigned gw = (unsigned)((Pt->ncutrows + 3) / 4);
+    // gather rows exist iff there are element matrices and the method is not
+    // naive WQ; block rows iff not every row is a gather row
+    const bool gather = Pt->gmat && Pt->method != TW_METHOD_NAIVE;
+    const bool block = !gather || Pt->method == TW_METHOD_DWQ;
+    if (precision == TW_PREC_FP32) {
+      if (gather)
+        k_cutrows_gather<P, float><<<gw, 128, 0, s>>>(ra, Pt->cutrows, Pt->ncutrows, col,
+                                                      (float *)valv);
+      if (block)
+        k_cutrows<P, float><<<Pt->ncutrows, 128, 0, s>>>(ra, Pt->cutrows, col, (float *)valv);
+    } else {
+      if (gather)
+        k_cutrows_gather<P, double><<<gw, 128, 0, s>>>(ra, Pt->cutrows, Pt->ncutrows, col, val);
+      if (block)
+        k_cutrows<P, double><<<Pt->ncutrows, 128, 0, s>>>(ra, Pt->cutrows, col, val);
+    }
+    if (gather) TW_LAUNCH();
+    if (block) TW_LAUNCH();
     prof_stop(ps, TW_STAGE_CUTROWS, s);
-    TW_LAUNCH();
   }
   return 0;
 }

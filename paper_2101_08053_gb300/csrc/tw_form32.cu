@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(256) k_interior32(Dir A, Dir B, const float2 *
                                                     const int32_t *__restrict__ act,
                                                     const int64_t *__restrict__ rp,
                                                     int32_t *__restrict__ col, void *__restrict__ valv) {
-  __shared__ __align__(16) char smem[interior32_smem(P, T)];
+  __shared__ __align__(16) char smem[interior32_smem(P, T, SPLIT)];
   interior_tile32<P, SPLIT>(A, B, Cf, V1f, V2f, fstate, act, rp, col, valv, blockIdx.y,
                             blockIdx.x * T, T, smem);
 }
@@ -68,7 +68,7 @@ int ensure_split_tables(tw_patch *P, cudaStream_t s) {
 
 template <int P>
 static void launch32(tw_patch *Pt, bool split, int32_t *col, void *val, cudaStream_t s) {
-  constexpr int T = 32;
+  constexpr int T = P <= 5 ? 32 : 16;  // the tile's output buffer stays within static smem
   Dir &A = Pt->d[0];
   Dir &B = Pt->d[1];
   dim3 grid((A.n + T - 1) / T, B.n);
