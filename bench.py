@@ -181,8 +181,47 @@ def interior_flops(p, nel, fstate):
 
 
 def fp64_peak_gflops():
-    """FP64 (DFMA) rate of a GB300, as the profiling recipe lists it."""
-    return 1250.0
+    """FP64 peak of a GB300 from its unit counts and clock: 152 SMs x 2 DFMA
+    per clock x 2 flop x 2.07 GHz (a DFMA-loop probe measured 1 255.6 GFLOP/s)."""
+    return 152 * 2 * 2 * 2.07
+
+
+# DRAM bytes per k_interior launch over the timed step (dram__bytes_read.sum +
+# dram__bytes_write.sum of its 12 launches / 12, one ncu capture kept under
+# profiles/), valid only for the kernel sources it was taken with
+INTERIOR_TRAFFIC = {
+    "bytes_per_launch": 69440533,
+    "sources_sha256": {
+        "paper_2101_08053_gb300/csrc/tw_interior.cuh":
+            "9b0b894c99a4c477aefd4f279970588eec901791beef3fc5015b0c6ba72d578f",
+    },
+}
+
+
+def interior_traffic():
+    import hashlib
+    for rel, h in INTERIOR_TRAFFIC["sources_sha256"].items():
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            if hashlib.sha256(fh.read()).hexdigest() != h:
+                return None
+    return INTERIOR_TRAFFIC["bytes_per_launch"]
+
+
+def max_over_ranks(x, world, device):
+    """The largest per-rank value (a step time) over all ranks; the identity
+    on one rank.  The job's time is the slowest rank's."""
+    if world == 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, units_per_rank, ms):
+    """Whole-job throughput: every rank processes units_per_rank units (weak
+    scaling, replicas) in the slowest rank's ms."""
+    return world * units_per_rank / (ms * 1e-3)
 
 
 def run_ours(args, rank, world, local_rank):
@@ -293,14 +332,8 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
     api.profile_enable(False)
     stage = {k: api.profile_read(k) for k in api.STAGES}
-    ms_local = float(np.mean(times))
-    if world > 1:
-        t = torch.tensor([ms_local], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    else:
-        ms = ms_local
-    value = world * nnz_step / (ms * 1e-3)
+    ms = max_over_ranks(float(np.mean(times)), world, dev)
+    value = job_rate(world, nnz_step, ms)
 
     # end to end through the C-ABI with host buffers: descriptors from host
     # memory, CSR copied back to pinned host buffers, inside the timed region
@@ -332,11 +365,7 @@ def run_ours(args, rank, world, local_rank):
         t0 = time.perf_counter()
         e2e_step()
         et.append(time.perf_counter() - t0)
-    e2e_ms = float(np.mean(et)) * 1e3
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(float(np.mean(et)) * 1e3, world, dev)
 
     # the reduced-precision forms against the plain FP64 GPU form: formation
     # only (patch tables resident), serialised, relative Frobenius error
@@ -410,12 +439,13 @@ def run_ours(args, rank, world, local_rank):
         "adjoint": adjoint, "precision": precision,
         "roofline": {"bound": "alu", "kernel": "k_interior (interior rows, WQ + sum factorisation)",
                      "achieved": round(achieved, 4), "peak": peak, "unit": "TFLOP/s",
-                     "frac": round(achieved / peak, 4), "traffic": None,
+                     "frac": round(achieved / peak, 4), "traffic": interior_traffic(),
                      "flops_per_launch": flops_per_launch, "avg_launch_ms": avg_launch_ms,
                      "timing": "events on the launching stream over a serialised pass of the "
                                "same steps (the batched step overlaps kernels of different "
                                "patches)",
-                     "peak_source": "FP64 rate listed by the profiling recipe (not measured)"},
+                     "peak_source": "GB300 unit counts x max clock (152 SMs x 2 DFMA/clk x "
+                                    "2.07 GHz); a DFMA probe measured 1.2556 TFLOP/s"},
     }
 
 
@@ -697,7 +727,7 @@ def main():
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic", "config": dict(config, nnz_per_step=r["nnz_step"],
                                                     parallelism="replicas" if world > 1 else "single"),
-                "e2e": {"value": world * r["nnz_step"] / (r["e2e_ms"] * 1e-3), "unit": UNIT,
+                "e2e": {"value": job_rate(world, r["nnz_step"], r["e2e_ms"]), "unit": UNIT,
                         "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]},
                 "gpu_launches": r["launches"], "clocks": r["clocks"], "roofline": r["roofline"],
                 "cpu_baseline": cpu, "stage_ms_per_step_serial": r["stage_ms"],

@@ -24,17 +24,6 @@
 
 namespace tw {
 
-template <int P, int T>
-__global__ void __launch_bounds__(256) k_interior(Dir A, Dir B, const double *__restrict__ C,
-                                                  const uint8_t *__restrict__ fstate,
-                                                  const int32_t *__restrict__ act,
-                                                  const int64_t *__restrict__ rp,
-                                                  int32_t *__restrict__ col,
-                                                  double *__restrict__ val) {
-  __shared__ __align__(16) char smem[interior_smem(P, T)];
-  interior_tile<P>(A, B, C, fstate, act, rp, col, val, blockIdx.y, blockIdx.x * T, T, smem);
-}
-
 // rows that need the region part or element integration (the rest go to
 // k_cutrows_gather)
 template <int P, typename OutT>

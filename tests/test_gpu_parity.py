@@ -47,7 +47,8 @@ def compare_full(spec, tol=TOL):
     assert np.all(np.isfinite(v))
     r = rel_fro(v, oval)
     assert r <= tol, r
-    assert np.max(np.abs(v - oval)) <= tol * np.max(np.abs(oval))
+    if oval.size:
+        assert np.max(np.abs(v - oval)) <= tol * np.max(np.abs(oval))
     return G, O, (rp, col, val), (orp, ocol, oval)
 
 
@@ -87,6 +88,35 @@ def test_density_coefficient():
 def test_untrimmed_and_high_cut_order():
     compare_full(synth.make_spec(5, 9, {"kind": "none", "params": [], "ctrl": None}))
     compare_full(synth.make_spec(3, 13, synth.circle(0.5, 0.5, 0.3), cut_order=9, method="dwq"))
+
+
+DEGENERATE = {
+    # a hole inside one element (the element holds the whole curve)
+    "hole_in_one_element": synth.circle(0.51, 0.52, 0.003),
+    # everything trimmed away: no active function, empty matrix
+    "all_invisible": synth.circle(0.5, 0.5, 2.0),
+    # keep the inside of a small circle: a few active functions, all cut
+    "keep_inside_small": dict(synth.circle(0.5, 0.5, 0.05), keep_inside=True),
+    # a circle crossing the patch boundary
+    "crossing_boundary": synth.circle(0.0, 0.5, 0.3),
+}
+
+
+@pytest.mark.parametrize("case", sorted(DEGENERATE))
+@pytest.mark.parametrize("method", ["hybrid", "dwq"])
+def test_degenerate_trims(case, method):
+    spec = synth.make_spec(2, (12, 11), DEGENERATE[case], method=method)
+    G, O, (rp, col, val), _ = compare_full(spec)
+    f = synth.func_sinsin()
+    b = G.rhs(f).cpu().numpy()
+    ob = O.rhs(f)
+    assert b.shape == ob.shape
+    if ob.size:
+        assert rel_fro(b, ob) <= TOL
+    u, it, rel = G.l2_project(f, (rp, col, val), check=False)
+    assert u.shape[0] == G.n_rows
+    if case == "all_invisible":
+        assert G.n_rows == 0 and G.nnz == 0 and it == 0
 
 
 def test_config4_shaped_patches():
