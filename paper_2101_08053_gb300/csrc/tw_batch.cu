@@ -34,7 +34,8 @@ struct BatchPatch {
   int p;
 };
 
-enum { IT_INTERIOR = 0, IT_CUTROW = 1, IT_ROWPTR = 2 };
+enum { IT_INTERIOR = 0, IT_CUTROW = 1, IT_ROWPTR = 2, IT_GATHER = 3 };
+#define TW_GATHER_ROWS 8  // gather rows per item: one per warp of the block
 #define TW_RP_CHUNK 4096
 
 template <int PREC>
@@ -71,9 +72,27 @@ __device__ __forceinline__ void run_cutrow(const BatchPatch &b, int P, int g, ch
   }
 }
 
-// item = {kind | P << 4 | T << 8, patch, x, y}
 template <int PREC>
-__global__ void __launch_bounds__(256) k_batch(const BatchPatch *__restrict__ bp,
+__device__ __forceinline__ void run_gather(const BatchPatch &b, int P, int g, int lane,
+                                           const double **tab) {
+  switch (P) {
+#define TW_CG(PP)                                                                    \
+  case PP:                                                                           \
+    if constexpr (PREC == TW_PREC_FP32)                                              \
+      cutrow_gather_warp<PP, float>(b.ra, g, lane, tab, b.col, (float *)b.val);      \
+    else                                                                             \
+      cutrow_gather_warp<PP, double>(b.ra, g, lane, tab, b.col, (double *)b.val);    \
+    break;
+    TW_CG(1) TW_CG(2) TW_CG(3) TW_CG(4) TW_CG(5) TW_CG(6)
+#undef TW_CG
+  }
+}
+
+// item = {kind | P << 4 | T << 8, patch, x, y}; a gather item is up to
+// TW_GATHER_ROWS cut rows (x = first index into the patch's cut-row list,
+// y = count), one per warp
+template <int PREC>
+__global__ void __launch_bounds__(256, 3) k_batch(const BatchPatch *__restrict__ bp,
                                                const int4 *__restrict__ items, int nitems,
                                                int *counter) {
   extern __shared__ __align__(16) char smem[];
@@ -91,6 +110,11 @@ __global__ void __launch_bounds__(256) k_batch(const BatchPatch *__restrict__ bp
       run_interior<PREC>(b, P, w.z, w.w, T, smem);
     } else if (kind == IT_CUTROW) {
       run_cutrow<PREC>(b, P, w.z, smem);
+    } else if (kind == IT_GATHER) {
+      const int wib = threadIdx.x >> 5;
+      if (wib < w.w)
+        run_gather<PREC>(b, P, b.cutrows[w.z + wib], threadIdx.x & 31,
+                         (const double **)smem + wib * (TW_MAXP1 * TW_MAXP1));
     } else {
       const int64_t lo = (int64_t)w.z * TW_RP_CHUNK;
       const int64_t hi = min(b.nrp, lo + TW_RP_CHUNK);
@@ -100,16 +124,22 @@ __global__ void __launch_bounds__(256) k_batch(const BatchPatch *__restrict__ bp
   }
 }
 
-static size_t batch_smem(int prec, int tmax) {
-  size_t s = sizeof(CutSmem<TW_MAXP>);
-  size_t i64 = interior_smem(TW_MAXP, tmax);
-  size_t i32 = interior32_smem(TW_MAXP, tmax, prec == TW_PREC_FP32X2);
-  s = std::max(s, prec == TW_PREC_FP64 ? i64 : i32);
+// candidate interior tiles per degree: up to 64 rows at p <= 4, 32 above, so
+// the tile's staged outputs keep the block's shared memory near 56 KB
+static const int g_tiles[3] = {16, 32, 64};
+static int tile_max(int p) { return p <= 4 ? 64 : 32; }
+
+static size_t batch_smem(int prec) {
+  size_t s = std::max(sizeof(CutSmem<TW_MAXP>),
+                      sizeof(double *) * TW_GATHER_ROWS * TW_MAXP1 * TW_MAXP1);
+  for (int p = 1; p <= TW_MAXP; p++) {
+    const int t = tile_max(p);
+    size_t i = prec == TW_PREC_FP64 ? interior_smem(p, t)
+                                    : interior32_smem(p, t, prec == TW_PREC_FP32X2);
+    s = std::max(s, i);
+  }
   return (s + 15) / 16 * 16;
 }
-
-static const int g_tiles[3] = {16, 32, 64};
-#define TW_TILE_MAX 64
 
 static std::mutex g_tune_mu;
 static int g_tuned[64][3][TW_MAXP + 1];  // [device][precision][p] -> tile (0: not tuned)
@@ -239,7 +269,7 @@ extern "C" int tw_batch_create(tw_patch *const *patches, int n, int precision,
   tw_batch *B = (tw_batch *)calloc(1, sizeof(tw_batch));
   B->n = n;
   B->precision = precision;
-  B->smem = batch_smem(precision, TW_TILE_MAX);
+  B->smem = batch_smem(precision);
   int dev = 0, nsm = 0, occ = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -289,6 +319,8 @@ extern "C" int tw_batch_create(tw_patch *const *patches, int n, int precision,
     }
     double best = 1e300;
     for (int c = 0; c < 3; c++) {
+      B->tune_ms[p][c] = 0.0;
+      if (g_tiles[c] > tile_max(p)) continue;
       std::vector<int4> it;
       interior_items(pt, p, g_tiles[c], it);
       B->tune_ms[p][c] = 0.0;
@@ -322,6 +354,8 @@ extern "C" int tw_batch_create(tw_patch *const *patches, int n, int precision,
 
   // the work list: cut rows (heaviest) by degree descending, interior tiles by
   // degree descending, row-pointer copies last
+  // rows that only gather precomputed element matrices (cutrow_is_gather) go
+  // in groups of TW_GATHER_ROWS, one warp each; the others are one item each
   std::vector<int4> items;
   for (int p = TW_MAXP; p >= 1; p--)
     for (int k = 0; k < n; k++) {
@@ -329,7 +363,32 @@ extern "C" int tw_batch_create(tw_patch *const *patches, int n, int precision,
       if (P->p != p || P->ncutrows == 0) continue;
       std::vector<int32_t> rows(P->ncutrows);
       cudaMemcpy(rows.data(), P->cutrows, sizeof(int32_t) * P->ncutrows, cudaMemcpyDeviceToHost);
-      for (int32_t g : rows) items.push_back(make_int4(item_code(IT_CUTROW, p, 0), k, g, 0));
+      const bool gather = P->gmat && P->method != TW_METHOD_NAIVE;
+      std::vector<int32_t> choice;
+      if (gather && P->method == TW_METHOD_DWQ) {
+        choice.resize((size_t)4 * P->d[0].n * P->d[1].n);
+        cudaMemcpy(choice.data(), P->choice, sizeof(int32_t) * choice.size(),
+                   cudaMemcpyDeviceToHost);
+      }
+      int run0 = -1, runn = 0;
+      for (int r = 0; r <= P->ncutrows; r++) {
+        bool isg = false;
+        if (r < P->ncutrows && gather)
+          isg = choice.empty() || choice[(size_t)4 * rows[r]] < 0;
+        if (isg && runn > 0 && run0 + runn == r && runn < TW_GATHER_ROWS) {
+          runn++;
+          continue;
+        }
+        if (runn > 0) items.push_back(make_int4(item_code(IT_GATHER, p, 0), k, run0, runn));
+        runn = 0;
+        if (r == P->ncutrows) break;
+        if (isg) {
+          run0 = r;
+          runn = 1;
+        } else {
+          items.push_back(make_int4(item_code(IT_CUTROW, p, 0), k, rows[r], 0));
+        }
+      }
     }
   for (int p = TW_MAXP; p >= 1; p--) interior_items(pt, p, B->tile[p], items);
   for (int k = 0; k < n; k++) {
