@@ -13,6 +13,10 @@
  *    tw_patch_table are DEVICE memory owned by the caller (e.g. torch tensors).
  *  - A tw_patch owns its device tables (allocated in tw_patch_create, freed in
  *    tw_patch_destroy).  It is not thread-safe; distinct patches are.
+ *  - The library's device memory (patch tables, per-call scratch) comes from
+ *    one stream-ordered pool per device that the library creates on first use
+ *    and that keeps freed memory for reuse until the process exits (it holds
+ *    at most the peak of the library's live allocations).
  *  - `stream` is a cudaStream_t (NULL = legacy default stream).  All work is
  *    ordered on it; calls that must size outputs synchronise it (documented).
  *  - There is no CPU fallback: without a usable sm_103a device every call that

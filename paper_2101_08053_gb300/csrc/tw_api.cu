@@ -60,13 +60,44 @@ int check_cuda(cudaError_t e, const char *what) {
   return TW_ECUDA;
 }
 
+// The library's device memory comes from one stream-ordered pool per device
+// that keeps freed memory for reuse (release threshold: unlimited), so a
+// patch's tables are carved from memory the previous patches returned rather
+// than mapped anew after every synchronisation.  The pool holds at most the
+// peak of the library's live allocations until the process exits.
+#define TW_POOL_MAX_DEVICES 64
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pool[TW_POOL_MAX_DEVICES];
+
+static cudaMemPool_t library_pool() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= TW_POOL_MAX_DEVICES) return nullptr;
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  if (!g_pool[dev]) {
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) return nullptr;
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    g_pool[dev] = pool;
+  }
+  return g_pool[dev];
+}
+
 void *dalloc(tw_patch *P, size_t bytes) {
   if (P->nallocs >= (int)(sizeof(P->allocs) / sizeof(P->allocs[0]))) {
     set_error("internal: too many device allocations for one patch");
     return nullptr;
   }
   void *p = nullptr;
-  cudaError_t e = cudaMallocAsync(&p, bytes ? bytes : 16, P->stream);
+  cudaMemPool_t pool = library_pool();
+  cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, bytes ? bytes : 16, pool, P->stream)
+                       : cudaMallocAsync(&p, bytes ? bytes : 16, P->stream);
   if (e != cudaSuccess) {
     set_error("device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
     return nullptr;
