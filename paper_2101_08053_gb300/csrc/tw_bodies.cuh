@@ -23,6 +23,8 @@ struct CutSmem {
   double Tg[P1 * P1];
   int rk[2][TW_RC];
   int nr[2], nnest[2], nest[2][TW_RC];
+  double pv[2][TW_RC][P1], pd[2][TW_RC][P1];  // basis values / derivatives at the region points
+  int pe[2][TW_RC];                            // and their elements
   const double *eM[P1 * P1];  // per support element: its matrix row of this test function
   int jact[W * W];            // active index of each row entry (-1: none)
   unsigned msk[8];            // ballots of the active entries, one per 32 entries
@@ -187,6 +189,26 @@ __device__ void cutrow_item(const RowArgs &a, int g, int32_t *__restrict__ col,
         S.cg[ia * TW_RC + ib] = c;
       }
     }
+    // basis values and derivatives at every region point, once per row: from
+    // the tables at base points, by Cox-de Boor at nested points
+    const bool unit_c = a.G.coef_kind == TW_COEF_ONE;
+    for (int t = tid; t < m1 + m2 && !unit_c; t += blockDim.x) {
+      const int d = t < m1 ? 0 : 1, j = d == 0 ? t : t - m1;
+      const Dir &D = d == 0 ? A : B;
+      const int k = S.rk[d][j];
+      if (k >= 0) {
+        S.pe[d][j] = D.qel[k];
+        for (int q = 0; q <= P; q++) {
+          S.pv[d][j][q] = D.Bq[(size_t)k * P1 + q];
+          S.pd[d][j][q] = D.dBq[(size_t)k * P1 + q];
+        }
+      } else {
+        const double x = S.rx[d][j];
+        const int e = elem_of(D.bp, D.nel, x);
+        S.pe[d][j] = e;
+        basis_ders(D.U, e + P, x, P, S.pv[d][j], S.pd[d][j]);
+      }
+    }
     if (tid == 0) {
       int na = 0, nb = 0;
       for (int ia = 0; ia < m1; ia++)
@@ -217,7 +239,10 @@ __device__ void cutrow_item(const RowArgs &a, int g, int32_t *__restrict__ col,
               break;
             }
         }
-        S.cg[ia * TW_RC + ib] = coef_at(a.G, A, B, S.rx[0][ia], S.rx[1][ib]);
+        S.cg[ia * TW_RC + ib] =
+            unit_c ? 1.0
+                   : coef_from(a.G, P, S.rx[0][ia], S.rx[1][ib], S.pe[0][ia], S.pv[0][ia],
+                               S.pd[0][ia], S.pe[1][ib], S.pv[1][ib], S.pd[1][ib]);
       }
     }
     __syncthreads();

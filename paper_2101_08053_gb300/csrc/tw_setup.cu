@@ -1134,33 +1134,43 @@ template <int P>
 __global__ void __launch_bounds__(256) k_gauss_matrices(Dir A, Dir B, const int32_t *glist, int ng,
                                                        const double *gc, const uint8_t *fstate,
                                                        int method, double *M) {
-  constexpr int P1 = P + 1, NL = P1 * P1;
+  constexpr int P1 = P + 1, NL = P1 * P1, P3 = P1 * P1 * P1;
   const int sl = blockIdx.x;
   if (sl >= ng) return;
   const int e = glist[sl], e1 = e % A.nel, e2 = e / A.nel;
-  __shared__ double T[P1 * P1 * P1];
+  __shared__ double T[P3];
+  // weighted products of the element's basis at its Gauss points,
+  // W[g][a][b] = w_g h B_a(x_g) B_b(x_g), per direction
+  __shared__ double W1[P3], W2[P3];
   // only the rows of test functions formed by the cut-row kernel are ever
   // read (cut functions; every active function for the Gauss method)
-  __shared__ int need[NL];
+  __shared__ int flag[NL], need[NL];
   __shared__ int nneed;
-  if (threadIdx.x == 0) {
-    int n = 0;
-    for (int a = 0; a < NL; a++) {
-      const uint8_t st = fstate[(size_t)(e2 + a / P1) * A.n + (e1 + a % P1)];
-      if (st != TW_FUNC_EXTERIOR && (method == TW_METHOD_GAUSS || st == TW_FUNC_CUT)) need[n++] = a;
-    }
-    nneed = n;
-  }
   const double h1 = 0.5 * (A.bp[e1 + 1] - A.bp[e1]), h2 = 0.5 * (B.bp[e2 + 1] - B.bp[e2]);
   const double *GB1 = A.GB + (size_t)e1 * NL;  // [g][a]
   const double *GB2 = B.GB + (size_t)e2 * NL;
   const double *c = gc + (size_t)sl * NL;      // [g2][g1]
-  for (int id = threadIdx.x; id < P1 * P1 * P1; id += blockDim.x) {
+  for (int id = threadIdx.x; id < P3; id += blockDim.x) {
+    const int g = id / NL, a = (id / P1) % P1, b = id % P1;
+    W1[id] = A.gw[g] * h1 * GB1[g * P1 + a] * GB1[g * P1 + b];
+    W2[id] = B.gw[g] * h2 * GB2[g * P1 + a] * GB2[g * P1 + b];
+  }
+  for (int a = threadIdx.x; a < NL; a += blockDim.x) {
+    const uint8_t st = fstate[(size_t)(e2 + a / P1) * A.n + (e1 + a % P1)];
+    flag[a] = st != TW_FUNC_EXTERIOR && (method == TW_METHOD_GAUSS || st == TW_FUNC_CUT);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int n = 0;
+    for (int a = 0; a < NL; a++)
+      if (flag[a]) need[n++] = a;
+    nneed = n;
+  }
+  for (int id = threadIdx.x; id < P3; id += blockDim.x) {
     const int a1 = id / NL, b1 = (id / P1) % P1, g2 = id % P1;
     double s = 0.0;
 #pragma unroll
-    for (int g1 = 0; g1 < P1; g1++)
-      s = fma(A.gw[g1] * h1 * GB1[g1 * P1 + a1] * GB1[g1 * P1 + b1], c[g2 * P1 + g1], s);
+    for (int g1 = 0; g1 < P1; g1++) s = fma(W1[(g1 * P1 + a1) * P1 + b1], c[g2 * P1 + g1], s);
     T[id] = s;
   }
   __syncthreads();
@@ -1171,7 +1181,7 @@ __global__ void __launch_bounds__(256) k_gauss_matrices(Dir A, Dir B, const int3
     double s = 0.0;
 #pragma unroll
     for (int g2 = 0; g2 < P1; g2++)
-      s = fma(T[(a1 * P1 + b1) * P1 + g2], B.gw[g2] * h2 * GB2[g2 * P1 + a2] * GB2[g2 * P1 + b2], s);
+      s = fma(T[(a1 * P1 + b1) * P1 + g2], W2[(g2 * P1 + a2) * P1 + b2], s);
     Me[a * NL + b] = s;
   }
 }
