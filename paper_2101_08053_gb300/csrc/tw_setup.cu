@@ -139,7 +139,10 @@ __global__ void k_gauss_nodes(int q, double *x, double *w) {
   w[k] = 2.0 / ((1.0 - z * z) * dp * dp);
 }
 
-__global__ void k_wq_points(Dir D) {
+// the per-direction table kernels run both directions in one launch:
+// blockIdx.y picks the direction
+__global__ void k_wq_points(Dir D0, Dir D1) {
+  const Dir &D = blockIdx.y ? D1 : D0;
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= D.nq) return;
   int p = D.p, e, j, m;
@@ -162,7 +165,8 @@ __global__ void k_wq_points(Dir D) {
   }
 }
 
-__global__ void k_wq_ranges(Dir D) {
+__global__ void k_wq_ranges(Dir D0, Dir D1) {
+  const Dir &D = blockIdx.y ? D1 : D0;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= D.n) return;
   int lo = max(0, i - D.p), hi = min(D.nel - 1, i);
@@ -170,7 +174,8 @@ __global__ void k_wq_ranges(Dir D) {
   D.qcnt[i] = wq_off(hi + 1, D.p, D.nel) - D.qbeg[i];
 }
 
-__global__ void k_gauss_tables(Dir D) {
+__global__ void k_gauss_tables(Dir D0, Dir D1) {
+  const Dir &D = blockIdx.y ? D1 : D0;
   int id = blockIdx.x * blockDim.x + threadIdx.x;
   int p1 = D.p + 1;
   if (id >= D.nel * p1) return;
@@ -194,7 +199,8 @@ __device__ __forceinline__ double Bjk(const Dir &D, int j, int k) {
 // Eq. 5 for test function i: min-norm weights, then V = W * B_j (R2, R3).
 // One warp per test function: lanes own the columns (points) of the system.
 #define TW_WQ_WARPS 4
-__global__ void __launch_bounds__(32 * TW_WQ_WARPS) k_wq_weights(Dir D, int *flag) {
+__global__ void __launch_bounds__(32 * TW_WQ_WARPS) k_wq_weights(Dir D0, Dir D1, int *flag) {
+  const Dir &D = blockIdx.y ? D1 : D0;
   __shared__ double sA[TW_WQ_WARPS][TW_WIN * (TW_QMAX + 1)];
   __shared__ double sb[TW_WQ_WARPS][TW_WIN], sd[TW_WQ_WARPS][TW_WIN], sbeta[TW_WQ_WARPS][TW_WIN];
   __shared__ int sing[TW_WQ_WARPS];
@@ -689,24 +695,100 @@ __global__ void k_cut_gather(const int64_t *off, int ncut, int cap, const double
   for (int64_t k = threadIdx.x; k < n3; k += blockDim.x) dst[k] = src[k];
 }
 
-// per cut point: basis values in both directions and w * c
-__global__ void k_cut_point_tables(Geo G, Dir A, Dir B, const int32_t *cut_list,
-                                   const int64_t *off, int ncut, const double *pts, double *Bt,
-                                   double *wc) {
-  int ci = blockIdx.x;
+// per cut point: basis values in both directions and w * c.  The points come
+// in Gauss lines of constant outer coordinate (R6); for the spline geometry
+// the outer direction's basis and the control-net sums over it are formed once
+// per line, so det J costs 4(p+1) FMAs per point instead of 4(p+1)^2.
+#define TW_CPT_THREADS 128
+__global__ void __launch_bounds__(TW_CPT_THREADS)
+    k_cut_point_tables(Geo G, Dir A, Dir B, const int32_t *cut_list, const int64_t *off,
+                       const int32_t *cut_o, int ncut, const double *pts, double *Bt,
+                       double *wc) {
+  const int ci = blockIdx.x;
   if (ci >= ncut) return;
-  int e = cut_list[ci];
-  int e1 = e % A.nel, e2 = e / A.nel, p1 = A.p + 1;
-  for (int64_t k = off[ci] + threadIdx.x; k < off[ci + 1]; k += blockDim.x) {
-    double x1 = pts[3 * k], x2 = pts[3 * k + 1];
-    double v1[TW_MAXP1], d1[TW_MAXP1], v2[TW_MAXP1], d2[TW_MAXP1];
-    basis_ders(A.U, e1 + A.p, x1, A.p, v1, d1);
-    basis_ders(B.U, e2 + B.p, x2, B.p, v2, d2);
-    for (int a = 0; a < p1; a++) {
-      Bt[(2 * k) * p1 + a] = v1[a];
-      Bt[(2 * k + 1) * p1 + a] = v2[a];
+  const int e = cut_list[ci];
+  const int e1 = e % A.nel, e2 = e / A.nel, p = A.p, p1 = p + 1;
+  const int o = cut_o[ci], in = 1 - o;
+  const int eo = o == 0 ? e1 : e2, ei = o == 0 ? e2 : e1;
+  const Dir &Do = o == 0 ? A : B;
+  const Dir &Di = o == 0 ? B : A;
+  const bool geo = G.geom_kind == TW_GEOM_SPLINE && G.coef_kind != TW_COEF_ONE;
+  __shared__ double OV[TW_CPT_THREADS][TW_MAXP1];     // outer basis values of each line
+  __shared__ double LS[TW_CPT_THREADS][4][TW_MAXP1];  // control-net sums over the outer index
+  __shared__ int lid[TW_CPT_THREADS];
+  const int64_t k0 = off[ci], k1 = off[ci + 1];
+  for (int64_t base = k0; base < k1; base += TW_CPT_THREADS) {
+    const int t = threadIdx.x;
+    const int64_t k = base + t;
+    const bool live = k < k1;
+    const bool start = live && (t == 0 || pts[3 * k + o] != pts[3 * (k - 1) + o]);
+    lid[t] = start;
+    __syncthreads();
+    if (t == 0) {  // line index of each point in this chunk (a chunk opens a line)
+      int c = -1;
+      for (int j = 0; j < TW_CPT_THREADS && base + j < k1; j++) {
+        c += lid[j];
+        lid[j] = c;
+      }
     }
-    wc[k] = pts[3 * k + 2] * coef_from(G, A.p, x1, x2, e1, v1, d1, e2, v2, d2);
+    __syncthreads();
+    if (start) {
+      const int l = lid[t];
+      const double s = pts[3 * k + o];
+      double v[TW_MAXP1], d[TW_MAXP1];
+      basis_ders(Do.U, eo + p, s, p, v, d);
+      for (int a = 0; a <= p; a++) OV[l][a] = v[a];
+      if (geo) {
+        // o = 0: sums over a (xi1) for each inner b; o = 1: over b for each inner a
+        for (int j = 0; j <= p; j++) {
+          double sxd = 0, syd = 0, sxv = 0, syv = 0;
+          for (int a = 0; a <= p; a++) {
+            const int ia = o == 0 ? e1 + a : e1 + j, ib = o == 0 ? e2 + j : e2 + a;
+            const double *pt = G.ctrl + 2 * ((size_t)ib * G.n1 + ia);
+            sxd += pt[0] * d[a];
+            syd += pt[1] * d[a];
+            sxv += pt[0] * v[a];
+            syv += pt[1] * v[a];
+          }
+          LS[l][0][j] = sxd;
+          LS[l][1][j] = syd;
+          LS[l][2][j] = sxv;
+          LS[l][3][j] = syv;
+        }
+      }
+    }
+    __syncthreads();
+    if (live) {
+      const int l = lid[t];
+      const double x1 = pts[3 * k], x2 = pts[3 * k + 1];
+      const double xi = o == 0 ? x2 : x1;
+      double v[TW_MAXP1], d[TW_MAXP1];
+      basis_ders(Di.U, ei + p, xi, p, v, d);
+      for (int a = 0; a < p1; a++) {
+        Bt[(2 * k + o) * p1 + a] = OV[l][a];
+        Bt[(2 * k + in) * p1 + a] = v[a];
+      }
+      double c = 1.0;
+      if (G.coef_kind != TW_COEF_ONE) {
+        if (geo) {
+          // derivative along the outer direction: outer-derivative sums times the
+          // inner values; along the inner one: outer-value sums times the inner
+          // derivatives
+          double xo = 0, yo = 0, xn = 0, yn = 0;
+          for (int j = 0; j <= p; j++) {
+            xo += LS[l][0][j] * v[j];
+            yo += LS[l][1][j] * v[j];
+            xn += LS[l][2][j] * d[j];
+            yn += LS[l][3][j] * d[j];
+          }
+          // det J = x_xi1 y_xi2 - x_xi2 y_xi1
+          c = o == 0 ? xo * yn - xn * yo : xn * yo - xo * yn;
+        }
+        if (G.coef_kind == TW_COEF_DENSITY) c *= density_at(G, x1, x2);
+      }
+      wc[k] = pts[3 * k + 2] * c;
+    }
+    __syncthreads();
   }
 }
 
@@ -1271,16 +1353,18 @@ int build_tables(tw_patch *P) {
   P->qrule = qr;
   const double *qgx = qr, *qgw = qr + P->qc;
 
-  // WQ layout, basis tables, weights (Eq. 5)
-  for (int d = 0; d < 2; d++) {
-    Dir &D = P->d[d];
-    k_wq_points<<<G1(D.nq)>>>(D);
+  // WQ layout, basis tables, weights (Eq. 5): both directions per launch
+  {
+    auto g2 = [](int64_t n) { return dim3((unsigned)((n + 255) / 256), 2); };
+    k_wq_points<<<g2(std::max(A.nq, B.nq)), 256, 0, st>>>(A, B);
     TW_LAUNCH();
-    k_wq_ranges<<<G1(D.n)>>>(D);
+    k_wq_ranges<<<g2(std::max(A.n, B.n)), 256, 0, st>>>(A, B);
     TW_LAUNCH();
-    k_gauss_tables<<<G1(D.nel * p1)>>>(D);
+    k_gauss_tables<<<g2((int64_t)std::max(A.nel, B.nel) * p1), 256, 0, st>>>(A, B);
     TW_LAUNCH();
-    k_wq_weights<<<(D.n + TW_WQ_WARPS - 1) / TW_WQ_WARPS, 32 * TW_WQ_WARPS, 0, st>>>(D, P->flag);
+    const int nw = std::max(A.n, B.n);
+    k_wq_weights<<<dim3((nw + TW_WQ_WARPS - 1) / TW_WQ_WARPS, 2), 32 * TW_WQ_WARPS, 0, st>>>(
+        A, B, P->flag);
     TW_LAUNCH();
   }
   if (P->curve.kind == TW_TRIM_BSPLINE3) {
@@ -1453,8 +1537,9 @@ int build_tables(tw_patch *P) {
           nullptr, P->cut_off, P->cut_pts, P->cut_o, P->flag, nullptr, 0, nullptr);
     }
     TW_LAUNCH();
-    k_cut_point_tables<<<P->ncut, 128, 0, st>>>(P->geo, A, B, P->cut_list, P->cut_off, P->ncut,
-                                                P->cut_pts, P->cut_B, P->cut_wc);
+    k_cut_point_tables<<<P->ncut, TW_CPT_THREADS, 0, st>>>(P->geo, A, B, P->cut_list, P->cut_off,
+                                                           P->cut_o, P->ncut, P->cut_pts, P->cut_B,
+                                                           P->cut_wc);
     TW_LAUNCH();
     launch_cut_matrices(P, st);
   }
