@@ -89,20 +89,38 @@ static cudaMemPool_t library_pool() {
   return g_pool[dev];
 }
 
+// During tw_patch_create the small tables are carved from TW_ARENA_SLAB-byte
+// slabs (256-byte aligned), so creating a patch makes a handful of pool
+// allocations instead of one per table; larger tables get their own.
+#define TW_ARENA_SLAB ((size_t)2 << 20)
+
 void *dalloc(tw_patch *P, size_t bytes) {
+  size_t need = ((bytes ? bytes : 16) + 255) & ~(size_t)255;
+  if (P->arena_on && need <= P->arena_left) {
+    void *q = P->arena;
+    P->arena += need;
+    P->arena_left -= need;
+    return q;
+  }
+  const bool slab = P->arena_on && need <= TW_ARENA_SLAB / 4;
   if (P->nallocs >= (int)(sizeof(P->allocs) / sizeof(P->allocs[0]))) {
     set_error("internal: too many device allocations for one patch");
     return nullptr;
   }
   void *p = nullptr;
+  const size_t sz = slab ? TW_ARENA_SLAB : need;
   cudaMemPool_t pool = library_pool();
-  cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, bytes ? bytes : 16, pool, P->stream)
-                       : cudaMallocAsync(&p, bytes ? bytes : 16, P->stream);
+  cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, sz, pool, P->stream)
+                       : cudaMallocAsync(&p, sz, P->stream);
   if (e != cudaSuccess) {
     set_error("device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
     return nullptr;
   }
   P->allocs[P->nallocs++] = p;
+  if (slab) {
+    P->arena = (char *)p + need;
+    P->arena_left = TW_ARENA_SLAB - need;
+  }
   return p;
 }
 
@@ -254,6 +272,7 @@ extern "C" int tw_patch_create(const tw_patch_desc *desc, tw_patch **out) {
   }
 
   tw_patch *P = (tw_patch *)calloc(1, sizeof(tw_patch));
+  if (P) P->arena_on = 1;
   P->p = p;
   P->method = desc->method;
   P->qc = desc->cut_order > 0 ? desc->cut_order : p + 1;
@@ -375,6 +394,7 @@ extern "C" int tw_patch_create(const tw_patch_desc *desc, tw_patch **out) {
     if (rc) goto fail;
   }
 #undef ALLOC
+  P->arena_on = 0;
   *out = P;
   return TW_OK;
 fail:

@@ -662,6 +662,10 @@ struct tw_patch {
   int ndwqrows;
   // scratch
   int32_t *flag;     // error flags (device)
+  // while the patch is created its small tables are carved from slabs
+  char *arena;
+  size_t arena_left;
+  int arena_on;
   int64_t *i64tmp;
 };
 
