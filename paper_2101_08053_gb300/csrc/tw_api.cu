@@ -29,12 +29,12 @@ static std::vector<ProfRec> g_prof;
 
 int prof_start(cudaStream_t s) {
   if (!g_prof_on) return -1;
-  std::lock_guard<std::mutex> lock(g_prof_mu);
   ProfRec r;
   r.stage = -1;
   cudaEventCreate(&r.a);
   cudaEventCreate(&r.b);
   cudaEventRecord(r.a, s);
+  std::lock_guard<std::mutex> lock(g_prof_mu);
   g_prof.push_back(r);
   return (int)g_prof.size() - 1;
 }
