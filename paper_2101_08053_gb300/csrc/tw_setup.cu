@@ -715,51 +715,57 @@ __global__ void __launch_bounds__(TW_CPT_THREADS)
   const bool geo = G.geom_kind == TW_GEOM_SPLINE && G.coef_kind != TW_COEF_ONE;
   __shared__ double OV[TW_CPT_THREADS][TW_MAXP1];     // outer basis values of each line
   __shared__ double LS[TW_CPT_THREADS][4][TW_MAXP1];  // control-net sums over the outer index
-  __shared__ int lid[TW_CPT_THREADS];
+  __shared__ int64_t lfirst[TW_CPT_THREADS];          // first point of each line
+  __shared__ unsigned wmask[TW_CPT_THREADS / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t k0 = off[ci], k1 = off[ci + 1];
   for (int64_t base = k0; base < k1; base += TW_CPT_THREADS) {
     const int t = threadIdx.x;
     const int64_t k = base + t;
     const bool live = k < k1;
+    // a line opens at the chunk's first point and where the outer coordinate changes
     const bool start = live && (t == 0 || pts[3 * k + o] != pts[3 * (k - 1) + o]);
-    lid[t] = start;
+    const unsigned m = __ballot_sync(0xffffffffu, start);
+    if (lane == 0) wmask[wid] = m;
     __syncthreads();
-    if (t == 0) {  // line index of each point in this chunk (a chunk opens a line)
-      int c = -1;
-      for (int j = 0; j < TW_CPT_THREADS && base + j < k1; j++) {
-        c += lid[j];
-        lid[j] = c;
-      }
+    int before = 0, nl = 0;
+    for (int w = 0; w < TW_CPT_THREADS / 32; w++) {
+      const int c = __popc(wmask[w]);
+      if (w < wid) before += c;
+      nl += c;
     }
+    // line of this point = (line starts up to and including it) - 1
+    const int l = before + __popc(m & ((2u << lane) - 1u)) - 1;
+    if (start) lfirst[l] = k;
     __syncthreads();
-    if (start) {
-      const int l = lid[t];
-      const double s = pts[3 * k + o];
+    // per line and inner index j: the outer basis at the line and the control
+    // net summed over the outer index (o = 0: over a for each b = j; o = 1:
+    // over b for each a = j)
+    for (int u = t; u < nl * p1; u += TW_CPT_THREADS) {
+      const int L = u / p1, j = u % p1;
+      const double sL = pts[3 * lfirst[L] + o];
       double v[TW_MAXP1], d[TW_MAXP1];
-      basis_ders(Do.U, eo + p, s, p, v, d);
-      for (int a = 0; a <= p; a++) OV[l][a] = v[a];
+      basis_ders(Do.U, eo + p, sL, p, v, d);
+      if (j == 0)
+        for (int a = 0; a <= p; a++) OV[L][a] = v[a];
       if (geo) {
-        // o = 0: sums over a (xi1) for each inner b; o = 1: over b for each inner a
-        for (int j = 0; j <= p; j++) {
-          double sxd = 0, syd = 0, sxv = 0, syv = 0;
-          for (int a = 0; a <= p; a++) {
-            const int ia = o == 0 ? e1 + a : e1 + j, ib = o == 0 ? e2 + j : e2 + a;
-            const double *pt = G.ctrl + 2 * ((size_t)ib * G.n1 + ia);
-            sxd += pt[0] * d[a];
-            syd += pt[1] * d[a];
-            sxv += pt[0] * v[a];
-            syv += pt[1] * v[a];
-          }
-          LS[l][0][j] = sxd;
-          LS[l][1][j] = syd;
-          LS[l][2][j] = sxv;
-          LS[l][3][j] = syv;
+        double sxd = 0, syd = 0, sxv = 0, syv = 0;
+        for (int a = 0; a <= p; a++) {
+          const int ia = o == 0 ? e1 + a : e1 + j, ib = o == 0 ? e2 + j : e2 + a;
+          const double *pt = G.ctrl + 2 * ((size_t)ib * G.n1 + ia);
+          sxd += pt[0] * d[a];
+          syd += pt[1] * d[a];
+          sxv += pt[0] * v[a];
+          syv += pt[1] * v[a];
         }
+        LS[L][0][j] = sxd;
+        LS[L][1][j] = syd;
+        LS[L][2][j] = sxv;
+        LS[L][3][j] = syv;
       }
     }
     __syncthreads();
     if (live) {
-      const int l = lid[t];
       const double x1 = pts[3 * k], x2 = pts[3 * k + 1];
       const double xi = o == 0 ? x2 : x1;
       double v[TW_MAXP1], d[TW_MAXP1];
@@ -917,7 +923,8 @@ __device__ double ref_fn(const Dir &D, int s, int m, double x) {
 // The refined basis is tabulated once per window point and per window Gauss
 // point (shared memory); each refined system is then assembled by lookup and
 // solved by its own thread.
-#define TW_DWQ_THREADS 128
+#define TW_DWQ_THREADS 256  // 8 warps: the 2p refined systems of p <= 4 in one round
+#define TW_DWQ_SMEM (sizeof(double) * (TW_DWQ_THREADS / 32) * TW_WIN * (TW_QMAX + 1))
 __global__ void __launch_bounds__(TW_DWQ_THREADS)
     k_dwq_build(Dir D, const int32_t *disc_list, int ndisc, double *out_x, int32_t *out_np,
                 double *out_w, int32_t *out_k, int32_t *out_e, double *out_B, int32_t *out_r,
@@ -1042,7 +1049,9 @@ __global__ void __launch_bounds__(TW_DWQ_THREADS)
   __syncthreads();
   // step 3: WQ weights of the refined functions l = s .. s+2p-1 (Eq. 5), one
   // warp per refined system, lanes over the points of its support
-  __shared__ double sA[TW_DWQ_THREADS / 32][TW_WIN * (TW_QMAX + 1)];
+  // one system matrix per warp, in dynamic shared memory (TW_DWQ_SMEM bytes)
+  extern __shared__ double dwq_dyn[];
+  double (*sA)[TW_WIN * (TW_QMAX + 1)] = (double (*)[TW_WIN * (TW_QMAX + 1)])dwq_dyn;
   __shared__ double sb[TW_DWQ_THREADS / 32][TW_WIN], sd[TW_DWQ_THREADS / 32][TW_WIN],
       sbeta[TW_DWQ_THREADS / 32][TW_WIN];
   __shared__ int sing[TW_DWQ_THREADS / 32];
@@ -1560,7 +1569,14 @@ int build_tables(tw_patch *P) {
     k_compact<<<G1(D.nel + 1)>>>(dflag[d], dpos[d], dlist, P->disc_slot[d], D.nel + 1);
     TW_LAUNCH();
     if (nd > 0) {
-      k_dwq_build<<<nd, TW_DWQ_THREADS, 0, st>>>(D, dlist, nd, P->dwq_x[d], P->dwq_np[d], P->dwq_w[d],
+      static std::once_flag dwq_attr[64];
+      int dev = 0;
+      cudaGetDevice(&dev);
+      std::call_once(dwq_attr[dev & 63], [] {
+        cudaFuncSetAttribute(k_dwq_build, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)TW_DWQ_SMEM);
+      });
+      k_dwq_build<<<nd, TW_DWQ_THREADS, TW_DWQ_SMEM, st>>>(D, dlist, nd, P->dwq_x[d], P->dwq_np[d], P->dwq_w[d],
                                                  P->dwq_k[d], P->dwq_e[d], P->dwq_B[d],
                                                  P->dwq_r[d], P->flag);
       TW_LAUNCH();
