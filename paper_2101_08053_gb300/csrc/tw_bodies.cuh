@@ -440,52 +440,85 @@ __device__ void interior_tile32(const Dir &A, const Dir &B, const float2 *__rest
   for (int t = threadIdx.x; t < qc2 * W; t += blockDim.x) V2s[t] = V2f[(size_t)i2 * B.qmax * W + t];
   for (int t = threadIdx.x; t < W; t += blockDim.x) cr2[t] = B.crange[i2 * W + t];
   __syncthreads();
-  // stage 1: Y[r2][k1] = sum_{k2} V2[i2][k2][r2] c[k2][k1]
-  for (int idx = threadIdx.x; idx < W * K; idx += blockDim.x) {
-    const int r2 = idx / K, kk = idx - r2 * K;
+  // stage 1: Y[r2][k1] = sum_{k2} V2[i2][k2][r2] c[k2][k1]; a thread owns two
+  // neighbouring k1 of one r2, so each weight it loads serves two sums
+  const int K2 = (K + 1) >> 1;
+  for (int idx = threadIdx.x; idx < W * K2; idx += blockDim.x) {
+    const int r2 = idx / K2, kk = 2 * (idx - r2 * K2);
+    const bool two = kk + 1 < K;
     const int lo = cr2[r2] & 0xffff, hi = cr2[r2] >> 16;
     const float2 *cc = Cf + (size_t)(qb2 + lo) * A.nq + kA + kk;
-    float sh = 0.f, sl = 0.f;
+    float sh0 = 0.f, sl0 = 0.f, sh1 = 0.f, sl1 = 0.f;
     for (int c2 = lo; c2 < hi; c2++, cc += A.nq) {
-      if (SPLIT) df_fma(V2s[c2 * W + r2], *cc, sh, sl);
-      else sh = fmaf(V2s[c2 * W + r2].x, cc->x, sh);
+      const float2 vv = V2s[c2 * W + r2];
+      const float2 c0 = cc[0];
+      const float2 c1 = two ? cc[1] : make_float2(0.f, 0.f);
+      if (SPLIT) {
+        df_fma(vv, c0, sh0, sl0);
+        df_fma(vv, c1, sh1, sl1);
+      } else {
+        sh0 = fmaf(vv.x, c0.x, sh0);
+        sh1 = fmaf(vv.x, c1.x, sh1);
+      }
     }
-    Y[r2 * KMAX + kk] = make_float2(sh, sl);
+    Y[r2 * KMAX + kk] = make_float2(sh0, sl0);
+    if (two) Y[r2 * KMAX + kk + 1] = make_float2(sh1, sl1);
   }
   __syncthreads();
   // stage 2 (point-major for rows away from the end elements) into the
-  // tile's output buffer os[t][r2][r1]
-  const int NR = (i1b - i1a) * W;
+  // tile's output buffer os[t][r2][r1].  In FP32 a thread owns two
+  // neighbouring r2 of one row, so each weighted basis value it loads serves
+  // two outputs; the split form keeps one r2 per thread (its register
+  // footprint would otherwise halve the occupancy)
+  constexpr int NRP = SPLIT ? 1 : 2;
+  constexpr int WH = (W + NRP - 1) / NRP;
+  const int NR = (i1b - i1a) * WH;
   for (int idx = threadIdx.x; idx < NR; idx += blockDim.x) {
-    const int t = idx / W, r2 = idx - t * W;
+    const int t = idx / WH, r2a = NRP * (idx - t * WH), r2b = r2a + 1;
     const int i1 = i1a + t;
     const int g = i2 * n1 + i1;
-    const int j2 = i2 - P + r2;
-    if (fstate[g] != TW_FUNC_INTERIOR || j2 < 0 || j2 >= B.n) continue;
-    const float2 *y = Y + r2 * KMAX + (A.qbeg[i1] - kA);
+    if (fstate[g] != TW_FUNC_INTERIOR) continue;
+    const int j2a = i2 - P + r2a, j2b = j2a + 1;
+    const bool va = j2a >= 0 && j2a < B.n;
+    const bool vb = NRP == 2 && r2b < W && j2b >= 0 && j2b < B.n;
+    if (!va && !vb) continue;
+    const int yo = A.qbeg[i1] - kA;
+    const float2 *ya = Y + r2a * KMAX + yo;
+    const float2 *yb = Y + (vb ? r2b : r2a) * KMAX + yo;
     const float2 *v = V1f + ((size_t)i1 * A.qmax) * W;
-    OutT *o = os + ((size_t)t * W + r2) * W;
+    OutT *oa = os + ((size_t)t * W + r2a) * W;
+    OutT *ob = oa + W;
     if (i1 >= P + 1 && i1 <= A.nel - 2) {
-      float ah[W], al[W];
+      float aha[W], ala[W], ahb[W], alb[W];
 #pragma unroll
-      for (int r = 0; r < W; r++) ah[r] = al[r] = 0.f;
+      for (int r = 0; r < W; r++) aha[r] = ala[r] = ahb[r] = alb[r] = 0.f;
 #pragma unroll
       for (int el = 0; el <= P; el++) {
 #pragma unroll
         for (int pt = 0; pt < 2; pt++) {
           const int c1 = 2 * el + pt;
-          const float2 yv = y[c1];
+          const float2 yva = ya[c1], yvb = yb[c1];
 #pragma unroll
           for (int a = 0; a <= P; a++) {
-            if (SPLIT) df_fma(v[c1 * W + el + a], yv, ah[el + a], al[el + a]);
-            else ah[el + a] = fmaf(v[c1 * W + el + a].x, yv.x, ah[el + a]);
+            const float2 vv = v[c1 * W + el + a];
+            if constexpr (SPLIT) {
+              df_fma(vv, yva, aha[el + a], ala[el + a]);
+            } else {
+              aha[el + a] = fmaf(vv.x, yva.x, aha[el + a]);
+              ahb[el + a] = fmaf(vv.x, yvb.x, ahb[el + a]);
+            }
           }
         }
       }
 #pragma unroll
       for (int r = 0; r < W; r++) {
-        if (SPLIT) o[r] = (double)ah[r] + (double)al[r];
-        else o[r] = ah[r];
+        if (SPLIT) {
+          if (va) oa[r] = (double)aha[r] + (double)ala[r];
+          if (vb) ob[r] = (double)ahb[r] + (double)alb[r];
+        } else {
+          if (va) oa[r] = aha[r];
+          if (vb) ob[r] = ahb[r];
+        }
       }
     } else {
       for (int r1 = 0; r1 < W; r1++) {
@@ -493,13 +526,23 @@ __device__ void interior_tile32(const Dir &A, const Dir &B, const float2 *__rest
         if (j1 < 0 || j1 >= n1) continue;
         const int cr = A.crange[i1 * W + r1];
         const int lo = cr & 0xffff, hi = cr >> 16;
-        float sh = 0.f, sl = 0.f;
+        float sha = 0.f, sla = 0.f, shb = 0.f, slb = 0.f;
         for (int c1 = lo; c1 < hi; c1++) {
-          if (SPLIT) df_fma(v[c1 * W + r1], y[c1], sh, sl);
-          else sh = fmaf(v[c1 * W + r1].x, y[c1].x, sh);
+          const float2 vv = v[c1 * W + r1];
+          if constexpr (SPLIT) {
+            df_fma(vv, ya[c1], sha, sla);
+          } else {
+            sha = fmaf(vv.x, ya[c1].x, sha);
+            shb = fmaf(vv.x, yb[c1].x, shb);
+          }
         }
-        if (SPLIT) o[r1] = (double)sh + (double)sl;
-        else o[r1] = sh;
+        if (SPLIT) {
+          if (va) oa[r1] = (double)sha + (double)sla;
+          if (vb) ob[r1] = (double)shb + (double)slb;
+        } else {
+          if (va) oa[r1] = sha;
+          if (vb) ob[r1] = shb;
+        }
       }
     }
   }
@@ -515,10 +558,19 @@ __device__ void interior_tile32(const Dir &A, const Dir &B, const float2 *__rest
     const int lo1 = max(0, i1 - P), w1 = min(n1 - 1, i1 + P) - lo1 + 1, d1 = lo1 - (i1 - P);
     const int64_t rowbase = rp[act[g]];
     const OutT *src = os + (size_t)t * W * W;
-    for (int k = lane; k < w1 * w2; k += 32) {
-      const int q2 = k / w1, q1 = k - q2 * w1;
-      val[rowbase + k] = src[(q2 + d2) * W + q1 + d1];
-      col[rowbase + k] = act[(lo2 + q2) * n1 + lo1 + q1];
+    if (w1 == W && w2 == W) {  // full band: the row is the tile's W x W block
+      const int32_t *arow = act + (size_t)lo2 * n1 + lo1;
+      for (int k = lane; k < W * W; k += 32) {
+        const int q2 = k / W, q1 = k - q2 * W;
+        val[rowbase + k] = src[k];
+        col[rowbase + k] = arow[q2 * n1 + q1];
+      }
+    } else {
+      for (int k = lane; k < w1 * w2; k += 32) {
+        const int q2 = k / w1, q1 = k - q2 * w1;
+        val[rowbase + k] = src[(q2 + d2) * W + q1 + d1];
+        col[rowbase + k] = act[(lo2 + q2) * n1 + lo1 + q1];
+      }
     }
   }
   __syncthreads();  // the tile's smem is reused by the next item
