@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB = os.path.join(HERE, "liboracle.so")
 SOURCES = ["or_core.c", "or_curve.c", "or_patch.c"]
 
-TRIM = {"none": 0, "circle": 1, "ellipse": 2, "bspline3": 3}
+TRIM = {"none": 0, "circle": 1, "ellipse": 2, "bspline3": 3, "line": 4}
 GEOM = {"identity": 0, "spline": 1}
 COEF = {"one": 0, "detj": 1, "density": 2}
 METHOD = {"gauss": 0, "hybrid": 1, "dwq": 2, "naive": 3}

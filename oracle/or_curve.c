@@ -189,6 +189,16 @@ int or_curve_line_hits(const or_desc *d, int o, double s, double lo, double hi,
                        double *out, int cap) {
   int n = 0;
   if (d->trim_kind == OR_TRIM_NONE) return 0;
+  if (d->trim_kind == OR_TRIM_LINE) {
+    /* the point p0 + t (p1 - p0) with coordinate o equal to s */
+    const double *q = d->trim_params;
+    double p0o = q[o], p0i = q[1 - o], dro = q[2 + o] - q[o], dri = q[3 - o] - q[1 - o];
+    if (dro == 0.0) return 0;
+    double t = (s - p0o) / dro;
+    double v = fma(t, dri, p0i);
+    if (v > lo && v < hi && cap > 0) out[n++] = v;
+    return n;
+  }
   if (d->trim_kind == OR_TRIM_CIRCLE || d->trim_kind == OR_TRIM_ELLIPSE) {
     double v[2];
     int m = conic_line(d, o, s, v);
@@ -277,6 +287,11 @@ void or_curve_point0(const or_desc *d, double *xy) {
 /* 1 if (x, y) lies inside the closed curve (ray casting for the spline) */
 int or_curve_inside(const or_desc *d, double x, double y) {
   const double *q = d->trim_params;
+  if (d->trim_kind == OR_TRIM_LINE) {
+    /* left of the directed line: (p1 - p0) x (p - p0) > 0 */
+    double dx = q[2] - q[0], dy = q[3] - q[1];
+    return fma(dx, y - q[1], -(dy * (x - q[0]))) > 0.0;
+  }
   if (d->trim_kind == OR_TRIM_CIRCLE) {
     double dx = x - q[0], dy = y - q[1];
     return dx * dx + dy * dy < q[2] * q[2];

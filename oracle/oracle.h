@@ -37,6 +37,7 @@
 #define OR_TRIM_CIRCLE 1   /* prm: cx, cy, r                     */
 #define OR_TRIM_ELLIPSE 2  /* prm: cx, cy, a, b, phi             */
 #define OR_TRIM_BSPLINE3 3 /* periodic uniform cubic, nctrl x 2  */
+#define OR_TRIM_LINE 4     /* prm: x0, y0, x1, y1; "inside" = the half-plane left of (x0,y0)->(x1,y1) */
 
 #define OR_GEOM_IDENTITY 0
 #define OR_GEOM_SPLINE 1   /* control net in the patch basis, (i2*n1+i1)*2+comp */

@@ -49,6 +49,23 @@ def circle(cx=0.5, cy=0.5, r=0.27, keep_inside=False):
     return {"kind": "circle", "params": [cx, cy, r], "ctrl": None, "keep_inside": keep_inside}
 
 
+def line(x0, y0, x1, y1, keep_inside=False):
+    """Half-plane trim by the straight line through (x0, y0) and (x1, y1);
+    "inside" is the side left of the direction (x0, y0) -> (x1, y1)."""
+    return {"kind": "line", "params": [x0, y0, x1, y1], "ctrl": None, "keep_inside": keep_inside}
+
+
+# The line trim of the paper's mass-matrix example (its figure is not part of
+# the text): the line through (0, 0.31) and (1, 0.77), the part below it kept.
+LINE_TRIM = (0.0, 0.31, 1.0, 0.77)
+
+
+def line_trim_spec(p, nel=10, method="hybrid", cut_order=0):
+    """Unit square, identity geometry, c = 1, the straight-line trim above."""
+    return make_spec(p, nel, line(*LINE_TRIM, keep_inside=False), method=method,
+                     cut_order=cut_order)
+
+
 def ellipse(cx, cy, a, b, phi, keep_inside=False):
     return {"kind": "ellipse", "params": [cx, cy, a, b, phi], "ctrl": None,
             "keep_inside": keep_inside}

@@ -109,6 +109,42 @@ def bspline_curve_segment_poly(ctrl, s):
     return np.polyfit(us, xy[:, 0], 3), np.polyfit(us, xy[:, 1], 3)
 
 
+def line_removed_boundary_points(x0, y0, x1, y1, U1, U2, q=40):
+    """Points / weights of oint (.) dy around the part of the unit square
+    ABOVE the line through (x0, 0) .. (x1, 1)-spanning points (x0, y0) and
+    (x1, y1) with x0 = 0, x1 = 1 and 0 < y0, y1 < 1, counter-clockwise: the
+    line from left to right, then the right edge x = 1 upwards (the top edge
+    has dy = 0 and the left edge x = 0 contributes nothing, because the
+    x-antiderivatives vanish at 0).  Every piece is split at the knot lines."""
+    assert x0 == 0.0 and x1 == 1.0 and 0.0 < y0 < 1.0 and 0.0 < y1 < 1.0
+    gx, gw = np.polynomial.legendre.leggauss(q)
+    X, Y, W = [], [], []
+    # the line, t in [0, 1]: x = t, y = y0 + t (y1 - y0); split where x or y
+    # crosses a knot
+    br = {0.0, 1.0}
+    for k in np.unique(U1):
+        if 0.0 < k < 1.0:
+            br.add(float(k))
+    for k in np.unique(U2):
+        t = (k - y0) / (y1 - y0) if y1 != y0 else -1.0
+        if 0.0 < t < 1.0:
+            br.add(float(t))
+    br = sorted(br)
+    for a, b in zip(br[:-1], br[1:]):
+        t = a + (b - a) * (gx + 1) / 2
+        X.append(t)
+        Y.append(y0 + t * (y1 - y0))
+        W.append(gw * (b - a) / 2 * (y1 - y0))
+    # right edge, y from y1 to 1, split at the knots of U2
+    br = sorted({y1, 1.0} | {float(k) for k in np.unique(U2) if y1 < k < 1.0})
+    for a, b in zip(br[:-1], br[1:]):
+        yy = a + (b - a) * (gx + 1) / 2
+        X.append(np.ones_like(yy))
+        Y.append(yy)
+        W.append(gw * (b - a) / 2)
+    return np.concatenate(X), np.concatenate(Y), np.concatenate(W)
+
+
 def bspline_boundary_points(ctrl, U1, U2, q=40):
     """Points / weights of the line integral oint (.) dy along the periodic
     cubic B-spline curve, each segment split where it crosses a knot line."""

@@ -1,0 +1,111 @@
+"""Pins of the oracle on the straight-line (half-plane) trim, the trimming case
+of the paper's mass-matrix accuracy example (Sect. 4, Table 1), no GPU.
+
+Anchors, none of them the oracle's own code:
+  * crossings of the knot lines with the line against the explicit line
+    equation, the inside test against the sign of the cross product;
+  * classification against dense sampling of every element;
+  * the visible area against the trapezoid's closed form;
+  * every c = 1 entry of the Gauss, hybrid and DWQ matrices against Green's
+    theorem on the boundary of the removed part (cut order high enough for the
+    height-function rule to be exact on these polynomials);
+  * Table 1: hybrid Gauss and DWQ equal element Gauss to roundoff on the
+    10 x 10 line-trimmed basis for p = 1..6, naive WQ does not (p >= 2).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from pins import GreenEntries, line_removed_boundary_points
+
+X0, Y0, X1, Y1 = synth.LINE_TRIM
+
+
+def _desc(spec):
+    keep = []
+    return oracle.make_desc(spec, keep), keep
+
+
+def test_line_hits_and_inside_against_the_line_equation():
+    spec = synth.line_trim_spec(3)
+    d, keep = _desc(spec)
+    import ctypes as C
+    out = np.zeros(8)
+    L = oracle.lib()
+    for s in np.linspace(0.05, 0.95, 11):
+        n = L.or_curve_line_hits(C.byref(d), 0, float(s), -1e9, 1e9, out.ctypes.data_as(oracle.PD), 8)
+        assert n == 1
+        assert abs(out[0] - (Y0 + (s - X0) * (Y1 - Y0) / (X1 - X0))) < 1e-15
+        n = L.or_curve_line_hits(C.byref(d), 1, float(s), -1e9, 1e9, out.ctypes.data_as(oracle.PD), 8)
+        xs = X0 + (s - Y0) * (X1 - X0) / (Y1 - Y0)
+        assert n == (1 if -1e9 < xs < 1e9 else 0)
+        assert abs(out[0] - xs) < 1e-14
+    rng = np.random.default_rng(1)
+    for x, y in rng.uniform(0, 1, size=(200, 2)):
+        cross = (X1 - X0) * (y - Y0) - (Y1 - Y0) * (x - X0)
+        if abs(cross) > 1e-12:
+            assert L.or_curve_inside(C.byref(d), float(x), float(y)) == int(cross > 0)
+
+
+def test_classification_against_dense_samples():
+    spec = synth.line_trim_spec(2, nel=12)
+    P = oracle.Patch(spec)
+    es, fs, act = P.states()
+    U = np.unique(spec["knots"][0])
+    t = np.linspace(0.0, 1.0, 41)
+    for e2 in range(12):
+        for e1 in range(12):
+            xs = U[e1] + (U[e1 + 1] - U[e1]) * t
+            ys = U[e2] + (U[e2 + 1] - U[e2]) * t
+            XX, YY = np.meshgrid(xs, ys)
+            below = (X1 - X0) * (YY - Y0) - (Y1 - Y0) * (XX - X0) < 0  # right of the line
+            st = es[e2 * 12 + e1]
+            if below.all():
+                assert st == 1  # regular
+            elif not below.any():
+                assert st == 0  # invisible
+            else:
+                assert st == 2  # cut
+
+
+def test_visible_area_is_the_trapezoid():
+    P = oracle.Patch(synth.line_trim_spec(3))
+    assert abs(P.visible_area() - 0.5 * (Y0 + Y1)) < 1e-15
+
+
+@pytest.mark.parametrize("method", ["gauss", "hybrid", "dwq"])
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_entries_against_greens_theorem(method, p):
+    spec = synth.line_trim_spec(p, nel=7, method=method, cut_order=2 * p + 2)
+    P = oracle.Patch(spec)
+    rp, col, val = P.form()
+    es, fs, act = P.states()
+    U1, U2 = spec["knots"]
+    bnd = line_removed_boundary_points(X0, Y0, X1, Y1, U1, U2)
+    G = GreenEntries(U1, U2, p, bnd)
+    n1 = len(U1) - p - 1
+    rowg = np.flatnonzero(act >= 0)
+    gof = {int(act[g]): int(g) for g in rowg}
+    worst = 0.0
+    for r in range(P.n_rows):
+        g = gof[r]
+        i1, i2 = g % n1, g // n1
+        for k in range(rp[r], rp[r + 1]):
+            j = gof[int(col[k])]
+            ex = G.entry(i1, i2, j % n1, j // n1)
+            worst = max(worst, abs(val[k] - ex))
+    assert worst < 2e-15, worst
+
+
+def test_table1_line_trim():
+    """Table 1 on the line trim, 10 x 10 elements: the fast concepts against
+    standard Gauss in the Euclidean norm of the matrix difference."""
+    for p in (1, 2, 3, 4, 5, 6):
+        mats = {m: oracle.Patch(synth.line_trim_spec(p, 10, m)).form()[2]
+                for m in ("gauss", "hybrid", "dwq", "naive")}
+        ref = np.linalg.norm(mats["gauss"])
+        assert np.linalg.norm(mats["hybrid"] - mats["gauss"]) / ref < 1e-14
+        assert np.linalg.norm(mats["dwq"] - mats["gauss"]) / ref < 1e-14
+        if p >= 2:
+            assert np.linalg.norm(mats["naive"] - mats["gauss"]) / ref > 1e-6
