@@ -44,6 +44,8 @@ extern "C" {
 #define TW_TRIM_NONE 0
 #define TW_TRIM_CIRCLE 1   /* params: cx, cy, r                                  */
 #define TW_TRIM_ELLIPSE 2  /* params: cx, cy, a, b, phi (semi-axes, rotation)    */
+#define TW_TRIM_LINE 4     /* params: x0, y0, x1, y1 (distinct); "inside" is the half-plane
+                              left of the directed line (x0,y0) -> (x1,y1)   */
 #define TW_TRIM_BSPLINE3 3 /* periodic uniform cubic B-spline, nctrl x 2 points,
                               C(tau) = sum_m P_m N3((tau - m) mod nctrl)          */
 /* geometry map x(xi) */

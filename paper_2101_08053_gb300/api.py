@@ -12,7 +12,7 @@ import torch
 
 from . import _build
 
-TRIM = {"none": 0, "circle": 1, "ellipse": 2, "bspline3": 3}
+TRIM = {"none": 0, "circle": 1, "ellipse": 2, "bspline3": 3, "line": 4}
 GEOM = {"identity": 0, "spline": 1}
 COEF = {"one": 0, "detj": 1, "density": 2}
 METHOD = {"gauss": 0, "hybrid": 1, "dwq": 2, "naive": 3}

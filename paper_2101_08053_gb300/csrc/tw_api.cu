@@ -220,7 +220,7 @@ extern "C" int tw_patch_create(const tw_patch_desc *desc, tw_patch **out) {
   for (int d = 0; d < 2; d++)
     if (!valid_open_knots(desc->knots[d], desc->nknots[d], p, d ? "knots[1]" : "knots[0]"))
       return TW_EINVAL;
-  if (desc->trim_kind < TW_TRIM_NONE || desc->trim_kind > TW_TRIM_BSPLINE3) {
+  if (desc->trim_kind < TW_TRIM_NONE || desc->trim_kind > TW_TRIM_LINE) {
     set_error("tw_patch_create: unknown trim_kind %d", desc->trim_kind);
     return TW_EINVAL;
   }
@@ -230,6 +230,11 @@ extern "C" int tw_patch_create(const tw_patch_desc *desc, tw_patch **out) {
   }
   if (desc->trim_kind == TW_TRIM_ELLIPSE && !(desc->trim_params[2] > 0 && desc->trim_params[3] > 0)) {
     set_error("tw_patch_create: ellipse semi-axes must be > 0");
+    return TW_EINVAL;
+  }
+  if (desc->trim_kind == TW_TRIM_LINE &&
+      !(desc->trim_params[0] != desc->trim_params[2] || desc->trim_params[1] != desc->trim_params[3])) {
+    set_error("tw_patch_create: a trimming line needs two distinct points");
     return TW_EINVAL;
   }
   if (desc->trim_kind == TW_TRIM_BSPLINE3 &&

@@ -257,6 +257,16 @@ static __device__ int cubic_roots01(const double *c, double v, double *out) {
 static __device__ int curve_line_hits(const Curve &C, int o, double s, double lo, double hi, double *out,
                                int cap) {
   int n = 0;
+  if (C.kind == TW_TRIM_LINE) {
+    // the point p0 + t (p1 - p0) with coordinate o equal to s
+    const double p0o = C.prm[o], p0i = C.prm[1 - o];
+    const double dro = C.prm[2 + o] - C.prm[o], dri = C.prm[3 - o] - C.prm[1 - o];
+    if (dro == 0.0) return 0;
+    const double t = (s - p0o) / dro;
+    const double v = fma(t, dri, p0i);
+    if (v > lo && v < hi && cap > 0) out[n++] = v;
+    return n;
+  }
   if (C.kind == TW_TRIM_CIRCLE) {
     double c0 = o == 0 ? C.prm[0] : C.prm[1], c1 = o == 0 ? C.prm[1] : C.prm[0];
     double r = C.prm[2];
@@ -333,6 +343,11 @@ static __device__ int curve_line_hits(const Curve &C, int o, double s, double lo
 
 // 1 if (x, y) is inside the closed curve
 static __device__ int curve_inside(const Curve &C, double x, double y) {
+  if (C.kind == TW_TRIM_LINE) {
+    // left of the directed line: (p1 - p0) x (p - p0) > 0
+    const double dx = C.prm[2] - C.prm[0], dy = C.prm[3] - C.prm[1];
+    return fma(dx, y - C.prm[1], -(dy * (x - C.prm[0]))) > 0.0;
+  }
   if (C.kind == TW_TRIM_CIRCLE) {
     double dx = x - C.prm[0], dy = y - C.prm[1];
     return dx * dx + dy * dy < C.prm[2] * C.prm[2];

@@ -360,7 +360,9 @@ __global__ void k_classify_elems(Curve C, Dir A, Dir B, const double *hits, cons
     const double *h = hits + (size_t)(hc + e2) * TW_HITCAP;
     int right = 0;
     for (int k = 0; k < nh[hc + e2]; k++) right += h[k] > xc;
-    int inside = right & 1;
+    // parity of the crossings to the right for a closed curve; the half-plane
+    // of a line is tested directly
+    int inside = C.kind == TW_TRIM_LINE ? curve_inside(C, xc, 0.5 * (a2 + b2)) : (right & 1);
     int vis = C.keep_inside ? inside : !inside;
     st = vis ? TW_ELEM_REGULAR : TW_ELEM_INVISIBLE;
   }
@@ -641,6 +643,10 @@ __global__ void __launch_bounds__(TW_CUT_THREADS)
           int right = 0;
           for (int k = 0; k < neh; k++) right += eh[k] > s;
           int inside = right & 1;
+          if (C.kind == TW_TRIM_LINE) {  // a half-plane: test the first interval's midpoint
+            const double um = 0.5 * (h[0] + h[1]);
+            inside = o == 0 ? curve_inside(C, s, um) : curve_inside(C, um, s);
+          }
           vis0 = C.kind == TW_TRIM_NONE ? 1 : (C.keep_inside ? inside : !inside);
           for (int k = 0; k <= n; k++)
             if (h[k + 1] > h[k] && (vis0 ^ (k & 1))) count += q;

@@ -119,6 +119,36 @@ def test_degenerate_trims(case, method):
         assert G.n_rows == 0 and G.nnz == 0 and it == 0
 
 
+@pytest.mark.parametrize("method", ["gauss", "hybrid", "dwq", "naive"])
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5, 6])
+def test_line_trim_table1_sizes(p, method):
+    """The paper's mass-matrix example: a straight-line trim on 10 x 10 elements."""
+    compare_full(synth.line_trim_spec(p, 10, method))
+
+
+def test_line_trim_table1_on_the_gpu():
+    """Table 1 on the GPU path: hybrid Gauss and DWQ equal element Gauss to
+    roundoff, naive WQ does not (p >= 2)."""
+    for p in (1, 2, 3, 4, 5, 6):
+        mats = {}
+        for m in ("gauss", "hybrid", "dwq", "naive"):
+            G = gpu_patch(synth.line_trim_spec(p, 10, m))
+            mats[m] = G.form_mass("fp64")[2].cpu().numpy()
+        ref = np.linalg.norm(mats["gauss"])
+        assert np.linalg.norm(mats["hybrid"] - mats["gauss"]) / ref < 1e-14
+        assert np.linalg.norm(mats["dwq"] - mats["gauss"]) / ref < 1e-14
+        if p >= 2:
+            assert np.linalg.norm(mats["naive"] - mats["gauss"]) / ref > 1e-6
+
+
+def test_line_trim_ragged_and_steep():
+    """A steep line (more crossings of horizontal knot lines) on a ragged
+    patch, and the kept side flipped."""
+    steep = synth.line(0.2, 0.0, 0.65, 1.0, keep_inside=True)
+    compare_full(synth.make_spec(3, (13, 9), steep, method="hybrid"))
+    compare_full(synth.make_spec(4, (11, 14), synth.line(0.0, 0.62, 1.0, 0.21), method="dwq"))
+
+
 def test_config4_shaped_patches():
     rng = np.random.default_rng(synth.BASE_SEED + 4)
     for _ in range(3):
