@@ -305,3 +305,27 @@ def test_basis_tables_against_scipy(p):
             xx = a + (b - a) * (gx[g] + 1) / 2
             ref = [bvals(U, p, e + q, xx)[()] for q in range(p + 1)]
             assert np.allclose(GB[e, g], ref, atol=1e-14)
+
+
+@pytest.mark.parametrize("trim", ["circle", "line"])
+@pytest.mark.parametrize("p", [2, 3])
+def test_l2_projection_convergence_rates(trim, p):
+    """Sect. 4.2: the L2 projection of sin(2x) cos(3y) on the trimmed patch
+    converges at the optimal rate p + 1 under h-refinement; the error is
+    measured by tw_loss (the same rule as the oracle's L2 error)."""
+    f = synth.func_sincos(2.0, 3.0)
+    errs = []
+    for nel in (8, 16, 32, 64):
+        tr = synth.circle(0.5, 0.5, 0.27) if trim == "circle" else synth.line(*synth.LINE_TRIM)
+        spec = synth.make_spec(p, nel, tr, method="hybrid")
+        G = gpu_patch(spec)
+        csr = G.form_mass("fp64")
+        u, it, rel = G.l2_project(f, csr, tol=1e-13, check=False)
+        L, _ = G.loss(u, f)
+        errs.append(float(L.item()) ** 0.5)
+        if nel <= 16:  # the same rule as the oracle's loss, for the same u
+            O = oracle.Patch(spec)
+            L_o, _ = O.loss(u.cpu().numpy(), f)
+            assert abs(L_o ** 0.5 - errs[-1]) <= 1e-10 * errs[-1]
+    rates = [np.log2(errs[k] / errs[k + 1]) for k in range(len(errs) - 1)]
+    assert min(rates[1:]) > p + 0.6, rates
