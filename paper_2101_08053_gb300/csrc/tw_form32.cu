@@ -66,18 +66,21 @@ int ensure_split_tables(tw_patch *P, cudaStream_t s) {
   return check_cuda(cudaGetLastError(), "split tables");
 }
 
+// tiles as large as the static shared memory allows for the staged outputs:
+// split (FP64 outputs) 32 rows (16 at p = 6), FP32 64 rows (32 at p = 6)
 template <int P>
 static void launch32(tw_patch *Pt, bool split, int32_t *col, void *val, cudaStream_t s) {
-  constexpr int T = P <= 5 ? 32 : 16;  // the tile's output buffer stays within static smem
+  constexpr int TS = P <= 5 ? 32 : 16, TF = P <= 5 ? 64 : 32;
+  static_assert(interior32_smem(P, TS, true) <= 48 * 1024, "split tile exceeds static smem");
+  static_assert(interior32_smem(P, TF, false) <= 48 * 1024, "FP32 tile exceeds static smem");
   Dir &A = Pt->d[0];
   Dir &B = Pt->d[1];
-  dim3 grid((A.n + T - 1) / T, B.n);
   if (split)
-    k_interior32<P, T, true><<<grid, 256, 0, s>>>(A, B, Pt->Cf, Pt->Vf[0], Pt->Vf[1], Pt->fstate,
-                                                   Pt->act, Pt->row_ptr, col, val);
+    k_interior32<P, TS, true><<<dim3((A.n + TS - 1) / TS, B.n), 256, 0, s>>>(
+        A, B, Pt->Cf, Pt->Vf[0], Pt->Vf[1], Pt->fstate, Pt->act, Pt->row_ptr, col, val);
   else
-    k_interior32<P, T, false><<<grid, 256, 0, s>>>(A, B, Pt->Cf, Pt->Vf[0], Pt->Vf[1], Pt->fstate,
-                                                    Pt->act, Pt->row_ptr, col, val);
+    k_interior32<P, TF, false><<<dim3((A.n + TF - 1) / TF, B.n), 256, 0, s>>>(
+        A, B, Pt->Cf, Pt->Vf[0], Pt->Vf[1], Pt->fstate, Pt->act, Pt->row_ptr, col, val);
 }
 
 int launch_interior32(tw_patch *P, int precision, int32_t *col, void *val, cudaStream_t s) {
