@@ -40,6 +40,25 @@ def open_uniform_knots(p: int, nel: int, a: float = 0.0, b: float = 1.0) -> np.n
     return np.array([a] * (p + 1) + inner + [b] * (p + 1), dtype=np.float64)
 
 
+def graded_knots(p: int, nel: int, ratio: float = 1.15, a: float = 0.0, b: float = 1.0) -> np.ndarray:
+    """Open knot vector with simple interior knots graded geometrically (each
+    element `ratio` times the previous one), for non-uniform parity cases."""
+    h = ratio ** np.arange(nel)
+    x = np.concatenate([[0.0], np.cumsum(h)])
+    x = a + (b - a) * x / x[-1]
+    x[-1] = b
+    return np.array([a] * (p + 1) + list(x[1:-1]) + [b] * (p + 1), dtype=np.float64)
+
+
+def with_knots(spec, U1, U2):
+    """The spec on other knot vectors (same degree; nel from the knots)."""
+    s = dict(spec)
+    s["knots"] = [np.asarray(U1, dtype=np.float64), np.asarray(U2, dtype=np.float64)]
+    p = spec["p"]
+    s["nel"] = (len(U1) - 2 * p - 1, len(U2) - 2 * p - 1)
+    return s
+
+
 def greville(U: np.ndarray, p: int) -> np.ndarray:
     n = len(U) - p - 1
     return np.array([U[i + 1:i + p + 1].mean() for i in range(n)], dtype=np.float64)

@@ -329,3 +329,25 @@ def test_l2_projection_convergence_rates(trim, p):
             assert abs(L_o ** 0.5 - errs[-1]) <= 1e-10 * errs[-1]
     rates = [np.log2(errs[k] / errs[k + 1]) for k in range(len(errs) - 1)]
     assert min(rates[1:]) > p + 0.6, rates
+
+
+@pytest.mark.parametrize("method", ["gauss", "hybrid", "dwq", "naive"])
+@pytest.mark.parametrize("p", [2, 3, 5])
+def test_graded_knots(p, method):
+    """Non-uniform simple knots (reading R1), graded geometrically and
+    differently per direction, with a circular hole."""
+    U1 = synth.graded_knots(p, 9, 1.2)
+    U2 = synth.graded_knots(p, 12, 0.85)
+    spec = synth.with_knots(synth.make_spec(p, 4, synth.circle(0.47, 0.52, 0.29), method=method),
+                            U1, U2)
+    compare_full(spec)
+
+
+def test_graded_knots_spline_hole_density():
+    rng = np.random.default_rng(31)
+    U1 = synth.graded_knots(4, 14, 1.1)
+    U2 = synth.graded_knots(4, 11, 0.9)
+    trim = synth.bspline_curve(rng, nc=8, radius=0.3, jitter=0.1, relative_jitter=True)
+    dens = synth.density(rng, q=2, m=7)
+    spec = synth.with_knots(synth.make_spec(4, 4, trim, coef=dens, method="dwq"), U1, U2)
+    compare_full(spec)

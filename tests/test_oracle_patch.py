@@ -110,6 +110,44 @@ def test_untrimmed_wq_exact_for_constant_c(p, nel):
     assert abs(vw.sum() - 1.0) < 1e-14
 
 
+@pytest.mark.parametrize("p,nel", [(2, 7), (3, 9), (5, 8)])
+def test_graded_knots_wq_exact_and_green(p, nel):
+    """Non-uniform simple knots (reading R1 admits them): WQ on an untrimmed
+    graded patch equals element Gauss for constant c, row sums equal
+    int B_i1 * int B_i2 = (U[i+p+1] - U[i]) / (p + 1) per direction, and on a
+    trimmed graded patch every c = 1 entry of the hybrid matrix matches
+    Green's theorem."""
+    U1 = synth.graded_knots(p, nel, 1.2)
+    U2 = synth.graded_knots(p, nel + 2, 0.85)
+    trim = {"kind": "none", "params": [], "ctrl": None}
+    W = oracle.Patch(synth.with_knots(synth.make_spec(p, 4, trim, method="hybrid"), U1, U2))
+    G = oracle.Patch(synth.with_knots(synth.make_spec(p, 4, trim, method="gauss"), U1, U2))
+    rp, col, vw = W.form()
+    _, _, vg = G.form()
+    assert np.max(np.abs(vw - vg)) < 1e-16
+    n1, n2 = len(U1) - p - 1, len(U2) - p - 1
+    I1 = (U1[p + 1:] - U1[:n1]) / (p + 1)
+    I2 = (U2[p + 1:] - U2[:n2]) / (p + 1)
+    rows = np.add.reduceat(vw, rp[:-1])
+    ref = np.array([I1[g % n1] * I2[g // n1] for g in range(n1 * n2)])
+    assert np.max(np.abs(rows - ref)) < 1e-16
+    cx, cy, r = 0.47, 0.52, 0.29
+    spec = synth.with_knots(synth.make_spec(p, 4, synth.circle(cx, cy, r), method="hybrid",
+                                            cut_order=16), U1, U2)
+    P = oracle.Patch(spec)
+    rp, col, val = P.form()
+    es, fs, act = P.states()
+    Gr = GreenEntries(U1, U2, p, circle_boundary_points(cx, cy, r, U1, U2))
+    gof = {int(act[g]): int(g) for g in np.flatnonzero(act >= 0)}
+    worst = 0.0
+    for row in range(P.n_rows):
+        g = gof[row]
+        for k in range(rp[row], rp[row + 1]):
+            j = gof[int(col[k])]
+            worst = max(worst, abs(val[k] - Gr.entry(g % n1, g // n1, j % n1, j // n1)))
+    assert worst < 2e-15, worst
+
+
 @pytest.mark.parametrize("method", ["gauss", "hybrid", "dwq"])
 @pytest.mark.parametrize("p,nel", [(1, 7), (2, 6), (3, 5), (4, 8), (6, 6)])
 def test_entries_against_greens_theorem_circle(method, p, nel):
