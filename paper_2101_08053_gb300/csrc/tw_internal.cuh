@@ -566,14 +566,18 @@ struct RowArgs {
 // warp-cooperative min-norm solve of A w = b (m x N, m <= 2p+1, N <= 32): lane c
 // owns column c.  LQ with Householder reflectors from the right, reductions by
 // a fixed shuffle tree (deterministic).  A (leading dimension lda, shared
-// memory) is overwritten with L and the reflectors; w[c] is returned in lane c.
+// memory) is overwritten with L and the reflectors; ssh is 32 doubles of the
+// warp's shared scratch; w[c] is returned in lane c.
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
 static __device__ double warp_minnorm(int m, int N, double *A, int lda, const double *b, double *diag,
-                               double *beta, int lane, int *singular) {
+                               double *beta, double *ssh, int lane, int *singular) {
+  // GB300 issues one FP64 warp instruction per 16 cycles per SM, so the
+  // reflectors' row products run with lanes over rows (one FMA per column)
+  // instead of one warp reduction per row
   for (int k = 0; k < m; k++) {
     double x = (lane >= k && lane < N) ? A[k * lda + lane] : 0.0;
     double nrm2 = warp_sum(x * x);
@@ -587,34 +591,46 @@ static __device__ double warp_minnorm(int m, int N, double *A, int lda, const do
     double v0 = akk - alpha;
     double vn2 = v0 * v0 + (nrm2 - akk * akk);
     double bk = vn2 > 0.0 ? 2.0 / vn2 : 0.0;
-    double v = lane == k ? v0 : x;
-    for (int r = k + 1; r < m; r++) {
-      double a = (lane >= k && lane < N) ? A[r * lda + lane] : 0.0;
-      double s = warp_sum(a * v) * bk;
-      if (lane >= k && lane < N) A[r * lda + lane] = a - s * v;
-    }
     __syncwarp();
-    if (lane >= k && lane < N) A[k * lda + lane] = v;
+    // the reflector vector v (columns k..N-1) replaces row k
+    if (lane >= k && lane < N) A[k * lda + lane] = lane == k ? v0 : x;
     if (lane == 0) {
       diag[k] = alpha;
       beta[k] = bk;
     }
     __syncwarp();
+    // s_r = bk * (row r . v) for the rows below k, lane r
+    double sr = 0.0;
+    if (lane > k && lane < m) {
+      const double *ar = A + lane * lda, *vk = A + k * lda;
+      for (int c = k; c < N; c++) sr = fma(ar[c], vk[c], sr);
+      sr *= bk;
+    }
+    ssh[lane] = sr;
+    __syncwarp();
+    // row r -= s_r v, lanes over columns
+    if (lane >= k && lane < N) {
+      const double vc = A[k * lda + lane];
+      for (int r = k + 1; r < m; r++) A[r * lda + lane] = fma(-ssh[r], vc, A[r * lda + lane]);
+    }
+    __syncwarp();
   }
-  // forward substitution L y = b, y kept in lane r
+  // forward substitution L y = b (L below the diagonal of A, diagonal in
+  // diag), lanes over rows: lane j's value is final when step j reaches it
+  double rhs = lane < m ? b[lane] : 0.0;
+  const double dinv = lane < m ? 1.0 / diag[lane] : 0.0;
   double y = 0.0;
-  for (int r = 0; r < m; r++) {
-    double t = (lane < r) ? A[r * lda + lane] * y : 0.0;
-    double s = warp_sum(t);
-    double yr = (b[r] - s) / diag[r];
-    if (lane == r) y = yr;
+  for (int j = 0; j < m; j++) {
+    const double yj = __shfl_sync(0xffffffffu, rhs * dinv, j);
+    if (lane == j) y = yj;
+    if (lane > j && lane < m) rhs = fma(-A[lane * lda + j], yj, rhs);
   }
   // w = H_0 ... H_{m-1} [y; 0]
   double w = lane < m ? y : 0.0;
   for (int k = m - 1; k >= 0; k--) {
     double v = (lane >= k && lane < N) ? A[k * lda + lane] : 0.0;
-    double s = warp_sum(v * w) * beta[k];
-    w -= s * v;
+    double sdot = warp_sum(v * w) * beta[k];
+    w -= sdot * v;
   }
   return lane < N ? w : 0.0;
 }

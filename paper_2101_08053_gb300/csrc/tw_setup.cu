@@ -204,6 +204,7 @@ __global__ void __launch_bounds__(32 * TW_WQ_WARPS) k_wq_weights(Dir D0, Dir D1,
   __shared__ double sA[TW_WQ_WARPS][TW_WIN * (TW_QMAX + 1)];
   __shared__ double sb[TW_WQ_WARPS][TW_WIN], sd[TW_WQ_WARPS][TW_WIN], sbeta[TW_WQ_WARPS][TW_WIN];
   __shared__ int sing[TW_WQ_WARPS];
+  __shared__ double sss[TW_WQ_WARPS][32];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i = blockIdx.x * TW_WQ_WARPS + wib;
   if (i >= D.n) return;
@@ -232,7 +233,7 @@ __global__ void __launch_bounds__(32 * TW_WQ_WARPS) k_wq_weights(Dir D0, Dir D1,
   }
   if (lane == 0) sing[wib] = 0;
   __syncwarp();
-  double wc = warp_minnorm(m, N, A, lda, sb[wib], sd[wib], sbeta[wib], lane, &sing[wib]);
+  double wc = warp_minnorm(m, N, A, lda, sb[wib], sd[wib], sbeta[wib], sss[wib], lane, &sing[wib]);
   __syncwarp();
   if (lane == 0 && sing[wib]) atomicOr(flag, TWF_SINGULAR);
   for (int c = lane; c < D.qmax; c += 32) {
@@ -1061,6 +1062,7 @@ __global__ void __launch_bounds__(TW_DWQ_THREADS)
   __shared__ double sb[TW_DWQ_THREADS / 32][TW_WIN], sd[TW_DWQ_THREADS / 32][TW_WIN],
       sbeta[TW_DWQ_THREADS / 32][TW_WIN];
   __shared__ int sing[TW_DWQ_THREADS / 32];
+  __shared__ double sss[TW_DWQ_THREADS / 32][32];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int lda = TW_QMAX + 1;
   for (int li = wib; li < 2 * p && np_ > 0; li += TW_DWQ_THREADS / 32) {
@@ -1106,7 +1108,7 @@ __global__ void __launch_bounds__(TW_DWQ_THREADS)
     if (lane == 0) sing[wib] = 0;
     __syncwarp();
     double wv = 0.0;
-    if (N > 0) wv = warp_minnorm(m, N, A, lda, sb[wib], sd[wib], sbeta[wib], lane, &sing[wib]);
+    if (N > 0) wv = warp_minnorm(m, N, A, lda, sb[wib], sd[wib], sbeta[wib], sss[wib], lane, &sing[wib]);
     __syncwarp();
     if (lane == 0 && sing[wib]) atomicOr(flag, TWF_SINGULAR);
     for (int k = lane; k < np_; k += 32) Wt[li][k] = 0.0;
