@@ -951,66 +951,81 @@ __global__ void __launch_bounds__(TW_DWQ_THREADS)
   __shared__ double Wt[2 * TW_MAXP][TW_LQMAX];         // refined weights of l = s + row
   int ewlo = max(0, s - p), ewhi = min(D.nel - 1, s + p - 1);
   int nwe = ewhi - ewlo + 1;
-  if (threadIdx.x == 0) {
-    // refined points: base points + nested points next to t (R5)
-    int n = 0;
-    for (int e = ewlo; e <= ewhi; e++) {
-      int k0 = wq_off(e, p, D.nel), k1 = wq_off(e + 1, p, D.nel);
-      int m = k1 - k0;
-      int nb0 = n;
-      for (int k = k0; k < k1; k++) {
-        if (n < TW_LQMAX) {
-          xs[n] = D.xq[k];
-          xk[n] = k;
-        }
+  // refined points: base points + nested points next to t (R5).  Lane e of the
+  // first warp assembles and sorts window element e's points (at most p + 1),
+  // a warp scan of the counts places them
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x, e = ewlo + lane;
+    int m = 0, add = 0, k0 = 0;
+    if (lane < nwe) {
+      k0 = wq_off(e, p, D.nel);
+      m = wq_off(e + 1, p, D.nel) - k0;
+      if ((e == s - 1 || e == s) && m < p1) add = p1 - m;
+    }
+    const int cnt = m + add;
+    int incl = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    const int off = incl - cnt;
+    if (lane < nwe && total <= TW_LQMAX) {
+      double lx[TW_MAXP1 + 1];
+      int lk[TW_MAXP1 + 1];
+      int n = 0;
+      for (int k = k0; k < k0 + m; k++) {
+        lx[n] = D.xq[k];
+        lk[n] = k;
         n++;
       }
-      if ((e == s - 1 || e == s) && m < p1) {
+      if (add > 0) {
         // gaps (a, x1), (x1, x2), (x2, b); fewest points first, ties: middle,
         // then the gap next to t, then the other
-        int add = p1 - m;
         double ed[4] = {D.bp[e], D.xq[k0], D.xq[k0 + 1], D.bp[e + 1]};
-        int cnt[3] = {0, 0, 0};
+        int gc[3] = {0, 0, 0};
         int nearg = (e == s - 1) ? 2 : 0;
         int pref[3] = {1, nearg, 2 - nearg};
         for (int r = 0; r < add; r++) {
           int best = pref[0];
           for (int k = 1; k < 3; k++)
-            if (cnt[pref[k]] < cnt[best]) best = pref[k];
-          cnt[best]++;
+            if (gc[pref[k]] < gc[best]) best = pref[k];
+          gc[best]++;
         }
         for (int gp = 0; gp < 3; gp++)
-          for (int j = 0; j < cnt[gp]; j++) {
-            if (n < TW_LQMAX) {
-              xs[n] = ed[gp] + (ed[gp + 1] - ed[gp]) * (double)(j + 1) / (double)(cnt[gp] + 1);
-              xk[n] = -1;
-            }
+          for (int j = 0; j < gc[gp]; j++) {
+            lx[n] = ed[gp] + (ed[gp + 1] - ed[gp]) * (double)(j + 1) / (double)(gc[gp] + 1);
+            lk[n] = -1;
             n++;
           }
       }
-      if (n <= TW_LQMAX) {  // insertion sort of (x, k) pairs within the element
-        for (int a2 = nb0 + 1; a2 < n; a2++) {
-          double x = xs[a2];
-          int kk = xk[a2], b2 = a2 - 1;
-          while (b2 >= nb0 && xs[b2] > x) {
-            xs[b2 + 1] = xs[b2];
-            xk[b2 + 1] = xk[b2];
-            b2--;
-          }
-          xs[b2 + 1] = x;
-          xk[b2 + 1] = kk;
+      // insertion sort of the element's (x, k) pairs
+      for (int a2 = 1; a2 < n; a2++) {
+        double x = lx[a2];
+        int kk = lk[a2], b2 = a2 - 1;
+        while (b2 >= 0 && lx[b2] > x) {
+          lx[b2 + 1] = lx[b2];
+          lk[b2 + 1] = lk[b2];
+          b2--;
         }
+        lx[b2 + 1] = x;
+        lk[b2 + 1] = kk;
+      }
+      for (int j = 0; j < n; j++) {
+        xs[off + j] = lx[j];
+        xk[off + j] = lk[j];
       }
     }
-    if (n > TW_LQMAX) {
-      atomicOr(flag, TWF_LQMAX);
-      n = 0;
+    if (lane == 0) {
+      if (total > TW_LQMAX) atomicOr(flag, TWF_LQMAX);
+      npts = total > TW_LQMAX ? 0 : total;
     }
-    npts = n;
   }
-  // step 1: S columns by p local Boehm insertions (Eq. 10) on B_i's own knots
-  if (threadIdx.x < p) {
-    int i = s + threadIdx.x;
+  // step 1: S columns by p local Boehm insertions (Eq. 10) on B_i's own knots,
+  // in the second warp, concurrently with the first warp's point assembly
+  const int sc_col = (int)threadIdx.x - 32;
+  if (sc_col >= 0 && sc_col < p) {
+    int i = s + sc_col;
     double tau[2 * TW_MAXP + 2], c[TW_MAXP1], cn[TW_MAXP1];
     int L = p + 2;
     for (int k = 0; k < L; k++) tau[k] = D.U[i + k];
@@ -1034,7 +1049,7 @@ __global__ void __launch_bounds__(TW_DWQ_THREADS)
       tau[sp + 1] = t;
       L++;
     }
-    for (int r = 0; r <= p; r++) Sc[threadIdx.x][r] = c[r];
+    for (int r = 0; r <= p; r++) Sc[sc_col][r] = c[r];
   }
   __syncthreads();
   const int np_ = npts;
