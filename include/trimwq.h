@@ -214,6 +214,48 @@ int tw_l2_project_adjoint(tw_patch *patch, const tw_func *f, const int64_t *row_
                           const double *u, double *lam, double *grad, double tol, int maxit,
                           int *iters, double *relres, void *stream);
 
+/* Extended B-splines (Sect. 3 and Sect. 4.2: the paper stabilises every L2
+ * projection with the extended B-splines of Hoellig, Reif and Wipper).
+ * An active function is inner when an element of its support is regular,
+ * outer otherwise.  Each outer j is tied to the nearest array l + {0..p}^2 of
+ * inner functions (l within [j - 2p - 1, j + p + 1] per direction; nearest
+ * centre, ties to the smaller l2, then l1) with the coefficients e_{i,j} that
+ * carry the B-spline coefficients of every polynomial of degree <= p from the
+ * array to j.  E (n_rows x n_inner) holds the identity on inner rows and
+ * e_{i,j} on outer rows; the extended basis has mass matrix E^T M E and
+ * right-hand side E^T b, and a coefficient vector x of it is u = E x.
+ *
+ * tw_extension_build: builds the patch's extension tables once (later calls
+ * only report); info4 (host) = [n_inner, n_outer, nnz of E, nnz of E^T M E].
+ * Synchronises the patch's stream.  TW_EUNSUPPORTED when an outer function
+ * has no all-inner array within reach (the mesh is too coarse for the trim). */
+int tw_extension_build(tw_patch *patch, int64_t *info4);
+
+/* E as CSR (device, caller-owned): e_row_ptr[n_rows + 1], e_col/e_val[nnz of
+ * E]; outer rows hold their (p+1)^2 array entries (a2-major, ascending
+ * columns), zeros included.  Asynchronous.  TW_EINVAL before
+ * tw_extension_build. */
+int tw_extension_matrix(tw_patch *patch, int64_t *e_row_ptr, int32_t *e_col, double *e_val,
+                        void *stream);
+
+/* E^T M E from the FP64 CSR of tw_form_mass (device inputs) into device
+ * outputs x_row_ptr[n_inner + 1], x_col/x_val[nnz of E^T M E].  Row a holds
+ * every inner b reached through a stored M[r][s] with E[r][a], E[s][b]
+ * stored (structural zeros kept), columns ascending; each value is a
+ * fixed-order sum (deterministic).  Synchronises `stream` to check the input;
+ * TW_EINVAL if the CSR does not have the patch's pattern. */
+int tw_form_mass_extended(tw_patch *patch, const int64_t *row_ptr, const int32_t *col,
+                          const double *val, int64_t *x_row_ptr, int32_t *x_col, double *x_val,
+                          void *stream);
+
+/* Extended L2 projection: x from Jacobi-PCG on (E^T M E + (E^T M E)^T)/2
+ * x = E^T b(f) (the CSR of tw_form_mass_extended), returned as u = E x
+ * (u[n_rows], device).  tol, maxit, *iters, *relres as for tw_l2_project.
+ * Synchronises `stream` every few iterations; TW_ENOCONV if not converged. */
+int tw_l2_project_extended(tw_patch *patch, const tw_func *f, const int64_t *x_row_ptr,
+                           const int32_t *x_col, const double *x_val, double *u, double tol,
+                           int maxit, int *iters, double *relres, void *stream);
+
 /* Device copies of the classification: estate[nel1*nel2], fstate[n1*n2]
  * (uint8, TW_ELEM_* / TW_FUNC_*), act[n1*n2] (int32 active index or -1). */
 int tw_states(const tw_patch *patch, uint8_t *estate, uint8_t *fstate, int32_t *act,

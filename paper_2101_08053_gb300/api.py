@@ -87,6 +87,11 @@ def load(build: bool = True):
     L.tw_l2_project_adjoint.argtypes = [vp, C.POINTER(FuncDesc), vp, vp, vp, vp, vp, vp, vp,
                                         C.c_double, C.c_int, C.POINTER(C.c_int),
                                         C.POINTER(C.c_double), vp]
+    L.tw_extension_build.argtypes = [vp, i64p]
+    L.tw_extension_matrix.argtypes = [vp, vp, vp, vp, vp]
+    L.tw_form_mass_extended.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+    L.tw_l2_project_extended.argtypes = [vp, C.POINTER(FuncDesc), vp, vp, vp, vp, C.c_double,
+                                         C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double), vp]
     L.tw_states.argtypes = [vp, vp, vp, vp, vp]
     L.tw_patch_table.argtypes = [vp, C.c_int, vp, C.c_int64, i64p, vp]
     L.tw_launch_count.restype = C.c_int64
@@ -305,6 +310,57 @@ class Patch:
         if check:
             _check(rc)
         return grad[:m2 * m1].view(m2, m1), lam[:self.n_rows], it.value, rel.value
+
+    def extension(self):
+        """tw_extension_build: (n_inner, n_outer, nnz of E, nnz of E^T M E)."""
+        info = np.zeros(4, dtype=np.int64)
+        _check(load().tw_extension_build(self._h, info.ctypes.data_as(C.POINTER(C.c_int64))))
+        return tuple(int(v) for v in info)
+
+    def extension_matrix(self, stream=None):
+        """E as (row_ptr, col, val) device tensors (n_rows x n_inner)."""
+        torch = _torch()
+        n_inner, n_outer, nnz_e, nnz_x = self.extension()
+        rp = torch.empty(self.n_rows + 1, dtype=torch.int64, device="cuda")
+        col = torch.empty(max(nnz_e, 1), dtype=torch.int32, device="cuda")
+        val = torch.empty(max(nnz_e, 1), dtype=torch.float64, device="cuda")
+        _check(load().tw_extension_matrix(self._h, C.c_void_p(rp.data_ptr()),
+                                          C.c_void_p(col.data_ptr()), C.c_void_p(val.data_ptr()),
+                                          _stream(stream)))
+        return rp, col[:nnz_e], val[:nnz_e]
+
+    def form_mass_extended(self, csr, stream=None):
+        """E^T M E from the FP64 CSR of form_mass, as (row_ptr, col, val)."""
+        torch = _torch()
+        n_inner, n_outer, nnz_e, nnz_x = self.extension()
+        rp, col, val = csr
+        xrp = torch.empty(n_inner + 1, dtype=torch.int64, device="cuda")
+        xcol = torch.empty(max(nnz_x, 1), dtype=torch.int32, device="cuda")
+        xval = torch.empty(max(nnz_x, 1), dtype=torch.float64, device="cuda")
+        _check(load().tw_form_mass_extended(
+            self._h, C.c_void_p(rp.data_ptr()), C.c_void_p(col.data_ptr()),
+            C.c_void_p(val.data_ptr()), C.c_void_p(xrp.data_ptr()), C.c_void_p(xcol.data_ptr()),
+            C.c_void_p(xval.data_ptr()), _stream(stream)))
+        return xrp, xcol[:nnz_x], xval[:nnz_x]
+
+    def l2_project_extended(self, f, xcsr, tol=1e-12, maxit=None, stream=None, check=True):
+        """Extended L2 projection: (u = E x on the active basis, iterations, residual)."""
+        torch = _torch()
+        keep = []
+        fd = make_func_desc(f, keep)
+        n_inner = self.extension()[0]
+        rp, col, val = xcsr
+        u = torch.empty(max(self.n_rows, 1), dtype=torch.float64, device="cuda")
+        it = C.c_int(0)
+        rel = C.c_double(0)
+        rc = load().tw_l2_project_extended(
+            self._h, C.byref(fd), C.c_void_p(rp.data_ptr()), C.c_void_p(col.data_ptr()),
+            C.c_void_p(val.data_ptr()), C.c_void_p(u.data_ptr()), tol,
+            int(maxit if maxit is not None else 10 * max(n_inner, 1)), C.byref(it),
+            C.byref(rel), _stream(stream))
+        if check:
+            _check(rc)
+        return u[:self.n_rows], it.value, rel.value
 
     def states(self, stream=None):
         torch = _torch()

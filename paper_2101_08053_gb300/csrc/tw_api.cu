@@ -201,6 +201,7 @@ extern "C" int tw_patch_destroy(tw_patch *P) {
   if (!P) return TW_OK;
   for (int k = P->nallocs - 1; k >= 0; k--) cudaFreeAsync(P->allocs[k], P->stream);
   cudaStreamSynchronize(P->stream);
+  free(P->ext);
   free(P);
   return TW_OK;
 }

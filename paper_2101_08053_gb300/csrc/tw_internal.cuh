@@ -698,6 +698,9 @@ struct tw_patch {
   size_t arena_left;
   int arena_on;
   int64_t *i64tmp;
+  // extended B-spline tables (host struct with device pointers), built on
+  // demand by tw_extension_build
+  void *ext;
 };
 
 // host helpers shared by the translation units
@@ -729,6 +732,10 @@ RowArgs row_args(tw_patch *P);
 int cg_solve(tw_patch *P, const int64_t *rp, const int32_t *col, const double *val,
              const double *b, double *x, double tol, int maxit, int *iters, double *relres,
              cudaStream_t s);
+// the same for an n x n system with nnz entries (e.g. the extended mass matrix)
+int cg_solve_n(tw_patch *P, int64_t n, int64_t nnz, const int64_t *rp, const int32_t *col,
+               const double *val, const double *b, double *x, double tol, int maxit, int *iters,
+               double *relres, cudaStream_t s);
 int loss_run(tw_patch *P, const tw_func *g, const double *u, double *loss, double *dLdu,
              cudaStream_t s);
 int adjoint_run(tw_patch *P, const tw_func *f, const int64_t *rp, const int32_t *col,

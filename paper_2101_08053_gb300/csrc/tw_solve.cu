@@ -400,10 +400,9 @@ static void cg_iteration(const CgBufs &B, int it, cudaStream_t s) {
 // chunks of CG_CHUNK replayed from a CUDA graph (captured once per call on a
 // private stream, launched on s); the residual is read back after each chunk.
 #define CG_CHUNK 8
-static int cg_core(tw_patch *P, const int64_t *rp, const int32_t *col, const double *val,
-                   const double *b, double *u, double tol, int maxit, int *iters, double *relres,
-                   cudaStream_t s) {
-  int64_t n = P->n_rows, nnz = P->nnz;
+static int cg_core(tw_patch *P, int64_t n, int64_t nnz, const int64_t *rp, const int32_t *col,
+                   const double *val, const double *b, double *u, double tol, int maxit,
+                   int *iters, double *relres, cudaStream_t s) {
   if (n == 0) {
     if (iters) *iters = 0;
     if (relres) *relres = 0.0;
@@ -500,14 +499,20 @@ static int cg_impl(tw_patch *P, const tw_func *f, const int64_t *rp, const int32
   if (!b) return TW_ENOMEM;
   int rc = rhs_impl(P, f, b, s);
   if (rc) return rc;
-  return cg_core(P, rp, col, val, b, u, tol, maxit, iters, relres, s);
+  return cg_core(P, P->n_rows, P->nnz, rp, col, val, b, u, tol, maxit, iters, relres, s);
 }
 
 int cg_solve(tw_patch *P, const int64_t *rp, const int32_t *col, const double *val,
              const double *b, double *x, double tol, int maxit, int *iters, double *relres,
              cudaStream_t s) {
+  return cg_solve_n(P, P->n_rows, P->nnz, rp, col, val, b, x, tol, maxit, iters, relres, s);
+}
+
+int cg_solve_n(tw_patch *P, int64_t n, int64_t nnz, const int64_t *rp, const int32_t *col,
+               const double *val, const double *b, double *x, double tol, int maxit, int *iters,
+               double *relres, cudaStream_t s) {
   int mark = P->nallocs;
-  int rc = cg_core(P, rp, col, val, b, x, tol, maxit, iters, relres, s);
+  int rc = cg_core(P, n, nnz, rp, col, val, b, x, tol, maxit, iters, relres, s);
   release_to(P, mark);
   return rc;
 }

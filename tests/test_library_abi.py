@@ -30,7 +30,9 @@ def test_library_exports_every_declared_symbol():
 def test_header_symbols_cover_the_binding():
     syms = set(declared_symbols())
     for s in ["tw_patch_create", "tw_patch_destroy", "tw_form_mass", "tw_rhs", "tw_l2_project",
-              "tw_states", "tw_patch_info", "tw_patch_table", "tw_last_error", "tw_launch_count"]:
+              "tw_states", "tw_patch_info", "tw_patch_table", "tw_last_error", "tw_launch_count",
+              "tw_extension_build", "tw_extension_matrix", "tw_form_mass_extended",
+              "tw_l2_project_extended"]:
         assert s in syms
 
 
