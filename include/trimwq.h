@@ -256,6 +256,17 @@ int tw_l2_project_extended(tw_patch *patch, const tw_func *f, const int64_t *x_r
                            const int32_t *x_col, const double *x_val, double *u, double tol,
                            int maxit, int *iters, double *relres, void *stream);
 
+/* Differentiation of the extended L2 projection (as tw_l2_project_adjoint):
+ * u = E x from tw_l2_project_extended (same CSR), lam = E mu with
+ * (E^T M_s E) mu = E^T dL/du solved by the same CG, and grad as for
+ * tw_l2_project_adjoint with that lam (E does not depend on the density, so
+ * the gradient formula is unchanged).  TW_EINVAL without TW_COEF_DENSITY or
+ * before tw_extension_build.  Synchronises `stream`; deterministic. */
+int tw_l2_project_adjoint_extended(tw_patch *patch, const tw_func *f, const int64_t *x_row_ptr,
+                                   const int32_t *x_col, const double *x_val, const double *dLdu,
+                                   const double *u, double *lam, double *grad, double tol,
+                                   int maxit, int *iters, double *relres, void *stream);
+
 /* Device copies of the classification: estate[nel1*nel2], fstate[n1*n2]
  * (uint8, TW_ELEM_* / TW_FUNC_*), act[n1*n2] (int32 active index or -1). */
 int tw_states(const tw_patch *patch, uint8_t *estate, uint8_t *fstate, int32_t *act,

@@ -92,6 +92,9 @@ def load(build: bool = True):
     L.tw_form_mass_extended.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
     L.tw_l2_project_extended.argtypes = [vp, C.POINTER(FuncDesc), vp, vp, vp, vp, C.c_double,
                                          C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double), vp]
+    L.tw_l2_project_adjoint_extended.argtypes = [vp, C.POINTER(FuncDesc), vp, vp, vp, vp, vp,
+                                                 vp, vp, C.c_double, C.c_int,
+                                                 C.POINTER(C.c_int), C.POINTER(C.c_double), vp]
     L.tw_states.argtypes = [vp, vp, vp, vp, vp]
     L.tw_patch_table.argtypes = [vp, C.c_int, vp, C.c_int64, i64p, vp]
     L.tw_launch_count.restype = C.c_int64
@@ -362,6 +365,32 @@ class Patch:
             _check(rc)
         return u[:self.n_rows], it.value, rel.value
 
+    def l2_project_adjoint_extended(self, f, xcsr, dLdu, u, tol=1e-12, maxit=None, stream=None,
+                                    check=True):
+        """tw_l2_project_adjoint_extended: (dL/dd as (m2, m1), lambda = E mu,
+        iterations, residual)."""
+        torch = _torch()
+        keep = []
+        fd = make_func_desc(f, keep)
+        n_inner = self.extension()[0]
+        rp, col, val = xcsr
+        dLdu = dLdu.contiguous()
+        u = u.contiguous()
+        lam = torch.empty(max(self.n_rows, 1), dtype=torch.float64, device="cuda")
+        m2, m1 = self.density_shape()
+        grad = torch.empty(max(m2 * m1, 1), dtype=torch.float64, device="cuda")
+        it = C.c_int(0)
+        rel = C.c_double(0)
+        rc = load().tw_l2_project_adjoint_extended(
+            self._h, C.byref(fd), C.c_void_p(rp.data_ptr()), C.c_void_p(col.data_ptr()),
+            C.c_void_p(val.data_ptr()), C.c_void_p(dLdu.data_ptr()), C.c_void_p(u.data_ptr()),
+            C.c_void_p(lam.data_ptr()), C.c_void_p(grad.data_ptr()), tol,
+            int(maxit if maxit is not None else 10 * max(n_inner, 1)), C.byref(it),
+            C.byref(rel), _stream(stream))
+        if check:
+            _check(rc)
+        return grad[:m2 * m1].view(m2, m1), lam[:self.n_rows], it.value, rel.value
+
     def states(self, stream=None):
         torch = _torch()
         es = torch.empty(self.nel1 * self.nel2, dtype=torch.uint8, device="cuda")
@@ -452,27 +481,35 @@ class ProjectionLoss(torch.autograd.Function):
     """L(d) = sum_q omega_q detJ (u_h - g)^2, u_h the L2 projection of f onto
     the trimmed patch's spline space under c = rho(d) det J, as a function of
     the density coefficients d (m2 x m1).  forward: patch setup, formation,
-    CG and tw_loss; backward: tw_l2_project_adjoint."""
+    CG and tw_loss; backward: tw_l2_project_adjoint.  With extended=True the
+    projection and its adjoint run in the extended B-spline basis
+    (tw_form_mass_extended, tw_l2_project_extended and
+    tw_l2_project_adjoint_extended)."""
 
     @staticmethod
-    def forward(ctx, dcoef, spec, f, g, tol):
+    def forward(ctx, dcoef, spec, f, g, tol, extended):
         d = dcoef.detach().to("cpu", torch.float64).numpy()
         P = Patch(_density_spec(spec, d))
         csr = P.form_mass("fp64")
-        u, _, _ = P.l2_project(f, csr, tol=tol)
+        if extended:
+            csr = P.form_mass_extended(csr)
+            u, _, _ = P.l2_project_extended(f, csr, tol=tol)
+        else:
+            u, _, _ = P.l2_project(f, csr, tol=tol)
         L, dLdu = P.loss(u, g)
-        ctx.state = (P, csr, u, dLdu, f, tol)
+        ctx.state = (P, csr, u, dLdu, f, tol, extended)
         return L.to(dcoef.device, dcoef.dtype)
 
     @staticmethod
     def backward(ctx, gout):
-        P, csr, u, dLdu, f, tol = ctx.state
-        grad, _, _, _ = P.l2_project_adjoint(f, csr, dLdu, u, tol=tol)
+        P, csr, u, dLdu, f, tol, extended = ctx.state
+        adj = P.l2_project_adjoint_extended if extended else P.l2_project_adjoint
+        grad, _, _, _ = adj(f, csr, dLdu, u, tol=tol)
         ctx.state = None
-        return gout * grad.to(gout.device, gout.dtype), None, None, None, None
+        return gout * grad.to(gout.device, gout.dtype), None, None, None, None, None
 
 
-def projection_loss(dcoef, spec, f, g, tol=1e-13):
+def projection_loss(dcoef, spec, f, g, tol=1e-13, extended=False):
     """Differentiable projection loss (see ProjectionLoss)."""
     _torch()
-    return ProjectionLoss.apply(dcoef, spec, f, g, tol)
+    return ProjectionLoss.apply(dcoef, spec, f, g, tol, extended)

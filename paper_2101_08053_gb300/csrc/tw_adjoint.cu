@@ -783,4 +783,13 @@ int adjoint_run(tw_patch *P, const tw_func *f, const int64_t *rp, const int32_t 
   return rc;
 }
 
+// the gradient stage alone (lam given), for the extended projection's adjoint
+int adjoint_grad(tw_patch *P, const tw_func *f, const double *u, const double *lam, double *grad,
+                 cudaStream_t s) {
+  int ps = prof_start(s);
+  int rc = grad_impl(P, f, u, lam, grad, s);
+  prof_stop(ps, TW_STAGE_ADJOINT, s);
+  return rc;
+}
+
 }  // namespace tw

@@ -585,6 +585,30 @@ static int need_ext(tw_patch *P, const char *what) {
   return TW_OK;
 }
 
+// out = E A^{-1} E^T y for active-length y and out, A the symmetric part of
+// the extended mass matrix (CG to tol); the patch's stream must be s
+static int ext_solve(tw_patch *P, const int64_t *xrp, const int32_t *xcol, const double *xval,
+                     const double *y, double *out, double tol, int maxit, int *iters,
+                     double *relres, cudaStream_t st) {
+  const ExtTables *T = (const ExtTables *)P->ext;
+  const int mark = P->nallocs;
+  const int64_t n = P->n_rows, ni = T->X.n_inner;
+  double *yx = (double *)dalloc(P, sizeof(double) * (2 * ni + 2));
+  if (!yx) return TW_ENOMEM;
+  double *x = yx + ni + 1;
+  if (ni > 0) {
+    k_ext_restrict<<<GX(ni)>>>(T->X, y, yx);
+    TW_LAUNCH();
+  }
+  int rc = cg_solve_n(P, ni, T->nnz_x, xrp, xcol, xval, yx, x, tol, maxit, iters, relres, st);
+  if ((!rc || rc == TW_ENOCONV) && n > 0) {
+    k_ext_expand<<<GX(n)>>>(T->X, x, out);
+    TW_LAUNCH();
+  }
+  release_to(P, mark);
+  return rc;
+}
+
 }  // namespace tw
 
 using namespace tw;
@@ -666,28 +690,48 @@ extern "C" int tw_l2_project_extended(tw_patch *P, const tw_func *f, const int64
   }
   int rc = need_ext(P, "tw_l2_project_extended");
   if (rc) return rc;
-  const ExtTables *T = (const ExtTables *)P->ext;
   cudaStream_t keep = P->stream, st = (cudaStream_t)stream;
   P->stream = st;
   const int mark = P->nallocs;
-  const int64_t n = P->n_rows, ni = T->X.n_inner;
-  double *b = (double *)dalloc(P, sizeof(double) * (n + 2 * ni + 2));
+  double *b = (double *)dalloc(P, sizeof(double) * (P->n_rows + 1));
   if (!b) rc = TW_ENOMEM;
-  double *bx = b + n + 1, *x = bx + ni + 1;
   const int ps = prof_start(st);
   if (!rc) rc = rhs_launch(P, f, b, st);
-  if (!rc && ni > 0) {
-    k_ext_restrict<<<GX(ni)>>>(T->X, b, bx);
-    TW_LAUNCH();
-  }
-  if (!rc)
-    rc = cg_solve_n(P, ni, T->nnz_x, x_row_ptr, x_col, x_val, bx, x, tol, maxit, iters, relres,
-                    st);
-  if ((!rc || rc == TW_ENOCONV) && n > 0) {
-    k_ext_expand<<<GX(n)>>>(T->X, x, u);
-    TW_LAUNCH();
-  }
+  if (!rc) rc = ext_solve(P, x_row_ptr, x_col, x_val, b, u, tol, maxit, iters, relres, st);
   prof_stop(ps, TW_STAGE_CG, st);
+  release_to(P, mark);
+  P->stream = keep;
+  return rc;
+}
+
+extern "C" int tw_l2_project_adjoint_extended(tw_patch *P, const tw_func *f,
+                                              const int64_t *x_row_ptr, const int32_t *x_col,
+                                              const double *x_val, const double *dLdu,
+                                              const double *u, double *lam, double *grad,
+                                              double tol, int maxit, int *iters, double *relres,
+                                              void *stream) {
+  if (!P || !f || !x_row_ptr || !x_col || !x_val || !dLdu || !u || !lam || !grad) {
+    set_error("tw_l2_project_adjoint_extended: NULL argument");
+    return TW_EINVAL;
+  }
+  if (P->geo.coef_kind != TW_COEF_DENSITY) {
+    set_error("tw_l2_project_adjoint_extended: the patch has no density spline "
+              "(TW_COEF_DENSITY)");
+    return TW_EINVAL;
+  }
+  if (!(tol > 0) || maxit < 0) {
+    set_error("tw_l2_project_adjoint_extended: need tol > 0 and maxit >= 0");
+    return TW_EINVAL;
+  }
+  int rc = need_ext(P, "tw_l2_project_adjoint_extended");
+  if (rc) return rc;
+  cudaStream_t keep = P->stream, st = (cudaStream_t)stream;
+  P->stream = st;
+  const int mark = P->nallocs;
+  const int ps = prof_start(st);
+  rc = ext_solve(P, x_row_ptr, x_col, x_val, dLdu, lam, tol, maxit, iters, relres, st);
+  prof_stop(ps, TW_STAGE_CG, st);
+  if (!rc) rc = adjoint_grad(P, f, u, lam, grad, st);
   release_to(P, mark);
   P->stream = keep;
   return rc;

@@ -741,6 +741,9 @@ int loss_run(tw_patch *P, const tw_func *g, const double *u, double *loss, doubl
 int adjoint_run(tw_patch *P, const tw_func *f, const int64_t *rp, const int32_t *col,
                 const double *val, const double *dLdu, const double *u, double *lam,
                 double *grad, double tol, int maxit, int *iters, double *relres, cudaStream_t s);
+// dL/dd from u and a given lambda (the patch's stream must be s)
+int adjoint_grad(tw_patch *P, const tw_func *f, const double *u, const double *lam, double *grad,
+                 cudaStream_t s);
 }  // namespace tw
 
 #define TW_LAUNCH() (tw::g_launches++)

@@ -248,3 +248,104 @@ def test_full_size_512_extension_against_oracle_e():
     u, it, rel = P.l2_project_extended(f, P.form_mass_extended(csr), tol=1e-12)
     u2, it2, rel2 = P.l2_project_extended(f, P.form_mass_extended(csr), tol=1e-12)
     assert torch.equal(u, u2) and it == it2
+
+
+# ---------------------------------------------------------------------------
+# differentiation of the extended projection (reading R12 with u = E x)
+
+G_FN = synth.func_gauss(8.0, 0.3, 0.7)
+
+
+def _density_case(seed=11, nel=(9, 8), m=6, p=3, r=0.29):
+    dens = synth.density(np.random.default_rng(seed), q=2, m=m)
+    return synth.make_spec(p, nel, synth.circle(0.5, 0.5, r), coef=dens)
+
+
+def _with_coef(spec, coef):
+    s = dict(spec)
+    c = dict(spec["coef"])
+    c["coef"] = np.asarray(coef, dtype=np.float64).reshape(c["coef"].shape)
+    s["coef"] = c
+    return s
+
+
+def test_extended_adjoint_lambda_against_oracle_system():
+    spec = _density_case(nel=(14, 13), m=8)
+    P, (ni, no, nnz_e, nnz_x) = _gpu(spec)
+    assert no > 0
+    csr = P.form_mass("fp64")
+    xcsr = P.form_mass_extended(csr)
+    u, _, _ = P.l2_project_extended(G_FN, xcsr, tol=1e-13)
+    L, dl = P.loss(u, G_FN)
+    grad, lam, it, rel = P.l2_project_adjoint_extended(G_FN, xcsr, dl, u, tol=1e-13)
+    O = oracle.Patch(spec)
+    X = Extension(O)
+    lamh = lam.cpu().numpy()
+    mu = lamh[X.act[X.inner]]
+    # lam = E mu on every row, and mu solves the oracle's extended adjoint system
+    assert np.max(np.abs(X.E @ mu - lamh)) <= 1e-14 * np.max(np.abs(lamh))
+    orp, ocol, oval = O.form()
+    n = O.n_rows
+    M = sp.csr_matrix((oval, ocol, orp), shape=(n, n))
+    A = X.E.T @ (0.5 * (M + M.T)) @ X.E
+    r = X.E.T @ dl.cpu().numpy()
+    assert np.linalg.norm(A @ mu - r) <= 1e-11 * np.linalg.norm(r)
+    # the gradient stage with this lam and u equals the oracle's
+    Ograd = O.density_grad(u.cpu().numpy(), lamh, G_FN)
+    ref = np.max(np.abs(Ograd))
+    assert np.max(np.abs(grad.cpu().numpy() - Ograd)) <= 1e-12 * ref
+
+
+def _dense_extended_loss(spec):
+    """L(d) with the GPU's own M(d), b(d), E and tw_loss; u = E x by a dense
+    solve of the extended system."""
+    from paper_2101_08053_gb300 import Patch
+    P = Patch(spec)
+    ni = P.extension()[0]
+    csr = P.form_mass("fp64")
+    rp, col, val = _csr_host(csr)
+    n = P.n_rows
+    M = sp.csr_matrix((val, col, rp), shape=(n, n))
+    erp, ecol, ev = _csr_host(P.extension_matrix())
+    E = sp.csr_matrix((ev, ecol, erp), shape=(n, ni))
+    A = (E.T @ (0.5 * (M + M.T)) @ E).toarray()
+    b = P.rhs(G_FN).cpu().numpy()
+    u = E @ np.linalg.solve(A, E.T @ b)
+    L, dl = P.loss(torch.from_numpy(u).cuda(), G_FN)
+    return L.item(), u, dl, P, csr
+
+
+def test_extended_gradient_against_finite_differences():
+    spec = _density_case(nel=(11, 10), r=0.33)  # 14 outer functions
+    d0 = spec["coef"]["coef"].ravel().copy()
+    L, u, dl, P, csr = _dense_extended_loss(spec)
+    xcsr = P.form_mass_extended(csr)
+    grad, lam, it, rel = P.l2_project_adjoint_extended(G_FN, xcsr, dl, torch.from_numpy(u).cuda(),
+                                                       tol=1e-14)
+    grad = grad.cpu().numpy().ravel()
+    scale = np.max(np.abs(grad))
+    h = 1e-4
+    rng = np.random.default_rng(9)
+    for k in list(rng.choice(d0.size, 4, replace=False)):
+        dp, dm = d0.copy(), d0.copy()
+        dp[k] += h
+        dm[k] -= h
+        fd = (_dense_extended_loss(_with_coef(spec, dp))[0] -
+              _dense_extended_loss(_with_coef(spec, dm))[0]) / (2 * h)
+        assert abs(fd - grad[k]) <= 1e-6 * scale, (k, fd, grad[k])
+
+
+def test_extended_autograd_matches_adjoint():
+    from paper_2101_08053_gb300 import Patch, projection_loss
+    spec = _density_case(nel=(10, 10))
+    d = torch.tensor(spec["coef"]["coef"], dtype=torch.float64, requires_grad=True)
+    L = projection_loss(d, spec, G_FN, G_FN, extended=True)
+    L.backward()
+    P = Patch(spec)
+    P.extension()
+    xcsr = P.form_mass_extended(P.form_mass("fp64"))
+    u, _, _ = P.l2_project_extended(G_FN, xcsr, tol=1e-13)
+    L2, dl = P.loss(u, G_FN)
+    grad, _, _, _ = P.l2_project_adjoint_extended(G_FN, xcsr, dl, u, tol=1e-13)
+    assert L.item() == L2.item()
+    assert torch.equal(d.grad, grad.cpu())
