@@ -443,6 +443,9 @@ def run_ours(args, rank, world, local_rank):
     precision = None
     if not args.no_precision:
         precision = run_precision(api, torch, args, stream, flush)
+    extension = None
+    if not args.no_extension:
+        extension = run_extension(api, torch, args, stream)
 
     # roofline of the dominant kernel (interior rows, FP64 DFMA-bound)
     flops = 0.0
@@ -464,7 +467,7 @@ def run_ours(args, rank, world, local_rank):
         "value": value, "ms": ms, "nnz_step": nnz_step, "infos": infos, "launches": launches,
         "clocks": clocks, "e2e_ms": e2e_ms, "h2d": h2d, "d2h": d2h, "stage_ms": stage_ms,
         "stage_ms_batched": stage_ms_batched, "modes": modes, "batched": batched,
-        "adjoint": adjoint, "precision": precision,
+        "adjoint": adjoint, "precision": precision, "extension": extension,
         "roofline": {"bound": "alu", "kernel": "k_interior (interior rows, WQ + sum factorisation)",
                      "achieved": round(achieved, 4), "peak": peak, "unit": "TFLOP/s",
                      "frac": round(achieved / peak, 4), "traffic": interior_traffic(),
@@ -662,6 +665,61 @@ def run_adjoint(api, torch, args, stream):
             "cg_iterations_forward_adjoint": list(its[-1]), "n_coefficients": 1024}
 
 
+def run_extension(api, torch, args, stream):
+    """Extended B-splines on the 512^2, p = 4 patch of the sweep (spline
+    geometry, c = det J, 12-point B-spline hole): build of the extension
+    tables, formation of E^T M E, and the L2 projection of sin(2x) cos(3y)
+    with and without the extension (CG iterations, time, largest coefficient,
+    relative L2 error from tw_loss)."""
+    spec = synth.config2(p=4, nel=512)
+    f = synth.func_sincos(2.0, 3.0)
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        e0, e1 = ev(), ev()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1)
+
+    acc = {"build": [], "form_extended": [], "project_extended": [], "project_plain": []}
+    for step in range(max(1, args.warmup) + max(1, args.steps)):
+        P = api.Patch(spec)
+        csr = P.form_mass("fp64")
+        info, t_b = timed(P.extension)
+        xcsr, t_x = timed(lambda: P.form_mass_extended(csr))
+        (ue, it_e, rel_e), t_pe = timed(lambda: P.l2_project_extended(f, xcsr, tol=1e-12,
+                                                                      check=False))
+        (u0, it_0, rel_0), t_p0 = timed(lambda: P.l2_project(f, csr, tol=1e-12, check=False))
+        if step >= max(1, args.warmup):
+            for k, t in zip(acc, (t_b, t_x, t_pe, t_p0)):
+                acc[k].append(t)
+        if step == max(1, args.warmup) + max(1, args.steps) - 1:
+            zero = torch.zeros_like(ue)
+            fn2 = P.loss(zero, f)[0].item()
+            err_e = (P.loss(ue, f)[0].item() / fn2) ** 0.5
+            err_0 = (P.loss(u0, f)[0].item() / fn2) ** 0.5
+            umax_e = torch.max(torch.abs(ue)).item()
+            umax_0 = torch.max(torch.abs(u0)).item()
+            n_rows, nnz = P.n_rows, P.nnz
+        P.close()
+    ms = {k: round(float(np.mean(v)), 3) for k, v in acc.items()}
+    n_inner, n_outer, nnz_e, nnz_x = info
+    return {"workload": "512x512 elements, p = 4, perturbed spline geometry (c = det J), "
+                        "12-point cubic B-spline hole; f = sin(2x) cos(3y)",
+            "ms": ms, "rows": n_rows, "inner": n_inner, "outer": n_outer, "nnz": nnz,
+            "nnz_extended": nnz_x,
+            "form_extended_nnz_per_s": round(nnz_x / (ms["form_extended"] * 1e-3), 1),
+            "cg_iterations": {"extended": it_e, "plain": it_0},
+            "cg_relres": {"extended": rel_e, "plain": rel_0},
+            "max_abs_coefficient": {"extended": umax_e, "plain": umax_0},
+            "rel_l2_error": {"extended": err_e, "plain": err_0}}
+
+
 def oracle_sample(seconds_budget=None, rows_per_patch=300, seed=0):
     """Oracle time for the whole workload, extrapolated from full set-up plus a
     seeded sample of rows per patch (single thread)."""
@@ -702,6 +760,8 @@ def main():
                     help="skip the density-gradient (adjoint) section")
     ap.add_argument("--no-precision", action="store_true",
                     help="skip the 1024^2 precision-variant section")
+    ap.add_argument("--no-extension", action="store_true",
+                    help="skip the extended B-spline section")
     args = ap.parse_args()
     if args.case:
         select_case(args.case)
@@ -763,7 +823,7 @@ def main():
                 "stage_ms_per_step_batched": r["stage_ms_batched"],
                 "precision_modes_formation_only": r["modes"],
                 "batched_config4": r["batched"], "adjoint_config5": r["adjoint"],
-                "precision_config3": r["precision"]}
+                "precision_config3": r["precision"], "extension_config2": r["extension"]}
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()

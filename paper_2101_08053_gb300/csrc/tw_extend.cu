@@ -15,6 +15,7 @@
 // E^T M E and the right-hand side E^T b; its L2 projection solves
 // E^T M_s E x = E^T b and returns u = E x.
 #include <climits>
+#include <mutex>
 
 #include "tw_internal.cuh"
 
@@ -40,6 +41,8 @@ struct Ext {
   const int32_t *inng;      // g -> inner index or -1
   const int32_t *outg;      // g -> outer index or -1
   const int32_t *inner_g;   // inner index -> g
+  const int32_t *ainn;      // active row -> inner index or -1
+  const int32_t *aout;      // active row -> outer index or -1
   const int32_t *arr;       // outer index -> g of its array's first member l
   const int32_t *ocol;      // outer index x pp: inner indices of the array (a2-major)
   const double *oval;       // outer index x pp: e1[a1] * e2[a2]
@@ -217,11 +220,16 @@ __global__ void k_ext_tlist(Ext X, int64_t *cnt, int32_t *et_r, double *et_e) {
 
 // ---------------------------------------------------------------------------
 // E^T M E.  Row a is a plain copy of M's row when a is no array member and
-// all its active neighbours are inner; otherwise its columns are the inner b
-// reached through a's transposed list, M's band and the neighbours' arrays,
-// collected as a bitmask over the window |b - a| <= 5p + 2 (one warp per row;
-// atomicOr of bits is order-independent) and each value is the fixed-order
-// sum  sum_{r in col(a)} E[r][a] sum_{s in col(b)} E[s][b] M[r][s].
+// all its active neighbours are inner ("copy rows", almost all of them);
+// otherwise ("near rows", next to the trim) its columns are the inner b
+// reached through a's transposed list, M's band and the neighbours' arrays.
+// The pattern is counted at build time as a bitmask over the window
+// |b - a| <= 5p + 2 (one warp per row; atomicOr of bits is order-independent).
+// A near row's values accumulate in a dense window of shared memory:
+//   row a = sum_{r in col(a)} E[r][a] sum_{s in M's row r} M[r][s] E[s][.]
+// with lanes prefetching 32 entries of M's row and the entries applied one
+// after another (lanes over the array of an outer s), so every value is a
+// fixed-order sum.
 
 __device__ __forceinline__ bool ext_row_is_copy(const Ext &X, int64_t a, int lane, int *count) {
   const int n1 = X.n1, n2 = X.n2, p = X.p, w = 2 * p + 1;
@@ -288,13 +296,16 @@ __device__ bool ext_row_bits(const Ext &X, int64_t a, int lane, unsigned *bm, in
   return true;
 }
 
-__global__ void __launch_bounds__(TW_EXT_THREADS) k_ext_xcount(Ext X, int64_t *cnt, int *flag) {
+__global__ void __launch_bounds__(TW_EXT_THREADS)
+    k_ext_xcount(Ext X, int64_t *cnt, int32_t *near_row, int *flag) {
   __shared__ unsigned bm_all[TW_EXT_WARPS][TW_EXT_WORDS];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t a = (int64_t)blockIdx.x * TW_EXT_WARPS + wib;
   if (a >= X.n_inner) return;
   int c;
-  if (ext_row_is_copy(X, a, lane, &c)) {
+  const bool copy = ext_row_is_copy(X, a, lane, &c);
+  if (lane == 0) near_row[a] = !copy;
+  if (copy) {
     if (lane == 0) cnt[a] = c;
     return;
   }
@@ -311,61 +322,127 @@ __global__ void __launch_bounds__(TW_EXT_THREADS) k_ext_xcount(Ext X, int64_t *c
   if (lane == 0) cnt[a] = n;
 }
 
-// M[r][s] from the CSR (0 outside the row's pattern)
-__device__ __forceinline__ double csr_at(const int64_t *rp, const int32_t *col, const double *val,
-                                         int32_t r, int32_t s) {
-  int64_t lo = rp[r], hi = rp[r + 1] - 1;
-  while (lo <= hi) {
-    const int64_t m = (lo + hi) >> 1;
-    const int32_t c = col[m];
-    if (c == s) return val[m];
-    if (c < s) lo = m + 1;
-    else hi = m - 1;
-  }
-  return 0.0;
-}
-
 __global__ void __launch_bounds__(TW_EXT_THREADS)
-    k_ext_xfill(Ext X, const int64_t *rp, const int32_t *col, const double *val,
-                const int64_t *xrp, int32_t *xcol, double *xval, int *flag) {
-  __shared__ unsigned bm_all[TW_EXT_WARPS][TW_EXT_WORDS];
+    k_ext_xcopy(Ext X, const int32_t *near_row, const int64_t *rp, const int32_t *col,
+                const double *val, const int64_t *xrp, int32_t *xcol, double *xval, int *flag) {
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t a = (int64_t)blockIdx.x * TW_EXT_WARPS + wib;
-  if (a >= X.n_inner) return;
+  if (a >= X.n_inner || near_row[a]) return;
   const int64_t x0 = xrp[a], len = xrp[a + 1] - x0;
-  int c;
-  if (ext_row_is_copy(X, a, lane, &c)) {
-    const int32_t r = X.act[X.inner_g[a]];
-    const int64_t m0 = rp[r];
-    if (rp[r + 1] - m0 != len) {
-      if (lane == 0) atomicOr(flag, TWF_EXT_CSR);
-      return;
-    }
-    int bad = 0;
-    for (int64_t k = lane; k < len; k += 32) {
-      const int32_t s = col[m0 + k];
-      const int32_t b = (s >= 0 && s < X.n_rows) ? X.inng[X.rowg[s]] : -1;
-      bad |= b < 0;
-      xcol[x0 + k] = b < 0 ? 0 : b;
-      xval[x0 + k] = val[m0 + k];
-    }
-    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(flag, TWF_EXT_CSR);
+  const int32_t r = X.act[X.inner_g[a]];
+  const int64_t m0 = rp[r];
+  if (rp[r + 1] - m0 != len) {
+    if (lane == 0) atomicOr(flag, TWF_EXT_CSR);
     return;
   }
-  const int n1 = X.n1, W = 5 * X.p + 2, side = 2 * W + 1;
-  unsigned *bm = bm_all[wib];
-  if (!ext_row_bits(X, a, lane, bm, W, side, flag)) return;
+  int bad = 0;
+  for (int64_t k = lane; k < len; k += 32) {
+    const int32_t s = col[m0 + k];
+    const int32_t b = (s >= 0 && s < X.n_rows) ? X.ainn[s] : -1;
+    bad |= b < 0;
+    xcol[x0 + k] = b < 0 ? 0 : b;
+    xval[x0 + k] = val[m0 + k];
+  }
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(flag, TWF_EXT_CSR);
+}
+
+#define TW_EXT_NEAR_WARPS 4
+// dynamic shared memory of k_ext_xnear for degree p: per warp the value
+// window (side^2 doubles) and its bitmask, in 4-byte words, rounded up to an
+// even count so that every warp's window starts 8-byte aligned
+__host__ __device__ __forceinline__ size_t ext_near_words(int p) {
+  const int side = 2 * (5 * p + 2) + 1, cells = side * side;
+  const size_t w = (size_t)cells * 2 + (((size_t)cells + 31) / 32);
+  return (w + 1) & ~(size_t)1;
+}
+
+__global__ void __launch_bounds__(32 * TW_EXT_NEAR_WARPS)
+    k_ext_xnear(Ext X, const int32_t *near_list, int64_t n_near, const int64_t *rp,
+                const int32_t *col, const double *val, const int64_t *xrp, int32_t *xcol,
+                double *xval, int *flag) {
+  extern __shared__ double ext_dyn[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t ni = (int64_t)blockIdx.x * TW_EXT_NEAR_WARPS + wib;
+  if (ni >= n_near) return;
+  const int p = X.p, p1 = p + 1, pp = X.pp, n1 = X.n1;
+  const int W = 5 * p + 2, side = 2 * W + 1, cells = side * side, words = (cells + 31) >> 5;
+  double *cv = (double *)((unsigned *)ext_dyn + (size_t)wib * ext_near_words(p));
+  unsigned *bm = (unsigned *)(cv + cells);
+  const int32_t a = near_list[ni];
   const int g = X.inner_g[a], a1 = g % n1, a2 = g / n1;
-  const int words = (side * side + 31) >> 5;
+  for (int k = lane; k < cells; k += 32) cv[k] = 0.0;
+  for (int k = lane; k < words; k += 32) bm[k] = 0u;
+  __syncwarp();
+  int bad = 0;
+  for (int64_t t = X.et_rp[a]; t < X.et_rp[a + 1]; t++) {
+    const int32_t r = X.et_r[t];
+    const double er = X.et_e[t];
+    const int64_t k_end = rp[r + 1];
+    for (int64_t k0 = rp[r]; k0 < k_end; k0 += 32) {
+      // lane j prefetches entry k0 + j: its weight and where it lands
+      const int64_t k = k0 + lane;
+      int cell = -1, o = -1;  // inner s: its cell; outer s: its index and array corner
+      int c1 = 0, c2 = 0;
+      double mv = 0.0;
+      if (k < k_end) {
+        const int32_t s = col[k];
+        if (s < 0 || s >= X.n_rows) {
+          bad = 1;
+        } else {
+          mv = er * val[k];
+          const int32_t bi = X.ainn[s];
+          if (bi >= 0) {
+            const int gb = X.inner_g[bi];
+            const int d1 = gb % n1 - a1 + W, d2 = gb / n1 - a2 + W;
+            if (d1 < 0 || d1 >= side || d2 < 0 || d2 >= side) bad = 1;
+            else cell = d2 * side + d1;
+          } else {
+            const int oo = X.aout[s];
+            const int l = X.arr[oo];
+            c1 = l % n1 - a1 + W;
+            c2 = l / n1 - a2 + W;
+            if (c1 < 0 || c1 + p >= side || c2 < 0 || c2 + p >= side) bad = 1;
+            else o = oo;
+          }
+        }
+      }
+      const int nk = (int)min((int64_t)32, k_end - k0);
+      for (int j = 0; j < nk; j++) {
+        const double mj = __shfl_sync(0xffffffffu, mv, j);
+        const int cj = __shfl_sync(0xffffffffu, cell, j);
+        const int oj = __shfl_sync(0xffffffffu, o, j);
+        const int q1 = __shfl_sync(0xffffffffu, c1, j), q2 = __shfl_sync(0xffffffffu, c2, j);
+        if (cj >= 0) {
+          if (lane == 0) {
+            cv[cj] += mj;
+            bm[cj >> 5] |= 1u << (cj & 31);
+          }
+        } else if (oj >= 0) {
+          for (int q = lane; q < pp; q += 32) {
+            const int c = (q2 + q / p1) * side + q1 + q % p1;
+            cv[c] = fma(mj, X.oval[(int64_t)oj * pp + q], cv[c]);
+            atomicOr(&bm[c >> 5], 1u << (c & 31));
+          }
+        }
+        __syncwarp();
+      }
+    }
+  }
+  if (__any_sync(0xffffffffu, bad)) {
+    if (lane == 0) atomicOr(flag, TWF_EXT_CSR);
+    return;
+  }
+  // write the window's cells in ascending g order (row-major in (b2, b1))
+  const int64_t x0 = xrp[a], len = xrp[a + 1] - x0;
   int64_t base = 0;
   for (int w0 = 0; w0 < words; w0 += 32) {
     const int wi = w0 + lane;
     unsigned bits = wi < words ? bm[wi] : 0u;
     const int nb = __popc(bits);
     int incl = nb;
-    for (int o = 1; o < 32; o <<= 1) {
-      const int v = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += v;
+    for (int d = 1; d < 32; d <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += v;
     }
     int64_t k = base + incl - nb;
     while (bits) {
@@ -373,24 +450,28 @@ __global__ void __launch_bounds__(TW_EXT_THREADS)
       bits &= bits - 1;
       const int idx = wi * 32 + bit;
       const int b1 = a1 + idx % side - W, b2 = a2 + idx / side - W;
-      const int32_t b = X.inng[b2 * n1 + b1];
-      double v = 0.0;
-      for (int64_t t = X.et_rp[a]; t < X.et_rp[a + 1]; t++) {
-        const int32_t r = X.et_r[t];
-        double inner = 0.0;
-        for (int64_t q = X.et_rp[b]; q < X.et_rp[b + 1]; q++)
-          inner += X.et_e[q] * csr_at(rp, col, val, r, X.et_r[q]);
-        v += X.et_e[t] * inner;
-      }
       if (k < len) {
-        xcol[x0 + k] = b;
-        xval[x0 + k] = v;
+        xcol[x0 + k] = X.inng[b2 * n1 + b1];
+        xval[x0 + k] = cv[idx];
       }
       k++;
     }
     base += __shfl_sync(0xffffffffu, incl, 31);
   }
   if (base != len && lane == 0) atomicOr(flag, TWF_EXT_CSR);
+}
+
+__global__ void k_ext_amaps(int64_t nf, const int32_t *act, const int32_t *inng,
+                            const int32_t *outg, int32_t *ainn, int32_t *aout) {
+  int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= nf || act[g] < 0) return;
+  ainn[act[g]] = inng[g];
+  aout[act[g]] = outg[g];
+}
+
+__global__ void k_ext_compact(int64_t n, const int32_t *flag, const int32_t *pos, int32_t *list) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && flag[i]) list[pos[i]] = (int32_t)i;
 }
 
 // E^T y (inner) and E x (active)
@@ -448,7 +529,9 @@ struct ExtTables {
   Ext X;
   int64_t *pos;      // g: packed (inner before, outer before)
   int64_t *xrp;      // E^T M E row pointer (n_inner + 1)
-  int64_t nnz_x, nnz_t;
+  int32_t *near_row; // inner index: 1 for a near row (not a copy of M's row)
+  int32_t *near_list;
+  int64_t nnz_x, nnz_t, n_near;
 };
 
 static int ext_flag(tw_patch *P, const char *what) {
@@ -510,6 +593,13 @@ static int ext_build_impl(tw_patch *P) {
   TW_LAUNCH();
   k_ext_arrays<<<GX(nf)>>>(n1, n2, p, inng, ok);
   TW_LAUNCH();
+  int32_t *ainn = (int32_t *)dalloc(P, sizeof(int32_t) * (n + 1));
+  int32_t *aout = (int32_t *)dalloc(P, sizeof(int32_t) * (n + 1));
+  if (!ainn || !aout) return TW_ENOMEM;
+  k_ext_amaps<<<GX(nf)>>>(nf, P->act, inng, outg, ainn, aout);
+  TW_LAUNCH();
+  X.ainn = ainn;
+  X.aout = aout;
   int64_t htot = 0;
   cudaMemcpyAsync(&htot, tot, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
   if ((rc = check_cuda(cudaStreamSynchronize(st), "tw_extension_build"))) return rc;
@@ -527,7 +617,12 @@ static int ext_build_impl(tw_patch *P) {
   int64_t *et_rp = (int64_t *)dalloc(P, sizeof(int64_t) * (ni + 1));
   int64_t *xcnt = (int64_t *)dalloc(P, sizeof(int64_t) * (ni + 1));
   T->xrp = (int64_t *)dalloc(P, sizeof(int64_t) * (ni + 1));
-  if (!arr || !ocol || !oval || !near || !tcnt || !et_rp || !xcnt || !T->xrp) return TW_ENOMEM;
+  T->near_row = (int32_t *)dalloc(P, sizeof(int32_t) * (ni + 1));
+  int32_t *near_pos = (int32_t *)dalloc(P, sizeof(int32_t) * (ni + 1));
+  T->near_list = (int32_t *)dalloc(P, sizeof(int32_t) * (ni + 1));
+  if (!arr || !ocol || !oval || !near || !tcnt || !et_rp || !xcnt || !T->xrp || !T->near_row ||
+      !near_pos || !T->near_list)
+    return TW_ENOMEM;
   if (no > 0) {
     k_ext_outer<<<GX(no)>>>(A, B, no, outer_g, ok, inng, arr, ocol, oval, P->flag);
     TW_LAUNCH();
@@ -564,12 +659,22 @@ static int ext_build_impl(tw_patch *P) {
   X.et_e = et_e;
   if (ni > 0) {
     k_ext_xcount<<<(unsigned)((ni + TW_EXT_WARPS - 1) / TW_EXT_WARPS), TW_EXT_THREADS, 0, st>>>(
-        X, xcnt, P->flag);
+        X, xcnt, T->near_row, P->flag);
     TW_LAUNCH();
   }
   if ((rc = exclusive_scan_i64(xcnt, T->xrp, ni + 1, tot + 2, st, P))) return rc;
   cudaMemcpyAsync(&T->nnz_x, tot + 2, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
-  return ext_flag(P, "tw_extension_build");
+  int32_t *tot32 = (int32_t *)(tot + 3);
+  if ((rc = exclusive_scan_i32(T->near_row, near_pos, ni, tot32, st, P))) return rc;
+  if (ni > 0) {
+    k_ext_compact<<<GX(ni)>>>(ni, T->near_row, near_pos, T->near_list);
+    TW_LAUNCH();
+  }
+  int32_t hn = 0;
+  cudaMemcpyAsync(&hn, tot32, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  rc = ext_flag(P, "tw_extension_build");
+  T->n_near = hn;
+  return rc;
 }
 
 void ext_free(tw_patch *P) {
@@ -667,8 +772,22 @@ extern "C" int tw_form_mass_extended(tw_patch *P, const int64_t *row_ptr, const 
   cudaMemsetAsync(P->flag, 0, sizeof(int), st);
   cudaMemcpyAsync(x_row_ptr, T->xrp, sizeof(int64_t) * (ni + 1), cudaMemcpyDeviceToDevice, st);
   if (ni > 0) {
-    k_ext_xfill<<<(unsigned)((ni + TW_EXT_WARPS - 1) / TW_EXT_WARPS), TW_EXT_THREADS, 0, st>>>(
-        T->X, row_ptr, col, val, T->xrp, x_col, x_val, P->flag);
+    k_ext_xcopy<<<(unsigned)((ni + TW_EXT_WARPS - 1) / TW_EXT_WARPS), TW_EXT_THREADS, 0, st>>>(
+        T->X, T->near_row, row_ptr, col, val, T->xrp, x_col, x_val, P->flag);
+    TW_LAUNCH();
+  }
+  if (T->n_near > 0) {
+    static std::once_flag near_attr[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::call_once(near_attr[dev & 63], [] {
+      cudaFuncSetAttribute(k_ext_xnear, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(TW_EXT_NEAR_WARPS * ext_near_words(TW_MAXP) * 4));
+    });
+    const size_t smem = TW_EXT_NEAR_WARPS * ext_near_words(T->X.p) * 4;
+    k_ext_xnear<<<(unsigned)((T->n_near + TW_EXT_NEAR_WARPS - 1) / TW_EXT_NEAR_WARPS),
+                  32 * TW_EXT_NEAR_WARPS, smem, st>>>(T->X, T->near_list, T->n_near, row_ptr,
+                                                      col, val, T->xrp, x_col, x_val, P->flag);
     TW_LAUNCH();
   }
   rc = ext_flag(P, "tw_form_mass_extended");
