@@ -17,7 +17,7 @@ template <int P>
 struct CutSmem {
   static constexpr int W = 2 * P + 1, P1 = P + 1;
   double acc[W * W];
-  double rx[2][TW_RC], rw[2][TW_RC], rb[2][TW_RC][W];
+  double rx[2][TW_RC], rb[2][TW_RC][W];  // rb: weight x basis value
   double cg[TW_RC * TW_RC];
   double Z[W * TW_RC];
   double Tg[P1 * P1];
@@ -25,6 +25,9 @@ struct CutSmem {
   int nr[2], nnest[2], nest[2][TW_RC];
   double pv[2][TW_RC][P1], pd[2][TW_RC][P1];  // basis values / derivatives at the region points
   int pe[2][TW_RC];                            // and their elements
+  // spline geometry: control net contracted over a nested point's direction,
+  // [nested point][control row / column - (i - P)][x', y' along 1; x, y]
+  double T0[P][W][4], T1[P][W][4];
   const double *eM[P1 * P1];  // per support element: its matrix row of this test function
   int jact[W * W];            // active index of each row entry (-1: none)
   unsigned msk[8];            // ballots of the active entries, one per 32 entries
@@ -144,11 +147,11 @@ __device__ void cutrow_item(const RowArgs &a, int g, int32_t *__restrict__ col,
         if (lane < n) {
           const int k = D.qbeg[i] + lane;
           S.rx[d][lane] = D.xq[k];
-          S.rw[d][lane] = D.W[(size_t)i * D.qmax + lane];
+          const double wk = D.W[(size_t)i * D.qmax + lane];
           S.rk[d][lane] = k;
           for (int r = 0; r < W; r++) {
             int aa = i - P + r - D.qel[k];
-            S.rb[d][lane][r] = (aa >= 0 && aa <= P) ? D.Bq[k * P1 + aa] : 0.0;
+            S.rb[d][lane][r] = wk * ((aa >= 0 && aa <= P) ? D.Bq[k * P1 + aa] : 0.0);
           }
         }
       } else {
@@ -164,13 +167,14 @@ __device__ void cutrow_item(const RowArgs &a, int g, int32_t *__restrict__ col,
         if (lane < n) {
           const size_t k = (size_t)sl * TW_LQMAX + k0 + lane;
           S.rx[d][lane] = a.dwq_x[d][k];
-          S.rw[d][lane] = a.dwq_w[d][(((size_t)sl * P + (i - s)) * 2 + side) * TW_LQMAX + k0 + lane];
+          const double wk =
+              a.dwq_w[d][(((size_t)sl * P + (i - s)) * 2 + side) * TW_LQMAX + k0 + lane];
           S.rk[d][lane] = a.dwq_k[d][k];  // base points read c from the grid
           const int e = a.dwq_e[d][k];
           const double *Bv = a.dwq_B[d] + k * P1;
           for (int r = 0; r < W; r++) {
             int aa = i - P + r - e;
-            S.rb[d][lane][r] = (aa >= 0 && aa <= P) ? Bv[aa] : 0.0;
+            S.rb[d][lane][r] = wk * ((aa >= 0 && aa <= P) ? Bv[aa] : 0.0);
           }
         }
       }
@@ -222,6 +226,52 @@ __device__ void cutrow_item(const RowArgs &a, int g, int32_t *__restrict__ col,
     {
       const int na = S.nnest[0], nb = S.nnest[1];
       const int tot = na * m2 + (m1 - na) * nb;
+      // spline geometry: J at (nested x1, any x2) from the net contracted over
+      // direction 0 at x1 (4 (p+1) terms per pair instead of 4 (p+1)^2; the
+      // same sums in the same order as coef_from), and at (base x1, nested
+      // x2) from the net contracted over direction 1 at x2
+      const bool fact = !unit_c && a.G.geom_kind == TW_GEOM_SPLINE && na <= P && nb <= P;
+      if (fact) {
+        const int n2 = B.n;
+        for (int t = tid; t < (na + nb) * W; t += blockDim.x) {
+          const int n = t / W, rr = t % W;
+          const bool d0 = n < na;
+          const int ix = d0 ? S.nest[0][n] : S.nest[1][n - na];
+          double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+          if (d0) {
+            const int R = i2 - P + rr, e1 = S.pe[0][ix];
+            if (R >= 0 && R < n2)
+              for (int aa = 0; aa <= P; aa++) {
+                const double *pt = a.G.ctrl + 2 * ((size_t)R * a.G.n1 + (e1 + aa));
+                s0 += pt[0] * S.pd[0][ix][aa];
+                s1 += pt[1] * S.pd[0][ix][aa];
+                s2 += pt[0] * S.pv[0][ix][aa];
+                s3 += pt[1] * S.pv[0][ix][aa];
+              }
+            double *T = S.T0[n][rr];
+            T[0] = s0;
+            T[1] = s1;
+            T[2] = s2;
+            T[3] = s3;
+          } else {
+            const int Cc = i1 - P + rr, e2 = S.pe[1][ix];
+            if (Cc >= 0 && Cc < n1)
+              for (int b = 0; b <= P; b++) {
+                const double *pt = a.G.ctrl + 2 * ((size_t)(e2 + b) * a.G.n1 + Cc);
+                s0 += pt[0] * S.pv[1][ix][b];
+                s1 += pt[1] * S.pv[1][ix][b];
+                s2 += pt[0] * S.pd[1][ix][b];
+                s3 += pt[1] * S.pd[1][ix][b];
+              }
+            double *T = S.T1[n - na][rr];
+            T[0] = s0;
+            T[1] = s1;
+            T[2] = s2;
+            T[3] = s3;
+          }
+        }
+        __syncthreads();
+      }
       for (int t = tid; t < tot; t += blockDim.x) {
         int ia, ib;
         if (t < na * m2) {
@@ -239,24 +289,51 @@ __device__ void cutrow_item(const RowArgs &a, int g, int32_t *__restrict__ col,
               break;
             }
         }
-        S.cg[ia * TW_RC + ib] =
-            unit_c ? 1.0
-                   : coef_from(a.G, P, S.rx[0][ia], S.rx[1][ib], S.pe[0][ia], S.pv[0][ia],
-                               S.pd[0][ia], S.pe[1][ib], S.pv[1][ib], S.pd[1][ib]);
+        double c;
+        if (unit_c) {
+          c = 1.0;
+        } else if (fact) {
+          double xa = 0, ya = 0, xb = 0, yb = 0;
+          if (t < na * m2) {
+            // rows e2 + b of the net, contracted over direction 0 at x1
+            const double(*T)[4] = S.T0[t / m2] + (S.pe[1][ib] - (i2 - P));
+            for (int b = 0; b <= P; b++) {
+              xa += T[b][0] * S.pv[1][ib][b];
+              ya += T[b][1] * S.pv[1][ib][b];
+              xb += T[b][2] * S.pd[1][ib][b];
+              yb += T[b][3] * S.pd[1][ib][b];
+            }
+          } else {
+            // columns e1 + a, contracted over direction 1 at x2
+            const double(*T)[4] = S.T1[(t - na * m2) % nb] + (S.pe[0][ia] - (i1 - P));
+            for (int aa = 0; aa <= P; aa++) {
+              xa += T[aa][0] * S.pd[0][ia][aa];
+              ya += T[aa][1] * S.pd[0][ia][aa];
+              xb += T[aa][2] * S.pv[0][ia][aa];
+              yb += T[aa][3] * S.pv[0][ia][aa];
+            }
+          }
+          c = xa * yb - xb * ya;
+          if (a.G.coef_kind == TW_COEF_DENSITY) c *= density_at(a.G, S.rx[0][ia], S.rx[1][ib]);
+        } else {
+          c = coef_from(a.G, P, S.rx[0][ia], S.rx[1][ib], S.pe[0][ia], S.pv[0][ia], S.pd[0][ia],
+                        S.pe[1][ib], S.pv[1][ib], S.pd[1][ib]);
+        }
+        S.cg[ia * TW_RC + ib] = c;
       }
     }
     __syncthreads();
     for (int t = tid; t < W * m1; t += blockDim.x) {
       int r2 = t / m1, ia = t % m1;
       double s = 0.0;
-      for (int ib = 0; ib < m2; ib++) s = fma(S.rw[1][ib] * S.rb[1][ib][r2], S.cg[ia * TW_RC + ib], s);
+      for (int ib = 0; ib < m2; ib++) s = fma(S.rb[1][ib][r2], S.cg[ia * TW_RC + ib], s);
       S.Z[r2 * TW_RC + ia] = s;
     }
     __syncthreads();
     for (int t = tid; t < W * W; t += blockDim.x) {
       int r2 = t / W, q1 = t % W;
       double s = 0.0;
-      for (int ia = 0; ia < m1; ia++) s = fma(S.rw[0][ia] * S.rb[0][ia][q1], S.Z[r2 * TW_RC + ia], s);
+      for (int ia = 0; ia < m1; ia++) s = fma(S.rb[0][ia][q1], S.Z[r2 * TW_RC + ia], s);
       S.acc[t] += s;
     }
     __syncthreads();
