@@ -525,16 +525,24 @@ __global__ void k_curve_features(Curve C, double *feat, int *nfeat, int fcap, in
 // lines are solved here.  The visibility of a line's first interval is that of
 // its end on the element edge, i.e. the parity of the edge line's crossings
 // beyond it (the same ray test as curve_inside, read from the table).
-#define TW_CUT_THREADS 64
-__global__ void __launch_bounds__(TW_CUT_THREADS)
-    k_cut_rule(Curve C, Dir A, Dir B, const int32_t *cut_list, int ncut, const double *qgx,
-               const double *qgw, int q, const double *hits, const int *nh, const double *feat,
-               const int *nfeat, int fcap, int64_t *cnt, const int64_t *off, double *pts,
-               int32_t *cut_o, int *flag, double *scr, int cap,
-               unsigned long long *ovf) {
-  const int ci = blockIdx.x;
+// Cut-element rules (reading R6) in three flat passes, so that every lane of
+// the root finding has a Gauss line of its own (a block per element left
+// three quarters of the lanes idle):
+//  k_cut_breaks  thread per cut element: inner direction and the sorted
+//                breakpoints of the outer interval; (pieces) x q lines
+//  k_cut_lines   thread per Gauss line of every element: the curve's
+//                crossings of the line (stored) and the line's point count
+//  k_cut_write   thread per line: its points, after the scan of the counts
+// The points are grouped by element, then by line, visible interval and
+// Gauss point.
+
+// per element: cut_o, the breakpoints (br[ci * TW_BRCAP ..]) and its line count
+__global__ void k_cut_breaks(Dir A, Dir B, const int32_t *cut_list, int ncut, int q,
+                             const double *hits, const int *nh, const double *feat,
+                             const int *nfeat, int fcap, int32_t *cut_o, int32_t *nbr_out,
+                             double *br_all, int64_t *nlines, int *flag) {
+  const int ci = blockIdx.x * blockDim.x + threadIdx.x;
   if (ci >= ncut) return;
-  const int tid = threadIdx.x;
   const int e = cut_list[ci];
   const int e1 = e % A.nel, e2 = e / A.nel;
   const double a[2] = {A.bp[e1], B.bp[e2]}, b[2] = {A.bp[e1 + 1], B.bp[e2 + 1]};
@@ -542,165 +550,192 @@ __global__ void __launch_bounds__(TW_CUT_THREADS)
   const int hv = A.nel + 1;  // first horizontal knot line in the table
   // knot lines of the four edges: [o][side] (o = 0: x = const, o = 1: y = const)
   const int eline[2][2] = {{e1, e1 + 1}, {hv + e2, hv + e2 + 1}};
-  __shared__ double br[TW_BRCAP];
-  __shared__ int nbr, s_o, s_bad;
-  __shared__ int64_t scan[TW_CUT_THREADS];
-  if (tid == 0) {
-    int bad = 0;
-    // 1. extent of the curve in the box: edge crossings and tangent points,
-    //    each counted up to TW_CORNER beyond the element
-    double lo0 = 1e300, lo1 = 1e300, hi0 = -1e300, hi1 = -1e300;
-    for (int o = 0; o < 2; o++)
-      for (int sd = 0; sd < 2; sd++) {
-        int l = eline[o][sd];
-        double s = sd ? b[o] : a[o];
-        const double *h = hits + (size_t)l * TW_HITCAP;
-        for (int k = 0; k < nh[l]; k++) {
-          double v = h[k];
-          if (!(v > a[1 - o] - dl[1 - o] && v < b[1 - o] + dl[1 - o])) continue;
-          double X = o == 0 ? s : v, Y = o == 0 ? v : s;
-          lo0 = fmin(lo0, X); hi0 = fmax(hi0, X); lo1 = fmin(lo1, Y); hi1 = fmax(hi1, Y);
-        }
-      }
-    for (int kind = 0; kind < 2; kind++)
-      for (int k = 0; k < nfeat[kind]; k++) {
-        double X = feat[((size_t)kind * fcap + k) * 2], Y = feat[((size_t)kind * fcap + k) * 2 + 1];
-        if (X >= a[0] - dl[0] && X <= b[0] + dl[0] && Y >= a[1] - dl[1] && Y <= b[1] + dl[1]) {
-          lo0 = fmin(lo0, X); hi0 = fmax(hi0, X); lo1 = fmin(lo1, Y); hi1 = fmax(hi1, Y);
-        }
-      }
-    // equal extents within TW_TIE of the element size: o = 0
-    const int o = (hi0 - lo0 >= hi1 - lo1 - TW_TIE * fmax(b[0] - a[0], b[1] - a[1])) ? 0 : 1;
-    const int in = 1 - o;
-    // 2. breakpoints along o: crossings of the two edges parallel to o, tangent
-    //    points that fold the lines xi_o = const, the spline's segment joints
-    int n = 0;
-    br[n++] = a[o];
-    br[n++] = b[o];
+  double *br = br_all + (size_t)ci * TW_BRCAP;
+  int bad = 0;
+  // 1. extent of the curve in the box: edge crossings and tangent points,
+  //    each counted up to TW_CORNER beyond the element
+  double lo0 = 1e300, lo1 = 1e300, hi0 = -1e300, hi1 = -1e300;
+  for (int o = 0; o < 2; o++)
     for (int sd = 0; sd < 2; sd++) {
-      int l = eline[in][sd];
+      int l = eline[o][sd];
+      double sv = sd ? b[o] : a[o];
       const double *h = hits + (size_t)l * TW_HITCAP;
-      for (int k = 0; k < nh[l]; k++)
-        if (h[k] > a[o] && h[k] < b[o]) {
-          if (n >= TW_BRCAP) { bad = 1; break; }
-          br[n++] = h[k];
-        }
-    }
-    const int kinds[2] = {o, 2};
-    for (int kk = 0; kk < 2; kk++) {
-      int kind = kinds[kk];
-      for (int k = 0; k < nfeat[kind]; k++) {
-        const double *f = feat + ((size_t)kind * fcap + k) * 2;
-        double xo = f[o], xi = f[in];
-        if (xo > a[o] && xo < b[o] && xi >= a[in] && xi <= b[in]) {
-          if (n >= TW_BRCAP) { bad = 1; break; }
-          br[n++] = xo;
-        }
+      for (int k = 0; k < nh[l]; k++) {
+        double v = h[k];
+        if (!(v > a[1 - o] - dl[1 - o] && v < b[1 - o] + dl[1 - o])) continue;
+        double X = o == 0 ? sv : v, Y = o == 0 ? v : sv;
+        lo0 = fmin(lo0, X); hi0 = fmax(hi0, X); lo1 = fmin(lo1, Y); hi1 = fmax(hi1, Y);
       }
     }
+  for (int kind = 0; kind < 2; kind++)
+    for (int k = 0; k < nfeat[kind]; k++) {
+      double X = feat[((size_t)kind * fcap + k) * 2], Y = feat[((size_t)kind * fcap + k) * 2 + 1];
+      if (X >= a[0] - dl[0] && X <= b[0] + dl[0] && Y >= a[1] - dl[1] && Y <= b[1] + dl[1]) {
+        lo0 = fmin(lo0, X); hi0 = fmax(hi0, X); lo1 = fmin(lo1, Y); hi1 = fmax(hi1, Y);
+      }
+    }
+  // equal extents within TW_TIE of the element size: o = 0
+  const int o = (hi0 - lo0 >= hi1 - lo1 - TW_TIE * fmax(b[0] - a[0], b[1] - a[1])) ? 0 : 1;
+  const int in = 1 - o;
+  // 2. breakpoints along o: crossings of the two edges parallel to o, tangent
+  //    points that fold the lines xi_o = const, the spline's segment joints
+  int n = 0;
+  br[n++] = a[o];
+  br[n++] = b[o];
+  for (int sd = 0; sd < 2 && !bad; sd++) {
+    int l = eline[in][sd];
+    const double *h = hits + (size_t)l * TW_HITCAP;
+    for (int k = 0; k < nh[l]; k++)
+      if (h[k] > a[o] && h[k] < b[o]) {
+        if (n >= TW_BRCAP) { bad = 1; break; }
+        br[n++] = h[k];
+      }
+  }
+  const int kinds[2] = {o, 2};
+  for (int kk = 0; kk < 2 && !bad; kk++) {
+    int kind = kinds[kk];
+    for (int k = 0; k < nfeat[kind]; k++) {
+      const double *f = feat + ((size_t)kind * fcap + k) * 2;
+      double xo = f[o], xi = f[in];
+      if (xo > a[o] && xo < b[o] && xi >= a[in] && xi <= b[in]) {
+        if (n >= TW_BRCAP) { bad = 1; break; }
+        br[n++] = xo;
+      }
+    }
+  }
+  if (bad) {
+    atomicOr(flag, TWF_BRCAP);
+    n = 1;
+  } else {
     sort_small(br, n);
-    nbr = n;
-    s_o = o;
-    s_bad = bad;
-    if (cut_o) cut_o[ci] = o;
   }
-  __syncthreads();
-  if (s_bad) {
-    if (tid == 0) {
-      atomicOr(flag, TWF_BRCAP);
-      if (cnt) cnt[ci] = 0;
-    }
-    return;
+  cut_o[ci] = o;
+  nbr_out[ci] = n;
+  nlines[ci] = (int64_t)(n - 1) * q;
+}
+
+// the element of line li: the last ci with line_off[ci] <= li
+__device__ __forceinline__ int cut_line_elem(const int64_t *line_off, int ncut, int64_t li) {
+  int lo = 0, hi = ncut - 1;
+  while (lo < hi) {
+    const int m = (lo + hi + 1) >> 1;
+    if (line_off[m] <= li) lo = m;
+    else hi = m - 1;
   }
-  const int o = s_o, in = 1 - o;
-  // crossings of the edge line through each line's first end (xi_in = a_in)
-  const int lfirst = eline[in][0];
-  const double *eh = hits + (size_t)lfirst * TW_HITCAP;
-  const int neh = nh[lfirst];
-  // 3. Gauss lines of every piece; crossings split the inner range and the
-  //    visibility alternates at each crossing
-  const int nlines = (nbr - 1) * q;
-  const int64_t base0 = off ? off[ci] : 0;
-  int64_t base = 0;
-  for (int start = 0; start < nlines; start += TW_CUT_THREADS) {
-    int li = start + tid;
-    double h[TW_HITCAP + 2];
-    int n = -1, vis0 = 0;
-    double s = 0.0, ws = 0.0;
+  return lo;
+}
+
+// one Gauss line: its coordinate s, weight ws and inner interval [lo, hi]
+struct CutLine {
+  int ci, o;
+  double s, ws, lo, hi;
+};
+
+__device__ __forceinline__ CutLine cut_line(Dir A, Dir B, const int32_t *cut_list,
+                                            const int32_t *cut_o, const double *br_all,
+                                            const int64_t *line_off, int ncut, int q,
+                                            const double *qgx, const double *qgw, int64_t li) {
+  CutLine L;
+  L.ci = cut_line_elem(line_off, ncut, li);
+  const int e = cut_list[L.ci], e1 = e % A.nel, e2 = e / A.nel;
+  L.o = cut_o[L.ci];
+  const int in = 1 - L.o;
+  const int64_t loc = li - line_off[L.ci];
+  const int pc = (int)(loc / q), g = (int)(loc % q);
+  const double *br = br_all + (size_t)L.ci * TW_BRCAP;
+  const double s0 = br[pc], s1 = br[pc + 1];
+  L.s = s0 + (s1 - s0) * 0.5 * (qgx[g] + 1.0);
+  L.ws = qgw[g] * 0.5 * (s1 - s0);
+  L.lo = in == 0 ? A.bp[e1] : B.bp[e2];
+  L.hi = in == 0 ? A.bp[e1 + 1] : B.bp[e2 + 1];
+  if (!(s1 > s0)) L.ws = -1.0;  // an empty piece: no points
+  return L;
+}
+
+// crossings (lh[li * TW_HITCAP ..], ln[li] of them; -1 for an empty piece),
+// the visibility of the first interval and the line's point count
+__global__ void k_cut_lines(Curve C, Dir A, Dir B, const int32_t *cut_list, int ncut, int q,
+                            const double *qgx, const double *qgw, const double *hits,
+                            const int *nh, const int32_t *cut_o, const double *br_all,
+                            const int64_t *line_off, const int64_t *nl_tot, double *lh,
+                            int32_t *ln, int8_t *lvis, int64_t *lcnt, int *flag) {
+  const int64_t L = *nl_tot;
+  for (int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; li < L;
+       li += (int64_t)gridDim.x * blockDim.x) {
+    const CutLine cl = cut_line(A, B, cut_list, cut_o, br_all, line_off, ncut, q, qgx, qgw, li);
     int64_t count = 0;
-    if (li < nlines) {
-      int pc = li / q, g = li % q;
-      double s0 = br[pc], s1 = br[pc + 1];
-      if (s1 > s0) {
-        s = s0 + (s1 - s0) * 0.5 * (qgx[g] + 1.0);
-        ws = qgw[g] * 0.5 * (s1 - s0);
-        n = curve_line_hits(C, o, s, a[in], b[in], h + 1, TW_HITCAP);
-        if (n < 0) {
-          atomicOr(flag, TWF_HITCAP);
-          n = -1;
-        } else {
-          h[0] = a[in];
-          h[n + 1] = b[in];
-          int right = 0;
-          for (int k = 0; k < neh; k++) right += eh[k] > s;
-          int inside = right & 1;
-          if (C.kind == TW_TRIM_LINE) {  // a half-plane: test the first interval's midpoint
-            const double um = 0.5 * (h[0] + h[1]);
-            inside = o == 0 ? curve_inside(C, s, um) : curve_inside(C, um, s);
-          }
-          vis0 = C.kind == TW_TRIM_NONE ? 1 : (C.keep_inside ? inside : !inside);
-          for (int k = 0; k <= n; k++)
-            if (h[k + 1] > h[k] && (vis0 ^ (k & 1))) count += q;
+    int n = -1, vis0 = 0;
+    if (cl.ws >= 0.0) {
+      double h[TW_HITCAP + 2];
+      n = curve_line_hits(C, cl.o, cl.s, cl.lo, cl.hi, h + 1, TW_HITCAP);
+      if (n < 0) {
+        atomicOr(flag, TWF_HITCAP);
+        n = -1;
+      } else {
+        h[0] = cl.lo;
+        h[n + 1] = cl.hi;
+        // crossings of the edge line through the lines' first ends
+        const int e = cut_list[cl.ci], e1 = e % A.nel, e2 = e / A.nel;
+        const int lfirst = cl.o == 1 ? e1 : A.nel + 1 + e2;
+        const double *eh = hits + (size_t)lfirst * TW_HITCAP;
+        int right = 0;
+        for (int k = 0; k < nh[lfirst]; k++) right += eh[k] > cl.s;
+        int inside = right & 1;
+        if (C.kind == TW_TRIM_LINE) {  // a half-plane: test the first interval's midpoint
+          const double um = 0.5 * (h[0] + h[1]);
+          inside = cl.o == 0 ? curve_inside(C, cl.s, um) : curve_inside(C, um, cl.s);
         }
+        vis0 = C.kind == TW_TRIM_NONE ? 1 : (C.keep_inside ? inside : !inside);
+        for (int k = 0; k <= n; k++)
+          if (h[k + 1] > h[k] && (vis0 ^ (k & 1))) count += q;
+        for (int k = 0; k < n; k++) lh[li * TW_HITCAP + k] = h[k + 1];
       }
     }
-    scan[tid] = count;
-    __syncthreads();
-    for (int d = 1; d < TW_CUT_THREADS; d <<= 1) {
-      int64_t v = tid >= d ? scan[tid - d] : 0;
-      __syncthreads();
-      scan[tid] += v;
-      __syncthreads();
-    }
-    int64_t mine = base + scan[tid] - count;
-    double *dst = nullptr;
-    if (pts) dst = pts + 3 * (base0 + mine);
-    else if (scr && mine + count <= cap) dst = scr + 3 * ((int64_t)ci * cap + mine);
-    if (dst && count > 0) {
-      int64_t w0 = 0;
-      for (int k = 0; k <= n; k++) {
-        double u0 = h[k], u1 = h[k + 1];
-        if (!(u1 > u0) || !(vis0 ^ (k & 1))) continue;
-        for (int hh = 0; hh < q; hh++) {
-          double u = u0 + (u1 - u0) * 0.5 * (qgx[hh] + 1.0);
-          double w = ws * qgw[hh] * 0.5 * (u1 - u0);
-          double *o3 = dst + 3 * w0;
-          o3[0] = o == 0 ? s : u;
-          o3[1] = o == 0 ? u : s;
-          o3[2] = w;
-          w0++;
-        }
-      }
-    }
-    base += scan[TW_CUT_THREADS - 1];
-    __syncthreads();
-  }
-  if (cnt && tid == 0) {
-    cnt[ci] = base;
-    if (scr && base > cap) atomicAdd(ovf, 1ull);
+    ln[li] = n;
+    lvis[li] = (int8_t)vis0;
+    lcnt[li] = count;
   }
 }
 
-// copy each element's points from its scratch slot to the packed array
-__global__ void k_cut_gather(const int64_t *off, int ncut, int cap, const double *scr,
-                             double *pts) {
-  const int ci = blockIdx.x;
-  if (ci >= ncut) return;
-  const int64_t n3 = 3 * (off[ci + 1] - off[ci]);
-  const double *src = scr + 3 * (int64_t)ci * cap;
-  double *dst = pts + 3 * off[ci];
-  for (int64_t k = threadIdx.x; k < n3; k += blockDim.x) dst[k] = src[k];
+__global__ void k_cut_write(Dir A, Dir B, const int32_t *cut_list, int ncut, int q,
+                            const double *qgx, const double *qgw, const int32_t *cut_o,
+                            const double *br_all, const int64_t *line_off, const int64_t *nl_tot,
+                            const double *lh, const int32_t *ln, const int8_t *lvis,
+                            const int64_t *lpos, double *pts) {
+  const int64_t L = *nl_tot;
+  for (int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; li < L;
+       li += (int64_t)gridDim.x * blockDim.x) {
+    const int n = ln[li];
+    if (n < 0) continue;
+    const CutLine cl = cut_line(A, B, cut_list, cut_o, br_all, line_off, ncut, q, qgx, qgw, li);
+    const int vis0 = lvis[li];
+    double *dst = pts + 3 * lpos[li];
+    int64_t w0 = 0;
+    for (int k = 0; k <= n; k++) {
+      const double u0 = k == 0 ? cl.lo : lh[li * TW_HITCAP + k - 1];
+      const double u1 = k == n ? cl.hi : lh[li * TW_HITCAP + k];
+      if (!(u1 > u0) || !(vis0 ^ (k & 1))) continue;
+      for (int hh = 0; hh < q; hh++) {
+        double u = u0 + (u1 - u0) * 0.5 * (qgx[hh] + 1.0);
+        double w = cl.ws * qgw[hh] * 0.5 * (u1 - u0);
+        double *o3 = dst + 3 * w0;
+        o3[0] = cl.o == 0 ? cl.s : u;
+        o3[1] = cl.o == 0 ? u : cl.s;
+        o3[2] = w;
+        w0++;
+      }
+    }
+  }
 }
+
+// per element: offset of its first point (cut_off[ncut] = all points)
+__global__ void k_cut_offsets(int ncut, const int64_t *line_off, const int64_t *lpos,
+                              const int64_t *npts, int64_t *cut_off) {
+  const int ci = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ci < ncut) cut_off[ci] = lpos[line_off[ci]];
+  if (ci == ncut) cut_off[ci] = *npts;
+}
+
 
 // per cut point: basis values in both directions and w * c.  The points come
 // in Gauss lines of constant outer coordinate (R6); for the spline geometry
@@ -1487,10 +1522,9 @@ int build_tables(tw_patch *P) {
   P->cutrows = (int32_t *)dalloc(P, sizeof(int32_t) * (P->ncutrows + 1));
   P->cut_list = (int32_t *)dalloc(P, sizeof(int32_t) * (P->ncut + 1));
   P->cut_off = (int64_t *)dalloc(P, sizeof(int64_t) * (P->ncut + 1));
-  int64_t *ccount = (int64_t *)dalloc(P, sizeof(int64_t) * (P->ncut + 1));
   int32_t *glist = (int32_t *)dalloc(P, sizeof(int32_t) * (P->ngslot + 1));
   P->gc = (double *)dalloc(P, sizeof(double) * ((size_t)P->ngslot * p1 * p1 + 1));
-  if (!P->rowg || !P->row_ptr || !cnt || !P->cutrows || !P->cut_list || !P->cut_off || !ccount ||
+  if (!P->rowg || !P->row_ptr || !cnt || !P->cutrows || !P->cut_list || !P->cut_off ||
       !glist || !P->gc)
     return TW_ENOMEM;
   k_act_finalize<<<G1(nf)>>>(aflag, P->act, P->rowg, nf);
@@ -1531,26 +1565,47 @@ int build_tables(tw_patch *P) {
       launch_gauss_matrices(P, glist, st);
     }
   }
-  // cut-element rules: one pass counts the points and writes them to a slot
-  // of `cap` points per element; after the scan they are packed.  Only if an
-  // element overflows its slot is the rule evaluated a second time in place.
-  const int cap = 16 * P->qc * P->qc;
-  double *cscr = nullptr;
+  // cut-element rules: breakpoints per element, then one thread per Gauss line
+  // (crossings and point count), a scan, and the points written per line
   P->cut_o = (int32_t *)dalloc(P, sizeof(int32_t) * (P->ncut + 1));
   if (!P->cut_o) return TW_ENOMEM;
-  cudaMemsetAsync(tot64 + 2, 0, sizeof(int64_t), st);
+  cudaMemsetAsync(tot64 + 1, 0, sizeof(int64_t), st);
+  double *cbr = nullptr, *clh = nullptr;
+  int64_t *line_off = nullptr, *lpos = nullptr;
+  int32_t *cln = nullptr;
+  int8_t *clv = nullptr;
+  int64_t nlines = 0;
   if (P->ncut > 0) {
-    cscr = (double *)dalloc(P, sizeof(double) * 3 * (size_t)P->ncut * cap);
-    if (!cscr) return TW_ENOMEM;
-    k_cut_rule<<<P->ncut, TW_CUT_THREADS, 0, st>>>(
-        P->curve, A, B, P->cut_list, P->ncut, qgx, qgw, P->qc, lh, lnh, feat, nfeat, fcap, ccount,
-        nullptr, nullptr, P->cut_o, P->flag, cscr, cap, (unsigned long long *)(tot64 + 2));
+    cbr = (double *)dalloc(P, sizeof(double) * (size_t)P->ncut * TW_BRCAP);
+    int32_t *cnbr = (int32_t *)dalloc(P, sizeof(int32_t) * P->ncut);
+    int64_t *cnl = (int64_t *)dalloc(P, sizeof(int64_t) * (P->ncut + 1));
+    line_off = (int64_t *)dalloc(P, sizeof(int64_t) * (P->ncut + 1));
+    if (!cbr || !cnbr || !cnl || !line_off) return TW_ENOMEM;
+    cudaMemsetAsync(cnl + P->ncut, 0, sizeof(int64_t), st);
+    k_cut_breaks<<<G1(P->ncut)>>>(A, B, P->cut_list, P->ncut, P->qc, lh, lnh, feat, nfeat, fcap,
+                                  P->cut_o, cnbr, cbr, cnl, P->flag);
     TW_LAUNCH();
-    if ((rc = exclusive_scan_i64(ccount, P->cut_off, P->ncut, tot64 + 1, st, P))) return rc;
-    k_set_last<<<1, 1, 0, st>>>(P->cut_off, P->ncut, tot64 + 1);
+    if ((rc = exclusive_scan_i64(cnl, line_off, P->ncut + 1, tot64 + 2, st, P))) return rc;
+    cudaMemcpyAsync(&nlines, tot64 + 2, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+    if ((rc = check_cuda(cudaStreamSynchronize(st), "cut rules"))) return rc;
+    clh = (double *)dalloc(P, sizeof(double) * ((size_t)nlines * TW_HITCAP + 1));
+    cln = (int32_t *)dalloc(P, sizeof(int32_t) * (nlines + 1));
+    clv = (int8_t *)dalloc(P, nlines + 1);
+    int64_t *clc = (int64_t *)dalloc(P, sizeof(int64_t) * (nlines + 1));
+    lpos = (int64_t *)dalloc(P, sizeof(int64_t) * (nlines + 1));
+    if (!clh || !cln || !clv || !clc || !lpos) return TW_ENOMEM;
+    cudaMemsetAsync(clc + nlines, 0, sizeof(int64_t), st);
+    if (nlines > 0) {
+      k_cut_lines<<<G1(nlines)>>>(P->curve, A, B, P->cut_list, P->ncut, P->qc, qgx, qgw, lh, lnh,
+                                  P->cut_o, cbr, line_off, tot64 + 2, clh, cln, clv, clc,
+                                  P->flag);
+      TW_LAUNCH();
+    }
+    if ((rc = exclusive_scan_i64(clc, lpos, nlines + 1, tot64 + 1, st, P))) return rc;
+    k_cut_offsets<<<G1(P->ncut + 1)>>>(P->ncut, line_off, lpos, tot64 + 1, P->cut_off);
     TW_LAUNCH();
   }
-  int64_t h64[3] = {0, 0, 0};
+  int64_t h64[2] = {0, 0};
   cudaMemcpyAsync(h64, tot64, sizeof(h64), cudaMemcpyDeviceToHost, st);
   if ((rc = read_flag(P, "cut rules"))) return rc;
   P->nnz = h64[0];
@@ -1561,14 +1616,11 @@ int build_tables(tw_patch *P) {
   P->cut_M = (double *)dalloc(P, sizeof(double) * ((size_t)P->ncut * p1 * p1 * p1 * p1 + 1));
   if (!P->cut_pts || !P->cut_wc || !P->cut_B || !P->cut_M) return TW_ENOMEM;
   if (P->ncut > 0) {
-    if (h64[2] == 0) {
-      k_cut_gather<<<P->ncut, 128, 0, st>>>(P->cut_off, P->ncut, cap, cscr, P->cut_pts);
-    } else {
-      k_cut_rule<<<P->ncut, TW_CUT_THREADS, 0, st>>>(
-          P->curve, A, B, P->cut_list, P->ncut, qgx, qgw, P->qc, lh, lnh, feat, nfeat, fcap,
-          nullptr, P->cut_off, P->cut_pts, P->cut_o, P->flag, nullptr, 0, nullptr);
+    if (nlines > 0) {
+      k_cut_write<<<G1(nlines)>>>(A, B, P->cut_list, P->ncut, P->qc, qgx, qgw, P->cut_o, cbr,
+                                  line_off, tot64 + 2, clh, cln, clv, lpos, P->cut_pts);
+      TW_LAUNCH();
     }
-    TW_LAUNCH();
     k_cut_point_tables<<<P->ncut, TW_CPT_THREADS, 0, st>>>(P->geo, A, B, P->cut_list, P->cut_off,
                                                            P->cut_o, P->ncut, P->cut_pts, P->cut_B,
                                                            P->cut_wc);
