@@ -285,13 +285,15 @@ extern "C" int tw_patch_create(const tw_patch_desc *desc, tw_patch **out) {
   P->stream = (cudaStream_t)desc->stream;
   int rc = TW_ENOMEM;
   cudaStream_t st = P->stream;
+  // host staging of the breakpoints, kept until the set-up's final
+  // synchronisation (the copies may read them until then)
+  double *hbp[2] = {nullptr, nullptr};
 #define ALLOC(ptr, T, n)                                   \
   do {                                                     \
     (ptr) = (T *)dalloc(P, sizeof(T) * (size_t)(n));       \
     if (!(ptr)) goto fail;                                 \
   } while (0)
   {
-    double *hbp = nullptr;
     for (int d = 0; d < 2; d++) {
       Dir &D = P->d[d];
       D.p = p;
@@ -327,13 +329,14 @@ extern "C" int tw_patch_create(const tw_patch_desc *desc, tw_patch **out) {
       ALLOC(D.crange, int, (size_t)D.n * W);
       ALLOC(D.GB, double, (size_t)D.nel * (p + 1) * (p + 1));
       ALLOC(D.dGB, double, (size_t)D.nel * (p + 1) * (p + 1));
-      hbp = (double *)malloc(sizeof(double) * (D.nel + 1));
-      for (int e = 0; e <= D.nel; e++) hbp[e] = desc->knots[d][p + e];
+      hbp[d] = (double *)malloc(sizeof(double) * (D.nel + 1));
+      if (!hbp[d]) {
+        set_error("tw_patch_create: out of host memory");
+        goto fail;
+      }
+      for (int e = 0; e <= D.nel; e++) hbp[d][e] = desc->knots[d][p + e];
       cudaMemcpyAsync(D.U, desc->knots[d], sizeof(double) * D.nk, cudaMemcpyHostToDevice, st);
-      cudaMemcpyAsync(D.bp, hbp, sizeof(double) * (D.nel + 1), cudaMemcpyHostToDevice, st);
-      cudaStreamSynchronize(st);
-      free(hbp);
-      hbp = nullptr;
+      cudaMemcpyAsync(D.bp, hbp[d], sizeof(double) * (D.nel + 1), cudaMemcpyHostToDevice, st);
     }
     Dir &A = P->d[0];
     Dir &B = P->d[1];
@@ -401,11 +404,15 @@ extern "C" int tw_patch_create(const tw_patch_desc *desc, tw_patch **out) {
   }
 #undef ALLOC
   P->arena_on = 0;
+  free(hbp[0]);  // build_tables ended with a synchronisation of the stream
+  free(hbp[1]);
   *out = P;
   return TW_OK;
 fail:
   if (rc == TW_ENOMEM && !g_err[0]) set_error("tw_patch_create: out of device memory");
-  tw_patch_destroy(P);
+  tw_patch_destroy(P);  // synchronises the stream before the staging is freed
+  free(hbp[0]);
+  free(hbp[1]);
   return rc;
 }
 

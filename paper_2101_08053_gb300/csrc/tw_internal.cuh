@@ -136,6 +136,50 @@ __device__ __forceinline__ void basis_ders(const double *U, int span, double x, 
   }
 }
 
+// The Cox-de Boor denominators right[r+1] + left[j-r] equal the knot
+// differences U[span+r+1] - U[span+1-j+r], which do not depend on x: for many
+// points on one span their reciprocals are formed once.
+//   rc[j*(j-1)/2 + r]  1 / (U[span+r+1] - U[span+1-j+r]),  j = 1..p, r < j
+//   rd[a]              1 / (U[span+a] - U[span+a-p]) (0 if equal), a = 1..p
+#define TW_SPAN_RC (TW_MAXP * TW_MAXP1 / 2)
+__device__ __forceinline__ void span_recips(const double *U, int span, int p, double *rc,
+                                            double *rd) {
+  for (int j = 1; j <= p; j++)
+    for (int r = 0; r < j; r++) rc[j * (j - 1) / 2 + r] = 1.0 / (U[span + r + 1] - U[span + 1 - j + r]);
+  rd[0] = 0.0;
+  for (int a = 1; a <= p; a++) {
+    const double d = U[span + a] - U[span + a - p];
+    rd[a] = d > 0.0 ? 1.0 / d : 0.0;
+  }
+}
+
+// basis_ders with the span's reciprocals (span_recips): products only
+static __device__ __noinline__ void basis_ders_rc(const double *U, int span, double x, int p,
+                                                  const double *rc, const double *rd, double *N,
+                                                  double *dN) {
+  double left[TW_MAXP1], right[TW_MAXP1], Nm[TW_MAXP1];
+  N[0] = 1.0;
+  Nm[0] = 1.0;
+  for (int j = 1; j <= p; j++) {
+    left[j] = x - U[span + 1 - j];
+    right[j] = U[span + j] - x;
+    if (j == p)
+      for (int r = 0; r < p; r++) Nm[r] = N[r];
+    double saved = 0.0;
+    for (int r = 0; r < j; r++) {
+      const double t = N[r] * rc[j * (j - 1) / 2 + r];
+      N[r] = saved + right[r + 1] * t;
+      saved = left[j - r] * t;
+    }
+    N[j] = saved;
+  }
+  for (int a = 0; a <= p; a++) {
+    const double l = a >= 1 ? Nm[a - 1] * rd[a] : 0.0;
+    const double r = a <= p - 1 ? Nm[a] * rd[a + 1] : 0.0;
+    dN[a] = p * (l - r);
+  }
+}
+
 // span of x in a knot vector (binary search over [lo, hi))
 __device__ __forceinline__ int find_span(const double *U, int lo, int hi, double x) {
   // returns s in [lo, hi-1] with U[s] <= x < U[s+1]; clamps at the ends

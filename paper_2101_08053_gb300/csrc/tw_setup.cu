@@ -759,6 +759,10 @@ __global__ void __launch_bounds__(TW_CPT_THREADS)
   __shared__ double LS[TW_CPT_THREADS][4][TW_MAXP1];  // control-net sums over the outer index
   __shared__ int64_t lfirst[TW_CPT_THREADS];          // first point of each line
   __shared__ unsigned wmask[TW_CPT_THREADS / 32];
+  // reciprocal knot differences of the element's outer and inner spans
+  __shared__ double rco[TW_SPAN_RC], rdo[TW_MAXP1], rci[TW_SPAN_RC], rdi[TW_MAXP1];
+  if (threadIdx.x == 0) span_recips(Do.U, eo + p, p, rco, rdo);
+  if (threadIdx.x == 32) span_recips(Di.U, ei + p, p, rci, rdi);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t k0 = off[ci], k1 = off[ci + 1];
   for (int64_t base = k0; base < k1; base += TW_CPT_THREADS) {
@@ -787,7 +791,7 @@ __global__ void __launch_bounds__(TW_CPT_THREADS)
       const int L = u / p1, j = u % p1;
       const double sL = pts[3 * lfirst[L] + o];
       double v[TW_MAXP1], d[TW_MAXP1];
-      basis_ders(Do.U, eo + p, sL, p, v, d);
+      basis_ders_rc(Do.U, eo + p, sL, p, rco, rdo, v, d);
       if (j == 0)
         for (int a = 0; a <= p; a++) OV[L][a] = v[a];
       if (geo) {
@@ -811,7 +815,7 @@ __global__ void __launch_bounds__(TW_CPT_THREADS)
       const double x1 = pts[3 * k], x2 = pts[3 * k + 1];
       const double xi = o == 0 ? x2 : x1;
       double v[TW_MAXP1], d[TW_MAXP1];
-      basis_ders(Di.U, ei + p, xi, p, v, d);
+      basis_ders_rc(Di.U, ei + p, xi, p, rci, rdi, v, d);
       for (int a = 0; a < p1; a++) {
         Bt[(2 * k + o) * p1 + a] = OV[l][a];
         Bt[(2 * k + in) * p1 + a] = v[a];
