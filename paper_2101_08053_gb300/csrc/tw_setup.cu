@@ -862,17 +862,64 @@ __global__ void k_gauss_flags(Dir A, Dir B, const uint8_t *estate, const uint8_t
   gflag[e] = f;
 }
 
-__global__ void k_gauss_c(Geo G, Dir A, Dir B, const int32_t *glist, int ng, double *gc) {
-  int id = blockIdx.x * blockDim.x + threadIdx.x;
-  int p1 = A.p + 1;
-  if (id >= ng * p1 * p1) return;
-  int sl = id / (p1 * p1), g1 = id % p1, g2 = (id / p1) % p1;
-  int e = glist[sl], e1 = e % A.nel, e2 = e / A.nel;
-  double x1 = A.bp[e1] + (A.bp[e1 + 1] - A.bp[e1]) * 0.5 * (A.gx[g1] + 1.0);
-  double x2 = B.bp[e2] + (B.bp[e2 + 1] - B.bp[e2]) * 0.5 * (B.gx[g2] + 1.0);
-  gc[(size_t)sl * p1 * p1 + g2 * p1 + g1] =
-      coef_from(G, A.p, x1, x2, e1, A.GB + (e1 * p1 + g1) * p1, A.dGB + (e1 * p1 + g1) * p1, e2,
-                B.GB + (e2 * p1 + g2) * p1, B.dGB + (e2 * p1 + g2) * p1);
+// c at the Gauss points of the listed elements, one warp per element.  For the
+// spline geometry the control net is contracted over direction 1 once per
+// (g1, b) and then per point over b: the same sums, in the same order, as
+// coef_from, with 4 (p+1)^3 instead of 4 (p+1)^4 products per element.
+#define TW_GC_WARPS 4
+__global__ void __launch_bounds__(32 * TW_GC_WARPS)
+    k_gauss_c(Geo G, Dir A, Dir B, const int32_t *glist, int ng, double *gc) {
+  __shared__ double T[TW_GC_WARPS][TW_MAXP1][TW_MAXP1][4];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int sl = blockIdx.x * TW_GC_WARPS + w;
+  if (sl >= ng) return;
+  const int p = A.p, p1 = p + 1;
+  const int e = glist[sl], e1 = e % A.nel, e2 = e / A.nel;
+  const bool spline = G.geom_kind == TW_GEOM_SPLINE && G.coef_kind != TW_COEF_ONE;
+  if (spline) {
+    for (int t = lane; t < p1 * p1; t += 32) {
+      const int g1 = t / p1, bb = t % p1;
+      const double *v1 = A.GB + (e1 * p1 + g1) * p1, *d1 = A.dGB + (e1 * p1 + g1) * p1;
+      double sxa = 0, sya = 0, sxb = 0, syb = 0;
+      for (int aa = 0; aa <= p; aa++) {
+        const double *pt = G.ctrl + 2 * ((size_t)(e2 + bb) * G.n1 + (e1 + aa));
+        sxa += pt[0] * d1[aa];
+        sya += pt[1] * d1[aa];
+        sxb += pt[0] * v1[aa];
+        syb += pt[1] * v1[aa];
+      }
+      T[w][g1][bb][0] = sxa;
+      T[w][g1][bb][1] = sya;
+      T[w][g1][bb][2] = sxb;
+      T[w][g1][bb][3] = syb;
+    }
+    __syncwarp();
+  }
+  for (int t = lane; t < p1 * p1; t += 32) {
+    const int g1 = t % p1, g2 = t / p1;
+    double c = 1.0;
+    if (G.coef_kind != TW_COEF_ONE) {
+      double dj = 1.0;
+      if (G.geom_kind == TW_GEOM_SPLINE) {
+        const double *v2 = B.GB + (e2 * p1 + g2) * p1, *d2 = B.dGB + (e2 * p1 + g2) * p1;
+        double xa = 0, ya = 0, xb = 0, yb = 0;
+        for (int bb = 0; bb <= p; bb++) {
+          xa += T[w][g1][bb][0] * v2[bb];
+          ya += T[w][g1][bb][1] * v2[bb];
+          xb += T[w][g1][bb][2] * d2[bb];
+          yb += T[w][g1][bb][3] * d2[bb];
+        }
+        dj = xa * yb - xb * ya;
+      }
+      if (G.coef_kind == TW_COEF_DENSITY) {
+        const double x1 = A.bp[e1] + (A.bp[e1 + 1] - A.bp[e1]) * 0.5 * (A.gx[g1] + 1.0);
+        const double x2 = B.bp[e2] + (B.bp[e2 + 1] - B.bp[e2]) * 0.5 * (B.gx[g2] + 1.0);
+        dj *= density_at(G, x1, x2);
+      }
+      c = dj;
+    }
+    gc[(size_t)sl * p1 * p1 + g2 * p1 + g1] = c;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1272,7 +1319,8 @@ __global__ void __launch_bounds__(64) k_cut_matrices(const int64_t *off, const i
 
 static void launch_cut_matrices(tw_patch *P, cudaStream_t st) {
   switch (P->p) {
-#define TW_CM(PP) case PP: k_cut_matrices<PP><<<P->ncut, 64, 0, st>>>(P->cut_off, P->cut_o, P->ncut, P->cut_pts, P->cut_B, P->cut_wc, P->cut_M); break;
+// one warp per element while the (p+1)^2 owner threads fit in it
+#define TW_CM(PP) case PP: k_cut_matrices<PP><<<P->ncut, (PP + 1) * (PP + 1) <= 32 ? 32 : 64, 0, st>>>(P->cut_off, P->cut_o, P->ncut, P->cut_pts, P->cut_B, P->cut_wc, P->cut_M); break;
     TW_CM(1) TW_CM(2) TW_CM(3) TW_CM(4) TW_CM(5) TW_CM(6)
 #undef TW_CM
   }
@@ -1558,7 +1606,8 @@ int build_tables(tw_patch *P) {
   // element Gauss c tables and element matrices (skipped above TW_GMAT_BUDGET
   // bytes: the cut-row kernel then integrates those elements row by row)
   if (P->ngslot > 0) {
-    k_gauss_c<<<G1((int64_t)P->ngslot * p1 * p1)>>>(P->geo, A, B, glist, P->ngslot, P->gc);
+    k_gauss_c<<<(unsigned)((P->ngslot + TW_GC_WARPS - 1) / TW_GC_WARPS), 32 * TW_GC_WARPS, 0,
+                st>>>(P->geo, A, B, glist, P->ngslot, P->gc);
     TW_LAUNCH();
     size_t nl = (size_t)p1 * p1;
     size_t bytes = (size_t)P->ngslot * nl * nl * sizeof(double);
