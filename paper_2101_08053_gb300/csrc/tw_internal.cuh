@@ -643,14 +643,22 @@ static __device__ double warp_minnorm(int m, int N, double *A, int lda, const do
       beta[k] = bk;
     }
     __syncwarp();
-    // s_r = bk * (row r . v) for the rows below k, lane r
-    double sr = 0.0;
-    if (lane > k && lane < m) {
-      const double *ar = A + lane * lda, *vk = A + k * lda;
-      for (int c = k; c < N; c++) sr = fma(ar[c], vk[c], sr);
-      sr *= bk;
+    // s_r = bk * (row r . v) for the R rows below k: C lanes per row (the
+    // largest power of two with R C <= 32) take every C-th column, then a
+    // fixed shuffle tree inside each group of C lanes
+    const int R = m - k - 1;
+    if (R > 0) {
+      int C = 32;
+      while (C * R > 32) C >>= 1;
+      const int rr = lane / C, c0 = lane & (C - 1);
+      double sr = 0.0;
+      if (rr < R) {
+        const double *ar = A + (k + 1 + rr) * lda, *vk = A + k * lda;
+        for (int c = k + c0; c < N; c += C) sr = fma(ar[c], vk[c], sr);
+      }
+      for (int o = C >> 1; o > 0; o >>= 1) sr += __shfl_xor_sync(0xffffffffu, sr, o);
+      if (rr < R && c0 == 0) ssh[k + 1 + rr] = sr * bk;
     }
-    ssh[lane] = sr;
     __syncwarp();
     // row r -= s_r v, lanes over columns
     if (lane >= k && lane < N) {
