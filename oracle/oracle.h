@@ -18,8 +18,8 @@
  *   Sect. 3.2               hybrid Gauss for S^r of cut functions
  *   Sect. 3.3, Eqs. 9-10    discontinuous weighted quadrature (knot insertion)
  *   Sect. 4.2               L2 projection
- * The readings taken where the paper is silent are listed in the design doc
- * (R1..R14) and restated at the routine that applies them.
+ * Where the paper is silent, a reading (R1..R14) is taken; each is stated at
+ * the routine that applies it.
  *
  * Parity status: every function is pinned by tests/test_oracle_*.py against
  * closed forms, brute force or textbook special cases, except the c = det J
