@@ -75,3 +75,23 @@ def test_descriptor_validation_on_host(bad):
     assert rc == code
     assert len(L.tw_last_error()) > 0
     assert not h.value
+
+
+def test_extension_entry_points_reject_null_arguments_on_host():
+    """The extended B-spline entry points check their arguments before any
+    device work: NULL patch or buffers give TW_EINVAL and an error text."""
+    from paper_2101_08053_gb300 import api
+    L = api.load()
+    info = np.zeros(4, dtype=np.int64)
+    assert L.tw_extension_build(None, info.ctypes.data_as(C.POINTER(C.c_int64))) == -1
+    assert len(L.tw_last_error()) > 0
+    assert L.tw_extension_matrix(None, None, None, None, None) == -1
+    assert L.tw_form_mass_extended(None, None, None, None, None, None, None, None) == -1
+    keep = []
+    fd = api.make_func_desc(synth.func_sincos(2.0, 3.0), keep)
+    it, rel = C.c_int(0), C.c_double(0)
+    assert L.tw_l2_project_extended(None, C.byref(fd), None, None, None, None, 1e-12, 10,
+                                    C.byref(it), C.byref(rel), None) == -1
+    assert L.tw_l2_project_adjoint_extended(None, C.byref(fd), None, None, None, None, None,
+                                            None, None, 1e-12, 10, C.byref(it), C.byref(rel),
+                                            None) == -1

@@ -5,7 +5,8 @@ mathematics fixes independently of oracle/extension.py:
   prod_{mu != a} (j - l - mu) / (a - mu) (a closed form, not the blossom route);
 - the extended space reproduces polynomials: the B-spline coefficients of a
   tensor polynomial, fitted by scipy's spline interpolation, satisfy
-  c_active = E c_inner (uniform and graded knots, different per direction);
+  c_active = E c_inner (uniform and graded knots, different per direction;
+  circle, straight-line and cubic B-spline trims);
 - every chosen array is all-inner and no all-inner array anywhere in the patch
   is nearer (brute force over all arrays, no search window);
 - the extended L2 projection of a polynomial returns its coefficients exactly;
@@ -70,9 +71,20 @@ def _graded_spec(p, nel, r, ratios=(1.12, 0.9)):
 
 @pytest.mark.parametrize("p,nel,r,graded", [
     (2, 16, 0.27, False), (3, 18, 0.3, True), (4, 20, 0.31, True), (5, 24, 0.29, True),
+    (3, 12, "line", False), (4, 22, "bspline", True),
 ])
 def test_extension_reproduces_polynomials(p, nel, r, graded):
-    spec = _graded_spec(p, nel, r) if graded else synth.make_spec(p, nel, synth.circle(0.5, 0.5, r))
+    if r == "line":
+        spec = synth.line_trim_spec(p, nel=nel)
+    elif r == "bspline":
+        tr = synth.bspline_curve(np.random.default_rng(7), nc=8, radius=0.28, jitter=0.15,
+                                 relative_jitter=True)
+        spec = synth.with_knots(synth.make_spec(p, nel, tr), synth.graded_knots(p, nel, 1.1),
+                                synth.graded_knots(p, nel, 0.92))
+    elif graded:
+        spec = _graded_spec(p, nel, r)
+    else:
+        spec = synth.make_spec(p, nel, synth.circle(0.5, 0.5, r))
     P = oracle.Patch(spec)
     X = Extension(P)
     es, fs, act = P.states()
