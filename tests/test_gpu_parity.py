@@ -201,7 +201,49 @@ def test_determinism_bitwise():
     assert torch.equal(a, c)
 
 
-@pytest.mark.parametrize("p,method", [(3, "hybrid"), (4, "dwq"), (5, "hybrid")])
+def _sampled_rows_parity(spec, n_random, cut_stride, seed):
+    """The whole matrix from the GPU; seeded random rows and every cut_stride-th
+    cut row against the oracle's row-by-row formation (pattern bit-exact,
+    values within TOL relative Frobenius over the sampled rows)."""
+    G = gpu_patch(spec)
+    O = oracle.Patch(spec)
+    assert (G.n_rows, G.nnz) == (O.n_rows, O.nnz)
+    rp, col, val = G.form_mass()
+    torch.cuda.synchronize()
+    rp = rp.cpu().numpy()
+    col = col.cpu().numpy()
+    val = val.cpu().numpy()
+    assert np.all(np.isfinite(val))
+    rng = np.random.default_rng(seed)
+    es, fs, act = O.states()
+    cut_rows = act[(fs == 2)]
+    rows = np.unique(np.concatenate([rng.integers(0, G.n_rows, n_random), cut_rows[::cut_stride]]))
+    num = den = 0.0
+    for r in rows:
+        oc, ov = O.form_row(int(r))
+        assert np.array_equal(col[rp[r]:rp[r + 1]], oc)
+        mv = val[rp[r]:rp[r + 1]]
+        num += np.sum((mv - ov) ** 2)
+        den += np.sum(ov ** 2)
+    assert np.sqrt(num / den) <= TOL
+
+
+@pytest.mark.parametrize("p", [4, 6])
+def test_full_size_config3_sampled_rows(p):
+    """1024 x 1024 elements, p = 4 and 6 (the largest patches, 61.5 M and
+    129 M nonzeros), circular hole, perturbed spline geometry."""
+    _sampled_rows_parity(synth.config3(p=p, nel=1024), 300, 29, p)
+
+
+@pytest.mark.parametrize("p", [3, 4, 5])
+@pytest.mark.parametrize("method", ["hybrid", "dwq"])
+def test_benchmark_128_patches_full(p, method):
+    """The six 128 x 128 patches of the benchmark sweep, whole matrices."""
+    compare_full(synth.config2(p=p, nel=128, method=method))
+
+
+@pytest.mark.parametrize("p,method", [(3, "hybrid"), (4, "dwq"), (5, "hybrid"),
+                                      (3, "dwq"), (4, "hybrid"), (5, "dwq")])
 def test_full_size_config2_sampled_rows(p, method):
     """512 x 512 elements (the benchmark's patches): the whole matrix from the
     GPU, 400 seeded rows (and every cut row among the first 100k) against the
