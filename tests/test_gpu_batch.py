@@ -59,3 +59,38 @@ def test_batch_against_oracle():
         assert np.array_equal(o[0].cpu().numpy(), orp)
         v = o[2][:P.nnz].cpu().numpy()
         assert np.linalg.norm(v - oval) / np.linalg.norm(oval) <= 1e-12
+
+
+@pytest.mark.parametrize("mode", ["fp64", "fp32"])
+def test_batch_config4_full_size(mode):
+    """The benchmark's batch: 512 patches of degree 2..6 and 16..256 elements
+    per direction (713 M nonzeros), one persistent launch.  Every patch's CSR
+    equals its one-patch formation bit for bit on 24 seeded patches, and the
+    three smallest of those equal the oracle's whole matrices (FP64)."""
+    from paper_2101_08053_gb300 import Batch, Patch
+    rng = np.random.default_rng(synth.BASE_SEED + 4)
+    specs = [synth.config4_patch(rng, method="hybrid") for _ in range(512)]
+    patches = [Patch(s) for s in specs]
+    outs = [P.alloc_csr(mode) for P in patches]
+    B = Batch(patches, outs, mode)
+    B.run()
+    torch.cuda.synchronize()
+    pick = np.random.default_rng(44).choice(len(patches), 24, replace=False)
+    for k in pick:
+        P = patches[k]
+        r, c, v = P.form_mass(mode)
+        torch.cuda.synchronize()
+        assert torch.equal(outs[k][0], r)
+        assert torch.equal(outs[k][1][:P.nnz], c)
+        assert torch.equal(outs[k][2][:P.nnz], v)
+    if mode == "fp64":
+        for k in sorted(pick, key=lambda j: patches[j].nnz)[:3]:
+            O = oracle.Patch(specs[k])
+            orp, ocol, oval = O.form()
+            assert np.array_equal(outs[k][0].cpu().numpy(), orp)
+            assert np.array_equal(outs[k][1][:patches[k].nnz].cpu().numpy(), ocol)
+            vv = outs[k][2][:patches[k].nnz].cpu().numpy()
+            assert np.linalg.norm(vv - oval) <= 1e-12 * np.linalg.norm(oval)
+    B.close()
+    for P in patches:
+        P.close()
