@@ -367,3 +367,26 @@ def test_density_grid_against_scipy():
     X1, X2 = np.meshgrid(P.wq_grid(0), P.wq_grid(1), indexing="xy")
     ref = dens(np.stack([X1.ravel(), X2.ravel()], 1)).reshape(C.shape)
     assert np.max(np.abs(C - ref)) < 1e-14
+
+
+def test_cg_solves_the_symmetric_part_of_a_nonsymmetric_matrix():
+    """Reading R10: with c = det J the WQ rows give m_ij != m_ji; CG solves
+    (M + M^T)/2 u = b (against scipy's direct solve of that system), not M."""
+    rng = np.random.default_rng(6)
+    p, nel = 3, 10
+    net = synth.perturbed_bilinear_net(rng, p, nel)
+    spec = synth.make_spec(p, nel, {"kind": "none"}, geom={"kind": "spline", "ctrl": net},
+                           coef={"kind": "detj"}, method="hybrid")
+    P = oracle.Patch(spec)
+    rp, col, val = P.form()
+    n = P.n_rows
+    M = sp.csr_matrix((val, col, rp), shape=(n, n))
+    asym = spla.norm(M - M.T) / spla.norm(M)
+    assert asym > 1e-6  # the rule really is non-symmetric here
+    b = P.rhs(synth.func_sincos(2.0, 3.0))
+    u, it, rel = P.cg(rp, col, val, b, tol=1e-14)
+    Ms = 0.5 * (M + M.T)
+    ref = spla.spsolve(Ms.tocsc(), b)
+    assert np.max(np.abs(u - ref)) <= 1e-10 * np.max(np.abs(ref))
+    plain = spla.spsolve(M.tocsc(), b)
+    assert np.max(np.abs(plain - ref)) > 1e3 * np.max(np.abs(u - ref))
