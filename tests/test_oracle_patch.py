@@ -390,3 +390,25 @@ def test_cg_solves_the_symmetric_part_of_a_nonsymmetric_matrix():
     assert np.max(np.abs(u - ref)) <= 1e-10 * np.max(np.abs(ref))
     plain = spla.spsolve(M.tocsc(), b)
     assert np.max(np.abs(plain - ref)) > 1e3 * np.max(np.abs(u - ref))
+
+
+@pytest.mark.parametrize("p,i,side,expected", [
+    # p = 3, disc t = 1/2 on 8 uniform elements (h = 1/8).  The element left of
+    # t holds its 2 base points at 1/3, 2/3 and gets p + 1 - 2 = 2 nested
+    # points: the first in the middle gap (1/2), the second in the gap next to
+    # t (5/6).  Right of t the gap next to t is the first one (1/6).
+    (3, 4, 0, [1 + 1 / 3, 1 + 2 / 3, 2 + 1 / 3, 2 + 2 / 3, 3 + 1 / 3, 3 + 1 / 2, 3 + 2 / 3,
+               3 + 5 / 6]),
+    (3, 4, 1, [4 + 1 / 6, 4 + 1 / 3, 4 + 1 / 2, 4 + 2 / 3]),
+    # p = 5: 4 nested points, one per gap (middle, next to t, far), the fourth
+    # again in the middle (ties go to the middle gap): middle gap at its thirds
+    (5, 6, 0, [1 + 1 / 3, 1 + 2 / 3, 2 + 1 / 3, 2 + 2 / 3, 3 + 1 / 6, 3 + 1 / 3, 3 + 4 / 9,
+               3 + 5 / 9, 3 + 2 / 3, 3 + 5 / 6]),
+])
+def test_dwq_nested_points_by_hand(p, i, side, expected):
+    """Reading R5 on a hand-worked case: the points of the DWQ rule of B_i on
+    one side of the disc knot t = 1/2 (in units of h, from 0)."""
+    spec = synth.make_spec(p, 8, synth.circle(0.5, 0.5, 0.2), method="dwq")
+    P = oracle.Patch(spec)
+    x = P.dwq_rule(0, 4, side, i)[:, 0]
+    assert np.allclose(x, np.array(expected) / 8.0, rtol=0, atol=1e-15)
