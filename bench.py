@@ -14,6 +14,13 @@ The --impl reference arm times the CPU oracle (single thread) on a bounded
 sample of the same workload: full set-up of each patch plus a seeded sample
 of rows, extrapolated to the whole matrix.
 
+Besides the step, the JSON line carries: e2e (the same step with the CSRs
+copied to pinned host memory), the roofline of the interior-row kernel, the
+formation-only rates of the three precisions, the 512-patch batched run, the
+density-gradient workload (256^2, p = 3), the 1024^2 precision study with its
+L2 projections, and the extended B-spline projection at 512^2, p = 4; each
+section can be skipped with its --no-* flag.
+
 Multi-GPU: the path has no exchange step; each rank forms its own copy of the
 workload (weak scaling, replicas), timings are max-reduced over ranks.
 """
