@@ -151,3 +151,39 @@ def test_gradient_against_finite_differences(method, geom):
     fd = (_chain(_with_coef(spec, d0 + h * v), G, G)[0] -
           _chain(_with_coef(spec, d0 - h * v), G, G)[0]) / (2 * h)
     assert abs(fd - grad @ v) <= 1e-6 * scale * np.linalg.norm(v, 1) / math.sqrt(d0.size)
+
+
+def test_targets_against_closed_forms_and_quadrature():
+    """The targets f, g the projection and the loss use: at u = 0 the loss is
+    the integral of g^2 over the visible domain (identity geometry), against
+    closed forms on the untrimmed square (sin.cos, sin.sin) and against
+    scipy's adaptive quadrature on the line-trimmed square for the Gaussian
+    bump (the trim makes the domain asymmetric, so a swapped centre shows)."""
+    import math
+    from scipy.integrate import dblquad
+
+    def s2(a):  # integral of sin^2(a x) over [0, 1]
+        return 0.5 - math.sin(2 * a) / (4 * a)
+
+    def c2(a):  # integral of cos^2(a x) over [0, 1]
+        return 0.5 + math.sin(2 * a) / (4 * a)
+
+    P = oracle.Patch(synth.make_spec(3, 16, {"kind": "none"}))
+    u = np.zeros(P.n_rows)
+    L, _ = P.loss(u, synth.func_sincos(2.0, 3.0))
+    assert abs(L - s2(2.0) * c2(3.0)) <= 1e-12
+    L, _ = P.loss(u, synth.func_sinsin(2.5, 1.5))
+    assert abs(L - s2(2.5) * s2(1.5)) <= 1e-12
+    P = oracle.Patch(synth.line_trim_spec(3, nel=16))
+    u = np.zeros(P.n_rows)
+    L, _ = P.loss(u, synth.func_gauss(8.0, 0.3, 0.7))
+    x0, y0, x1, y1 = synth.LINE_TRIM
+    ref = dblquad(lambda y, x: math.exp(-16.0 * ((x - 0.3) ** 2 + (y - 0.7) ** 2)), 0.0, 1.0,
+                  lambda x: 0.0, lambda x: y0 + (y1 - y0) * x, epsabs=1e-14, epsrel=1e-13)[0]
+    assert abs(L - ref) <= 1e-10 * ref
+    # sin(2x) cos(3y) on the same asymmetric domain (on the square a swap of
+    # x and y would integrate to the same value)
+    L, _ = P.loss(u, synth.func_sincos(2.0, 3.0))
+    ref = dblquad(lambda y, x: (math.sin(2.0 * x) * math.cos(3.0 * y)) ** 2, 0.0, 1.0,
+                  lambda x: 0.0, lambda x: y0 + (y1 - y0) * x, epsabs=1e-14, epsrel=1e-13)[0]
+    assert abs(L - ref) <= 1e-10 * ref
