@@ -187,3 +187,35 @@ def test_targets_against_closed_forms_and_quadrature():
     ref = dblquad(lambda y, x: (math.sin(2.0 * x) * math.cos(3.0 * y)) ** 2, 0.0, 1.0,
                   lambda x: 0.0, lambda x: y0 + (y1 - y0) * x, epsabs=1e-14, epsrel=1e-13)[0]
     assert abs(L - ref) <= 1e-10 * ref
+
+
+def test_physical_points_on_an_exact_bilinear_geometry():
+    """The target is evaluated at x(xi): with an unperturbed bilinear control
+    net the patch is exactly the quadrilateral (0,0), (1,0), (1.15,1.1),
+    (0.05,0.95), and the loss at u = 0 (sum of w det J g(x(xi))^2) equals the
+    integral of g^2 over that quadrilateral (two triangles, scipy)."""
+    import math
+    from scipy.integrate import dblquad
+
+    p, nel = 3, 12
+    net = synth.perturbed_bilinear_net(np.random.default_rng(0), p, nel, amplitude_h=0.0)
+    spec = synth.make_spec(p, nel, {"kind": "none"}, geom={"kind": "spline", "ctrl": net},
+                           coef={"kind": "detj"})
+    P = oracle.Patch(spec)
+    L, _ = P.loss(np.zeros(P.n_rows), synth.func_gauss(4.0, 0.6, 0.4))
+
+    def tri(a, b, c):
+        (ax, ay), (bx, by), (cx, cy) = a, b, c
+        jac = abs((bx - ax) * (cy - ay) - (cx - ax) * (by - ay))
+
+        def f(t, s):
+            x = ax + s * (bx - ax) + t * (cx - ax)
+            y = ay + s * (by - ay) + t * (cy - ay)
+            return math.exp(-8.0 * ((x - 0.6) ** 2 + (y - 0.4) ** 2))
+
+        return jac * dblquad(f, 0.0, 1.0, lambda s: 0.0, lambda s: 1.0 - s, epsabs=1e-14,
+                             epsrel=1e-13)[0]
+
+    corners = [(0.0, 0.0), (1.0, 0.0), (1.15, 1.1), (0.05, 0.95)]
+    ref = tri(corners[0], corners[1], corners[2]) + tri(corners[0], corners[2], corners[3])
+    assert abs(L - ref) <= 1e-10 * ref

@@ -412,3 +412,13 @@ def test_dwq_nested_points_by_hand(p, i, side, expected):
     P = oracle.Patch(spec)
     x = P.dwq_rule(0, 4, side, i)[:, 0]
     assert np.allclose(x, np.array(expected) / 8.0, rtol=0, atol=1e-15)
+
+
+def test_l2_error_of_zero_is_the_norm_of_f():
+    """or_l2_error at u = 0: relative error 1 and ||f|| = sqrt(int f^2), a
+    closed form for sin(2x) cos(3y) on the untrimmed square."""
+    import math
+    P = oracle.Patch(synth.make_spec(3, 16, {"kind": "none"}))
+    e, fn = P.l2_error(np.zeros(P.n_rows), synth.func_sincos(2.0, 3.0))
+    ref = math.sqrt((0.5 - math.sin(4.0) / 8.0) * (0.5 + math.sin(6.0) / 12.0))
+    assert abs(fn - ref) <= 1e-12 and abs(e - 1.0) <= 1e-14
