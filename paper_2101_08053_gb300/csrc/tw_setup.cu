@@ -1649,9 +1649,11 @@ int build_tables(tw_patch *P) {
     if (!clh || !cln || !clv || !clc || !lpos) return TW_ENOMEM;
     cudaMemsetAsync(clc + nlines, 0, sizeof(int64_t), st);
     if (nlines > 0) {
-      k_cut_lines<<<G1(nlines)>>>(P->curve, A, B, P->cut_list, P->ncut, P->qc, qgx, qgw, lh, lnh,
-                                  P->cut_o, cbr, line_off, tot64 + 2, clh, cln, clv, clc,
-                                  P->flag);
+      // 64-thread blocks: a patch has only ~10^4 lines, and 256-thread
+      // blocks would leave most SMs idle on this FP64-heavy kernel
+      k_cut_lines<<<(unsigned)((nlines + 63) / 64), 64, 0, st>>>(
+          P->curve, A, B, P->cut_list, P->ncut, P->qc, qgx, qgw, lh, lnh, P->cut_o, cbr, line_off,
+          tot64 + 2, clh, cln, clv, clc, P->flag);
       TW_LAUNCH();
     }
     if ((rc = exclusive_scan_i64(clc, lpos, nlines + 1, tot64 + 1, st, P))) return rc;
@@ -1670,8 +1672,9 @@ int build_tables(tw_patch *P) {
   if (!P->cut_pts || !P->cut_wc || !P->cut_B || !P->cut_M) return TW_ENOMEM;
   if (P->ncut > 0) {
     if (nlines > 0) {
-      k_cut_write<<<G1(nlines)>>>(A, B, P->cut_list, P->ncut, P->qc, qgx, qgw, P->cut_o, cbr,
-                                  line_off, tot64 + 2, clh, cln, clv, lpos, P->cut_pts);
+      k_cut_write<<<(unsigned)((nlines + 63) / 64), 64, 0, st>>>(
+          A, B, P->cut_list, P->ncut, P->qc, qgx, qgw, P->cut_o, cbr, line_off, tot64 + 2, clh,
+          cln, clv, lpos, P->cut_pts);
       TW_LAUNCH();
     }
     k_cut_point_tables<<<P->ncut, TW_CPT_THREADS, 0, st>>>(P->geo, A, B, P->cut_list, P->cut_off,
