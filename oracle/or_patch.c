@@ -23,6 +23,13 @@
  * replaced by N_k det J (each rule is linear in c).
  * No sum factorisation, blocking or reordering is applied here: the point of
  * the oracle is that each step can be checked by eye against the paper.
+ *
+ * Parity unpinned (no test outside the oracle can tell the alternatives
+ * apart, since every admissible choice is exact at c = 1): the tie between
+ * regions with the same element count and fewer discs in or_dwq_choice
+ * (reading R7), and the test of the curve's first point inside the element
+ * in classify (reading R8; redundant for every curve that crosses a knot
+ * line).  The GPU path is held to the same choices by the parity tests.
  */
 #include "oracle.h"
 
