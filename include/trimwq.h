@@ -134,9 +134,13 @@ typedef struct tw_patch tw_patch;
  * malformed descriptor, TW_EUNSUPPORTED for p outside 1..6, p[0] != p[1] or a
  * curve too complex for one element, TW_ENOMEM / TW_ECUDA otherwise. */
 int tw_patch_create(const tw_patch_desc *desc, tw_patch **out);
+/* Frees the patch's device tables (stream-ordered on the patch's stream).
+ * The paper has no counterpart: resource management only. */
 int tw_patch_destroy(tw_patch *patch);
 
-/* Host copy of the patch sizes:
+/* Host copy of the patch sizes (the counts behind Sect. 2.2's split of the
+ * basis into interior, cut and exterior functions, Eq. 8, and the sizes of the
+ * rules of Sects. 2.1-3.3):
  *  [0] n1 [1] n2 [2] nel1 [3] nel2 [4] nq1 [5] nq2 [6] n_rows [7] nnz
  *  [8] cut elements [9] cut functions [10] cut-rule points [11] DWQ rows
  *  [12] disc knots (both directions) [13] interior rows [14] p [15] method */
@@ -156,6 +160,33 @@ int tw_form_mass(tw_patch *patch, int precision, int64_t *row_ptr, int32_t *col,
  * rule applied to f * c (Sect. 4.2).  Device output, asynchronous. */
 int tw_rhs(tw_patch *patch, const tw_func *f, double *b, void *stream);
 
+/* Two-phase right-hand side, for an f the library cannot evaluate itself
+ * (Sect. 4.2's L2 projection of a given f; reading R9: b_i is row i's own
+ * quadrature rule applied to f c).
+ * tw_rhs_points lists every point at which some row's rule evaluates f, in
+ * this order:
+ *   [0, nq1*nq2)        the WQ grid, index k2*nq1 + k1 (interior rows, Eq. 7,
+ *                       and the masked rule of naive rows)
+ *   next ng*(p+1)^2     the element Gauss points (p+1 per direction) of the ng
+ *                       regular elements that cut rows integrate by Gauss
+ *                       (Sect. 3.2), element by element, g1 fastest
+ *   next ncutpts        the cut-element rules (Sect. 3.1), in the order of
+ *                       tw_patch_table's table 5
+ *   the rest            the DWQ region points of each DWQ row (Sect. 3.3), row
+ *                       by row in ascending active index, direction 1 fastest
+ * A point may appear more than once (shared by several rows' rules).
+ * *npts (host) receives the length of the list.  xi (device, 2*npts doubles,
+ * or NULL) receives the parameter points (xi1, xi2) interleaved, x (device,
+ * 2*npts doubles, or NULL) the physical points x(xi); with both NULL only the
+ * length is returned.  The first call on a patch sizes the list and
+ * synchronises `stream`; later calls are asynchronous.
+ * tw_rhs_values: b[n_rows] (device) from fvals[npts] (device), the values of
+ * f at the listed points -- at the physical points x(xi) when f is a function
+ * of the physical coordinates, as for tw_rhs.  The same sums, in the same
+ * order, as tw_rhs computes with f evaluated itself.  Asynchronous. */
+int tw_rhs_points(tw_patch *patch, int64_t *npts, double *xi, double *x, void *stream);
+int tw_rhs_values(tw_patch *patch, const double *fvals, double *b, void *stream);
+
 /* Allocation-free right-hand side.  The paper has no counterpart: this exists
  * for callers that cannot allocate device memory while they run -- a process
  * whose device memory belongs to another allocator (a framework's caching
@@ -174,12 +205,18 @@ int tw_rhs(tw_patch *patch, const tw_func *f, double *b, void *stream);
  *    behind; nothing in it has to start at zero, since each call writes all of
  *    the scratch it reads.  Calls that overlap on the GPU (other streams, other
  *    threads) race on the array: order them on one stream.
- *  - A spline f's host arrays are copied into the array with cudaMemcpyAsync on
- *    `stream` during the call. */
+ *  - A spline f's host arrays (knots, coefficients) are copied into the array
+ *    with cudaMemcpyAsync on `stream`.  From pageable memory the copy is staged
+ *    before the call returns; from pinned (page-locked) memory it runs when the
+ *    stream reaches it, so pinned arrays must stay valid and unchanged until
+ *    then (synchronise the stream, or record an event and wait on it, before
+ *    freeing or rewriting them). */
 #define TW_RHS_STATIC_MAX (1 << 21)
 int tw_rhs_static(tw_patch *patch, const tw_func *f, double *b, void *stream);
 
-/* L2 projection: Jacobi-preconditioned CG on (M + M^T)/2 with the CSR produced
+/* L2 projection (Sect. 4.2; the paper names no solver, the symmetric part is
+ * taken because WQ rows with a non-constant c make M non-symmetric, Sect. 2.1):
+ * Jacobi-preconditioned CG on (M + M^T)/2 with the CSR produced
  * by tw_form_mass (FP64) and the rhs of f, until ||r||/||b|| <= tol or maxit
  * iterations.  u[n_rows] device output; *iters, *relres host outputs.
  * Synchronises `stream` every few iterations.  TW_ENOCONV if not converged. */
@@ -267,12 +304,15 @@ int tw_l2_project_adjoint_extended(tw_patch *patch, const tw_func *f, const int6
                                    const double *u, double *lam, double *grad, double tol,
                                    int maxit, int *iters, double *relres, void *stream);
 
-/* Device copies of the classification: estate[nel1*nel2], fstate[n1*n2]
+/* Device copies of the classification of Sect. 2.2 (elements regular, cut or
+ * invisible; functions interior, cut or exterior, Eq. 8): estate[nel1*nel2], fstate[n1*n2]
  * (uint8, TW_ELEM_* / TW_FUNC_*), act[n1*n2] (int32 active index or -1). */
 int tw_states(const tw_patch *patch, uint8_t *estate, uint8_t *fstate, int32_t *act,
               void *stream);
 
-/* Device copy of an internal table, for parity tests.  `which`:
+/* Device copy of an internal table, for parity tests (the tables of Sects.
+ * 2.1-3.3: WQ points and weights, Eqs. 4-5; c at the grid, Eq. 6; cut-element
+ * rules, Sect. 3.1; DWQ choices, Sect. 3.3; Gauss rules and basis values).  `which`:
  *  0/1  WQ points of direction 0/1 (double, nq)
  *  2/3  WQ weights of direction 0/1 (double, n x qmax, local point index)
  *  4    c at the WQ grid (double, nq2 x nq1, k1 fastest)
@@ -290,7 +330,9 @@ int tw_states(const tw_patch *patch, uint8_t *estate, uint8_t *fstate, int32_t *
 int tw_patch_table(const tw_patch *patch, int which, void *dst, int64_t cap, int64_t *count,
                    void *stream);
 
-/* Batched formation (many patches, one persistent launch, CUDA graph).
+/* Batched formation (many patches, one persistent launch, CUDA graph).  The
+ * paper forms one patch at a time; each patch's CSR is the one of
+ * tw_form_mass (Eqs. 6-7 and Sects. 3.2-3.3), only the scheduling differs.
  * tw_batch_create takes n existing patches (which must outlive the batch) and
  * their caller-owned device CSR buffers (sized as for tw_form_mass), picks the
  * interior-row tile for each degree present by timing candidate tiles on these
@@ -299,7 +341,11 @@ int tw_patch_table(const tw_patch *patch, int which, void *dst, int64_t cap, int
  * and captures one graph: a memset of the work counter and one persistent
  * kernel whose blocks take items until none are left.  Synchronises `stream`.
  * tw_batch_run replays the graph on `stream` (asynchronous); the CSRs equal
- * those of tw_form_mass bit for bit.
+ * those of tw_form_mass bit for bit.  Every replay of one batch resets and
+ * uses the same device work counter and writes the same CSR buffers, so two
+ * replays of one batch must not overlap on the GPU: issue them on one stream
+ * (or make the later stream wait on an event recorded after the earlier
+ * replay).  Distinct batches are independent.
  * tw_batch_info: [0] patches [1] items [2] persistent blocks [3] dynamic
  * shared memory per block [4..9] interior tile chosen for p = 1..6. */
 typedef struct tw_batch tw_batch;
@@ -309,11 +355,19 @@ int tw_batch_run(tw_batch *batch, void *stream);
 int tw_batch_info(const tw_batch *batch, int64_t *info10);
 int tw_batch_destroy(tw_batch *batch);
 
-/* Number of kernels this library has launched in this process. */
+/* Number of kernels this library has launched in this process.  The paper has
+ * no counterpart: an instrumentation counter. */
 int64_t tw_launch_count(void);
 
+/* Read-only view of the library's device memory on the current device (no
+ * counterpart in the paper: instrumentation): info3[0] = allocations the
+ * library has made from its pool in this process (all devices), info3[1] =
+ * bytes the pool holds reserved on the current device, info3[2] = bytes of it
+ * in use.  Allocates nothing; 0 for a device the library has not used. */
+int tw_pool_info(int64_t *info3);
+
 /* Stage timing with CUDA events recorded on the launching stream around each
- * stage (off by default; the paper splits its timings the same way, Sect. 4.2:
+ * stage (off by default; the paper splits its timings the same way, Sect. 4.2.2:
  * quadrature set-up, interior rows, regular part and cut elements of cut rows).
  * tw_profile_read waits for the recorded events, returns the summed device
  * time in ms and the number of launches of `stage` since the last read, and
@@ -330,6 +384,7 @@ int64_t tw_launch_count(void);
 int tw_profile_enable(int on);
 int tw_profile_read(int stage, double *total_ms, int64_t *count);
 
+/* Text of the calling thread's last error (no counterpart in the paper). */
 const char *tw_last_error(void);
 
 #ifdef __cplusplus

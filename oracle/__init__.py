@@ -1,5 +1,11 @@
 """ctypes binding of the FP64 CPU oracle (plain C in this folder).
 
+Two builds of the same sources: liboracle.so (single thread, the oracle the
+tests pin) and liboracle_omp.so (compiled with -fopenmp, so the pragmas on the
+independent loops -- WQ weights per function, c per grid line, DWQ choice per
+function, rows -- run on all host cores; it serves only the benchmark's
+all-cores CPU baseline).
+
 TEST INFRASTRUCTURE ONLY: tests/, __graft_entry__.smoke() and bench.py's CPU
 baseline / reference arm are the only callers.  The product library never
 imports, links or calls this package.
@@ -14,6 +20,7 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB = os.path.join(HERE, "liboracle.so")
+LIB_OMP = os.path.join(HERE, "liboracle_omp.so")
 SOURCES = ["or_core.c", "or_curve.c", "or_patch.c"]
 
 TRIM = {"none": 0, "circle": 1, "ellipse": 2, "bspline3": 3, "line": 4}
@@ -23,17 +30,28 @@ METHOD = {"gauss": 0, "hybrid": 1, "dwq": 2, "naive": 3}
 FUNC = {"spline": 0, "sinsin": 1, "sincos": 2, "gauss": 3}
 
 
-def build(force: bool = False) -> str:
-    """Compile liboracle.so with gcc (single-threaded, -O2, FP64)."""
+def _build_one(out, extra, force):
     srcs = [os.path.join(HERE, s) for s in SOURCES]
     hdr = os.path.join(HERE, "oracle.h")
-    if not force and os.path.exists(LIB):
-        t = os.path.getmtime(LIB)
+    if not force and os.path.exists(out):
+        t = os.path.getmtime(out)
         if all(os.path.getmtime(s) <= t for s in srcs + [hdr]):
-            return LIB
-    tmp = LIB + ".tmp%d" % os.getpid()
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp] + srcs + ["-lm"])
-    os.replace(tmp, LIB)
+            return out
+    tmp = out + ".tmp%d" % os.getpid()
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared"] + extra + ["-o", tmp]
+                          + srcs + ["-lm"])
+    os.replace(tmp, out)
+    return out
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so with gcc (single-threaded, -O2, FP64) and, where
+    the compiler has OpenMP, liboracle_omp.so."""
+    _build_one(LIB, [], force)
+    try:
+        _build_one(LIB_OMP, ["-fopenmp"], force)
+    except (subprocess.CalledProcessError, OSError):
+        pass
     return LIB
 
 
@@ -71,17 +89,30 @@ class Func(C.Structure):
 
 
 _lib = None
+_lib_omp = None
 PD = C.POINTER(C.c_double)
 PI64 = C.POINTER(C.c_int64)
 PI32 = C.POINTER(C.c_int32)
 PU8 = C.POINTER(C.c_uint8)
 
 
-def lib():
-    global _lib
+def lib(omp=False):
+    global _lib, _lib_omp
+    if omp:
+        if _lib_omp is None:
+            build()
+            if not os.path.exists(LIB_OMP):
+                return None
+            _lib_omp = _declare(C.CDLL(LIB_OMP))
+        return _lib_omp
     if _lib is None:
         build()
-        L = C.CDLL(LIB)
+        _lib = _declare(C.CDLL(LIB))
+    return _lib
+
+
+def _declare(L):
+    if True:
         L.or_bspline.restype = C.c_double
         L.or_bspline.argtypes = [PD, C.c_int, C.c_int, C.c_int, C.c_double]
         L.or_bspline_deriv.restype = C.c_double
@@ -109,6 +140,7 @@ def lib():
         L.or_form.argtypes = [C.c_void_p, PI64, PI32, PD]
         L.or_form_row.argtypes = [C.c_void_p, C.c_int64, PI32, PD]
         L.or_rhs.argtypes = [C.c_void_p, C.POINTER(Func), PD]
+        L.or_row_points.argtypes = [C.c_void_p, C.c_int64, PD, C.c_int]
         L.or_cg.argtypes = [C.c_void_p, PI64, PI32, PD, PD, PD, C.c_double, C.c_int, PD]
         L.or_l2_error.restype = C.c_double
         L.or_l2_error.argtypes = [C.c_void_p, PD, C.POINTER(Func), PD]
@@ -117,8 +149,9 @@ def lib():
         L.or_loss.restype = C.c_double
         L.or_loss.argtypes = [C.c_void_p, PD, C.POINTER(Func), PD]
         L.or_density_grad.argtypes = [C.c_void_p, PD, PD, C.POINTER(Func), PD]
-        _lib = L
-    return _lib
+        L.or_form_rows.argtypes = [C.c_void_p, PI64, C.c_int64, PD, PI32]
+        L.or_threads.restype = C.c_int
+    return L
 
 
 def _pd(a):
@@ -191,6 +224,12 @@ def make_func(f, keep):
         keep.append(cf)
         s.coef = _pd(cf)
     return s
+
+
+def threads(omp=False):
+    """Threads the oracle's parallel loops use in the given build."""
+    L = lib(omp)
+    return int(L.or_threads()) if L is not None else 0
 
 
 # ---- univariate helpers ----------------------------------------------------
@@ -272,76 +311,112 @@ def curve_area(trim, nsub=8):
 # ---- patch -----------------------------------------------------------------
 
 class Patch:
-    def __init__(self, spec):
+    def __init__(self, spec, omp=False):
+        """omp=True builds the patch with the all-cores library (benchmark
+        baseline only)."""
         self.spec = spec
+        self._L = lib(omp)
+        if self._L is None:
+            raise RuntimeError("the OpenMP build of the oracle is not available")
         keep = []
         d = make_desc(spec, keep)
-        self._h = lib().or_create(C.byref(d))
+        self._h = self._L.or_create(C.byref(d))
         dims = np.zeros(8, dtype=np.int64)
-        lib().or_dims(self._h, dims.ctypes.data_as(PI64))
+        self._L.or_dims(self._h, dims.ctypes.data_as(PI64))
         (self.n1, self.n2, self.nel1, self.nel2, self.nq1, self.nq2,
          self.n_rows, self.nnz) = [int(v) for v in dims]
         self.p = spec["p"]
 
     def __del__(self):
         if getattr(self, "_h", None):
-            lib().or_destroy(self._h)
+            self._L.or_destroy(self._h)
             self._h = None
 
     def states(self):
         es = np.zeros(self.nel1 * self.nel2, dtype=np.uint8)
         fs = np.zeros(self.n1 * self.n2, dtype=np.uint8)
         act = np.zeros(self.n1 * self.n2, dtype=np.int32)
-        lib().or_states(self._h, es.ctypes.data_as(PU8), fs.ctypes.data_as(PU8),
+        self._L.or_states(self._h, es.ctypes.data_as(PU8), fs.ctypes.data_as(PU8),
                         act.ctypes.data_as(PI32))
         return es, fs, act
 
     def wq_grid(self, d):
         x = np.zeros(self.nq1 if d == 0 else self.nq2)
-        lib().or_wq_grid(self._h, d, _pd(x))
+        self._L.or_wq_grid(self._h, d, _pd(x))
         return x
 
     def cgrid(self):
         c = np.zeros(self.nq1 * self.nq2)
-        lib().or_cgrid(self._h, _pd(c))
+        self._L.or_cgrid(self._h, _pd(c))
         return c.reshape(self.nq2, self.nq1)
 
     def cut_rule(self, e1, e2):
         cap = 1 << 16
         out = np.zeros(3 * cap)
-        n = lib().or_cut_rule(self._h, e1, e2, _pd(out), cap)
+        n = self._L.or_cut_rule(self._h, e1, e2, _pd(out), cap)
         return out[:3 * n].reshape(n, 3).copy()
 
     def dwq_rule(self, d, s, side, i):
         cap = 4096
         out = np.zeros(2 * cap)
-        n = lib().or_dwq_rule(self._h, d, s, side, i, _pd(out), cap)
+        n = self._L.or_dwq_rule(self._h, d, s, side, i, _pd(out), cap)
         return out[:2 * n].reshape(n, 2).copy()
 
     def dwq_choice(self, i1, i2):
         out = np.zeros(4, dtype=np.int32)
-        lib().or_dwq_choice(self._h, i1, i2, out.ctypes.data_as(PI32))
+        self._L.or_dwq_choice(self._h, i1, i2, out.ctypes.data_as(PI32))
         return tuple(int(v) for v in out)
 
     def form(self):
         rp = np.zeros(self.n_rows + 1, dtype=np.int64)
         col = np.zeros(max(self.nnz, 1), dtype=np.int32)
         val = np.zeros(max(self.nnz, 1), dtype=np.float64)
-        lib().or_form(self._h, rp.ctypes.data_as(PI64), col.ctypes.data_as(PI32), _pd(val))
+        self._L.or_form(self._h, rp.ctypes.data_as(PI64), col.ctypes.data_as(PI32), _pd(val))
         return rp, col[:self.nnz], val[:self.nnz]
+
+    def form_rows(self, rows):
+        """Entries of the rows `rows` (in C, in parallel with the all-cores
+        library): (values, counts), values padded to (2p+1)^2 per row."""
+        rows = np.ascontiguousarray(rows, dtype=np.int64)
+        w = (2 * self.p + 1) ** 2
+        val = np.zeros(max(len(rows), 1) * w)
+        cnt = np.zeros(max(len(rows), 1), dtype=np.int32)
+        self._L.or_form_rows(self._h, rows.ctypes.data_as(PI64), len(rows), _pd(val),
+                             cnt.ctypes.data_as(PI32))
+        return val[:len(rows) * w].reshape(len(rows), w), cnt[:len(rows)]
 
     def form_row(self, r):
         cap = (2 * self.p + 1) ** 2
         col = np.zeros(cap, dtype=np.int32)
         val = np.zeros(cap)
-        n = lib().or_form_row(self._h, int(r), col.ctypes.data_as(PI32), _pd(val))
+        n = self._L.or_form_row(self._h, int(r), col.ctypes.data_as(PI32), _pd(val))
         return col[:n].copy(), val[:n].copy()
 
     def rhs(self, f):
         keep = []
         fs = make_func(f, keep)
         b = np.zeros(self.n_rows)
-        lib().or_rhs(self._h, C.byref(fs), _pd(b))
+        self._L.or_rhs(self._h, C.byref(fs), _pd(b))
+        return b
+
+    def row_points(self, r):
+        """The quadrature rule of active row r: an (n, 5) array of xi1, xi2,
+        x1, x2 (physical point) and the weight with B_i and c folded in."""
+        cap = 1 << 14
+        while True:
+            out = np.zeros(5 * cap)
+            n = self._L.or_row_points(self._h, int(r), _pd(out), cap)
+            if n <= cap:
+                return out[:5 * n].reshape(n, 5).copy()
+            cap = n
+
+    def rhs_from(self, f):
+        """b_i = sum over row i's rule of w c f(x) for a Python callable
+        f(x1, x2) of the physical point (vectorised over numpy arrays)."""
+        b = np.zeros(self.n_rows)
+        for r in range(self.n_rows):
+            q = self.row_points(r)
+            b[r] = float(np.sum(q[:, 4] * f(q[:, 2], q[:, 3])))
         return b
 
     def cg(self, rp, col, val, b, tol=1e-12, maxit=None):
@@ -351,7 +426,7 @@ class Patch:
         col = np.ascontiguousarray(col, dtype=np.int32)
         val = _f64(val)
         b = _f64(b)
-        it = lib().or_cg(self._h, rp.ctypes.data_as(PI64), col.ctypes.data_as(PI32), _pd(val),
+        it = self._L.or_cg(self._h, rp.ctypes.data_as(PI64), col.ctypes.data_as(PI32), _pd(val),
                          _pd(b), _pd(u), tol, maxit or 10 * self.n_rows, C.byref(rel))
         return u, it, rel.value
 
@@ -360,11 +435,11 @@ class Patch:
         fs = make_func(f, keep)
         fn = C.c_double(0)
         u = _f64(u)
-        e = lib().or_l2_error(self._h, _pd(u), C.byref(fs), C.byref(fn))
+        e = self._L.or_l2_error(self._h, _pd(u), C.byref(fs), C.byref(fn))
         return e, fn.value
 
     def visible_area(self):
-        return lib().or_visible_area(self._h)
+        return self._L.or_visible_area(self._h)
 
     def loss(self, u, g):
         """(L, dL/du) of reading R12."""
@@ -372,7 +447,7 @@ class Patch:
         gs = make_func(g, keep)
         u = _f64(u)
         dl = np.zeros(self.n_rows)
-        L = lib().or_loss(self._h, _pd(u), C.byref(gs), _pd(dl))
+        L = self._L.or_loss(self._h, _pd(u), C.byref(gs), _pd(dl))
         return L, dl
 
     def density_grad(self, u, lam, g):
@@ -382,5 +457,5 @@ class Patch:
         m1 = len(c["knots"][0]) - c["p"] - 1
         m2 = len(c["knots"][1]) - c["p"] - 1
         out = np.zeros(m1 * m2)
-        lib().or_density_grad(self._h, _pd(_f64(u)), _pd(_f64(lam)), C.byref(gs), _pd(out))
+        self._L.or_density_grad(self._h, _pd(_f64(u)), _pd(_f64(lam)), C.byref(gs), _pd(out))
         return out.reshape(m2, m1)

@@ -36,6 +36,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 int or_curve_folds(const or_desc *d, int o, double *pts, int cap);
 int or_curve_joints(const or_desc *d, double *pts, int cap);
@@ -227,6 +230,7 @@ static void setup_dir(or_patch *P, int dir) {
       }
   }
   D->W = (double *)malloc(sizeof(double) * (size_t)D->n * D->nq);
+#pragma omp parallel for schedule(dynamic, 8)
   for (int i = 0; i < D->n; i++)
     or_wq_weights(D->U, D->nk, D->p, D->xq, D->nq, i, D->W + (size_t)i * D->nq);
   D->gx = (double *)malloc(sizeof(double) * p1);
@@ -841,6 +845,7 @@ or_patch *or_create(const or_desc *d) {
   P->qc = d->cut_order > 0 ? d->cut_order : (d->p[0] > d->p[1] ? d->p[0] : d->p[1]) + 1;
   const dirdata *A = &P->D[0], *B = &P->D[1];
   P->C = (double *)malloc(sizeof(double) * (size_t)A->nq * B->nq);
+#pragma omp parallel for schedule(static)
   for (int k2 = 0; k2 < B->nq; k2++)
     for (int k1 = 0; k1 < A->nq; k1++)
       P->C[(size_t)k2 * A->nq + k1] =
@@ -853,6 +858,7 @@ or_patch *or_create(const or_desc *d) {
   P->gc = (double *)malloc(sizeof(double) * ne * (A->p + 1) * (B->p + 1));
   P->gc_done = (uint8_t *)calloc(ne, 1);
   P->choice = (int *)malloc(sizeof(int) * 4 * (size_t)A->n * B->n);
+#pragma omp parallel for schedule(dynamic, 64)
   for (int g = 0; g < A->n * B->n; g++) {
     P->choice[4 * g] = -1;
     if (d->method == OR_METHOD_DWQ && P->fstate[g] == OR_FUNC_CUT)
@@ -928,6 +934,32 @@ int or_form_row(const or_patch *Pc, int64_t row, int32_t *col, double *val) {
   return n;
 }
 
+/* Rows rows[0..n) of the matrix, row k's values at val + k * (2p+1)^2 and its
+ * entry count in cnt[k].  The rows are independent: with OpenMP (the oracle's
+ * all-cores build) they are formed in parallel; the lazily filled table of c
+ * at the element Gauss points is filled for every element first, so that the
+ * rows only read shared state. */
+void or_form_rows(const or_patch *Pc, const int64_t *rows, int64_t n, double *val, int *cnt) {
+  or_patch *P = (or_patch *)Pc;
+  const dirdata *A = &P->D[0], *B = &P->D[1];
+  const int ne = A->nel * B->nel;
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int e = 0; e < ne; e++)
+    if (P->estate[e] == OR_ELEM_REGULAR) gauss_c(P, e % A->nel, e / A->nel);
+  const int64_t w = (int64_t)(2 * A->p + 1) * (2 * B->p + 1);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t k = 0; k < n; k++) cnt[k] = or_form_row(P, rows[k], NULL, val + k * w);
+}
+
+/* threads the parallel loops use (1 in the single-thread build) */
+int or_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
 void or_form(const or_patch *P, int64_t *row_ptr, int32_t *col, double *val) {
   int64_t pos = 0;
   row_ptr[0] = 0;
@@ -979,6 +1011,24 @@ void or_rhs(const or_patch *Pc, const or_func *f, double *b) {
     b[r] = s;
   }
   free(R.v);
+}
+
+int or_row_points(const or_patch *Pc, int64_t row, double *out, int cap) {
+  or_patch *P = (or_patch *)Pc;
+  rbuf R = {0};
+  int n = row_rule(P, (int)P->rowg[row], &R);
+  for (int k = 0; k < n && k < cap; k++) {
+    const rpoint *q = &R.v[k];
+    double X[2];
+    phys_from(P, q->x[0], q->x[1], q->e[0], q->bv[0], q->e[1], q->bv[1], X);
+    out[5 * k] = q->x[0];
+    out[5 * k + 1] = q->x[1];
+    out[5 * k + 2] = X[0];
+    out[5 * k + 3] = X[1];
+    out[5 * k + 4] = q->wc;
+  }
+  free(R.v);
+  return n;
 }
 
 static int64_t find_pos(const int64_t *rp, const int32_t *col, int64_t r, int32_t c) {

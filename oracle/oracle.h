@@ -134,7 +134,15 @@ int or_dwq_rule(const or_patch *P, int dir, int s, int side, int i, double *pts,
 int or_dwq_choice(const or_patch *P, int i1, int i2, int *out /* 4 */);
 void or_form(const or_patch *P, int64_t *row_ptr, int32_t *col, double *val);
 int or_form_row(const or_patch *P, int64_t row, int32_t *col, double *val);
+void or_form_rows(const or_patch *P, const int64_t *rows, int64_t n, double *val, int *cnt);
+int or_threads(void);
 void or_rhs(const or_patch *P, const or_func *f, double *b);
+/* The quadrature rule of one row (reading R9's rule, the one or_rhs applies to
+ * f c): for each point k, out[5k..5k+4] = xi1, xi2, x1, x2 (the physical point
+ * x(xi)) and the weight with the test function and c folded in, so that
+ * b_row = sum_k out[5k+4] f(x1, x2) for any f.  Returns the number of points;
+ * writes at most cap of them. */
+int or_row_points(const or_patch *P, int64_t row, double *out, int cap);
 int or_cg(const or_patch *P, const int64_t *row_ptr, const int32_t *col,
           const double *val, const double *b, double *u, double tol, int maxit,
           double *relres);

@@ -81,6 +81,8 @@ def load(build: bool = True):
     L.tw_patch_info.argtypes = [vp, i64p]
     L.tw_form_mass.argtypes = [vp, C.c_int, vp, vp, vp, vp]
     L.tw_rhs.argtypes = [vp, C.POINTER(FuncDesc), vp, vp]
+    L.tw_rhs_points.argtypes = [vp, i64p, vp, vp, vp]
+    L.tw_rhs_values.argtypes = [vp, vp, vp, vp]
     L.tw_l2_project.argtypes = [vp, C.POINTER(FuncDesc), vp, vp, vp, vp, C.c_double, C.c_int,
                                 C.POINTER(C.c_int), C.POINTER(C.c_double), vp]
     L.tw_loss.argtypes = [vp, C.POINTER(FuncDesc), vp, vp, vp, vp]
@@ -98,6 +100,7 @@ def load(build: bool = True):
     L.tw_states.argtypes = [vp, vp, vp, vp, vp]
     L.tw_patch_table.argtypes = [vp, C.c_int, vp, C.c_int64, i64p, vp]
     L.tw_launch_count.restype = C.c_int64
+    L.tw_pool_info.argtypes = [i64p]
     L.tw_batch_create.argtypes = [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.POINTER(C.c_void_p),
                                   C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), vp,
                                   C.POINTER(C.c_void_p)]
@@ -252,6 +255,31 @@ class Patch:
         fd = make_func_desc(f, keep)
         b = torch.empty(max(self.n_rows, 1), dtype=torch.float64, device="cuda")
         _check(load().tw_rhs(self._h, C.byref(fd), C.c_void_p(b.data_ptr()), _stream(stream)))
+        return b[:self.n_rows]
+
+    def rhs_points(self, physical=True, stream=None):
+        """Every point at which a row's rule evaluates f (tw_rhs_points):
+        (xi, x), (npts, 2) float64 device tensors of the parameter and the
+        physical points (x is None unless `physical`)."""
+        torch = _torch()
+        n = C.c_int64(0)
+        _check(load().tw_rhs_points(self._h, C.byref(n), None, None, _stream(stream)))
+        xi = torch.empty((max(n.value, 1), 2), dtype=torch.float64, device="cuda")
+        x = torch.empty((max(n.value, 1), 2), dtype=torch.float64, device="cuda") if physical else None
+        _check(load().tw_rhs_points(self._h, C.byref(n), C.c_void_p(xi.data_ptr()),
+                                    C.c_void_p(x.data_ptr()) if physical else None,
+                                    _stream(stream)))
+        return xi[:n.value], (x[:n.value] if physical else None)
+
+    def rhs_values(self, fvals, stream=None):
+        """b from the values of f at the points of rhs_points (tw_rhs_values);
+        fvals is a float64 device tensor of length npts."""
+        torch = _torch()
+        fv = fvals.contiguous()
+        assert fv.dtype == torch.float64 and fv.is_cuda
+        b = torch.empty(max(self.n_rows, 1), dtype=torch.float64, device="cuda")
+        _check(load().tw_rhs_values(self._h, C.c_void_p(fv.data_ptr()), C.c_void_p(b.data_ptr()),
+                                    _stream(stream)))
         return b[:self.n_rows]
 
     def l2_project(self, f, csr, tol=1e-12, maxit=None, stream=None, check=True):
@@ -452,6 +480,14 @@ class Batch:
 
 def launch_count() -> int:
     return int(load().tw_launch_count())
+
+
+def pool_info():
+    """(allocations from the library pool so far, bytes reserved and bytes in
+    use by the pool on the current device)."""
+    out = (C.c_int64 * 3)()
+    _check(load().tw_pool_info(out))
+    return int(out[0]), int(out[1]), int(out[2])
 
 
 STAGES = {"setup": 0, "interior": 1, "cutrows": 2, "rhs": 3, "cg": 4, "loss": 5, "adjoint": 6}

@@ -17,6 +17,7 @@
 namespace tw {
 
 std::atomic<int64_t> g_launches{0};
+std::atomic<int64_t> g_pool_allocs{0};
 static std::mutex g_prof_mu;
 
 // ---- stage profiler: event pairs on the launching stream ----
@@ -117,6 +118,7 @@ void *dalloc(tw_patch *P, size_t bytes) {
     return nullptr;
   }
   P->allocs[P->nallocs++] = p;
+  g_pool_allocs++;
   if (slab) {
     P->arena = (char *)p + need;
     P->arena_left = TW_ARENA_SLAB - need;
@@ -164,6 +166,30 @@ using namespace tw;
 
 extern "C" const char *tw_last_error(void) { return g_err; }
 extern "C" int64_t tw_launch_count(void) { return g_launches.load(); }
+
+extern "C" int tw_pool_info(int64_t *info3) {
+  if (!info3) {
+    tw::set_error("tw_pool_info: NULL argument");
+    return TW_EINVAL;
+  }
+  info3[0] = tw::g_pool_allocs.load();
+  info3[1] = info3[2] = 0;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= TW_POOL_MAX_DEVICES) return TW_OK;
+  cudaMemPool_t pool;
+  {
+    std::lock_guard<std::mutex> lock(tw::g_pool_mu);
+    pool = tw::g_pool[dev];
+  }
+  if (!pool) return TW_OK;
+  uint64_t v = 0;
+  if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &v) == cudaSuccess)
+    info3[1] = (int64_t)v;
+  v = 0;
+  if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &v) == cudaSuccess)
+    info3[2] = (int64_t)v;
+  return TW_OK;
+}
 
 extern "C" int tw_profile_enable(int on) {
   g_prof_on = on != 0;
@@ -511,6 +537,22 @@ extern "C" int tw_rhs(tw_patch *P, const tw_func *f, double *b, void *stream) {
     return TW_EINVAL;
   }
   return rhs_launch(P, f, b, (cudaStream_t)stream);
+}
+
+extern "C" int tw_rhs_points(tw_patch *P, int64_t *npts, double *xi, double *x, void *stream) {
+  if (!P || !npts) {
+    set_error("tw_rhs_points: NULL argument");
+    return TW_EINVAL;
+  }
+  return rhs_points_run(P, npts, xi, x, (cudaStream_t)stream);
+}
+
+extern "C" int tw_rhs_values(tw_patch *P, const double *fvals, double *b, void *stream) {
+  if (!P || !b || (!fvals && (int64_t)P->d[0].nq * P->d[1].nq > 0)) {
+    set_error("tw_rhs_values: NULL argument");
+    return TW_EINVAL;
+  }
+  return rhs_values_run(P, fvals, b, (cudaStream_t)stream);
 }
 
 extern "C" int tw_l2_project(tw_patch *P, const tw_func *f, const int64_t *row_ptr,

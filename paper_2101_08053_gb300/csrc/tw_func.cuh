@@ -16,6 +16,16 @@ struct Func {
   const double *coef;
 };
 
+// Where the value of f at a rule point is found when f is given by its values
+// at the points of tw_rhs_points: the WQ grid from 0, the element Gauss points
+// from gbase, the cut-rule points from cbase and the DWQ region points of cut
+// row r from dbase + roff[r].
+struct PtIndex {
+  const double *FV;
+  const int64_t *roff;
+  int64_t gbase, cbase, dbase;
+};
+
 static __device__ __forceinline__ void phys_at(const Geo &G, const Dir &A, const Dir &B, double x1,
                                         double x2, double *X) {
   if (G.geom_kind != TW_GEOM_SPLINE) {

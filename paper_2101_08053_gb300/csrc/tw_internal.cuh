@@ -750,6 +750,12 @@ struct tw_patch {
   size_t arena_left;
   int arena_on;
   int64_t *i64tmp;
+  // rule points of the rhs for an f given by values (built on first use):
+  // per cut row the offset of its DWQ region points, their device total, and
+  // the length of the whole list (-1 until read back)
+  int64_t *pt_roff;
+  int64_t *pt_dtot;
+  int64_t pt_total;
   // extended B-spline tables (host struct with device pointers), built on
   // demand by tw_extension_build
   void *ext;
@@ -758,6 +764,7 @@ struct tw_patch {
 // host helpers shared by the translation units
 namespace tw {
 extern std::atomic<int64_t> g_launches;
+extern std::atomic<int64_t> g_pool_allocs;  // allocations made from the library pool
 int prof_start(cudaStream_t s);                  // -1 when profiling is off
 void prof_stop(int slot, int stage, cudaStream_t s);
 void set_error(const char *fmt, ...);
@@ -776,6 +783,8 @@ int form_mass_launch(tw_patch *P, int precision, int64_t *row_ptr, int32_t *col,
                      cudaStream_t s);
 int launch_interior32(tw_patch *P, int precision, int32_t *col, void *val, cudaStream_t s);
 int rhs_launch(tw_patch *P, const tw_func *f, double *b, cudaStream_t s);
+int rhs_points_run(tw_patch *P, int64_t *npts, double *xi, double *X, cudaStream_t s);
+int rhs_values_run(tw_patch *P, const double *FV, double *b, cudaStream_t s);
 int l2_project_run(tw_patch *P, const tw_func *f, const int64_t *rp, const int32_t *col,
                    const double *val, double *u, double tol, int maxit, int *iters,
                    double *relres, cudaStream_t s);

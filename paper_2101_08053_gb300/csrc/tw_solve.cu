@@ -37,10 +37,80 @@ __global__ void k_rhs_interior(Dir A, Dir B, const uint8_t *fstate, const int32_
   b[act[g]] = s;
 }
 
+// The region part of a cut row's rule (DWQ region, or the masked WQ rule of a
+// naive row): the 1-D points rx, weights rw and base WQ indices rk (-1 for a
+// DWQ window point) per direction, and the element range r0..r1 the region
+// covers.  kind: 0 Gauss rows (no region), 1 naive, 2 DWQ with a region.
+struct RegionRule {
+  double rx[2][32], rw[2][32];
+  int rk[2][32], nr[2];
+  int r0[2], r1[2];
+};
+
+__device__ __forceinline__ int cut_row_kind(const RowArgs &a, int g) {
+  if (a.method == TW_METHOD_GAUSS || a.method == TW_METHOD_HYBRID) return 0;
+  if (a.method == TW_METHOD_NAIVE) return 1;
+  return a.choice[4 * g] >= 0 ? 2 : 0;
+}
+
+__device__ void region_rule(const RowArgs &a, int g, int kind, RegionRule &R) {
+  const Dir &A = a.A;
+  const Dir &B = a.B;
+  const int P = A.p;
+  const int i1 = g % A.n, i2 = g / A.n;
+  const int lo1 = max(0, i1 - P), hi1 = min(A.nel - 1, i1);
+  const int lo2 = max(0, i2 - P), hi2 = min(B.nel - 1, i2);
+  R.r0[0] = R.r0[1] = 1;
+  R.r1[0] = R.r1[1] = 0;
+  R.nr[0] = R.nr[1] = 0;
+  if (kind == 0) return;
+  for (int d = 0; d < 2; d++) {
+    const Dir &D = d == 0 ? A : B;
+    int i = d == 0 ? i1 : i2;
+    int n = 0;
+    int ck = kind == 2 ? a.choice[4 * g + 2 * d] : 0;
+    int s = kind == 2 ? a.choice[4 * g + 2 * d + 1] : -1;
+    int lo = d == 0 ? lo1 : lo2, hi = d == 0 ? hi1 : hi2;
+    R.r0[d] = ck == 2 ? s : lo;
+    R.r1[d] = ck == 1 ? s - 1 : hi;
+    if (ck == 0) {
+      for (int c = 0; c < D.qcnt[i] && n < 32; c++) {
+        R.rx[d][n] = D.xq[D.qbeg[i] + c];
+        R.rw[d][n] = D.W[(size_t)i * D.qmax + c];
+        R.rk[d][n] = D.qbeg[i] + c;
+        n++;
+      }
+    } else {
+      int side = ck - 1, sl = a.disc_slot[d][s];
+      double t = D.bp[s];
+      const double *xs = a.dwq_x[d] + (size_t)sl * TW_LQMAX;
+      const double *ws = a.dwq_w[d] + (((size_t)sl * P + (i - s)) * 2 + side) * TW_LQMAX;
+      for (int k = 0; k < a.dwq_np[d][sl] && n < 32; k++) {
+        double x = xs[k];
+        if (!(x > D.U[i] && x < D.U[i + P + 1])) continue;
+        if (side == 0 ? !(x < t) : !(x > t)) continue;
+        R.rx[d][n] = x;
+        R.rw[d][n] = ws[k];
+        R.rk[d][n] = -1;
+        n++;
+      }
+    }
+    R.nr[d] = n;
+  }
+  if (kind == 1) {  // region unused for element exclusion: naive uses no Gauss
+    R.r0[0] = R.r0[1] = 1;
+    R.r1[0] = R.r1[1] = 0;
+  }
+}
+
 // one warp per cut row: the same three parts as k_cutrows, applied to f; the
-// lanes share the row's points and the warp adds their sums in a fixed order
-__global__ void __launch_bounds__(128) k_rhs_cut(RowArgs a, Func f, const int32_t *rows,
-                                                 int nrows, const double *FC, double *b) {
+// lanes share the row's points and the warp adds their sums in a fixed order.
+// VALUES: f is read at the listed rule points (tw_rhs_values) instead of being
+// evaluated; the index of each point follows the list of tw_rhs_points.
+template <bool VALUES>
+__global__ void __launch_bounds__(128) k_rhs_cut(RowArgs a, Func f, PtIndex pi,
+                                                 const int32_t *rows, int nrows, const double *FC,
+                                                 double *b) {
   const int lane = threadIdx.x & 31;
   const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (r >= nrows) return;  // the whole warp
@@ -49,72 +119,33 @@ __global__ void __launch_bounds__(128) k_rhs_cut(RowArgs a, Func f, const int32_
   const int P = A.p, p1 = P + 1;
   int g = rows[r];
   int i1 = g % A.n, i2 = g / A.n;
-  int kind;
-  if (a.method == TW_METHOD_GAUSS || a.method == TW_METHOD_HYBRID) kind = 0;
-  else if (a.method == TW_METHOD_NAIVE) kind = 1;
-  else kind = a.choice[4 * g] >= 0 ? 2 : 0;
+  const int kind = cut_row_kind(a, g);
   int lo1 = max(0, i1 - P), hi1 = min(A.nel - 1, i1);
   int lo2 = max(0, i2 - P), hi2 = min(B.nel - 1, i2);
-  int r0[2] = {1, 1}, r1[2] = {0, 0};
+  RegionRule R;
+  region_rule(a, g, kind, R);
   double sum = 0.0;
   if (kind != 0) {
-    double rx[2][32], rw[2][32];
-    int rk[2][32], nr[2];
-    for (int d = 0; d < 2; d++) {
-      const Dir &D = d == 0 ? A : B;
-      int i = d == 0 ? i1 : i2;
-      int n = 0;
-      int ck = kind == 2 ? a.choice[4 * g + 2 * d] : 0;
-      int s = kind == 2 ? a.choice[4 * g + 2 * d + 1] : -1;
-      int lo = d == 0 ? lo1 : lo2, hi = d == 0 ? hi1 : hi2;
-      r0[d] = ck == 2 ? s : lo;
-      r1[d] = ck == 1 ? s - 1 : hi;
-      if (ck == 0) {
-        for (int c = 0; c < D.qcnt[i] && n < 32; c++) {
-          rx[d][n] = D.xq[D.qbeg[i] + c];
-          rw[d][n] = D.W[(size_t)i * D.qmax + c];
-          rk[d][n] = D.qbeg[i] + c;
-          n++;
-        }
-      } else {
-        int side = ck - 1, sl = a.disc_slot[d][s];
-        double t = D.bp[s];
-        const double *xs = a.dwq_x[d] + (size_t)sl * TW_LQMAX;
-        const double *ws = a.dwq_w[d] + (((size_t)sl * P + (i - s)) * 2 + side) * TW_LQMAX;
-        for (int k = 0; k < a.dwq_np[d][sl] && n < 32; k++) {
-          double x = xs[k];
-          if (!(x > D.U[i] && x < D.U[i + P + 1])) continue;
-          if (side == 0 ? !(x < t) : !(x > t)) continue;
-          rx[d][n] = x;
-          rw[d][n] = ws[k];
-          rk[d][n] = -1;
-          n++;
-        }
-      }
-      nr[d] = n;
-    }
-    if (kind == 1) {  // region unused for element exclusion: naive uses no Gauss
-      r0[0] = r0[1] = 1;
-      r1[0] = r1[1] = 0;
-    }
-    for (int t = lane; t < nr[0] * nr[1]; t += 32) {
-      const int ia = t % nr[0], ib = t / nr[0];
-      int k1 = rk[0][ia], k2 = rk[1][ib];
+    for (int t = lane; t < R.nr[0] * R.nr[1]; t += 32) {
+      const int ia = t % R.nr[0], ib = t / R.nr[0];
+      int k1 = R.rk[0][ia], k2 = R.rk[1][ib];
       double v;
       if (k1 >= 0 && k2 >= 0) {
         v = FC[(size_t)k2 * A.nq + k1];
         if (kind == 1 && a.estate[B.qel[k2] * A.nel + A.qel[k1]] != TW_ELEM_REGULAR) v = 0.0;
       } else {
-        v = coef_at(a.G, A, B, rx[0][ia], rx[1][ib]) * fpoint(f, a.G, A, B, rx[0][ia], rx[1][ib]);
+        const double fv = VALUES ? pi.FV[pi.dbase + pi.roff[r] + t]
+                                 : fpoint(f, a.G, A, B, R.rx[0][ia], R.rx[1][ib]);
+        v = coef_at(a.G, A, B, R.rx[0][ia], R.rx[1][ib]) * fv;
       }
-      sum += rw[0][ia] * rw[1][ib] * v;
+      sum += R.rw[0][ia] * R.rw[1][ib] * v;
     }
   }
   for (int e2 = lo2; e2 <= hi2; e2++)
     for (int e1 = lo1; e1 <= hi1; e1++) {
       int e = e2 * A.nel + e1;
       uint8_t st = a.estate[e];
-      bool inR = e1 >= r0[0] && e1 <= r1[0] && e2 >= r0[1] && e2 <= r1[1];
+      bool inR = e1 >= R.r0[0] && e1 <= R.r1[0] && e2 >= R.r0[1] && e2 <= R.r1[1];
       if (st == TW_ELEM_REGULAR && kind != 1 && !inR) {
         const double *cgp = a.gc + (size_t)a.gslot[e] * p1 * p1;
         double h1 = 0.5 * (A.bp[e1 + 1] - A.bp[e1]), h2 = 0.5 * (B.bp[e2 + 1] - B.bp[e2]);
@@ -123,14 +154,17 @@ __global__ void __launch_bounds__(128) k_rhs_cut(RowArgs a, Func f, const int32_
           double x1 = A.bp[e1] + h1 * (A.gx[g1] + 1.0), x2 = B.bp[e2] + h2 * (B.gx[g2] + 1.0);
           double w = A.gw[g1] * h1 * B.gw[g2] * h2 * A.GB[(e1 * p1 + g1) * p1 + (i1 - e1)] *
                      B.GB[(e2 * p1 + g2) * p1 + (i2 - e2)];
-          sum += w * cgp[g2 * p1 + g1] * fpoint(f, a.G, A, B, x1, x2);
+          const double fv = VALUES ? pi.FV[pi.gbase + (int64_t)a.gslot[e] * p1 * p1 + t]
+                                   : fpoint(f, a.G, A, B, x1, x2);
+          sum += w * cgp[g2 * p1 + g1] * fv;
         }
       } else if (st == TW_ELEM_CUT) {
         int cs = a.cut_slot[e];
         for (int64_t q = a.cut_off[cs] + lane; q < a.cut_off[cs + 1]; q += 32) {
           const double *Bv = a.cut_B + 2 * q * p1;
           const double *xq = a.cut_pts + 3 * q;
-          sum += a.cut_wc[q] * Bv[i1 - e1] * Bv[p1 + (i2 - e2)] * fpoint(f, a.G, A, B, xq[0], xq[1]);
+          const double fv = VALUES ? pi.FV[pi.cbase + q] : fpoint(f, a.G, A, B, xq[0], xq[1]);
+          sum += a.cut_wc[q] * Bv[i1 - e1] * Bv[p1 + (i2 - e2)] * fv;
         }
       }
     }
@@ -356,7 +390,8 @@ static int rhs_impl(tw_patch *P, const tw_func *f, double *b, cudaStream_t s) {
     TW_LAUNCH();
   }
   if (P->ncutrows > 0) {
-    k_rhs_cut<<<(P->ncutrows + 3) / 4, 128, 0, s>>>(row_args(P), F, P->cutrows, P->ncutrows, FC, b);
+    k_rhs_cut<false><<<(P->ncutrows + 3) / 4, 128, 0, s>>>(row_args(P), F, PtIndex{}, P->cutrows,
+                                                            P->ncutrows, FC, b);
     TW_LAUNCH();
   }
   return check_cuda(cudaGetLastError(), "tw_rhs");
@@ -369,6 +404,201 @@ int rhs_launch(tw_patch *P, const tw_func *f, double *b, cudaStream_t s) {
   int mark = P->nallocs;
   int ps = prof_start(s);
   int rc = rhs_impl(P, f, b, s);
+  prof_stop(ps, TW_STAGE_RHS, s);
+  release_to(P, mark);
+  P->stream = keep;
+  return rc;
+}
+
+// ---------------------------------------------------------------------------
+// Rule points of the right-hand side for an f given by values (tw_rhs_points,
+// tw_rhs_values).  The list: the WQ grid (k2 * nq1 + k1), the element Gauss
+// points of the Gauss slots (slot, then g2, g1), the cut-rule points, the DWQ
+// region points of each cut row (row, then ib, ia as k_rhs_cut walks them).
+// Every point is formed by the same expression the rhs kernels use, so a value
+// listed for it is the value tw_rhs would have evaluated there.
+
+__device__ __forceinline__ void put_point(const RowArgs &a, int64_t k, double x1, double x2,
+                                          double *xi, double *X) {
+  if (xi) {
+    xi[2 * k] = x1;
+    xi[2 * k + 1] = x2;
+  }
+  if (X) {
+    double Q[2];
+    phys_at(a.G, a.A, a.B, x1, x2, Q);
+    X[2 * k] = Q[0];
+    X[2 * k + 1] = Q[1];
+  }
+}
+
+// number of DWQ region points of each cut row; cnt[nrows] = 0 (for the scan)
+__global__ void k_pts_count(RowArgs a, const int32_t *rows, int nrows, int64_t *cnt) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r > nrows) return;
+  if (r == nrows) {
+    cnt[r] = 0;
+    return;
+  }
+  const int g = rows[r];
+  const int kind = cut_row_kind(a, g);
+  if (kind != 2) {
+    cnt[r] = 0;
+    return;
+  }
+  RegionRule R;
+  region_rule(a, g, kind, R);
+  cnt[r] = (int64_t)R.nr[0] * R.nr[1];
+}
+
+__global__ void k_pts_grid(RowArgs a, double *xi, double *X) {
+  const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= (int64_t)a.A.nq * a.B.nq) return;
+  const int k1 = (int)(id % a.A.nq), k2 = (int)(id / a.A.nq);
+  put_point(a, id, a.A.xq[k1], a.B.xq[k2], xi, X);
+}
+
+// thread per (element, Gauss point); elements without a Gauss slot write nothing
+__global__ void k_pts_gauss(RowArgs a, int64_t base, double *xi, double *X) {
+  const Dir &A = a.A;
+  const Dir &B = a.B;
+  const int p1 = A.p + 1;
+  const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= (int64_t)A.nel * B.nel * p1 * p1) return;
+  const int e = (int)(id / (p1 * p1)), t = (int)(id % (p1 * p1));
+  const int sl = a.gslot[e];
+  if (sl < 0) return;
+  const int e1 = e % A.nel, e2 = e / A.nel, g1 = t % p1, g2 = t / p1;
+  const double h1 = 0.5 * (A.bp[e1 + 1] - A.bp[e1]), h2 = 0.5 * (B.bp[e2 + 1] - B.bp[e2]);
+  const double x1 = A.bp[e1] + h1 * (A.gx[g1] + 1.0), x2 = B.bp[e2] + h2 * (B.gx[g2] + 1.0);
+  put_point(a, base + (int64_t)sl * p1 * p1 + t, x1, x2, xi, X);
+}
+
+__global__ void k_pts_cut(RowArgs a, int64_t base, int64_t npts, double *xi, double *X) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= npts) return;
+  put_point(a, base + q, a.cut_pts[3 * q], a.cut_pts[3 * q + 1], xi, X);
+}
+
+// one warp per cut row
+__global__ void __launch_bounds__(128) k_pts_dwq(RowArgs a, const int32_t *rows, int nrows,
+                                                 const int64_t *roff, int64_t base, double *xi,
+                                                 double *X) {
+  const int lane = threadIdx.x & 31;
+  const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (r >= nrows) return;
+  const int g = rows[r];
+  const int kind = cut_row_kind(a, g);
+  if (kind != 2) return;
+  RegionRule R;
+  region_rule(a, g, kind, R);
+  for (int t = lane; t < R.nr[0] * R.nr[1]; t += 32) {
+    const int ia = t % R.nr[0], ib = t / R.nr[0];
+    put_point(a, base + roff[r] + t, R.rx[0][ia], R.rx[1][ib], xi, X);
+  }
+}
+
+__global__ void k_fc_values(const double *C, const double *FV, double *FC, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) FC[i] = C[i] * FV[i];
+}
+
+// per-row offsets of the DWQ region points (patch-owned, built on first use)
+static int ensure_point_index(tw_patch *P, cudaStream_t s) {
+  if (P->pt_roff) return 0;
+  const int64_t n = (int64_t)P->ncutrows + 1;
+  int64_t *buf = (int64_t *)dalloc(P, sizeof(int64_t) * (2 * n + 1));
+  if (!buf) return TW_ENOMEM;
+  int64_t *cnt = buf, *roff = buf + n, *tot = buf + 2 * n;
+  k_pts_count<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(row_args(P), P->cutrows, P->ncutrows,
+                                                          cnt);
+  TW_LAUNCH();
+  int rc = exclusive_scan_i64(cnt, roff, n, tot, s, P);
+  if (rc) return rc;
+  P->pt_roff = roff;
+  P->pt_dtot = tot;
+  P->pt_total = -1;
+  return check_cuda(cudaGetLastError(), "rhs point index");
+}
+
+static PtIndex point_index(const tw_patch *P, const double *FV) {
+  const int64_t p1 = P->p + 1;
+  PtIndex pi;
+  pi.FV = FV;
+  pi.roff = P->pt_roff;
+  pi.gbase = (int64_t)P->d[0].nq * P->d[1].nq;
+  pi.cbase = pi.gbase + (int64_t)P->ngslot * p1 * p1;
+  pi.dbase = pi.cbase + P->ncutpts;
+  return pi;
+}
+
+int rhs_points_run(tw_patch *P, int64_t *npts, double *xi, double *X, cudaStream_t s) {
+  cudaStream_t keep = P->stream;
+  P->stream = s;
+  int rc = ensure_point_index(P, s);
+  if (!rc && P->pt_total < 0) {
+    int64_t h = 0;
+    rc = check_cuda(cudaMemcpyAsync(&h, P->pt_dtot, sizeof(int64_t), cudaMemcpyDeviceToHost, s),
+                    "tw_rhs_points: count");
+    if (!rc) rc = check_cuda(cudaStreamSynchronize(s), "tw_rhs_points: count");
+    if (!rc) P->pt_total = point_index(P, nullptr).dbase + h;
+  }
+  P->stream = keep;
+  if (rc) return rc;
+  *npts = P->pt_total;
+  if (!xi && !X) return 0;
+  const PtIndex pi = point_index(P, nullptr);
+  const RowArgs ra = row_args(P);
+  const int64_t ng = pi.gbase;
+  const int64_t p1 = P->p + 1;
+  const int64_t ngp = (int64_t)P->d[0].nel * P->d[1].nel * p1 * p1;
+  k_pts_grid<<<(unsigned)((ng + 255) / 256), 256, 0, s>>>(ra, xi, X);
+  TW_LAUNCH();
+  if (P->ngslot > 0) {
+    k_pts_gauss<<<(unsigned)((ngp + 255) / 256), 256, 0, s>>>(ra, pi.gbase, xi, X);
+    TW_LAUNCH();
+  }
+  if (P->ncutpts > 0) {
+    k_pts_cut<<<(unsigned)((P->ncutpts + 255) / 256), 256, 0, s>>>(ra, pi.cbase, P->ncutpts, xi,
+                                                                  X);
+    TW_LAUNCH();
+  }
+  if (P->ncutrows > 0 && P->method == TW_METHOD_DWQ) {
+    k_pts_dwq<<<(P->ncutrows + 3) / 4, 128, 0, s>>>(ra, P->cutrows, P->ncutrows, P->pt_roff,
+                                                    pi.dbase, xi, X);
+    TW_LAUNCH();
+  }
+  return check_cuda(cudaGetLastError(), "tw_rhs_points");
+}
+
+int rhs_values_run(tw_patch *P, const double *FV, double *b, cudaStream_t s) {
+  cudaStream_t keep = P->stream;
+  P->stream = s;
+  int rc = ensure_point_index(P, s);
+  int mark = P->nallocs;
+  int ps = prof_start(s);
+  Dir &A = P->d[0];
+  Dir &B = P->d[1];
+  const int64_t ng = (int64_t)A.nq * B.nq;
+  double *FC = rc ? nullptr : (double *)dalloc(P, sizeof(double) * ng);
+  if (!rc && !FC) rc = TW_ENOMEM;
+  if (!rc) {
+    k_fc_values<<<(unsigned)((ng + 255) / 256), 256, 0, s>>>(P->C, FV, FC, ng);
+    TW_LAUNCH();
+    if (P->method != TW_METHOD_GAUSS) {
+      const int64_t nf = (int64_t)A.n * B.n;
+      k_rhs_interior<<<(unsigned)((nf + 255) / 256), 256, 0, s>>>(A, B, P->fstate, P->act, FC, b);
+      TW_LAUNCH();
+    }
+    if (P->ncutrows > 0) {
+      Func F;
+      memset(&F, 0, sizeof(F));
+      k_rhs_cut<true><<<(P->ncutrows + 3) / 4, 128, 0, s>>>(row_args(P), F, point_index(P, FV),
+                                                            P->cutrows, P->ncutrows, FC, b);
+      TW_LAUNCH();
+    }
+    rc = check_cuda(cudaGetLastError(), "tw_rhs_values");
+  }
   prof_stop(ps, TW_STAGE_RHS, s);
   release_to(P, mark);
   P->stream = keep;
@@ -641,8 +871,8 @@ extern "C" int tw_rhs_static(tw_patch *P, const tw_func *f, double *b, void *str
     TW_LAUNCH();
   }
   if (P->ncutrows > 0) {
-    k_rhs_cut<<<(P->ncutrows + 3) / 4, 128, 0, s>>>(row_args(P), F, P->cutrows, P->ncutrows, scr,
-                                                     b);
+    k_rhs_cut<false><<<(P->ncutrows + 3) / 4, 128, 0, s>>>(row_args(P), F, PtIndex{},
+                                                            P->cutrows, P->ncutrows, scr, b);
     TW_LAUNCH();
   }
   return check_cuda(cudaGetLastError(), "tw_rhs_static");

@@ -422,3 +422,29 @@ def test_l2_error_of_zero_is_the_norm_of_f():
     e, fn = P.l2_error(np.zeros(P.n_rows), synth.func_sincos(2.0, 3.0))
     ref = math.sqrt((0.5 - math.sin(4.0) / 8.0) * (0.5 + math.sin(6.0) / 12.0))
     assert abs(fn - ref) <= 1e-12 and abs(e - 1.0) <= 1e-14
+
+
+@pytest.mark.parametrize("method", ["hybrid", "dwq", "naive", "gauss"])
+def test_row_points_carry_the_rhs_rule(method):
+    """or_row_points lists the rule that or_rhs applies (reading R9): summing
+    w c f over the listed physical points gives or_rhs's b for the built-in
+    kinds, so the pins of or_rhs carry over to an f given only as values."""
+    rng = np.random.default_rng(9)
+    spec = synth.make_spec(3, 9, synth.bspline_curve(rng, nc=12, radius=0.3, jitter=0.05),
+                           geom={"kind": "spline", "ctrl": synth.perturbed_bilinear_net(rng, 3, 9)},
+                           coef={"kind": "detj"}, method=method)
+    P = oracle.Patch(spec)
+    for fk, fn in [(synth.func_sinsin(), lambda x, y: np.sin(math.pi * x) * np.sin(math.pi * y)),
+                   (synth.func_gauss(), lambda x, y: np.exp(-10 * ((x - 0.3) ** 2 + (y - 0.7) ** 2)))]:
+        b = P.rhs(fk)
+        b2 = P.rhs_from(fn)
+        assert np.max(np.abs(b - b2)) <= 1e-15 * np.max(np.abs(b)) * 10
+    if method == "gauss":
+        return
+    # the points of an interior row are its tensor WQ rule
+    es, fs, act = P.states()
+    g = [g for g in np.where(fs == 1)[0]][len(np.where(fs == 1)[0]) // 2]
+    q = P.row_points(act[g])
+    x1, x2 = P.wq_grid(0), P.wq_grid(1)
+    assert set(np.round(q[:, 0], 15)) <= set(np.round(x1, 15))
+    assert set(np.round(q[:, 1], 15)) <= set(np.round(x2, 15))
