@@ -30,6 +30,7 @@ import argparse
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -727,9 +728,26 @@ def run_extension(api, torch, args, stream):
             "rel_l2_error": {"extended": err_e, "plain": err_0}}
 
 
-def oracle_sample(seconds_budget=None, rows_per_patch=300, seed=0):
-    """Oracle time for the whole workload, extrapolated from full set-up plus a
-    seeded sample of rows per patch (single thread)."""
+def host_cpu():
+    """Core count and CPU model of the host the oracle runs on."""
+    model = platform.processor() or platform.machine()
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().startswith("Model name:"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"cpu_count": os.cpu_count(), "model": model, "machine": platform.machine()}
+
+
+def oracle_sample(rows_per_patch=300, seed=0, omp=False):
+    """Oracle time for the whole workload: full set-up of every patch plus a
+    seeded sample of rows per patch formed in C (or_form_rows), the row time
+    extrapolated to all rows.  omp=False: the single-thread oracle; omp=True:
+    the same code built with OpenMP, on all host cores.  Returns (nnz/s,
+    extrapolated seconds, process CPU seconds, threads, nnz)."""
     import oracle
 
     rng = np.random.default_rng(seed)
@@ -738,17 +756,41 @@ def oracle_sample(seconds_budget=None, rows_per_patch=300, seed=0):
     cpu0 = time.process_time()
     for s in specs():
         t0 = time.perf_counter()
-        O = oracle.Patch(s)
+        O = oracle.Patch(s, omp=omp)
         t_setup = time.perf_counter() - t0
         rows = rng.integers(0, O.n_rows, rows_per_patch)
         t0 = time.perf_counter()
-        for r in rows:
-            O.form_row(int(r))
+        O.form_rows(rows)
         t_rows = time.perf_counter() - t0
         t_full += t_setup + t_rows * O.n_rows / rows_per_patch
         nnz += O.nnz
     cpu = time.process_time() - cpu0
-    return nnz / t_full, t_full, cpu
+    return nnz / t_full, t_full, cpu, oracle.threads(omp), nnz
+
+
+def cpu_baseline_block(rows_single=300, rows_omp=3000, seed=0):
+    """The oracle on the host cores: the all-cores build as the baseline, the
+    single-thread one beside it."""
+    import oracle
+
+    v1, t1, c1, _, _ = oracle_sample(rows_single, seed, omp=False)
+    host = host_cpu()
+    out = {"value": v1, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": "full set-up of all 12 patches + %d seeded rows per patch, time "
+                     "extrapolated per row to the whole matrices (%.1f s of CPU), one thread"
+                     % (rows_single, c1),
+           "host": host}
+    if oracle.lib(True) is not None:
+        vn, tn, cn, th, _ = oracle_sample(rows_omp, seed, omp=True)
+        out = {"value": vn, "unit": UNIT, "cores": th, "kind": "oracle",
+               "sample": "full set-up of all 12 patches + %d seeded rows per patch, time "
+                         "extrapolated per row to the whole matrices (%.1f s of CPU), the "
+                         "oracle built with OpenMP (row-parallel, the same loops) on %d threads"
+                         % (rows_omp, cn, th),
+               "host": host,
+               "single_thread": {"value": v1, "unit": UNIT, "cores": 1,
+                                 "sample": "%d seeded rows per patch" % rows_single}}
+    return out
 
 
 def main():
@@ -784,11 +826,15 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
+        import oracle
+        omp = oracle.lib(True) is not None
+        rows = 1000 if omp else 100
         for _ in range(args.warmup):
-            oracle_sample(rows_per_patch=100)
+            oracle_sample(rows_per_patch=rows, omp=omp)
         vals, walls, cpus = [], [], []
+        nnz, th = 0, 1
         for k in range(args.steps):
-            v, t, c = oracle_sample(rows_per_patch=100, seed=k)
+            v, t, c, th, nnz = oracle_sample(rows_per_patch=rows, seed=k, omp=omp)
             vals.append(v)
             walls.append(t)
             cpus.append(c)
@@ -797,10 +843,14 @@ def main():
                 "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": float(np.mean(walls)) * 1e3, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": config,
-                "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                 "sample": "full set-up of all 12 patches + 100 seeded rows "
-                                           "per patch, extrapolated per row"},
+                "config": dict(config, nnz_per_step=int(nnz), parallelism="single"),
+                "cpu_baseline": {"value": value, "unit": UNIT, "cores": th, "kind": "oracle",
+                                 "sample": "full set-up of all 12 patches + %d seeded rows per "
+                                           "patch, extrapolated per row%s; ms_per_step is that "
+                                           "extrapolated time" % (
+                                               rows, ", OpenMP build on %d threads" % th
+                                               if omp else ", one thread"),
+                                 "host": host_cpu()},
                 "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
@@ -813,11 +863,7 @@ def main():
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline:
-            v, t, c = oracle_sample()
-            cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": "full set-up of all 12 patches + 300 seeded rows per patch, "
-                             "time extrapolated per row to the whole matrices "
-                             "(%.1f s of CPU)" % c}
+            cpu = cpu_baseline_block()
         line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
