@@ -271,53 +271,30 @@ def run_ours(args, rank, world, local_rank):
         P.close()
     nnz_step = sum(i[1] for i in infos)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    # the batch's patches are independent: greedy-balance them (by nnz) over
-    # `--streams` streams, each driven by its own host thread
+    # the patches are independent: each is one job of tw_run_jobs (created and
+    # formed on its own stream by the library's native thread pool), largest
+    # first; `--streams` native threads take the jobs
+    order = sorted(range(len(sp)), key=lambda k: -infos[k][1])
+    jstreams = [torch.cuda.Stream(device=dev) for _ in order]
+    jobs = api.Jobs([sp[k] for k in order], jstreams, outs=[outs[k] for k in order],
+                    nthreads=max(1, args.streams))
     ns = max(1, min(args.streams, len(sp)))
-    streams = [torch.cuda.Stream(device=dev) for _ in range(ns)]
-    load = [0] * ns
-    assign = [[] for _ in range(ns)]
-    for idx in sorted(range(len(sp)), key=lambda k: -infos[k][1]):
-        k = min(range(ns), key=lambda j: load[j])
-        assign[k].append(idx)
-        load[k] += infos[idx][1]
+    streams = jstreams
 
-    def run_batch(body, tag=None):
+    def step(tag=None):
         start = torch.cuda.Event()
         start.record(stream)
-        errors = []
-
-        def worker(k):
-            try:
-                torch.cuda.set_device(local_rank)
-                if tag:  # NVTX range per launching thread (ncu --nvtx-include)
-                    torch.cuda.nvtx.range_push(tag)
-                with torch.cuda.stream(streams[k]):
-                    streams[k].wait_event(start)
-                    for idx in assign[k]:
-                        body(idx)
-                if tag:
-                    torch.cuda.nvtx.range_pop()
-            except Exception as exc:  # surfaced after the join
-                errors.append(exc)
-
-        threads = [threading.Thread(target=worker, args=(k,)) for k in range(ns)]
-        for t in threads:
-            t.start()
-        for t in threads:
-            t.join()
-        if errors:
-            raise errors[0]
-        for s_ in streams:
+        for s_ in jstreams:
+            s_.wait_event(start)
+        jobs.run()
+        jobs.destroy()  # each destroy waits for its patch's stream
+        for s_ in jstreams:
             stream.wait_stream(s_)
 
     def form_one(idx):
         P = api.Patch(sp[idx])
         P.form_mass("fp64", out=outs[idx])
         P.close()
-
-    def step(tag=None):
-        run_batch(form_one, tag)
 
     for _ in range(args.warmup):
         step()
@@ -382,15 +359,16 @@ def run_ours(args, rank, world, local_rank):
         h2d += np.asarray(s["geom"]["ctrl"]).nbytes
     d2h = sum(o[0].numel() * 8 + o[1].numel() * 4 + o[2].numel() * 8 for o in outs)
 
-    def e2e_one(idx):
-        P = api.Patch(sp[idx])
-        P.form_mass("fp64", out=outs[idx])
-        for a, b in zip(host[idx], outs[idx]):
-            a.copy_(b, non_blocking=True)
-        P.close()
+    e2e_jobs = api.Jobs([sp[k] for k in order], jstreams, outs=[outs[k] for k in order],
+                        host=[host[k] for k in order], nthreads=max(1, args.streams))
 
     def e2e_step():
-        run_batch(e2e_one)
+        start = torch.cuda.Event()
+        start.record(stream)
+        for s_ in jstreams:
+            s_.wait_event(start)
+        e2e_jobs.run()
+        e2e_jobs.destroy()
         torch.cuda.synchronize()
 
     e2e_step()
@@ -528,10 +506,38 @@ def run_batched(api, torch, args, stream, streams, dev):
             torch.cuda.synchronize()
             ts.append(e0.elapsed_time(e1))
         ms = float(np.mean(ts))
+
+        # the same patches formed one tw_form_mass call per patch, serially on
+        # one stream and spread over the streams, into the same buffers
+        def per_patch(nstreams):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sts = [stream] if nstreams == 1 else streams[:nstreams]
+            for st in sts:
+                st.wait_event(e0)
+            for k, P in enumerate(patches):
+                P.form_mass(mode, out=outs[k], stream=sts[k % len(sts)])
+            for st in sts:
+                ev = torch.cuda.Event()
+                ev.record(st)
+                stream.wait_event(ev)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1)
+
+        per = {}
+        for nst in (1, len(streams)):
+            per_patch(nst)
+            t = float(np.mean([per_patch(nst) for _ in range(max(1, args.steps))]))
+            per["streams_%d" % nst] = {"form_ms": round(t, 3), "form_nnz_per_s": nnz / (t * 1e-3)}
+        best = min(v["form_ms"] for v in per.values())
         res[mode] = {"form_nnz_per_s": nnz / (ms * 1e-3), "form_ms": round(ms, 3),
                      "batch_create_s": round(create_s, 3), "items": B.items,
                      "persistent_blocks": B.blocks,
-                     "tiles": {str(p): t for p, t in B.tiles.items() if any(P.p == p for P in patches)}}
+                     "tiles": {str(p): t for p, t in B.tiles.items() if any(P.p == p for P in patches)},
+                     "per_patch_launches": per,
+                     "vs_per_patch": round(best / ms, 3)}
         B.close()
         del outs
     for P in patches:

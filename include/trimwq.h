@@ -355,6 +355,37 @@ int tw_batch_run(tw_batch *batch, void *stream);
 int tw_batch_info(const tw_batch *batch, int64_t *info10);
 int tw_batch_destroy(tw_batch *batch);
 
+/* Many patches at once (no counterpart in the paper, which forms one patch at
+ * a time; the matrices are those of tw_patch_create + tw_form_mass).  Each job
+ * creates a patch from its host descriptor, with all its work ordered on the
+ * descriptor's stream; if row_ptr is set it then forms the mass matrix into
+ * those device buffers (capacities checked: TW_EINVAL, patch kept), and if
+ * h_row_ptr / h_col / h_val are set it copies the CSR into that host memory
+ * with cudaMemcpyAsync on the stream (pinned memory: the copies complete when
+ * the stream does).  The jobs run on a persistent pool of native host threads
+ * that the library starts on first use (nthreads threads with the calling
+ * thread, 0 = one per host core, at most one per job and 64), so the set-up
+ * chains of different patches overlap on the GPU.  Returns when every job's
+ * host part is done (each create has synchronised its stream; formations and
+ * copies may still run); the first failing job's status is returned and its
+ * message is in tw_last_error.  Give each job its own stream.  The caller
+ * destroys every non-NULL patch. */
+typedef struct {
+  const tw_patch_desc *desc; /* in */
+  int precision;             /* in: TW_PREC_* of the formation */
+  int64_t *row_ptr;          /* in: device CSR buffers, or NULL (set-up only) */
+  int32_t *col;
+  void *val;
+  int64_t rows_capacity;     /* in: row_ptr holds rows_capacity + 1 entries */
+  int64_t nnz_capacity;      /* in: col and val hold nnz_capacity entries */
+  int64_t *h_row_ptr;        /* in: host destinations of the CSR, or NULL */
+  int32_t *h_col;
+  void *h_val;
+  tw_patch *patch;           /* out: the created patch, or NULL */
+  int status;                /* out: TW_OK or TW_E* */
+} tw_job;
+int tw_run_jobs(tw_job *jobs, int n, int nthreads);
+
 /* Number of kernels this library has launched in this process.  The paper has
  * no counterpart: an instrumentation counter. */
 int64_t tw_launch_count(void);

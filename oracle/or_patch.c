@@ -936,16 +936,30 @@ int or_form_row(const or_patch *Pc, int64_t row, int32_t *col, double *val) {
 
 /* Rows rows[0..n) of the matrix, row k's values at val + k * (2p+1)^2 and its
  * entry count in cnt[k].  The rows are independent: with OpenMP (the oracle's
- * all-cores build) they are formed in parallel; the lazily filled table of c
- * at the element Gauss points is filled for every element first, so that the
- * rows only read shared state. */
+ * all-cores build) they are formed in parallel.  The lazily filled table of c
+ * at the element Gauss points is filled first for the regular elements that
+ * these rows' Gauss parts use (the ones row-by-row formation would fill), so
+ * that the rows only read shared state. */
 void or_form_rows(const or_patch *Pc, const int64_t *rows, int64_t n, double *val, int *cnt) {
   or_patch *P = (or_patch *)Pc;
   const dirdata *A = &P->D[0], *B = &P->D[1];
   const int ne = A->nel * B->nel;
+  uint8_t *need = (uint8_t *)calloc((size_t)ne, 1);
+  for (int64_t k = 0; k < n; k++) {
+    const int g = (int)P->rowg[rows[k]];
+    const int kind = row_kind(P, g);
+    if (kind != ROW_GAUSS && kind != ROW_DWQ) continue;
+    const int i1 = g % A->n, i2 = g / A->n;
+    for (int e2 = i2 - B->p; e2 <= i2; e2++)
+      for (int e1 = i1 - A->p; e1 <= i1; e1++)
+        if (e1 >= 0 && e2 >= 0 && e1 < A->nel && e2 < B->nel &&
+            P->estate[e2 * A->nel + e1] == OR_ELEM_REGULAR)
+          need[e2 * A->nel + e1] = 1;
+  }
 #pragma omp parallel for schedule(dynamic, 64)
   for (int e = 0; e < ne; e++)
-    if (P->estate[e] == OR_ELEM_REGULAR) gauss_c(P, e % A->nel, e / A->nel);
+    if (need[e]) gauss_c(P, e % A->nel, e / A->nel);
+  free(need);
   const int64_t w = (int64_t)(2 * A->p + 1) * (2 * B->p + 1);
 #pragma omp parallel for schedule(dynamic, 16)
   for (int64_t k = 0; k < n; k++) cnt[k] = or_form_row(P, rows[k], NULL, val + k * w);

@@ -14,7 +14,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libtrimwq.so")
 BUILD_DIR = os.path.join(ROOT, "_build")
 UNITS = ["tw_setup.cu", "tw_form.cu", "tw_form32.cu", "tw_batch.cu", "tw_solve.cu", "tw_adjoint.cu",
-         "tw_extend.cu", "tw_api.cu"]
+         "tw_extend.cu", "tw_jobs.cu", "tw_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 

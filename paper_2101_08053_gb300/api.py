@@ -52,6 +52,23 @@ class PatchDesc(C.Structure):
     ]
 
 
+class JobDesc(C.Structure):
+    _fields_ = [
+        ("desc", C.POINTER(PatchDesc)),
+        ("precision", C.c_int),
+        ("row_ptr", C.c_void_p),
+        ("col", C.c_void_p),
+        ("val", C.c_void_p),
+        ("rows_capacity", C.c_int64),
+        ("nnz_capacity", C.c_int64),
+        ("h_row_ptr", C.c_void_p),
+        ("h_col", C.c_void_p),
+        ("h_val", C.c_void_p),
+        ("patch", C.c_void_p),
+        ("status", C.c_int),
+    ]
+
+
 class FuncDesc(C.Structure):
     _fields_ = [
         ("kind", C.c_int),
@@ -99,6 +116,7 @@ def load(build: bool = True):
                                                  C.POINTER(C.c_int), C.POINTER(C.c_double), vp]
     L.tw_states.argtypes = [vp, vp, vp, vp, vp]
     L.tw_patch_table.argtypes = [vp, C.c_int, vp, C.c_int64, i64p, vp]
+    L.tw_run_jobs.argtypes = [C.POINTER(JobDesc), C.c_int, C.c_int]
     L.tw_launch_count.restype = C.c_int64
     L.tw_pool_info.argtypes = [i64p]
     L.tw_batch_create.argtypes = [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.POINTER(C.c_void_p),
@@ -438,6 +456,50 @@ class Patch:
         _check(L.tw_patch_table(self._h, which, C.c_void_p(t.data_ptr()), n.value, C.byref(n),
                                 _stream(stream)))
         return t[:n.value]
+
+
+class Jobs:
+    """tw_run_jobs: create and form many patches, each on its own stream, from
+    the library's native thread pool.  specs and streams (torch streams) per
+    job; outs: CSR device buffers per job (Patch.alloc_csr) or None for set-up
+    only; host: host CSR buffers per job (pinned tensors) or None.  The
+    descriptors are built once here; run() may be called repeatedly and
+    returns the created patches' handles for destroy()."""
+
+    def __init__(self, specs, streams, outs=None, precision="fp64", host=None, nthreads=0):
+        n = len(specs)
+        self._keep = []
+        self._descs = (PatchDesc * n)()
+        self._jobs = (JobDesc * n)()
+        self.n, self.nthreads = n, int(nthreads)
+        for k, sp in enumerate(specs):
+            d = make_patch_desc(sp, self._keep)
+            d.stream = _stream(streams[k])
+            self._descs[k] = d
+            J = self._jobs[k]
+            J.desc = C.pointer(self._descs[k])
+            J.precision = PREC[precision]
+            if outs is not None:
+                rp, col, val = outs[k]
+                J.row_ptr, J.col, J.val = rp.data_ptr(), col.data_ptr(), val.data_ptr()
+                J.rows_capacity, J.nnz_capacity = rp.numel() - 1, col.numel()
+            if host is not None:
+                hr, hc, hv = host[k]
+                J.h_row_ptr, J.h_col, J.h_val = hr.data_ptr(), hc.data_ptr(), hv.data_ptr()
+        self.handles = []
+
+    def run(self):
+        rc = load().tw_run_jobs(self._jobs, self.n, self.nthreads)
+        self.handles = [self._jobs[k].patch for k in range(self.n)]
+        _check(rc)
+        return self.handles
+
+    def destroy(self):
+        L = load()
+        for h in self.handles:
+            if h:
+                L.tw_patch_destroy(h)
+        self.handles = []
 
 
 class Batch:
