@@ -7,6 +7,7 @@
 
 #include <type_traits>
 
+#include "tw_bulk.cuh"
 #include "tw_interior.cuh"
 
 namespace tw {
@@ -474,83 +475,180 @@ __device__ __forceinline__ void df_fma(float2 a, float2 b, float &sh, float &sl)
   sl = __fadd_rn(sl, __fadd_rn(err, e));
 }
 
-// smem of one FP32-pipe tile: Y | V2s | the tile's outputs (T rows x W^2,
-// written out row by row with coalesced stores; double for the split mode) |
-// cr2 | flag
+// The tables of the FP32-pipe contraction.  FP32: c and the weighted basis
+// rounded to float; split: (hi, lo) float pairs.  The c grid is padded to a
+// row stride ldc of 16 bytes' multiple so that any 16-byte-aligned column range
+// of a row can be bulk-copied; Vc1 holds, per test function of direction 1
+// and point c1 of its support, the P+1 weighted basis values that can be
+// nonzero there (trial functions el .. el+P of the point's support element
+// el = c1 / 2; rows whose support has the two-point layout of inner
+// elements), padded by one row.
+struct Tables32 {
+  const void *C;  // float or float2, nq2 x ldc
+  int ldc;
+  const void *Vc1;  // float or float2, (n1 + 1) x (2P+2) x (P+1)
+  const float2 *V1f, *V2f;  // full weighted basis tables (hi, lo), n x qmax x W
+  int bulk_out;             // the CSR buffers are 16-byte aligned: bulk stores allowed
+};
+
+// Shared memory of one FP32-pipe tile (16-byte-aligned regions):
+//   slab  the c rows of supp B_i2 over the tile's columns (bulk-copied)
+//   vc    the tile's rows of Vc1 (bulk-copied)
+//   Y     stage-1 sums, W x KMAX
+//   V2s   the weighted basis of row i2
+//   os    the tile's outputs in CSR order (+ one 16-byte alignment shift)
+//   cs    their columns (+ the same)
+//   cr2   band ranges of row i2
 __host__ __device__ constexpr int interior32_kmax(int P, int T) { return (2 * T + 4 * P + 4) | 1; }
-__host__ __device__ constexpr size_t interior32_out_off(int P, int T) {
-  return sizeof(float2) * ((size_t)(2 * P + 1) * interior32_kmax(P, T) + TW_QMAX * (2 * P + 1));
+__host__ __device__ constexpr size_t a16(size_t x) { return (x + 15) / 16 * 16; }
+__host__ __device__ constexpr size_t interior32_slab_cols(int P, int T) {
+  return (size_t)interior32_kmax(P, T) + 8;  // columns rounded out to 16 bytes on both sides
+}
+struct Layout32 {
+  size_t slab, vc, y, v2, os, cs, cr2, total;
+};
+__host__ __device__ constexpr Layout32 interior32_layout(int P, int T, bool split) {
+  const size_t e = split ? sizeof(float2) : sizeof(float);
+  const size_t o = split ? sizeof(double) : sizeof(float);
+  const int W = 2 * P + 1, Q = 4 * P;  // Q bounds the WQ points of one support
+  Layout32 L{};
+  L.slab = 0;
+  L.vc = L.slab + a16(e * Q * interior32_slab_cols(P, T));
+  L.y = L.vc + a16(e * (size_t)T * (2 * P + 2) * (P + 1));
+  L.v2 = L.y + a16(e * (size_t)W * interior32_kmax(P, T));
+  L.os = L.v2 + a16(e * (size_t)Q * W);
+  L.cs = L.os + a16(o * ((size_t)T * W * W + 16 / o));
+  L.cr2 = L.cs + a16(sizeof(int) * ((size_t)T * W * W + 4));
+  L.total = L.cr2 + a16(sizeof(int) * (W + 2));
+  return L;
 }
 __host__ __device__ constexpr size_t interior32_smem(int P, int T, bool split = true) {
-  return interior32_out_off(P, T) +
-         (split ? sizeof(double) : sizeof(float)) * (size_t)T * (2 * P + 1) * (2 * P + 1) +
-         sizeof(int) * (2 * P + 2);
+  return interior32_layout(P, T, split).total;
 }
 
+// One tile of T test functions i1a .. i1a+T-1 of row i2 on the FP32 pipes.
+// One thread stages the c slab and the tile's Vc1 rows with bulk copies on
+// the mbarrier *bar (phase *phase, flipped here); stage 1 and stage 2 then
+// read shared memory only.  A tile whose rows are all interior with a full
+// band owns one contiguous CSR range: its values and columns are staged in
+// CSR order and written by bulk shared -> global copies (the unaligned head
+// and tail by plain stores); other tiles write one row per warp.  A wait that
+// runs out sets TWF_TIMEOUT in *flag and the block abandons the tile (the
+// decision is taken by the whole block, so no thread is left at a barrier).
 template <int P, bool SPLIT>
-__device__ void interior_tile32(const Dir &A, const Dir &B, const float2 *__restrict__ Cf,
-                                const float2 *__restrict__ V1f, const float2 *__restrict__ V2f,
+__device__ void interior_tile32(const Dir &A, const Dir &B, const Tables32 &tb,
                                 const uint8_t *__restrict__ fstate,
                                 const int32_t *__restrict__ act, const int64_t *__restrict__ rp,
                                 int32_t *__restrict__ col, void *__restrict__ valv, int i2,
-                                int i1a, int T, char *smem) {
-  constexpr int W = 2 * P + 1;
+                                int i1a, int T, char *smem, uint64_t *bar, uint32_t *phase,
+                                int *flag) {
+  constexpr int W = 2 * P + 1, NV = (2 * P + 2) * (P + 1);
+  using ET = typename std::conditional<SPLIT, float2, float>::type;
   using OutT = typename std::conditional<SPLIT, double, float>::type;
-  const int KMAX = interior32_kmax(P, T);
-  float2 *Y = (float2 *)smem;
-  float2 *V2s = Y + W * KMAX;
-  OutT *os = (OutT *)(smem + interior32_out_off(P, T));  // [t][r2][r1]
-  int *cr2 = (int *)(os + (size_t)T * W * W);
+  constexpr int AE = 16 / (int)sizeof(ET);    // elements per 16 bytes of a table
+  constexpr int AO = 16 / (int)sizeof(OutT);  // of the outputs
+  const Layout32 L = interior32_layout(P, T, SPLIT);
+  ET *slab = (ET *)(smem + L.slab);
+  ET *vcs = (ET *)(smem + L.vc);
+  ET *Y = (ET *)(smem + L.y);
+  ET *V2s = (ET *)(smem + L.v2);
+  OutT *osb = (OutT *)(smem + L.os);
+  int32_t *csb = (int32_t *)(smem + L.cs);
+  int *cr2 = (int *)(smem + L.cr2);
   int *anyintp = cr2 + W;
+  int *fullp = cr2 + W + 1;
+  const int KMAX = interior32_kmax(P, T);
   const int i1b = min(A.n, i1a + T);
+  const int nr = i1b - i1a;
   const int n1 = A.n;
-  if (threadIdx.x == 0) *anyintp = 0;
+  if (threadIdx.x == 0) {
+    *anyintp = 0;
+    *fullp = (i2 >= P && i2 <= B.n - 1 - P && i1a >= P && i1b - 1 <= n1 - 1 - P) ? 1 : 0;
+  }
   __syncthreads();
-  for (int t = threadIdx.x; t < i1b - i1a; t += blockDim.x)
+  for (int t = threadIdx.x; t < nr; t += blockDim.x) {
     if (fstate[i2 * n1 + i1a + t] == TW_FUNC_INTERIOR) *anyintp = 1;
+    else *fullp = 0;
+  }
   __syncthreads();
   if (!*anyintp) return;  // uniform across the block
+  const bool full = *fullp != 0;
   const int kA = A.qbeg[i1a];
   const int kB = A.qbeg[i1b - 1] + A.qcnt[i1b - 1];
-  const int K = kB - kA;
+  const int kA0 = kA & ~(AE - 1);
+  const int Kp = ((kB + AE - 1) & ~(AE - 1)) - kA0;  // slab row length, whole 16-byte units
+  const int off = kA - kA0;
   const int qb2 = B.qbeg[i2], qc2 = B.qcnt[i2];
-  for (int t = threadIdx.x; t < qc2 * W; t += blockDim.x) V2s[t] = V2f[(size_t)i2 * B.qmax * W + t];
+  // bulk loads: qc2 slab rows and the tile's Vc1 rows (even row count)
+  if (threadIdx.x == 0) {
+    const int nvr = (nr + 1) & ~1;
+    const uint32_t rowb = (uint32_t)(sizeof(ET) * Kp);
+    const uint32_t vcb = (uint32_t)(sizeof(ET) * NV * nvr);
+    mbar_arrive_expect(bar, rowb * qc2 + vcb);
+    const ET *C = (const ET *)tb.C;
+    for (int c2 = 0; c2 < qc2; c2++)
+      bulk_g2s(slab + (size_t)c2 * Kp, C + (size_t)(qb2 + c2) * tb.ldc + kA0, rowb, bar);
+    bulk_g2s(vcs, (const ET *)tb.Vc1 + (size_t)i1a * NV, vcb, bar);
+  }
+  const float2 *V2f = tb.V2f + (size_t)i2 * B.qmax * W;
+  for (int t = threadIdx.x; t < qc2 * W; t += blockDim.x) {
+    if constexpr (SPLIT) V2s[t] = V2f[t];
+    else V2s[t] = V2f[t].x;
+  }
   for (int t = threadIdx.x; t < W; t += blockDim.x) cr2[t] = B.crange[i2 * W + t];
-  __syncthreads();
-  // stage 1: Y[r2][k1] = sum_{k2} V2[i2][k2][r2] c[k2][k1]; a thread owns two
-  // neighbouring k1 of one r2, so each weight it loads serves two sums
+  const int ok = __syncthreads_and(mbar_wait_bounded(bar, *phase) ? 1 : 0);
+  *phase ^= 1u;
+  if (!ok) {
+    if (threadIdx.x == 0) atomicOr(flag, TWF_TIMEOUT);
+    return;
+  }
+  const int K = kB - kA;
+  // stage 1: Y[r2][k1] = sum_{k2} V2[i2][k2][r2] c[k2][k1], two columns per thread
   const int K2 = (K + 1) >> 1;
   for (int idx = threadIdx.x; idx < W * K2; idx += blockDim.x) {
     const int r2 = idx / K2, kk = 2 * (idx - r2 * K2);
     const bool two = kk + 1 < K;
     const int lo = cr2[r2] & 0xffff, hi = cr2[r2] >> 16;
-    const float2 *cc = Cf + (size_t)(qb2 + lo) * A.nq + kA + kk;
+    const ET *cc = slab + (size_t)lo * Kp + off + kk;
     float sh0 = 0.f, sl0 = 0.f, sh1 = 0.f, sl1 = 0.f;
-    for (int c2 = lo; c2 < hi; c2++, cc += A.nq) {
-      const float2 vv = V2s[c2 * W + r2];
-      const float2 c0 = cc[0];
-      const float2 c1 = two ? cc[1] : make_float2(0.f, 0.f);
-      if (SPLIT) {
+    for (int c2 = lo; c2 < hi; c2++, cc += Kp) {
+      const ET vv = V2s[c2 * W + r2];
+      const ET c0 = cc[0];
+      if constexpr (SPLIT) {
+        const float2 c1 = two ? cc[1] : make_float2(0.f, 0.f);
         df_fma(vv, c0, sh0, sl0);
         df_fma(vv, c1, sh1, sl1);
       } else {
-        sh0 = fmaf(vv.x, c0.x, sh0);
-        sh1 = fmaf(vv.x, c1.x, sh1);
+        const float c1 = two ? cc[1] : 0.f;
+        sh0 = fmaf(vv, c0, sh0);
+        sh1 = fmaf(vv, c1, sh1);
       }
     }
-    Y[r2 * KMAX + kk] = make_float2(sh0, sl0);
-    if (two) Y[r2 * KMAX + kk + 1] = make_float2(sh1, sl1);
+    if constexpr (SPLIT) {
+      Y[r2 * KMAX + kk] = make_float2(sh0, sl0);
+      if (two) Y[r2 * KMAX + kk + 1] = make_float2(sh1, sl1);
+    } else {
+      Y[r2 * KMAX + kk] = sh0;
+      if (two) Y[r2 * KMAX + kk + 1] = sh1;
+    }
   }
   __syncthreads();
-  // stage 2 (point-major for rows away from the end elements) into the
-  // tile's output buffer os[t][r2][r1].  In FP32 a thread owns two
-  // neighbouring r2 of one row, so each weighted basis value it loads serves
-  // two outputs; the split form keeps one r2 per thread (its register
-  // footprint would otherwise halve the occupancy)
+  // the tile's CSR range (full tiles): base position and the alignment shift
+  // that puts 16-byte units of the range on 16-byte units of shared memory
+  int64_t base = 0;
+  int sho = 0, shc = 0;
+  if (full) {
+    base = rp[act[i2 * n1 + i1a]];
+    sho = (int)(base & (AO - 1));
+    shc = (int)(base & 3);
+  }
+  // stage 2 (point-major for rows away from the end elements, from vcs) into
+  // os: full tiles at CSR position (t W + r2) W + r1 (+ shift), others at
+  // [t][r2][r1].  In FP32 a thread owns two neighbouring r2 of one row
   constexpr int NRP = SPLIT ? 1 : 2;
   constexpr int WH = (W + NRP - 1) / NRP;
-  const int NR = (i1b - i1a) * WH;
-  for (int idx = threadIdx.x; idx < NR; idx += blockDim.x) {
+  OutT *os = osb + (full ? sho : 0);
+  for (int idx = threadIdx.x; idx < nr * WH; idx += blockDim.x) {
     const int t = idx / WH, r2a = NRP * (idx - t * WH), r2b = r2a + 1;
     const int i1 = i1a + t;
     const int g = i2 * n1 + i1;
@@ -560,12 +658,12 @@ __device__ void interior_tile32(const Dir &A, const Dir &B, const float2 *__rest
     const bool vb = NRP == 2 && r2b < W && j2b >= 0 && j2b < B.n;
     if (!va && !vb) continue;
     const int yo = A.qbeg[i1] - kA;
-    const float2 *ya = Y + r2a * KMAX + yo;
-    const float2 *yb = Y + (vb ? r2b : r2a) * KMAX + yo;
-    const float2 *v = V1f + ((size_t)i1 * A.qmax) * W;
+    const ET *ya = Y + r2a * KMAX + yo;
+    const ET *yb = Y + (vb ? r2b : r2a) * KMAX + yo;
     OutT *oa = os + ((size_t)t * W + r2a) * W;
     OutT *ob = oa + W;
     if (i1 >= P + 1 && i1 <= A.nel - 2) {
+      const ET *v = vcs + (size_t)t * NV;
       float aha[W], ala[W], ahb[W], alb[W];
 #pragma unroll
       for (int r = 0; r < W; r++) aha[r] = ala[r] = ahb[r] = alb[r] = 0.f;
@@ -574,48 +672,47 @@ __device__ void interior_tile32(const Dir &A, const Dir &B, const float2 *__rest
 #pragma unroll
         for (int pt = 0; pt < 2; pt++) {
           const int c1 = 2 * el + pt;
-          const float2 yva = ya[c1], yvb = yb[c1];
+          const ET yva = ya[c1], yvb = yb[c1];
 #pragma unroll
           for (int a = 0; a <= P; a++) {
-            const float2 vv = v[c1 * W + el + a];
+            const ET vv = v[c1 * (P + 1) + a];
             if constexpr (SPLIT) {
               df_fma(vv, yva, aha[el + a], ala[el + a]);
             } else {
-              aha[el + a] = fmaf(vv.x, yva.x, aha[el + a]);
-              ahb[el + a] = fmaf(vv.x, yvb.x, ahb[el + a]);
+              aha[el + a] = fmaf(vv, yva, aha[el + a]);
+              ahb[el + a] = fmaf(vv, yvb, ahb[el + a]);
             }
           }
         }
       }
 #pragma unroll
       for (int r = 0; r < W; r++) {
-        if (SPLIT) {
-          if (va) oa[r] = (double)aha[r] + (double)ala[r];
-          if (vb) ob[r] = (double)ahb[r] + (double)alb[r];
+        if constexpr (SPLIT) {
+          if (va) oa[r] = widen_f32(aha[r]) + widen_f32(ala[r]);
         } else {
           if (va) oa[r] = aha[r];
           if (vb) ob[r] = ahb[r];
         }
       }
     } else {
+      const float2 *v = tb.V1f + ((size_t)i1 * A.qmax) * W;
       for (int r1 = 0; r1 < W; r1++) {
         const int j1 = i1 - P + r1;
         if (j1 < 0 || j1 >= n1) continue;
         const int cr = A.crange[i1 * W + r1];
         const int lo = cr & 0xffff, hi = cr >> 16;
-        float sha = 0.f, sla = 0.f, shb = 0.f, slb = 0.f;
+        float sha = 0.f, sla = 0.f, shb = 0.f;
         for (int c1 = lo; c1 < hi; c1++) {
           const float2 vv = v[c1 * W + r1];
           if constexpr (SPLIT) {
             df_fma(vv, ya[c1], sha, sla);
           } else {
-            sha = fmaf(vv.x, ya[c1].x, sha);
-            shb = fmaf(vv.x, yb[c1].x, shb);
+            sha = fmaf(vv.x, ya[c1], sha);
+            shb = fmaf(vv.x, yb[c1], shb);
           }
         }
-        if (SPLIT) {
-          if (va) oa[r1] = (double)sha + (double)sla;
-          if (vb) ob[r1] = (double)shb + (double)slb;
+        if constexpr (SPLIT) {
+          if (va) oa[r1] = widen_f32(sha) + widen_f32(sla);
         } else {
           if (va) oa[r1] = sha;
           if (vb) ob[r1] = shb;
@@ -623,26 +720,42 @@ __device__ void interior_tile32(const Dir &A, const Dir &B, const float2 *__rest
       }
     }
   }
-  __syncthreads();
-  // write out: one warp per row of the tile, consecutive lanes on consecutive
-  // CSR positions (j2 major, j1 minor over the valid part of the band)
   OutT *val = (OutT *)valv;
-  const int nw = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int lo2 = max(0, i2 - P), w2 = min(B.n - 1, i2 + P) - lo2 + 1, d2 = lo2 - (i2 - P);
-  for (int t = wid; t < i1b - i1a; t += nw) {
-    const int i1 = i1a + t, g = i2 * n1 + i1;
-    if (fstate[g] != TW_FUNC_INTERIOR) continue;  // the whole warp
-    const int lo1 = max(0, i1 - P), w1 = min(n1 - 1, i1 + P) - lo1 + 1, d1 = lo1 - (i1 - P);
-    const int64_t rowbase = rp[act[g]];
-    const OutT *src = os + (size_t)t * W * W;
-    if (w1 == W && w2 == W) {  // full band: the row is the tile's W x W block
-      const int32_t *arow = act + (size_t)lo2 * n1 + lo1;
-      for (int k = lane; k < W * W; k += 32) {
-        const int q2 = k / W, q1 = k - q2 * W;
-        val[rowbase + k] = src[k];
-        col[rowbase + k] = arow[q2 * n1 + q1];
-      }
-    } else {
+  if (full) {
+    // columns of the full band, in CSR order
+    int32_t *cs = csb + shc;
+    const int L2 = nr * W * W;
+    for (int k = threadIdx.x; k < L2; k += blockDim.x) {
+      const int t = k / (W * W), q = k - t * W * W, q2 = q / W, q1 = q - q2 * W;
+      cs[k] = act[(i2 - P + q2) * n1 + (i1a + t - P + q1)];
+    }
+    fence_proxy_async_smem();
+    __syncthreads();
+    // head and tail by plain stores, the 16-byte units between by bulk copies
+    const int hv = (AO - sho) & (AO - 1), hc = (4 - shc) & 3;
+    const int mv = tb.bulk_out && L2 > hv ? (L2 - hv) / AO * AO : 0;
+    const int mc = tb.bulk_out && L2 > hc ? (L2 - hc) / 4 * 4 : 0;
+    for (int k = threadIdx.x; k < L2; k += blockDim.x) {
+      if (k < hv || k >= hv + mv) val[base + k] = os[k];
+      if (k < hc || k >= hc + mc) col[base + k] = cs[k];
+    }
+    if (threadIdx.x == 0) {
+      if (mv > 0) bulk_s2g(val + base + hv, os + hv, (uint32_t)(sizeof(OutT) * mv));
+      if (mc > 0) bulk_s2g(col + base + hc, cs + hc, (uint32_t)(sizeof(int32_t) * mc));
+      bulk_commit();
+      bulk_wait_read();  // shared memory is free for the next tile when the block moves on
+    }
+  } else {
+    __syncthreads();
+    // one warp per row, consecutive lanes on consecutive CSR positions
+    const int nw = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int lo2 = max(0, i2 - P), w2 = min(B.n - 1, i2 + P) - lo2 + 1, d2 = lo2 - (i2 - P);
+    for (int t = wid; t < nr; t += nw) {
+      const int i1 = i1a + t, g = i2 * n1 + i1;
+      if (fstate[g] != TW_FUNC_INTERIOR) continue;  // the whole warp
+      const int lo1 = max(0, i1 - P), w1 = min(n1 - 1, i1 + P) - lo1 + 1, d1 = lo1 - (i1 - P);
+      const int64_t rowbase = rp[act[g]];
+      const OutT *src = os + (size_t)t * W * W;
       for (int k = lane; k < w1 * w2; k += 32) {
         const int q2 = k / w1, q1 = k - q2 * w1;
         val[rowbase + k] = src[(q2 + d2) * W + q1 + d1];
@@ -650,7 +763,7 @@ __device__ void interior_tile32(const Dir &A, const Dir &B, const float2 *__rest
       }
     }
   }
-  __syncthreads();  // the tile's smem is reused by the next item
+  __syncthreads();  // the tile's shared memory is reused by the next item
 }
 
 }  // namespace tw

@@ -9,8 +9,11 @@
 //                   TwoSum with the rounding errors carried in a second FP32
 //                   accumulator, so the result keeps ~46 bits and is written
 //                   as FP64.
-// The tables (V of both directions, c on the WQ grid) are split once per
-// patch, on first use.  Cut rows always run in FP64 (k_cutrows).
+// The tables (V of both directions, c on the WQ grid, the band values of
+// direction 1 per point) are split once per patch, on first use; each tile
+// stages its slab of c and its rows of band values in shared memory with bulk
+// copies and, when its CSR range is contiguous, writes it with bulk copies
+// (interior_tile32).  Cut rows always run in FP64 (k_cutrows).
 #include "tw_bodies.cuh"
 
 namespace tw {
@@ -26,17 +29,43 @@ __global__ void k_split_table(const double *src, float2 *dst, int64_t n) {
   if (i < n) dst[i] = split_f64(src[i]);
 }
 
+// c rounded to float with rows padded to ld (the pad columns are zero)
+__global__ void k_round_rows(const double *src, float *dst, int n1, int n2, int ld) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)n2 * ld) return;
+  const int k2 = (int)(i / ld), k1 = (int)(i % ld);
+  dst[i] = k1 < n1 ? __double2float_rn(src[(size_t)k2 * n1 + k1]) : 0.f;
+}
+
+// Vc[i][c1][a] = V[i][c1][c1 / 2 + a], a = 0..P: the band values that can be
+// nonzero at point c1 of supp B_i when every support element holds two points
+// (rows P+1 .. nel-2); zero elsewhere and in the pad row n
+__global__ void k_band_table(Dir D, float2 *vcf, float *vch) {
+  const int P = D.p, W = 2 * P + 1, NV = (2 * P + 2) * (P + 1);
+  int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= (int64_t)(D.n + 1) * NV) return;
+  const int i = (int)(id / NV), r = (int)(id % NV), c1 = r / (P + 1), a = r % (P + 1);
+  double v = 0.0;
+  if (i >= P + 1 && i <= D.nel - 2) v = D.V[((size_t)i * D.qmax + c1) * W + c1 / 2 + a];
+  const float2 h = split_f64(v);
+  vcf[id] = h;
+  vch[id] = h.x;
+}
+
 template <int P, int T, bool SPLIT>
-__global__ void __launch_bounds__(256) k_interior32(Dir A, Dir B, const float2 *__restrict__ Cf,
-                                                    const float2 *__restrict__ V1f,
-                                                    const float2 *__restrict__ V2f,
+__global__ void __launch_bounds__(256) k_interior32(Dir A, Dir B, Tables32 tb,
                                                     const uint8_t *__restrict__ fstate,
                                                     const int32_t *__restrict__ act,
                                                     const int64_t *__restrict__ rp,
-                                                    int32_t *__restrict__ col, void *__restrict__ valv) {
-  __shared__ __align__(16) char smem[interior32_smem(P, T, SPLIT)];
-  interior_tile32<P, SPLIT>(A, B, Cf, V1f, V2f, fstate, act, rp, col, valv, blockIdx.y,
-                            blockIdx.x * T, T, smem);
+                                                    int32_t *__restrict__ col, void *__restrict__ valv,
+                                                    int *flag) {
+  extern __shared__ __align__(16) char smem[];
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) mbar_init(&bar);
+  __syncthreads();
+  uint32_t phase = 0;
+  interior_tile32<P, SPLIT>(A, B, tb, fstate, act, rp, col, valv, blockIdx.y, blockIdx.x * T, T,
+                            smem, &bar, &phase, flag);
 }
 
 // split the patch's tables on first use (patch-owned)
@@ -47,59 +76,96 @@ int ensure_split_tables(tw_patch *P, cudaStream_t s) {
   cudaStream_t keep = P->stream;
   P->stream = s;
   const int W = 2 * P->p + 1;
-  int64_t nc = (int64_t)A.nq * B.nq;
+  const int NV = (2 * P->p + 2) * (P->p + 1);
+  const int ldh = (A.nq + 3) & ~3;
+  int64_t nc = (int64_t)A.nq * B.nq, nh = (int64_t)B.nq * ldh;
   int64_t nv[2] = {(int64_t)A.n * A.qmax * W, (int64_t)B.n * B.qmax * W};
+  int64_t nb = (int64_t)(A.n + 1) * NV;
   float2 *cf = (float2 *)dalloc(P, sizeof(float2) * nc);
   float2 *v0 = (float2 *)dalloc(P, sizeof(float2) * nv[0]);
   float2 *v1 = (float2 *)dalloc(P, sizeof(float2) * nv[1]);
+  float *ch = (float *)dalloc(P, sizeof(float) * nh);
+  float2 *vcf = (float2 *)dalloc(P, sizeof(float2) * nb);
+  float *vch = (float *)dalloc(P, sizeof(float) * nb);
   P->stream = keep;
-  if (!cf || !v0 || !v1) return TW_ENOMEM;
+  if (!cf || !v0 || !v1 || !ch || !vcf || !vch) return TW_ENOMEM;
   k_split_table<<<(unsigned)((nc + 255) / 256), 256, 0, s>>>(P->C, cf, nc);
   TW_LAUNCH();
   k_split_table<<<(unsigned)((nv[0] + 255) / 256), 256, 0, s>>>(A.V, v0, nv[0]);
   TW_LAUNCH();
   k_split_table<<<(unsigned)((nv[1] + 255) / 256), 256, 0, s>>>(B.V, v1, nv[1]);
   TW_LAUNCH();
+  k_round_rows<<<(unsigned)((nh + 255) / 256), 256, 0, s>>>(P->C, ch, A.nq, B.nq, ldh);
+  TW_LAUNCH();
+  k_band_table<<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(A, vcf, vch);
+  TW_LAUNCH();
   P->Cf = cf;
   P->Vf[0] = v0;
   P->Vf[1] = v1;
+  P->Ch = ch;
+  P->ldh = ldh;
+  P->Vcf = vcf;
+  P->Vch = vch;
   return check_cuda(cudaGetLastError(), "split tables");
 }
 
-// tiles as large as the static shared memory allows for the staged outputs:
-// split (FP64 outputs) 32 rows (16 at p = 6), FP32 64 rows (32 at p = 6)
-template <int P>
-static void launch32(tw_patch *Pt, bool split, int32_t *col, void *val, cudaStream_t s) {
-  constexpr int TS = P <= 5 ? 32 : 16, TF = P <= 5 ? 64 : 32;
-  static_assert(interior32_smem(P, TS, true) <= 48 * 1024, "split tile exceeds static smem");
-  static_assert(interior32_smem(P, TF, false) <= 48 * 1024, "FP32 tile exceeds static smem");
+Tables32 tables32(const tw_patch *P, bool split, const void *col, const void *val) {
+  Tables32 tb;
+  tb.C = split ? (const void *)P->Cf : (const void *)P->Ch;
+  tb.ldc = split ? P->d[0].nq : P->ldh;
+  tb.Vc1 = split ? (const void *)P->Vcf : (const void *)P->Vch;
+  tb.V1f = P->Vf[0];
+  tb.V2f = P->Vf[1];
+  tb.bulk_out = ((uintptr_t)col % 16 == 0 && (uintptr_t)val % 16 == 0) ? 1 : 0;
+  return tb;
+}
+
+// tiles of 32 rows (16 at p = 6): values and columns of a tile are staged in
+// shared memory for its bulk stores
+template <int P, bool SPLIT>
+static cudaError_t launch32_t(tw_patch *Pt, int32_t *col, void *val, cudaStream_t s) {
+  constexpr int T = P <= 5 ? 32 : 16;
+  constexpr size_t smem = interior32_smem(P, T, SPLIT);
+  static_assert(smem <= 200 * 1024, "FP32-pipe tile exceeds shared memory");
+  cudaError_t e = cudaFuncSetAttribute(k_interior32<P, T, SPLIT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
   Dir &A = Pt->d[0];
   Dir &B = Pt->d[1];
-  if (split)
-    k_interior32<P, TS, true><<<dim3((A.n + TS - 1) / TS, B.n), 256, 0, s>>>(
-        A, B, Pt->Cf, Pt->Vf[0], Pt->Vf[1], Pt->fstate, Pt->act, Pt->row_ptr, col, val);
-  else
-    k_interior32<P, TF, false><<<dim3((A.n + TF - 1) / TF, B.n), 256, 0, s>>>(
-        A, B, Pt->Cf, Pt->Vf[0], Pt->Vf[1], Pt->fstate, Pt->act, Pt->row_ptr, col, val);
+  k_interior32<P, T, SPLIT><<<dim3((A.n + T - 1) / T, B.n), 256, smem, s>>>(
+      A, B, tables32(Pt, SPLIT, col, val), Pt->fstate, Pt->act, Pt->row_ptr, col, val, Pt->flag);
+  return cudaSuccess;
+}
+
+template <int P>
+static cudaError_t launch32(tw_patch *Pt, bool split, int32_t *col, void *val, cudaStream_t s) {
+  return split ? launch32_t<P, true>(Pt, col, val, s) : launch32_t<P, false>(Pt, col, val, s);
 }
 
 int launch_interior32(tw_patch *P, int precision, int32_t *col, void *val, cudaStream_t s) {
   int rc = ensure_split_tables(P, s);
   if (rc) return rc;
   if (P->n_interior == 0) return 0;
+  if (P->d[0].qmax > 4 * P->p || P->d[1].qmax > 4 * P->p) {
+    set_error("interior contraction: %d / %d WQ points in one support exceed 4p", P->d[0].qmax,
+              P->d[1].qmax);
+    return TW_EUNSUPPORTED;
+  }
   bool split = precision == TW_PREC_FP32X2;
   int ps = prof_start(s);
+  cudaError_t e = cudaErrorInvalidValue;
   switch (P->p) {
-    case 1: launch32<1>(P, split, col, val, s); break;
-    case 2: launch32<2>(P, split, col, val, s); break;
-    case 3: launch32<3>(P, split, col, val, s); break;
-    case 4: launch32<4>(P, split, col, val, s); break;
-    case 5: launch32<5>(P, split, col, val, s); break;
-    case 6: launch32<6>(P, split, col, val, s); break;
+    case 1: e = launch32<1>(P, split, col, val, s); break;
+    case 2: e = launch32<2>(P, split, col, val, s); break;
+    case 3: e = launch32<3>(P, split, col, val, s); break;
+    case 4: e = launch32<4>(P, split, col, val, s); break;
+    case 5: e = launch32<5>(P, split, col, val, s); break;
+    case 6: e = launch32<6>(P, split, col, val, s); break;
     default: return TW_EUNSUPPORTED;
   }
   prof_stop(ps, TW_STAGE_INTERIOR, s);
   TW_LAUNCH();
+  if (e != cudaSuccess) return check_cuda(e, "interior contraction (FP32 pipes): attributes");
   return check_cuda(cudaGetLastError(), "interior contraction (FP32 pipes)");
 }
 

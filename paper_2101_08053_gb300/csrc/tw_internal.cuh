@@ -36,6 +36,7 @@
 #define TWF_QMAX 8
 #define TWF_LQMAX 16
 #define TWF_RULECAP 32
+#define TWF_TIMEOUT 64  // a bounded wait on a bulk copy ran out
 
 namespace tw {
 
@@ -742,6 +743,10 @@ struct tw_patch {
   double *gmat;      // ngslot x (p+1)^4 element matrices of the Gauss elements (or NULL)
   float2 *Cf;        // c on the WQ grid as hi/lo FP32 pairs (created on first FP32 form)
   float2 *Vf[2];     // weighted basis tables as hi/lo FP32 pairs
+  float *Ch;         // c rounded to float, rows padded to ldh (a multiple of 4)
+  int ldh;
+  float2 *Vcf;       // direction-1 band values per (function, point) as pairs ((n1+1) rows)
+  float *Vch;        // the same rounded to float
   int ndwqrows;
   // scratch
   int32_t *flag;     // error flags (device)
