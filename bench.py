@@ -420,6 +420,7 @@ def run_ours(args, rank, world, local_rank):
     # elements per direction, ellipse or 8-point spline holes; tables built on
     # the streams, then every matrix formed by one persistent launch replayed
     # from a CUDA graph (tiles by the autotuner), FP64 and FP32
+    remark1 = None if args.no_remark1 else run_remark1(api, torch, args, stream, flush)
     batched = None
     if not args.no_batched:
         batched = run_batched(api, torch, args, stream, streams, dev)
@@ -453,6 +454,7 @@ def run_ours(args, rank, world, local_rank):
         "value": value, "ms": ms, "nnz_step": nnz_step, "infos": infos, "launches": launches,
         "clocks": clocks, "e2e_ms": e2e_ms, "h2d": h2d, "d2h": d2h, "stage_ms": stage_ms,
         "stage_ms_batched": stage_ms_batched, "modes": modes, "batched": batched,
+        "remark1": remark1,
         "adjoint": adjoint, "precision": precision, "extension": extension,
         "roofline": {"bound": "alu", "kernel": "k_interior (interior rows, WQ + sum factorisation)",
                      "achieved": round(achieved, 4), "peak": peak, "unit": "TFLOP/s",
@@ -543,6 +545,49 @@ def run_batched(api, torch, args, stream, streams, dev):
     for P in patches:
         P.close()
     return res
+
+
+def run_remark1(api, torch, args, stream, flush):
+    """The cut rows' Gauss part two ways, config-2 geometry and hole at 512^2,
+    hybrid Gauss, p = 3..6: element matrices of the regular elements near the
+    curve (formed in set-up) gathered by the cut rows, against Remark 1's
+    row-level sum factorisation (Sect. 3.2).  Device times from the stage
+    profiler (events on the launching stream), L2 flushed before each pass."""
+    out = {}
+    for p in (3, 4, 5, 6):
+        spec = synth.config2(p=p, nel=512, method="hybrid")
+        api.profile_enable(True)
+        for st in api.STAGES:
+            api.profile_read(st)
+        gm, cr_e, cr_s = [], [], []
+        P = None
+        for rep in range(max(2, args.steps)):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            if P is not None:
+                P.close()
+            P = api.Patch(spec)
+            torch.cuda.synchronize()
+            gm.append(api.profile_read("gaussmat")[0])
+            api.profile_read("setup")
+            csr = P.alloc_csr("fp64")
+            for rowsf, acc in ((False, cr_e), (True, cr_s)):
+                flush.fill_(1.0)
+                torch.cuda.synchronize()
+                api.profile_read("cutrows")
+                P.form_mass("fp64", out=csr, rowsf=rowsf)
+                torch.cuda.synchronize()
+                acc.append(api.profile_read("cutrows")[0])
+            api.profile_read("interior")
+        api.profile_enable(False)
+        e_ms = float(np.mean(gm[1:])) + float(np.mean(cr_e[1:]))
+        s_ms = float(np.mean(cr_s[1:]))
+        out["p%d" % p] = {"cut_rows": P.n_cut_fns, "element_matrices_ms": round(float(np.mean(gm[1:])), 4),
+                          "gather_ms": round(float(np.mean(cr_e[1:])), 4),
+                          "element_form_ms": round(e_ms, 4), "remark1_ms": round(s_ms, 4),
+                          "remark1_over_element": round(s_ms / e_ms, 3)}
+        P.close()
+    return out
 
 
 def run_precision(api, torch, args, stream, flush):
@@ -817,6 +862,8 @@ def main():
                     help="skip the 1024^2 precision-variant section")
     ap.add_argument("--no-extension", action="store_true",
                     help="skip the extended B-spline section")
+    ap.add_argument("--no-remark1", action="store_true",
+                    help="skip the comparison of the cut rows' two Gauss forms")
     args = ap.parse_args()
     if args.case:
         select_case(args.case)
@@ -882,7 +929,8 @@ def main():
                 "stage_ms_per_step_batched": r["stage_ms_batched"],
                 "precision_modes_formation_only": r["modes"],
                 "batched_config4": r["batched"], "adjoint_config5": r["adjoint"],
-                "precision_config3": r["precision"], "extension_config2": r["extension"]}
+                "precision_config3": r["precision"], "extension_config2": r["extension"],
+                "remark1_config2": r["remark1"]}
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()

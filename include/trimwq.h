@@ -156,6 +156,18 @@ int tw_patch_info(const tw_patch *patch, int64_t *info16);
 int tw_form_mass(tw_patch *patch, int precision, int64_t *row_ptr, int32_t *col, void *val,
                  void *stream);
 
+/* The same CSR as tw_form_mass, with the Gauss part of every cut row that has
+ * no region part (hybrid Gauss rows, Gauss-method rows, DWQ rows without a
+ * region) formed by the row-level sum factorisation of Sect. 3.2, Remark 1:
+ * one tensor rule of element Gauss points (p+1 per direction) over the whole
+ * support with the coefficient c set to zero off the regular elements,
+ * contracted direction by direction as in Eq. 7; cut elements are added from
+ * their element matrices.  The values equal tw_form_mass's to rounding (the
+ * same quadrature summed in another order); the element matrices of the
+ * regular elements are not read.  Asynchronous on `stream`. */
+int tw_form_mass_rowsf(tw_patch *patch, int precision, int64_t *row_ptr, int32_t *col, void *val,
+                       void *stream);
+
 /* Right-hand side b[n_rows] of the L2 projection: each row's own quadrature
  * rule applied to f * c (Sect. 4.2).  Device output, asynchronous. */
 int tw_rhs(tw_patch *patch, const tw_func *f, double *b, void *stream);
@@ -411,7 +423,9 @@ int tw_pool_info(int64_t *info3);
 #define TW_STAGE_LOSS 5      /* tw_loss                                       */
 #define TW_STAGE_ADJOINT 6   /* tw_l2_project_adjoint's gradient kernels (its  
                                 CG counts as TW_STAGE_CG)                     */
-#define TW_NSTAGES 7
+#define TW_STAGE_GAUSSMAT 7  /* inside tw_patch_create: the element matrices of
+                                the regular elements near the curve           */
+#define TW_NSTAGES 8
 int tw_profile_enable(int on);
 int tw_profile_read(int stage, double *total_ms, int64_t *count);
 

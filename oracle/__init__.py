@@ -139,6 +139,7 @@ def _declare(L):
         L.or_dwq_choice.argtypes = [C.c_void_p, C.c_int, C.c_int, PI32]
         L.or_form.argtypes = [C.c_void_p, PI64, PI32, PD]
         L.or_form_row.argtypes = [C.c_void_p, C.c_int64, PI32, PD]
+        L.or_form_row_remark1.argtypes = [C.c_void_p, C.c_int64, PI32, PD]
         L.or_rhs.argtypes = [C.c_void_p, C.POINTER(Func), PD]
         L.or_row_points.argtypes = [C.c_void_p, C.c_int64, PD, C.c_int]
         L.or_cg.argtypes = [C.c_void_p, PI64, PI32, PD, PD, PD, C.c_double, C.c_int, PD]
@@ -373,6 +374,17 @@ class Patch:
         val = np.zeros(max(self.nnz, 1), dtype=np.float64)
         self._L.or_form(self._h, rp.ctypes.data_as(PI64), col.ctypes.data_as(PI32), _pd(val))
         return rp, col[:self.nnz], val[:self.nnz]
+
+    def form_row_remark1(self, r):
+        """Row r with its Gauss part as Remark 1's masked tensor rule over the
+        whole support; None for a row with a region part."""
+        cap = (2 * self.p + 1) ** 2
+        col = np.zeros(cap, dtype=np.int32)
+        val = np.zeros(cap)
+        n = self._L.or_form_row_remark1(self._h, int(r), col.ctypes.data_as(PI32), _pd(val))
+        if n < 0:
+            return None
+        return col[:n].copy(), val[:n].copy()
 
     def form_rows(self, rows):
         """Entries of the rows `rows` (in C, in parallel with the all-cores

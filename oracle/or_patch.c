@@ -934,6 +934,62 @@ int or_form_row(const or_patch *Pc, int64_t row, int32_t *col, double *val) {
   return n;
 }
 
+/* Remark 1 of Sect. 3.2: the Gauss part of a cut row written as one tensor rule
+ * over the whole support, the element Gauss points of every support element
+ * with the coefficient c set to zero at the points outside S^r (the regular
+ * elements); the cut elements keep their cut rule.  For rows without a region
+ * part (hybrid Gauss rows, Gauss-method rows, DWQ rows without a region) the
+ * result is the row of or_form_row summed in another order.  Returns the
+ * number of entries, or -1 for a row with a region part. */
+int or_form_row_remark1(const or_patch *Pc, int64_t row, int32_t *col, double *val) {
+  or_patch *P = (or_patch *)Pc;
+  const dirdata *A = &P->D[0], *B = &P->D[1];
+  int g = (int)P->rowg[row];
+  int kind = row_kind(P, g);
+  if (kind != ROW_GAUSS) return -1;
+  int i1 = g % A->n, i2 = g / A->n;
+  int lo1 = i1 - A->p < 0 ? 0 : i1 - A->p, hi1 = i1 < A->nel - 1 ? i1 : A->nel - 1;
+  int lo2 = i2 - B->p < 0 ? 0 : i2 - B->p, hi2 = i2 < B->nel - 1 ? i2 : B->nel - 1;
+  int p1 = A->p + 1, p2 = B->p + 1;
+  rbuf R = {0};
+  for (int e2 = lo2; e2 <= hi2; e2++)
+    for (int e1 = lo1; e1 <= hi1; e1++) {
+      const int reg = P->estate[e2 * A->nel + e1] == OR_ELEM_REGULAR;
+      const double *c = reg ? gauss_c(P, e1, e2) : NULL;
+      double h1 = A->bp[e1 + 1] - A->bp[e1], h2 = B->bp[e2 + 1] - B->bp[e2];
+      for (int g2 = 0; g2 < p2; g2++)
+        for (int g1 = 0; g1 < p1; g1++) {
+          const double *v1 = A->GBv + ((size_t)e1 * p1 + g1) * p1;
+          const double *v2 = B->GBv + ((size_t)e2 * p2 + g2) * p2;
+          rpoint *r = rnew(&R);
+          r->x[0] = A->bp[e1] + h1 * 0.5 * (A->gx[g1] + 1.0);
+          r->x[1] = B->bp[e2] + h2 * 0.5 * (B->gx[g2] + 1.0);
+          r->e[0] = e1;
+          r->e[1] = e2;
+          for (int a = 0; a < p1; a++) r->bv[0][a] = v1[a];
+          for (int b = 0; b < p2; b++) r->bv[1][b] = v2[b];
+          double w = A->gw[g1] * 0.5 * h1 * B->gw[g2] * 0.5 * h2 * v1[i1 - e1] * v2[i2 - e2];
+          r->wc = reg ? w * c[g2 * p1 + g1] : 0.0; /* c set to zero off S^r */
+          r->w = reg ? w : 0.0;
+        }
+    }
+  for (int e2 = lo2; e2 <= hi2; e2++)
+    for (int e1 = lo1; e1 <= hi1; e1++)
+      if (P->estate[e2 * A->nel + e1] == OR_ELEM_CUT) add_cut_elem(P, i1, i2, e1, e2, &R);
+  int n = 0;
+  for (int j2 = i2 - B->p; j2 <= i2 + B->p; j2++)
+    for (int j1 = i1 - A->p; j1 <= i1 + A->p; j1++) {
+      if (j1 < 0 || j2 < 0 || j1 >= A->n || j2 >= B->n) continue;
+      int32_t a = P->act[j2 * A->n + j1];
+      if (a < 0) continue;
+      if (col) col[n] = a;
+      if (val) val[n] = rule_apply(&R, A->p, B->p, j1, j2);
+      n++;
+    }
+  free(R.v);
+  return n;
+}
+
 /* Rows rows[0..n) of the matrix, row k's values at val + k * (2p+1)^2 and its
  * entry count in cnt[k].  The rows are independent: with OpenMP (the oracle's
  * all-cores build) they are formed in parallel.  The lazily filled table of c

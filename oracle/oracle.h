@@ -134,6 +134,7 @@ int or_dwq_rule(const or_patch *P, int dir, int s, int side, int i, double *pts,
 int or_dwq_choice(const or_patch *P, int i1, int i2, int *out /* 4 */);
 void or_form(const or_patch *P, int64_t *row_ptr, int32_t *col, double *val);
 int or_form_row(const or_patch *P, int64_t row, int32_t *col, double *val);
+int or_form_row_remark1(const or_patch *P, int64_t row, int32_t *col, double *val);
 void or_form_rows(const or_patch *P, const int64_t *rows, int64_t n, double *val, int *cnt);
 int or_threads(void);
 void or_rhs(const or_patch *P, const or_func *f, double *b);

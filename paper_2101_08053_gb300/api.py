@@ -97,6 +97,7 @@ def load(build: bool = True):
     L.tw_patch_destroy.argtypes = [vp]
     L.tw_patch_info.argtypes = [vp, i64p]
     L.tw_form_mass.argtypes = [vp, C.c_int, vp, vp, vp, vp]
+    L.tw_form_mass_rowsf.argtypes = [vp, C.c_int, vp, vp, vp, vp]
     L.tw_rhs.argtypes = [vp, C.POINTER(FuncDesc), vp, vp]
     L.tw_rhs_points.argtypes = [vp, i64p, vp, vp, vp]
     L.tw_rhs_values.argtypes = [vp, vp, vp, vp]
@@ -259,12 +260,14 @@ class Patch:
         val = torch.empty(max(self.nnz, 1), dtype=dt, device="cuda")
         return rp, col, val
 
-    def form_mass(self, precision="fp64", out=None, stream=None):
-        """tw_form_mass into (row_ptr, col, val) device tensors."""
+    def form_mass(self, precision="fp64", out=None, stream=None, rowsf=False):
+        """tw_form_mass (or, with rowsf, tw_form_mass_rowsf: Remark 1's row-level
+        sum factorisation of the cut rows' Gauss part) into (row_ptr, col, val)
+        device tensors."""
         rp, col, val = out if out is not None else self.alloc_csr(precision)
-        _check(load().tw_form_mass(self._h, PREC[precision], C.c_void_p(rp.data_ptr()),
-                                   C.c_void_p(col.data_ptr()), C.c_void_p(val.data_ptr()),
-                                   _stream(stream)))
+        fn = load().tw_form_mass_rowsf if rowsf else load().tw_form_mass
+        _check(fn(self._h, PREC[precision], C.c_void_p(rp.data_ptr()),
+                  C.c_void_p(col.data_ptr()), C.c_void_p(val.data_ptr()), _stream(stream)))
         return rp, col[:self.nnz], val[:self.nnz]
 
     def rhs(self, f, stream=None):
@@ -552,7 +555,8 @@ def pool_info():
     return int(out[0]), int(out[1]), int(out[2])
 
 
-STAGES = {"setup": 0, "interior": 1, "cutrows": 2, "rhs": 3, "cg": 4, "loss": 5, "adjoint": 6}
+STAGES = {"setup": 0, "interior": 1, "cutrows": 2, "rhs": 3, "cg": 4, "loss": 5, "adjoint": 6,
+          "gaussmat": 7}
 
 
 def profile_enable(on: bool = True):

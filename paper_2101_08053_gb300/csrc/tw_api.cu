@@ -479,6 +479,19 @@ extern "C" int tw_form_mass(tw_patch *P, int precision, int64_t *row_ptr, int32_
   return form_mass_launch(P, precision, row_ptr, col, val, (cudaStream_t)stream);
 }
 
+extern "C" int tw_form_mass_rowsf(tw_patch *P, int precision, int64_t *row_ptr, int32_t *col,
+                                  void *val, void *stream) {
+  if (!P || !row_ptr || (P->nnz > 0 && (!col || !val))) {
+    set_error("tw_form_mass_rowsf: NULL argument");
+    return TW_EINVAL;
+  }
+  if (precision != TW_PREC_FP64 && precision != TW_PREC_FP32 && precision != TW_PREC_FP32X2) {
+    set_error("tw_form_mass_rowsf: unknown precision %d", precision);
+    return TW_EINVAL;
+  }
+  return form_mass_launch(P, precision, row_ptr, col, val, (cudaStream_t)stream, true);
+}
+
 extern "C" int tw_states(const tw_patch *P, uint8_t *estate, uint8_t *fstate, int32_t *act,
                          void *stream) {
   if (!P) {

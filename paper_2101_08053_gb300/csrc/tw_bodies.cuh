@@ -498,7 +498,8 @@ struct Tables32 {
 //   V2s   the weighted basis of row i2
 //   os    the tile's outputs in CSR order (+ one 16-byte alignment shift)
 //   cs    their columns (+ the same)
-//   cr2   band ranges of row i2
+//   sc    the tile's scalars, the band ranges of row i2, per row the interior
+//         flag and the first WQ point
 __host__ __device__ constexpr int interior32_kmax(int P, int T) { return (2 * T + 4 * P + 4) | 1; }
 __host__ __device__ constexpr size_t a16(size_t x) { return (x + 15) / 16 * 16; }
 __host__ __device__ constexpr size_t interior32_slab_cols(int P, int T) {
@@ -519,7 +520,7 @@ __host__ __device__ constexpr Layout32 interior32_layout(int P, int T, bool spli
   L.os = L.v2 + a16(e * (size_t)Q * W);
   L.cs = L.os + a16(o * ((size_t)T * W * W + 16 / o));
   L.cr2 = L.cs + a16(sizeof(int) * ((size_t)T * W * W + 4));
-  L.total = L.cr2 + a16(sizeof(int) * (W + 2));
+  L.total = L.cr2 + a16(sizeof(int) * (8 + W + 2 * (size_t)T));
   return L;
 }
 __host__ __device__ constexpr size_t interior32_smem(int P, int T, bool split = true) {
@@ -554,31 +555,41 @@ __device__ void interior_tile32(const Dir &A, const Dir &B, const Tables32 &tb,
   ET *V2s = (ET *)(smem + L.v2);
   OutT *osb = (OutT *)(smem + L.os);
   int32_t *csb = (int32_t *)(smem + L.cs);
-  int *cr2 = (int *)(smem + L.cr2);
-  int *anyintp = cr2 + W;
-  int *fullp = cr2 + W + 1;
+  // [0] any interior [1] full [2] kA [3] kB [4] qb2 [5] qc2 [6..7] CSR base (8-byte aligned)
+  int *sc = (int *)(smem + L.cr2);
+  int *cr2 = sc + 8;
+  int *rowint = cr2 + W, *rowq = rowint + T;
   const int KMAX = interior32_kmax(P, T);
   const int i1b = min(A.n, i1a + T);
   const int nr = i1b - i1a;
   const int n1 = A.n;
+  // the tile's scalars, loaded once (the CSR base of a full tile included)
   if (threadIdx.x == 0) {
-    *anyintp = 0;
-    *fullp = (i2 >= P && i2 <= B.n - 1 - P && i1a >= P && i1b - 1 <= n1 - 1 - P) ? 1 : 0;
+    const bool range = i2 >= P && i2 <= B.n - 1 - P && i1a >= P && i1b - 1 <= n1 - 1 - P;
+    sc[0] = 0;
+    sc[1] = range ? 1 : 0;
+    sc[2] = A.qbeg[i1a];
+    sc[3] = A.qbeg[i1b - 1] + A.qcnt[i1b - 1];
+    sc[4] = B.qbeg[i2];
+    sc[5] = B.qcnt[i2];
+    const int a0 = range ? act[i2 * n1 + i1a] : -1;
+    *(int64_t *)(sc + 6) = a0 >= 0 ? rp[a0] : 0;
   }
   __syncthreads();
   for (int t = threadIdx.x; t < nr; t += blockDim.x) {
-    if (fstate[i2 * n1 + i1a + t] == TW_FUNC_INTERIOR) *anyintp = 1;
-    else *fullp = 0;
+    const bool in = fstate[i2 * n1 + i1a + t] == TW_FUNC_INTERIOR;
+    rowint[t] = in ? 1 : 0;
+    rowq[t] = A.qbeg[i1a + t];
+    if (in) sc[0] = 1;
+    else sc[1] = 0;
   }
   __syncthreads();
-  if (!*anyintp) return;  // uniform across the block
-  const bool full = *fullp != 0;
-  const int kA = A.qbeg[i1a];
-  const int kB = A.qbeg[i1b - 1] + A.qcnt[i1b - 1];
+  if (!sc[0]) return;  // uniform across the block
+  const bool full = sc[1] != 0;
+  const int kA = sc[2], kB = sc[3], qb2 = sc[4], qc2 = sc[5];
   const int kA0 = kA & ~(AE - 1);
   const int Kp = ((kB + AE - 1) & ~(AE - 1)) - kA0;  // slab row length, whole 16-byte units
   const int off = kA - kA0;
-  const int qb2 = B.qbeg[i2], qc2 = B.qcnt[i2];
   // bulk loads: qc2 slab rows and the tile's Vc1 rows (even row count)
   if (threadIdx.x == 0) {
     const int nvr = (nr + 1) & ~1;
@@ -596,7 +607,10 @@ __device__ void interior_tile32(const Dir &A, const Dir &B, const Tables32 &tb,
     else V2s[t] = V2f[t].x;
   }
   for (int t = threadIdx.x; t < W; t += blockDim.x) cr2[t] = B.crange[i2 * W + t];
-  const int ok = __syncthreads_and(mbar_wait_bounded(bar, *phase) ? 1 : 0);
+  // one thread waits for the copies (bounded); the block barrier then orders
+  // the copied data before every other thread's reads, and carries the
+  // outcome to all threads
+  const int ok = __syncthreads_and(threadIdx.x == 0 ? (mbar_wait_bounded(bar, *phase) ? 1 : 0) : 1);
   *phase ^= 1u;
   if (!ok) {
     if (threadIdx.x == 0) atomicOr(flag, TWF_TIMEOUT);
@@ -611,6 +625,7 @@ __device__ void interior_tile32(const Dir &A, const Dir &B, const Tables32 &tb,
     const int lo = cr2[r2] & 0xffff, hi = cr2[r2] >> 16;
     const ET *cc = slab + (size_t)lo * Kp + off + kk;
     float sh0 = 0.f, sl0 = 0.f, sh1 = 0.f, sl1 = 0.f;
+#pragma unroll 4
     for (int c2 = lo; c2 < hi; c2++, cc += Kp) {
       const ET vv = V2s[c2 * W + r2];
       const ET c0 = cc[0];
@@ -635,13 +650,8 @@ __device__ void interior_tile32(const Dir &A, const Dir &B, const Tables32 &tb,
   __syncthreads();
   // the tile's CSR range (full tiles): base position and the alignment shift
   // that puts 16-byte units of the range on 16-byte units of shared memory
-  int64_t base = 0;
-  int sho = 0, shc = 0;
-  if (full) {
-    base = rp[act[i2 * n1 + i1a]];
-    sho = (int)(base & (AO - 1));
-    shc = (int)(base & 3);
-  }
+  const int64_t base = full ? *(const int64_t *)(sc + 6) : 0;
+  const int sho = (int)(base & (AO - 1)), shc = (int)(base & 3);
   // stage 2 (point-major for rows away from the end elements, from vcs) into
   // os: full tiles at CSR position (t W + r2) W + r1 (+ shift), others at
   // [t][r2][r1].  In FP32 a thread owns two neighbouring r2 of one row
@@ -651,13 +661,12 @@ __device__ void interior_tile32(const Dir &A, const Dir &B, const Tables32 &tb,
   for (int idx = threadIdx.x; idx < nr * WH; idx += blockDim.x) {
     const int t = idx / WH, r2a = NRP * (idx - t * WH), r2b = r2a + 1;
     const int i1 = i1a + t;
-    const int g = i2 * n1 + i1;
-    if (fstate[g] != TW_FUNC_INTERIOR) continue;
+    if (!rowint[t]) continue;
     const int j2a = i2 - P + r2a, j2b = j2a + 1;
     const bool va = j2a >= 0 && j2a < B.n;
     const bool vb = NRP == 2 && r2b < W && j2b >= 0 && j2b < B.n;
     if (!va && !vb) continue;
-    const int yo = A.qbeg[i1] - kA;
+    const int yo = rowq[t] - kA;
     const ET *ya = Y + r2a * KMAX + yo;
     const ET *yb = Y + (vb ? r2b : r2a) * KMAX + yo;
     OutT *oa = os + ((size_t)t * W + r2a) * W;
@@ -722,12 +731,17 @@ __device__ void interior_tile32(const Dir &A, const Dir &B, const Tables32 &tb,
   }
   OutT *val = (OutT *)valv;
   if (full) {
-    // columns of the full band, in CSR order
+    // columns of the full band, in CSR order.  Every trial function of a full
+    // tile is active (it overlaps an interior function), so along one trial
+    // row j2 the active indices are consecutive: col = act(j2, i1a - P) + t + q1
     int32_t *cs = csb + shc;
     const int L2 = nr * W * W;
-    for (int k = threadIdx.x; k < L2; k += blockDim.x) {
-      const int t = k / (W * W), q = k - t * W * W, q2 = q / W, q1 = q - q2 * W;
-      cs[k] = act[(i2 - P + q2) * n1 + (i1a + t - P + q1)];
+    for (int k = threadIdx.x; k < nr * W; k += blockDim.x) {
+      const int t = k / W, q2 = k - t * W;
+      const int32_t c0 = act[(i2 - P + q2) * n1 + i1a - P] + t;
+      int32_t *dst = cs + (size_t)k * W;
+#pragma unroll
+      for (int q1 = 0; q1 < W; q1++) dst[q1] = c0 + q1;
     }
     fence_proxy_async_smem();
     __syncthreads();
@@ -735,9 +749,14 @@ __device__ void interior_tile32(const Dir &A, const Dir &B, const Tables32 &tb,
     const int hv = (AO - sho) & (AO - 1), hc = (4 - shc) & 3;
     const int mv = tb.bulk_out && L2 > hv ? (L2 - hv) / AO * AO : 0;
     const int mc = tb.bulk_out && L2 > hc ? (L2 - hc) / 4 * 4 : 0;
-    for (int k = threadIdx.x; k < L2; k += blockDim.x) {
-      if (k < hv || k >= hv + mv) val[base + k] = os[k];
-      if (k < hc || k >= hc + mc) col[base + k] = cs[k];
+    const int tv = mv > 0 ? L2 - hv - mv : L2, tc = mc > 0 ? L2 - hc - mc : L2;
+    for (int k = threadIdx.x; k < (mv > 0 ? hv + tv : L2); k += blockDim.x) {
+      const int kk = k < hv || mv == 0 ? k : k + mv;
+      val[base + kk] = os[kk];
+    }
+    for (int k = threadIdx.x; k < (mc > 0 ? hc + tc : L2); k += blockDim.x) {
+      const int kk = k < hc || mc == 0 ? k : k + mc;
+      col[base + kk] = cs[kk];
     }
     if (threadIdx.x == 0) {
       if (mv > 0) bulk_s2g(val + base + hv, os + hv, (uint32_t)(sizeof(OutT) * mv));

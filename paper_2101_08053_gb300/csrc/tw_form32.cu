@@ -52,8 +52,16 @@ __global__ void k_band_table(Dir D, float2 *vcf, float *vch) {
   vch[id] = h.x;
 }
 
+// threads of a one-patch block: one per stage-2 item of the tile (a row and
+// two neighbouring r2 in FP32, one r2 in split precision), rounded to warps,
+// so that no phase of the tile leaves a large part of the block waiting
+__host__ __device__ constexpr int interior32_threads(int P, int T, bool split) {
+  return (T * (split ? 2 * P + 1 : P + 1) + 31) / 32 * 32;
+}
+
 template <int P, int T, bool SPLIT>
-__global__ void __launch_bounds__(256) k_interior32(Dir A, Dir B, Tables32 tb,
+__global__ void __launch_bounds__(interior32_threads(P, T, SPLIT))
+    k_interior32(Dir A, Dir B, Tables32 tb,
                                                     const uint8_t *__restrict__ fstate,
                                                     const int32_t *__restrict__ act,
                                                     const int64_t *__restrict__ rp,
@@ -120,11 +128,12 @@ Tables32 tables32(const tw_patch *P, bool split, const void *col, const void *va
   return tb;
 }
 
-// tiles of 32 rows (16 at p = 6): values and columns of a tile are staged in
-// shared memory for its bulk stores
+// tiles of 32 rows for FP32 and 16 for split precision (half of that at
+// p = 6): values and columns of a tile are staged in shared memory for its
+// bulk stores, and these heights keep 6 blocks resident per SM
 template <int P, bool SPLIT>
 static cudaError_t launch32_t(tw_patch *Pt, int32_t *col, void *val, cudaStream_t s) {
-  constexpr int T = P <= 5 ? 32 : 16;
+  constexpr int T = (SPLIT ? 16 : 32) / (P <= 5 ? 1 : 2);
   constexpr size_t smem = interior32_smem(P, T, SPLIT);
   static_assert(smem <= 200 * 1024, "FP32-pipe tile exceeds shared memory");
   cudaError_t e = cudaFuncSetAttribute(k_interior32<P, T, SPLIT>,
@@ -132,7 +141,8 @@ static cudaError_t launch32_t(tw_patch *Pt, int32_t *col, void *val, cudaStream_
   if (e != cudaSuccess) return e;
   Dir &A = Pt->d[0];
   Dir &B = Pt->d[1];
-  k_interior32<P, T, SPLIT><<<dim3((A.n + T - 1) / T, B.n), 256, smem, s>>>(
+  k_interior32<P, T, SPLIT><<<dim3((A.n + T - 1) / T, B.n), interior32_threads(P, T, SPLIT), smem,
+                              s>>>(
       A, B, tables32(Pt, SPLIT, col, val), Pt->fstate, Pt->act, Pt->row_ptr, col, val, Pt->flag);
   return cudaSuccess;
 }

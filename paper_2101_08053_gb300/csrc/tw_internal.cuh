@@ -785,7 +785,7 @@ int build_tables(tw_patch *P);
 // computed once per process and device and kept until exit
 int gauss_rule(int q, cudaStream_t s, const double **out);
 int form_mass_launch(tw_patch *P, int precision, int64_t *row_ptr, int32_t *col, void *val,
-                     cudaStream_t s);
+                     cudaStream_t s, bool rowsf = false);
 int launch_interior32(tw_patch *P, int precision, int32_t *col, void *val, cudaStream_t s);
 int rhs_launch(tw_patch *P, const tw_func *f, double *b, cudaStream_t s);
 int rhs_points_run(tw_patch *P, int64_t *npts, double *xi, double *X, cudaStream_t s);

@@ -1387,7 +1387,13 @@ __global__ void __launch_bounds__(256) k_gauss_matrices(Dir A, Dir B, const int3
   }
 }
 
+static void launch_gauss_matrices_impl(tw_patch *P, const int32_t *glist, cudaStream_t st);
 static void launch_gauss_matrices(tw_patch *P, const int32_t *glist, cudaStream_t st) {
+  int ps = prof_start(st);
+  launch_gauss_matrices_impl(P, glist, st);
+  prof_stop(ps, TW_STAGE_GAUSSMAT, st);
+}
+static void launch_gauss_matrices_impl(tw_patch *P, const int32_t *glist, cudaStream_t st) {
   switch (P->p) {
 #define TW_GM(PP) case PP: k_gauss_matrices<PP><<<P->ngslot, 256, 0, st>>>(P->d[0], P->d[1], glist, P->ngslot, P->gc, P->fstate, P->method, P->gmat); break;
     TW_GM(1) TW_GM(2) TW_GM(3) TW_GM(4) TW_GM(5) TW_GM(6)

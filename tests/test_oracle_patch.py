@@ -448,3 +448,34 @@ def test_row_points_carry_the_rhs_rule(method):
     x1, x2 = P.wq_grid(0), P.wq_grid(1)
     assert set(np.round(q[:, 0], 15)) <= set(np.round(x1, 15))
     assert set(np.round(q[:, 1], 15)) <= set(np.round(x2, 15))
+
+
+@pytest.mark.parametrize("method,geom", [("hybrid", "identity"), ("hybrid", "spline"),
+                                         ("gauss", "spline"), ("dwq", "spline")])
+def test_remark1_rows_equal_element_gauss_rows(method, geom):
+    """Remark 1 of Sect. 3.2: the Gauss part of a cut row as one tensor rule over
+    the whole support with c set to zero off the regular elements is the same
+    quadrature as element Gauss on the regular elements, so every row without a
+    region part equals or_form_row to rounding (c = 1 and c = det J)."""
+    rng = np.random.default_rng(21)
+    p, nel = 3, 12
+    g = ({"kind": "spline", "ctrl": synth.perturbed_bilinear_net(rng, p, nel)}
+         if geom == "spline" else None)
+    spec = synth.make_spec(p, nel, synth.bspline_curve(rng, nc=12, radius=0.3, jitter=0.05),
+                           geom=g, coef={"kind": "detj" if g else "one"}, method=method)
+    P = oracle.Patch(spec)
+    es, fs, act = P.states()
+    rows = [int(act[g_]) for g_ in np.where(fs == 2)[0]]
+    if method == "gauss":
+        rows = list(range(P.n_rows))
+    nchecked = 0
+    for r in rows:
+        res = P.form_row_remark1(r)
+        if res is None:  # a DWQ row with a region part
+            continue
+        c1, v1 = res
+        c0, v0 = P.form_row(r)
+        assert np.array_equal(c0, c1)
+        assert np.max(np.abs(v1 - v0)) <= 1e-15 * max(1.0, np.max(np.abs(v0)) * 10), r
+        nchecked += 1
+    assert nchecked > 0
