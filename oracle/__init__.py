@@ -55,6 +55,16 @@ def build(force: bool = False) -> str:
     return LIB
 
 
+class Trim(C.Structure):
+    _fields_ = [
+        ("kind", C.c_int),
+        ("keep_inside", C.c_int),
+        ("params", C.c_double * 6),
+        ("nctrl", C.c_int),
+        ("ctrl", C.POINTER(C.c_double)),
+    ]
+
+
 class Desc(C.Structure):
     _fields_ = [
         ("p", C.c_int * 2),
@@ -74,6 +84,8 @@ class Desc(C.Structure):
         ("dens_coef", C.POINTER(C.c_double)),
         ("method", C.c_int),
         ("cut_order", C.c_int),
+        ("trim_nextra", C.c_int),
+        ("trim_extra", C.POINTER(Trim)),
     ]
 
 
@@ -205,6 +217,23 @@ def make_desc(spec, keep):
         d.dens_coef = _pd(dc)
     d.method = METHOD[spec["method"]]
     d.cut_order = spec.get("cut_order", 0)
+    extra = spec.get("extra_trims", [])
+    if extra:
+        arr = (Trim * len(extra))()
+        for k, t in enumerate(extra):
+            arr[k].kind = TRIM[t["kind"]]
+            arr[k].keep_inside = int(bool(t.get("keep_inside", False)))
+            prm = list(t.get("params", [])) + [0.0] * 6
+            for m in range(6):
+                arr[k].params[m] = prm[m]
+            if t.get("ctrl") is not None:
+                ctrl = _f64(t["ctrl"])
+                keep.append(ctrl)
+                arr[k].nctrl = ctrl.shape[0]
+                arr[k].ctrl = _pd(ctrl)
+        keep.append(arr)
+        d.trim_nextra = len(extra)
+        d.trim_extra = C.cast(arr, C.POINTER(Trim))
     return d
 
 

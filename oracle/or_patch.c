@@ -75,8 +75,10 @@ typedef struct {
 
 struct or_patch {
   or_desc d;
+  int ncurves;            /* trimming curves: cd[k] is the descriptor with curve k */
+  or_desc cd[OR_MAXCURVES];
   dirdata D[2];
-  double *own[16];
+  double *own[32];
   int nown;
   uint8_t *estate, *fstate;
   int32_t *act;
@@ -188,10 +190,43 @@ static void phys_from(const or_patch *P, double x1, double x2, int e1, const dou
     }
 }
 
+/* the visible domain is the intersection of every curve's kept side */
 static int visible(const or_patch *P, double x, double y) {
-  if (P->d.trim_kind == OR_TRIM_NONE) return 1;
-  int in = or_curve_inside(&P->d, x, y);
-  return P->d.trim_keep_inside ? in : !in;
+  for (int k = 0; k < P->ncurves; k++) {
+    const or_desc *c = &P->cd[k];
+    if (c->trim_kind == OR_TRIM_NONE) continue;
+    int in = or_curve_inside(c, x, y);
+    if (c->trim_keep_inside ? !in : in) return 0;
+  }
+  return 1;
+}
+
+static int cmpd(const void *a, const void *b);
+
+/* crossings of every curve with the line xi_o = s inside (lo, hi), ascending */
+static int set_line_hits(const or_patch *P, int o, double s, double lo, double hi, double *out,
+                         int cap) {
+  int n = 0;
+  for (int k = 0; k < P->ncurves; k++) {
+    if (P->cd[k].trim_kind == OR_TRIM_NONE) continue;
+    n += or_curve_line_hits(&P->cd[k], o, s, lo, hi, out + n, cap - n);
+  }
+  qsort(out, (size_t)n, sizeof(double), cmpd);
+  return n;
+}
+
+static int set_folds(const or_patch *P, int o, double *pts, int cap) {
+  int n = 0;
+  for (int k = 0; k < P->ncurves; k++)
+    if (P->cd[k].trim_kind != OR_TRIM_NONE) n += or_curve_folds(&P->cd[k], o, pts + 2 * n, cap - n);
+  return n;
+}
+
+static int set_joints(const or_patch *P, double *pts, int cap) {
+  int n = 0;
+  for (int k = 0; k < P->ncurves; k++)
+    if (P->cd[k].trim_kind != OR_TRIM_NONE) n += or_curve_joints(&P->cd[k], pts + 2 * n, cap - n);
+  return n;
 }
 
 /* ------------------------------------------------------------------ */
@@ -274,7 +309,7 @@ static void classify(or_patch *P) {
   dirdata *A = &P->D[0], *B = &P->D[1];
   int ne = A->nel * B->nel;
   P->estate = (uint8_t *)malloc((size_t)ne);
-  if (P->d.trim_kind == OR_TRIM_NONE) {
+  if (P->ncurves == 1 && P->d.trim_kind == OR_TRIM_NONE) {
     memset(P->estate, OR_ELEM_REGULAR, (size_t)ne);
   } else {
     /* crossings of the curve with every knot line */
@@ -283,11 +318,11 @@ static void classify(or_patch *P) {
     double *hh = (double *)malloc(sizeof(double) * (size_t)(B->nel + 1) * HITCAP);
     int *hn = (int *)malloc(sizeof(int) * (size_t)(B->nel + 1));
     for (int e = 0; e <= A->nel; e++)
-      vn[e] = or_curve_line_hits(&P->d, 0, A->bp[e], -1e300, 1e300, vh + (size_t)e * HITCAP, HITCAP);
+      vn[e] = set_line_hits(P, 0, A->bp[e], -1e300, 1e300, vh + (size_t)e * HITCAP, HITCAP);
     for (int e = 0; e <= B->nel; e++)
-      hn[e] = or_curve_line_hits(&P->d, 1, B->bp[e], -1e300, 1e300, hh + (size_t)e * HITCAP, HITCAP);
-    double p0[2];
-    or_curve_point0(&P->d, p0);
+      hn[e] = set_line_hits(P, 1, B->bp[e], -1e300, 1e300, hh + (size_t)e * HITCAP, HITCAP);
+    double p0[OR_MAXCURVES][2];
+    for (int k = 0; k < P->ncurves; k++) or_curve_point0(&P->cd[k], p0[k]);
     for (int e2 = 0; e2 < B->nel; e2++)
       for (int e1 = 0; e1 < A->nel; e1++) {
         double a1 = A->bp[e1], b1 = A->bp[e1 + 1], a2 = B->bp[e2], b2 = B->bp[e2 + 1];
@@ -297,8 +332,10 @@ static void classify(or_patch *P) {
         int cut = any_in(vh + (size_t)e1 * HITCAP, vn[e1], a2 + d2, b2 - d2) ||
                   any_in(vh + (size_t)(e1 + 1) * HITCAP, vn[e1 + 1], a2 + d2, b2 - d2) ||
                   any_in(hh + (size_t)e2 * HITCAP, hn[e2], a1 + d1, b1 - d1) ||
-                  any_in(hh + (size_t)(e2 + 1) * HITCAP, hn[e2 + 1], a1 + d1, b1 - d1) ||
-                  (p0[0] > a1 && p0[0] < b1 && p0[1] > a2 && p0[1] < b2);
+                  any_in(hh + (size_t)(e2 + 1) * HITCAP, hn[e2 + 1], a1 + d1, b1 - d1);
+        /* a whole curve inside the element */
+        for (int k = 0; k < P->ncurves && !cut; k++)
+          cut = p0[k][0] > a1 && p0[k][0] < b1 && p0[k][1] > a2 && p0[k][1] < b2;
         uint8_t st;
         if (cut) st = OR_ELEM_CUT;
         else st = visible(P, 0.5 * (a1 + b1), 0.5 * (a2 + b2)) ? OR_ELEM_REGULAR : OR_ELEM_INVISIBLE;
@@ -375,7 +412,6 @@ static int cmpd(const void *a, const void *b) {
  *     inner range into intervals, the visible ones (midpoint test) get q Gauss
  *     points each. */
 static void cut_rule_build(const or_patch *P, int e1, int e2, dbuf *out) {
-  const or_desc *d = &P->d;
   double a[2] = {P->D[0].bp[e1], P->D[1].bp[e2]};
   double b[2] = {P->D[0].bp[e1 + 1], P->D[1].bp[e2 + 1]};
   int q = P->qc;
@@ -395,14 +431,14 @@ static void cut_rule_build(const or_patch *P, int e1, int e2, dbuf *out) {
   for (int o = 0; o < 2; o++)
     for (int side = 0; side < 2; side++) {
       double s = side ? b[o] : a[o];
-      int n = or_curve_line_hits(d, o, s, a[1 - o] - del[1 - o], b[1 - o] + del[1 - o], hits, HITCAP);
+      int n = set_line_hits(P, o, s, a[1 - o] - del[1 - o], b[1 - o] + del[1 - o], hits, HITCAP);
       for (int k = 0; k < n; k++) {
         if (o == 0) BBOX(s, hits[k]);
         else BBOX(hits[k], s);
       }
     }
   for (int o = 0; o < 2; o++) {
-    int n = or_curve_folds(d, o, pts, HITCAP);
+    int n = set_folds(P, o, pts, HITCAP);
     for (int k = 0; k < n; k++) {
       double x = pts[2 * k], y = pts[2 * k + 1];
       if (x >= a[0] - del[0] && x <= b[0] + del[0] && y >= a[1] - del[1] && y <= b[1] + del[1])
@@ -419,16 +455,16 @@ static void cut_rule_build(const or_patch *P, int e1, int e2, dbuf *out) {
   push(&br, b[o]);
   for (int side = 0; side < 2; side++) {
     double s = side ? b[in] : a[in];
-    int n = or_curve_line_hits(d, in, s, a[o], b[o], hits, HITCAP);
+    int n = set_line_hits(P, in, s, a[o], b[o], hits, HITCAP);
     for (int k = 0; k < n; k++) push(&br, hits[k]);
   }
   {
-    int n = or_curve_folds(d, o, pts, HITCAP);
+    int n = set_folds(P, o, pts, HITCAP);
     for (int k = 0; k < n; k++) {
       double xo = pts[2 * k + o], xi = pts[2 * k + in];
       if (xo > a[o] && xo < b[o] && xi >= a[in] && xi <= b[in]) push(&br, xo);
     }
-    n = or_curve_joints(d, pts, HITCAP);
+    n = set_joints(P, pts, HITCAP);
     for (int k = 0; k < n; k++) {
       double xo = pts[2 * k + o], xi = pts[2 * k + in];
       if (xo > a[o] && xo < b[o] && xi >= a[in] && xi <= b[in]) push(&br, xo);
@@ -442,7 +478,7 @@ static void cut_rule_build(const or_patch *P, int e1, int e2, dbuf *out) {
     for (int g = 0; g < q; g++) {
       double s = s0 + (s1 - s0) * 0.5 * (gx[g] + 1.0);
       double ws = gw[g] * 0.5 * (s1 - s0);
-      int n = or_curve_line_hits(d, o, s, a[in], b[in], hits, HITCAP);
+      int n = set_line_hits(P, o, s, a[in], b[in], hits, HITCAP);
       ends[0] = a[in];
       for (int k = 0; k < n; k++) ends[k + 1] = hits[k];
       ends[n + 1] = b[in];
@@ -834,6 +870,21 @@ or_patch *or_create(const or_desc *d) {
   int n[2];
   for (int dd = 0; dd < 2; dd++) n[dd] = d->nknots[dd] - d->p[dd] - 1;
   P->d.trim_ctrl = dup(P, d->trim_ctrl, d->trim_kind == OR_TRIM_BSPLINE3 ? 2 * (size_t)d->trim_nctrl : 0);
+  /* the curves, each as a copy of the descriptor with that curve in the trim fields */
+  P->ncurves = 1;
+  P->cd[0] = P->d;
+  for (int k = 0; k < d->trim_nextra && P->ncurves < OR_MAXCURVES; k++) {
+    const or_trim *t = &d->trim_extra[k];
+    or_desc c = P->d;
+    c.trim_kind = t->kind;
+    c.trim_keep_inside = t->keep_inside;
+    for (int m = 0; m < 6; m++) c.trim_params[m] = t->params[m];
+    c.trim_nctrl = t->nctrl;
+    c.trim_ctrl = dup(P, t->ctrl, t->kind == OR_TRIM_BSPLINE3 ? 2 * (size_t)t->nctrl : 0);
+    P->cd[P->ncurves++] = c;
+  }
+  P->d.trim_nextra = 0;
+  P->d.trim_extra = NULL;
   P->d.geom_ctrl = dup(P, d->geom_ctrl, d->geom_kind == OR_GEOM_SPLINE ? 2 * (size_t)n[0] * n[1] : 0);
   if (d->coef_kind == OR_COEF_DENSITY) {
     for (int dd = 0; dd < 2; dd++) P->d.dens_knots[dd] = dup(P, d->dens_knots[dd], (size_t)d->dens_nknots[dd]);

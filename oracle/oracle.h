@@ -63,6 +63,17 @@
 #define OR_FUNC_INTERIOR 1
 #define OR_FUNC_CUT 2
 
+/* one more trimming curve of a patch (same fields as the descriptor's first) */
+typedef struct {
+  int kind;
+  int keep_inside;
+  double params[6];
+  int nctrl;
+  const double *ctrl;
+} or_trim;
+
+#define OR_MAXCURVES 8
+
 typedef struct {
   int p[2];
   int nknots[2];
@@ -81,6 +92,11 @@ typedef struct {
   const double *dens_coef; /* (k2*m1 + k1) */
   int method;
   int cut_order; /* Gauss order on cut-element pieces; 0 -> p+1 */
+  /* further trimming curves (at most OR_MAXCURVES - 1): the visible domain is
+   * the intersection of every curve's kept side (outside for a hole, inside
+   * for keep_inside) */
+  int trim_nextra;
+  const or_trim *trim_extra;
 } or_desc;
 
 typedef struct {

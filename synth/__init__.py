@@ -18,6 +18,8 @@ A *patch spec* is a plain dict:
               "knots": [V1, V2], "coef": (m2, m1)}
     method   "gauss" | "hybrid" | "dwq" | "naive"
     cut_order  Gauss order on cut-element pieces (0 -> p + 1)
+    extra_trims  (optional) further trimming curves, each a dict like trim; the
+             visible domain is the intersection of every curve's kept side
 """
 from __future__ import annotations
 
@@ -132,9 +134,9 @@ def density(rng: np.random.Generator, q=2, m=32, lo=0.5, hi=2.0):
             "coef": rng.uniform(lo, hi, size=(m, m)).astype(np.float64)}
 
 
-def make_spec(p, nel, trim, geom=None, coef=None, method="hybrid", cut_order=0):
+def make_spec(p, nel, trim, geom=None, coef=None, method="hybrid", cut_order=0, extra_trims=None):
     nel = (nel, nel) if np.isscalar(nel) else tuple(nel)
-    return {
+    spec = {
         "p": int(p),
         "nel": nel,
         "knots": [open_uniform_knots(p, nel[0]), open_uniform_knots(p, nel[1])],
@@ -144,6 +146,23 @@ def make_spec(p, nel, trim, geom=None, coef=None, method="hybrid", cut_order=0):
         "method": method,
         "cut_order": int(cut_order),
     }
+    if extra_trims:
+        spec["extra_trims"] = list(extra_trims)
+    return spec
+
+
+def two_holes(rng=None):
+    """A circular hole and a seeded 10-point spline hole, disjoint."""
+    rng = rng or np.random.default_rng(BASE_SEED + 6)
+    return [circle(0.3, 0.32, 0.17),
+            bspline_curve(rng, nc=10, radius=0.16, jitter=0.02, center=(0.68, 0.66))]
+
+
+def annulus():
+    """The ring between an ellipse (a hole) and the circle around it (the
+    inside kept): a visible domain bounded by two loops."""
+    return [circle(0.5, 0.5, 0.44, keep_inside=True),
+            ellipse(0.52, 0.47, 0.2, 0.13, 0.4)]
 
 
 # ---------------------------------------------------------------------------

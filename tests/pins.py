@@ -216,3 +216,32 @@ class GreenEntries:
             self._I2[k2] = line_product_integral(self.U2, self.p, k2[0], k2[1])
         hole = float(np.sum(self._G[k1] * self._H[k2] * self.bnd[2]))
         return self._I1[k1] * self._I2[k2] - hole
+
+
+def ellipse_boundary_points(cx, cy, a, b, phi, U1, U2, q=40):
+    """Points / weights of oint (.) dy along the ellipse (counter-clockwise in
+    its parameter t), split where it crosses a knot line.  With c = cos phi,
+    s = sin phi: x - cx = Rx cos(t + dx), y - cy = Ry cos(t - dy)."""
+    cp, sp = math.cos(phi), math.sin(phi)
+    Rx, dx = math.hypot(a * cp, b * sp), math.atan2(b * sp, a * cp)
+    Ry, dy = math.hypot(a * sp, b * cp), math.atan2(b * cp, a * sp)
+    th = [0.0, 2 * math.pi]
+    for k in np.unique(U1):
+        v = (k - cx) / Rx
+        if -1 < v < 1:
+            ac = math.acos(v)
+            th += [(ac - dx) % (2 * math.pi), (-ac - dx) % (2 * math.pi)]
+    for k in np.unique(U2):
+        v = (k - cy) / Ry
+        if -1 < v < 1:
+            ac = math.acos(v)
+            th += [(ac + dy) % (2 * math.pi), (-ac + dy) % (2 * math.pi)]
+    br = np.unique(np.array(th))
+    gx, gw = np.polynomial.legendre.leggauss(q)
+    X, Y, W = [], [], []
+    for t0, t1 in zip(br[:-1], br[1:]):
+        t = t0 + (t1 - t0) * (gx + 1) / 2
+        X.append(cx + a * np.cos(t) * cp - b * np.sin(t) * sp)
+        Y.append(cy + a * np.cos(t) * sp + b * np.sin(t) * cp)
+        W.append(gw * (t1 - t0) / 2 * (-a * np.sin(t) * sp + b * np.cos(t) * cp))
+    return np.concatenate(X), np.concatenate(Y), np.concatenate(W)
