@@ -83,12 +83,28 @@ extern "C" {
 #define TW_FUNC_INTERIOR 1
 #define TW_FUNC_CUT 2
 
+/* One further trimming curve of a patch (the same fields as the descriptor's
+ * trim_*).  A patch may carry up to TW_MAXCURVES curves in all. */
+#define TW_MAXCURVES 8
+typedef struct {
+  int kind;
+  int keep_inside;
+  double params[6];
+  int nctrl;
+  const double *ctrl;
+} tw_trim_curve;
+
 /* Patch descriptor.  Field layout is shared with the CPU oracle's descriptor
  * so that one seeded generator can fill both; the values are the contract.
  *  p[d]          degree per direction, 1..6; p[0] must equal p[1]
  *  knots[d]      open knot vector (p+1 equal end knots, strictly increasing
  *                simple interior knots), nknots[d] = n_d + p + 1, >= 2 elements
  *  trim_*        the trimming curve; keep_inside = 0 keeps the outside (a hole)
+ *  trim_nextra,  further curves (trim_nextra <= TW_MAXCURVES - 1, host array):
+ *  trim_extra    the visible domain is the intersection of every curve's kept
+ *                side -- several holes, a half-plane with holes, or the ring
+ *                between a kept closed curve and a hole inside it (Sect. 4's
+ *                domains bounded by several curves)
  *  geom_ctrl     n2*n1*2 doubles for TW_GEOM_SPLINE, else NULL
  *  dens_*        density spline for TW_COEF_DENSITY
  *  cut_order     Gauss order on the pieces of a cut element (0 -> p+1)
@@ -112,6 +128,8 @@ typedef struct {
   int method;
   int cut_order;
   void *stream;
+  int trim_nextra;
+  const tw_trim_curve *trim_extra;
 } tw_patch_desc;
 
 typedef struct {

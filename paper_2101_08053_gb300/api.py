@@ -29,6 +29,16 @@ class TWError(RuntimeError):
         self.code = code
 
 
+class TrimCurve(C.Structure):
+    _fields_ = [
+        ("kind", C.c_int),
+        ("keep_inside", C.c_int),
+        ("params", C.c_double * 6),
+        ("nctrl", C.c_int),
+        ("ctrl", PD),
+    ]
+
+
 class PatchDesc(C.Structure):
     _fields_ = [
         ("p", C.c_int * 2),
@@ -49,6 +59,8 @@ class PatchDesc(C.Structure):
         ("method", C.c_int),
         ("cut_order", C.c_int),
         ("stream", C.c_void_p),
+        ("trim_nextra", C.c_int),
+        ("trim_extra", C.POINTER(TrimCurve)),
     ]
 
 
@@ -199,6 +211,23 @@ def make_patch_desc(spec, keep):
         d.dens_coef = _pd(dc)
     d.method = METHOD[spec["method"]]
     d.cut_order = spec.get("cut_order", 0)
+    extra = spec.get("extra_trims", [])
+    if extra:
+        arr = (TrimCurve * len(extra))()
+        for k, t in enumerate(extra):
+            arr[k].kind = TRIM[t["kind"]]
+            arr[k].keep_inside = int(bool(t.get("keep_inside", False)))
+            prm = list(t.get("params", [])) + [0.0] * 6
+            for m in range(6):
+                arr[k].params[m] = prm[m]
+            if t.get("ctrl") is not None:
+                ctrl = _f64(t["ctrl"])
+                keep.append(ctrl)
+                arr[k].nctrl = ctrl.shape[0]
+                arr[k].ctrl = ctrl.ctypes.data_as(PD)
+        keep.append(arr)
+        d.trim_nextra = len(extra)
+        d.trim_extra = C.cast(arr, C.POINTER(TrimCurve))
     return d
 
 

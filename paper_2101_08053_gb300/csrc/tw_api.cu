@@ -164,6 +164,43 @@ static int valid_open_knots(const double *U, int nk, int p, const char *what) {
 
 using namespace tw;
 
+// curve k of a descriptor: -1 the trim_* fields, else trim_extra[k]
+static tw_trim_curve curve_of(const tw_patch_desc *d, int k) {
+  if (k >= 0) return d->trim_extra[k];
+  tw_trim_curve t;
+  t.kind = d->trim_kind;
+  t.keep_inside = d->trim_keep_inside;
+  for (int m = 0; m < 6; m++) t.params[m] = d->trim_params[m];
+  t.nctrl = d->trim_nctrl;
+  t.ctrl = d->trim_ctrl;
+  return t;
+}
+
+static bool valid_curve(const tw_trim_curve &t, int k) {
+  const char *which = k < 0 ? "trim" : "trim_extra";
+  if (t.kind < TW_TRIM_NONE || t.kind > TW_TRIM_LINE) {
+    set_error("tw_patch_create: unknown %s kind %d", which, t.kind);
+    return false;
+  }
+  if (t.kind == TW_TRIM_CIRCLE && !(t.params[2] > 0)) {
+    set_error("tw_patch_create: circle radius must be > 0");
+    return false;
+  }
+  if (t.kind == TW_TRIM_ELLIPSE && !(t.params[2] > 0 && t.params[3] > 0)) {
+    set_error("tw_patch_create: ellipse semi-axes must be > 0");
+    return false;
+  }
+  if (t.kind == TW_TRIM_LINE && !(t.params[0] != t.params[2] || t.params[1] != t.params[3])) {
+    set_error("tw_patch_create: a trimming line needs two distinct points");
+    return false;
+  }
+  if (t.kind == TW_TRIM_BSPLINE3 && (!t.ctrl || t.nctrl < 4 || t.nctrl > 4096)) {
+    set_error("tw_patch_create: spline curve needs 4..4096 control points");
+    return false;
+  }
+  return true;
+}
+
 extern "C" const char *tw_last_error(void) { return g_err; }
 extern "C" int64_t tw_launch_count(void) { return g_launches.load(); }
 
@@ -247,27 +284,14 @@ extern "C" int tw_patch_create(const tw_patch_desc *desc, tw_patch **out) {
   for (int d = 0; d < 2; d++)
     if (!valid_open_knots(desc->knots[d], desc->nknots[d], p, d ? "knots[1]" : "knots[0]"))
       return TW_EINVAL;
-  if (desc->trim_kind < TW_TRIM_NONE || desc->trim_kind > TW_TRIM_LINE) {
-    set_error("tw_patch_create: unknown trim_kind %d", desc->trim_kind);
+  if (desc->trim_nextra < 0 || desc->trim_nextra > TW_MAXCURVES - 1 ||
+      (desc->trim_nextra > 0 && !desc->trim_extra)) {
+    set_error("tw_patch_create: trim_nextra must be 0..%d with a curve array", TW_MAXCURVES - 1);
     return TW_EINVAL;
   }
-  if (desc->trim_kind == TW_TRIM_CIRCLE && !(desc->trim_params[2] > 0)) {
-    set_error("tw_patch_create: circle radius must be > 0");
-    return TW_EINVAL;
-  }
-  if (desc->trim_kind == TW_TRIM_ELLIPSE && !(desc->trim_params[2] > 0 && desc->trim_params[3] > 0)) {
-    set_error("tw_patch_create: ellipse semi-axes must be > 0");
-    return TW_EINVAL;
-  }
-  if (desc->trim_kind == TW_TRIM_LINE &&
-      !(desc->trim_params[0] != desc->trim_params[2] || desc->trim_params[1] != desc->trim_params[3])) {
-    set_error("tw_patch_create: a trimming line needs two distinct points");
-    return TW_EINVAL;
-  }
-  if (desc->trim_kind == TW_TRIM_BSPLINE3 &&
-      (!desc->trim_ctrl || desc->trim_nctrl < 4 || desc->trim_nctrl > 4096)) {
-    set_error("tw_patch_create: spline curve needs 4..4096 control points");
-    return TW_EINVAL;
+  for (int k = -1; k < desc->trim_nextra; k++) {
+    tw_trim_curve t = curve_of(desc, k);
+    if (!valid_curve(t, k)) return TW_EINVAL;
   }
   if (desc->geom_kind != TW_GEOM_IDENTITY && desc->geom_kind != TW_GEOM_SPLINE) {
     set_error("tw_patch_create: unknown geom_kind %d", desc->geom_kind);
@@ -366,20 +390,29 @@ extern "C" int tw_patch_create(const tw_patch_desc *desc, tw_patch **out) {
     }
     Dir &A = P->d[0];
     Dir &B = P->d[1];
-    // curve
-    P->curve.kind = desc->trim_kind;
-    P->curve.keep_inside = desc->trim_keep_inside;
-    for (int k = 0; k < 6; k++) P->curve.prm[k] = desc->trim_params[k];
-    P->curve.nc = desc->trim_kind == TW_TRIM_BSPLINE3 ? desc->trim_nctrl : 0;
-    if (P->curve.nc > 0) {
-      double *seg, *box;
-      ALLOC(P->curve_ctrl, double, 2 * P->curve.nc);
-      ALLOC(seg, double, 8 * P->curve.nc);
-      ALLOC(box, double, 4 * P->curve.nc);
-      P->curve.seg = seg;
-      P->curve.box = box;
-      cudaMemcpyAsync(P->curve_ctrl, desc->trim_ctrl, sizeof(double) * 2 * P->curve.nc,
-                      cudaMemcpyHostToDevice, st);
+    // curves (the untrimmed kind left out)
+    P->curves.n = 0;
+    for (int k = -1; k < desc->trim_nextra; k++) {
+      const tw_trim_curve t = curve_of(desc, k);
+      if (t.kind == TW_TRIM_NONE) continue;
+      const int ci = P->curves.n++;
+      Curve &Cv = P->curves.c[ci];
+      Cv.kind = t.kind;
+      Cv.keep_inside = t.keep_inside;
+      for (int m = 0; m < 6; m++) Cv.prm[m] = t.params[m];
+      Cv.nc = t.kind == TW_TRIM_BSPLINE3 ? t.nctrl : 0;
+      Cv.seg = Cv.box = nullptr;
+      P->curve_ctrl[ci] = nullptr;
+      if (Cv.nc > 0) {
+        double *seg, *box;
+        ALLOC(P->curve_ctrl[ci], double, 2 * Cv.nc);
+        ALLOC(seg, double, 8 * Cv.nc);
+        ALLOC(box, double, 4 * Cv.nc);
+        Cv.seg = seg;
+        Cv.box = box;
+        cudaMemcpyAsync(P->curve_ctrl[ci], t.ctrl, sizeof(double) * 2 * Cv.nc,
+                        cudaMemcpyHostToDevice, st);
+      }
     }
     // geometry and coefficient
     P->geo.geom_kind = desc->geom_kind;

@@ -424,6 +424,43 @@ __device__ __forceinline__ int visible(const Curve &C, double x, double y) {
   return C.keep_inside ? in : !in;
 }
 
+// the trimming curves of a patch (kind != TW_TRIM_NONE; n = 0: untrimmed); the
+// visible domain is the intersection of every curve's kept side
+struct CurveSet {
+  int n;
+  Curve c[TW_MAXCURVES];
+};
+
+// crossings of every curve with the line xi_o = s inside (lo, hi), ascending;
+// -1 when more than cap
+static __device__ int set_line_hits(const CurveSet &S, int o, double s, double lo, double hi,
+                                    double *out, int cap) {
+  int n = 0;
+  for (int k = 0; k < S.n; k++) {
+    if (cap - n < 2) return -1;  // a conic writes up to two crossings unchecked
+    const int m = curve_line_hits(S.c[k], o, s, lo, hi, out + n, cap - n);
+    if (m < 0) return -1;
+    n += m;
+  }
+  if (S.n > 1)
+    for (int i = 1; i < n; i++) {
+      const double x = out[i];
+      int j = i - 1;
+      while (j >= 0 && out[j] > x) {
+        out[j + 1] = out[j];
+        j--;
+      }
+      out[j + 1] = x;
+    }
+  return n;
+}
+
+__device__ __forceinline__ int set_visible(const CurveSet &S, double x, double y) {
+  for (int k = 0; k < S.n; k++)
+    if (!visible(S.c[k], x, y)) return 0;
+  return 1;
+}
+
 // curve points where d(coordinate o)/d(param) = 0; returns count (pts as x,y)
 static __device__ int curve_folds(const Curve &C, int o, double *pts, int cap) {
   if (C.kind == TW_TRIM_CIRCLE) {
@@ -696,8 +733,8 @@ struct tw_patch {
   int p, method, qc;
   tw::Dir d[2];
   const double *qrule;  // cut-piece Gauss rule (cached, not owned)
-  tw::Curve curve;
-  double *curve_ctrl;  // device copy of the spline curve's control points
+  tw::CurveSet curves;
+  double *curve_ctrl[TW_MAXCURVES];  // device copies of spline curves' control points
   tw::Geo geo;
   cudaStream_t stream;
   // owned device allocations

@@ -297,7 +297,7 @@ __device__ void curve_point0(const Curve &C, double *xy) {
 // vertical knot lines x = bp1[l], [nel1+1, nel1+nel2+1] the horizontal knot
 // lines, and the last nel2 the horizontal lines through the element centres of
 // each row (visibility by the parity of crossings to the right, reading R8).
-__global__ void k_line_hits(Curve C, Dir A, Dir B, double *hits, int *nh, int *flag) {
+__global__ void k_line_hits(CurveSet C, Dir A, Dir B, double *hits, int *nh, int *flag) {
   int l = blockIdx.x * blockDim.x + threadIdx.x;
   int nl = (A.nel + 1) + (B.nel + 1) + B.nel;
   if (l >= nl) return;
@@ -314,7 +314,7 @@ __global__ void k_line_hits(Curve C, Dir A, Dir B, double *hits, int *nh, int *f
     o = 1;
     s = 0.5 * (B.bp[e2] + B.bp[e2 + 1]);
   }
-  int n = curve_line_hits(C, o, s, -1e300, 1e300, hits + (size_t)l * TW_HITCAP, TW_HITCAP);
+  int n = set_line_hits(C, o, s, -1e300, 1e300, hits + (size_t)l * TW_HITCAP, TW_HITCAP);
   if (n < 0) {
     atomicOr(flag, TWF_HITCAP);
     n = 0;
@@ -331,12 +331,12 @@ __device__ __forceinline__ int any_hit_in(const double *h, int n, double lo, dou
 // R8: an element is cut iff the curve meets its open box: a crossing inside
 // one of its four open edges (corner touches excluded), or the whole curve
 // inside it; otherwise visible iff its centre is
-__global__ void k_classify_elems(Curve C, Dir A, Dir B, const double *hits, const int *nh,
+__global__ void k_classify_elems(CurveSet C, Dir A, Dir B, const double *hits, const int *nh,
                                  uint8_t *estate) {
   int id = blockIdx.x * blockDim.x + threadIdx.x;
   if (id >= A.nel * B.nel) return;
   int e1 = id % A.nel, e2 = id / A.nel;
-  if (C.kind == TW_TRIM_NONE) {
+  if (C.n == 0) {
     estate[id] = TW_ELEM_REGULAR;
     return;
   }
@@ -348,9 +348,9 @@ __global__ void k_classify_elems(Curve C, Dir A, Dir B, const double *hits, cons
             any_hit_in(hits + (size_t)(e1 + 1) * TW_HITCAP, nh[e1 + 1], a2 + d2, b2 - d2) ||
             any_hit_in(hits + (size_t)(hv + e2) * TW_HITCAP, nh[hv + e2], a1 + d1, b1 - d1) ||
             any_hit_in(hits + (size_t)(hv + e2 + 1) * TW_HITCAP, nh[hv + e2 + 1], a1 + d1, b1 - d1);
-  if (!cut) {
+  for (int k = 0; k < C.n && !cut; k++) {  // a whole curve inside the element
     double p0[2];
-    curve_point0(C, p0);
+    curve_point0(C.c[k], p0);
     cut = p0[0] > a1 && p0[0] < b1 && p0[1] > a2 && p0[1] < b2;
   }
   uint8_t st;
@@ -358,13 +358,19 @@ __global__ void k_classify_elems(Curve C, Dir A, Dir B, const double *hits, cons
     st = TW_ELEM_CUT;
   } else {
     double xc = 0.5 * (a1 + b1);
-    const double *h = hits + (size_t)(hc + e2) * TW_HITCAP;
-    int right = 0;
-    for (int k = 0; k < nh[hc + e2]; k++) right += h[k] > xc;
-    // parity of the crossings to the right for a closed curve; the half-plane
-    // of a line is tested directly
-    int inside = C.kind == TW_TRIM_LINE ? curve_inside(C, xc, 0.5 * (a2 + b2)) : (right & 1);
-    int vis = C.keep_inside ? inside : !inside;
+    int vis;
+    if (C.n == 1) {
+      const Curve &C0 = C.c[0];
+      const double *h = hits + (size_t)(hc + e2) * TW_HITCAP;
+      int right = 0;
+      for (int k = 0; k < nh[hc + e2]; k++) right += h[k] > xc;
+      // parity of the crossings to the right for a closed curve; the half-plane
+      // of a line is tested directly
+      int inside = C0.kind == TW_TRIM_LINE ? curve_inside(C0, xc, 0.5 * (a2 + b2)) : (right & 1);
+      vis = C0.keep_inside ? inside : !inside;
+    } else {  // several curves: the centre against every curve's kept side
+      vis = set_visible(C, xc, 0.5 * (a2 + b2));
+    }
     st = vis ? TW_ELEM_REGULAR : TW_ELEM_INVISIBLE;
   }
   estate[id] = st;
@@ -495,21 +501,26 @@ __device__ void sort_small(double *v, int n) {
 // Curve-wide features, once per patch: tangent points of both kinds (the
 // curve's tangent parallel to an axis) and the spline's segment joints.
 // feat[(kind * fcap + k) * 2 + {0,1}], nfeat[kind], kind 2 = joints.
-__global__ void k_curve_features(Curve C, double *feat, int *nfeat, int fcap, int *flag) {
+__global__ void k_curve_features(CurveSet S, double *feat, int *nfeat, int fcap, int *flag) {
   int kind = threadIdx.x;
   if (kind >= 3) return;
   double *out = feat + (size_t)kind * fcap * 2;
   int n = 0;
-  if (kind < 2) {
-    n = curve_folds(C, kind, out, fcap);
-    if (n < 0) {
-      atomicOr(flag, TWF_HITCAP);
-      n = 0;
-    }
-  } else if (C.kind == TW_TRIM_BSPLINE3) {
-    for (int sg = 0; sg < C.nc && n < fcap; sg++, n++) {
-      out[2 * n] = C.seg[8 * sg];
-      out[2 * n + 1] = C.seg[8 * sg + 4];
+  for (int ci = 0; ci < S.n; ci++) {
+    const Curve &C = S.c[ci];
+    if (kind < 2) {
+      // a conic writes its two tangent points unchecked
+      const int m = fcap - n >= 2 ? curve_folds(C, kind, out + 2 * n, fcap - n) : -1;
+      if (m < 0) {
+        atomicOr(flag, TWF_HITCAP);
+        break;
+      }
+      n += m;
+    } else if (C.kind == TW_TRIM_BSPLINE3) {
+      for (int sg = 0; sg < C.nc && n < fcap; sg++, n++) {
+        out[2 * n] = C.seg[8 * sg];
+        out[2 * n + 1] = C.seg[8 * sg + 4];
+      }
     }
   }
   nfeat[kind] = n;
@@ -654,45 +665,60 @@ __device__ __forceinline__ CutLine cut_line(Dir A, Dir B, const int32_t *cut_lis
 
 // crossings (lh[li * TW_HITCAP ..], ln[li] of them; -1 for an empty piece),
 // the visibility of the first interval and the line's point count
-__global__ void k_cut_lines(Curve C, Dir A, Dir B, const int32_t *cut_list, int ncut, int q,
+__global__ void k_cut_lines(CurveSet C, Dir A, Dir B, const int32_t *cut_list, int ncut, int q,
                             const double *qgx, const double *qgw, const double *hits,
                             const int *nh, const int32_t *cut_o, const double *br_all,
                             const int64_t *line_off, const int64_t *nl_tot, double *lh,
-                            int32_t *ln, int8_t *lvis, int64_t *lcnt, int *flag) {
+                            int32_t *ln, uint64_t *lvis, int64_t *lcnt, int *flag) {
   const int64_t L = *nl_tot;
   for (int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; li < L;
        li += (int64_t)gridDim.x * blockDim.x) {
     const CutLine cl = cut_line(A, B, cut_list, cut_o, br_all, line_off, ncut, q, qgx, qgw, li);
     int64_t count = 0;
-    int n = -1, vis0 = 0;
+    int n = -1;
+    uint64_t vis = 0;  // bit k: interval k of the line is visible
     if (cl.ws >= 0.0) {
       double h[TW_HITCAP + 2];
-      n = curve_line_hits(C, cl.o, cl.s, cl.lo, cl.hi, h + 1, TW_HITCAP);
+      n = set_line_hits(C, cl.o, cl.s, cl.lo, cl.hi, h + 1, TW_HITCAP);
       if (n < 0) {
         atomicOr(flag, TWF_HITCAP);
         n = -1;
       } else {
         h[0] = cl.lo;
         h[n + 1] = cl.hi;
-        // crossings of the edge line through the lines' first ends
-        const int e = cut_list[cl.ci], e1 = e % A.nel, e2 = e / A.nel;
-        const int lfirst = cl.o == 1 ? e1 : A.nel + 1 + e2;
-        const double *eh = hits + (size_t)lfirst * TW_HITCAP;
-        int right = 0;
-        for (int k = 0; k < nh[lfirst]; k++) right += eh[k] > cl.s;
-        int inside = right & 1;
-        if (C.kind == TW_TRIM_LINE) {  // a half-plane: test the first interval's midpoint
-          const double um = 0.5 * (h[0] + h[1]);
-          inside = cl.o == 0 ? curve_inside(C, cl.s, um) : curve_inside(C, um, cl.s);
+        if (C.n == 1) {
+          // one closed curve: the first interval's visibility from the parity
+          // of the edge line's crossings beyond the line's first end, then
+          // alternation at each crossing
+          const Curve &C0 = C.c[0];
+          const int e = cut_list[cl.ci], e1 = e % A.nel, e2 = e / A.nel;
+          const int lfirst = cl.o == 1 ? e1 : A.nel + 1 + e2;
+          const double *eh = hits + (size_t)lfirst * TW_HITCAP;
+          int right = 0;
+          for (int k = 0; k < nh[lfirst]; k++) right += eh[k] > cl.s;
+          int inside = right & 1;
+          if (C0.kind == TW_TRIM_LINE) {  // a half-plane: test the first interval's midpoint
+            const double um = 0.5 * (h[0] + h[1]);
+            inside = cl.o == 0 ? curve_inside(C0, cl.s, um) : curve_inside(C0, um, cl.s);
+          }
+          const int vis0 = C0.keep_inside ? inside : !inside;
+          for (int k = 0; k <= n; k++)
+            if (vis0 ^ (k & 1)) vis |= 1ull << k;
+        } else {
+          // several curves: each interval's midpoint against every kept side
+          for (int k = 0; k <= n; k++) {
+            const double um = 0.5 * (h[k] + h[k + 1]);
+            const int v = cl.o == 0 ? set_visible(C, cl.s, um) : set_visible(C, um, cl.s);
+            if (v) vis |= 1ull << k;
+          }
         }
-        vis0 = C.kind == TW_TRIM_NONE ? 1 : (C.keep_inside ? inside : !inside);
         for (int k = 0; k <= n; k++)
-          if (h[k + 1] > h[k] && (vis0 ^ (k & 1))) count += q;
+          if (h[k + 1] > h[k] && ((vis >> k) & 1ull)) count += q;
         for (int k = 0; k < n; k++) lh[li * TW_HITCAP + k] = h[k + 1];
       }
     }
     ln[li] = n;
-    lvis[li] = (int8_t)vis0;
+    lvis[li] = vis;
     lcnt[li] = count;
   }
 }
@@ -700,7 +726,7 @@ __global__ void k_cut_lines(Curve C, Dir A, Dir B, const int32_t *cut_list, int 
 __global__ void k_cut_write(Dir A, Dir B, const int32_t *cut_list, int ncut, int q,
                             const double *qgx, const double *qgw, const int32_t *cut_o,
                             const double *br_all, const int64_t *line_off, const int64_t *nl_tot,
-                            const double *lh, const int32_t *ln, const int8_t *lvis,
+                            const double *lh, const int32_t *ln, const uint64_t *lvis,
                             const int64_t *lpos, double *pts) {
   const int64_t L = *nl_tot;
   for (int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; li < L;
@@ -708,13 +734,13 @@ __global__ void k_cut_write(Dir A, Dir B, const int32_t *cut_list, int ncut, int
     const int n = ln[li];
     if (n < 0) continue;
     const CutLine cl = cut_line(A, B, cut_list, cut_o, br_all, line_off, ncut, q, qgx, qgw, li);
-    const int vis0 = lvis[li];
+    const uint64_t vis = lvis[li];
     double *dst = pts + 3 * lpos[li];
     int64_t w0 = 0;
     for (int k = 0; k <= n; k++) {
       const double u0 = k == 0 ? cl.lo : lh[li * TW_HITCAP + k - 1];
       const double u1 = k == n ? cl.hi : lh[li * TW_HITCAP + k];
-      if (!(u1 > u0) || !(vis0 ^ (k & 1))) continue;
+      if (!(u1 > u0) || !((vis >> k) & 1ull)) continue;
       for (int hh = 0; hh < q; hh++) {
         double u = u0 + (u1 - u0) * 0.5 * (qgx[hh] + 1.0);
         double w = cl.ws * qgw[hh] * 0.5 * (u1 - u0);
@@ -1492,9 +1518,10 @@ int build_tables(tw_patch *P) {
         A, B, P->flag);
     TW_LAUNCH();
   }
-  if (P->curve.kind == TW_TRIM_BSPLINE3) {
-    k_curve_segments<<<G1(P->curve.nc)>>>(P->curve_ctrl, P->curve.nc, (double *)P->curve.seg,
-                                          (double *)P->curve.box);
+  for (int ci = 0; ci < P->curves.n; ci++) {
+    const Curve &Cv = P->curves.c[ci];
+    if (Cv.kind != TW_TRIM_BSPLINE3) continue;
+    k_curve_segments<<<G1(Cv.nc)>>>(P->curve_ctrl[ci], Cv.nc, (double *)Cv.seg, (double *)Cv.box);
     TW_LAUNCH();
   }
   if ((rc = check_cuda(cudaGetLastError(), "wq tables"))) return rc;
@@ -1505,7 +1532,8 @@ int build_tables(tw_patch *P) {
   int32_t *cflag = (int32_t *)dalloc(P, sizeof(int32_t) * nf);
   int32_t *cpos = (int32_t *)dalloc(P, sizeof(int32_t) * nf);
   if (!aflag || !cflag || !cpos) return TW_ENOMEM;
-  int fcap = 2 * P->curve.nc + 4;
+  int fcap = 4;
+  for (int ci = 0; ci < P->curves.n; ci++) fcap += 2 * P->curves.c[ci].nc + 4;
   double *lh, *feat;
   int *lnh, *nfeat;
   {
@@ -1515,13 +1543,13 @@ int build_tables(tw_patch *P) {
     feat = (double *)dalloc(P, sizeof(double) * 3 * 2 * (size_t)fcap);
     nfeat = (int *)dalloc(P, sizeof(int) * 4);
     if (!lh || !lnh || !feat || !nfeat) return TW_ENOMEM;
-    if (P->curve.kind != TW_TRIM_NONE) {
-      k_line_hits<<<G1(nl)>>>(P->curve, A, B, lh, lnh, P->flag);
+    if (P->curves.n > 0) {
+      k_line_hits<<<G1(nl)>>>(P->curves, A, B, lh, lnh, P->flag);
       TW_LAUNCH();
-      k_curve_features<<<1, 32, 0, st>>>(P->curve, feat, nfeat, fcap, P->flag);
+      k_curve_features<<<1, 32, 0, st>>>(P->curves, feat, nfeat, fcap, P->flag);
       TW_LAUNCH();
     }
-    k_classify_elems<<<G1(ne)>>>(P->curve, A, B, lh, lnh, P->estate);
+    k_classify_elems<<<G1(ne)>>>(P->curves, A, B, lh, lnh, P->estate);
     TW_LAUNCH();
   }
   k_classify_funcs<<<G1(nf)>>>(A, B, P->estate, P->fstate, aflag, P->method, cflag, counters);
@@ -1632,7 +1660,7 @@ int build_tables(tw_patch *P) {
   double *cbr = nullptr, *clh = nullptr;
   int64_t *line_off = nullptr, *lpos = nullptr;
   int32_t *cln = nullptr;
-  int8_t *clv = nullptr;
+  uint64_t *clv = nullptr;
   int64_t nlines = 0;
   if (P->ncut > 0) {
     cbr = (double *)dalloc(P, sizeof(double) * (size_t)P->ncut * TW_BRCAP);
@@ -1649,7 +1677,7 @@ int build_tables(tw_patch *P) {
     if ((rc = check_cuda(cudaStreamSynchronize(st), "cut rules"))) return rc;
     clh = (double *)dalloc(P, sizeof(double) * ((size_t)nlines * TW_HITCAP + 1));
     cln = (int32_t *)dalloc(P, sizeof(int32_t) * (nlines + 1));
-    clv = (int8_t *)dalloc(P, nlines + 1);
+    clv = (uint64_t *)dalloc(P, sizeof(uint64_t) * (nlines + 1));
     int64_t *clc = (int64_t *)dalloc(P, sizeof(int64_t) * (nlines + 1));
     lpos = (int64_t *)dalloc(P, sizeof(int64_t) * (nlines + 1));
     if (!clh || !cln || !clv || !clc || !lpos) return TW_ENOMEM;
@@ -1658,7 +1686,7 @@ int build_tables(tw_patch *P) {
       // 64-thread blocks: a patch has only ~10^4 lines, and 256-thread
       // blocks would leave most SMs idle on this FP64-heavy kernel
       k_cut_lines<<<(unsigned)((nlines + 63) / 64), 64, 0, st>>>(
-          P->curve, A, B, P->cut_list, P->ncut, P->qc, qgx, qgw, lh, lnh, P->cut_o, cbr, line_off,
+          P->curves, A, B, P->cut_list, P->ncut, P->qc, qgx, qgw, lh, lnh, P->cut_o, cbr, line_off,
           tot64 + 2, clh, cln, clv, clc, P->flag);
       TW_LAUNCH();
     }

@@ -36,7 +36,8 @@ def test_header_symbols_cover_the_binding():
         assert s in syms
 
 
-@pytest.mark.parametrize("bad", ["degree", "mixed", "knots", "closed", "trim", "method", "cut"])
+@pytest.mark.parametrize("bad", ["degree", "mixed", "knots", "closed", "trim", "method", "cut",
+                                 "extra_count", "extra_null", "extra_curve"])
 def test_descriptor_validation_on_host(bad):
     from paper_2101_08053_gb300 import api
     L = api.load()
@@ -66,6 +67,23 @@ def test_descriptor_validation_on_host(bad):
         code = -1
     elif bad == "method":
         d.method = 7
+        code = -1
+    elif bad == "extra_count":  # more curves than TW_MAXCURVES
+        d.trim_nextra = 8
+        arr = (api.TrimCurve * 8)()
+        keep.append(arr)
+        d.trim_extra = C.cast(arr, C.POINTER(api.TrimCurve))
+        code = -1
+    elif bad == "extra_null":
+        d.trim_nextra = 1
+        code = -1
+    elif bad == "extra_curve":  # a second curve with a negative radius
+        arr = (api.TrimCurve * 1)()
+        arr[0].kind = 1
+        arr[0].params[2] = -0.2
+        keep.append(arr)
+        d.trim_nextra = 1
+        d.trim_extra = C.cast(arr, C.POINTER(api.TrimCurve))
         code = -1
     else:
         d.cut_order = 1000
