@@ -188,6 +188,58 @@ def interior_flops(p, nel, fstate):
 # ---------------------------------------------------------------------------
 
 
+def minnorm_flops(m, N):
+    """FP64 operations of the minimum-norm solution of an m x N system (m <= N)
+    by Householder reflectors applied from the right (reading R2): per reflector
+    k the norm of its part of row k (2 (N - k)), its application to the m - k - 1
+    rows below (a dot product and an update, 4 (N - k) each) and its step of the
+    back transformation (4 (N - k)); then the forward substitution (m^2)."""
+    return sum(2 * (N - k) + 4 * (m - k - 1) * (N - k) + 4 * (N - k) for k in range(m)) + m * m
+
+
+def wq_points_per_element(p, nel, nested=()):
+    """Reading R1 (and R5 for the elements next to a disc): p + 1 points in the
+    two end elements and in the elements listed in `nested`, 2 elsewhere."""
+    return [p + 1 if e in (0, nel - 1) or e in nested else 2 for e in range(nel)]
+
+
+def setup_minnorm_flops(p, nel1, nel2, ndisc):
+    """Algorithmic FP64 operations of the set-up's min-norm solves: the WQ
+    weights of every test function of both directions (Eq. 5) and, per disc
+    knot, the 2p refined systems of the DWQ rule (Sect. 3.3: t inserted p times,
+    nested points next to it; counted for a disc away from the patch's ends)."""
+    total = 0
+    for nel in (nel1, nel2):
+        n = nel + p
+        cnt = wq_points_per_element(p, nel)
+        for i in range(n):
+            lo, hi = max(0, i - p), min(i, nel - 1)
+            N = sum(cnt[lo:hi + 1])
+            m = min(n - 1, i + p) - max(0, i - p) + 1
+            total += minnorm_flops(m, N)
+    # one interior disc of direction 1: refined knots with t of multiplicity p + 1
+    nel = nel1
+    s = nel // 2
+    U = synth.open_uniform_knots(p, nel)
+    t = U[p + s]
+    R = np.concatenate([U[:p + s + 1], [t] * p, U[p + s + 1:]])
+    cnt = wq_points_per_element(p, nel, nested=(s - 1, s))
+    bp = U[p:p + nel + 1]
+    nref = len(R) - p - 1
+
+    def supp(l):
+        return R[l], R[l + p + 1]
+
+    per_disc = 0
+    for l in range(s, s + 2 * p):
+        a, b = supp(l)
+        m = sum(1 for k in range(max(0, l - p), min(nref, l + p + 1))
+                if min(b, supp(k)[1]) > max(a, supp(k)[0]))
+        N = sum(cnt[e] for e in range(nel) if bp[e] >= a and bp[e + 1] <= b)
+        per_disc += minnorm_flops(m, N)
+    return total + ndisc * per_disc
+
+
 def fp64_peak_gflops():
     """FP64 peak of a GB300 from its unit counts and clock: 152 SMs x 2 DFMA
     per clock x 2 flop x 2.07 GHz (a DFMA-loop probe measured 1 255.6 GFLOP/s)."""
@@ -267,7 +319,7 @@ def run_ours(args, rank, world, local_rank):
     for s in sp:
         P = api.Patch(s)
         outs.append(P.alloc_csr("fp64"))
-        infos.append((P.n_rows, P.nnz, P.n_cut_fns, P.n_cut_elems, P.n_dwq_rows))
+        infos.append((P.n_rows, P.nnz, P.n_cut_fns, P.n_cut_elems, P.n_dwq_rows, P.n_discs))
         P.close()
     nnz_step = sum(i[1] for i in infos)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -447,6 +499,12 @@ def run_ours(args, rank, world, local_rank):
     flops_per_launch = flops / max(1, launches_per_step)
     achieved = flops_per_launch / (avg_launch_ms * 1e-3) / 1e12
     peak = fp64_peak_gflops() / 1e3
+    # the set-up's min-norm solves (WQ weights, DWQ rules), timed in the same
+    # serialised pass by their profiler stages
+    su_flops = sum(setup_minnorm_flops(s_["p"], s_["nel"][0], s_["nel"][1], info[5])
+                   for s_, info in zip(sp, infos))
+    su_ms = (stage["wq_weights"][0] + stage["dwq"][0]) / max(1, args.steps)
+    su_achieved = su_flops / (su_ms * 1e-3) / 1e12 if su_ms > 0 else 0.0
     stage_ms = {k: round(v[0] / max(1, args.steps), 3) for k, v in stage.items() if v[1]}
     stage_ms_batched = {k: round(v[0] / max(1, args.steps), 3) for k, v in stage_batched.items()
                         if v[1]}
@@ -465,6 +523,16 @@ def run_ours(args, rank, world, local_rank):
                                "patches)",
                      "peak_source": "GB300 unit counts x max clock (152 SMs x 2 DFMA/clk x "
                                     "2.07 GHz); a DFMA probe measured 1.2556 TFLOP/s"},
+        "roofline_setup": {"bound": "alu",
+                           "kernel": "k_wq_weights + k_dwq_build (the set-up's min-norm solves, "
+                                     "Eq. 5 and Sect. 3.3)",
+                           "achieved": round(su_achieved, 5), "peak": peak, "unit": "TFLOP/s",
+                           "frac": round(su_achieved / peak, 5), "traffic": None,
+                           "flops_per_step": su_flops, "ms_per_step": round(su_ms, 4),
+                           "timing": "stage events around the two kernels in the serialised pass",
+                           "flops": "Householder LQ per system: reflector norms, application "
+                                    "to the rows below, back transformation, forward "
+                                    "substitution (bench.minnorm_flops)"},
     }
 
 
@@ -925,6 +993,7 @@ def main():
                 "e2e": {"value": job_rate(world, r["nnz_step"], r["e2e_ms"]), "unit": UNIT,
                         "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]},
                 "gpu_launches": r["launches"], "clocks": r["clocks"], "roofline": r["roofline"],
+                "roofline_setup": r["roofline_setup"],
                 "cpu_baseline": cpu, "stage_ms_per_step_serial": r["stage_ms"],
                 "stage_ms_per_step_batched": r["stage_ms_batched"],
                 "precision_modes_formation_only": r["modes"],

@@ -443,7 +443,9 @@ int tw_pool_info(int64_t *info3);
                                 CG counts as TW_STAGE_CG)                     */
 #define TW_STAGE_GAUSSMAT 7  /* inside tw_patch_create: the element matrices of
                                 the regular elements near the curve           */
-#define TW_NSTAGES 8
+#define TW_STAGE_WQW 8       /* inside tw_patch_create: the WQ weight solves (Eq. 5) */
+#define TW_STAGE_DWQ 9       /* inside tw_patch_create: the DWQ rules (Sect. 3.3)    */
+#define TW_NSTAGES 10
 int tw_profile_enable(int on);
 int tw_profile_read(int stage, double *total_ms, int64_t *count);
 

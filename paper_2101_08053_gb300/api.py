@@ -585,7 +585,7 @@ def pool_info():
 
 
 STAGES = {"setup": 0, "interior": 1, "cutrows": 2, "rhs": 3, "cg": 4, "loss": 5, "adjoint": 6,
-          "gaussmat": 7}
+          "gaussmat": 7, "wq_weights": 8, "dwq": 9}
 
 
 def profile_enable(on: bool = True):

@@ -1514,8 +1514,10 @@ int build_tables(tw_patch *P) {
     k_gauss_tables<<<g2((int64_t)std::max(A.nel, B.nel) * p1), 256, 0, st>>>(A, B);
     TW_LAUNCH();
     const int nw = std::max(A.n, B.n);
+    const int pw = prof_start(st);
     k_wq_weights<<<dim3((nw + TW_WQ_WARPS - 1) / TW_WQ_WARPS, 2), 32 * TW_WQ_WARPS, 0, st>>>(
         A, B, P->flag);
+    prof_stop(pw, TW_STAGE_WQW, st);
     TW_LAUNCH();
   }
   for (int ci = 0; ci < P->curves.n; ci++) {
@@ -1741,9 +1743,11 @@ int build_tables(tw_patch *P) {
         cudaFuncSetAttribute(k_dwq_build, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)TW_DWQ_SMEM);
       });
+      const int pd = prof_start(st);
       k_dwq_build<<<nd, TW_DWQ_THREADS, TW_DWQ_SMEM, st>>>(D, dlist, nd, P->dwq_x[d], P->dwq_np[d], P->dwq_w[d],
                                                  P->dwq_k[d], P->dwq_e[d], P->dwq_B[d],
                                                  P->dwq_r[d], P->flag);
+      prof_stop(pd, TW_STAGE_DWQ, st);
       TW_LAUNCH();
     }
   }
