@@ -148,12 +148,15 @@ typedef struct tw_patch tw_patch;
  *   exactness system Eq. 5 (min-norm solution), basis tables, c at the WQ grid,
  *   classification of elements and functions (Sect. 2.2), the cut-element rules
  *   (Sect. 3.1), the DWQ rules (Sect. 3.3, Eqs. 9-10) and the CSR pattern.
- * Synchronises desc->stream once at the end (sizes).  Returns TW_EINVAL for a
+ * Synchronises desc->stream between stages (table sizes read back) and at the
+ * end (the device-side checks).  Returns TW_EINVAL for a
  * malformed descriptor, TW_EUNSUPPORTED for p outside 1..6, p[0] != p[1] or a
  * curve too complex for one element, TW_ENOMEM / TW_ECUDA otherwise. */
 int tw_patch_create(const tw_patch_desc *desc, tw_patch **out);
-/* Frees the patch's device tables (stream-ordered on the patch's stream).
- * The paper has no counterpart: resource management only. */
+/* Frees the patch's device tables, stream-ordered on the patch's stream: the
+ * call does not wait for the stream, and work already queued there that reads
+ * the tables completes first.  The paper has no counterpart: resource
+ * management only. */
 int tw_patch_destroy(tw_patch *patch);
 
 /* Host copy of the patch sizes (the counts behind Sect. 2.2's split of the

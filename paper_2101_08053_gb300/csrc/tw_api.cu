@@ -260,10 +260,12 @@ extern "C" int tw_profile_read(int stage, double *total_ms, int64_t *count) {
   return TW_OK;
 }
 
+// Stream-ordered: the frees run when the patch's stream reaches them, and no
+// pending work of the patch reads its host structures (every call that copies
+// into them synchronises before it returns), so they are released at once.
 extern "C" int tw_patch_destroy(tw_patch *P) {
   if (!P) return TW_OK;
   for (int k = P->nallocs - 1; k >= 0; k--) cudaFreeAsync(P->allocs[k], P->stream);
-  cudaStreamSynchronize(P->stream);
   free(P->ext);
   free(P);
   return TW_OK;
@@ -328,7 +330,11 @@ extern "C" int tw_patch_create(const tw_patch_desc *desc, tw_patch **out) {
   }
 
   tw_patch *P = (tw_patch *)calloc(1, sizeof(tw_patch));
-  if (P) P->arena_on = 1;
+  if (!P) {
+    set_error("tw_patch_create: out of host memory");
+    return TW_ENOMEM;
+  }
+  P->arena_on = 1;
   P->p = p;
   P->method = desc->method;
   P->qc = desc->cut_order > 0 ? desc->cut_order : p + 1;
@@ -469,7 +475,8 @@ extern "C" int tw_patch_create(const tw_patch_desc *desc, tw_patch **out) {
   return TW_OK;
 fail:
   if (rc == TW_ENOMEM && !g_err[0]) set_error("tw_patch_create: out of device memory");
-  tw_patch_destroy(P);  // synchronises the stream before the staging is freed
+  if (P) cudaStreamSynchronize(P->stream);  // the copies from the staging are done
+  tw_patch_destroy(P);
   free(hbp[0]);
   free(hbp[1]);
   return rc;

@@ -654,8 +654,9 @@ __device__ void interior_tile32(const Dir &A, const Dir &B, const Tables32 &tb,
   const int sho = (int)(base & (AO - 1)), shc = (int)(base & 3);
   // stage 2 (point-major for rows away from the end elements, from vcs) into
   // os: full tiles at CSR position (t W + r2) W + r1 (+ shift), others at
-  // [t][r2][r1].  In FP32 a thread owns two neighbouring r2 of one row
-  constexpr int NRP = SPLIT ? 1 : 2;
+  // [t][r2][r1].  A thread owns one (row, r2) item; in FP32 below p = 6 two
+  // neighbouring r2 of one row (measured faster at p = 4, slower at p = 6)
+  constexpr int NRP = (SPLIT || P >= 6) ? 1 : 2;
   constexpr int WH = (W + NRP - 1) / NRP;
   OutT *os = osb + (full ? sho : 0);
   for (int idx = threadIdx.x; idx < nr * WH; idx += blockDim.x) {

@@ -53,10 +53,10 @@ __global__ void k_band_table(Dir D, float2 *vcf, float *vch) {
 }
 
 // threads of a one-patch block: one per stage-2 item of the tile (a row and
-// two neighbouring r2 in FP32, one r2 in split precision), rounded to warps,
-// so that no phase of the tile leaves a large part of the block waiting
+// one r2; a row and two neighbouring r2 in FP32 below p = 6), rounded to
+// warps, so that no phase of the tile leaves a large part of the block waiting
 __host__ __device__ constexpr int interior32_threads(int P, int T, bool split) {
-  return (T * (split ? 2 * P + 1 : P + 1) + 31) / 32 * 32;
+  return (T * ((split || P >= 6) ? 2 * P + 1 : P + 1) + 31) / 32 * 32;
 }
 
 template <int P, int T, bool SPLIT>

@@ -951,50 +951,87 @@ __global__ void __launch_bounds__(32 * TW_GC_WARPS)
 // ---------------------------------------------------------------------------
 // DWQ (Sect. 3.3)
 
-// R7: region R = R1 x R2 of regular elements with the most elements
-__global__ void k_dwq_choice(Dir A, Dir B, const uint8_t *estate, const uint8_t *fstate,
-                             int32_t *choice, int32_t *dflag0, int32_t *dflag1, int32_t *counter) {
-  int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= A.n * B.n) return;
-  int32_t *out = choice + 4 * g;
-  out[0] = out[1] = out[2] = out[3] = -1;
-  if (fstate[g] != TW_FUNC_CUT) return;
-  int i[2] = {g % A.n, g / A.n};
-  const Dir *D[2] = {&A, &B};
-  int lo[2], hi[2], nopt[2];
-  for (int d = 0; d < 2; d++) {
-    lo[d] = max(0, i[d] - D[d]->p);
-    hi[d] = min(D[d]->nel - 1, i[d]);
-    nopt[d] = 1 + 2 * (hi[d] - lo[d]);
-  }
-  int bestn = 0, bestdisc = 0, bk[2] = {-1, -1}, bs[2] = {-1, -1};
-  for (int oa = 0; oa < nopt[0]; oa++)
-    for (int ob = 0; ob < nopt[1]; ob++) {
-      int kind[2], sv[2], r0[2], r1[2];
-      int oo[2] = {oa, ob};
-      for (int d = 0; d < 2; d++) {
-        int m = hi[d] - lo[d];
-        if (oo[d] == 0) { kind[d] = 0; sv[d] = -1; r0[d] = lo[d]; r1[d] = hi[d]; }
-        else if (oo[d] <= m) { kind[d] = 1; sv[d] = lo[d] + oo[d]; r0[d] = lo[d]; r1[d] = sv[d] - 1; }
-        else { kind[d] = 2; sv[d] = lo[d] + oo[d] - m; r0[d] = sv[d]; r1[d] = hi[d]; }
-      }
-      int nel = (r1[0] - r0[0] + 1) * (r1[1] - r0[1] + 1);
-      int disc = (kind[0] != 0) + (kind[1] != 0);
-      if (nel < bestn || (nel == bestn && disc >= bestdisc && bestn > 0)) continue;
-      int ok = 1;
-      for (int e2 = r0[1]; e2 <= r1[1] && ok; e2++)
-        for (int e1 = r0[0]; e1 <= r1[0] && ok; e1++)
-          ok = estate[e2 * A.nel + e1] == TW_ELEM_REGULAR;
-      if (!ok) continue;
-      bestn = nel;
-      bestdisc = disc;
-      bk[0] = kind[0]; bs[0] = sv[0]; bk[1] = kind[1]; bs[1] = sv[1];
+// R7: region R = R1 x R2 of regular elements with the most elements.  One
+// warp per cut function (from the compacted list of cut functions, count on
+// the device): the support's elements are counted into a 2-D prefix table of
+// non-regular elements, so each candidate's "all regular" test is four
+// lookups; lanes take the candidates c = oa * nopt1 + ob (the order of the
+// tie rules) and a warp max over the key (elements, fewer discs, earlier c)
+// picks the first best candidate.
+#define TW_CHOICE_WARPS 4
+__global__ void __launch_bounds__(32 * TW_CHOICE_WARPS)
+    k_dwq_choice(Dir A, Dir B, const uint8_t *estate, const int32_t *cutfn,
+                 const int32_t *ncutfn, int32_t *choice, int32_t *dflag0, int32_t *dflag1,
+                 int32_t *counter) {
+  constexpr int PW = TW_MAXP1 + 1;  // prefix table width (support <= p+1 elements)
+  __shared__ int pre[TW_CHOICE_WARPS][PW * PW];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int *T = pre[wib];
+  const int nitems = *ncutfn;
+  for (int item = blockIdx.x * TW_CHOICE_WARPS + wib; item < nitems;
+       item += gridDim.x * TW_CHOICE_WARPS) {
+    const int g = cutfn[item];
+    const int i[2] = {g % A.n, g / A.n};
+    const Dir *D[2] = {&A, &B};
+    int lo[2], hi[2], nopt[2];
+    for (int d = 0; d < 2; d++) {
+      lo[d] = max(0, i[d] - D[d]->p);
+      hi[d] = min(D[d]->nel - 1, i[d]);
+      nopt[d] = 1 + 2 * (hi[d] - lo[d]);
     }
-  if (bestn == 0) return;
-  out[0] = bk[0]; out[1] = bs[0]; out[2] = bk[1]; out[3] = bs[1];
-  if (bk[0]) dflag0[bs[0]] = 1;
-  if (bk[1]) dflag1[bs[1]] = 1;
-  atomicAdd(counter, 1);
+    const int w1 = hi[0] - lo[0] + 1, w2 = hi[1] - lo[1] + 1;
+    // T[y][x] = non-regular elements in [lo0, lo0 + x) x [lo1, lo1 + y)
+    for (int t = lane; t < PW * PW; t += 32) T[t] = 0;
+    __syncwarp();
+    for (int t = lane; t < w1 * w2; t += 32) {
+      const int x = t % w1, y = t / w1;
+      T[(y + 1) * PW + x + 1] = estate[(lo[1] + y) * A.nel + lo[0] + x] != TW_ELEM_REGULAR;
+    }
+    __syncwarp();
+    if (lane < w2)  // prefix along x, row by row
+      for (int x = 1; x <= w1; x++) T[(lane + 1) * PW + x] += T[(lane + 1) * PW + x - 1];
+    __syncwarp();
+    if (lane <= w1)  // then along y, column by column
+      for (int y = 1; y <= w2; y++) T[y * PW + lane] += T[(y - 1) * PW + lane];
+    __syncwarp();
+    int best = 0;
+    for (int c = lane; c < nopt[0] * nopt[1]; c += 32) {
+      const int oo[2] = {c / nopt[1], c % nopt[1]};
+      int kind[2], r0[2], r1[2];
+      for (int d = 0; d < 2; d++) {
+        const int m = hi[d] - lo[d];
+        if (oo[d] == 0) { kind[d] = 0; r0[d] = lo[d]; r1[d] = hi[d]; }
+        else if (oo[d] <= m) { kind[d] = 1; r0[d] = lo[d]; r1[d] = lo[d] + oo[d] - 1; }
+        else { kind[d] = 2; r0[d] = lo[d] + oo[d] - m; r1[d] = hi[d]; }
+      }
+      const int x0 = r0[0] - lo[0], x1 = r1[0] - lo[0] + 1;
+      const int y0 = r0[1] - lo[1], y1 = r1[1] - lo[1] + 1;
+      const int bad = T[y1 * PW + x1] - T[y0 * PW + x1] - T[y1 * PW + x0] + T[y0 * PW + x0];
+      if (bad) continue;
+      const int nel = (x1 - x0) * (y1 - y0);
+      const int disc = (kind[0] != 0) + (kind[1] != 0);
+      const int key = (nel << 16) | ((3 - disc) << 10) | (1023 - c);
+      best = max(best, key);
+    }
+    best = __reduce_max_sync(0xffffffffu, best);
+    if (best > 0 && lane == 0) {
+      const int c = 1023 - (best & 1023);
+      const int oo[2] = {c / nopt[1], c % nopt[1]};
+      int out[4];
+      for (int d = 0; d < 2; d++) {
+        const int m = hi[d] - lo[d];
+        if (oo[d] == 0) { out[2 * d] = 0; out[2 * d + 1] = -1; }
+        else if (oo[d] <= m) { out[2 * d] = 1; out[2 * d + 1] = lo[d] + oo[d]; }
+        else { out[2 * d] = 2; out[2 * d + 1] = lo[d] + oo[d] - m; }
+      }
+      int32_t *o = choice + 4 * g;
+      o[0] = out[0]; o[1] = out[1]; o[2] = out[2]; o[3] = out[3];
+      if (out[0]) dflag0[out[1]] = 1;
+      if (out[2]) dflag1[out[3]] = 1;
+      atomicAdd(counter, 1);
+    }
+    __syncwarp();  // T is reused by the warp's next function
+  }
 }
 
 // refined knot vector after inserting t = U[p+s] p more times
@@ -1038,19 +1075,31 @@ __device__ double ref_fn(const Dir &D, int s, int m, double x) {
   return N[a];
 }
 
-// One block per disc knot t = bp[s] of one direction: steps 1-4 of Sect. 3.3.
-// The refined basis is tabulated once per window point and per window Gauss
-// point (shared memory); each refined system is then assembled by lookup and
-// solved by its own thread.
-#define TW_DWQ_THREADS 256  // 8 warps: the 2p refined systems of p <= 4 in one round
+// The DWQ rules of both directions' disc knots, written per direction.
+struct DwqOut {
+  const int32_t *list;  // disc knots s (element index of t = bp[s])
+  int n;
+  double *x, *w, *B;
+  int32_t *np, *k, *e, *r;
+};
+
+// One block per disc knot t = bp[s], the blocks of direction 0 first, then
+// those of direction 1 (one launch for both): steps 1-4 of Sect. 3.3.  The
+// refined basis is tabulated once per window point and per window Gauss point
+// (shared memory); each refined system is then assembled by lookup and solved
+// by its own warp.
+#define TW_DWQ_THREADS 384  // 12 warps: the 2p refined systems of every p <= 6 in one round
 #define TW_DWQ_SMEM (sizeof(double) * (TW_DWQ_THREADS / 32) * TW_WIN * (TW_QMAX + 1))
 __global__ void __launch_bounds__(TW_DWQ_THREADS)
-    k_dwq_build(Dir D, const int32_t *disc_list, int ndisc, double *out_x, int32_t *out_np,
-                double *out_w, int32_t *out_k, int32_t *out_e, double *out_B, int32_t *out_r,
-                int *flag) {
-  int slot = blockIdx.x;
-  if (slot >= ndisc) return;
-  int s = disc_list[slot];
+    k_dwq_build(Dir A, Dir B, DwqOut o0, DwqOut o1, int *flag) {
+  const bool d1 = (int)blockIdx.x >= o0.n;
+  const int slot = d1 ? (int)blockIdx.x - o0.n : (int)blockIdx.x;
+  const DwqOut &O = d1 ? o1 : o0;
+  if (slot >= O.n) return;
+  const Dir &D = d1 ? B : A;
+  double *out_x = O.x, *out_w = O.w, *out_B = O.B;
+  int32_t *out_np = O.np, *out_k = O.k, *out_e = O.e, *out_r = O.r;
+  int s = O.list[slot];
   int p = D.p, p1 = p + 1;
   double t = D.bp[s];
   __shared__ double xs[TW_LQMAX];
@@ -1578,13 +1627,19 @@ int build_tables(tw_patch *P) {
     if (!dflag[d] || !dpos[d]) return TW_ENOMEM;
     cudaMemsetAsync(dflag[d], 0, sizeof(int32_t) * (P->d[d].nel + 1), st);
   }
+  cudaMemsetAsync(P->choice, 0xff, sizeof(int32_t) * 4 * nf, st);
   if (P->method == TW_METHOD_DWQ) {
-    k_dwq_choice<<<G1(nf)>>>(A, B, P->estate, P->fstate, P->choice, dflag[0], dflag[1],
-                             counters + 2);
-  } else {
-    cudaMemsetAsync(P->choice, 0xff, sizeof(int32_t) * 4 * nf, st);
+    // the cut functions (cflag marks exactly those for DWQ) as a list, its
+    // length read by the choice kernel from the scan's total
+    int32_t *cfl = (int32_t *)dalloc(P, sizeof(int32_t) * nf);
+    if (!cfl) return TW_ENOMEM;
+    k_compact<<<G1(nf)>>>(cflag, cpos, cfl, nullptr, nf);
+    TW_LAUNCH();
+    const int nb = (int)std::min<int64_t>((nf + TW_CHOICE_WARPS - 1) / TW_CHOICE_WARPS, 152 * 8);
+    k_dwq_choice<<<nb, 32 * TW_CHOICE_WARPS, 0, st>>>(A, B, P->estate, cfl, tot32 + 1, P->choice,
+                                                       dflag[0], dflag[1], counters + 2);
+    TW_LAUNCH();
   }
-  TW_LAUNCH();
   for (int d = 0; d < 2; d++)
     if ((rc = exclusive_scan_i32(dflag[d], dpos[d], P->d[d].nel + 1, tot32 + 4 + d, st, P)))
       return rc;
@@ -1719,7 +1774,8 @@ int build_tables(tw_patch *P) {
     TW_LAUNCH();
     launch_cut_matrices(P, st);
   }
-  // DWQ rules per disc knot
+  // DWQ rules per disc knot, both directions in one launch
+  DwqOut dout[2];
   for (int d = 0; d < 2; d++) {
     Dir &D = P->d[d];
     int nd = P->ndisc[d];
@@ -1735,21 +1791,22 @@ int build_tables(tw_patch *P) {
     if (!P->dwq_x[d] || !P->dwq_np[d] || !P->dwq_w[d] || !dlist) return TW_ENOMEM;
     k_compact<<<G1(D.nel + 1)>>>(dflag[d], dpos[d], dlist, P->disc_slot[d], D.nel + 1);
     TW_LAUNCH();
-    if (nd > 0) {
-      static std::once_flag dwq_attr[64];
-      int dev = 0;
-      cudaGetDevice(&dev);
-      std::call_once(dwq_attr[dev & 63], [] {
-        cudaFuncSetAttribute(k_dwq_build, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)TW_DWQ_SMEM);
-      });
-      const int pd = prof_start(st);
-      k_dwq_build<<<nd, TW_DWQ_THREADS, TW_DWQ_SMEM, st>>>(D, dlist, nd, P->dwq_x[d], P->dwq_np[d], P->dwq_w[d],
-                                                 P->dwq_k[d], P->dwq_e[d], P->dwq_B[d],
-                                                 P->dwq_r[d], P->flag);
-      prof_stop(pd, TW_STAGE_DWQ, st);
-      TW_LAUNCH();
-    }
+    dout[d] = DwqOut{dlist, nd, P->dwq_x[d], P->dwq_w[d], P->dwq_B[d],
+                     P->dwq_np[d], P->dwq_k[d], P->dwq_e[d], P->dwq_r[d]};
+  }
+  if (P->ndisc[0] + P->ndisc[1] > 0) {
+    static std::once_flag dwq_attr[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::call_once(dwq_attr[dev & 63], [] {
+      cudaFuncSetAttribute(k_dwq_build, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)TW_DWQ_SMEM);
+    });
+    const int pd = prof_start(st);
+    k_dwq_build<<<P->ndisc[0] + P->ndisc[1], TW_DWQ_THREADS, TW_DWQ_SMEM, st>>>(
+        A, B, dout[0], dout[1], P->flag);
+    prof_stop(pd, TW_STAGE_DWQ, st);
+    TW_LAUNCH();
   }
   if ((rc = check_cuda(cudaGetLastError(), "set-up kernels"))) return rc;
   return read_flag(P, "patch set-up");
