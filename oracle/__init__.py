@@ -340,11 +340,28 @@ def curve_area(trim, nsub=8):
 
 # ---- patch -----------------------------------------------------------------
 
+
+def check_knots(U, p):
+    """Open knot vector (p+1 equal end knots, no more), non-decreasing, every
+    interior knot of multiplicity 1..p (continuity C^{p-m}, reading R1)."""
+    if len(U) < 2 * p + 3 or np.any(np.diff(U) < 0):
+        raise ValueError("knots must be non-decreasing with at least two elements")
+    if np.any(U[:p + 1] != U[0]) or np.any(U[-p - 1:] != U[-1]) or not (U[p + 1] > U[0]) \
+            or not (U[-p - 2] < U[-1]):
+        raise ValueError("knot vector is not open (exactly p+1 equal end knots)")
+    inner = U[p + 1:len(U) - p - 1]
+    if inner.size:
+        _, counts = np.unique(inner, return_counts=True)
+        if counts.max() > p:
+            raise ValueError("an interior knot of multiplicity %d > p" % counts.max())
+
 class Patch:
     def __init__(self, spec, omp=False):
         """omp=True builds the patch with the all-cores library (benchmark
         baseline only)."""
         self.spec = spec
+        for U in spec["knots"]:
+            check_knots(np.asarray(U, dtype=np.float64), spec["p"])
         self._L = lib(omp)
         if self._L is None:
             raise RuntimeError("the OpenMP build of the oracle is not available")

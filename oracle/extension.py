@@ -133,6 +133,12 @@ class Extension:
         self.P = P
         p, n1, n2 = P.p, P.n1, P.n2
         U1, U2 = [np.asarray(u, dtype=np.float64) for u in P.spec["knots"]]
+        for U in (U1, U2):
+            inner_knots = U[p + 1:len(U) - p - 1]
+            if inner_knots.size and np.any(np.diff(inner_knots) == 0):
+                # the arrays (R16) are read on simple knots: with a repeated
+                # knot p+1 consecutive functions need not share an element
+                raise ValueError("extended B-splines need simple interior knots")
         es, fs, act = P.states()
         self.act = act
         self.inner, self.outer = classify(P)

@@ -168,14 +168,17 @@ static int mult_of(const double *U, int nk, double v) {
   return m;
 }
 
-/* Reading R1: an element touching a knot of multiplicity p+1 gets p+1 points,
- * every other element 2; points uniform in the element's interior. */
+/* Reading R1: an element touching a knot of multiplicity 2 or more (a domain
+ * end, a repeated interior knot of a mixed-continuity vector, a DWQ disc in
+ * its refined space) gets p+1 points, every other element 2; points uniform
+ * in the element's interior.  The zero-length spans of repeated knots get
+ * none. */
 int or_wq_points(const double *U, int nk, int p, double *x) {
   int cnt = 0;
   for (int j = p; j < nk - p - 1; j++) {
     double a = U[j], b = U[j + 1];
     if (!(b > a)) continue;
-    int m = (mult_of(U, nk, a) == p + 1 || mult_of(U, nk, b) == p + 1) ? p + 1 : 2;
+    int m = (mult_of(U, nk, a) >= 2 || mult_of(U, nk, b) >= 2) ? p + 1 : 2;
     for (int q = 0; q < m; q++) {
       if (x) x[cnt] = a + (b - a) * (double)(q + 1) / (double)(m + 1);
       cnt++;

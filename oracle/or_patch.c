@@ -277,7 +277,12 @@ static void setup_dir(or_patch *P, int dir) {
     for (int g = 0; g < p1; g++) {
       double a = D->bp[e], b = D->bp[e + 1];
       double x = a + (b - a) * 0.5 * (D->gx[g] + 1.0);
-      basis_at(D, e, x, D->GBv + ((size_t)e * p1 + g) * p1, D->GBd + ((size_t)e * p1 + g) * p1);
+      double *v = D->GBv + ((size_t)e * p1 + g) * p1, *dv = D->GBd + ((size_t)e * p1 + g) * p1;
+      if (b > a) {
+        basis_at(D, e, x, v, dv);
+      } else { /* the zero-length span of a repeated knot: nothing lives on it */
+        for (int k = 0; k < p1; k++) v[k] = dv[k] = 0.0;
+      }
     }
 }
 
@@ -310,7 +315,11 @@ static void classify(or_patch *P) {
   int ne = A->nel * B->nel;
   P->estate = (uint8_t *)malloc((size_t)ne);
   if (P->ncurves == 1 && P->d.trim_kind == OR_TRIM_NONE) {
-    memset(P->estate, OR_ELEM_REGULAR, (size_t)ne);
+    for (int e2 = 0; e2 < B->nel; e2++)
+      for (int e1 = 0; e1 < A->nel; e1++)
+        P->estate[e2 * A->nel + e1] =
+            (A->bp[e1 + 1] > A->bp[e1] && B->bp[e2 + 1] > B->bp[e2]) ? OR_ELEM_REGULAR
+                                                                     : OR_ELEM_EMPTY;
   } else {
     /* crossings of the curve with every knot line */
     double *vh = (double *)malloc(sizeof(double) * (size_t)(A->nel + 1) * HITCAP);
@@ -326,6 +335,10 @@ static void classify(or_patch *P) {
     for (int e2 = 0; e2 < B->nel; e2++)
       for (int e1 = 0; e1 < A->nel; e1++) {
         double a1 = A->bp[e1], b1 = A->bp[e1 + 1], a2 = B->bp[e2], b2 = B->bp[e2 + 1];
+        if (!(b1 > a1) || !(b2 > a2)) { /* R1, R8: an empty span has no measure */
+          P->estate[e2 * A->nel + e1] = OR_ELEM_EMPTY;
+          continue;
+        }
         /* R8: a crossing within TW_CORNER of an edge's end is a corner touch,
          * not a cut (keeps the decision off rounding at curves through corners) */
         double d1 = CORNER * (b1 - a1), d2 = CORNER * (b2 - a2);
@@ -357,6 +370,7 @@ static void classify(or_patch *P) {
         for (int e1 = i1 - A->p; e1 <= i1; e1++) {
           if (e1 < 0 || e2 < 0 || e1 >= A->nel || e2 >= B->nel) continue;
           uint8_t s = P->estate[e2 * A->nel + e1];
+          if (s == OR_ELEM_EMPTY) continue; /* R8: the states of the elements with measure */
           tot++;
           if (s == OR_ELEM_REGULAR) nreg++;
           if (s == OR_ELEM_INVISIBLE) ninv++;
@@ -625,9 +639,12 @@ int or_dwq_rule(const or_patch *P, int dir, int s, int side, int i, double *pts,
 
 /* Reading R7: the candidate regions R = R1 x R2, each R_d the whole support
  * (kind 0), its part left of an interior support knot bp[s] (kind 1) or right
- * of it (kind 2).  Valid if every element of R is regular; the valid one with
- * most elements wins, then fewer discs, then the first in the order
- * (kind 0; kind 1 with s ascending; kind 2 with s ascending), direction 1 outer. */
+ * of it (kind 2).  Valid if every element of R is regular (or empty: the
+ * zero-length span of a repeated knot has no measure) and every disc bp[s]
+ * is a simple knot (elements s-1 and s not empty: inserting t p times must
+ * give multiplicity p+1); the valid one with most elements wins, then fewer
+ * discs, then the first in the order (kind 0; kind 1 with s ascending; kind 2
+ * with s ascending), direction 1 outer. */
 static void opt_range(int kind, int s, int lo, int hi, int *r0, int *r1) {
   if (kind == 0) { *r0 = lo; *r1 = hi; }
   else if (kind == 1) { *r0 = lo; *r1 = s - 1; }
@@ -653,9 +670,16 @@ int or_dwq_choice(const or_patch *P, int i1, int i2, int *out) {
       opt_range(opts[0][a][0], opts[0][a][1], lo[0], hi[0], &r0[0], &r1[0]);
       opt_range(opts[1][b][0], opts[1][b][1], lo[1], hi[1], &r0[1], &r1[1]);
       int ok = 1;
+      for (int dd = 0; dd < 2 && ok; dd++) {
+        const dirdata *D = &P->D[dd];
+        int kind = dd == 0 ? opts[0][a][0] : opts[1][b][0], s = dd == 0 ? opts[0][a][1] : opts[1][b][1];
+        if (kind != 0 && !(D->bp[s - 1] < D->bp[s] && D->bp[s] < D->bp[s + 1])) ok = 0;
+      }
       for (int e2 = r0[1]; e2 <= r1[1] && ok; e2++)
-        for (int e1 = r0[0]; e1 <= r1[0] && ok; e1++)
-          if (P->estate[e2 * A->nel + e1] != OR_ELEM_REGULAR) ok = 0;
+        for (int e1 = r0[0]; e1 <= r1[0] && ok; e1++) {
+          uint8_t st = P->estate[e2 * A->nel + e1];
+          if (st != OR_ELEM_REGULAR && st != OR_ELEM_EMPTY) ok = 0;
+        }
       if (!ok) continue;
       int nel = (r1[0] - r0[0] + 1) * (r1[1] - r0[1] + 1);
       int disc = (opts[0][a][0] != 0) + (opts[1][b][0] != 0);
@@ -1237,7 +1261,7 @@ double or_l2_error(const or_patch *Pc, const double *u, const or_func *f, double
   for (int e2 = 0; e2 < B->nel; e2++)
     for (int e1 = 0; e1 < A->nel; e1++) {
       uint8_t st = P->estate[e2 * A->nel + e1];
-      if (st == OR_ELEM_INVISIBLE) continue;
+      if (st == OR_ELEM_INVISIBLE || st == OR_ELEM_EMPTY) continue;
       rbuf R = {0};
       if (st == OR_ELEM_REGULAR) {
         double h1 = A->bp[e1 + 1] - A->bp[e1], h2 = B->bp[e2 + 1] - B->bp[e2];
@@ -1347,7 +1371,7 @@ double or_loss(const or_patch *Pc, const double *u, const or_func *g, double *dL
     for (int e1 = 0; e1 < A->nel; e1++) {
       int e = e2 * A->nel + e1;
       uint8_t st = P->estate[e];
-      if (st == OR_ELEM_INVISIBLE) continue;
+      if (st == OR_ELEM_INVISIBLE || st == OR_ELEM_EMPTY) continue;
       int np = st == OR_ELEM_REGULAR ? p1 * p2 : (int)(P->cut_off[e + 1] - P->cut_off[e]);
       for (int q = 0; q < np; q++) {
         double x[2], om;

@@ -59,6 +59,7 @@
 #define OR_ELEM_INVISIBLE 0
 #define OR_ELEM_REGULAR 1
 #define OR_ELEM_CUT 2
+#define OR_ELEM_EMPTY 3 /* a zero-length span of a repeated knot: no measure */
 #define OR_FUNC_EXTERIOR 0
 #define OR_FUNC_INTERIOR 1
 #define OR_FUNC_CUT 2

@@ -52,6 +52,17 @@ def graded_knots(p: int, nel: int, ratio: float = 1.15, a: float = 0.0, b: float
     return np.array([a] * (p + 1) + list(x[1:-1]) + [b] * (p + 1), dtype=np.float64)
 
 
+def mixed_knots(p: int, nel: int, reps: dict, a: float = 0.0, b: float = 1.0) -> np.ndarray:
+    """Open knot vector over nel equal elements whose k-th interior knot
+    (k = 1 .. nel-1) appears reps.get(k, 1) times: continuity C^{p-m} at a
+    knot of multiplicity m (mixed-continuity cases)."""
+    U = [a] * (p + 1)
+    for k in range(1, nel):
+        U += [a + (b - a) * k / nel] * int(reps.get(k, 1))
+    U += [b] * (p + 1)
+    return np.array(U, dtype=np.float64)
+
+
 def with_knots(spec, U1, U2):
     """The spec on other knot vectors (same degree; nel from the knots)."""
     s = dict(spec)
@@ -105,14 +116,18 @@ def bspline_curve(rng: np.random.Generator, nc=12, radius=0.3, jitter=0.05,
             "keep_inside": keep_inside}
 
 
-def perturbed_bilinear_net(rng: np.random.Generator, p: int, nel: int, amplitude_h=0.05):
+def perturbed_bilinear_net(rng: np.random.Generator, p: int, nel: int, amplitude_h=0.05,
+                           knots=None):
     """Control net P_ij = A(gamma_i1, gamma_i2) + delta_ij: A the bilinear map
     with corners (0,0), (1,0), (1.15,1.1), (0.05,0.95); gamma the Greville
-    abscissae; delta a smooth seeded field of three Fourier modes scaled so
-    that max |delta| = amplitude_h / nel."""
-    U = open_uniform_knots(p, nel)
-    g = greville(U, p)
-    g1, g2 = np.meshgrid(g, g, indexing="xy")  # [i2, i1]
+    abscissae (of open uniform knots, or of knots = (U1, U2)); delta a smooth
+    seeded field of three Fourier modes scaled so that max |delta| =
+    amplitude_h / nel."""
+    if knots is None:
+        ga = gb = greville(open_uniform_knots(p, nel), p)
+    else:
+        ga, gb = greville(np.asarray(knots[0]), p), greville(np.asarray(knots[1]), p)
+    g1, g2 = np.meshgrid(ga, gb, indexing="xy")  # [i2, i1]
     c00, c10, c11, c01 = map(np.array, ([0.0, 0.0], [1.0, 0.0], [1.15, 1.1], [0.05, 0.95]))
     A = ((1 - g1)[..., None] * (1 - g2)[..., None] * c00 + g1[..., None] * (1 - g2)[..., None] * c10
          + g1[..., None] * g2[..., None] * c11 + (1 - g1)[..., None] * g2[..., None] * c01)
