@@ -79,6 +79,7 @@ extern "C" {
 #define TW_ELEM_INVISIBLE 0
 #define TW_ELEM_REGULAR 1
 #define TW_ELEM_CUT 2
+#define TW_ELEM_EMPTY 3  /* zero-length span of a repeated knot: no measure */
 #define TW_FUNC_EXTERIOR 0
 #define TW_FUNC_INTERIOR 1
 #define TW_FUNC_CUT 2
@@ -97,8 +98,14 @@ typedef struct {
 /* Patch descriptor.  Field layout is shared with the CPU oracle's descriptor
  * so that one seeded generator can fill both; the values are the contract.
  *  p[d]          degree per direction, 1..6; p[0] must equal p[1]
- *  knots[d]      open knot vector (p+1 equal end knots, strictly increasing
- *                simple interior knots), nknots[d] = n_d + p + 1, >= 2 elements
+ *  knots[d]      open knot vector: p+1 equal end knots (no more), interior
+ *                knots non-decreasing, each of multiplicity m <= p (continuity
+ *                C^{p-m} there, Sect. 2.1: mixed continuity); nknots[d] =
+ *                n_d + p + 1, >= 2 knot spans.  The elements are the knot
+ *                spans; the zero-length spans of repeated knots are empty
+ *                elements (no quadrature points, state TW_ELEM_EMPTY), and an
+ *                element touching a knot of multiplicity >= 2 carries p+1 WQ
+ *                points (else 2).  Extended B-splines need simple knots.
  *  trim_*        the trimming curve; keep_inside = 0 keeps the outside (a hole)
  *  trim_nextra,  further curves (trim_nextra <= TW_MAXCURVES - 1, host array):
  *  trim_extra    the visible domain is the intersection of every curve's kept

@@ -4,6 +4,7 @@
 // step of the method runs in a kernel.
 #include <cmath>
 #include <cstdarg>
+#include <algorithm>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -130,7 +131,22 @@ void release_to(tw_patch *P, int mark) {
   while (P->nallocs > mark) cudaFreeAsync(P->allocs[--P->nallocs], P->stream);
 }
 
-static int wq_count(int p, int nel) { return 2 * (p + 1) + 2 * (nel - 2); }
+// R1 point counts per knot span: none on the zero-length span of a repeated
+// knot, p+1 on a span touching a knot of multiplicity >= 2 (the domain ends, a
+// repeated interior knot), 2 elsewhere.  cnt[e] for e = 0..nel-1.
+static void wq_counts(const double *U, int nk, int p, int nel, int *cnt) {
+  auto mult = [&](int j) {  // multiplicity of the knot value U[j]
+    int a = j, b = j;
+    while (a > 0 && U[a - 1] == U[j]) a--;
+    while (b + 1 < nk && U[b + 1] == U[j]) b++;
+    return b - a + 1;
+  };
+  for (int e = 0; e < nel; e++) {
+    const int j = p + e;
+    if (!(U[j + 1] > U[j])) cnt[e] = 0;
+    else cnt[e] = (mult(j) >= 2 || mult(j + 1) >= 2) ? p + 1 : 2;
+  }
+}
 
 static int valid_open_knots(const double *U, int nk, int p, const char *what) {
   if (!U) {
@@ -152,9 +168,19 @@ static int valid_open_knots(const double *U, int nk, int p, const char *what) {
       set_error("%s: knot vector is not open (p+1 equal end knots)", what);
       return 0;
     }
+  if (!(U[p + 1] > U[p]) || !(U[nk - 1 - p] > U[nk - 2 - p])) {
+    set_error("%s: knot vector is not open (more than p+1 equal end knots)", what);
+    return 0;
+  }
   for (int k = p; k < nk - p - 1; k++)
-    if (!(U[k + 1] > U[k])) {
-      set_error("%s: interior knots must be strictly increasing (simple)", what);
+    if (U[k + 1] < U[k]) {
+      set_error("%s: knots must be non-decreasing", what);
+      return 0;
+    }
+  // interior knots (positions p+1 .. nk-p-2) of multiplicity m <= p: C^{p-m}
+  for (int k = p + 1; k + p <= nk - p - 2; k++)
+    if (U[k + p] == U[k]) {
+      set_error("%s: interior knot %g of multiplicity > p (C^-1)", what, U[k]);
       return 0;
     }
   return 1;
@@ -344,6 +370,8 @@ extern "C" int tw_patch_create(const tw_patch_desc *desc, tw_patch **out) {
   // host staging of the breakpoints, kept until the set-up's final
   // synchronisation (the copies may read them until then)
   double *hbp[2] = {nullptr, nullptr};
+  int *hoff[2] = {nullptr, nullptr};
+  uint8_t *htwo[2] = {nullptr, nullptr};
 #define ALLOC(ptr, T, n)                                   \
   do {                                                     \
     (ptr) = (T *)dalloc(P, sizeof(T) * (size_t)(n));       \
@@ -356,16 +384,42 @@ extern "C" int tw_patch_create(const tw_patch_desc *desc, tw_patch **out) {
       D.nk = desc->nknots[d];
       D.n = D.nk - p - 1;
       D.nel = D.n - p;
-      D.nq = wq_count(p, D.nel);
+      // the WQ layout (R1) on the host: offsets per element, two-point rows
+      hoff[d] = (int *)malloc(sizeof(int) * (D.nel + 1));
+      htwo[d] = (uint8_t *)malloc((size_t)D.n);
+      if (!hoff[d] || !htwo[d]) {
+        set_error("tw_patch_create: out of host memory");
+        goto fail;
+      }
+      wq_counts(desc->knots[d], D.nk, p, D.nel, hoff[d] + 1);
+      hoff[d][0] = 0;
+      for (int e = 0; e < D.nel; e++) {
+        if (hoff[d][e + 1] == 0) P->mixed = 1;
+        hoff[d][e + 1] += hoff[d][e];
+      }
+      D.nq = hoff[d][D.nel];
       D.qmax = 0;
       for (int i = 0; i < D.n; i++) {
         int lo = i - p < 0 ? 0 : i - p, hi = i < D.nel - 1 ? i : D.nel - 1;
-        auto off = [&](int e) {
-          return e <= 0 ? 0 : (e >= D.nel ? D.nq : (p + 1) + 2 * (e - 1));
-        };
-        int c = off(hi + 1) - off(lo);
+        int c = hoff[d][hi + 1] - hoff[d][lo];
         if (c > D.qmax) D.qmax = c;
+        // point-major rows: away from the end elements, two points in each
+        // support element (every such row for simple knots)
+        bool two = i >= p + 1 && i <= D.nel - 2;
+        for (int e = lo; e <= hi && two; e++) two = hoff[d][e + 1] - hoff[d][e] == 2;
+        htwo[d][i] = two ? 1 : 0;
       }
+      if (d == 0)  // WQ points of the tiles of T consecutive test functions i1
+        for (int lt = 0; lt < 7; lt++) {
+          const int T = 1 << lt;
+          int km = 0;
+          for (int i1a = 0; i1a < D.n; i1a += T) {
+            const int i1b = std::min(D.n, i1a + T);
+            const int k = hoff[d][std::min(D.nel - 1, i1b - 1) + 1] - hoff[d][std::max(0, i1a - p)];
+            km = std::max(km, k);
+          }
+          P->ktile[lt] = km;
+        }
       if (D.qmax > TW_QMAX) {
         set_error("tw_patch_create: %d WQ points in one support exceed %d", D.qmax, TW_QMAX);
         rc = TW_EUNSUPPORTED;
@@ -385,6 +439,10 @@ extern "C" int tw_patch_create(const tw_patch_desc *desc, tw_patch **out) {
       ALLOC(D.crange, int, (size_t)D.n * W);
       ALLOC(D.GB, double, (size_t)D.nel * (p + 1) * (p + 1));
       ALLOC(D.dGB, double, (size_t)D.nel * (p + 1) * (p + 1));
+      ALLOC(D.qoff, int, D.nel + 1);
+      ALLOC(D.two, uint8_t, D.n);
+      cudaMemcpyAsync(D.qoff, hoff[d], sizeof(int) * (D.nel + 1), cudaMemcpyHostToDevice, st);
+      cudaMemcpyAsync(D.two, htwo[d], (size_t)D.n, cudaMemcpyHostToDevice, st);
       hbp[d] = (double *)malloc(sizeof(double) * (D.nel + 1));
       if (!hbp[d]) {
         set_error("tw_patch_create: out of host memory");
@@ -396,6 +454,7 @@ extern "C" int tw_patch_create(const tw_patch_desc *desc, tw_patch **out) {
     }
     Dir &A = P->d[0];
     Dir &B = P->d[1];
+    A.mixed = B.mixed = P->mixed;
     // curves (the untrimmed kind left out)
     P->curves.n = 0;
     for (int k = -1; k < desc->trim_nextra; k++) {
@@ -469,16 +528,22 @@ extern "C" int tw_patch_create(const tw_patch_desc *desc, tw_patch **out) {
   }
 #undef ALLOC
   P->arena_on = 0;
-  free(hbp[0]);  // build_tables ended with a synchronisation of the stream
-  free(hbp[1]);
+  for (int d = 0; d < 2; d++) {  // build_tables ended with a synchronisation of the stream
+    free(hbp[d]);
+    free(hoff[d]);
+    free(htwo[d]);
+  }
   *out = P;
   return TW_OK;
 fail:
   if (rc == TW_ENOMEM && !g_err[0]) set_error("tw_patch_create: out of device memory");
   if (P) cudaStreamSynchronize(P->stream);  // the copies from the staging are done
   tw_patch_destroy(P);
-  free(hbp[0]);
-  free(hbp[1]);
+  for (int d = 0; d < 2; d++) {
+    free(hbp[d]);
+    free(hoff[d]);
+    free(htwo[d]);
+  }
   return rc;
 }
 

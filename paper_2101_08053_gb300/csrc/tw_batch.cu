@@ -49,10 +49,11 @@ __device__ __forceinline__ void run_interior(const BatchPatch &b, int i2, int i1
   const RowArgs &a = b.ra;
   if constexpr (PREC == TW_PREC_FP64)
     interior_tile<P>(a.A, a.B, a.C, a.fstate, a.act, a.rp, b.col, (double *)b.val, i2, i1a, T,
-                     smem);
+                     smem, interior_kmax(P, T), a.A.mixed != 0);
   else
     interior_tile32<P, PREC == TW_PREC_FP32X2>(a.A, a.B, b.tb, a.fstate, a.act, a.rp, b.col,
-                                               b.val, i2, i1a, T, smem, bar, phase, a.flag);
+                                               b.val, i2, i1a, T, smem, bar, phase, a.flag,
+                                               a.A.mixed != 0);
 }
 
 template <int PREC, int P>
@@ -293,6 +294,16 @@ extern "C" int tw_batch_create(tw_patch *const *patches, int n, int precision,
       set_error("tw_batch_create: patch %d or its outputs are NULL", k);
       return TW_EINVAL;
     }
+    // the persistent kernel carves tiles of 16, 32 or 64 rows with the static
+    // bound on their WQ points (simple knots always fit; a mixed-continuity
+    // patch with many points next to repeated knots may not)
+    for (int lt = 4; lt <= 6; lt++)
+      if (P->ktile[lt] > interior_kmax(P->p, 1 << lt)) {
+        set_error("tw_batch_create: patch %d has %d WQ points under a tile of %d rows, beyond "
+                  "the batch's %d (form it with tw_form_mass)",
+                  k, P->ktile[lt], 1 << lt, interior_kmax(P->p, 1 << lt));
+        return TW_EUNSUPPORTED;
+      }
     if (precision != TW_PREC_FP64) {
       if (P->d[0].qmax > 4 * P->p || P->d[1].qmax > 4 * P->p) {
         set_error("tw_batch_create: patch %d has more than 4p WQ points in one support", k);

@@ -461,6 +461,36 @@ __device__ void cutrow_item(const RowArgs &a, int g, int32_t *__restrict__ col,
   __syncthreads();  // smem reused by the next item
 }
 
+// One interior row whose band holds inactive neighbours (possible only with a
+// repeated knot, where j may share just the empty span with B_i): the active
+// entries in ascending column order, positions from one ballot per 32
+// entries.  src is the row's [r2][r1] block; called by a whole warp.
+template <int P, typename OutT>
+__device__ __forceinline__ void band_write_compact(const OutT *src, const int32_t *__restrict__ act,
+                                                   int n1, int lo1, int w1, int d1, int lo2,
+                                                   int w2, int d2, int64_t rowbase, int lane,
+                                                   int32_t *__restrict__ col,
+                                                   OutT *__restrict__ val) {
+  constexpr int W = 2 * P + 1;
+  int64_t pos = rowbase;
+  for (int k0 = 0; k0 < w1 * w2; k0 += 32) {
+    const int k = k0 + lane;
+    int ja = -1, q1 = 0, q2 = 0;
+    if (k < w1 * w2) {
+      q2 = k / w1;
+      q1 = k - q2 * w1;
+      ja = act[(lo2 + q2) * n1 + lo1 + q1];
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, ja >= 0);
+    if (ja >= 0) {
+      const int64_t ps = pos + __popc(m & ((1u << lane) - 1u));
+      val[ps] = src[(q2 + d2) * W + q1 + d1];
+      col[ps] = ja;
+    }
+    pos += __popc(m);
+  }
+}
+
 // s = (sh, sl) += a * b, a and b pairs; products and sums error-free in the
 // leading parts (__fmul_rn / __fadd_rn are never contracted into FMAs)
 __device__ __forceinline__ void df_fma(float2 a, float2 b, float &sh, float &sl) {
@@ -500,28 +530,35 @@ struct Tables32 {
 //   cs    their columns (+ the same)
 //   sc    the tile's scalars, the band ranges of row i2, per row the interior
 //         flag and the first WQ point
+// kmax bounds the WQ points under the tile's rows (odd; the static bound for
+// simple knots), q those of one support (4P for simple knots); a
+// mixed-continuity vector passes its own, larger bounds.
 __host__ __device__ constexpr int interior32_kmax(int P, int T) { return (2 * T + 4 * P + 4) | 1; }
 __host__ __device__ constexpr size_t a16(size_t x) { return (x + 15) / 16 * 16; }
-__host__ __device__ constexpr size_t interior32_slab_cols(int P, int T) {
-  return (size_t)interior32_kmax(P, T) + 8;  // columns rounded out to 16 bytes on both sides
+__host__ __device__ constexpr size_t interior32_slab_cols(int kmax) {
+  return (size_t)kmax + 8;  // columns rounded out to 16 bytes on both sides
 }
 struct Layout32 {
   size_t slab, vc, y, v2, os, cs, cr2, total;
 };
-__host__ __device__ constexpr Layout32 interior32_layout(int P, int T, bool split) {
+__host__ __device__ constexpr Layout32 interior32_layout(int P, int T, bool split, int kmax,
+                                                         int q) {
   const size_t e = split ? sizeof(float2) : sizeof(float);
   const size_t o = split ? sizeof(double) : sizeof(float);
-  const int W = 2 * P + 1, Q = 4 * P;  // Q bounds the WQ points of one support
+  const int W = 2 * P + 1, Q = q;  // Q bounds the WQ points of one support
   Layout32 L{};
   L.slab = 0;
-  L.vc = L.slab + a16(e * Q * interior32_slab_cols(P, T));
+  L.vc = L.slab + a16(e * Q * interior32_slab_cols(kmax));
   L.y = L.vc + a16(e * (size_t)T * (2 * P + 2) * (P + 1));
-  L.v2 = L.y + a16(e * (size_t)W * interior32_kmax(P, T));
+  L.v2 = L.y + a16(e * (size_t)W * kmax);
   L.os = L.v2 + a16(e * (size_t)Q * W);
   L.cs = L.os + a16(o * ((size_t)T * W * W + 16 / o));
   L.cr2 = L.cs + a16(sizeof(int) * ((size_t)T * W * W + 4));
   L.total = L.cr2 + a16(sizeof(int) * (8 + W + 2 * (size_t)T));
   return L;
+}
+__host__ __device__ constexpr Layout32 interior32_layout(int P, int T, bool split) {
+  return interior32_layout(P, T, split, interior32_kmax(P, T), 4 * P);
 }
 __host__ __device__ constexpr size_t interior32_smem(int P, int T, bool split = true) {
   return interior32_layout(P, T, split).total;
@@ -542,13 +579,15 @@ __device__ void interior_tile32(const Dir &A, const Dir &B, const Tables32 &tb,
                                 const int32_t *__restrict__ act, const int64_t *__restrict__ rp,
                                 int32_t *__restrict__ col, void *__restrict__ valv, int i2,
                                 int i1a, int T, char *smem, uint64_t *bar, uint32_t *phase,
-                                int *flag) {
+                                int *flag, bool mixed, int kmax = 0, int q = 0) {
   constexpr int W = 2 * P + 1, NV = (2 * P + 2) * (P + 1);
   using ET = typename std::conditional<SPLIT, float2, float>::type;
   using OutT = typename std::conditional<SPLIT, double, float>::type;
   constexpr int AE = 16 / (int)sizeof(ET);    // elements per 16 bytes of a table
   constexpr int AO = 16 / (int)sizeof(OutT);  // of the outputs
-  const Layout32 L = interior32_layout(P, T, SPLIT);
+  if (kmax <= 0) kmax = interior32_kmax(P, T);
+  if (q <= 0) q = 4 * P;
+  const Layout32 L = interior32_layout(P, T, SPLIT, kmax, q);
   ET *slab = (ET *)(smem + L.slab);
   ET *vcs = (ET *)(smem + L.vc);
   ET *Y = (ET *)(smem + L.y);
@@ -559,7 +598,7 @@ __device__ void interior_tile32(const Dir &A, const Dir &B, const Tables32 &tb,
   int *sc = (int *)(smem + L.cr2);
   int *cr2 = sc + 8;
   int *rowint = cr2 + W, *rowq = rowint + T;
-  const int KMAX = interior32_kmax(P, T);
+  const int KMAX = kmax;
   const int i1b = min(A.n, i1a + T);
   const int nr = i1b - i1a;
   const int n1 = A.n;
@@ -577,11 +616,15 @@ __device__ void interior_tile32(const Dir &A, const Dir &B, const Tables32 &tb,
   }
   __syncthreads();
   for (int t = threadIdx.x; t < nr; t += blockDim.x) {
-    const bool in = fstate[i2 * n1 + i1a + t] == TW_FUNC_INTERIOR;
+    const int g = i2 * n1 + i1a + t;
+    const bool in = fstate[g] == TW_FUNC_INTERIOR;
     rowint[t] = in ? 1 : 0;
     rowq[t] = A.qbeg[i1a + t];
     if (in) sc[0] = 1;
-    else sc[1] = 0;
+    // a full tile needs every row's whole band active: always so for simple
+    // knots; with a repeated knot a band neighbour may share only the empty
+    // span with B_i and be exterior
+    if (!in || (mixed && rp[act[g] + 1] - rp[act[g]] != (int64_t)W * W)) sc[1] = 0;
   }
   __syncthreads();
   if (!sc[0]) return;  // uniform across the block
@@ -672,7 +715,7 @@ __device__ void interior_tile32(const Dir &A, const Dir &B, const Tables32 &tb,
     const ET *yb = Y + (vb ? r2b : r2a) * KMAX + yo;
     OutT *oa = os + ((size_t)t * W + r2a) * W;
     OutT *ob = oa + W;
-    if (i1 >= P + 1 && i1 <= A.nel - 2) {
+    if (i1 >= P + 1 && i1 <= A.nel - 2 && (!mixed || A.two[i1])) {
       const ET *v = vcs + (size_t)t * NV;
       float aha[W], ala[W], ahb[W], alb[W];
 #pragma unroll
@@ -776,10 +819,14 @@ __device__ void interior_tile32(const Dir &A, const Dir &B, const Tables32 &tb,
       const int lo1 = max(0, i1 - P), w1 = min(n1 - 1, i1 + P) - lo1 + 1, d1 = lo1 - (i1 - P);
       const int64_t rowbase = rp[act[g]];
       const OutT *src = os + (size_t)t * W * W;
-      for (int k = lane; k < w1 * w2; k += 32) {
-        const int q2 = k / w1, q1 = k - q2 * w1;
-        val[rowbase + k] = src[(q2 + d2) * W + q1 + d1];
-        col[rowbase + k] = act[(lo2 + q2) * n1 + lo1 + q1];
+      if (!mixed || rp[act[g] + 1] - rowbase == (int64_t)w1 * w2) {  // whole band active
+        for (int k = lane; k < w1 * w2; k += 32) {
+          const int q2 = k / w1, q1 = k - q2 * w1;
+          val[rowbase + k] = src[(q2 + d2) * W + q1 + d1];
+          col[rowbase + k] = act[(lo2 + q2) * n1 + lo1 + q1];
+        }
+      } else {
+        band_write_compact<P>(src, act, n1, lo1, w1, d1, lo2, w2, d2, rowbase, lane, col, val);
       }
     }
   }

@@ -723,6 +723,10 @@ extern "C" int tw_extension_build(tw_patch *P, int64_t *info4) {
     set_error("tw_extension_build: NULL argument");
     return TW_EINVAL;
   }
+  if (P->mixed) {  // R16's arrays are read on simple knots
+    set_error("tw_extension_build: extended B-splines need simple interior knots");
+    return TW_EUNSUPPORTED;
+  }
   if (!P->ext) {
     const int mark = P->nallocs;
     int rc = ext_build_impl(P);

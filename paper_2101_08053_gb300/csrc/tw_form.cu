@@ -20,6 +20,8 @@
 //                   a region): one warp per row gathers the element rows.
 //                   Every output is owned by one thread and summed in a fixed
 //                   order, so the matrix is bitwise reproducible.
+#include <algorithm>
+
 #include "tw_bodies.cuh"
 
 namespace tw {
@@ -194,7 +196,8 @@ __global__ void k_copy_i64(const int64_t *src, int64_t *dst, int64_t n) {
 template <int P>
 static int launch_form(tw_patch *Pt, int precision, int64_t *rp, int32_t *col, void *valv,
                        cudaStream_t s, bool rowsf) {
-  constexpr int T = P <= 5 ? 32 : 16;  // the tile's output buffer stays within static smem
+  constexpr int T = P <= 5 ? 32 : 16;  // the tile's output buffer stays within 48 KB
+  constexpr int LT = P <= 5 ? 5 : 4;   // log2 T
   Dir &A = Pt->d[0];
   Dir &B = Pt->d[1];
   double *val = (double *)valv;
@@ -203,8 +206,23 @@ static int launch_form(tw_patch *Pt, int precision, int64_t *rp, int32_t *col, v
     if (rc) return rc;
   } else if (Pt->method != TW_METHOD_GAUSS && Pt->n_interior > 0) {
     dim3 grid((A.n + T - 1) / T, B.n);
+    // the stage-1 buffer holds the WQ points under a tile: the static bound
+    // for simple knots, the patch's own (odd) for a mixed-continuity vector
+    const int kmax = std::max(interior_kmax(P, T), Pt->ktile[LT] | 1);
+    const size_t smem = interior_smem(P, T, kmax);
     int ps = prof_start(s);
-    k_interior<P, T><<<grid, 256, 0, s>>>(A, B, Pt->C, Pt->fstate, Pt->act, Pt->row_ptr, col, val);
+    if (!Pt->mixed) {
+      k_interior<P, T, false><<<grid, 256, 0, s>>>(A, B, Pt->C, Pt->fstate, Pt->act,
+                                                   Pt->row_ptr, col, val, kmax);
+    } else {
+      if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(
+            k_interior<P, T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return check_cuda(e, "interior contraction: shared memory");
+      }
+      k_interior<P, T, true><<<grid, 256, smem, s>>>(A, B, Pt->C, Pt->fstate, Pt->act,
+                                                     Pt->row_ptr, col, val, kmax);
+    }
     prof_stop(ps, TW_STAGE_INTERIOR, s);
     TW_LAUNCH();
   }

@@ -14,6 +14,8 @@
 // stages its slab of c and its rows of band values in shared memory with bulk
 // copies and, when its CSR range is contiguous, writes it with bulk copies
 // (interior_tile32).  Cut rows always run in FP64 (k_cutrows).
+#include <algorithm>
+
 #include "tw_bodies.cuh"
 
 namespace tw {
@@ -29,6 +31,16 @@ __global__ void k_split_table(const double *src, float2 *dst, int64_t n) {
   if (i < n) dst[i] = split_f64(src[i]);
 }
 
+// c as (hi, lo) float pairs with rows padded to ld pairs, so that every row
+// starts on 16 bytes for the bulk copies (the pad columns are zero; nq1 is odd
+// for some mixed-continuity vectors)
+__global__ void k_split_rows(const double *src, float2 *dst, int n1, int n2, int ld) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)n2 * ld) return;
+  const int k2 = (int)(i / ld), k1 = (int)(i % ld);
+  dst[i] = k1 < n1 ? split_f64(src[(size_t)k2 * n1 + k1]) : make_float2(0.f, 0.f);
+}
+
 // c rounded to float with rows padded to ld (the pad columns are zero)
 __global__ void k_round_rows(const double *src, float *dst, int n1, int n2, int ld) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -39,14 +51,15 @@ __global__ void k_round_rows(const double *src, float *dst, int n1, int n2, int 
 
 // Vc[i][c1][a] = V[i][c1][c1 / 2 + a], a = 0..P: the band values that can be
 // nonzero at point c1 of supp B_i when every support element holds two points
-// (rows P+1 .. nel-2); zero elsewhere and in the pad row n
+// (D.two: rows P+1 .. nel-2 for simple knots); zero elsewhere and in the pad
+// row n
 __global__ void k_band_table(Dir D, float2 *vcf, float *vch) {
   const int P = D.p, W = 2 * P + 1, NV = (2 * P + 2) * (P + 1);
   int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (id >= (int64_t)(D.n + 1) * NV) return;
   const int i = (int)(id / NV), r = (int)(id % NV), c1 = r / (P + 1), a = r % (P + 1);
   double v = 0.0;
-  if (i >= P + 1 && i <= D.nel - 2) v = D.V[((size_t)i * D.qmax + c1) * W + c1 / 2 + a];
+  if (i < D.n && D.two[i]) v = D.V[((size_t)i * D.qmax + c1) * W + c1 / 2 + a];
   const float2 h = split_f64(v);
   vcf[id] = h;
   vch[id] = h.x;
@@ -59,21 +72,23 @@ __host__ __device__ constexpr int interior32_threads(int P, int T, bool split) {
   return (T * ((split || P >= 6) ? 2 * P + 1 : P + 1) + 31) / 32 * 32;
 }
 
-template <int P, int T, bool SPLIT>
+// MIXED: the patch has a repeated knot (runtime layout from kmax and q, the
+// two-point and whole-band tests); otherwise the static layout of simple knots
+template <int P, int T, bool SPLIT, bool MIXED>
 __global__ void __launch_bounds__(interior32_threads(P, T, SPLIT))
     k_interior32(Dir A, Dir B, Tables32 tb,
                                                     const uint8_t *__restrict__ fstate,
                                                     const int32_t *__restrict__ act,
                                                     const int64_t *__restrict__ rp,
                                                     int32_t *__restrict__ col, void *__restrict__ valv,
-                                                    int *flag) {
+                                                    int *flag, int kmax, int q) {
   extern __shared__ __align__(16) char smem[];
   __shared__ uint64_t bar;
   if (threadIdx.x == 0) mbar_init(&bar);
   __syncthreads();
   uint32_t phase = 0;
   interior_tile32<P, SPLIT>(A, B, tb, fstate, act, rp, col, valv, blockIdx.y, blockIdx.x * T, T,
-                            smem, &bar, &phase, flag);
+                            smem, &bar, &phase, flag, MIXED, MIXED ? kmax : 0, MIXED ? q : 0);
 }
 
 // split the patch's tables on first use (patch-owned)
@@ -85,8 +100,8 @@ int ensure_split_tables(tw_patch *P, cudaStream_t s) {
   P->stream = s;
   const int W = 2 * P->p + 1;
   const int NV = (2 * P->p + 2) * (P->p + 1);
-  const int ldh = (A.nq + 3) & ~3;
-  int64_t nc = (int64_t)A.nq * B.nq, nh = (int64_t)B.nq * ldh;
+  const int ldh = (A.nq + 3) & ~3, ldf = (A.nq + 1) & ~1;  // 16-byte rows
+  int64_t nc = (int64_t)B.nq * ldf, nh = (int64_t)B.nq * ldh;
   int64_t nv[2] = {(int64_t)A.n * A.qmax * W, (int64_t)B.n * B.qmax * W};
   int64_t nb = (int64_t)(A.n + 1) * NV;
   float2 *cf = (float2 *)dalloc(P, sizeof(float2) * nc);
@@ -97,7 +112,7 @@ int ensure_split_tables(tw_patch *P, cudaStream_t s) {
   float *vch = (float *)dalloc(P, sizeof(float) * nb);
   P->stream = keep;
   if (!cf || !v0 || !v1 || !ch || !vcf || !vch) return TW_ENOMEM;
-  k_split_table<<<(unsigned)((nc + 255) / 256), 256, 0, s>>>(P->C, cf, nc);
+  k_split_rows<<<(unsigned)((nc + 255) / 256), 256, 0, s>>>(P->C, cf, A.nq, B.nq, ldf);
   TW_LAUNCH();
   k_split_table<<<(unsigned)((nv[0] + 255) / 256), 256, 0, s>>>(A.V, v0, nv[0]);
   TW_LAUNCH();
@@ -108,6 +123,7 @@ int ensure_split_tables(tw_patch *P, cudaStream_t s) {
   k_band_table<<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(A, vcf, vch);
   TW_LAUNCH();
   P->Cf = cf;
+  P->ldf = ldf;
   P->Vf[0] = v0;
   P->Vf[1] = v1;
   P->Ch = ch;
@@ -120,7 +136,7 @@ int ensure_split_tables(tw_patch *P, cudaStream_t s) {
 Tables32 tables32(const tw_patch *P, bool split, const void *col, const void *val) {
   Tables32 tb;
   tb.C = split ? (const void *)P->Cf : (const void *)P->Ch;
-  tb.ldc = split ? P->d[0].nq : P->ldh;
+  tb.ldc = split ? P->ldf : P->ldh;
   tb.Vc1 = split ? (const void *)P->Vcf : (const void *)P->Vch;
   tb.V1f = P->Vf[0];
   tb.V2f = P->Vf[1];
@@ -134,16 +150,32 @@ Tables32 tables32(const tw_patch *P, bool split, const void *col, const void *va
 template <int P, bool SPLIT>
 static cudaError_t launch32_t(tw_patch *Pt, int32_t *col, void *val, cudaStream_t s) {
   constexpr int T = (SPLIT ? 16 : 32) / (P <= 5 ? 1 : 2);
-  constexpr size_t smem = interior32_smem(P, T, SPLIT);
-  static_assert(smem <= 200 * 1024, "FP32-pipe tile exceeds shared memory");
-  cudaError_t e = cudaFuncSetAttribute(k_interior32<P, T, SPLIT>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
+  constexpr int LT = (SPLIT ? 4 : 5) - (P <= 5 ? 0 : 1);  // log2 T
+  static_assert(interior32_smem(P, T, SPLIT) <= 200 * 1024, "FP32-pipe tile exceeds shared memory");
   Dir &A = Pt->d[0];
   Dir &B = Pt->d[1];
-  k_interior32<P, T, SPLIT><<<dim3((A.n + T - 1) / T, B.n), interior32_threads(P, T, SPLIT), smem,
-                              s>>>(
-      A, B, tables32(Pt, SPLIT, col, val), Pt->fstate, Pt->act, Pt->row_ptr, col, val, Pt->flag);
+  // the static bounds for simple knots; a mixed-continuity vector's own
+  const int kmax = std::max(interior32_kmax(P, T), Pt->ktile[LT] | 1);
+  const int q = std::max(4 * P, std::max(A.qmax, B.qmax));
+  const dim3 grid((A.n + T - 1) / T, B.n);
+  const int nt = interior32_threads(P, T, SPLIT);
+  const Tables32 tb = tables32(Pt, SPLIT, col, val);
+  if (!Pt->mixed) {
+    constexpr size_t smem = interior32_smem(P, T, SPLIT);
+    cudaError_t e = cudaFuncSetAttribute(k_interior32<P, T, SPLIT, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_interior32<P, T, SPLIT, false><<<grid, nt, smem, s>>>(A, B, tb, Pt->fstate, Pt->act,
+                                                            Pt->row_ptr, col, val, Pt->flag, 0, 0);
+    return cudaSuccess;
+  }
+  const size_t smem = interior32_layout(P, T, SPLIT, kmax, q).total;
+  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+  cudaError_t e = cudaFuncSetAttribute(k_interior32<P, T, SPLIT, true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_interior32<P, T, SPLIT, true><<<grid, nt, smem, s>>>(A, B, tb, Pt->fstate, Pt->act,
+                                                         Pt->row_ptr, col, val, Pt->flag, kmax, q);
   return cudaSuccess;
 }
 
@@ -156,11 +188,6 @@ int launch_interior32(tw_patch *P, int precision, int32_t *col, void *val, cudaS
   int rc = ensure_split_tables(P, s);
   if (rc) return rc;
   if (P->n_interior == 0) return 0;
-  if (P->d[0].qmax > 4 * P->p || P->d[1].qmax > 4 * P->p) {
-    set_error("interior contraction: %d / %d WQ points in one support exceed 4p", P->d[0].qmax,
-              P->d[1].qmax);
-    return TW_EUNSUPPORTED;
-  }
   bool split = precision == TW_PREC_FP32X2;
   int ps = prof_start(s);
   cudaError_t e = cudaErrorInvalidValue;

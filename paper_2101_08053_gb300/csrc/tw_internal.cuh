@@ -49,7 +49,10 @@ struct Curve {
 
 struct Dir {
   int p, n, nel, nk, nq, qmax;
+  int mixed;    // the patch has a repeated interior knot (either direction)
   double *U, *bp;
+  int *qoff;    // nel+1: first WQ point of each element (R1; empty spans hold none)
+  uint8_t *two; // n: every element of supp B_i holds exactly two points
   double *xq;   // nq
   int *qel;     // nq
   int *qbeg;    // n
@@ -731,6 +734,8 @@ static __device__ double warp_minnorm(int m, int N, double *A, int lda, const do
 // the patch object (host struct with device pointers)
 struct tw_patch {
   int p, method, qc;
+  int ktile[7];  // most WQ points of direction 0 under a tile of 2^k test functions i1
+  int mixed;     // some knot span is empty (a repeated interior knot)
   tw::Dir d[2];
   const double *qrule;  // cut-piece Gauss rule (cached, not owned)
   tw::CurveSet curves;
@@ -781,7 +786,7 @@ struct tw_patch {
   float2 *Cf;        // c on the WQ grid as hi/lo FP32 pairs (created on first FP32 form)
   float2 *Vf[2];     // weighted basis tables as hi/lo FP32 pairs
   float *Ch;         // c rounded to float, rows padded to ldh (a multiple of 4)
-  int ldh;
+  int ldh, ldf;      // ldf: the row stride of Cf in pairs (even)
   float2 *Vcf;       // direction-1 band values per (function, point) as pairs ((n1+1) rows)
   float *Vch;        // the same rounded to float
   int ndwqrows;

@@ -15,12 +15,12 @@
 
 namespace tw {
 
-// point offset of element e in the WQ layout (R1): elements 0 and nel-1
-// touch the (p+1)-fold end knots and carry p+1 points, every other element 2
-__host__ __device__ __forceinline__ int wq_off(int e, int p, int nel) {
-  if (e <= 0) return 0;
-  if (e >= nel) return 2 * (p + 1) + 2 * (nel - 2);
-  return (p + 1) + 2 * (e - 1);
+// point offset of element e in the WQ layout (R1, the table D.qoff built
+// from the knots): p+1 points in an element touching a knot of multiplicity
+// >= 2 (the domain ends, repeated interior knots), none on the zero-length
+// span of a repeated knot, 2 elsewhere
+__device__ __forceinline__ int wq_off(const Dir &D, int e) {
+  return D.qoff[e <= 0 ? 0 : (e >= D.nel ? D.nel : e)];
 }
 
 // ---------------------------------------------------------------------------
@@ -141,27 +141,25 @@ __global__ void k_gauss_nodes(int q, double *x, double *w) {
 
 // the per-direction table kernels run both directions in one launch:
 // blockIdx.y picks the direction
+// thread per element: its m = qoff[e+1] - qoff[e] points (R1), uniform in
+// the element's interior, with the basis and derivatives there
 __global__ void k_wq_points(Dir D0, Dir D1) {
   const Dir &D = blockIdx.y ? D1 : D0;
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= D.nq) return;
-  int p = D.p, e, j, m;
-  if (k < p + 1) {
-    e = 0; j = k; m = p + 1;
-  } else if (k >= D.nq - (p + 1)) {
-    e = D.nel - 1; j = k - (D.nq - p - 1); m = p + 1;
-  } else {
-    e = 1 + (k - p - 1) / 2; j = (k - p - 1) % 2; m = 2;
-  }
-  double a = D.bp[e], b = D.bp[e + 1];
-  double x = a + (b - a) * (double)(j + 1) / (double)(m + 1);
-  D.xq[k] = x;
-  D.qel[k] = e;
-  double N[TW_MAXP1], dN[TW_MAXP1];
-  basis_ders(D.U, e + p, x, p, N, dN);
-  for (int a2 = 0; a2 <= p; a2++) {
-    D.Bq[k * (p + 1) + a2] = N[a2];
-    D.dBq[k * (p + 1) + a2] = dN[a2];
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= D.nel) return;
+  const int p = D.p, k0 = D.qoff[e], m = D.qoff[e + 1] - k0;
+  const double a = D.bp[e], b = D.bp[e + 1];
+  for (int j = 0; j < m; j++) {
+    const int k = k0 + j;
+    const double x = a + (b - a) * (double)(j + 1) / (double)(m + 1);
+    D.xq[k] = x;
+    D.qel[k] = e;
+    double N[TW_MAXP1], dN[TW_MAXP1];
+    basis_ders(D.U, e + p, x, p, N, dN);
+    for (int a2 = 0; a2 <= p; a2++) {
+      D.Bq[k * (p + 1) + a2] = N[a2];
+      D.dBq[k * (p + 1) + a2] = dN[a2];
+    }
   }
 }
 
@@ -170,8 +168,8 @@ __global__ void k_wq_ranges(Dir D0, Dir D1) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= D.n) return;
   int lo = max(0, i - D.p), hi = min(D.nel - 1, i);
-  D.qbeg[i] = wq_off(lo, D.p, D.nel);
-  D.qcnt[i] = wq_off(hi + 1, D.p, D.nel) - D.qbeg[i];
+  D.qbeg[i] = wq_off(D, lo);
+  D.qcnt[i] = wq_off(D, hi + 1) - D.qbeg[i];
 }
 
 __global__ void k_gauss_tables(Dir D0, Dir D1) {
@@ -183,7 +181,11 @@ __global__ void k_gauss_tables(Dir D0, Dir D1) {
   double a = D.bp[e], b = D.bp[e + 1];
   double x = a + (b - a) * 0.5 * (D.gx[g] + 1.0);
   double N[TW_MAXP1], dN[TW_MAXP1];
-  basis_ders(D.U, e + D.p, x, D.p, N, dN);
+  if (b > a) {
+    basis_ders(D.U, e + D.p, x, D.p, N, dN);
+  } else {  // the zero-length span of a repeated knot: nothing lives on it
+    for (int k = 0; k < p1; k++) N[k] = dN[k] = 0.0;
+  }
   for (int k = 0; k < p1; k++) {
     D.GB[(e * p1 + g) * p1 + k] = N[k];
     D.dGB[(e * p1 + g) * p1 + k] = dN[k];
@@ -209,7 +211,12 @@ __global__ void __launch_bounds__(32 * TW_WQ_WARPS) k_wq_weights(Dir D0, Dir D1,
   const int i = blockIdx.x * TW_WQ_WARPS + wib;
   if (i >= D.n) return;
   const int p = D.p, p1 = p + 1, W2 = 2 * p + 1, lda = TW_QMAX + 1;
-  const int jlo = max(0, i - p), jhi = min(D.n - 1, i + p);
+  // Eq. 5's equations: the trial functions whose support overlaps supp B_i
+  // with positive measure, a contiguous run of i-p .. i+p (with a repeated
+  // knot some of them only touch supp B_i at that knot)
+  int jlo = max(0, i - p), jhi = min(D.n - 1, i + p);
+  while (jlo < i && !(D.U[jlo + p + 1] > D.U[i])) jlo++;
+  while (jhi > i && !(D.U[jhi] < D.U[i + p + 1])) jhi--;
   const int m = jhi - jlo + 1;
   const int q0 = D.qbeg[i], N = D.qcnt[i];
   if (N > TW_QMAX) {
@@ -251,8 +258,8 @@ __global__ void __launch_bounds__(32 * TW_WQ_WARPS) k_wq_weights(Dir D0, Dir D1,
     int lo = 0, hi = 0;
     if (j >= 0 && j < D.n) {
       int ea = max(elo, max(0, j - p)), eb = min(ehi, min(D.nel - 1, j));
-      lo = wq_off(ea, p, D.nel) - q0;
-      hi = wq_off(eb + 1, p, D.nel) - q0;
+      lo = wq_off(D, ea) - q0;
+      hi = wq_off(D, eb + 1) - q0;
     }
     D.crange[i * W2 + r] = lo | (hi << 16);
   }
@@ -336,11 +343,15 @@ __global__ void k_classify_elems(CurveSet C, Dir A, Dir B, const double *hits, c
   int id = blockIdx.x * blockDim.x + threadIdx.x;
   if (id >= A.nel * B.nel) return;
   int e1 = id % A.nel, e2 = id / A.nel;
+  double a1 = A.bp[e1], b1 = A.bp[e1 + 1], a2 = B.bp[e2], b2 = B.bp[e2 + 1];
+  if (!(b1 > a1) || !(b2 > a2)) {  // R8: an empty span has no measure
+    estate[id] = TW_ELEM_EMPTY;
+    return;
+  }
   if (C.n == 0) {
     estate[id] = TW_ELEM_REGULAR;
     return;
   }
-  double a1 = A.bp[e1], b1 = A.bp[e1 + 1], a2 = B.bp[e2], b2 = B.bp[e2 + 1];
   double d1 = TW_CORNER * (b1 - a1), d2 = TW_CORNER * (b2 - a2);
   const int hv = A.nel + 1;  // first horizontal knot line
   const int hc = A.nel + B.nel + 2;  // first centre line
@@ -386,6 +397,7 @@ __global__ void k_classify_funcs(Dir A, Dir B, const uint8_t *estate, uint8_t *f
   for (int e2 = max(0, i2 - B.p); e2 <= min(B.nel - 1, i2); e2++)
     for (int e1 = max(0, i1 - A.p); e1 <= min(A.nel - 1, i1); e1++) {
       uint8_t s = estate[e2 * A.nel + e1];
+      if (s == TW_ELEM_EMPTY) continue;  // R8: the states of the elements with measure
       tot++;
       nreg += s == TW_ELEM_REGULAR;
       ninv += s == TW_ELEM_INVISIBLE;
@@ -951,7 +963,8 @@ __global__ void __launch_bounds__(32 * TW_GC_WARPS)
 // ---------------------------------------------------------------------------
 // DWQ (Sect. 3.3)
 
-// R7: region R = R1 x R2 of regular elements with the most elements.  One
+// R7: region R = R1 x R2 of regular (or empty) elements with simple discs and
+// the most elements.  One
 // warp per cut function (from the compacted list of cut functions, count on
 // the device): the support's elements are counted into a 2-D prefix table of
 // non-regular elements, so each candidate's "all regular" test is four
@@ -983,9 +996,10 @@ __global__ void __launch_bounds__(32 * TW_CHOICE_WARPS)
     // T[y][x] = non-regular elements in [lo0, lo0 + x) x [lo1, lo1 + y)
     for (int t = lane; t < PW * PW; t += 32) T[t] = 0;
     __syncwarp();
-    for (int t = lane; t < w1 * w2; t += 32) {
+    for (int t = lane; t < w1 * w2; t += 32) {  // empty elements have no measure
       const int x = t % w1, y = t / w1;
-      T[(y + 1) * PW + x + 1] = estate[(lo[1] + y) * A.nel + lo[0] + x] != TW_ELEM_REGULAR;
+      const uint8_t st = estate[(lo[1] + y) * A.nel + lo[0] + x];
+      T[(y + 1) * PW + x + 1] = st != TW_ELEM_REGULAR && st != TW_ELEM_EMPTY;
     }
     __syncwarp();
     if (lane < w2)  // prefix along x, row by row
@@ -1008,6 +1022,15 @@ __global__ void __launch_bounds__(32 * TW_CHOICE_WARPS)
       const int y0 = r0[1] - lo[1], y1 = r1[1] - lo[1] + 1;
       const int bad = T[y1 * PW + x1] - T[y0 * PW + x1] - T[y1 * PW + x0] + T[y0 * PW + x0];
       if (bad) continue;
+      // a disc is a simple knot: t inserted p times reaches multiplicity p+1
+      bool simple = true;
+      for (int d = 0; d < 2; d++)
+        if (kind[d] != 0) {
+          const double *bp = D[d]->bp;
+          const int sv = kind[d] == 1 ? r1[d] + 1 : r0[d];
+          simple = simple && bp[sv - 1] < bp[sv] && bp[sv] < bp[sv + 1];
+        }
+      if (!simple) continue;
       const int nel = (x1 - x0) * (y1 - y0);
       const int disc = (kind[0] != 0) + (kind[1] != 0);
       const int key = (nel << 16) | ((3 - disc) << 10) | (1023 - c);
@@ -1119,8 +1142,8 @@ __global__ void __launch_bounds__(TW_DWQ_THREADS)
     const int lane = threadIdx.x, e = ewlo + lane;
     int m = 0, add = 0, k0 = 0;
     if (lane < nwe) {
-      k0 = wq_off(e, p, D.nel);
-      m = wq_off(e + 1, p, D.nel) - k0;
+      k0 = wq_off(D, e);
+      m = wq_off(D, e + 1) - k0;
       if ((e == s - 1 || e == s) && m < p1) add = p1 - m;
     }
     const int cnt = m + add;
@@ -1225,7 +1248,9 @@ __global__ void __launch_bounds__(TW_DWQ_THREADS)
     } else {
       int j = id - np_, el = j / p1, g = j % p1, e = ewlo + el;
       double x = D.bp[e] + (D.bp[e + 1] - D.bp[e]) * 0.5 * (D.gx[g] + 1.0);
-      ref_basis(D, s, e, x, N);
+      if (D.bp[e + 1] > D.bp[e]) ref_basis(D, s, e, x, N);
+      else  // the zero-length span of a repeated knot
+        for (int a2 = 0; a2 <= p; a2++) N[a2] = 0.0;
       for (int a2 = 0; a2 <= p; a2++) RG[el][g][a2] = N[a2];
     }
   }
@@ -1273,7 +1298,7 @@ __global__ void __launch_bounds__(TW_DWQ_THREADS)
       for (int el = 0; el < nwe; el++) {
         int e = ewlo + el;
         double ea = D.bp[e], eb = D.bp[e + 1];
-        if (eb <= ul || ea >= uh) continue;
+        if (eb <= ul || ea >= uh || !(eb > ea)) continue;
         int f0 = e + (e >= s ? p : 0);
         int al = l - f0, am = mr - f0;
         if (al < 0 || al > p || am < 0 || am > p) continue;
@@ -1556,7 +1581,7 @@ int build_tables(tw_patch *P) {
   // WQ layout, basis tables, weights (Eq. 5): both directions per launch
   {
     auto g2 = [](int64_t n) { return dim3((unsigned)((n + 255) / 256), 2); };
-    k_wq_points<<<g2(std::max(A.nq, B.nq)), 256, 0, st>>>(A, B);
+    k_wq_points<<<g2(std::max(A.nel, B.nel)), 256, 0, st>>>(A, B);
     TW_LAUNCH();
     k_wq_ranges<<<g2(std::max(A.n, B.n)), 256, 0, st>>>(A, B);
     TW_LAUNCH();
