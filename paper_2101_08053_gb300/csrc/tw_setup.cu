@@ -215,8 +215,10 @@ __global__ void __launch_bounds__(32 * TW_WQ_WARPS) k_wq_weights(Dir D0, Dir D1,
   // with positive measure, a contiguous run of i-p .. i+p (with a repeated
   // knot some of them only touch supp B_i at that knot)
   int jlo = max(0, i - p), jhi = min(D.n - 1, i + p);
-  while (jlo < i && !(D.U[jlo + p + 1] > D.U[i])) jlo++;
-  while (jhi > i && !(D.U[jhi] < D.U[i + p + 1])) jhi--;
+  if (D.mixed) {  // simple knots: the whole run overlaps
+    while (jlo < i && !(D.U[jlo + p + 1] > D.U[i])) jlo++;
+    while (jhi > i && !(D.U[jhi] < D.U[i + p + 1])) jhi--;
+  }
   const int m = jhi - jlo + 1;
   const int q0 = D.qbeg[i], N = D.qcnt[i];
   if (N > TW_QMAX) {
