@@ -648,84 +648,135 @@ struct RowArgs {
 };
 
 // ---------------------------------------------------------------------------
-// warp-cooperative min-norm solve of A w = b (m x N, m <= 2p+1, N <= 32): lane c
-// owns column c.  LQ with Householder reflectors from the right, reductions by
-// a fixed shuffle tree (deterministic).  A (leading dimension lda, shared
-// memory) is overwritten with L and the reflectors; ssh is 32 doubles of the
-// warp's shared scratch; w[c] is returned in lane c.
+// warp reductions by a fixed shuffle tree (deterministic)
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
-static __device__ double warp_minnorm(int m, int N, double *A, int lda, const double *b, double *diag,
-                               double *beta, double *ssh, int lane, int *singular) {
-  // GB300 issues one FP64 warp instruction per 16 cycles per SM, so the
-  // reflectors' row products run with lanes over rows (one FMA per column)
-  // instead of one warp reduction per row
-  for (int k = 0; k < m; k++) {
-    double x = (lane >= k && lane < N) ? A[k * lda + lane] : 0.0;
-    double nrm2 = warp_sum(x * x);
-    double akk = A[k * lda + k];
-    double nrm = sqrt(nrm2);
-    if (nrm == 0.0) {
-      *singular = 1;
-      return 0.0;
+// sum over the G consecutive lanes of one group (G a power of two <= 32)
+template <int G>
+__device__ __forceinline__ double group_sum(double v) {
+#pragma unroll
+  for (int o = G >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Minimum-norm solutions of 32/G small systems at once (Eq. 5, reading R2),
+// one per group of G consecutive lanes: an LQ factorisation A = L Q by
+// Householder reflectors applied from the right (reflector k from row k,
+// applied to the rows below), then L y = b by forward substitution and
+// w = H_0 ... H_{m-1} [y; 0].  Every FP64 instruction serves all the warp's
+// systems (GB300 issues one FP64 warp instruction per 16 cycles per SM).
+// The group's system: A (m x N, row stride lda) in shared memory, b (m) in
+// shared memory; lane gl of the group owns the columns (and the rows of the
+// triangular solve) gl + G u, u < CPL.  Loop bounds are the warp's largest m
+// and N; a group past its own m idles.  On return w[u] is the weight of
+// column gl + G u (0 beyond N), A holds the reflectors, diag / beta (m, shared
+// per group) their data; *singular (per group) is set when a reflector's norm
+// vanishes (the group's weights are then 0).  Called by the whole warp.
+template <int G, int CPL>
+__device__ void group_minnorm(int m, int N, double *A, int lda, const double *b, double *diag,
+                              double *beta, int gl, int *singular, double (&w)[CPL]) {
+  const unsigned FULL = 0xffffffffu;
+  const int M = __reduce_max_sync(FULL, (unsigned)m);
+  const int NN = __reduce_max_sync(FULL, (unsigned)N);
+  const int U = (NN + G - 1) / G;  // <= CPL
+  bool ok = m > 0 && N > 0;
+  for (int k = 0; k < M; k++) {
+    const bool act = ok && k < m;
+    double part = 0.0;
+#pragma unroll
+    for (int u = 0; u < CPL; u++) {
+      if (u >= U) break;  // warp-uniform
+      const int c = gl + G * u;
+      const double x = (act && c >= k && c < N) ? A[k * lda + c] : 0.0;
+      part = fma(x, x, part);
     }
-    double alpha = akk >= 0.0 ? -nrm : nrm;
-    double v0 = akk - alpha;
-    double vn2 = v0 * v0 + (nrm2 - akk * akk);
-    double bk = vn2 > 0.0 ? 2.0 / vn2 : 0.0;
+    const double nrm2 = group_sum<G>(part);
+    const double akk = act ? A[k * lda + k] : 0.0;
+    const double nrm = sqrt(nrm2);
+    if (act && nrm == 0.0) {
+      ok = false;
+      if (gl == 0) *singular = 1;
+    }
+    const bool go = act && ok;
+    const double alpha = akk >= 0.0 ? -nrm : nrm;
+    const double v0 = akk - alpha;
+    const double vn2 = v0 * v0 + (nrm2 - akk * akk);
+    const double bk = (go && vn2 > 0.0) ? 2.0 / vn2 : 0.0;
     __syncwarp();
-    // the reflector vector v (columns k..N-1) replaces row k
-    if (lane >= k && lane < N) A[k * lda + lane] = lane == k ? v0 : x;
-    if (lane == 0) {
+    // the reflector v (columns k..N-1) replaces row k: only column k changes
+    if (go && gl == (k & (G - 1))) A[k * lda + k] = v0;
+    if (go && gl == 0) {
       diag[k] = alpha;
       beta[k] = bk;
     }
     __syncwarp();
-    // s_r = bk * (row r . v) for the R rows below k: C lanes per row (the
-    // largest power of two with R C <= 32) take every C-th column, then a
-    // fixed shuffle tree inside each group of C lanes
-    const int R = m - k - 1;
-    if (R > 0) {
-      int C = 32;
-      while (C * R > 32) C >>= 1;
-      const int rr = lane / C, c0 = lane & (C - 1);
+    // rows below: r -= bk (r . v) v
+    for (int r = k + 1; r < M; r++) {
+      const bool ra = go && r < m;
       double sr = 0.0;
-      if (rr < R) {
-        const double *ar = A + (k + 1 + rr) * lda, *vk = A + k * lda;
-        for (int c = k + c0; c < N; c += C) sr = fma(ar[c], vk[c], sr);
+#pragma unroll
+      for (int u = 0; u < CPL; u++) {
+        if (u >= U) break;  // warp-uniform
+        const int c = gl + G * u;
+        if (ra && c >= k && c < N) sr = fma(A[r * lda + c], A[k * lda + c], sr);
       }
-      for (int o = C >> 1; o > 0; o >>= 1) sr += __shfl_xor_sync(0xffffffffu, sr, o);
-      if (rr < R && c0 == 0) ssh[k + 1 + rr] = sr * bk;
-    }
-    __syncwarp();
-    // row r -= s_r v, lanes over columns
-    if (lane >= k && lane < N) {
-      const double vc = A[k * lda + lane];
-      for (int r = k + 1; r < m; r++) A[r * lda + lane] = fma(-ssh[r], vc, A[r * lda + lane]);
+      sr = group_sum<G>(sr) * bk;
+#pragma unroll
+      for (int u = 0; u < CPL; u++) {
+        if (u >= U) break;  // warp-uniform
+        const int c = gl + G * u;
+        if (ra && c >= k && c < N) A[r * lda + c] = fma(-sr, A[k * lda + c], A[r * lda + c]);
+      }
     }
     __syncwarp();
   }
   // forward substitution L y = b (L below the diagonal of A, diagonal in
-  // diag), lanes over rows: lane j's value is final when step j reaches it
-  double rhs = lane < m ? b[lane] : 0.0;
-  const double dinv = lane < m ? 1.0 / diag[lane] : 0.0;
-  double y = 0.0;
-  for (int j = 0; j < m; j++) {
-    const double yj = __shfl_sync(0xffffffffu, rhs * dinv, j);
-    if (lane == j) y = yj;
-    if (lane > j && lane < m) rhs = fma(-A[lane * lda + j], yj, rhs);
+  // diag); y_j lives on its owner lane, slot j / G
+  double y[CPL];
+#pragma unroll
+  for (int u = 0; u < CPL; u++) y[u] = 0.0;
+  for (int j = 0; j < M; j++) {
+    const bool ja = ok && j < m;
+    double part = 0.0;
+#pragma unroll
+    for (int u = 0; u < CPL; u++) {
+      if (u >= U) break;  // warp-uniform
+      const int i = gl + G * u;
+      if (ja && i < j) part = fma(A[j * lda + i], y[u], part);
+    }
+    const double s = group_sum<G>(part);
+    const double yj = ja ? (b[j] - s) * (1.0 / diag[j]) : 0.0;
+#pragma unroll
+    for (int u = 0; u < CPL; u++)
+      if (gl + G * u == j) y[u] = yj;
   }
   // w = H_0 ... H_{m-1} [y; 0]
-  double w = lane < m ? y : 0.0;
-  for (int k = m - 1; k >= 0; k--) {
-    double v = (lane >= k && lane < N) ? A[k * lda + lane] : 0.0;
-    double sdot = warp_sum(v * w) * beta[k];
-    w -= sdot * v;
+#pragma unroll
+  for (int u = 0; u < CPL; u++) w[u] = (ok && gl + G * u < m) ? y[u] : 0.0;
+  for (int k = M - 1; k >= 0; k--) {
+    const bool go = ok && k < m;
+    double part = 0.0;
+#pragma unroll
+    for (int u = 0; u < CPL; u++) {
+      if (u >= U) break;  // warp-uniform
+      const int c = gl + G * u;
+      if (go && c >= k && c < N) part = fma(A[k * lda + c], w[u], part);
+    }
+    const double tot = group_sum<G>(part);  // every lane takes part in the shuffles
+    const double sd = go ? tot * beta[k] : 0.0;
+#pragma unroll
+    for (int u = 0; u < CPL; u++) {
+      if (u >= U) break;  // warp-uniform
+      const int c = gl + G * u;
+      if (go && c >= k && c < N) w[u] = fma(-sd, A[k * lda + c], w[u]);
+    }
   }
-  return lane < N ? w : 0.0;
+#pragma unroll
+  for (int u = 0; u < CPL; u++)
+    if (!ok || gl + G * u >= N) w[u] = 0.0;
 }
 
 }  // namespace tw

@@ -199,38 +199,50 @@ __device__ __forceinline__ double Bjk(const Dir &D, int j, int k) {
 }
 
 // Eq. 5 for test function i: min-norm weights, then V = W * B_j (R2, R3).
-// One warp per test function: lanes own the columns (points) of the system.
-#define TW_WQ_WARPS 4
-__global__ void __launch_bounds__(32 * TW_WQ_WARPS) k_wq_weights(Dir D0, Dir D1, int *flag) {
+// Groups of TW_WQ_G lanes own one test function each (group_minnorm: the
+// lanes of a group own the points c = gl + G u of its system), so a warp
+// solves 32 / TW_WQ_G systems at once; the systems' matrices sit in dynamic
+// shared memory with row stride lda = max qmax + 1.
+#define TW_WQ_WARPS 2
+#define TW_WQ_G 8
+#define TW_WQ_SYS (TW_WQ_WARPS * 32 / TW_WQ_G)  // systems per block
+#define TW_WQ_CPL ((TW_QMAX + TW_WQ_G - 1) / TW_WQ_G)
+__global__ void __launch_bounds__(32 * TW_WQ_WARPS) k_wq_weights(Dir D0, Dir D1, int lda,
+                                                                int *flag) {
   const Dir &D = blockIdx.y ? D1 : D0;
-  __shared__ double sA[TW_WQ_WARPS][TW_WIN * (TW_QMAX + 1)];
-  __shared__ double sb[TW_WQ_WARPS][TW_WIN], sd[TW_WQ_WARPS][TW_WIN], sbeta[TW_WQ_WARPS][TW_WIN];
-  __shared__ int sing[TW_WQ_WARPS];
-  __shared__ double sss[TW_WQ_WARPS][32];
-  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int i = blockIdx.x * TW_WQ_WARPS + wib;
-  if (i >= D.n) return;
-  const int p = D.p, p1 = p + 1, W2 = 2 * p + 1, lda = TW_QMAX + 1;
+  extern __shared__ double wq_dyn[];  // TW_WQ_SYS x TW_WIN x lda
+  __shared__ double sb[TW_WQ_SYS][TW_WIN], sd[TW_WQ_SYS][TW_WIN], sbeta[TW_WQ_SYS][TW_WIN];
+  __shared__ int sing[TW_WQ_SYS];
+  constexpr int G = TW_WQ_G, CPL = TW_WQ_CPL;
+  const int lane = threadIdx.x & 31, gl = lane & (G - 1);
+  const int sys = threadIdx.x / G;  // the block's system of this lane's group
+  const int i = blockIdx.x * TW_WQ_SYS + sys;
+  const int p = D.p, p1 = p + 1, W2 = 2 * p + 1;
   // Eq. 5's equations: the trial functions whose support overlaps supp B_i
   // with positive measure, a contiguous run of i-p .. i+p (with a repeated
   // knot some of them only touch supp B_i at that knot)
-  int jlo = max(0, i - p), jhi = min(D.n - 1, i + p);
-  if (D.mixed) {  // simple knots: the whole run overlaps
-    while (jlo < i && !(D.U[jlo + p + 1] > D.U[i])) jlo++;
-    while (jhi > i && !(D.U[jhi] < D.U[i + p + 1])) jhi--;
+  int m = 0, N = 0, jlo = 0, q0 = 0;
+  if (i < D.n) {
+    jlo = max(0, i - p);
+    int jhi = min(D.n - 1, i + p);
+    if (D.mixed) {  // simple knots: the whole run overlaps
+      while (jlo < i && !(D.U[jlo + p + 1] > D.U[i])) jlo++;
+      while (jhi > i && !(D.U[jhi] < D.U[i + p + 1])) jhi--;
+    }
+    m = jhi - jlo + 1;
+    q0 = D.qbeg[i];
+    N = D.qcnt[i];
+    if (N > TW_QMAX || N >= lda) {
+      if (gl == 0) atomicOr(flag, TWF_QMAX);
+      m = N = 0;
+    }
   }
-  const int m = jhi - jlo + 1;
-  const int q0 = D.qbeg[i], N = D.qcnt[i];
-  if (N > TW_QMAX) {
-    if (lane == 0) atomicOr(flag, TWF_QMAX);
-    return;
-  }
-  double *A = sA[wib];
+  double *A = wq_dyn + (size_t)sys * TW_WIN * lda;
   const int elo = max(0, i - p), ehi = min(D.nel - 1, i);
-  if (lane < N)
-    for (int r = 0; r < m; r++) A[r * lda + lane] = Bjk(D, jlo + r, q0 + lane);
-  if (lane < m) {
-    int j = jlo + lane;
+  for (int c = gl; c < N; c += G)
+    for (int r = 0; r < m; r++) A[r * lda + c] = Bjk(D, jlo + r, q0 + c);
+  for (int r = gl; r < m; r += G) {
+    int j = jlo + r;
     double s = 0.0;
     int ea = max(elo, max(0, j - p)), eb = min(ehi, min(D.nel - 1, j));
     for (int e = ea; e <= eb; e++) {
@@ -238,25 +250,30 @@ __global__ void __launch_bounds__(32 * TW_WQ_WARPS) k_wq_weights(Dir D0, Dir D1,
       for (int g = 0; g < p1; g++)
         s += D.gw[g] * h * D.GB[(e * p1 + g) * p1 + (i - e)] * D.GB[(e * p1 + g) * p1 + (j - e)];
     }
-    sb[wib][lane] = s;
+    sb[sys][r] = s;
   }
-  if (lane == 0) sing[wib] = 0;
+  if (gl == 0) sing[sys] = 0;
   __syncwarp();
-  double wc = warp_minnorm(m, N, A, lda, sb[wib], sd[wib], sbeta[wib], sss[wib], lane, &sing[wib]);
+  double w[CPL];
+  group_minnorm<G, CPL>(m, N, A, lda, sb[sys], sd[sys], sbeta[sys], gl, &sing[sys], w);
   __syncwarp();
-  if (lane == 0 && sing[wib]) atomicOr(flag, TWF_SINGULAR);
-  for (int c = lane; c < D.qmax; c += 32) {
-    double w = (c < N) ? wc : 0.0;  // lane c holds column c (N <= 32)
-    D.W[(size_t)i * D.qmax + c] = w;
+  if (i >= D.n) return;  // the group only (no collective below)
+  if (gl == 0 && sing[sys]) atomicOr(flag, TWF_SINGULAR);
+#pragma unroll
+  for (int u = 0; u < CPL; u++) {
+    const int c = gl + G * u;
+    if (c >= D.qmax) break;
+    const double wc = c < N ? w[u] : 0.0;
+    D.W[(size_t)i * D.qmax + c] = wc;
     for (int r = 0; r < W2; r++) {
       int j = i - p + r;
       double v = 0.0;
-      if (c < N && j >= 0 && j < D.n) v = w * Bjk(D, j, q0 + c);
+      if (c < N && j >= 0 && j < D.n) v = wc * Bjk(D, j, q0 + c);
       D.V[((size_t)i * D.qmax + c) * W2 + r] = v;
     }
   }
-  if (lane < W2) {
-    int r = lane, j = i - p + r;
+  for (int r = gl; r < W2; r += G) {
+    int j = i - p + r;
     int lo = 0, hi = 0;
     if (j >= 0 && j < D.n) {
       int ea = max(elo, max(0, j - p)), eb = min(ehi, min(D.nel - 1, j));
@@ -1113,8 +1130,9 @@ struct DwqOut {
 // refined basis is tabulated once per window point and per window Gauss point
 // (shared memory); each refined system is then assembled by lookup and solved
 // by its own warp.
-#define TW_DWQ_THREADS 384  // 12 warps: the 2p refined systems of every p <= 6 in one round
-#define TW_DWQ_SMEM (sizeof(double) * (TW_DWQ_THREADS / 32) * TW_WIN * (TW_QMAX + 1))
+#define TW_DWQ_THREADS 384  // 12 warps for the window points and the refined basis tables
+#define TW_DWQ_G 4          // lanes per refined system in the solves (step 3)
+#define TW_DWQ_SMEM (sizeof(double) * 2 * TW_MAXP * TW_WIN * (TW_QMAX + 1))
 __global__ void __launch_bounds__(TW_DWQ_THREADS)
     k_dwq_build(Dir A, Dir B, DwqOut o0, DwqOut o1, int *flag) {
   const bool d1 = (int)blockIdx.x >= o0.n;
@@ -1257,45 +1275,49 @@ __global__ void __launch_bounds__(TW_DWQ_THREADS)
     }
   }
   __syncthreads();
-  // step 3: WQ weights of the refined functions l = s .. s+2p-1 (Eq. 5), one
-  // warp per refined system, lanes over the points of its support
-  // one system matrix per warp, in dynamic shared memory (TW_DWQ_SMEM bytes)
+  // step 3: WQ weights of the refined functions l = s .. s+2p-1 (Eq. 5): a
+  // group of TW_DWQ_G lanes per refined system (group_minnorm), eight systems
+  // per warp, so the first ceil(2p / 8) warps solve them all; the systems'
+  // matrices sit in dynamic shared memory (TW_DWQ_SMEM bytes)
+  constexpr int G = TW_DWQ_G, CPL = (TW_QMAX + TW_DWQ_G - 1) / TW_DWQ_G;
   extern __shared__ double dwq_dyn[];
   double (*sA)[TW_WIN * (TW_QMAX + 1)] = (double (*)[TW_WIN * (TW_QMAX + 1)])dwq_dyn;
-  __shared__ double sb[TW_DWQ_THREADS / 32][TW_WIN], sd[TW_DWQ_THREADS / 32][TW_WIN],
-      sbeta[TW_DWQ_THREADS / 32][TW_WIN];
-  __shared__ int sing[TW_DWQ_THREADS / 32];
-  __shared__ double sss[TW_DWQ_THREADS / 32][32];
-  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __shared__ double sb[2 * TW_MAXP][TW_WIN], sd[2 * TW_MAXP][TW_WIN], sbeta[2 * TW_MAXP][TW_WIN];
+  __shared__ int sing[2 * TW_MAXP];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31, gl = lane & (G - 1);
   const int lda = TW_QMAX + 1;
-  for (int li = wib; li < 2 * p && np_ > 0; li += TW_DWQ_THREADS / 32) {
+  if (wib * (32 / G) < 2 * p && np_ > 0) {  // warp-uniform
+    const int li = wib * (32 / G) + lane / G;
+    const bool live = li < 2 * p;
     int l = s + li;
     int nref = D.n + p;
-    double ul = ref_knot(D, s, l), uh = ref_knot(D, s, l + p + 1);
-    int rows[TW_WIN], m = 0;
-    for (int mm = max(0, l - p); mm <= min(nref - 1, l + p); mm++) {
-      double lo = fmax(ul, ref_knot(D, s, mm)), hi = fmin(uh, ref_knot(D, s, mm + p + 1));
-      if (hi > lo) rows[m++] = mm;
-    }
-    // points of supp B~_l: a contiguous run of the sorted window points
-    int c0 = 0;
-    while (c0 < np_ && !(xs[c0] > ul)) c0++;
-    int N = 0;
-    while (c0 + N < np_ && xs[c0 + N] < uh) N++;
-    if (N > TW_QMAX) {
-      if (lane == 0) atomicOr(flag, TWF_QMAX);
-      N = 0;
-    }
-    double *A = sA[wib];
-    if (lane < N) {
-      int k = c0 + lane;
-      for (int r = 0; r < m; r++) {
-        int aa = rows[r] - rsp[k];
-        A[r * lda + lane] = (aa >= 0 && aa <= p) ? RB[k][aa] : 0.0;
+    int rows[TW_WIN], m = 0, c0 = 0, N = 0;
+    double ul = 0.0, uh = 0.0;
+    if (live) {
+      ul = ref_knot(D, s, l);
+      uh = ref_knot(D, s, l + p + 1);
+      for (int mm = max(0, l - p); mm <= min(nref - 1, l + p); mm++) {
+        double lo = fmax(ul, ref_knot(D, s, mm)), hi = fmin(uh, ref_knot(D, s, mm + p + 1));
+        if (hi > lo) rows[m++] = mm;
+      }
+      // points of supp B~_l: a contiguous run of the sorted window points
+      while (c0 < np_ && !(xs[c0] > ul)) c0++;
+      while (c0 + N < np_ && xs[c0 + N] < uh) N++;
+      if (N > TW_QMAX) {
+        if (gl == 0) atomicOr(flag, TWF_QMAX);
+        N = 0;
       }
     }
-    if (lane < m) {
-      int mr = rows[lane];
+    double *A = sA[live ? li : 0];
+    for (int c = gl; c < N; c += G) {
+      int k = c0 + c;
+      for (int r = 0; r < m; r++) {
+        int aa = rows[r] - rsp[k];
+        A[r * lda + c] = (aa >= 0 && aa <= p) ? RB[k][aa] : 0.0;
+      }
+    }
+    for (int r = gl; r < m && N > 0; r += G) {
+      int mr = rows[r];
       double acc = 0.0;
       for (int el = 0; el < nwe; el++) {
         int e = ewlo + el;
@@ -1306,17 +1328,27 @@ __global__ void __launch_bounds__(TW_DWQ_THREADS)
         if (al < 0 || al > p || am < 0 || am > p) continue;
         for (int g = 0; g < p1; g++) acc += D.gw[g] * 0.5 * (eb - ea) * RG[el][g][al] * RG[el][g][am];
       }
-      sb[wib][lane] = acc;
+      sb[li][r] = acc;
     }
-    if (lane == 0) sing[wib] = 0;
+    if (live && gl == 0) sing[li] = 0;
     __syncwarp();
-    double wv = 0.0;
-    if (N > 0) wv = warp_minnorm(m, N, A, lda, sb[wib], sd[wib], sbeta[wib], sss[wib], lane, &sing[wib]);
+    double w[CPL];
+    const int ms = N > 0 ? m : 0;
+    group_minnorm<G, CPL>(ms, N, A, lda, live ? sb[li] : sb[0], live ? sd[li] : sd[0],
+                          live ? sbeta[li] : sbeta[0], gl, live ? &sing[li] : &sing[0], w);
     __syncwarp();
-    if (lane == 0 && sing[wib]) atomicOr(flag, TWF_SINGULAR);
-    for (int k = lane; k < np_; k += 32) Wt[li][k] = 0.0;
+    if (live) {
+      if (gl == 0 && sing[li]) atomicOr(flag, TWF_SINGULAR);
+      for (int k = gl; k < np_; k += G) Wt[li][k] = 0.0;
+    }
     __syncwarp();
-    if (lane < N) Wt[li][c0 + lane] = wv;
+    if (live) {
+#pragma unroll
+      for (int u = 0; u < CPL; u++) {
+        const int c = gl + G * u;
+        if (c < N) Wt[li][c0 + c] = w[u];
+      }
+    }
     __syncwarp();
   }
   __syncthreads();
@@ -1590,9 +1622,11 @@ int build_tables(tw_patch *P) {
     k_gauss_tables<<<g2((int64_t)std::max(A.nel, B.nel) * p1), 256, 0, st>>>(A, B);
     TW_LAUNCH();
     const int nw = std::max(A.n, B.n);
+    const int lda = std::max(A.qmax, B.qmax) + 1;
+    const size_t wsm = sizeof(double) * TW_WQ_SYS * TW_WIN * lda;
     const int pw = prof_start(st);
-    k_wq_weights<<<dim3((nw + TW_WQ_WARPS - 1) / TW_WQ_WARPS, 2), 32 * TW_WQ_WARPS, 0, st>>>(
-        A, B, P->flag);
+    k_wq_weights<<<dim3((nw + TW_WQ_SYS - 1) / TW_WQ_SYS, 2), 32 * TW_WQ_WARPS, wsm, st>>>(
+        A, B, lda, P->flag);
     prof_stop(pw, TW_STAGE_WQW, st);
     TW_LAUNCH();
   }
