@@ -1106,16 +1106,6 @@ __device__ void ref_basis(const Dir &D, int s, int e, double x, double *N) {
   }
 }
 
-// refined function m at x (0 if off its span)
-__device__ double ref_fn(const Dir &D, int s, int m, double x) {
-  int e = elem_of(D.bp, D.nel, x);
-  int span = e + D.p + (e >= s ? D.p : 0);
-  int a = m - (span - D.p);
-  if (a < 0 || a > D.p) return 0.0;
-  double N[TW_MAXP1];
-  ref_basis(D, s, e, x, N);
-  return N[a];
-}
 
 // The DWQ rules of both directions' disc knots, written per direction.
 struct DwqOut {
@@ -1130,8 +1120,8 @@ struct DwqOut {
 // refined basis is tabulated once per window point and per window Gauss point
 // (shared memory); each refined system is then assembled by lookup and solved
 // by its own warp.
-#define TW_DWQ_THREADS 384  // 12 warps for the window points and the refined basis tables
-#define TW_DWQ_G 4          // lanes per refined system in the solves (step 3)
+#define TW_DWQ_THREADS 128  // 4 warps: three solve the 2p <= 12 refined systems (step 3)
+#define TW_DWQ_G 8          // lanes per refined system in the solves
 #define TW_DWQ_SMEM (sizeof(double) * 2 * TW_MAXP * TW_WIN * (TW_QMAX + 1))
 __global__ void __launch_bounds__(TW_DWQ_THREADS)
     k_dwq_build(Dir A, Dir B, DwqOut o0, DwqOut o1, int *flag) {
