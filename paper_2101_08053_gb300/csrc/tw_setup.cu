@@ -797,14 +797,20 @@ __global__ void k_cut_offsets(int ncut, const int64_t *line_off, const int64_t *
 // per cut point: basis values in both directions and w * c.  The points come
 // in Gauss lines of constant outer coordinate (R6); for the spline geometry
 // the outer direction's basis and the control-net sums over it are formed once
-// per line, so det J costs 4(p+1) FMAs per point instead of 4(p+1)^2.
-#define TW_CPT_THREADS 128
+// per line, so det J costs 4(p+1) FMAs per point instead of 4(p+1)^2.  One
+// warp per cut element walks its points in chunks of 32: a ballot marks the
+// lines that open in the chunk, the opening lane forms its line's outer basis,
+// the lanes then form the control-net sums per (line, j), and each lane
+// finishes its point; the warp synchronises only with itself.
+#define TW_CPT_WARPS 4
+#define TW_CPT_THREADS (32 * TW_CPT_WARPS)
 __global__ void __launch_bounds__(TW_CPT_THREADS)
     k_cut_point_tables(Geo G, Dir A, Dir B, const int32_t *cut_list, const int64_t *off,
                        const int32_t *cut_o, int ncut, const double *pts, double *Bt,
                        double *wc) {
-  const int ci = blockIdx.x;
-  if (ci >= ncut) return;
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ci = blockIdx.x * TW_CPT_WARPS + wib;
+  if (ci >= ncut) return;  // the whole warp
   const int e = cut_list[ci];
   const int e1 = e % A.nel, e2 = e / A.nel, p = A.p, p1 = p + 1;
   const int o = cut_o[ci], in = 1 - o;
@@ -812,62 +818,59 @@ __global__ void __launch_bounds__(TW_CPT_THREADS)
   const Dir &Do = o == 0 ? A : B;
   const Dir &Di = o == 0 ? B : A;
   const bool geo = G.geom_kind == TW_GEOM_SPLINE && G.coef_kind != TW_COEF_ONE;
-  __shared__ double OV[TW_CPT_THREADS][TW_MAXP1];     // outer basis values of each line
-  __shared__ double LS[TW_CPT_THREADS][4][TW_MAXP1];  // control-net sums over the outer index
-  __shared__ int64_t lfirst[TW_CPT_THREADS];          // first point of each line
-  __shared__ unsigned wmask[TW_CPT_THREADS / 32];
+  // per warp: the lines of the current chunk (at most 32)
+  __shared__ double OVs[TW_CPT_WARPS][32][TW_MAXP1], ODs[TW_CPT_WARPS][32][TW_MAXP1];
+  __shared__ double LSs[TW_CPT_WARPS][32][4][TW_MAXP1];  // control-net sums over the outer index
   // reciprocal knot differences of the element's outer and inner spans
-  __shared__ double rco[TW_SPAN_RC], rdo[TW_MAXP1], rci[TW_SPAN_RC], rdi[TW_MAXP1];
-  if (threadIdx.x == 0) span_recips(Do.U, eo + p, p, rco, rdo);
-  if (threadIdx.x == 32) span_recips(Di.U, ei + p, p, rci, rdi);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __shared__ double rcos[TW_CPT_WARPS][TW_SPAN_RC], rdos[TW_CPT_WARPS][TW_MAXP1];
+  __shared__ double rcis[TW_CPT_WARPS][TW_SPAN_RC], rdis[TW_CPT_WARPS][TW_MAXP1];
+  double(*OV)[TW_MAXP1] = OVs[wib];
+  double(*OD)[TW_MAXP1] = ODs[wib];
+  double(*LS)[4][TW_MAXP1] = LSs[wib];
+  double *rco = rcos[wib], *rdo = rdos[wib], *rci = rcis[wib], *rdi = rdis[wib];
+  if (lane == 0) span_recips(Do.U, eo + p, p, rco, rdo);
+  if (lane == 1) span_recips(Di.U, ei + p, p, rci, rdi);
+  __syncwarp();
   const int64_t k0 = off[ci], k1 = off[ci + 1];
-  for (int64_t base = k0; base < k1; base += TW_CPT_THREADS) {
-    const int t = threadIdx.x;
-    const int64_t k = base + t;
+  for (int64_t base = k0; base < k1; base += 32) {
+    const int64_t k = base + lane;
     const bool live = k < k1;
     // a line opens at the chunk's first point and where the outer coordinate changes
-    const bool start = live && (t == 0 || pts[3 * k + o] != pts[3 * (k - 1) + o]);
+    const double so = live ? pts[3 * k + o] : 0.0;
+    const bool start = live && (lane == 0 || so != pts[3 * (k - 1) + o]);
     const unsigned m = __ballot_sync(0xffffffffu, start);
-    if (lane == 0) wmask[wid] = m;
-    __syncthreads();
-    int before = 0, nl = 0;
-    for (int w = 0; w < TW_CPT_THREADS / 32; w++) {
-      const int c = __popc(wmask[w]);
-      if (w < wid) before += c;
-      nl += c;
-    }
+    const int nl = __popc(m);
     // line of this point = (line starts up to and including it) - 1
-    const int l = before + __popc(m & ((2u << lane) - 1u)) - 1;
-    if (start) lfirst[l] = k;
-    __syncthreads();
-    // per line and inner index j: the outer basis at the line and the control
-    // net summed over the outer index (o = 0: over a for each b = j; o = 1:
-    // over b for each a = j)
-    for (int u = t; u < nl * p1; u += TW_CPT_THREADS) {
-      const int L = u / p1, j = u % p1;
-      const double sL = pts[3 * lfirst[L] + o];
+    const int l = __popc(m & ((2u << lane) - 1u)) - 1;
+    if (start) {  // the line's outer basis, once
       double v[TW_MAXP1], d[TW_MAXP1];
-      basis_ders_rc(Do.U, eo + p, sL, p, rco, rdo, v, d);
-      if (j == 0)
-        for (int a = 0; a <= p; a++) OV[L][a] = v[a];
-      if (geo) {
+      basis_ders_rc(Do.U, eo + p, so, p, rco, rdo, v, d);
+      for (int a = 0; a <= p; a++) {
+        OV[l][a] = v[a];
+        OD[l][a] = d[a];
+      }
+    }
+    __syncwarp();
+    // per line and inner index j: the control net summed over the outer index
+    // (o = 0: over a for each b = j; o = 1: over b for each a = j)
+    if (geo)
+      for (int u = lane; u < nl * p1; u += 32) {
+        const int L = u / p1, j = u % p1;
         double sxd = 0, syd = 0, sxv = 0, syv = 0;
         for (int a = 0; a <= p; a++) {
           const int ia = o == 0 ? e1 + a : e1 + j, ib = o == 0 ? e2 + j : e2 + a;
           const double *pt = G.ctrl + 2 * ((size_t)ib * G.n1 + ia);
-          sxd += pt[0] * d[a];
-          syd += pt[1] * d[a];
-          sxv += pt[0] * v[a];
-          syv += pt[1] * v[a];
+          sxd += pt[0] * OD[L][a];
+          syd += pt[1] * OD[L][a];
+          sxv += pt[0] * OV[L][a];
+          syv += pt[1] * OV[L][a];
         }
         LS[L][0][j] = sxd;
         LS[L][1][j] = syd;
         LS[L][2][j] = sxv;
         LS[L][3][j] = syv;
       }
-    }
-    __syncthreads();
+    __syncwarp();
     if (live) {
       const double x1 = pts[3 * k], x2 = pts[3 * k + 1];
       const double xi = o == 0 ? x2 : x1;
@@ -897,7 +900,7 @@ __global__ void __launch_bounds__(TW_CPT_THREADS)
       }
       wc[k] = pts[3 * k + 2] * c;
     }
-    __syncthreads();
+    __syncwarp();  // the chunk's line data are rewritten by the next chunk
   }
 }
 
@@ -1388,28 +1391,30 @@ __global__ void __launch_bounds__(TW_DWQ_THREADS)
 // element's rule (Sect. 3.1), sum-factorised along the rule's Gauss lines: on a
 // line xi_o = s the outer basis values are constant, so the inner sums
 // I[ai][bi] = sum_h w_h c_h B_ai(u_h) B_bi(u_h) are formed first and then
-// M[(ao,ai)][(bo,bi)] += B_ao(s) B_bo(s) I[ai][bi].  Thread (ao, bo) owns
-// (p+1)^2 accumulators; sums run in point order (deterministic).
+// M[(ao,ai)][(bo,bi)] += B_ao(s) B_bo(s) I[ai][bi].  The lines and their
+// points come from the rule's layout (line_off per element, lpos per line).
+// Thread (ao, bo) owns (p+1)^2 accumulators; sums run in point order
+// (deterministic).
 template <int P>
-__global__ void __launch_bounds__(64) k_cut_matrices(const int64_t *off, const int32_t *cut_o,
-                                                     int ncut, const double *pts,
-                                                     const double *Bt, const double *wc,
-                                                     double *M) {
+__global__ void __launch_bounds__(64) k_cut_matrices(const int64_t *line_off,
+                                                     const int64_t *lpos, const int32_t *cut_o,
+                                                     int ncut, const double *Bt,
+                                                     const double *wc, double *M) {
   constexpr int P1 = P + 1, NL = P1 * P1;
   const int ci = blockIdx.x;
   if (ci >= ncut) return;
   const int t = threadIdx.x;
   const int o = cut_o[ci], in = 1 - o;
-  const int64_t q0 = off[ci], q1 = off[ci + 1];
   __shared__ double I[NL];
   double acc[NL];
 #pragma unroll
   for (int k = 0; k < NL; k++) acc[k] = 0.0;
   const int ao = t / P1, bo = t % P1;
-  for (int64_t k = q0; k < q1;) {
-    const double s = pts[3 * k + o];
-    int64_t ke = k + 1;
-    while (ke < q1 && pts[3 * ke + o] == s) ke++;
+  // the element's Gauss lines (R6) and their points, from the rule's layout
+  const int64_t L0 = line_off[ci], L1 = line_off[ci + 1];
+  for (int64_t L = L0; L < L1; L++) {
+    const int64_t k = lpos[L], ke = lpos[L + 1];
+    if (ke == k) continue;  // a line with no visible interval (uniform)
     if (t < NL) {
       const int ai = t / P1, bi = t % P1;
       double sum = 0.0;
@@ -1427,7 +1432,6 @@ __global__ void __launch_bounds__(64) k_cut_matrices(const int64_t *off, const i
       for (int m = 0; m < NL; m++) acc[m] = fma(f, I[m], acc[m]);
     }
     __syncthreads();
-    k = ke;
   }
   if (t < NL) {
     double *Me = M + (size_t)ci * NL * NL;
@@ -1441,10 +1445,11 @@ __global__ void __launch_bounds__(64) k_cut_matrices(const int64_t *off, const i
   }
 }
 
-static void launch_cut_matrices(tw_patch *P, cudaStream_t st) {
+static void launch_cut_matrices(tw_patch *P, const int64_t *line_off, const int64_t *lpos,
+                                cudaStream_t st) {
   switch (P->p) {
 // one warp per element while the (p+1)^2 owner threads fit in it
-#define TW_CM(PP) case PP: k_cut_matrices<PP><<<P->ncut, (PP + 1) * (PP + 1) <= 32 ? 32 : 64, 0, st>>>(P->cut_off, P->cut_o, P->ncut, P->cut_pts, P->cut_B, P->cut_wc, P->cut_M); break;
+#define TW_CM(PP) case PP: k_cut_matrices<PP><<<P->ncut, (PP + 1) * (PP + 1) <= 32 ? 32 : 64, 0, st>>>(line_off, lpos, P->cut_o, P->ncut, P->cut_B, P->cut_wc, P->cut_M); break;
     TW_CM(1) TW_CM(2) TW_CM(3) TW_CM(4) TW_CM(5) TW_CM(6)
 #undef TW_CM
   }
@@ -1819,11 +1824,11 @@ int build_tables(tw_patch *P) {
           cln, clv, lpos, P->cut_pts);
       TW_LAUNCH();
     }
-    k_cut_point_tables<<<P->ncut, TW_CPT_THREADS, 0, st>>>(P->geo, A, B, P->cut_list, P->cut_off,
-                                                           P->cut_o, P->ncut, P->cut_pts, P->cut_B,
-                                                           P->cut_wc);
+    k_cut_point_tables<<<(P->ncut + TW_CPT_WARPS - 1) / TW_CPT_WARPS, TW_CPT_THREADS, 0, st>>>(
+        P->geo, A, B, P->cut_list, P->cut_off, P->cut_o, P->ncut, P->cut_pts, P->cut_B,
+        P->cut_wc);
     TW_LAUNCH();
-    launch_cut_matrices(P, st);
+    launch_cut_matrices(P, line_off, lpos, st);
   }
   // DWQ rules per disc knot, both directions in one launch
   DwqOut dout[2];
