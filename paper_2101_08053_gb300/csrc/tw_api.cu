@@ -439,6 +439,7 @@ extern "C" int tw_patch_create(const tw_patch_desc *desc, tw_patch **out) {
       ALLOC(D.crange, int, (size_t)D.n * W);
       ALLOC(D.GB, double, (size_t)D.nel * (p + 1) * (p + 1));
       ALLOC(D.dGB, double, (size_t)D.nel * (p + 1) * (p + 1));
+      ALLOC(D.GW, double, (size_t)D.nel * (p + 1) * (p + 1) * (p + 1));
       ALLOC(D.qoff, int, D.nel + 1);
       ALLOC(D.two, uint8_t, D.n);
       cudaMemcpyAsync(D.qoff, hoff[d], sizeof(int) * (D.nel + 1), cudaMemcpyHostToDevice, st);

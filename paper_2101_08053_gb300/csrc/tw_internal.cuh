@@ -64,6 +64,7 @@ struct Dir {
   int *crange;  // n x (2p+1): lo | (hi << 16) local point range where V != 0
   const double *gx, *gw;  // Gauss-Legendre on [-1,1], p+1 points (cached, not owned)
   double *GB, *dGB; // nel x (p+1) x (p+1): B_{e+a}(x_{e,g}) at [e][g][a]
+  double *GW;       // nel x (p+1)^3: w_g h_e B_{e+a}(x_{e,g}) B_{e+b}(x_{e,g}) at [e][g][a][b]
 };
 
 struct Geo {

@@ -190,6 +190,12 @@ __global__ void k_gauss_tables(Dir D0, Dir D1) {
     D.GB[(e * p1 + g) * p1 + k] = N[k];
     D.dGB[(e * p1 + g) * p1 + k] = dN[k];
   }
+  // the weighted products of the element matrices (Gauss weight x Jacobian of
+  // the span map x two basis values), once per element of the direction
+  const double hw = D.gw[g] * (0.5 * (b - a));
+  double *gw3 = D.GW + (size_t)(e * p1 + g) * p1 * p1;
+  for (int i = 0; i < p1; i++)
+    for (int k = 0; k < p1; k++) gw3[i * p1 + k] = hw * N[i] * N[k];
 }
 
 // B_j(x_k) from the WQ basis table (zero off the span)
@@ -1390,66 +1396,93 @@ __global__ void __launch_bounds__(TW_DWQ_THREADS)
 // Element matrices of the cut elements, M_e[a][b] = sum_q w_q c_q B_a B_b over the
 // element's rule (Sect. 3.1), sum-factorised along the rule's Gauss lines: on a
 // line xi_o = s the outer basis values are constant, so the inner sums
-// I[ai][bi] = sum_h w_h c_h B_ai(u_h) B_bi(u_h) are formed first and then
-// M[(ao,ai)][(bo,bi)] += B_ao(s) B_bo(s) I[ai][bi].  The lines and their
-// points come from the rule's layout (line_off per element, lpos per line).
-// Thread (ao, bo) owns (p+1)^2 accumulators; sums run in point order
-// (deterministic).
+// I(ai,bi) = sum_h w_h c_h B_ai(u_h) B_bi(u_h) are formed first and then
+// M[(ao,ai)][(bo,bi)] += B_ao(s) B_bo(s) I(ai,bi).  Both factors are symmetric
+// in their index pair, so only the unordered pairs {ao,bo} x {ai,bi} are
+// accumulated ((p+1)(p+2)/2 squared instead of (p+1)^4 products per line) and
+// M, symmetric, is written out from them.  One warp per element, no block
+// barrier: lane u < (p+1)(p+2)/2 forms the line's inner sum and outer product
+// of pair u, then every lane adds them into its share of the accumulators.
+// The lines and their points come from the rule's layout (line_off per
+// element, lpos per line); sums run in point and line order (deterministic).
+#define TW_CM_WARPS 4
 template <int P>
-__global__ void __launch_bounds__(64) k_cut_matrices(const int64_t *line_off,
-                                                     const int64_t *lpos, const int32_t *cut_o,
-                                                     int ncut, const double *Bt,
-                                                     const double *wc, double *M) {
-  constexpr int P1 = P + 1, NL = P1 * P1;
-  const int ci = blockIdx.x;
-  if (ci >= ncut) return;
-  const int t = threadIdx.x;
+__device__ __forceinline__ int sym_pair(int a, int b) {  // a <= b
+  return a * (P + 1) - a * (a - 1) / 2 + (b - a);
+}
+template <int P>
+__global__ void __launch_bounds__(32 * TW_CM_WARPS)
+    k_cut_matrices(const int64_t *line_off, const int64_t *lpos, const int32_t *cut_o, int ncut,
+                   const double *Bt, const double *wc, double *M) {
+  constexpr int P1 = P + 1, NL = P1 * P1, U = P1 * (P1 + 1) / 2, NO = U * U;
+  constexpr int NPL = (NO + 31) / 32;
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ci = blockIdx.x * TW_CM_WARPS + wib;
+  if (ci >= ncut) return;  // the whole warp
+  __shared__ double Fs[TW_CM_WARPS][U], Is[TW_CM_WARPS][U], As[TW_CM_WARPS][NO];
+  double *F = Fs[wib], *I = Is[wib], *Acc = As[wib];
   const int o = cut_o[ci], in = 1 - o;
-  __shared__ double I[NL];
-  double acc[NL];
+  // this lane's pair (lanes below U): u -> (pa, pb), pa <= pb
+  int pa = 0, pb = 0;
+  if (lane < U) {
+    int r = lane;
+    while (r >= P1 - pa) {
+      r -= P1 - pa;
+      pa++;
+    }
+    pb = pa + r;
+  }
+  double acc[NPL];
 #pragma unroll
-  for (int k = 0; k < NL; k++) acc[k] = 0.0;
-  const int ao = t / P1, bo = t % P1;
+  for (int j = 0; j < NPL; j++) acc[j] = 0.0;
   // the element's Gauss lines (R6) and their points, from the rule's layout
   const int64_t L0 = line_off[ci], L1 = line_off[ci + 1];
   for (int64_t L = L0; L < L1; L++) {
     const int64_t k = lpos[L], ke = lpos[L + 1];
     if (ke == k) continue;  // a line with no visible interval (uniform)
-    if (t < NL) {
-      const int ai = t / P1, bi = t % P1;
+    if (lane < U) {
       double sum = 0.0;
       for (int64_t h = k; h < ke; h++) {
         const double *bv = Bt + (2 * h + in) * P1;
-        sum = fma(wc[h] * bv[ai], bv[bi], sum);
+        sum = fma(wc[h] * bv[pa], bv[pb], sum);
       }
-      I[t] = sum;
-    }
-    __syncthreads();
-    if (t < NL) {
       const double *bo_ = Bt + (2 * k + o) * P1;
-      const double f = bo_[ao] * bo_[bo];
-#pragma unroll
-      for (int m = 0; m < NL; m++) acc[m] = fma(f, I[m], acc[m]);
+      I[lane] = sum;
+      F[lane] = bo_[pa] * bo_[pb];
     }
-    __syncthreads();
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < NPL; j++) {
+      const int m = lane + 32 * j;
+      if (m < NO) acc[j] = fma(F[m / U], I[m % U], acc[j]);
+    }
+    __syncwarp();  // F, I rewritten by the next line
   }
-  if (t < NL) {
-    double *Me = M + (size_t)ci * NL * NL;
 #pragma unroll
-    for (int m = 0; m < NL; m++) {
-      const int ai = m / P1, bi = m % P1;
-      const int a1 = o == 0 ? ao : ai, a2 = o == 0 ? ai : ao;
-      const int b1 = o == 0 ? bo : bi, b2 = o == 0 ? bi : bo;
-      Me[(a2 * P1 + a1) * NL + (b2 * P1 + b1)] = acc[m];
-    }
+  for (int j = 0; j < NPL; j++) {
+    const int m = lane + 32 * j;
+    if (m < NO) Acc[m] = acc[j];
+  }
+  __syncwarp();
+  // M[(a2,a1)][(b2,b1)] from the pair accumulators, consecutive lanes on
+  // consecutive entries
+  double *Me = M + (size_t)ci * NL * NL;
+  for (int t = lane; t < NL * NL; t += 32) {
+    const int r = t / NL, c = t % NL;
+    const int a1 = r % P1, a2 = r / P1, b1 = c % P1, b2 = c / P1;
+    const int ao = o == 0 ? a1 : a2, ai = o == 0 ? a2 : a1;
+    const int bo = o == 0 ? b1 : b2, bi = o == 0 ? b2 : b1;
+    const int po = sym_pair<P>(min(ao, bo), max(ao, bo));
+    const int pi = sym_pair<P>(min(ai, bi), max(ai, bi));
+    Me[t] = Acc[po * U + pi];
   }
 }
 
 static void launch_cut_matrices(tw_patch *P, const int64_t *line_off, const int64_t *lpos,
                                 cudaStream_t st) {
+  const unsigned nb = (unsigned)((P->ncut + TW_CM_WARPS - 1) / TW_CM_WARPS);
   switch (P->p) {
-// one warp per element while the (p+1)^2 owner threads fit in it
-#define TW_CM(PP) case PP: k_cut_matrices<PP><<<P->ncut, (PP + 1) * (PP + 1) <= 32 ? 32 : 64, 0, st>>>(line_off, lpos, P->cut_o, P->ncut, P->cut_B, P->cut_wc, P->cut_M); break;
+#define TW_CM(PP) case PP: k_cut_matrices<PP><<<nb, 32 * TW_CM_WARPS, 0, st>>>(line_off, lpos, P->cut_o, P->ncut, P->cut_B, P->cut_wc, P->cut_M); break;
     TW_CM(1) TW_CM(2) TW_CM(3) TW_CM(4) TW_CM(5) TW_CM(6)
 #undef TW_CM
   }
@@ -1476,14 +1509,11 @@ __global__ void __launch_bounds__(256) k_gauss_matrices(Dir A, Dir B, const int3
   // read (cut functions; every active function for the Gauss method)
   __shared__ int flag[NL], need[NL];
   __shared__ int nneed;
-  const double h1 = 0.5 * (A.bp[e1 + 1] - A.bp[e1]), h2 = 0.5 * (B.bp[e2 + 1] - B.bp[e2]);
-  const double *GB1 = A.GB + (size_t)e1 * NL;  // [g][a]
-  const double *GB2 = B.GB + (size_t)e2 * NL;
-  const double *c = gc + (size_t)sl * NL;      // [g2][g1]
+  const double *c = gc + (size_t)sl * NL;  // [g2][g1]
+  const double *GW1 = A.GW + (size_t)e1 * P3, *GW2 = B.GW + (size_t)e2 * P3;
   for (int id = threadIdx.x; id < P3; id += blockDim.x) {
-    const int g = id / NL, a = (id / P1) % P1, b = id % P1;
-    W1[id] = A.gw[g] * h1 * GB1[g * P1 + a] * GB1[g * P1 + b];
-    W2[id] = B.gw[g] * h2 * GB2[g * P1 + a] * GB2[g * P1 + b];
+    W1[id] = GW1[id];
+    W2[id] = GW2[id];
   }
   for (int a = threadIdx.x; a < NL; a += blockDim.x) {
     const uint8_t st = fstate[(size_t)(e2 + a / P1) * A.n + (e1 + a % P1)];
