@@ -340,6 +340,7 @@ extern "C" int tw_batch_create(tw_patch *const *patches, int n, int precision,
       ra.dwq_k[d] = P->dwq_k[d];
       ra.dwq_e[d] = P->dwq_e[d];
       ra.dwq_B[d] = P->dwq_B[d];
+      ra.dwq_dB[d] = P->dwq_dB[d];
       ra.dwq_r[d] = P->dwq_r[d];
     }
     ra.gmat = P->gmat;

@@ -23,6 +23,7 @@ struct CutSmem {
   double Z[W * TW_RC];
   double Tg[P1 * P1];
   int rk[2][TW_RC];
+  int rq[2][TW_RC];  // DWQ table index of each region point (-1: a WQ rule point)
   int nr[2], nnest[2], nest[2][TW_RC];
   double pv[2][TW_RC][P1], pd[2][TW_RC][P1];  // basis values / derivatives at the region points
   int pe[2][TW_RC];                            // and their elements
@@ -150,6 +151,7 @@ __device__ void cutrow_item(const RowArgs &a, int g, int32_t *__restrict__ col,
           S.rx[d][lane] = D.xq[k];
           const double wk = D.W[(size_t)i * D.qmax + lane];
           S.rk[d][lane] = k;
+          S.rq[d][lane] = -1;
           for (int r = 0; r < W; r++) {
             int aa = i - P + r - D.qel[k];
             S.rb[d][lane][r] = wk * ((aa >= 0 && aa <= P) ? D.Bq[k * P1 + aa] : 0.0);
@@ -171,6 +173,7 @@ __device__ void cutrow_item(const RowArgs &a, int g, int32_t *__restrict__ col,
           const double wk =
               a.dwq_w[d][(((size_t)sl * P + (i - s)) * 2 + side) * TW_LQMAX + k0 + lane];
           S.rk[d][lane] = a.dwq_k[d][k];  // base points read c from the grid
+          S.rq[d][lane] = (int)k;
           const int e = a.dwq_e[d][k];
           const double *Bv = a.dwq_B[d] + k * P1;
           for (int r = 0; r < W; r++) {
@@ -195,7 +198,7 @@ __device__ void cutrow_item(const RowArgs &a, int g, int32_t *__restrict__ col,
       }
     }
     // basis values and derivatives at every region point, once per row: from
-    // the tables at base points, by Cox-de Boor at nested points
+    // the WQ tables at base points, from the DWQ rule's tables at nested points
     const bool unit_c = a.G.coef_kind == TW_COEF_ONE;
     for (int t = tid; t < m1 + m2 && !unit_c; t += blockDim.x) {
       const int d = t < m1 ? 0 : 1, j = d == 0 ? t : t - m1;
@@ -207,11 +210,13 @@ __device__ void cutrow_item(const RowArgs &a, int g, int32_t *__restrict__ col,
           S.pv[d][j][q] = D.Bq[(size_t)k * P1 + q];
           S.pd[d][j][q] = D.dBq[(size_t)k * P1 + q];
         }
-      } else {
-        const double x = S.rx[d][j];
-        const int e = elem_of(D.bp, D.nel, x);
-        S.pe[d][j] = e;
-        basis_ders(D.U, e + P, x, P, S.pv[d][j], S.pd[d][j]);
+      } else {  // a nested point exists only in a DWQ rule
+        const int q = S.rq[d][j];
+        S.pe[d][j] = a.dwq_e[d][q];
+        for (int qq = 0; qq <= P; qq++) {
+          S.pv[d][j][qq] = a.dwq_B[d][(size_t)q * P1 + qq];
+          S.pd[d][j][qq] = a.dwq_dB[d][(size_t)q * P1 + qq];
+        }
       }
     }
     if (tid == 0) {

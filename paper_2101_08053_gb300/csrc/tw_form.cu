@@ -253,6 +253,7 @@ static int launch_form(tw_patch *Pt, int precision, int64_t *rp, int32_t *col, v
       ra.dwq_k[d] = Pt->dwq_k[d];
       ra.dwq_e[d] = Pt->dwq_e[d];
       ra.dwq_B[d] = Pt->dwq_B[d];
+      ra.dwq_dB[d] = Pt->dwq_dB[d];
       ra.dwq_r[d] = Pt->dwq_r[d];
     }
     ra.gmat = Pt->gmat;

@@ -141,6 +141,13 @@ __device__ __forceinline__ void basis_ders(const double *U, int span, double x, 
   }
 }
 
+// basis_ders as an out-of-line call, for a kernel that runs other copies of the
+// triangle too (the DWQ build, with its refined basis)
+static __device__ __noinline__ void basis_ders_ool(const double *U, int span, double x, int p,
+                                                   double *N, double *dN) {
+  basis_ders(U, span, x, p, N, dN);
+}
+
 // The Cox-de Boor denominators right[r+1] + left[j-r] equal the knot
 // differences U[span+r+1] - U[span+1-j+r], which do not depend on x: for many
 // points on one span their reciprocals are formed once.
@@ -155,6 +162,28 @@ __device__ __forceinline__ void span_recips(const double *U, int span, int p, do
   for (int a = 1; a <= p; a++) {
     const double d = U[span + a] - U[span + a - p];
     rd[a] = d > 0.0 ? 1.0 / d : 0.0;
+  }
+}
+// entry t of the same tables (t < p(p+1)/2: rc[t]; then rd[t - p(p+1)/2]), so
+// that the lanes of a warp share the divisions of one span
+__device__ __forceinline__ void span_recip_entry(const double *U, int span, int p, int t,
+                                                 double *rc, double *rd) {
+  const int nrc = p * (p + 1) / 2;
+  if (t < nrc) {
+    int j = 1, r = t;
+    while (r >= j) {
+      r -= j;
+      j++;
+    }
+    rc[t] = 1.0 / (U[span + r + 1] - U[span + 1 - j + r]);
+  } else {
+    const int a = t - nrc;
+    if (a == 0) {
+      rd[0] = 0.0;
+    } else {
+      const double d = U[span + a] - U[span + a - p];
+      rd[a] = d > 0.0 ? 1.0 / d : 0.0;
+    }
   }
 }
 
@@ -642,6 +671,7 @@ struct RowArgs {
   const int32_t *dwq_k[2];
   const int32_t *dwq_e[2];
   const double *dwq_B[2];
+  const double *dwq_dB[2];
   const int32_t *dwq_r[2];
   const double *gmat;
   int method;
@@ -833,6 +863,7 @@ struct tw_patch {
   int32_t *dwq_k[2]; // ndisc x TW_LQMAX: base WQ point index of each window point, -1 nested
   int32_t *dwq_e[2]; // ndisc x TW_LQMAX: coarse element of each window point
   double *dwq_B[2];  // ndisc x TW_LQMAX x (p+1): coarse basis values there
+  double *dwq_dB[2]; // ndisc x TW_LQMAX x (p+1): and their derivatives
   int32_t *dwq_r[2]; // ndisc x p x 2: window point run of (function, side)
   double *gmat;      // ngslot x (p+1)^4 element matrices of the Gauss elements (or NULL)
   float2 *Cf;        // c on the WQ grid as hi/lo FP32 pairs (created on first FP32 form)

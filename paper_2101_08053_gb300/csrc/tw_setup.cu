@@ -821,8 +821,7 @@ __global__ void __launch_bounds__(TW_CPT_THREADS)
   const int e1 = e % A.nel, e2 = e / A.nel, p = A.p, p1 = p + 1;
   const int o = cut_o[ci], in = 1 - o;
   const int eo = o == 0 ? e1 : e2, ei = o == 0 ? e2 : e1;
-  const Dir &Do = o == 0 ? A : B;
-  const Dir &Di = o == 0 ? B : A;
+  const double *Uo = o == 0 ? A.U : B.U, *Ui = o == 0 ? B.U : A.U;
   const bool geo = G.geom_kind == TW_GEOM_SPLINE && G.coef_kind != TW_COEF_ONE;
   // per warp: the lines of the current chunk (at most 32)
   __shared__ double OVs[TW_CPT_WARPS][32][TW_MAXP1], ODs[TW_CPT_WARPS][32][TW_MAXP1];
@@ -834,8 +833,14 @@ __global__ void __launch_bounds__(TW_CPT_THREADS)
   double(*OD)[TW_MAXP1] = ODs[wib];
   double(*LS)[4][TW_MAXP1] = LSs[wib];
   double *rco = rcos[wib], *rdo = rdos[wib], *rci = rcis[wib], *rdi = rdis[wib];
-  if (lane == 0) span_recips(Do.U, eo + p, p, rco, rdo);
-  if (lane == 1) span_recips(Di.U, ei + p, p, rci, rdi);
+  {  // both spans' reciprocal tables, one entry per lane
+    const int ne = p * (p + 1) / 2 + p + 1;
+    for (int t = lane; t < 2 * ne; t += 32) {
+      const bool ot = t < ne;
+      span_recip_entry(ot ? Uo : Ui, (ot ? eo : ei) + p, p, ot ? t : t - ne, ot ? rco : rci,
+                       ot ? rdo : rdi);
+    }
+  }
   __syncwarp();
   const int64_t k0 = off[ci], k1 = off[ci + 1];
   for (int64_t base = k0; base < k1; base += 32) {
@@ -850,7 +855,7 @@ __global__ void __launch_bounds__(TW_CPT_THREADS)
     const int l = __popc(m & ((2u << lane) - 1u)) - 1;
     if (start) {  // the line's outer basis, once
       double v[TW_MAXP1], d[TW_MAXP1];
-      basis_ders_rc(Do.U, eo + p, so, p, rco, rdo, v, d);
+      basis_ders_rc(Uo, eo + p, so, p, rco, rdo, v, d);
       for (int a = 0; a <= p; a++) {
         OV[l][a] = v[a];
         OD[l][a] = d[a];
@@ -881,7 +886,7 @@ __global__ void __launch_bounds__(TW_CPT_THREADS)
       const double x1 = pts[3 * k], x2 = pts[3 * k + 1];
       const double xi = o == 0 ? x2 : x1;
       double v[TW_MAXP1], d[TW_MAXP1];
-      basis_ders_rc(Di.U, ei + p, xi, p, rci, rdi, v, d);
+      basis_ders_rc(Ui, ei + p, xi, p, rci, rdi, v, d);
       for (int a = 0; a < p1; a++) {
         Bt[(2 * k + o) * p1 + a] = OV[l][a];
         Bt[(2 * k + in) * p1 + a] = v[a];
@@ -1093,13 +1098,16 @@ __device__ __forceinline__ double ref_knot(const Dir &D, int s, int k) {
   return D.U[k - p];
 }
 
-// values of the p+1 refined functions on the element e of x
-__device__ void ref_basis(const Dir &D, int s, int e, double x, double *N) {
+// values of the p+1 refined functions on the element e of x: the triangular
+// scheme with knots K[0..2p-1] = U'[span-p+1 .. span+p], its denominators
+// K[p+r] - K[p-j+r] taken as the reciprocals rc[j(j-1)/2 + r] of that span
+// (formed once per window element and shared by its points)
+static __device__ __noinline__ void ref_basis_rc(const Dir &D, int s, int e, double x,
+                                                 const double *rc, double *N) {
   int p = D.p;
   int span = e + p + (e >= s ? p : 0);
   double K[2 * TW_MAXP + 2];
   for (int k = 0; k < 2 * p; k++) K[k] = ref_knot(D, s, span - p + 1 + k);
-  // triangular scheme with knots K[0..2p-1] = U'[span-p+1 .. span+p]
   double left[TW_MAXP1], right[TW_MAXP1];
   N[0] = 1.0;
   for (int j = 1; j <= p; j++) {
@@ -1107,7 +1115,7 @@ __device__ void ref_basis(const Dir &D, int s, int e, double x, double *N) {
     right[j] = K[p - 1 + j] - x;
     double saved = 0.0;
     for (int r = 0; r < j; r++) {
-      double t = N[r] / (right[r + 1] + left[j - r]);
+      const double t = N[r] * rc[j * (j - 1) / 2 + r];
       N[r] = saved + right[r + 1] * t;
       saved = left[j - r] * t;
     }
@@ -1120,7 +1128,7 @@ __device__ void ref_basis(const Dir &D, int s, int e, double x, double *N) {
 struct DwqOut {
   const int32_t *list;  // disc knots s (element index of t = bp[s])
   int n;
-  double *x, *w, *B;
+  double *x, *w, *B, *dB;
   int32_t *np, *k, *e, *r;
 };
 
@@ -1139,7 +1147,7 @@ __global__ void __launch_bounds__(TW_DWQ_THREADS)
   const DwqOut &O = d1 ? o1 : o0;
   if (slot >= O.n) return;
   const Dir &D = d1 ? B : A;
-  double *out_x = O.x, *out_w = O.w, *out_B = O.B;
+  double *out_x = O.x, *out_w = O.w, *out_B = O.B, *out_dB = O.dB;
   int32_t *out_np = O.np, *out_k = O.k, *out_e = O.e, *out_r = O.r;
   int s = O.list[slot];
   int p = D.p, p1 = p + 1;
@@ -1224,6 +1232,22 @@ __global__ void __launch_bounds__(TW_DWQ_THREADS)
       npts = total > TW_LQMAX ? 0 : total;
     }
   }
+  // reciprocal knot differences of the window elements' refined spans, in the
+  // third and fourth warps (an empty span's entries are never read)
+  __shared__ double rcw[2 * TW_MAXP][TW_SPAN_RC];
+  if (threadIdx.x >= 64) {
+    const int nrc = p * (p + 1) / 2;
+    for (int id = (int)threadIdx.x - 64; id < nwe * nrc; id += (int)blockDim.x - 64) {
+      const int el = id / nrc, t0 = id - el * nrc, e = ewlo + el;
+      int j = 1, r = t0;
+      while (r >= j) {
+        r -= j;
+        j++;
+      }
+      const int span = e + p + (e >= s ? p : 0);
+      rcw[el][t0] = 1.0 / (ref_knot(D, s, span + 1 + r) - ref_knot(D, s, span + 1 - j + r));
+    }
+  }
   // step 1: S columns by p local Boehm insertions (Eq. 10) on B_i's own knots,
   // in the second warp, concurrently with the first warp's point assembly
   const int sc_col = (int)threadIdx.x - 32;
@@ -1261,13 +1285,13 @@ __global__ void __launch_bounds__(TW_DWQ_THREADS)
     double N[TW_MAXP1];
     if (id < np_) {
       int e = elem_of(D.bp, D.nel, xs[id]);
-      ref_basis(D, s, e, xs[id], N);
+      ref_basis_rc(D, s, e, xs[id], rcw[e - ewlo], N);
       rsp[id] = e + (e >= s ? p : 0);
       for (int a2 = 0; a2 <= p; a2++) RB[id][a2] = N[a2];
     } else {
       int j = id - np_, el = j / p1, g = j % p1, e = ewlo + el;
       double x = D.bp[e] + (D.bp[e + 1] - D.bp[e]) * 0.5 * (D.gx[g] + 1.0);
-      if (D.bp[e + 1] > D.bp[e]) ref_basis(D, s, e, x, N);
+      if (D.bp[e + 1] > D.bp[e]) ref_basis_rc(D, s, e, x, rcw[el], N);
       else  // the zero-length span of a repeated knot
         for (int a2 = 0; a2 <= p; a2++) N[a2] = 0.0;
       for (int a2 = 0; a2 <= p; a2++) RG[el][g][a2] = N[a2];
@@ -1369,15 +1393,19 @@ __global__ void __launch_bounds__(TW_DWQ_THREADS)
   for (int k = threadIdx.x; k < TW_LQMAX; k += blockDim.x) {
     out_x[(size_t)slot * TW_LQMAX + k] = k < np_ ? xs[k] : 0.0;
     out_k[(size_t)slot * TW_LQMAX + k] = k < np_ ? xk[k] : -1;
-    // coarse element and coarse basis values of each window point
+    // coarse element, coarse basis values and derivatives of each window
+    // point (the derivatives give the geometry map's Jacobian at nested points)
     int e = 0;
-    double N[TW_MAXP1];
+    double N[TW_MAXP1], dN[TW_MAXP1];
     if (k < np_) {
       e = elem_of(D.bp, D.nel, xs[k]);
-      basis_vals(D.U, e + p, xs[k], p, N);
+      basis_ders_ool(D.U, e + p, xs[k], p, N, dN);
     }
     out_e[(size_t)slot * TW_LQMAX + k] = e;
-    for (int a2 = 0; a2 <= p; a2++) out_B[((size_t)slot * TW_LQMAX + k) * p1 + a2] = k < np_ ? N[a2] : 0.0;
+    for (int a2 = 0; a2 <= p; a2++) {
+      out_B[((size_t)slot * TW_LQMAX + k) * p1 + a2] = k < np_ ? N[a2] : 0.0;
+      out_dB[((size_t)slot * TW_LQMAX + k) * p1 + a2] = k < np_ ? dN[a2] : 0.0;
+    }
   }
   // per coarse function i = s + col and side: the contiguous run of window
   // points inside supp B_i on that side of t
@@ -1871,14 +1899,16 @@ int build_tables(tw_patch *P) {
     P->dwq_k[d] = (int32_t *)dalloc(P, sizeof(int32_t) * ((size_t)nd * TW_LQMAX + 1));
     P->dwq_e[d] = (int32_t *)dalloc(P, sizeof(int32_t) * ((size_t)nd * TW_LQMAX + 1));
     P->dwq_B[d] = (double *)dalloc(P, sizeof(double) * ((size_t)nd * TW_LQMAX * p1 + 1));
+    P->dwq_dB[d] = (double *)dalloc(P, sizeof(double) * ((size_t)nd * TW_LQMAX * p1 + 1));
     P->dwq_r[d] = (int32_t *)dalloc(P, sizeof(int32_t) * ((size_t)nd * p * 2 + 1));
-    if (!P->dwq_k[d] || !P->dwq_e[d] || !P->dwq_B[d] || !P->dwq_r[d]) return TW_ENOMEM;
+    if (!P->dwq_k[d] || !P->dwq_e[d] || !P->dwq_B[d] || !P->dwq_dB[d] || !P->dwq_r[d])
+      return TW_ENOMEM;
     int32_t *dlist = (int32_t *)dalloc(P, sizeof(int32_t) * (nd + 1));
     if (!P->dwq_x[d] || !P->dwq_np[d] || !P->dwq_w[d] || !dlist) return TW_ENOMEM;
     k_compact<<<G1(D.nel + 1)>>>(dflag[d], dpos[d], dlist, P->disc_slot[d], D.nel + 1);
     TW_LAUNCH();
-    dout[d] = DwqOut{dlist, nd, P->dwq_x[d], P->dwq_w[d], P->dwq_B[d],
-                     P->dwq_np[d], P->dwq_k[d], P->dwq_e[d], P->dwq_r[d]};
+    dout[d] = DwqOut{dlist,          nd,           P->dwq_x[d], P->dwq_w[d], P->dwq_B[d],
+                     P->dwq_dB[d],   P->dwq_np[d], P->dwq_k[d], P->dwq_e[d], P->dwq_r[d]};
   }
   if (P->ndisc[0] + P->ndisc[1] > 0) {
     static std::once_flag dwq_attr[64];

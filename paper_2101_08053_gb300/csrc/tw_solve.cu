@@ -365,6 +365,7 @@ RowArgs row_args(tw_patch *Pt) {
     ra.dwq_k[d] = Pt->dwq_k[d];
     ra.dwq_e[d] = Pt->dwq_e[d];
     ra.dwq_B[d] = Pt->dwq_B[d];
+    ra.dwq_dB[d] = Pt->dwq_dB[d];
     ra.dwq_r[d] = Pt->dwq_r[d];
   }
   ra.gmat = Pt->gmat;
