@@ -141,13 +141,6 @@ __device__ __forceinline__ void basis_ders(const double *U, int span, double x, 
   }
 }
 
-// basis_ders as an out-of-line call, for a kernel that runs other copies of the
-// triangle too (the DWQ build, with its refined basis)
-static __device__ __noinline__ void basis_ders_ool(const double *U, int span, double x, int p,
-                                                   double *N, double *dN) {
-  basis_ders(U, span, x, p, N, dN);
-}
-
 // The Cox-de Boor denominators right[r+1] + left[j-r] equal the knot
 // differences U[span+r+1] - U[span+1-j+r], which do not depend on x: for many
 // points on one span their reciprocals are formed once.

@@ -1157,6 +1157,7 @@ __global__ void __launch_bounds__(TW_DWQ_THREADS)
   __shared__ double RB[TW_LQMAX][TW_MAXP1];      // refined functions on each point's span
   __shared__ int rsp[TW_LQMAX];                  // first refined function of that span
   __shared__ double RG[2 * TW_MAXP][TW_MAXP1][TW_MAXP1];  // [window element][g][a]
+  __shared__ double GWt[2 * TW_MAXP][TW_MAXP1];  // Gauss weight x half the element length
   __shared__ int npts;
   __shared__ double Sc[TW_MAXP][TW_MAXP1];             // S[i + r][i], i = s + col
   __shared__ double Wt[2 * TW_MAXP][TW_LQMAX];         // refined weights of l = s + row
@@ -1232,20 +1233,27 @@ __global__ void __launch_bounds__(TW_DWQ_THREADS)
       npts = total > TW_LQMAX ? 0 : total;
     }
   }
-  // reciprocal knot differences of the window elements' refined spans, in the
-  // third and fourth warps (an empty span's entries are never read)
+  // reciprocal knot differences of the window elements' refined spans and of
+  // their coarse spans, in the third and fourth warps (an empty span's entries
+  // are never read)
   __shared__ double rcw[2 * TW_MAXP][TW_SPAN_RC];
+  __shared__ double rcc[2 * TW_MAXP][TW_SPAN_RC], rdc[2 * TW_MAXP][TW_MAXP1];
   if (threadIdx.x >= 64) {
-    const int nrc = p * (p + 1) / 2;
-    for (int id = (int)threadIdx.x - 64; id < nwe * nrc; id += (int)blockDim.x - 64) {
-      const int el = id / nrc, t0 = id - el * nrc, e = ewlo + el;
-      int j = 1, r = t0;
-      while (r >= j) {
-        r -= j;
-        j++;
+    const int nrc = p * (p + 1) / 2, ne = nrc + p + 1;
+    for (int id = (int)threadIdx.x - 64; id < nwe * (nrc + ne); id += (int)blockDim.x - 64) {
+      if (id < nwe * nrc) {
+        const int el = id / nrc, t0 = id - el * nrc, e = ewlo + el;
+        int j = 1, r = t0;
+        while (r >= j) {
+          r -= j;
+          j++;
+        }
+        const int span = e + p + (e >= s ? p : 0);
+        rcw[el][t0] = 1.0 / (ref_knot(D, s, span + 1 + r) - ref_knot(D, s, span + 1 - j + r));
+      } else {
+        const int c = id - nwe * nrc, el = c / ne;
+        span_recip_entry(D.U, ewlo + el + p, p, c - el * ne, rcc[el], rdc[el]);
       }
-      const int span = e + p + (e >= s ? p : 0);
-      rcw[el][t0] = 1.0 / (ref_knot(D, s, span + 1 + r) - ref_knot(D, s, span + 1 - j + r));
     }
   }
   // step 1: S columns by p local Boehm insertions (Eq. 10) on B_i's own knots,
@@ -1285,12 +1293,15 @@ __global__ void __launch_bounds__(TW_DWQ_THREADS)
     double N[TW_MAXP1];
     if (id < np_) {
       int e = elem_of(D.bp, D.nel, xs[id]);
-      ref_basis_rc(D, s, e, xs[id], rcw[e - ewlo], N);
+      // (a window point lies inside a window element; the clamp only keeps
+      // the table read in bounds)
+      ref_basis_rc(D, s, e, xs[id], rcw[min(max(e - ewlo, 0), nwe - 1)], N);
       rsp[id] = e + (e >= s ? p : 0);
       for (int a2 = 0; a2 <= p; a2++) RB[id][a2] = N[a2];
     } else {
       int j = id - np_, el = j / p1, g = j % p1, e = ewlo + el;
       double x = D.bp[e] + (D.bp[e + 1] - D.bp[e]) * 0.5 * (D.gx[g] + 1.0);
+      GWt[el][g] = D.gw[g] * 0.5 * (D.bp[e + 1] - D.bp[e]);
       if (D.bp[e + 1] > D.bp[e]) ref_basis_rc(D, s, e, x, rcw[el], N);
       else  // the zero-length span of a repeated knot
         for (int a2 = 0; a2 <= p; a2++) N[a2] = 0.0;
@@ -1349,7 +1360,7 @@ __global__ void __launch_bounds__(TW_DWQ_THREADS)
         int f0 = e + (e >= s ? p : 0);
         int al = l - f0, am = mr - f0;
         if (al < 0 || al > p || am < 0 || am > p) continue;
-        for (int g = 0; g < p1; g++) acc += D.gw[g] * 0.5 * (eb - ea) * RG[el][g][al] * RG[el][g][am];
+        for (int g = 0; g < p1; g++) acc += GWt[el][g] * RG[el][g][al] * RG[el][g][am];
       }
       sb[li][r] = acc;
     }
@@ -1399,7 +1410,8 @@ __global__ void __launch_bounds__(TW_DWQ_THREADS)
     double N[TW_MAXP1], dN[TW_MAXP1];
     if (k < np_) {
       e = elem_of(D.bp, D.nel, xs[k]);
-      basis_ders_ool(D.U, e + p, xs[k], p, N, dN);
+      const int el = min(max(e - ewlo, 0), nwe - 1);
+      basis_ders_rc(D.U, e + p, xs[k], p, rcc[el], rdc[el], N, dN);
     }
     out_e[(size_t)slot * TW_LQMAX + k] = e;
     for (int a2 = 0; a2 <= p; a2++) {
