@@ -487,6 +487,38 @@ __device__ __forceinline__ int set_visible(const CurveSet &S, double x, double y
   return 1;
 }
 
+// the fold points of segment sg of a cubic spline curve (d(coordinate o)/du = 0
+// for u in (0, 1)), in root order; returns their count (at most 2)
+__device__ __forceinline__ int seg_folds(const Curve &C, int sg, int o, double *pts) {
+  const double *co = C.seg + 8 * sg + 4 * o;
+  double A = 3.0 * co[3], B = 2.0 * co[2], Cc = co[1];
+  double sc = fabs(A) + fabs(B) + fabs(Cc);
+  double r[2];
+  int nr = 0;
+  if (sc == 0.0) return 0;
+  if (fabs(A) <= 1e-14 * sc) {
+    if (B != 0.0) r[nr++] = -Cc / B;
+  } else {
+    double disc = B * B - 4.0 * A * Cc;
+    if (disc < 0.0) return 0;
+    double sq = sqrt(disc);
+    double q = -0.5 * (B + copysign(sq, B));
+    if (q != 0.0) {
+      r[nr++] = q / A;
+      r[nr++] = Cc / q;
+    }
+  }
+  if (nr == 2 && r[0] == r[1]) nr = 1;
+  int n = 0;
+  for (int k = 0; k < nr; k++) {
+    if (!(r[k] > 0.0 && r[k] < 1.0)) continue;
+    pts[2 * n] = horner3(C.seg + 8 * sg, r[k]);
+    pts[2 * n + 1] = horner3(C.seg + 8 * sg + 4, r[k]);
+    n++;
+  }
+  return n;
+}
+
 // curve points where d(coordinate o)/d(param) = 0; returns count (pts as x,y)
 static __device__ int curve_folds(const Curve &C, int o, double *pts, int cap) {
   if (C.kind == TW_TRIM_CIRCLE) {
@@ -510,32 +542,11 @@ static __device__ int curve_folds(const Curve &C, int o, double *pts, int cap) {
   int n = 0;
   if (C.kind == TW_TRIM_BSPLINE3) {
     for (int sg = 0; sg < C.nc; sg++) {
-      const double *co = C.seg + 8 * sg + 4 * o;
-      double A = 3.0 * co[3], B = 2.0 * co[2], Cc = co[1];
-      double sc = fabs(A) + fabs(B) + fabs(Cc);
-      double r[2];
-      int nr = 0;
-      if (sc == 0.0) continue;
-      if (fabs(A) <= 1e-14 * sc) {
-        if (B != 0.0) r[nr++] = -Cc / B;
-      } else {
-        double disc = B * B - 4.0 * A * Cc;
-        if (disc < 0.0) continue;
-        double sq = sqrt(disc);
-        double q = -0.5 * (B + copysign(sq, B));
-        if (q != 0.0) {
-          r[nr++] = q / A;
-          r[nr++] = Cc / q;
-        }
-      }
-      if (nr == 2 && r[0] == r[1]) nr = 1;
-      for (int k = 0; k < nr; k++) {
-        if (!(r[k] > 0.0 && r[k] < 1.0)) continue;
-        if (n >= cap) return -1;
-        pts[2 * n] = horner3(C.seg + 8 * sg, r[k]);
-        pts[2 * n + 1] = horner3(C.seg + 8 * sg + 4, r[k]);
-        n++;
-      }
+      double f[4];
+      const int m = seg_folds(C, sg, o, f);
+      if (n + m > cap) return -1;
+      for (int k = 0; k < 2 * m; k++) pts[2 * n + k] = f[k];
+      n += m;
     }
   }
   return n;

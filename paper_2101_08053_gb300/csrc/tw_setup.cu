@@ -24,56 +24,106 @@ __device__ __forceinline__ int wq_off(const Dir &D, int e) {
 }
 
 // ---------------------------------------------------------------------------
-// scans (three-phase, 1024-element blocks)
+// scans of 1024-element blocks (integer sums: exact in any order).  One launch
+// when the input fits one block; otherwise the block scans, then a pass in
+// which every block sums the totals of the blocks before it itself (no third
+// launch) while there are at most TW_SCAN_DIRECT blocks, else a one-block scan
+// of the totals between the two.
 
+#define TW_SCAN_DIRECT 2048
+
+// inclusive scan over the 1024 threads of a block (warp shuffles, two barriers)
 template <typename T>
-__global__ void k_scan_block(const T *in, T *out, T *bsum, int64_t n) {
-  __shared__ T sh[1024];
-  int t = threadIdx.x;
-  int64_t i = (int64_t)blockIdx.x * 1024 + t;
-  T v = i < n ? in[i] : (T)0;
-  sh[t] = v;
-  __syncthreads();
-  for (int off = 1; off < 1024; off <<= 1) {
-    T a = t >= off ? sh[t - off] : (T)0;
-    __syncthreads();
-    sh[t] += a;
-    __syncthreads();
+__device__ __forceinline__ T block_scan_incl(T v, T *wsum) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  T x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const T y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
   }
-  if (i < n) out[i] = sh[t] - v;
-  if (t == 1023) bsum[blockIdx.x] = sh[1023];
+  if (lane == 31) wsum[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    T w = wsum[lane];
+    for (int o = 1; o < 32; o <<= 1) {
+      const T y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    wsum[lane] = w;
+  }
+  __syncthreads();
+  return wid > 0 ? x + wsum[wid - 1] : x;
 }
 
+// block scan: out = exclusive scan within the block, bsum = the block's total;
+// a single-block scan also writes the grand total
 template <typename T>
-__global__ void k_scan_sums(T *bsum, int64_t nb, T *total) {
-  __shared__ T sh[1024];
+__global__ void __launch_bounds__(1024) k_scan_block(const T *in, T *out, T *bsum, int64_t n,
+                                                     T *total) {
+  __shared__ T wsum[32];
+  const int t = threadIdx.x;
+  const int64_t i = (int64_t)blockIdx.x * 1024 + t;
+  const T v = i < n ? in[i] : (T)0;
+  const T incl = block_scan_incl(v, wsum);
+  if (i < n) out[i] = incl - v;
+  if (t == 1023) {
+    bsum[blockIdx.x] = incl;
+    if (gridDim.x == 1) *total = incl;
+  }
+}
+
+// the totals of blocks scanned in place (exclusive), and the grand total, for
+// more than TW_SCAN_DIRECT blocks
+template <typename T>
+__global__ void __launch_bounds__(1024) k_scan_sums(T *bsum, int64_t nb, T *total) {
+  __shared__ T wsum[32];
   __shared__ T carry;
-  int t = threadIdx.x;
+  const int t = threadIdx.x;
   if (t == 0) carry = 0;
   __syncthreads();
   for (int64_t base = 0; base < nb; base += 1024) {
-    int64_t i = base + t;
-    T v = i < nb ? bsum[i] : (T)0;
-    sh[t] = v;
+    const int64_t i = base + t;
+    const T v = i < nb ? bsum[i] : (T)0;
+    const T incl = block_scan_incl(v, wsum);
+    const T c = carry;
+    if (i < nb) bsum[i] = c + incl - v;
     __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-      T a = t >= off ? sh[t - off] : (T)0;
-      __syncthreads();
-      sh[t] += a;
-      __syncthreads();
-    }
-    if (i < nb) bsum[i] = carry + sh[t] - v;
-    __syncthreads();
-    if (t == 0) carry += sh[1023];
+    if (t == 1023) carry = c + incl;
     __syncthreads();
   }
   if (t == 0) *total = carry;
 }
 
+// adds each block's carry: the sum of the totals of the blocks before it,
+// formed by the block itself (direct; the last block then writes the grand
+// total) or read from the scanned totals
 template <typename T>
-__global__ void k_scan_add(T *out, const T *bsum, int64_t n) {
-  int64_t i = (int64_t)blockIdx.x * 1024 + threadIdx.x;
-  if (i < n) out[i] += bsum[blockIdx.x];
+__global__ void __launch_bounds__(1024) k_scan_add(T *out, const T *bsum, int64_t n, T *total,
+                                                   int direct) {
+  __shared__ T wsum[32];
+  __shared__ T carry_s;
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  const int b = blockIdx.x;
+  T carry;
+  if (direct) {
+    T s = 0;
+    for (int j = t; j < b; j += 1024) s += bsum[j];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) wsum[wid] = s;
+    __syncthreads();
+    if (wid == 0) {
+      T w = wsum[lane];
+      for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(0xffffffffu, w, o);
+      if (lane == 0) carry_s = w;
+    }
+    __syncthreads();
+    carry = carry_s;
+  } else {
+    carry = bsum[b];
+  }
+  const int64_t i = (int64_t)b * 1024 + t;
+  if (i < n) out[i] += carry;
+  if (direct && b == (int)gridDim.x - 1 && t == 0) *total = carry + bsum[b];
 }
 
 template <typename T>
@@ -82,15 +132,20 @@ static int scan_impl(const T *in, T *out, int64_t n, T *total_dev, cudaStream_t 
     cudaMemsetAsync(total_dev, 0, sizeof(T), s);
     return 0;
   }
-  int64_t nb = (n + 1023) / 1024;
+  const int64_t nb = (n + 1023) / 1024;
   T *bsum = (T *)dalloc(P, sizeof(T) * nb);
   if (!bsum) return TW_ENOMEM;
-  k_scan_block<T><<<(unsigned)nb, 1024, 0, s>>>(in, out, bsum, n);
+  k_scan_block<T><<<(unsigned)nb, 1024, 0, s>>>(in, out, bsum, n, total_dev);
   TW_LAUNCH();
-  k_scan_sums<T><<<1, 1024, 0, s>>>(bsum, nb, total_dev);
-  TW_LAUNCH();
-  k_scan_add<T><<<(unsigned)nb, 1024, 0, s>>>(out, bsum, n);
-  TW_LAUNCH();
+  if (nb > 1) {
+    const int direct = nb <= TW_SCAN_DIRECT;
+    if (!direct) {
+      k_scan_sums<T><<<1, 1024, 0, s>>>(bsum, nb, total_dev);
+      TW_LAUNCH();
+    }
+    k_scan_add<T><<<(unsigned)nb, 1024, 0, s>>>(out, bsum, n, total_dev, direct);
+    TW_LAUNCH();
+  }
   return check_cuda(cudaGetLastError(), "scan");
 }
 
@@ -251,11 +306,8 @@ __global__ void __launch_bounds__(32 * TW_WQ_WARPS) k_wq_weights(Dir D0, Dir D1,
     int j = jlo + r;
     double s = 0.0;
     int ea = max(elo, max(0, j - p)), eb = min(ehi, min(D.nel - 1, j));
-    for (int e = ea; e <= eb; e++) {
-      double h = 0.5 * (D.bp[e + 1] - D.bp[e]);
-      for (int g = 0; g < p1; g++)
-        s += D.gw[g] * h * D.GB[(e * p1 + g) * p1 + (i - e)] * D.GB[(e * p1 + g) * p1 + (j - e)];
-    }
+    for (int e = ea; e <= eb; e++)  // the Gauss products w_g h B_i B_j, tabulated per element
+      for (int g = 0; g < p1; g++) s += D.GW[((size_t)(e * p1 + g) * p1 + (i - e)) * p1 + (j - e)];
     sb[sys][r] = s;
   }
   if (gl == 0) sing[sys] = 0;
@@ -537,30 +589,57 @@ __device__ void sort_small(double *v, int n) {
 
 // Curve-wide features, once per patch: tangent points of both kinds (the
 // curve's tangent parallel to an axis) and the spline's segment joints.
-// feat[(kind * fcap + k) * 2 + {0,1}], nfeat[kind], kind 2 = joints.
+// feat[(kind * fcap + k) * 2 + {0,1}], nfeat[kind], kind 2 = joints.  One
+// warp per kind (96 threads); a spline's segments are spread over the lanes
+// and their points placed in segment order by a warp scan of the counts.
 __global__ void k_curve_features(CurveSet S, double *feat, int *nfeat, int fcap, int *flag) {
-  int kind = threadIdx.x;
-  if (kind >= 3) return;
+  const int kind = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (kind >= 3) return;  // the whole warp
   double *out = feat + (size_t)kind * fcap * 2;
-  int n = 0;
-  for (int ci = 0; ci < S.n; ci++) {
+  int n = 0;  // warp-uniform
+  bool over = false;
+  for (int ci = 0; ci < S.n && !over; ci++) {
     const Curve &C = S.c[ci];
-    if (kind < 2) {
+    if (kind < 2 && C.kind == TW_TRIM_BSPLINE3) {
+      int add = 0;  // this curve's points so far
+      for (int s0 = 0; s0 < C.nc; s0 += 32) {
+        const int sg = s0 + lane;
+        double f[4];
+        const int m = sg < C.nc ? seg_folds(C, sg, kind, f) : 0;
+        int incl = m;
+        for (int o = 1; o < 32; o <<= 1) {
+          const int v = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += v;
+        }
+        const int tot = __shfl_sync(0xffffffffu, incl, 31);
+        if (n + add + tot > fcap) {
+          over = true;
+          break;
+        }
+        for (int k = 0; k < 2 * m; k++) out[2 * (n + add + incl - m) + k] = f[k];
+        add += tot;
+      }
+      if (!over) n += add;
+    } else if (kind < 2) {
       // a conic writes its two tangent points unchecked
-      const int m = fcap - n >= 2 ? curve_folds(C, kind, out + 2 * n, fcap - n) : -1;
-      if (m < 0) {
-        atomicOr(flag, TWF_HITCAP);
-        break;
+      int m = -1;
+      if (lane == 0) m = fcap - n >= 2 ? curve_folds(C, kind, out + 2 * n, fcap - n) : -1;
+      m = __shfl_sync(0xffffffffu, m, 0);
+      if (m < 0) over = true;
+      else n += m;
+    } else if (C.kind == TW_TRIM_BSPLINE3) {
+      const int m = min(C.nc, fcap - n);
+      for (int sg = lane; sg < m; sg += 32) {
+        out[2 * (n + sg)] = C.seg[8 * sg];
+        out[2 * (n + sg) + 1] = C.seg[8 * sg + 4];
       }
       n += m;
-    } else if (C.kind == TW_TRIM_BSPLINE3) {
-      for (int sg = 0; sg < C.nc && n < fcap; sg++, n++) {
-        out[2 * n] = C.seg[8 * sg];
-        out[2 * n + 1] = C.seg[8 * sg + 4];
-      }
     }
   }
-  nfeat[kind] = n;
+  if (lane == 0) {
+    if (over) atomicOr(flag, TWF_HITCAP);
+    nfeat[kind] = n;
+  }
 }
 
 // One block of 64 threads per cut element.  Pass 0 (pts == NULL) counts the
@@ -1654,6 +1733,10 @@ static int read_flag(tw_patch *P, const char *stage) {
 }
 
 #define G1(n) (unsigned)(((n) + 255) / 256), 256, 0, st
+// one warp per block, for the short thread-per-item kernels whose items each
+// run a long FP64 chain (basis evaluations, root finding): a 256-thread block
+// would put eight such warps on one SM's FP64 pipe while other SMs idle
+#define G32(n) (unsigned)(((n) + 31) / 32), 32, 0, st
 
 int build_tables(tw_patch *P) {
   cudaStream_t st = P->stream;
@@ -1680,11 +1763,12 @@ int build_tables(tw_patch *P) {
   // WQ layout, basis tables, weights (Eq. 5): both directions per launch
   {
     auto g2 = [](int64_t n) { return dim3((unsigned)((n + 255) / 256), 2); };
-    k_wq_points<<<g2(std::max(A.nel, B.nel)), 256, 0, st>>>(A, B);
+    auto g2w = [](int64_t n) { return dim3((unsigned)((n + 31) / 32), 2); };  // warp blocks (G32)
+    k_wq_points<<<g2w(std::max(A.nel, B.nel)), 32, 0, st>>>(A, B);
     TW_LAUNCH();
     k_wq_ranges<<<g2(std::max(A.n, B.n)), 256, 0, st>>>(A, B);
     TW_LAUNCH();
-    k_gauss_tables<<<g2((int64_t)std::max(A.nel, B.nel) * p1), 256, 0, st>>>(A, B);
+    k_gauss_tables<<<g2w((int64_t)std::max(A.nel, B.nel) * p1), 32, 0, st>>>(A, B);
     TW_LAUNCH();
     const int nw = std::max(A.n, B.n);
     const int lda = std::max(A.qmax, B.qmax) + 1;
@@ -1721,9 +1805,9 @@ int build_tables(tw_patch *P) {
     nfeat = (int *)dalloc(P, sizeof(int) * 4);
     if (!lh || !lnh || !feat || !nfeat) return TW_ENOMEM;
     if (P->curves.n > 0) {
-      k_line_hits<<<G1(nl)>>>(P->curves, A, B, lh, lnh, P->flag);
+      k_line_hits<<<G32(nl)>>>(P->curves, A, B, lh, lnh, P->flag);
       TW_LAUNCH();
-      k_curve_features<<<1, 32, 0, st>>>(P->curves, feat, nfeat, fcap, P->flag);
+      k_curve_features<<<1, 96, 0, st>>>(P->curves, feat, nfeat, fcap, P->flag);
       TW_LAUNCH();
     }
     k_classify_elems<<<G1(ne)>>>(P->curves, A, B, lh, lnh, P->estate);
@@ -1852,7 +1936,7 @@ int build_tables(tw_patch *P) {
     line_off = (int64_t *)dalloc(P, sizeof(int64_t) * (P->ncut + 1));
     if (!cbr || !cnbr || !cnl || !line_off) return TW_ENOMEM;
     cudaMemsetAsync(cnl + P->ncut, 0, sizeof(int64_t), st);
-    k_cut_breaks<<<G1(P->ncut)>>>(A, B, P->cut_list, P->ncut, P->qc, lh, lnh, feat, nfeat, fcap,
+    k_cut_breaks<<<G32(P->ncut)>>>(A, B, P->cut_list, P->ncut, P->qc, lh, lnh, feat, nfeat, fcap,
                                   P->cut_o, cnbr, cbr, cnl, P->flag);
     TW_LAUNCH();
     if ((rc = exclusive_scan_i64(cnl, line_off, P->ncut + 1, tot64 + 2, st, P))) return rc;

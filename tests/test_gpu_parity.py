@@ -399,3 +399,34 @@ def test_graded_knots_spline_hole_density():
     dens = synth.density(rng, q=2, m=7)
     spec = synth.with_knots(synth.make_spec(4, 4, trim, coef=dens, method="dwq"), U1, U2)
     compare_full(spec)
+
+
+@pytest.mark.parametrize("method", ["hybrid", "dwq"])
+def test_scans_beyond_direct_carry_at_2048(method):
+    """2048 x 2048 elements, p = 2: the function, element and row-pointer
+    scans run over more than 2048 blocks of 1024 entries, so the block totals
+    are scanned by their own pass before the carries are added.  States, the
+    active numbering and the matrix size bit-exact against the oracle, and
+    sampled rows (cut and interior, the first and the last) against rows the
+    oracle forms one by one, by the sampled-row bar (relative Frobenius over
+    the rows)."""
+    spec = synth.make_spec(2, 2048, synth.circle(0.47, 0.53, 0.29), method=method)
+    G = gpu_patch(spec)
+    O = oracle.Patch(spec)
+    assert (G.n_rows, G.nnz) == (O.n_rows, O.nnz)
+    es, fs, act = [t.cpu().numpy() for t in G.states()]
+    oes, ofs, oact = O.states()
+    assert np.array_equal(es, oes) and np.array_equal(fs, ofs) and np.array_equal(act, oact)
+    rp, col, val = [t.cpu().numpy() for t in G.form_mass("fp64")]
+    assert rp[-1] == O.nnz
+    rng = np.random.default_rng(20)
+    gs = list(rng.choice(np.where(ofs == 2)[0], 20, replace=False))
+    gs += list(rng.choice(np.where(ofs == 1)[0], 20, replace=False))
+    rows = [int(oact[g]) for g in gs] + [0, O.n_rows - 1]
+    num = den = 0.0
+    for row in rows:
+        oc, ov = O.form_row(row)
+        assert np.array_equal(col[rp[row]:rp[row + 1]], oc)
+        num += np.sum((val[rp[row]:rp[row + 1]] - ov) ** 2)
+        den += np.sum(ov ** 2)
+    assert np.sqrt(num / den) <= TOL
