@@ -55,20 +55,35 @@ __device__ __forceinline__ T block_scan_incl(T v, T *wsum) {
   return wid > 0 ? x + wsum[wid - 1] : x;
 }
 
+// One or two independent scans per launch (blockIdx.y picks the scan; blocks
+// past a scan's own count return).
+template <typename T>
+struct ScanJob {
+  const T *in;
+  T *out, *bsum, *total;
+  int64_t n, nb;
+  int direct;
+};
+template <typename T>
+struct ScanJobs {
+  ScanJob<T> j[2];
+};
+
 // block scan: out = exclusive scan within the block, bsum = the block's total;
 // a single-block scan also writes the grand total
 template <typename T>
-__global__ void __launch_bounds__(1024) k_scan_block(const T *in, T *out, T *bsum, int64_t n,
-                                                     T *total) {
+__global__ void __launch_bounds__(1024) k_scan_block(ScanJobs<T> J) {
   __shared__ T wsum[32];
+  const ScanJob<T> &S = J.j[blockIdx.y];
+  if ((int64_t)blockIdx.x >= S.nb) return;  // the whole block
   const int t = threadIdx.x;
   const int64_t i = (int64_t)blockIdx.x * 1024 + t;
-  const T v = i < n ? in[i] : (T)0;
+  const T v = i < S.n ? S.in[i] : (T)0;
   const T incl = block_scan_incl(v, wsum);
-  if (i < n) out[i] = incl - v;
+  if (i < S.n) S.out[i] = incl - v;
   if (t == 1023) {
-    bsum[blockIdx.x] = incl;
-    if (gridDim.x == 1) *total = incl;
+    S.bsum[blockIdx.x] = incl;
+    if (S.nb == 1) *S.total = incl;
   }
 }
 
@@ -98,16 +113,17 @@ __global__ void __launch_bounds__(1024) k_scan_sums(T *bsum, int64_t nb, T *tota
 // formed by the block itself (direct; the last block then writes the grand
 // total) or read from the scanned totals
 template <typename T>
-__global__ void __launch_bounds__(1024) k_scan_add(T *out, const T *bsum, int64_t n, T *total,
-                                                   int direct) {
+__global__ void __launch_bounds__(1024) k_scan_add(ScanJobs<T> J) {
   __shared__ T wsum[32];
   __shared__ T carry_s;
+  const ScanJob<T> &S = J.j[blockIdx.y];
+  const int64_t b = blockIdx.x;
+  if (S.nb < 2 || b >= S.nb) return;  // the whole block
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-  const int b = blockIdx.x;
   T carry;
-  if (direct) {
+  if (S.direct) {
     T s = 0;
-    for (int j = t; j < b; j += 1024) s += bsum[j];
+    for (int64_t j = t; j < b; j += 1024) s += S.bsum[j];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     if (lane == 0) wsum[wid] = s;
     __syncthreads();
@@ -119,34 +135,60 @@ __global__ void __launch_bounds__(1024) k_scan_add(T *out, const T *bsum, int64_
     __syncthreads();
     carry = carry_s;
   } else {
-    carry = bsum[b];
+    carry = S.bsum[b];
   }
-  const int64_t i = (int64_t)b * 1024 + t;
-  if (i < n) out[i] += carry;
-  if (direct && b == (int)gridDim.x - 1 && t == 0) *total = carry + bsum[b];
+  const int64_t i = b * 1024 + t;
+  if (i < S.n) S.out[i] += carry;
+  if (S.direct && b == S.nb - 1 && t == 0) *S.total = carry + S.bsum[b];
+}
+
+// exclusive scans of in0 (n0 entries) and, if n1 >= 0, of in1 (n1 entries),
+// with their totals, in two launches at most (three past TW_SCAN_DIRECT blocks)
+template <typename T>
+static int scan2_impl(const T *in0, T *out0, int64_t n0, T *tot0, const T *in1, T *out1,
+                      int64_t n1, T *tot1, cudaStream_t s, tw_patch *P) {
+  ScanJobs<T> J;
+  const int ns = n1 >= 0 ? 2 : 1;
+  int64_t nbmax = 0;
+  bool any_add = false;
+  for (int k = 0; k < ns; k++) {
+    ScanJob<T> &S = J.j[k];
+    S.in = k ? in1 : in0;
+    S.out = k ? out1 : out0;
+    S.total = k ? tot1 : tot0;
+    S.n = k ? n1 : n0;
+    S.nb = (S.n + 1023) / 1024;
+    S.direct = S.nb <= TW_SCAN_DIRECT;
+    S.bsum = nullptr;
+    if (S.n <= 0) {
+      S.nb = 0;
+      cudaMemsetAsync(S.total, 0, sizeof(T), s);
+      continue;
+    }
+    S.bsum = (T *)dalloc(P, sizeof(T) * S.nb);
+    if (!S.bsum) return TW_ENOMEM;
+    nbmax = std::max(nbmax, S.nb);
+    any_add = any_add || S.nb > 1;
+  }
+  if (ns == 1) J.j[1] = J.j[0];  // never read (gridDim.y = 1)
+  if (nbmax == 0) return 0;
+  k_scan_block<T><<<dim3((unsigned)nbmax, ns), 1024, 0, s>>>(J);
+  TW_LAUNCH();
+  if (any_add) {
+    for (int k = 0; k < ns; k++)
+      if (J.j[k].nb > 1 && !J.j[k].direct) {
+        k_scan_sums<T><<<1, 1024, 0, s>>>(J.j[k].bsum, J.j[k].nb, J.j[k].total);
+        TW_LAUNCH();
+      }
+    k_scan_add<T><<<dim3((unsigned)nbmax, ns), 1024, 0, s>>>(J);
+    TW_LAUNCH();
+  }
+  return check_cuda(cudaGetLastError(), "scan");
 }
 
 template <typename T>
 static int scan_impl(const T *in, T *out, int64_t n, T *total_dev, cudaStream_t s, tw_patch *P) {
-  if (n <= 0) {
-    cudaMemsetAsync(total_dev, 0, sizeof(T), s);
-    return 0;
-  }
-  const int64_t nb = (n + 1023) / 1024;
-  T *bsum = (T *)dalloc(P, sizeof(T) * nb);
-  if (!bsum) return TW_ENOMEM;
-  k_scan_block<T><<<(unsigned)nb, 1024, 0, s>>>(in, out, bsum, n, total_dev);
-  TW_LAUNCH();
-  if (nb > 1) {
-    const int direct = nb <= TW_SCAN_DIRECT;
-    if (!direct) {
-      k_scan_sums<T><<<1, 1024, 0, s>>>(bsum, nb, total_dev);
-      TW_LAUNCH();
-    }
-    k_scan_add<T><<<(unsigned)nb, 1024, 0, s>>>(out, bsum, n, total_dev, direct);
-    TW_LAUNCH();
-  }
-  return check_cuda(cudaGetLastError(), "scan");
+  return scan2_impl<T>(in, out, n, total_dev, nullptr, nullptr, -1, nullptr, s, P);
 }
 
 int exclusive_scan_i32(const int32_t *in, int32_t *out, int64_t n, int32_t *total, cudaStream_t s,
@@ -194,14 +236,15 @@ __global__ void k_gauss_nodes(int q, double *x, double *w) {
   w[k] = 2.0 / ((1.0 - z * z) * dp * dp);
 }
 
-// the per-direction table kernels run both directions in one launch:
-// blockIdx.y picks the direction
-// thread per element: its m = qoff[e+1] - qoff[e] points (R1), uniform in
-// the element's interior, with the basis and derivatives there
-__global__ void k_wq_points(Dir D0, Dir D1) {
-  const Dir &D = blockIdx.y ? D1 : D0;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= D.nel) return;
+// The per-direction tables, both directions and all three kinds in one launch
+// of one-warp blocks (blockIdx.y picks the direction; each item runs a long
+// FP64 chain, so the items are spread over many SMs).  Each kind is an
+// out-of-line routine, so no function holds two inlined copies of the
+// Cox-de Boor triangle.
+
+// element e: its m = qoff[e+1] - qoff[e] WQ points (R1), uniform in the
+// element's interior, with the basis and derivatives there
+static __device__ __noinline__ void wq_points_item(const Dir &D, int e) {
   const int p = D.p, k0 = D.qoff[e], m = D.qoff[e + 1] - k0;
   const double a = D.bp[e], b = D.bp[e + 1];
   for (int j = 0; j < m; j++) {
@@ -218,20 +261,18 @@ __global__ void k_wq_points(Dir D0, Dir D1) {
   }
 }
 
-__global__ void k_wq_ranges(Dir D0, Dir D1) {
-  const Dir &D = blockIdx.y ? D1 : D0;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= D.n) return;
+// test function i: the run of WQ points of its support
+__device__ __forceinline__ void wq_ranges_item(const Dir &D, int i) {
   int lo = max(0, i - D.p), hi = min(D.nel - 1, i);
   D.qbeg[i] = wq_off(D, lo);
   D.qcnt[i] = wq_off(D, hi + 1) - D.qbeg[i];
 }
 
-__global__ void k_gauss_tables(Dir D0, Dir D1) {
-  const Dir &D = blockIdx.y ? D1 : D0;
-  int id = blockIdx.x * blockDim.x + threadIdx.x;
+// Gauss point g of element e: basis values and derivatives, and the weighted
+// products of the element matrices (Gauss weight x Jacobian of the span map x
+// two basis values), once per element of the direction
+static __device__ __noinline__ void gauss_tables_item(const Dir &D, int id) {
   int p1 = D.p + 1;
-  if (id >= D.nel * p1) return;
   int e = id / p1, g = id % p1;
   double a = D.bp[e], b = D.bp[e + 1];
   double x = a + (b - a) * 0.5 * (D.gx[g] + 1.0);
@@ -245,12 +286,27 @@ __global__ void k_gauss_tables(Dir D0, Dir D1) {
     D.GB[(e * p1 + g) * p1 + k] = N[k];
     D.dGB[(e * p1 + g) * p1 + k] = dN[k];
   }
-  // the weighted products of the element matrices (Gauss weight x Jacobian of
-  // the span map x two basis values), once per element of the direction
   const double hw = D.gw[g] * (0.5 * (b - a));
   double *gw3 = D.GW + (size_t)(e * p1 + g) * p1 * p1;
   for (int i = 0; i < p1; i++)
     for (int k = 0; k < p1; k++) gw3[i * p1 + k] = hw * N[i] * N[k];
+}
+
+// blocks [0, b0): elements (WQ points); [b0, b0 + b1): test functions (WQ
+// ranges); the rest: element Gauss points (Gauss tables)
+__global__ void __launch_bounds__(32) k_dir_tables(Dir D0, Dir D1, int b0, int b1) {
+  const Dir &D = blockIdx.y ? D1 : D0;
+  const int b = blockIdx.x;
+  if (b < b0) {
+    const int e = b * 32 + threadIdx.x;
+    if (e < D.nel) wq_points_item(D, e);
+  } else if (b < b0 + b1) {
+    const int i = (b - b0) * 32 + threadIdx.x;
+    if (i < D.n) wq_ranges_item(D, i);
+  } else {
+    const int id = (b - b0 - b1) * 32 + threadIdx.x;
+    if (id < D.nel * (D.p + 1)) gauss_tables_item(D, id);
+  }
 }
 
 // B_j(x_k) from the WQ basis table (zero off the span)
@@ -381,10 +437,8 @@ __device__ void curve_point0(const Curve &C, double *xy) {
 // vertical knot lines x = bp1[l], [nel1+1, nel1+nel2+1] the horizontal knot
 // lines, and the last nel2 the horizontal lines through the element centres of
 // each row (visibility by the parity of crossings to the right, reading R8).
-__global__ void k_line_hits(CurveSet C, Dir A, Dir B, double *hits, int *nh, int *flag) {
-  int l = blockIdx.x * blockDim.x + threadIdx.x;
-  int nl = (A.nel + 1) + (B.nel + 1) + B.nel;
-  if (l >= nl) return;
+__device__ __forceinline__ void line_hits_item(const CurveSet &C, const Dir &A, const Dir &B,
+                                               int l, double *hits, int *nh, int *flag) {
   int o;
   double s;
   if (l <= A.nel) {
@@ -464,11 +518,17 @@ __global__ void k_classify_elems(CurveSet C, Dir A, Dir B, const double *hits, c
   estate[id] = st;
 }
 
-// function state from its support elements; active flag for the scan
+// function state from its support elements; active flag for the scan.  The
+// same threads clear the disc flags of both directions (nel + 1 each) and set
+// every DWQ choice to none (-1) for the stages after.
 __global__ void k_classify_funcs(Dir A, Dir B, const uint8_t *estate, uint8_t *fstate,
-                                 int32_t *aflag, int method, int32_t *cflag, int32_t *counters) {
+                                 int32_t *aflag, int method, int32_t *cflag, int32_t *counters,
+                                 int32_t *dflag0, int32_t *dflag1, int32_t *choice) {
   int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g <= A.nel) dflag0[g] = 0;
+  if (g <= B.nel) dflag1[g] = 0;
   if (g >= A.n * B.n) return;
+  reinterpret_cast<int4 *>(choice)[g] = make_int4(-1, -1, -1, -1);
   int i1 = g % A.n, i2 = g / A.n;
   int tot = 0, nreg = 0, ninv = 0;
   for (int e2 = max(0, i2 - B.p); e2 <= min(B.nel - 1, i2); e2++)
@@ -488,32 +548,46 @@ __global__ void k_classify_funcs(Dir A, Dir B, const uint8_t *estate, uint8_t *f
   if (st == TW_FUNC_INTERIOR) atomicAdd(&counters[1], 1);
 }
 
-__global__ void k_act_finalize(const int32_t *aflag, int32_t *act, int32_t *rowg, int64_t nf) {
+// compacted lists from flags (exclusive scans already in pos), up to four per
+// launch (blockIdx.y picks the list): list[pos[g]] = g for the flagged g, and
+// slot[g] = pos[g] or -1 when a slot map is asked for.  With slot == pos this
+// also turns the scan of the active flags into the active numbering (-1 for
+// the inactive) and list into its inverse.
+struct CompactJob {
+  const int32_t *flag, *pos;
+  int32_t *list, *slot;
+  int64_t n;
+};
+struct CompactJobs {
+  CompactJob j[4];
+};
+__global__ void k_compact(CompactJobs J) {
+  const CompactJob &C = J.j[blockIdx.y];
   int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= nf) return;
-  if (aflag[g]) {
-    rowg[act[g]] = (int32_t)g;
-  } else {
-    act[g] = -1;
+  if (g >= C.n) return;
+  if (C.flag[g]) {
+    const int32_t ps = C.pos[g];
+    C.list[ps] = (int32_t)g;
+    if (C.slot) C.slot[g] = ps;
+  } else if (C.slot) {
+    C.slot[g] = -1;
   }
 }
-
-// compacted list from flags (exclusive scan already in pos)
-__global__ void k_compact(const int32_t *flag, const int32_t *pos, int32_t *list, int32_t *slot,
-                          int64_t n) {
-  int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= n) return;
-  if (flag[g]) {
-    list[pos[g]] = (int32_t)g;
-    if (slot) slot[g] = pos[g];
-  } else if (slot) {
-    slot[g] = -1;
-  }
+static void launch_compact(const CompactJob *jobs, int nj, cudaStream_t st) {
+  CompactJobs J;
+  int64_t nmax = 0;
+  for (int k = 0; k < 4; k++) J.j[k] = jobs[k < nj ? k : 0];
+  for (int k = 0; k < nj; k++) nmax = std::max(nmax, jobs[k].n);
+  if (nmax == 0) return;
+  k_compact<<<dim3((unsigned)((nmax + 255) / 256), nj), 256, 0, st>>>(J);
+  TW_LAUNCH();
 }
 
-// R11: active columns in the (2p+1)^2 window
-__global__ void k_row_counts(Dir A, Dir B, const int32_t *act, int64_t *cnt) {
+// R11: active columns in the (2p+1)^2 window; cnt[n_rows] = 0 closes the
+// array, so that its exclusive scan ends with the total
+__global__ void k_row_counts(Dir A, Dir B, const int32_t *act, int64_t *cnt, int n_rows) {
   int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g == 0) cnt[n_rows] = 0;
   if (g >= A.n * B.n) return;
   int32_t r = act[g];
   if (r < 0) return;
@@ -523,8 +597,6 @@ __global__ void k_row_counts(Dir A, Dir B, const int32_t *act, int64_t *cnt) {
     for (int j1 = max(0, i1 - p); j1 <= min(A.n - 1, i1 + p); j1++) c += act[j2 * A.n + j1] >= 0;
   cnt[r] = c;
 }
-
-__global__ void k_set_last(int64_t *a, int64_t idx, const int64_t *v) { a[idx] = *v; }
 
 // sum-factorised det J on the WQ grid: stage A contracts direction 2
 __global__ void k_geo_stageA(Geo G, Dir A, Dir B, double *Gt) {
@@ -590,11 +662,11 @@ __device__ void sort_small(double *v, int n) {
 // Curve-wide features, once per patch: tangent points of both kinds (the
 // curve's tangent parallel to an axis) and the spline's segment joints.
 // feat[(kind * fcap + k) * 2 + {0,1}], nfeat[kind], kind 2 = joints.  One
-// warp per kind (96 threads); a spline's segments are spread over the lanes
-// and their points placed in segment order by a warp scan of the counts.
-__global__ void k_curve_features(CurveSet S, double *feat, int *nfeat, int fcap, int *flag) {
-  const int kind = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (kind >= 3) return;  // the whole warp
+// warp per kind; a spline's segments are spread over the lanes and their
+// points placed in segment order by a warp scan of the counts.
+__device__ __forceinline__ void curve_features_warp(const CurveSet &S, int kind, int lane,
+                                                    double *feat, int *nfeat, int fcap,
+                                                    int *flag) {
   double *out = feat + (size_t)kind * fcap * 2;
   int n = 0;  // warp-uniform
   bool over = false;
@@ -639,6 +711,20 @@ __global__ void k_curve_features(CurveSet S, double *feat, int *nfeat, int fcap,
   if (lane == 0) {
     if (over) atomicOr(flag, TWF_HITCAP);
     nfeat[kind] = n;
+  }
+}
+
+// the knot lines' crossings (one-warp blocks [0, nbl), a line per thread) and
+// the curve-wide features (three more blocks, a kind per block) in one launch
+__global__ void __launch_bounds__(32) k_curve_lines(CurveSet C, Dir A, Dir B, double *hits,
+                                                    int *nh, int nbl, double *feat, int *nfeat,
+                                                    int fcap, int *flag) {
+  const int b = blockIdx.x;
+  if (b < nbl) {
+    const int l = b * 32 + threadIdx.x;
+    if (l < (A.nel + 1) + (B.nel + 1) + B.nel) line_hits_item(C, A, B, l, hits, nh, flag);
+  } else {
+    curve_features_warp(C, b - nbl, threadIdx.x, feat, nfeat, fcap, flag);
   }
 }
 
@@ -994,23 +1080,6 @@ __global__ void __launch_bounds__(TW_CPT_THREADS)
   }
 }
 
-// regular elements whose Gauss points some row uses (hybrid Gauss, DWQ rest, Gauss method)
-__global__ void k_gauss_flags(Dir A, Dir B, const uint8_t *estate, const uint8_t *fstate,
-                              int method, int32_t *gflag) {
-  int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= A.nel * B.nel) return;
-  int f = 0;
-  if (estate[e] == TW_ELEM_REGULAR && method != TW_METHOD_NAIVE) {
-    if (method == TW_METHOD_GAUSS) {
-      f = 1;
-    } else {
-      int e1 = e % A.nel, e2 = e / A.nel;
-      for (int b = 0; b <= B.p && !f; b++)
-        for (int a = 0; a <= A.p && !f; a++) f = fstate[(e2 + b) * A.n + (e1 + a)] == TW_FUNC_CUT;
-    }
-  }
-  gflag[e] = f;
-}
 
 // c at the Gauss points of the listed elements, one warp per element.  For the
 // spline geometry the control net is contracted over direction 1 once per
@@ -1680,9 +1749,25 @@ static void launch_gauss_matrices_impl(tw_patch *P, const int32_t *glist, cudaSt
   TW_LAUNCH();
 }
 
-__global__ void k_is_cut(const uint8_t *es, int32_t *f, int64_t n) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) f[i] = es[i] == TW_ELEM_CUT;
+// per element: cut (for the cut list) and regular with Gauss points some row
+// uses (hybrid Gauss, DWQ rest, Gauss method: for the Gauss list)
+__global__ void k_elem_flags(Dir A, Dir B, const uint8_t *estate, const uint8_t *fstate,
+                             int method, int32_t *eflag, int32_t *gflag) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= A.nel * B.nel) return;
+  const uint8_t es = estate[e];
+  eflag[e] = es == TW_ELEM_CUT;
+  int f = 0;
+  if (es == TW_ELEM_REGULAR && method != TW_METHOD_NAIVE) {
+    if (method == TW_METHOD_GAUSS) {
+      f = 1;
+    } else {
+      int e1 = e % A.nel, e2 = e / A.nel;
+      for (int b = 0; b <= B.p && !f; b++)
+        for (int a = 0; a <= A.p && !f; a++) f = fstate[(e2 + b) * A.n + (e1 + a)] == TW_FUNC_CUT;
+    }
+  }
+  gflag[e] = f;
 }
 
 // ---------------------------------------------------------------------------
@@ -1762,13 +1847,9 @@ int build_tables(tw_patch *P) {
 
   // WQ layout, basis tables, weights (Eq. 5): both directions per launch
   {
-    auto g2 = [](int64_t n) { return dim3((unsigned)((n + 255) / 256), 2); };
-    auto g2w = [](int64_t n) { return dim3((unsigned)((n + 31) / 32), 2); };  // warp blocks (G32)
-    k_wq_points<<<g2w(std::max(A.nel, B.nel)), 32, 0, st>>>(A, B);
-    TW_LAUNCH();
-    k_wq_ranges<<<g2(std::max(A.n, B.n)), 256, 0, st>>>(A, B);
-    TW_LAUNCH();
-    k_gauss_tables<<<g2w((int64_t)std::max(A.nel, B.nel) * p1), 32, 0, st>>>(A, B);
+    const int b0 = (std::max(A.nel, B.nel) + 31) / 32, b1 = (std::max(A.n, B.n) + 31) / 32;
+    const int b2 = (std::max(A.nel, B.nel) * p1 + 31) / 32;
+    k_dir_tables<<<dim3(b0 + b1 + b2, 2), 32, 0, st>>>(A, B, b0, b1);
     TW_LAUNCH();
     const int nw = std::max(A.n, B.n);
     const int lda = std::max(A.qmax, B.qmax) + 1;
@@ -1792,7 +1873,17 @@ int build_tables(tw_patch *P) {
   int32_t *aflag = (int32_t *)dalloc(P, sizeof(int32_t) * nf);
   int32_t *cflag = (int32_t *)dalloc(P, sizeof(int32_t) * nf);
   int32_t *cpos = (int32_t *)dalloc(P, sizeof(int32_t) * nf);
-  if (!aflag || !cflag || !cpos) return TW_ENOMEM;
+  int32_t *eflag = (int32_t *)dalloc(P, sizeof(int32_t) * ne);
+  int32_t *epos = (int32_t *)dalloc(P, sizeof(int32_t) * ne);
+  int32_t *gflag = (int32_t *)dalloc(P, sizeof(int32_t) * ne);
+  int32_t *gpos = (int32_t *)dalloc(P, sizeof(int32_t) * ne);
+  if (!aflag || !cflag || !cpos || !eflag || !epos || !gflag || !gpos) return TW_ENOMEM;
+  int32_t *dflag[2], *dpos[2];  // disc knots of the DWQ regions (R7), per direction
+  for (int d = 0; d < 2; d++) {
+    dflag[d] = (int32_t *)dalloc(P, sizeof(int32_t) * (P->d[d].nel + 1));
+    dpos[d] = (int32_t *)dalloc(P, sizeof(int32_t) * (P->d[d].nel + 1));
+    if (!dflag[d] || !dpos[d]) return TW_ENOMEM;
+  }
   int fcap = 4;
   for (int ci = 0; ci < P->curves.n; ci++) fcap += 2 * P->curves.c[ci].nc + 4;
   double *lh, *feat;
@@ -1805,54 +1896,40 @@ int build_tables(tw_patch *P) {
     nfeat = (int *)dalloc(P, sizeof(int) * 4);
     if (!lh || !lnh || !feat || !nfeat) return TW_ENOMEM;
     if (P->curves.n > 0) {
-      k_line_hits<<<G32(nl)>>>(P->curves, A, B, lh, lnh, P->flag);
-      TW_LAUNCH();
-      k_curve_features<<<1, 96, 0, st>>>(P->curves, feat, nfeat, fcap, P->flag);
+      const int nbl = (nl + 31) / 32;
+      k_curve_lines<<<nbl + 3, 32, 0, st>>>(P->curves, A, B, lh, lnh, nbl, feat, nfeat, fcap,
+                                            P->flag);
       TW_LAUNCH();
     }
     k_classify_elems<<<G1(ne)>>>(P->curves, A, B, lh, lnh, P->estate);
     TW_LAUNCH();
   }
-  k_classify_funcs<<<G1(nf)>>>(A, B, P->estate, P->fstate, aflag, P->method, cflag, counters);
+  k_classify_funcs<<<G1(nf)>>>(A, B, P->estate, P->fstate, aflag, P->method, cflag, counters,
+                               dflag[0], dflag[1], P->choice);
   TW_LAUNCH();
-  if ((rc = exclusive_scan_i32(aflag, P->act, nf, tot32 + 0, st, P))) return rc;
-  if ((rc = exclusive_scan_i32(cflag, cpos, nf, tot32 + 1, st, P))) return rc;
-  // cut elements
-  int32_t *eflag = (int32_t *)dalloc(P, sizeof(int32_t) * ne);
-  int32_t *epos = (int32_t *)dalloc(P, sizeof(int32_t) * ne);
-  int32_t *gflag = (int32_t *)dalloc(P, sizeof(int32_t) * ne);
-  int32_t *gpos = (int32_t *)dalloc(P, sizeof(int32_t) * ne);
-  if (!eflag || !epos || !gflag || !gpos) return TW_ENOMEM;
-  k_is_cut<<<G1(ne)>>>(P->estate, eflag, ne);
+  if ((rc = scan2_impl<int32_t>(aflag, P->act, nf, tot32 + 0, cflag, cpos, nf, tot32 + 1, st, P)))
+    return rc;
+  // cut elements and the regular elements integrated by Gauss
+  k_elem_flags<<<G1(ne)>>>(A, B, P->estate, P->fstate, P->method, eflag, gflag);
   TW_LAUNCH();
-  if ((rc = exclusive_scan_i32(eflag, epos, ne, tot32 + 2, st, P))) return rc;
-  k_gauss_flags<<<G1(ne)>>>(A, B, P->estate, P->fstate, P->method, gflag);
-  TW_LAUNCH();
-  if ((rc = exclusive_scan_i32(gflag, gpos, ne, tot32 + 3, st, P))) return rc;
+  if ((rc = scan2_impl<int32_t>(eflag, epos, ne, tot32 + 2, gflag, gpos, ne, tot32 + 3, st, P)))
+    return rc;
   // DWQ choice (R7) and disc flags
-  int32_t *dflag[2], *dpos[2];
-  for (int d = 0; d < 2; d++) {
-    dflag[d] = (int32_t *)dalloc(P, sizeof(int32_t) * (P->d[d].nel + 1));
-    dpos[d] = (int32_t *)dalloc(P, sizeof(int32_t) * (P->d[d].nel + 1));
-    if (!dflag[d] || !dpos[d]) return TW_ENOMEM;
-    cudaMemsetAsync(dflag[d], 0, sizeof(int32_t) * (P->d[d].nel + 1), st);
-  }
-  cudaMemsetAsync(P->choice, 0xff, sizeof(int32_t) * 4 * nf, st);
   if (P->method == TW_METHOD_DWQ) {
     // the cut functions (cflag marks exactly those for DWQ) as a list, its
     // length read by the choice kernel from the scan's total
     int32_t *cfl = (int32_t *)dalloc(P, sizeof(int32_t) * nf);
     if (!cfl) return TW_ENOMEM;
-    k_compact<<<G1(nf)>>>(cflag, cpos, cfl, nullptr, nf);
-    TW_LAUNCH();
+    const CompactJob cj = {cflag, cpos, cfl, nullptr, nf};
+    launch_compact(&cj, 1, st);
     const int nb = (int)std::min<int64_t>((nf + TW_CHOICE_WARPS - 1) / TW_CHOICE_WARPS, 152 * 8);
     k_dwq_choice<<<nb, 32 * TW_CHOICE_WARPS, 0, st>>>(A, B, P->estate, cfl, tot32 + 1, P->choice,
                                                        dflag[0], dflag[1], counters + 2);
     TW_LAUNCH();
   }
-  for (int d = 0; d < 2; d++)
-    if ((rc = exclusive_scan_i32(dflag[d], dpos[d], P->d[d].nel + 1, tot32 + 4 + d, st, P)))
-      return rc;
+  if ((rc = scan2_impl<int32_t>(dflag[0], dpos[0], A.nel + 1, tot32 + 4, dflag[1], dpos[1],
+                                B.nel + 1, tot32 + 5, st, P)))
+    return rc;
   int32_t hc[8];
   int32_t hcount[4];
   cudaMemcpyAsync(hc, tot32, sizeof(hc), cudaMemcpyDeviceToHost, st);
@@ -1880,19 +1957,18 @@ int build_tables(tw_patch *P) {
   if (!P->rowg || !P->row_ptr || !cnt || !P->cutrows || !P->cut_list || !P->cut_off ||
       !glist || !P->gc)
     return TW_ENOMEM;
-  k_act_finalize<<<G1(nf)>>>(aflag, P->act, P->rowg, nf);
+  {  // active numbering (act, -1 off the active set) and its inverse rowg; the
+     // cut-row, cut-element and Gauss-element lists with their slot maps
+    const CompactJob cj[4] = {{aflag, P->act, P->rowg, P->act, nf},
+                              {cflag, cpos, P->cutrows, nullptr, nf},
+                              {eflag, epos, P->cut_list, P->cut_slot, ne},
+                              {gflag, gpos, glist, P->gslot, ne}};
+    launch_compact(cj, 4, st);
+  }
+  k_row_counts<<<G1(nf)>>>(A, B, P->act, cnt, P->n_rows);
   TW_LAUNCH();
-  k_row_counts<<<G1(nf)>>>(A, B, P->act, cnt);
-  TW_LAUNCH();
-  if ((rc = exclusive_scan_i64(cnt, P->row_ptr, P->n_rows, tot64 + 0, st, P))) return rc;
-  k_set_last<<<1, 1, 0, st>>>(P->row_ptr, P->n_rows, tot64 + 0);
-  TW_LAUNCH();
-  k_compact<<<G1(nf)>>>(cflag, cpos, P->cutrows, nullptr, nf);
-  TW_LAUNCH();
-  k_compact<<<G1(ne)>>>(eflag, epos, P->cut_list, P->cut_slot, ne);
-  TW_LAUNCH();
-  k_compact<<<G1(ne)>>>(gflag, gpos, glist, P->gslot, ne);
-  TW_LAUNCH();
+  // n_rows + 1 entries, the last 0: row_ptr[n_rows] = nnz
+  if ((rc = exclusive_scan_i64(cnt, P->row_ptr, P->n_rows + 1, tot64 + 0, st, P))) return rc;
 
   // c at the WQ grid (Eq. 6), sum-factorised for the spline geometry
   double *Gt = nullptr;
@@ -1986,6 +2062,7 @@ int build_tables(tw_patch *P) {
   }
   // DWQ rules per disc knot, both directions in one launch
   DwqOut dout[2];
+  CompactJob dj[2];  // the disc knots of both directions as lists, one launch
   for (int d = 0; d < 2; d++) {
     Dir &D = P->d[d];
     int nd = P->ndisc[d];
@@ -2001,11 +2078,11 @@ int build_tables(tw_patch *P) {
       return TW_ENOMEM;
     int32_t *dlist = (int32_t *)dalloc(P, sizeof(int32_t) * (nd + 1));
     if (!P->dwq_x[d] || !P->dwq_np[d] || !P->dwq_w[d] || !dlist) return TW_ENOMEM;
-    k_compact<<<G1(D.nel + 1)>>>(dflag[d], dpos[d], dlist, P->disc_slot[d], D.nel + 1);
-    TW_LAUNCH();
+    dj[d] = CompactJob{dflag[d], dpos[d], dlist, P->disc_slot[d], (int64_t)D.nel + 1};
     dout[d] = DwqOut{dlist,          nd,           P->dwq_x[d], P->dwq_w[d], P->dwq_B[d],
                      P->dwq_dB[d],   P->dwq_np[d], P->dwq_k[d], P->dwq_e[d], P->dwq_r[d]};
   }
+  launch_compact(dj, 2, st);
   if (P->ndisc[0] + P->ndisc[1] > 0) {
     static std::once_flag dwq_attr[64];
     int dev = 0;
