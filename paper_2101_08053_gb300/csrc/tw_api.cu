@@ -372,6 +372,19 @@ extern "C" int tw_patch_create(const tw_patch_desc *desc, tw_patch **out) {
   double *hbp[2] = {nullptr, nullptr};
   int *hoff[2] = {nullptr, nullptr};
   uint8_t *htwo[2] = {nullptr, nullptr};
+  // the small tables (knots, breakpoints, WQ offsets and flags, curve control
+  // points, the zeroed error flags) go up in one copy from one packed staging
+  // buffer, kept with the others: each entry is (address of the device
+  // pointer to set, host source or NULL for zeros, bytes)
+  struct Upload {
+    void *dst;
+    const void *src;
+    size_t bytes;
+  };
+  Upload ups[9 + TW_MAXCURVES];
+  int nup = 0;
+  char *hpack = nullptr, *dpack = nullptr;
+  size_t packed = 0;
 #define ALLOC(ptr, T, n)                                   \
   do {                                                     \
     (ptr) = (T *)dalloc(P, sizeof(T) * (size_t)(n));       \
@@ -426,8 +439,6 @@ extern "C" int tw_patch_create(const tw_patch_desc *desc, tw_patch **out) {
         goto fail;
       }
       int W = 2 * p + 1;
-      ALLOC(D.U, double, D.nk);
-      ALLOC(D.bp, double, D.nel + 1);
       ALLOC(D.xq, double, D.nq);
       ALLOC(D.qel, int, D.nq);
       ALLOC(D.qbeg, int, D.n);
@@ -440,18 +451,16 @@ extern "C" int tw_patch_create(const tw_patch_desc *desc, tw_patch **out) {
       ALLOC(D.GB, double, (size_t)D.nel * (p + 1) * (p + 1));
       ALLOC(D.dGB, double, (size_t)D.nel * (p + 1) * (p + 1));
       ALLOC(D.GW, double, (size_t)D.nel * (p + 1) * (p + 1) * (p + 1));
-      ALLOC(D.qoff, int, D.nel + 1);
-      ALLOC(D.two, uint8_t, D.n);
-      cudaMemcpyAsync(D.qoff, hoff[d], sizeof(int) * (D.nel + 1), cudaMemcpyHostToDevice, st);
-      cudaMemcpyAsync(D.two, htwo[d], (size_t)D.n, cudaMemcpyHostToDevice, st);
+      ups[nup++] = Upload{&D.qoff, hoff[d], sizeof(int) * (D.nel + 1)};
+      ups[nup++] = Upload{&D.two, htwo[d], (size_t)D.n};
       hbp[d] = (double *)malloc(sizeof(double) * (D.nel + 1));
       if (!hbp[d]) {
         set_error("tw_patch_create: out of host memory");
         goto fail;
       }
       for (int e = 0; e <= D.nel; e++) hbp[d][e] = desc->knots[d][p + e];
-      cudaMemcpyAsync(D.U, desc->knots[d], sizeof(double) * D.nk, cudaMemcpyHostToDevice, st);
-      cudaMemcpyAsync(D.bp, hbp[d], sizeof(double) * (D.nel + 1), cudaMemcpyHostToDevice, st);
+      ups[nup++] = Upload{&D.U, desc->knots[d], sizeof(double) * D.nk};
+      ups[nup++] = Upload{&D.bp, hbp[d], sizeof(double) * (D.nel + 1)};
     }
     Dir &A = P->d[0];
     Dir &B = P->d[1];
@@ -471,13 +480,11 @@ extern "C" int tw_patch_create(const tw_patch_desc *desc, tw_patch **out) {
       P->curve_ctrl[ci] = nullptr;
       if (Cv.nc > 0) {
         double *seg, *box;
-        ALLOC(P->curve_ctrl[ci], double, 2 * Cv.nc);
         ALLOC(seg, double, 8 * Cv.nc);
         ALLOC(box, double, 4 * Cv.nc);
         Cv.seg = seg;
         Cv.box = box;
-        cudaMemcpyAsync(P->curve_ctrl[ci], t.ctrl, sizeof(double) * 2 * Cv.nc,
-                        cudaMemcpyHostToDevice, st);
+        ups[nup++] = Upload{&P->curve_ctrl[ci], t.ctrl, sizeof(double) * 2 * Cv.nc};
       }
     }
     // geometry and coefficient
@@ -518,8 +525,25 @@ extern "C" int tw_patch_create(const tw_patch_desc *desc, tw_patch **out) {
     ALLOC(P->disc_slot[0], int32_t, A.nel + 1);
     ALLOC(P->disc_slot[1], int32_t, B.nel + 1);
     ALLOC(P->C, double, (size_t)A.nq * B.nq);
-    ALLOC(P->flag, int32_t, 4);
-    cudaMemsetAsync(P->flag, 0, 4 * sizeof(int32_t), st);
+    ups[nup++] = Upload{&P->flag, nullptr, 4 * sizeof(int32_t)};
+    for (int k = 0; k < nup; k++) packed += (ups[k].bytes + 15) & ~(size_t)15;
+    hpack = (char *)malloc(packed);
+    if (!hpack) {
+      set_error("tw_patch_create: out of host memory");
+      goto fail;
+    }
+    ALLOC(dpack, char, packed);
+    {
+      size_t off = 0;
+      for (int k = 0; k < nup; k++) {
+        if (ups[k].src) memcpy(hpack + off, ups[k].src, ups[k].bytes);
+        else memset(hpack + off, 0, ups[k].bytes);
+        void *dv = dpack + off;
+        memcpy(ups[k].dst, &dv, sizeof(void *));
+        off += (ups[k].bytes + 15) & ~(size_t)15;
+      }
+    }
+    cudaMemcpyAsync(dpack, hpack, packed, cudaMemcpyHostToDevice, st);
     {
       int ps = prof_start(st);
       rc = build_tables(P);
@@ -534,6 +558,7 @@ extern "C" int tw_patch_create(const tw_patch_desc *desc, tw_patch **out) {
     free(hoff[d]);
     free(htwo[d]);
   }
+  free(hpack);
   *out = P;
   return TW_OK;
 fail:
@@ -545,6 +570,7 @@ fail:
     free(hoff[d]);
     free(htwo[d]);
   }
+  free(hpack);
   return rc;
 }
 

@@ -1829,10 +1829,11 @@ int build_tables(tw_patch *P) {
   Dir &B = P->d[1];
   int p = P->p, p1 = p + 1;
   int rc;
-  int32_t *counters = (int32_t *)dalloc(P, 16 * sizeof(int32_t));
+  // counters[16] | tot32[8]: read back together after the classification
+  int32_t *counters = (int32_t *)dalloc(P, 24 * sizeof(int32_t));
   int64_t *tot64 = (int64_t *)dalloc(P, 4 * sizeof(int64_t));
-  int32_t *tot32 = (int32_t *)dalloc(P, 8 * sizeof(int32_t));
-  if (!counters || !tot64 || !tot32) return TW_ENOMEM;
+  if (!counters || !tot64) return TW_ENOMEM;
+  int32_t *tot32 = counters + 16;
   cudaMemsetAsync(counters, 0, 16 * sizeof(int32_t), st);
 
   // Gauss rules (p+1 for elements, qc for cut pieces), cached per process
@@ -1930,10 +1931,9 @@ int build_tables(tw_patch *P) {
   if ((rc = scan2_impl<int32_t>(dflag[0], dpos[0], A.nel + 1, tot32 + 4, dflag[1], dpos[1],
                                 B.nel + 1, tot32 + 5, st, P)))
     return rc;
-  int32_t hc[8];
-  int32_t hcount[4];
-  cudaMemcpyAsync(hc, tot32, sizeof(hc), cudaMemcpyDeviceToHost, st);
-  cudaMemcpyAsync(hcount, counters, sizeof(hcount), cudaMemcpyDeviceToHost, st);
+  int32_t h24[24];
+  cudaMemcpyAsync(h24, counters, sizeof(h24), cudaMemcpyDeviceToHost, st);
+  const int32_t *hcount = h24, *hc = h24 + 16;
   if ((rc = read_flag(P, "classification"))) return rc;
   P->n_rows = hc[0];
   P->ncutrows = hc[1];
