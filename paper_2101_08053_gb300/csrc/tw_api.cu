@@ -381,7 +381,7 @@ extern "C" int tw_patch_create(const tw_patch_desc *desc, tw_patch **out) {
     const void *src;
     size_t bytes;
   };
-  Upload ups[9 + TW_MAXCURVES];
+  Upload ups[11 + TW_MAXCURVES];
   int nup = 0;
   char *hpack = nullptr, *dpack = nullptr;
   size_t packed = 0;
@@ -526,6 +526,8 @@ extern "C" int tw_patch_create(const tw_patch_desc *desc, tw_patch **out) {
     ALLOC(P->disc_slot[1], int32_t, B.nel + 1);
     ALLOC(P->C, double, (size_t)A.nq * B.nq);
     ups[nup++] = Upload{&P->flag, nullptr, 4 * sizeof(int32_t)};
+    ups[nup++] = Upload{&P->cnt32, nullptr, 24 * sizeof(int32_t)};
+    ups[nup++] = Upload{&P->cnt64, nullptr, 4 * sizeof(int64_t)};
     for (int k = 0; k < nup; k++) packed += (ups[k].bytes + 15) & ~(size_t)15;
     hpack = (char *)malloc(packed);
     if (!hpack) {

@@ -822,6 +822,8 @@ struct tw_patch {
   int p, method, qc;
   int ktile[7];  // most WQ points of direction 0 under a tile of 2^k test functions i1
   int mixed;     // some knot span is empty (a repeated interior knot)
+  int32_t *cnt32;  // set-up counters and 32-bit scan totals (24, zeroed at creation)
+  int64_t *cnt64;  // 64-bit scan totals (4, zeroed at creation)
   tw::Dir d[2];
   const double *qrule;  // cut-piece Gauss rule (cached, not owned)
   tw::CurveSet curves;

@@ -292,9 +292,40 @@ static __device__ __noinline__ void gauss_tables_item(const Dir &D, int id) {
     for (int k = 0; k < p1; k++) gw3[i * p1 + k] = hw * N[i] * N[k];
 }
 
+// segment s of a closed cubic B-spline trimming curve (the periodic uniform
+// spline of its nc control points) in monomial form on u in [0, 1], with the
+// bounding box of its four control points
+__device__ __forceinline__ void curve_segment_item(const double *ctrl, int nc, double *seg,
+                                                   double *box, int s) {
+  for (int o = 0; o < 2; o++) {
+    double Q0 = ctrl[2 * (((s - 3) % nc + nc) % nc) + o];
+    double Q1 = ctrl[2 * (((s - 2) % nc + nc) % nc) + o];
+    double Q2 = ctrl[2 * (((s - 1) % nc + nc) % nc) + o];
+    double Q3 = ctrl[2 * s + o];
+    seg[8 * s + 4 * o + 0] = (Q0 + 4.0 * Q1 + Q2) / 6.0;
+    seg[8 * s + 4 * o + 1] = (Q2 - Q0) / 2.0;
+    seg[8 * s + 4 * o + 2] = (Q0 - 2.0 * Q1 + Q2) / 2.0;
+    seg[8 * s + 4 * o + 3] = (-Q0 + 3.0 * Q1 - 3.0 * Q2 + Q3) / 6.0;
+    box[4 * s + 2 * o] = fmin(fmin(Q0, Q1), fmin(Q2, Q3));
+    box[4 * s + 2 * o + 1] = fmax(fmax(Q0, Q1), fmax(Q2, Q3));
+  }
+}
+
+// the spline trimming curves whose segments a k_dir_tables launch forms
+// (curve k takes blocks blk[k] .. blk[k+1]-1 of that part)
+struct SegJobs {
+  int n;
+  int blk[TW_MAXCURVES + 1];
+  int nc[TW_MAXCURVES];
+  const double *ctrl[TW_MAXCURVES];
+  double *seg[TW_MAXCURVES], *box[TW_MAXCURVES];
+};
+
 // blocks [0, b0): elements (WQ points); [b0, b0 + b1): test functions (WQ
-// ranges); the rest: element Gauss points (Gauss tables)
-__global__ void __launch_bounds__(32) k_dir_tables(Dir D0, Dir D1, int b0, int b1) {
+// ranges); [b0 + b1, b0 + b1 + b2): element Gauss points (Gauss tables); the
+// rest (direction 0 only): the spline curves' segments
+__global__ void __launch_bounds__(32) k_dir_tables(Dir D0, Dir D1, int b0, int b1, int b2,
+                                                   SegJobs S) {
   const Dir &D = blockIdx.y ? D1 : D0;
   const int b = blockIdx.x;
   if (b < b0) {
@@ -303,9 +334,16 @@ __global__ void __launch_bounds__(32) k_dir_tables(Dir D0, Dir D1, int b0, int b
   } else if (b < b0 + b1) {
     const int i = (b - b0) * 32 + threadIdx.x;
     if (i < D.n) wq_ranges_item(D, i);
-  } else {
+  } else if (b < b0 + b1 + b2) {
     const int id = (b - b0 - b1) * 32 + threadIdx.x;
     if (id < D.nel * (D.p + 1)) gauss_tables_item(D, id);
+  } else if (blockIdx.y == 0) {
+    const int j = b - b0 - b1 - b2;
+    for (int k = 0; k < S.n; k++)
+      if (j >= S.blk[k] && j < S.blk[k + 1]) {
+        const int sg = (j - S.blk[k]) * 32 + threadIdx.x;
+        if (sg < S.nc[k]) curve_segment_item(S.ctrl[k], S.nc[k], S.seg[k], S.box[k], sg);
+      }
   }
 }
 
@@ -399,24 +437,8 @@ __global__ void __launch_bounds__(32 * TW_WQ_WARPS) k_wq_weights(Dir D0, Dir D1,
 }
 
 // ---------------------------------------------------------------------------
-// trimming curve: monomial segments of the periodic uniform cubic B-spline
+// trimming curve: its first point, the knot lines' crossings, its features
 
-__global__ void k_curve_segments(const double *ctrl, int nc, double *seg, double *box) {
-  int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= nc) return;
-  for (int o = 0; o < 2; o++) {
-    double Q0 = ctrl[2 * (((s - 3) % nc + nc) % nc) + o];
-    double Q1 = ctrl[2 * (((s - 2) % nc + nc) % nc) + o];
-    double Q2 = ctrl[2 * (((s - 1) % nc + nc) % nc) + o];
-    double Q3 = ctrl[2 * s + o];
-    seg[8 * s + 4 * o + 0] = (Q0 + 4.0 * Q1 + Q2) / 6.0;
-    seg[8 * s + 4 * o + 1] = (Q2 - Q0) / 2.0;
-    seg[8 * s + 4 * o + 2] = (Q0 - 2.0 * Q1 + Q2) / 2.0;
-    seg[8 * s + 4 * o + 3] = (-Q0 + 3.0 * Q1 - 3.0 * Q2 + Q3) / 6.0;
-    box[4 * s + 2 * o] = fmin(fmin(Q0, Q1), fmin(Q2, Q3));
-    box[4 * s + 2 * o + 1] = fmax(fmax(Q0, Q1), fmax(Q2, Q3));
-  }
-}
 
 __device__ void curve_point0(const Curve &C, double *xy) {
   if (C.kind == TW_TRIM_CIRCLE) {
@@ -599,9 +621,8 @@ __global__ void k_row_counts(Dir A, Dir B, const int32_t *act, int64_t *cnt, int
 }
 
 // sum-factorised det J on the WQ grid: stage A contracts direction 2
-__global__ void k_geo_stageA(Geo G, Dir A, Dir B, double *Gt) {
-  int id = blockIdx.x * blockDim.x + threadIdx.x;
-  if (id >= B.nq * A.n) return;
+__device__ __forceinline__ void geo_stageA_item(const Geo &G, const Dir &A, const Dir &B,
+                                                double *Gt, int id) {
   int k2 = id / A.n, i1 = id % A.n, p1 = B.p + 1;
   int e2 = B.qel[k2];
   double x = 0, y = 0, dx = 0, dy = 0;
@@ -755,6 +776,7 @@ __global__ void k_cut_breaks(Dir A, Dir B, const int32_t *cut_list, int ncut, in
                              const int *nfeat, int fcap, int32_t *cut_o, int32_t *nbr_out,
                              double *br_all, int64_t *nlines, int *flag) {
   const int ci = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ci == 0) nlines[ncut] = 0;  // closes the counts for their exclusive scan
   if (ci >= ncut) return;
   const int e = cut_list[ci];
   const int e1 = e % A.nel, e2 = e / A.nel;
@@ -873,6 +895,7 @@ __global__ void k_cut_lines(CurveSet C, Dir A, Dir B, const int32_t *cut_list, i
                             const int64_t *line_off, const int64_t *nl_tot, double *lh,
                             int32_t *ln, uint64_t *lvis, int64_t *lcnt, int *flag) {
   const int64_t L = *nl_tot;
+  if (blockIdx.x == 0 && threadIdx.x == 0) lcnt[L] = 0;  // closes the counts for their scan
   for (int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; li < L;
        li += (int64_t)gridDim.x * blockDim.x) {
     const CutLine cl = cut_line(A, B, cut_list, cut_o, br_all, line_off, ncut, q, qgx, qgw, li);
@@ -1085,13 +1108,9 @@ __global__ void __launch_bounds__(TW_CPT_THREADS)
 // spline geometry the control net is contracted over direction 1 once per
 // (g1, b) and then per point over b: the same sums, in the same order, as
 // coef_from, with 4 (p+1)^3 instead of 4 (p+1)^4 products per element.
-#define TW_GC_WARPS 4
-__global__ void __launch_bounds__(32 * TW_GC_WARPS)
-    k_gauss_c(Geo G, Dir A, Dir B, const int32_t *glist, int ng, double *gc) {
-  __shared__ double T[TW_GC_WARPS][TW_MAXP1][TW_MAXP1][4];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int sl = blockIdx.x * TW_GC_WARPS + w;
-  if (sl >= ng) return;
+__device__ __forceinline__ void gauss_c_warp(const Geo &G, const Dir &A, const Dir &B,
+                                             const int32_t *glist, double *gc, int sl, int lane,
+                                             double (*T)[TW_MAXP1][4]) {
   const int p = A.p, p1 = p + 1;
   const int e = glist[sl], e1 = e % A.nel, e2 = e / A.nel;
   const bool spline = G.geom_kind == TW_GEOM_SPLINE && G.coef_kind != TW_COEF_ONE;
@@ -1107,10 +1126,10 @@ __global__ void __launch_bounds__(32 * TW_GC_WARPS)
         sxb += pt[0] * v1[aa];
         syb += pt[1] * v1[aa];
       }
-      T[w][g1][bb][0] = sxa;
-      T[w][g1][bb][1] = sya;
-      T[w][g1][bb][2] = sxb;
-      T[w][g1][bb][3] = syb;
+      T[g1][bb][0] = sxa;
+      T[g1][bb][1] = sya;
+      T[g1][bb][2] = sxb;
+      T[g1][bb][3] = syb;
     }
     __syncwarp();
   }
@@ -1123,10 +1142,10 @@ __global__ void __launch_bounds__(32 * TW_GC_WARPS)
         const double *v2 = B.GB + (e2 * p1 + g2) * p1, *d2 = B.dGB + (e2 * p1 + g2) * p1;
         double xa = 0, ya = 0, xb = 0, yb = 0;
         for (int bb = 0; bb <= p; bb++) {
-          xa += T[w][g1][bb][0] * v2[bb];
-          ya += T[w][g1][bb][1] * v2[bb];
-          xb += T[w][g1][bb][2] * d2[bb];
-          yb += T[w][g1][bb][3] * d2[bb];
+          xa += T[g1][bb][0] * v2[bb];
+          ya += T[g1][bb][1] * v2[bb];
+          xb += T[g1][bb][2] * d2[bb];
+          yb += T[g1][bb][3] * d2[bb];
         }
         dj = xa * yb - xb * ya;
       }
@@ -1139,6 +1158,23 @@ __global__ void __launch_bounds__(32 * TW_GC_WARPS)
     }
     gc[(size_t)sl * p1 * p1 + g2 * p1 + g1] = c;
   }
+}
+
+// stage A of the grid's det J (blocks [0, nbA), a (k2, i1) per thread) and the
+// element-Gauss c tables (the other blocks, an element per warp) in one launch
+#define TW_GC_WARPS 8
+__global__ void __launch_bounds__(32 * TW_GC_WARPS)
+    k_geo_gauss_c(Geo G, Dir A, Dir B, double *Gt, int nbA, const int32_t *glist, int ng,
+                  double *gc) {
+  __shared__ double T[TW_GC_WARPS][TW_MAXP1][TW_MAXP1][4];
+  if ((int)blockIdx.x < nbA) {
+    const int id = blockIdx.x * blockDim.x + threadIdx.x;
+    if (id < B.nq * A.n) geo_stageA_item(G, A, B, Gt, id);
+    return;
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int sl = ((int)blockIdx.x - nbA) * TW_GC_WARPS + w;
+  if (sl < ng) gauss_c_warp(G, A, B, glist, gc, sl, lane, T[w]);
 }
 
 // ---------------------------------------------------------------------------
@@ -1829,12 +1865,11 @@ int build_tables(tw_patch *P) {
   Dir &B = P->d[1];
   int p = P->p, p1 = p + 1;
   int rc;
-  // counters[16] | tot32[8]: read back together after the classification
-  int32_t *counters = (int32_t *)dalloc(P, 24 * sizeof(int32_t));
-  int64_t *tot64 = (int64_t *)dalloc(P, 4 * sizeof(int64_t));
-  if (!counters || !tot64) return TW_ENOMEM;
+  // counters[16] | tot32[8] (read back together after the classification) and
+  // tot64[4]: zeroed by the patch's packed upload
+  int32_t *counters = P->cnt32;
+  int64_t *tot64 = P->cnt64;
   int32_t *tot32 = counters + 16;
-  cudaMemsetAsync(counters, 0, 16 * sizeof(int32_t), st);
 
   // Gauss rules (p+1 for elements, qc for cut pieces), cached per process
   const double *er = nullptr, *qr = nullptr;
@@ -1850,7 +1885,20 @@ int build_tables(tw_patch *P) {
   {
     const int b0 = (std::max(A.nel, B.nel) + 31) / 32, b1 = (std::max(A.n, B.n) + 31) / 32;
     const int b2 = (std::max(A.nel, B.nel) * p1 + 31) / 32;
-    k_dir_tables<<<dim3(b0 + b1 + b2, 2), 32, 0, st>>>(A, B, b0, b1);
+    SegJobs S;  // with the spline curves' segments
+    S.n = 0;
+    S.blk[0] = 0;
+    for (int ci = 0; ci < P->curves.n; ci++) {
+      const Curve &Cv = P->curves.c[ci];
+      if (Cv.kind != TW_TRIM_BSPLINE3) continue;
+      S.ctrl[S.n] = P->curve_ctrl[ci];
+      S.nc[S.n] = Cv.nc;
+      S.seg[S.n] = (double *)Cv.seg;
+      S.box[S.n] = (double *)Cv.box;
+      S.blk[S.n + 1] = S.blk[S.n] + (Cv.nc + 31) / 32;
+      S.n++;
+    }
+    k_dir_tables<<<dim3(b0 + b1 + b2 + S.blk[S.n], 2), 32, 0, st>>>(A, B, b0, b1, b2, S);
     TW_LAUNCH();
     const int nw = std::max(A.n, B.n);
     const int lda = std::max(A.qmax, B.qmax) + 1;
@@ -1859,12 +1907,6 @@ int build_tables(tw_patch *P) {
     k_wq_weights<<<dim3((nw + TW_WQ_SYS - 1) / TW_WQ_SYS, 2), 32 * TW_WQ_WARPS, wsm, st>>>(
         A, B, lda, P->flag);
     prof_stop(pw, TW_STAGE_WQW, st);
-    TW_LAUNCH();
-  }
-  for (int ci = 0; ci < P->curves.n; ci++) {
-    const Curve &Cv = P->curves.c[ci];
-    if (Cv.kind != TW_TRIM_BSPLINE3) continue;
-    k_curve_segments<<<G1(Cv.nc)>>>(P->curve_ctrl[ci], Cv.nc, (double *)Cv.seg, (double *)Cv.box);
     TW_LAUNCH();
   }
   if ((rc = check_cuda(cudaGetLastError(), "wq tables"))) return rc;
@@ -1975,17 +2017,21 @@ int build_tables(tw_patch *P) {
   if (P->geo.geom_kind == TW_GEOM_SPLINE && P->geo.coef_kind != TW_COEF_ONE) {
     Gt = (double *)dalloc(P, sizeof(double) * 4 * (size_t)B.nq * A.n);
     if (!Gt) return TW_ENOMEM;
-    k_geo_stageA<<<G1((int64_t)B.nq * A.n)>>>(P->geo, A, B, Gt);
-    TW_LAUNCH();
+  }
+  {  // stage A of the grid (spline geometry) with the element Gauss c tables
+    const int nbA = Gt ? (int)(((int64_t)B.nq * A.n + 255) / 256) : 0;
+    const int nbG = (P->ngslot + TW_GC_WARPS - 1) / TW_GC_WARPS;
+    if (nbA + nbG > 0) {
+      k_geo_gauss_c<<<nbA + nbG, 32 * TW_GC_WARPS, 0, st>>>(P->geo, A, B, Gt, nbA, glist,
+                                                           P->ngslot, P->gc);
+      TW_LAUNCH();
+    }
   }
   k_cgrid<<<G1((int64_t)A.nq * B.nq)>>>(P->geo, A, B, Gt, P->C);
   TW_LAUNCH();
-  // element Gauss c tables and element matrices (skipped above TW_GMAT_BUDGET
-  // bytes: the cut-row kernel then integrates those elements row by row)
+  // element matrices (skipped above TW_GMAT_BUDGET bytes: the cut-row kernel
+  // then integrates those elements row by row)
   if (P->ngslot > 0) {
-    k_gauss_c<<<(unsigned)((P->ngslot + TW_GC_WARPS - 1) / TW_GC_WARPS), 32 * TW_GC_WARPS, 0,
-                st>>>(P->geo, A, B, glist, P->ngslot, P->gc);
-    TW_LAUNCH();
     size_t nl = (size_t)p1 * p1;
     size_t bytes = (size_t)P->ngslot * nl * nl * sizeof(double);
     P->gmat = nullptr;
@@ -1999,7 +2045,6 @@ int build_tables(tw_patch *P) {
   // (crossings and point count), a scan, and the points written per line
   P->cut_o = (int32_t *)dalloc(P, sizeof(int32_t) * (P->ncut + 1));
   if (!P->cut_o) return TW_ENOMEM;
-  cudaMemsetAsync(tot64 + 1, 0, sizeof(int64_t), st);
   double *cbr = nullptr, *clh = nullptr;
   int64_t *line_off = nullptr, *lpos = nullptr;
   int32_t *cln = nullptr;
@@ -2011,7 +2056,6 @@ int build_tables(tw_patch *P) {
     int64_t *cnl = (int64_t *)dalloc(P, sizeof(int64_t) * (P->ncut + 1));
     line_off = (int64_t *)dalloc(P, sizeof(int64_t) * (P->ncut + 1));
     if (!cbr || !cnbr || !cnl || !line_off) return TW_ENOMEM;
-    cudaMemsetAsync(cnl + P->ncut, 0, sizeof(int64_t), st);
     k_cut_breaks<<<G32(P->ncut)>>>(A, B, P->cut_list, P->ncut, P->qc, lh, lnh, feat, nfeat, fcap,
                                   P->cut_o, cnbr, cbr, cnl, P->flag);
     TW_LAUNCH();
@@ -2024,7 +2068,7 @@ int build_tables(tw_patch *P) {
     int64_t *clc = (int64_t *)dalloc(P, sizeof(int64_t) * (nlines + 1));
     lpos = (int64_t *)dalloc(P, sizeof(int64_t) * (nlines + 1));
     if (!clh || !cln || !clv || !clc || !lpos) return TW_ENOMEM;
-    cudaMemsetAsync(clc + nlines, 0, sizeof(int64_t), st);
+    if (nlines == 0) cudaMemsetAsync(clc, 0, sizeof(int64_t), st);  // else closed by k_cut_lines
     if (nlines > 0) {
       // 64-thread blocks: a patch has only ~10^4 lines, and 256-thread
       // blocks would leave most SMs idle on this FP64-heavy kernel
