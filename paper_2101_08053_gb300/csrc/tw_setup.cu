@@ -242,22 +242,21 @@ __global__ void k_gauss_nodes(int q, double *x, double *w) {
 // out-of-line routine, so no function holds two inlined copies of the
 // Cox-de Boor triangle.
 
-// element e: its m = qoff[e+1] - qoff[e] WQ points (R1), uniform in the
-// element's interior, with the basis and derivatives there
-static __device__ __noinline__ void wq_points_item(const Dir &D, int e) {
+// WQ point j of element e (of its m = qoff[e+1] - qoff[e] <= p + 1 points,
+// R1): uniform in the element's interior, with the basis and derivatives there
+static __device__ __noinline__ void wq_point_item(const Dir &D, int e, int j) {
   const int p = D.p, k0 = D.qoff[e], m = D.qoff[e + 1] - k0;
+  if (j >= m) return;
   const double a = D.bp[e], b = D.bp[e + 1];
-  for (int j = 0; j < m; j++) {
-    const int k = k0 + j;
-    const double x = a + (b - a) * (double)(j + 1) / (double)(m + 1);
-    D.xq[k] = x;
-    D.qel[k] = e;
-    double N[TW_MAXP1], dN[TW_MAXP1];
-    basis_ders(D.U, e + p, x, p, N, dN);
-    for (int a2 = 0; a2 <= p; a2++) {
-      D.Bq[k * (p + 1) + a2] = N[a2];
-      D.dBq[k * (p + 1) + a2] = dN[a2];
-    }
+  const int k = k0 + j;
+  const double x = a + (b - a) * (double)(j + 1) / (double)(m + 1);
+  D.xq[k] = x;
+  D.qel[k] = e;
+  double N[TW_MAXP1], dN[TW_MAXP1];
+  basis_ders(D.U, e + p, x, p, N, dN);
+  for (int a2 = 0; a2 <= p; a2++) {
+    D.Bq[k * (p + 1) + a2] = N[a2];
+    D.dBq[k * (p + 1) + a2] = dN[a2];
   }
 }
 
@@ -321,7 +320,7 @@ struct SegJobs {
   double *seg[TW_MAXCURVES], *box[TW_MAXCURVES];
 };
 
-// blocks [0, b0): elements (WQ points); [b0, b0 + b1): test functions (WQ
+// blocks [0, b0): (element, point) pairs (WQ points); [b0, b0 + b1): test functions (WQ
 // ranges); [b0 + b1, b0 + b1 + b2): element Gauss points (Gauss tables); the
 // rest (direction 0 only): the spline curves' segments
 __global__ void __launch_bounds__(32) k_dir_tables(Dir D0, Dir D1, int b0, int b1, int b2,
@@ -329,8 +328,8 @@ __global__ void __launch_bounds__(32) k_dir_tables(Dir D0, Dir D1, int b0, int b
   const Dir &D = blockIdx.y ? D1 : D0;
   const int b = blockIdx.x;
   if (b < b0) {
-    const int e = b * 32 + threadIdx.x;
-    if (e < D.nel) wq_points_item(D, e);
+    const int t = b * 32 + threadIdx.x, e = t / (D.p + 1);
+    if (e < D.nel) wq_point_item(D, e, t - e * (D.p + 1));
   } else if (b < b0 + b1) {
     const int i = (b - b0) * 32 + threadIdx.x;
     if (i < D.n) wq_ranges_item(D, i);
@@ -948,17 +947,23 @@ __global__ void k_cut_lines(CurveSet C, Dir A, Dir B, const int32_t *cut_list, i
   }
 }
 
+// thread per Gauss line: its points; the thread of an element's first line
+// also writes the element's first point index (cut_off[ci]; every element of
+// a successful set-up has at least one line), line 0 the total (cut_off[ncut])
 __global__ void k_cut_write(Dir A, Dir B, const int32_t *cut_list, int ncut, int q,
                             const double *qgx, const double *qgw, const int32_t *cut_o,
                             const double *br_all, const int64_t *line_off, const int64_t *nl_tot,
                             const double *lh, const int32_t *ln, const uint64_t *lvis,
-                            const int64_t *lpos, double *pts) {
+                            const int64_t *lpos, const int64_t *npts, int64_t *cut_off,
+                            double *pts) {
   const int64_t L = *nl_tot;
   for (int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; li < L;
        li += (int64_t)gridDim.x * blockDim.x) {
+    const CutLine cl = cut_line(A, B, cut_list, cut_o, br_all, line_off, ncut, q, qgx, qgw, li);
+    if (line_off[cl.ci] == li) cut_off[cl.ci] = lpos[li];
+    if (li == 0) cut_off[ncut] = *npts;
     const int n = ln[li];
     if (n < 0) continue;
-    const CutLine cl = cut_line(A, B, cut_list, cut_o, br_all, line_off, ncut, q, qgx, qgw, li);
     const uint64_t vis = lvis[li];
     double *dst = pts + 3 * lpos[li];
     int64_t w0 = 0;
@@ -1883,7 +1888,7 @@ int build_tables(tw_patch *P) {
 
   // WQ layout, basis tables, weights (Eq. 5): both directions per launch
   {
-    const int b0 = (std::max(A.nel, B.nel) + 31) / 32, b1 = (std::max(A.n, B.n) + 31) / 32;
+    const int b0 = (std::max(A.nel, B.nel) * p1 + 31) / 32, b1 = (std::max(A.n, B.n) + 31) / 32;
     const int b2 = (std::max(A.nel, B.nel) * p1 + 31) / 32;
     SegJobs S;  // with the spline curves' segments
     S.n = 0;
@@ -2078,8 +2083,10 @@ int build_tables(tw_patch *P) {
       TW_LAUNCH();
     }
     if ((rc = exclusive_scan_i64(clc, lpos, nlines + 1, tot64 + 1, st, P))) return rc;
-    k_cut_offsets<<<G1(P->ncut + 1)>>>(P->ncut, line_off, lpos, tot64 + 1, P->cut_off);
-    TW_LAUNCH();
+    if (nlines == 0) {  // no Gauss lines (only after a breakpoint overflow): offsets here
+      k_cut_offsets<<<G1(P->ncut + 1)>>>(P->ncut, line_off, lpos, tot64 + 1, P->cut_off);
+      TW_LAUNCH();
+    }
   }
   int64_t h64[2] = {0, 0};
   cudaMemcpyAsync(h64, tot64, sizeof(h64), cudaMemcpyDeviceToHost, st);
@@ -2095,7 +2102,7 @@ int build_tables(tw_patch *P) {
     if (nlines > 0) {
       k_cut_write<<<(unsigned)((nlines + 63) / 64), 64, 0, st>>>(
           A, B, P->cut_list, P->ncut, P->qc, qgx, qgw, P->cut_o, cbr, line_off, tot64 + 2, clh,
-          cln, clv, lpos, P->cut_pts);
+          cln, clv, lpos, tot64 + 1, P->cut_off, P->cut_pts);
       TW_LAUNCH();
     }
     k_cut_point_tables<<<(P->ncut + TW_CPT_WARPS - 1) / TW_CPT_WARPS, TW_CPT_THREADS, 0, st>>>(
