@@ -1022,6 +1022,8 @@ __global__ void __launch_bounds__(TW_CPT_THREADS)
   // reciprocal knot differences of the element's outer and inner spans
   __shared__ double rcos[TW_CPT_WARPS][TW_SPAN_RC], rdos[TW_CPT_WARPS][TW_MAXP1];
   __shared__ double rcis[TW_CPT_WARPS][TW_SPAN_RC], rdis[TW_CPT_WARPS][TW_MAXP1];
+  // the element's (p+1) x (p+1) block of the geometry's control net, [b][a]
+  __shared__ double CPs[TW_CPT_WARPS][TW_MAXP1 * TW_MAXP1][2];
   double(*OV)[TW_MAXP1] = OVs[wib];
   double(*OD)[TW_MAXP1] = ODs[wib];
   double(*LS)[4][TW_MAXP1] = LSs[wib];
@@ -1034,6 +1036,13 @@ __global__ void __launch_bounds__(TW_CPT_THREADS)
                        ot ? rdo : rdi);
     }
   }
+  double(*CP)[2] = CPs[wib];
+  if (geo)
+    for (int t = lane; t < p1 * p1; t += 32) {
+      const double *pt = G.ctrl + 2 * ((size_t)(e2 + t / p1) * G.n1 + (e1 + t % p1));
+      CP[t][0] = pt[0];
+      CP[t][1] = pt[1];
+    }
   __syncwarp();
   const int64_t k0 = off[ci], k1 = off[ci + 1];
   for (int64_t base = k0; base < k1; base += 32) {
@@ -1062,8 +1071,7 @@ __global__ void __launch_bounds__(TW_CPT_THREADS)
         const int L = u / p1, j = u % p1;
         double sxd = 0, syd = 0, sxv = 0, syv = 0;
         for (int a = 0; a <= p; a++) {
-          const int ia = o == 0 ? e1 + a : e1 + j, ib = o == 0 ? e2 + j : e2 + a;
-          const double *pt = G.ctrl + 2 * ((size_t)ib * G.n1 + ia);
+          const double *pt = CP[o == 0 ? j * p1 + a : a * p1 + j];  // control point (e1+., e2+.)
           sxd += pt[0] * OD[L][a];
           syd += pt[1] * OD[L][a];
           sxv += pt[0] * OV[L][a];
@@ -1671,6 +1679,7 @@ __global__ void __launch_bounds__(32 * TW_CM_WARPS)
     if (ke == k) continue;  // a line with no visible interval (uniform)
     if (lane < U) {
       double sum = 0.0;
+#pragma unroll 4
       for (int64_t h = k; h < ke; h++) {
         const double *bv = Bt + (2 * h + in) * P1;
         sum = fma(wc[h] * bv[pa], bv[pb], sum);
