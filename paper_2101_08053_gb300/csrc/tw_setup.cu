@@ -753,7 +753,7 @@ __global__ void __launch_bounds__(32) k_curve_lines(CurveSet C, Dir A, Dir B, do
 // element's slot of cap points there (elements with more points leave cnt >
 // cap and are counted in *ovf); pass 1 writes them from off[ci] on.  Order:
 // piece, Gauss line, interval, inner Gauss point.  The element's edge
-// crossings come from the knot-line table (hits/nh of k_line_hits), the
+// crossings come from the knot-line table (hits/nh of k_curve_lines), the
 // tangent points and joints from the curve-wide feature list; only the Gauss
 // lines are solved here.  The visibility of a line's first interval is that of
 // its end on the element edge, i.e. the parity of the edge line's crossings
