@@ -43,13 +43,19 @@ __global__ void __launch_bounds__(128) k_cutrows(RowArgs a, const int32_t *__res
   cutrow_item<P, OutT>(a, g, col, val, smem);
 }
 
-// one warp per gather row
+// one warp per gather row; the launch also copies the patch's row pointer
+// (nrp entries) into the caller's CSR, grid-stride over all its threads
 template <int P, typename OutT>
 __global__ void __launch_bounds__(128) k_cutrows_gather(RowArgs a,
                                                         const int32_t *__restrict__ rows,
                                                         int nrows, int32_t *__restrict__ col,
-                                                        OutT *__restrict__ val) {
+                                                        OutT *__restrict__ val,
+                                                        int64_t *__restrict__ rp_out,
+                                                        int64_t nrp) {
   __shared__ const double *tab[4][(P + 1) * (P + 1)];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nrp;
+       i += (int64_t)gridDim.x * blockDim.x)
+    rp_out[i] = a.rp[i];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int r = blockIdx.x * 4 + wib;
   if (r >= nrows) return;  // the whole warp
@@ -272,7 +278,7 @@ static int launch_form(tw_patch *Pt, int precision, int64_t *rp, int32_t *col, v
     if (precision == TW_PREC_FP32) {
       if (gather)
         k_cutrows_gather<P, float><<<gw, 128, 0, s>>>(ra, Pt->cutrows, Pt->ncutrows, col,
-                                                      (float *)valv);
+                                                      (float *)valv, rp, Pt->n_rows + 1);
       if (sf)
         k_cutrows_sf<P, float><<<Pt->ncutrows, 128, 0, s>>>(ra, Pt->cutrows, Pt->ncutrows, col,
                                                              (float *)valv);
@@ -281,7 +287,8 @@ static int launch_form(tw_patch *Pt, int precision, int64_t *rp, int32_t *col, v
                                                           rsf);
     } else {
       if (gather)
-        k_cutrows_gather<P, double><<<gw, 128, 0, s>>>(ra, Pt->cutrows, Pt->ncutrows, col, val);
+        k_cutrows_gather<P, double><<<gw, 128, 0, s>>>(ra, Pt->cutrows, Pt->ncutrows, col, val,
+                                                       rp, Pt->n_rows + 1);
       if (sf)
         k_cutrows_sf<P, double><<<Pt->ncutrows, 128, 0, s>>>(ra, Pt->cutrows, Pt->ncutrows, col,
                                                               val);
@@ -292,15 +299,16 @@ static int launch_form(tw_patch *Pt, int precision, int64_t *rp, int32_t *col, v
     if (sf) TW_LAUNCH();
     if (block) TW_LAUNCH();
     prof_stop(ps, TW_STAGE_CUTROWS, s);
+    if (gather) return 0;  // the gather launch copied the row pointer
   }
+  const int64_t n = Pt->n_rows + 1;
+  k_copy_i64<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Pt->row_ptr, rp, n);
+  TW_LAUNCH();
   return 0;
 }
 
 int form_mass_launch(tw_patch *P, int precision, int64_t *rp, int32_t *col, void *val,
                      cudaStream_t s, bool rowsf) {
-  int64_t n = P->n_rows + 1;
-  k_copy_i64<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P->row_ptr, rp, n);
-  TW_LAUNCH();
   int rc;
   switch (P->p) {
     case 1: rc = launch_form<1>(P, precision, rp, col, val, s, rowsf); break;

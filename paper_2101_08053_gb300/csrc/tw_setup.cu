@@ -490,19 +490,15 @@ __device__ __forceinline__ int any_hit_in(const double *h, int n, double lo, dou
 // R8: an element is cut iff the curve meets its open box: a crossing inside
 // one of its four open edges (corner touches excluded), or the whole curve
 // inside it; otherwise visible iff its centre is
-__global__ void k_classify_elems(CurveSet C, Dir A, Dir B, const double *hits, const int *nh,
-                                 uint8_t *estate) {
-  int id = blockIdx.x * blockDim.x + threadIdx.x;
-  if (id >= A.nel * B.nel) return;
+__device__ __forceinline__ uint8_t classify_elem(const CurveSet &C, const Dir &A, const Dir &B,
+                                                 const double *hits, const int *nh, int id) {
   int e1 = id % A.nel, e2 = id / A.nel;
   double a1 = A.bp[e1], b1 = A.bp[e1 + 1], a2 = B.bp[e2], b2 = B.bp[e2 + 1];
   if (!(b1 > a1) || !(b2 > a2)) {  // R8: an empty span has no measure
-    estate[id] = TW_ELEM_EMPTY;
-    return;
+    return TW_ELEM_EMPTY;
   }
   if (C.n == 0) {
-    estate[id] = TW_ELEM_REGULAR;
-    return;
+    return TW_ELEM_REGULAR;
   }
   double d1 = TW_CORNER * (b1 - a1), d2 = TW_CORNER * (b2 - a2);
   const int hv = A.nel + 1;  // first horizontal knot line
@@ -536,7 +532,21 @@ __global__ void k_classify_elems(CurveSet C, Dir A, Dir B, const double *hits, c
     }
     st = vis ? TW_ELEM_REGULAR : TW_ELEM_INVISIBLE;
   }
+  return st;
+}
+
+// element states, with the flags of the cut elements (eflag) and, for the
+// Gauss method, of every regular element (gflag; for the hybrid and DWQ
+// methods the classification of the functions adds the regular elements
+// next to a cut function)
+__global__ void k_classify_elems(CurveSet C, Dir A, Dir B, const double *hits, const int *nh,
+                                 int method, uint8_t *estate, int32_t *eflag, int32_t *gflag) {
+  int id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= A.nel * B.nel) return;
+  const uint8_t st = classify_elem(C, A, B, hits, nh, id);
   estate[id] = st;
+  eflag[id] = st == TW_ELEM_CUT;
+  gflag[id] = method == TW_METHOD_GAUSS && st == TW_ELEM_REGULAR;
 }
 
 // function state from its support elements; active flag for the scan.  The
@@ -544,7 +554,8 @@ __global__ void k_classify_elems(CurveSet C, Dir A, Dir B, const double *hits, c
 // every DWQ choice to none (-1) for the stages after.
 __global__ void k_classify_funcs(Dir A, Dir B, const uint8_t *estate, uint8_t *fstate,
                                  int32_t *aflag, int method, int32_t *cflag, int32_t *counters,
-                                 int32_t *dflag0, int32_t *dflag1, int32_t *choice) {
+                                 int32_t *dflag0, int32_t *dflag1, int32_t *choice,
+                                 int32_t *gflag) {
   int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g <= A.nel) dflag0[g] = 0;
   if (g <= B.nel) dflag1[g] = 0;
@@ -567,6 +578,12 @@ __global__ void k_classify_funcs(Dir A, Dir B, const uint8_t *estate, uint8_t *f
   cflag[g] = c;
   if (st == TW_FUNC_CUT) atomicAdd(&counters[0], 1);
   if (st == TW_FUNC_INTERIOR) atomicAdd(&counters[1], 1);
+  // hybrid Gauss and DWQ: the regular elements of a cut function's support
+  // are integrated by Gauss (the same 1 from every such function)
+  if (st == TW_FUNC_CUT && (method == TW_METHOD_HYBRID || method == TW_METHOD_DWQ))
+    for (int e2 = max(0, i2 - B.p); e2 <= min(B.nel - 1, i2); e2++)
+      for (int e1 = max(0, i1 - A.p); e1 <= min(A.nel - 1, i1); e1++)
+        if (estate[e2 * A.nel + e1] == TW_ELEM_REGULAR) gflag[e2 * A.nel + e1] = 1;
 }
 
 // compacted lists from flags (exclusive scans already in pos), up to four per
@@ -1799,27 +1816,6 @@ static void launch_gauss_matrices_impl(tw_patch *P, const int32_t *glist, cudaSt
   TW_LAUNCH();
 }
 
-// per element: cut (for the cut list) and regular with Gauss points some row
-// uses (hybrid Gauss, DWQ rest, Gauss method: for the Gauss list)
-__global__ void k_elem_flags(Dir A, Dir B, const uint8_t *estate, const uint8_t *fstate,
-                             int method, int32_t *eflag, int32_t *gflag) {
-  int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= A.nel * B.nel) return;
-  const uint8_t es = estate[e];
-  eflag[e] = es == TW_ELEM_CUT;
-  int f = 0;
-  if (es == TW_ELEM_REGULAR && method != TW_METHOD_NAIVE) {
-    if (method == TW_METHOD_GAUSS) {
-      f = 1;
-    } else {
-      int e1 = e % A.nel, e2 = e / A.nel;
-      for (int b = 0; b <= B.p && !f; b++)
-        for (int a = 0; a <= A.p && !f; a++) f = fstate[(e2 + b) * A.n + (e1 + a)] == TW_FUNC_CUT;
-    }
-  }
-  gflag[e] = f;
-}
-
 // ---------------------------------------------------------------------------
 // host orchestration
 
@@ -1958,17 +1954,15 @@ int build_tables(tw_patch *P) {
                                             P->flag);
       TW_LAUNCH();
     }
-    k_classify_elems<<<G1(ne)>>>(P->curves, A, B, lh, lnh, P->estate);
+    k_classify_elems<<<G1(ne)>>>(P->curves, A, B, lh, lnh, P->method, P->estate, eflag, gflag);
     TW_LAUNCH();
   }
   k_classify_funcs<<<G1(nf)>>>(A, B, P->estate, P->fstate, aflag, P->method, cflag, counters,
-                               dflag[0], dflag[1], P->choice);
+                               dflag[0], dflag[1], P->choice, gflag);
   TW_LAUNCH();
   if ((rc = scan2_impl<int32_t>(aflag, P->act, nf, tot32 + 0, cflag, cpos, nf, tot32 + 1, st, P)))
     return rc;
-  // cut elements and the regular elements integrated by Gauss
-  k_elem_flags<<<G1(ne)>>>(A, B, P->estate, P->fstate, P->method, eflag, gflag);
-  TW_LAUNCH();
+  // cut elements and the regular elements integrated by Gauss (flagged above)
   if ((rc = scan2_impl<int32_t>(eflag, epos, ne, tot32 + 2, gflag, gpos, ne, tot32 + 3, st, P)))
     return rc;
   // DWQ choice (R7) and disc flags
